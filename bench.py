@@ -1,0 +1,320 @@
+"""Benchmark of the SE(2,N) inpainting hot path on GB300.
+
+One step = one whole inpaint of the 512x512, N=32 workload (seeded
+piecewise-smooth image, 80 % random mask plus 4-px bars every 32 px,
+beta = 0.25, 10 restoration intervals of 500 Crank-Nicolson steps, T = 2 per
+interval): orientation, lift, forward DFT, 10 x fused diffusion, 9 x
+(inverse DFT, static restoration, forward DFT), inverse DFT, projection,
+all through se2n_inpaint with the inputs resident in HBM.
+
+Metric: Mathieu updates per second, updates = frequencies x N x steps per
+interval x intervals = 512^2 * 32 * 500 * 10 per inpaint, over the whole
+inpaint time (value), plus ms per inpaint, the FP32 error against the FP64
+oracle, the diffusion kernel's roofline (FP32 ALU bound), the end-to-end
+number from host buffers (se2n_inpaint_host) and the oracle's CPU rate.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (torchrun): every rank inpaints its own image (replicas, weak
+scaling); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "Mathieu updates/s (M²·N·steps); ms per 512² N=32 inpaint, err vs FP64"
+UNIT = "updates/s"
+FLOPS_PER_UPDATE = 22          # per complex angle per CN step: 2 x (1 add + 5 FMA)
+GOLDEN = os.path.join(ROOT, "tests", "golden", "curves_noise_512_N32.npz")
+L2_FLUSH_BYTES = 256 << 20
+SM_COUNT, FP32_LANES_PER_SM = 152, 128
+
+
+def _workload():
+    return synth.workload_512()
+
+
+def _config(w, extra=None):
+    cfg = {
+        "workload": f"curves_noise_512_N32: {w.H}x{w.W} image, N={w.N}, beta={w.beta}, "
+                    f"{w.rounds} restoration intervals x {w.steps} CN steps, T={w.T}, eps={w.eps}, "
+                    "80% random mask + 4-px bars every 32 px",
+        "updates_per_step": w.updates(),
+        "l2": "flushed between timed steps (256 MiB write)",
+        "parallelism": "replicas",
+    }
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ----------------------------------------------------------------------------
+# clocks
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"se2n_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        try:
+            rows = [r.split(", ") for r in open(self.path).read().strip().splitlines()]
+        except OSError:
+            return None
+        rows = [r for r in rows if len(r) >= 9]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows]
+        mx = [float(r[2]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
+        load = [s for s in sm if s > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(mx), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows)}
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_1304_2062_gb300 import se2n
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    w = _workload()
+    f32 = w.f.astype(np.float32)
+    stream = torch.cuda.Stream(dev)
+    plan = se2n.se2n_plan_create(w.H, w.W, w.N, 0, stream)
+    prm = se2n.se2n_params_default(N=w.N, beta=w.beta, T=w.T, steps=w.steps, rounds=w.rounds, eps=w.eps,
+                                   sigma_smooth=w.sigma)
+    f_d = torch.tensor(f32, device=dev)
+    m_d = torch.tensor(w.mask, device=dev)
+    vol = torch.empty((w.N, w.H, w.W), dtype=torch.complex64, device=dev)
+    out = torch.empty((w.H, w.W), dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        se2n.se2n_inpaint(plan, f_d, m_d, None, prm, vol, out)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize(dev)
+        se2n.se2n_plan_profile(plan, True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        with ClockSampler(local_rank) as clocks:
+            for i in range(args.steps):
+                flush.zero_()
+                ev[i][0].record(stream)
+                step()
+                ev[i][1].record(stream)
+            torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        prof = se2n.se2n_plan_profile_read(plan, reset=True)
+        se2n.se2n_plan_profile(plan, False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * w.updates() * args.steps / (total_ms / 1e3)
+
+    # diffusion kernel roofline (FP32 ALU bound), from the live event timings
+    d_ms, d_calls = prof["diffuse"]
+    d_avg_s = d_ms / d_calls / 1e3
+    updates_per_launch = w.H * w.W * w.N * w.steps
+    achieved = FLOPS_PER_UPDATE * updates_per_launch / d_avg_s / 1e12
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
+    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "traffic": args.traffic,
+                "kernel": "k_diffuse<32,2,false>",
+                "flops_per_update": FLOPS_PER_UPDATE, "updates_per_launch": updates_per_launch,
+                "avg_launch_ms": round(d_avg_s * 1e3, 4),
+                "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop/FMA x 2070 MHz (derived, not measured)",
+                "diffuse_updates_per_s": updates_per_launch / d_avg_s,
+                "hbm_gbs_of_diffuse": round(16 * w.H * w.W * w.N / d_avg_s / 1e9, 1)}
+    stages = {k: {"ms_per_step": round(v[0] / args.steps, 4), "calls_per_step": v[1] / args.steps}
+              for k, v in prof.items() if k != "kernels"}
+    launches = int(prof["kernels"])
+
+    result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+              "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+              "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config(w),
+              "roofline": roofline, "gpu_launches": launches, "stages_ms": stages}
+    result["clocks"] = clocks.summary()
+
+    # end to end from pinned host buffers through se2n_inpaint_host
+    f_h = torch.tensor(f32).pin_memory()
+    m_h = torch.tensor(w.mask).pin_memory()
+    o_h = torch.empty((w.H, w.W), dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        se2n.se2n_inpaint_host(plan, f_h.data_ptr(), m_h.data_ptr(), prm, o_h.data_ptr())
+    e2e_ms = []
+    for _ in range(max(3, min(args.steps, 10))):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        se2n.se2n_inpaint_host(plan, f_h.data_ptr(), m_h.data_ptr(), prm, o_h.data_ptr())
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_step = statistics.median(e2e_ms)
+    result["e2e"] = {"value": world * w.updates() / (e2e_step / 1e3), "unit": UNIT,
+                     "ms_per_step": e2e_step, "h2d_bytes_per_step": f32.nbytes + w.mask.nbytes,
+                     "d2h_bytes_per_step": o_h.numel() * 4, "api": "se2n_inpaint_host (pinned host buffers)"}
+
+    # error of this result against the FP64 oracle (stored reference, same inputs)
+    if rank == 0 and os.path.exists(GOLDEN):
+        g = np.load(GOLDEN)
+        b_d = torch.tensor(g["bins"], device=dev)
+        with torch.cuda.stream(stream):
+            se2n.se2n_inpaint(plan, f_d, m_d, b_d, prm, vol, out)
+            own = torch.empty_like(b_d)
+            se2n.se2n_orient(plan, f_d, m_d, w.sigma, 1e-4, own)
+        torch.cuda.synchronize(dev)
+        got = out.cpu().numpy().astype(np.float64)
+        ref = g["out"].astype(np.float64)
+        result["err_vs_fp64"] = {
+            "rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+            "max_abs_over_max_f": float(np.abs(got - ref).max() / np.abs(w.f).max()),
+            "bins": "oracle's (FP64) bins given to both sides",
+            "own_bin_mismatches": int((own.cpu().numpy() != g["bins"]).sum()),
+            "oracle_seconds_for_this_result": float(g["oracle_seconds"][0])}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(w)
+    plan.close()
+    if dist:
+        dist.destroy_process_group()
+    return result
+
+
+# ----------------------------------------------------------------------------
+# the oracle as CPU baseline / reference arm
+# ----------------------------------------------------------------------------
+
+def _oracle_sample(w, steps, rounds):
+    import oracle
+    p = oracle.Params(N=w.N, beta=w.beta, T=w.T / w.rounds * rounds, steps=steps, rounds=rounds, eps=w.eps)
+    f = w.f.astype(np.float32).astype(np.float64)
+    t0 = time.perf_counter()
+    oracle.inpaint(f, w.mask, p)
+    dt = time.perf_counter() - t0
+    return w.H * w.W * w.N * steps * rounds, dt
+
+
+def cpu_baseline(w, steps=75, rounds=2):
+    upd, dt = _oracle_sample(w, steps, rounds)
+    return {"value": upd / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"the FP64 oracle's whole inpaint of the same 512x512 N=32 image with {rounds} intervals "
+                      f"x {steps} CN steps ({upd:.3g} updates, {dt:.1f} s), all host cores (OpenMP over "
+                      "frequencies, numpy FFTs)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    w = _workload()
+    steps, rounds = 20, 1
+    for _ in range(args.warmup):
+        _oracle_sample(w, steps, rounds)
+    times, upd = [], 0
+    for _ in range(args.steps):
+        upd, dt = _oracle_sample(w, steps, rounds)
+        times.append(dt)
+    total = sum(times)
+    value = upd * args.steps / total
+    sample = (f"each step: the FP64 oracle's inpaint of the 512x512 N=32 image with {rounds} interval x {steps} "
+              f"CN steps ({upd:.3g} updates), all host cores")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(w, {"reference_sample": f"{rounds} x {steps} steps per step"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per diffusion launch from an ncu capture of the current kernel")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", args.gpus))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.warmup < 3 and args.impl == "ours":
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+    else:
+        res = run_ours(args, rank, world, local_rank)
+    if rank == 0 and res is not None:
+        print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

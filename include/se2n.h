@@ -1,0 +1,248 @@
+/*
+ * se2n.h -- C ABI of the GB300 (sm_103a) library for the data-parallel hot
+ * path of SE(2,N) hypoelliptic-diffusion inpainting (Boscain, Chertovskih,
+ * Gauthier, Remizov, "Hypoelliptic diffusion and human vision: a
+ * semi-discrete new twist").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Units. The diffusion is written in pixel units,
+ *     dpsi_r/dt = -a_r^2 psi_r + beta (psi_{r+1} - 2 psi_r + psi_{r-1}),
+ *     a_r = wx cos(th_r) + wy sin(th_r),  wx = sin(2 pi l/W), wy = sin(2 pi k/H),
+ * for the DFT coefficient (k,l) of every angle plane. This is eq. (deceq)
+ * of the paper (Theorem 2) with unit mesh step; se2n_params_from_paper maps
+ * the paper's (alpha, T) on an M x M image to (beta, T) here exactly.
+ * Angles: th_r = pi r / N (directions, the paper's projectivised picture),
+ * or 2 pi r / N when the plan is created with angle_conv = 1.
+ *
+ * Layout. Images are row-major [H][W] (x = column, y = row); the lifted
+ * volume is row-major [N][H][W] of interleaved complex float (8 bytes per
+ * element, real then imaginary). Masks and bin maps are [H][W] uint8.
+ *
+ * Memory. Every pointer argument is DEVICE memory owned by the caller,
+ * except in se2n_inpaint_host. The plan owns only its cuFFT plans and small
+ * work buffers. Volumes must be 16-byte aligned, images 8-byte aligned, masks
+ * and bin maps 2-byte aligned (any cudaMalloc / torch allocation is).
+ *
+ * Streams and devices. Work is enqueued on the plan's stream (set at
+ * creation or by se2n_plan_set_stream) and every call returns after
+ * enqueueing, except se2n_inpaint_host which returns when the result is in
+ * host memory. Calls must be made with the plan's device current.
+ *
+ * Errors. Every call returns an se2n_status; nothing is thrown and no device
+ * code traps. Arguments are validated on the host before anything is
+ * enqueued; on SE2N_EINVAL nothing was enqueued. A CUDA or cuFFT failure
+ * returns SE2N_ECUDA / SE2N_ECUFFT and the CUDA error is kept for
+ * se2n_plan_last_cuda_error.
+ */
+#ifndef SE2N_H
+#define SE2N_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SE2N_API __attribute__((visibility("default")))
+#else
+#define SE2N_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum se2n_status {
+    SE2N_OK = 0,
+    SE2N_EINVAL = 1,        /* bad argument: null/host/misaligned pointer, size, parameter */
+    SE2N_ENOMEM = 2,        /* a device or host allocation failed */
+    SE2N_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+    SE2N_ECUFFT = 4,        /* a cuFFT call failed */
+    SE2N_EUNSUPPORTED = 5,  /* valid request this build has no kernel for (e.g. an N without an instantiation) */
+    SE2N_ENUMERIC = 6       /* parameters outside the range the FP32 scheme resolves */
+} se2n_status;
+
+/* Value of a bin-map entry for a "flat" pixel, lifted to every angle. */
+#define SE2N_BIN_FLAT 255
+
+/* Projection modes (Section 1.2.4 of the paper: maximum or average). */
+#define SE2N_PROJ_MAX 0
+#define SE2N_PROJ_MEAN 1
+
+/* se2n_diffuse flags. */
+#define SE2N_DIFFUSE_SM_FP64 1  /* Sherman-Morrison correction scalars in FP64 */
+
+/* Largest N this build has kernels for, and the N it supports. */
+#define SE2N_MAX_N 64
+
+typedef struct se2n_plan se2n_plan;
+
+/* Parameters of the whole method (pixel units).
+ *   T        total diffusion time; each of `rounds` restoration intervals
+ *            integrates T/rounds in `steps` Crank-Nicolson steps.
+ *   rounds   the paper's n (number of static-restoration treatments).
+ *   eps      the paper's epsilon in sigma = (eps h(0) + (1-eps) h(t_i)) / h(t_i).
+ *   sigma_smooth  Gaussian smoothing of the lift, in pixels.
+ *   flat_tol a pixel whose smoothed gradient is <= flat_tol * max|grad| is
+ *            lifted to every angle.
+ *   proj     SE2N_PROJ_MAX or SE2N_PROJ_MEAN.
+ *   final_mix  1: restore once more after the last interval (not in the paper).
+ *   guard    restoration divides by h(t_i) only where h(t_i) > guard.
+ *   diffuse_flags  SE2N_DIFFUSE_* flags passed to every diffusion. */
+typedef struct se2n_params {
+    int N;
+    double beta;
+    double T;
+    int steps;
+    int rounds;
+    double eps;
+    double sigma_smooth;
+    double flat_tol;
+    int proj;
+    int final_mix;
+    double guard;
+    int diffuse_flags;
+} se2n_params;
+
+/* Fill p with the defaults: N=32, beta=0.25, T=2, steps=100, rounds=1,
+ * eps=0.5, sigma_smooth=1, flat_tol=1e-4, proj=max, final_mix=0,
+ * guard=1e-12, diffuse_flags=0. SE2N_EINVAL if p is NULL. */
+SE2N_API se2n_status se2n_params_default(se2n_params *p);
+
+/* Map the paper's weighting alpha and time T_paper on an M x M image with N
+ * angles to pixel units. eq. (relation): beta_N = alpha (N / 2 pi)^2;
+ * eq. (FTE) has mesh step 1/sqrt(M) and a factor 1/2, hence
+ * beta = beta_N / M and T = (M/2) T_paper. SE2N_EINVAL for null outputs,
+ * M < 2, N < 3, alpha < 0 or T_paper < 0. */
+SE2N_API se2n_status se2n_params_from_paper(double alpha, double T_paper, int M, int N,
+                                   double *beta_out, double *T_out);
+
+/* Human-readable name of a status (static storage, never NULL). */
+SE2N_API const char *se2n_status_string(se2n_status s);
+
+/* Create a plan for H x W images with N angles. H and W even (>= 2), N one
+ * of 4, 8, 12, 16, 24, 30, 32, 48, 64 (else SE2N_EUNSUPPORTED), angle_conv 0
+ * (th_r = pi r/N) or 1 (2 pi r/N). stream is a cudaStream_t (NULL = the
+ * legacy default stream). Allocates the cuFFT plans (batch N over the
+ * volume, batch 1 and 2 over one plane) and a work area of about 24 H W
+ * bytes. *out is set only on SE2N_OK. */
+SE2N_API se2n_status se2n_plan_create(se2n_plan **out, int H, int W, int N, int angle_conv, void *stream);
+
+/* Release everything the plan owns (after synchronizing its stream). NULL is a no-op. */
+SE2N_API se2n_status se2n_plan_destroy(se2n_plan *plan);
+
+/* Change the stream later calls enqueue on. */
+SE2N_API se2n_status se2n_plan_set_stream(se2n_plan *plan, void *stream);
+
+/* Last CUDA error code (a cudaError_t value) seen by the plan, 0 if none. */
+SE2N_API int se2n_plan_last_cuda_error(const se2n_plan *plan);
+
+/* Direction bin of every pixel (Section 1.2.4, first item: smooth with a
+ * Gaussian, take the gradient, both in the FFT domain, lift to the closest
+ * angle). f0 = f * (mask != 0) is smoothed by exp(-2 pi^2 sigma^2 ((k/H)^2 +
+ * (l/W)^2)) and differentiated by i 2 pi l/W, i 2 pi k/H (signed
+ * frequencies, Nyquist term 0); the level-line direction phi = atan2(gy,gx) +
+ * pi/2 (mod pi) goes to bin floor(phi / dth + 1/2) mod N, dth = pi/N (or
+ * 2 pi/N). A pixel with |grad| <= flat_tol max|grad| gets SE2N_BIN_FLAT.
+ * f [H][W] float, mask [H][W] uint8 (nonzero = known), bins [H][W] uint8 out.
+ * sigma > 0, flat_tol >= 0. Decided in FP32: at pixels whose angle lies
+ * within FP32 rounding of a bin boundary, or whose |grad| lies within FP32
+ * rounding of the flat threshold, either neighbouring choice may come out. */
+SE2N_API se2n_status se2n_orient(se2n_plan *plan, const float *f, const uint8_t *mask, double sigma,
+                        double flat_tol, uint8_t *bins);
+
+/* Lift (Section 1.2.4): vol[r][y][x] = f0(x,y) if r is the pixel's bin (every
+ * r if the bin is SE2N_BIN_FLAT), else 0; imaginary parts 0. bins values must
+ * be < N or SE2N_BIN_FLAT (other values lift to no angle). vol is written
+ * completely (8 N H W bytes). */
+SE2N_API se2n_status se2n_lift(se2n_plan *plan, const float *f, const uint8_t *mask, const uint8_t *bins,
+                      void *vol);
+
+/* Unnormalised 2-D DFT of every angle plane, in place (Theorem 2): cuFFT C2C. */
+SE2N_API se2n_status se2n_forward(se2n_plan *plan, void *vol);
+
+/* Inverse 2-D DFT of every angle plane including 1/(H W), in place. */
+SE2N_API se2n_status se2n_inverse(se2n_plan *plan, void *vol);
+
+/* Crank-Nicolson integration of eq. (deceq) for every frequency of the
+ * transformed volume, in place: steps steps of dt = T/steps,
+ *     (I - dt/2 A) psi_new = (I + dt/2 A) psi,  A = -diag(a_r^2) + beta L,
+ * L the cyclic second difference (Section 4, remark after Theorem 2: CN, a
+ * tridiagonal matrix with two corner entries). All steps of a frequency run
+ * in one launch with the N-vector in registers; HBM is read and written
+ * once. beta > 0 (the jump rate of Section 2), T >= 0 (T = 0 is a no-op),
+ * steps >= 1, beta*dt >= 1e-30 and beta*dt <= 1e3 (else SE2N_ENUMERIC).
+ * flags: SE2N_DIFFUSE_SM_FP64 computes the corner (Sherman-Morrison)
+ * correction scalars in FP64. */
+SE2N_API se2n_status se2n_diffuse(se2n_plan *plan, void *vol_hat, double beta, double T, int steps, int flags);
+
+/* Static restoration (Section 5, SR) on the real volume, in place: with
+ * h(t) = max_r Re vol_r and h(0) = max_r of the lift of (f, mask, bins), a
+ * known pixel (mask != 0) with h(t) > guard has every angle scaled by
+ * sigma = (eps h(0) + (1-eps) h(t)) / h(t); a known pixel with h(t) <= guard
+ * becomes eps * lift + (1-eps) * Re vol. Imaginary parts are set to 0
+ * everywhere. 0 <= eps <= 1. */
+SE2N_API se2n_status se2n_mix(se2n_plan *plan, void *vol, const float *f, const uint8_t *mask,
+                     const uint8_t *bins, double eps, double guard);
+
+/* Projection to the image (Section 1.2.4): out = max_r Re vol_r
+ * (SE2N_PROJ_MAX) or the mean over r (SE2N_PROJ_MEAN). out [H][W] float. */
+SE2N_API se2n_status se2n_project(se2n_plan *plan, const void *vol, int proj, float *out);
+
+/* The whole method (Section 5, static restoration): bins (from se2n_orient
+ * with p->sigma_smooth and p->flat_tol, or the caller's bins_in if not NULL),
+ * lift, forward DFT, then p->rounds intervals of T/rounds: the first from
+ * the lift, each later one from the restored state (the restoration at t_0
+ * is the identity); the state at T is inverted, optionally restored once
+ * more (final_mix), and projected to out. vol [N][H][W] complex is caller
+ * scratch, overwritten; out [H][W] float. p->N must equal the plan's N. */
+SE2N_API se2n_status se2n_inpaint(se2n_plan *plan, const float *f, const uint8_t *mask, const uint8_t *bins_in,
+                         const se2n_params *p, void *vol, float *out);
+
+/* se2n_inpaint from HOST buffers: copies f and mask to the device, runs the
+ * method on plan-owned device buffers (allocated on the first call: the
+ * volume, 8 N H W bytes, plus the images) and copies the projected image
+ * back to out_host. Returns when out_host holds the result. f_host, mask_host
+ * and out_host are host memory (pinned memory makes the copies faster). */
+SE2N_API se2n_status se2n_inpaint_host(se2n_plan *plan, const float *f_host, const uint8_t *mask_host,
+                              const se2n_params *p, float *out_host);
+
+/* Tuning of the diffusion launch (used by the autotuner): threads per
+ * frequency P (1, 2 or 4; 0 = default for the plan's N), threads per block
+ * (multiple of 32, <= 1024; 0 = 128) and blocks (0 = as many as fit on the
+ * device at once). SE2N_EUNSUPPORTED if no kernel exists for (N, P). */
+SE2N_API se2n_status se2n_plan_tune_diffuse(se2n_plan *plan, int threads_per_freq, int block_threads, int blocks);
+
+/* Resource use of the current diffusion kernel choice: registers per thread,
+ * resident blocks per SM and threads per frequency. Any output may be NULL. */
+SE2N_API se2n_status se2n_plan_diffuse_info(se2n_plan *plan, int *regs_per_thread, int *blocks_per_sm,
+                                   int *threads_per_freq);
+
+/* Stage timing. When enabled, the plan brackets every stage it enqueues
+ * with CUDA events on its stream and counts its own kernel launches (cuFFT's
+ * kernels are not counted as launches of this library). Stages: */
+#define SE2N_STAGE_ORIENT 0
+#define SE2N_STAGE_LIFT 1
+#define SE2N_STAGE_FFT 2      /* forward and inverse DFTs (cuFFT) */
+#define SE2N_STAGE_DIFFUSE 3
+#define SE2N_STAGE_MIX 4
+#define SE2N_STAGE_PROJECT 5
+#define SE2N_NUM_STAGES 6
+
+typedef struct se2n_profile {
+    double ms[SE2N_NUM_STAGES];       /* device time accumulated per stage, milliseconds */
+    long long calls[SE2N_NUM_STAGES]; /* stage executions timed */
+    long long kernels;                /* kernels of this library launched (counted even when timing is off) */
+} se2n_profile;
+
+/* Turn stage timing on (1) or off (0); either way the accumulators are reset. */
+SE2N_API se2n_status se2n_plan_profile(se2n_plan *plan, int enable);
+
+/* Read the accumulated timings (synchronizes the plan's stream first);
+ * reset != 0 clears them afterwards. */
+SE2N_API se2n_status se2n_plan_profile_read(se2n_plan *plan, se2n_profile *out, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SE2N_H */

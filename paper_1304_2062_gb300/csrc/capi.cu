@@ -1,0 +1,493 @@
+// C ABI of libse2n: plans, argument validation, cuFFT wiring and the
+// orchestration of the whole inpainting method. Every check happens on the
+// host before anything is enqueued; device code never traps.
+#include <math.h>
+#include <new>
+#include <stdint.h>
+
+#include "se2n_internal.h"
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+se2n_status cuda_status(se2n_plan *plan, cudaError_t e) {
+    if (e == cudaSuccess) return SE2N_OK;
+    if (plan) plan->last_cuda_error = (int)e;
+    return e == cudaErrorMemoryAllocation ? SE2N_ENOMEM : SE2N_ECUDA;
+}
+
+se2n_status cufft_status(cufftResult r) {
+    if (r == CUFFT_SUCCESS) return SE2N_OK;
+    return r == CUFFT_ALLOC_FAILED ? SE2N_ENOMEM : SE2N_ECUFFT;
+}
+
+// Brackets one stage with CUDA events on the plan's stream when timing is on.
+struct StageTimer {
+    se2n_plan *plan;
+    int stage;
+    bool on;
+    StageTimer(se2n_plan *p, int s) : plan(p), stage(s), on(p->profiling) {
+        if (!on) return;
+        std::vector<cudaEvent_t> &ev = plan->stage_ev[stage];
+        const size_t need = 2 * (size_t)plan->stage_used[stage] + 2;
+        while (ev.size() < need) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                (void)cudaGetLastError();
+                on = false;
+                return;
+            }
+            ev.push_back(e);
+        }
+        cudaEventRecord(ev[need - 2], plan->stream);
+    }
+    ~StageTimer() {
+        if (!on) return;
+        const int u = plan->stage_used[stage]++;
+        cudaEventRecord(plan->stage_ev[stage][2 * u + 1], plan->stream);
+    }
+};
+
+#define SE2N_TRY(expr)                      \
+    do {                                    \
+        se2n_status _s = (expr);            \
+        if (_s != SE2N_OK) return _s;       \
+    } while (0)
+
+// Device (or managed) memory the current device can address; rejects host
+// pointers, which a kernel could not use.
+bool device_ptr(const void *p, size_t align) {
+    if (!p || ((uintptr_t)p % align) != 0) return false;
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+se2n_status check_plan(se2n_plan *plan) {
+    if (!plan) return SE2N_EINVAL;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != plan->device) return SE2N_EINVAL;
+    return SE2N_OK;
+}
+
+se2n_status diffuse_impl(se2n_plan *plan, float2 *vol, double beta, double T, int steps, int flags) {
+    if (!(beta > 0.0) || !(T >= 0.0) || steps < 1 || !isfinite(beta) || !isfinite(T)) return SE2N_EINVAL;
+    if (flags & ~SE2N_DIFFUSE_SM_FP64) return SE2N_EINVAL;
+    if (T == 0.0) return SE2N_OK;
+    const double dt = T / steps;
+    const double bdt = beta * dt;
+    if (!(bdt >= 1e-30 && bdt <= 1e3)) return SE2N_ENUMERIC;
+    const bool fp64 = (flags & SE2N_DIFFUSE_SM_FP64) != 0;
+
+    DiffuseArgs a;
+    a.vol = vol;
+    a.HW = plan->HW;
+    a.H = plan->H;
+    a.W = plan->W;
+    a.steps = steps;
+    a.inv_c_d = 2.0 / bdt;
+    a.inv_beta_d = 1.0 / beta;
+    a.inv_c = (float)a.inv_c_d;
+    a.inv_beta = (float)a.inv_beta_d;
+    const double dth = (plan->angle_conv ? 2.0 : 1.0) * kPi / plan->N;
+    for (int r = 0; r < SE2N_MAX_N; ++r) {
+        a.cs[r] = r < plan->N ? (float)cos(dth * r) : 0.0f;
+        a.sn[r] = r < plan->N ? (float)sin(dth * r) : 0.0f;
+    }
+    const int P = plan->diffuse_P;
+    const int block = plan->diffuse_block;
+    int blocks = plan->diffuse_blocks;
+    if (blocks <= 0) {
+        int per_sm = 0;
+        cudaError_t e = se2n_diffuse_occupancy(plan->N, P, fp64, block, &per_sm, nullptr);
+        if (e != cudaSuccess) return cuda_status(plan, e);
+        if (per_sm < 1) per_sm = 1;
+        blocks = plan->num_sms * per_sm;
+    }
+    const long long need = (plan->HW * P + block - 1) / block;
+    if (blocks > need) blocks = (int)need;
+    if (blocks < 1) blocks = 1;
+    StageTimer timer(plan, SE2N_STAGE_DIFFUSE);
+    plan->kernels += 1;
+    cudaError_t e = se2n_launch_diffuse(plan->N, P, fp64, a, block, blocks, plan->stream);
+    if (e == cudaErrorInvalidValue && !se2n_diffuse_has(plan->N, P)) return SE2N_EUNSUPPORTED;
+    return cuda_status(plan, e);
+}
+
+se2n_status fft(se2n_plan *plan, cufftHandle h, float2 *data, int dir) {
+    StageTimer timer(plan, SE2N_STAGE_FFT);
+    return cufft_status(cufftExecC2C(h, (cufftComplex *)data, (cufftComplex *)data, dir));
+}
+
+se2n_status orient_impl(se2n_plan *plan, const float *f, const uint8_t *mask, double sigma, double flat_tol,
+                        uint8_t *bins) {
+    if (!(sigma > 0.0) || !(flat_tol >= 0.0) || !isfinite(sigma) || !isfinite(flat_tol)) return SE2N_EINVAL;
+    const long long HW = plan->HW;
+    float2 *spec = plan->spec;
+    StageTimer timer(plan, SE2N_STAGE_ORIENT);
+    plan->kernels += 4;
+    SE2N_TRY(cuda_status(plan, se2n_launch_orient_prep(f, mask, spec, HW, plan->stream)));
+    SE2N_TRY(fft(plan, plan->fft_one, spec, CUFFT_FORWARD));
+    SE2N_TRY(cuda_status(plan, se2n_launch_grad_spec(spec, plan->H, plan->W, (float)sigma, plan->stream)));
+    SE2N_TRY(fft(plan, plan->fft_two, spec + HW, CUFFT_INVERSE));
+    SE2N_TRY(cuda_status(plan, cudaMemsetAsync(plan->gmax, 0, sizeof(unsigned int), plan->stream)));
+    SE2N_TRY(cuda_status(plan, se2n_launch_grad_max(spec + HW, spec + 2 * HW, HW, plan->gmax, plan->stream)));
+    const float tol2 = (float)(flat_tol * flat_tol);
+    return cuda_status(plan, se2n_launch_bins(spec + HW, spec + 2 * HW, HW, plan->gmax, tol2, plan->N,
+                                              plan->angle_conv, bins, plan->stream));
+}
+
+se2n_status lift_impl(se2n_plan *plan, const float *f, const uint8_t *mask, const uint8_t *bins, float2 *vol) {
+    StageTimer timer(plan, SE2N_STAGE_LIFT);
+    plan->kernels += 1;
+    return cuda_status(plan, se2n_launch_lift(f, mask, bins, vol, plan->HW, plan->N, plan->stream));
+}
+
+se2n_status mix_impl(se2n_plan *plan, float2 *vol, const float *f, const uint8_t *mask, const uint8_t *bins,
+                     float scale, float eps, float guard) {
+    StageTimer timer(plan, SE2N_STAGE_MIX);
+    plan->kernels += 1;
+    return cuda_status(plan, se2n_launch_mix(vol, f, mask, bins, plan->HW, plan->N, scale, eps, guard, plan->stream));
+}
+
+se2n_status project_impl(se2n_plan *plan, const float2 *vol, float scale, int proj, float *out) {
+    StageTimer timer(plan, SE2N_STAGE_PROJECT);
+    plan->kernels += 1;
+    return cuda_status(plan, se2n_launch_project(vol, plan->HW, plan->N, scale, proj, out, plan->stream));
+}
+
+se2n_status check_params(const se2n_plan *plan, const se2n_params *p) {
+    if (!p) return SE2N_EINVAL;
+    if (p->N != plan->N || !(p->beta > 0.0) || !(p->T >= 0.0) || p->steps < 1 || p->rounds < 1) return SE2N_EINVAL;
+    if (!(p->eps >= 0.0 && p->eps <= 1.0) || !(p->sigma_smooth > 0.0) || !(p->flat_tol >= 0.0)) return SE2N_EINVAL;
+    if ((p->proj != SE2N_PROJ_MAX && p->proj != SE2N_PROJ_MEAN) || (p->final_mix != 0 && p->final_mix != 1))
+        return SE2N_EINVAL;
+    if (!(p->guard >= 0.0) || (p->diffuse_flags & ~SE2N_DIFFUSE_SM_FP64)) return SE2N_EINVAL;
+    if (!isfinite(p->beta) || !isfinite(p->T) || !isfinite(p->sigma_smooth) || !isfinite(p->guard))
+        return SE2N_EINVAL;
+    if (p->T > 0.0) {
+        const double bdt = p->beta * (p->T / p->rounds) / p->steps;
+        if (!(bdt >= 1e-30 && bdt <= 1e3)) return SE2N_ENUMERIC;
+    }
+    return SE2N_OK;
+}
+
+se2n_status inpaint_impl(se2n_plan *plan, const float *f, const uint8_t *mask, const uint8_t *bins_in,
+                         const se2n_params *p, float2 *vol, float *out) {
+    const long long HW = plan->HW;
+    const int N = plan->N;
+    const uint8_t *bins = bins_in;
+    if (!bins) {
+        SE2N_TRY(orient_impl(plan, f, mask, p->sigma_smooth, p->flat_tol, plan->bins));
+        bins = plan->bins;
+    }
+    const double Tr = p->T / p->rounds;
+    const float inv_hw = (float)(1.0 / (double)HW);
+    SE2N_TRY(lift_impl(plan, f, mask, bins, vol));
+    SE2N_TRY(fft(plan, plan->fft_vol, vol, CUFFT_FORWARD));
+    SE2N_TRY(diffuse_impl(plan, vol, p->beta, Tr, p->steps, p->diffuse_flags));
+    for (int i = 1; i < p->rounds; ++i) {
+        // inverse DFT; its 1/(H W) is folded into the restoration kernel
+        SE2N_TRY(fft(plan, plan->fft_vol, vol, CUFFT_INVERSE));
+        SE2N_TRY(mix_impl(plan, vol, f, mask, bins, inv_hw, (float)p->eps, (float)p->guard));
+        SE2N_TRY(fft(plan, plan->fft_vol, vol, CUFFT_FORWARD));
+        SE2N_TRY(diffuse_impl(plan, vol, p->beta, Tr, p->steps, p->diffuse_flags));
+    }
+    SE2N_TRY(fft(plan, plan->fft_vol, vol, CUFFT_INVERSE));
+    float scale = inv_hw;
+    if (p->final_mix) {
+        SE2N_TRY(mix_impl(plan, vol, f, mask, bins, inv_hw, (float)p->eps, (float)p->guard));
+        scale = 1.0f;
+    }
+    return project_impl(plan, vol, scale, p->proj, out);
+}
+
+void free_plan(se2n_plan *plan) {
+    if (plan->fft_vol) cufftDestroy(plan->fft_vol);
+    if (plan->fft_one) cufftDestroy(plan->fft_one);
+    if (plan->fft_two) cufftDestroy(plan->fft_two);
+    cudaFree(plan->spec);
+    cudaFree(plan->gmax);
+    cudaFree(plan->bins);
+    cudaFree(plan->h_f);
+    cudaFree(plan->h_out);
+    cudaFree(plan->h_mask);
+    cudaFree(plan->h_vol);
+    for (int st = 0; st < SE2N_NUM_STAGES; ++st)
+        for (cudaEvent_t e : plan->stage_ev[st]) cudaEventDestroy(e);
+    delete plan;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *se2n_status_string(se2n_status s) {
+    switch (s) {
+        case SE2N_OK: return "SE2N_OK";
+        case SE2N_EINVAL: return "SE2N_EINVAL: invalid argument";
+        case SE2N_ENOMEM: return "SE2N_ENOMEM: allocation failed";
+        case SE2N_ECUDA: return "SE2N_ECUDA: CUDA error";
+        case SE2N_ECUFFT: return "SE2N_ECUFFT: cuFFT error";
+        case SE2N_EUNSUPPORTED: return "SE2N_EUNSUPPORTED: no kernel for this configuration";
+        case SE2N_ENUMERIC: return "SE2N_ENUMERIC: beta*dt outside the range the FP32 scheme resolves";
+    }
+    return "SE2N: unknown status";
+}
+
+se2n_status se2n_params_default(se2n_params *p) {
+    if (!p) return SE2N_EINVAL;
+    p->N = 32;
+    p->beta = 0.25;
+    p->T = 2.0;
+    p->steps = 100;
+    p->rounds = 1;
+    p->eps = 0.5;
+    p->sigma_smooth = 1.0;
+    p->flat_tol = 1e-4;
+    p->proj = SE2N_PROJ_MAX;
+    p->final_mix = 0;
+    p->guard = 1e-12;
+    p->diffuse_flags = 0;
+    return SE2N_OK;
+}
+
+se2n_status se2n_params_from_paper(double alpha, double T_paper, int M, int N, double *beta_out,
+                                   double *T_out) {
+    if (!beta_out || !T_out || M < 2 || N < 3 || !(alpha >= 0.0) || !(T_paper >= 0.0)) return SE2N_EINVAL;
+    const double beta_N = alpha * (N / (2.0 * kPi)) * (N / (2.0 * kPi));
+    *beta_out = beta_N / M;
+    *T_out = 0.5 * M * T_paper;
+    return SE2N_OK;
+}
+
+se2n_status se2n_plan_create(se2n_plan **out, int H, int W, int N, int angle_conv, void *stream) {
+    if (!out || H < 2 || W < 2 || (H % 2) || (W % 2)) return SE2N_EINVAL;
+    if ((long long)H * W > (1LL << 28)) return SE2N_EINVAL;
+    if (N < 3 || N > SE2N_MAX_N || (angle_conv != 0 && angle_conv != 1)) return SE2N_EINVAL;
+    if (!se2n_diffuse_has(N, se2n_diffuse_default_P(N))) return SE2N_EUNSUPPORTED;
+    se2n_plan *plan = new (std::nothrow) se2n_plan();
+    if (!plan) return SE2N_ENOMEM;
+    plan->H = H;
+    plan->W = W;
+    plan->N = N;
+    plan->angle_conv = angle_conv;
+    plan->HW = (long long)H * W;
+    plan->stream = (cudaStream_t)stream;
+    plan->diffuse_P = se2n_diffuse_default_P(N);
+    plan->diffuse_block = 128;
+    plan->diffuse_blocks = 0;
+    cudaError_t e = cudaGetDevice(&plan->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&plan->num_sms, cudaDevAttrMultiProcessorCount, plan->device);
+    if (e != cudaSuccess) {
+        delete plan;
+        return SE2N_ECUDA;
+    }
+    int n2[2] = {H, W};
+    cufftResult r = cufftPlanMany(&plan->fft_vol, 2, n2, nullptr, 1, (int)plan->HW, nullptr, 1, (int)plan->HW,
+                                  CUFFT_C2C, N);
+    if (r == CUFFT_SUCCESS) r = cufftPlan2d(&plan->fft_one, H, W, CUFFT_C2C);
+    if (r == CUFFT_SUCCESS)
+        r = cufftPlanMany(&plan->fft_two, 2, n2, nullptr, 1, (int)plan->HW, nullptr, 1, (int)plan->HW, CUFFT_C2C, 2);
+    if (r != CUFFT_SUCCESS) {
+        free_plan(plan);
+        return cufft_status(r);
+    }
+    e = cudaMalloc(&plan->spec, sizeof(float2) * 3 * plan->HW);
+    if (e == cudaSuccess) e = cudaMalloc(&plan->gmax, 256);
+    if (e == cudaSuccess) e = cudaMalloc(&plan->bins, plan->HW);
+    if (e != cudaSuccess) {
+        free_plan(plan);
+        return e == cudaErrorMemoryAllocation ? SE2N_ENOMEM : SE2N_ECUDA;
+    }
+    if (cufftSetStream(plan->fft_vol, plan->stream) != CUFFT_SUCCESS ||
+        cufftSetStream(plan->fft_one, plan->stream) != CUFFT_SUCCESS ||
+        cufftSetStream(plan->fft_two, plan->stream) != CUFFT_SUCCESS) {
+        free_plan(plan);
+        return SE2N_ECUFFT;
+    }
+    *out = plan;
+    return SE2N_OK;
+}
+
+se2n_status se2n_plan_destroy(se2n_plan *plan) {
+    if (!plan) return SE2N_OK;
+    cudaStreamSynchronize(plan->stream);
+    free_plan(plan);
+    return SE2N_OK;
+}
+
+se2n_status se2n_plan_set_stream(se2n_plan *plan, void *stream) {
+    SE2N_TRY(check_plan(plan));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cufftSetStream(plan->fft_vol, s) != CUFFT_SUCCESS || cufftSetStream(plan->fft_one, s) != CUFFT_SUCCESS ||
+        cufftSetStream(plan->fft_two, s) != CUFFT_SUCCESS)
+        return SE2N_ECUFFT;
+    plan->stream = s;
+    return SE2N_OK;
+}
+
+int se2n_plan_last_cuda_error(const se2n_plan *plan) { return plan ? plan->last_cuda_error : 0; }
+
+se2n_status se2n_orient(se2n_plan *plan, const float *f, const uint8_t *mask, double sigma, double flat_tol,
+                        uint8_t *bins) {
+    SE2N_TRY(check_plan(plan));
+    if (!device_ptr(f, 8) || !device_ptr(mask, 2) || !device_ptr(bins, 2)) return SE2N_EINVAL;
+    return orient_impl(plan, f, mask, sigma, flat_tol, bins);
+}
+
+se2n_status se2n_lift(se2n_plan *plan, const float *f, const uint8_t *mask, const uint8_t *bins, void *vol) {
+    SE2N_TRY(check_plan(plan));
+    if (!device_ptr(f, 8) || !device_ptr(mask, 2) || !device_ptr(bins, 2) || !device_ptr(vol, 16))
+        return SE2N_EINVAL;
+    return lift_impl(plan, f, mask, bins, (float2 *)vol);
+}
+
+se2n_status se2n_forward(se2n_plan *plan, void *vol) {
+    SE2N_TRY(check_plan(plan));
+    if (!device_ptr(vol, 16)) return SE2N_EINVAL;
+    return fft(plan, plan->fft_vol, (float2 *)vol, CUFFT_FORWARD);
+}
+
+se2n_status se2n_inverse(se2n_plan *plan, void *vol) {
+    SE2N_TRY(check_plan(plan));
+    if (!device_ptr(vol, 16)) return SE2N_EINVAL;
+    SE2N_TRY(fft(plan, plan->fft_vol, (float2 *)vol, CUFFT_INVERSE));
+    StageTimer timer(plan, SE2N_STAGE_FFT);
+    plan->kernels += 1;
+    return cuda_status(plan, se2n_launch_scale((float2 *)vol, plan->HW * plan->N, (float)(1.0 / (double)plan->HW),
+                                               plan->stream));
+}
+
+se2n_status se2n_diffuse(se2n_plan *plan, void *vol_hat, double beta, double T, int steps, int flags) {
+    SE2N_TRY(check_plan(plan));
+    if (!device_ptr(vol_hat, 16)) return SE2N_EINVAL;
+    return diffuse_impl(plan, (float2 *)vol_hat, beta, T, steps, flags);
+}
+
+se2n_status se2n_mix(se2n_plan *plan, void *vol, const float *f, const uint8_t *mask, const uint8_t *bins,
+                     double eps, double guard) {
+    SE2N_TRY(check_plan(plan));
+    if (!device_ptr(vol, 16) || !device_ptr(f, 8) || !device_ptr(mask, 2) || !device_ptr(bins, 2))
+        return SE2N_EINVAL;
+    if (!(eps >= 0.0 && eps <= 1.0) || !(guard >= 0.0) || !isfinite(guard)) return SE2N_EINVAL;
+    return mix_impl(plan, (float2 *)vol, f, mask, bins, 1.0f, (float)eps, (float)guard);
+}
+
+se2n_status se2n_project(se2n_plan *plan, const void *vol, int proj, float *out) {
+    SE2N_TRY(check_plan(plan));
+    if (!device_ptr(vol, 16) || !device_ptr(out, 8)) return SE2N_EINVAL;
+    if (proj != SE2N_PROJ_MAX && proj != SE2N_PROJ_MEAN) return SE2N_EINVAL;
+    return project_impl(plan, (const float2 *)vol, 1.0f, proj, out);
+}
+
+se2n_status se2n_inpaint(se2n_plan *plan, const float *f, const uint8_t *mask, const uint8_t *bins_in,
+                         const se2n_params *p, void *vol, float *out) {
+    SE2N_TRY(check_plan(plan));
+    SE2N_TRY(check_params(plan, p));
+    if (!device_ptr(f, 8) || !device_ptr(mask, 2) || !device_ptr(vol, 16) || !device_ptr(out, 8)) return SE2N_EINVAL;
+    if (bins_in && !device_ptr(bins_in, 2)) return SE2N_EINVAL;
+    return inpaint_impl(plan, f, mask, bins_in, p, (float2 *)vol, out);
+}
+
+se2n_status se2n_inpaint_host(se2n_plan *plan, const float *f_host, const uint8_t *mask_host,
+                              const se2n_params *p, float *out_host) {
+    SE2N_TRY(check_plan(plan));
+    SE2N_TRY(check_params(plan, p));
+    if (!f_host || !mask_host || !out_host) return SE2N_EINVAL;
+    const long long HW = plan->HW;
+    if (!plan->h_vol) {
+        cudaError_t e = cudaMalloc(&plan->h_vol, sizeof(float2) * HW * plan->N);
+        if (e == cudaSuccess) e = cudaMalloc(&plan->h_f, sizeof(float) * HW);
+        if (e == cudaSuccess) e = cudaMalloc(&plan->h_out, sizeof(float) * HW);
+        if (e == cudaSuccess) e = cudaMalloc(&plan->h_mask, HW);
+        if (e != cudaSuccess) {
+            cudaFree(plan->h_vol);
+            cudaFree(plan->h_f);
+            cudaFree(plan->h_out);
+            cudaFree(plan->h_mask);
+            plan->h_vol = nullptr;
+            plan->h_f = plan->h_out = nullptr;
+            plan->h_mask = nullptr;
+            return cuda_status(plan, e);
+        }
+    }
+    SE2N_TRY(cuda_status(plan, cudaMemcpyAsync(plan->h_f, f_host, sizeof(float) * HW, cudaMemcpyHostToDevice,
+                                               plan->stream)));
+    SE2N_TRY(cuda_status(plan, cudaMemcpyAsync(plan->h_mask, mask_host, HW, cudaMemcpyHostToDevice, plan->stream)));
+    SE2N_TRY(inpaint_impl(plan, plan->h_f, plan->h_mask, nullptr, p, plan->h_vol, plan->h_out));
+    SE2N_TRY(cuda_status(plan, cudaMemcpyAsync(out_host, plan->h_out, sizeof(float) * HW, cudaMemcpyDeviceToHost,
+                                               plan->stream)));
+    return cuda_status(plan, cudaStreamSynchronize(plan->stream));
+}
+
+se2n_status se2n_plan_tune_diffuse(se2n_plan *plan, int threads_per_freq, int block_threads, int blocks) {
+    SE2N_TRY(check_plan(plan));
+    const int P = threads_per_freq ? threads_per_freq : se2n_diffuse_default_P(plan->N);
+    const int block = block_threads ? block_threads : 128;
+    if (P != 1 && P != 2 && P != 4) return SE2N_EINVAL;
+    if (block < 32 || block > 256 || (block % 32) || blocks < 0) return SE2N_EINVAL;
+    if (!se2n_diffuse_has(plan->N, P)) return SE2N_EUNSUPPORTED;
+    plan->diffuse_P = P;
+    plan->diffuse_block = block;
+    plan->diffuse_blocks = blocks;
+    return SE2N_OK;
+}
+
+se2n_status se2n_plan_diffuse_info(se2n_plan *plan, int *regs_per_thread, int *blocks_per_sm,
+                                   int *threads_per_freq) {
+    SE2N_TRY(check_plan(plan));
+    int regs = 0, per_sm = 0;
+    cudaError_t e = se2n_diffuse_occupancy(plan->N, plan->diffuse_P, false, plan->diffuse_block, &per_sm, &regs);
+    if (e != cudaSuccess) return cuda_status(plan, e);
+    if (regs_per_thread) *regs_per_thread = regs;
+    if (blocks_per_sm) *blocks_per_sm = per_sm;
+    if (threads_per_freq) *threads_per_freq = plan->diffuse_P;
+    return SE2N_OK;
+}
+
+se2n_status se2n_plan_profile(se2n_plan *plan, int enable) {
+    SE2N_TRY(check_plan(plan));
+    SE2N_TRY(cuda_status(plan, cudaStreamSynchronize(plan->stream)));
+    plan->profiling = enable != 0;
+    for (int st = 0; st < SE2N_NUM_STAGES; ++st) {
+        plan->stage_used[st] = 0;
+        plan->prof_ms[st] = 0.0;
+        plan->prof_calls[st] = 0;
+    }
+    plan->kernels = 0;
+    return SE2N_OK;
+}
+
+se2n_status se2n_plan_profile_read(se2n_plan *plan, se2n_profile *out, int reset) {
+    SE2N_TRY(check_plan(plan));
+    if (!out) return SE2N_EINVAL;
+    SE2N_TRY(cuda_status(plan, cudaStreamSynchronize(plan->stream)));
+    for (int st = 0; st < SE2N_NUM_STAGES; ++st) {
+        for (int i = 0; i < plan->stage_used[st]; ++i) {
+            float ms = 0.0f;
+            cudaError_t e = cudaEventElapsedTime(&ms, plan->stage_ev[st][2 * i], plan->stage_ev[st][2 * i + 1]);
+            if (e != cudaSuccess) return cuda_status(plan, e);
+            plan->prof_ms[st] += ms;
+        }
+        plan->prof_calls[st] += plan->stage_used[st];
+        plan->stage_used[st] = 0;
+        out->ms[st] = plan->prof_ms[st];
+        out->calls[st] = plan->prof_calls[st];
+    }
+    out->kernels = plan->kernels;
+    if (reset) {
+        for (int st = 0; st < SE2N_NUM_STAGES; ++st) {
+            plan->prof_ms[st] = 0.0;
+            plan->prof_calls[st] = 0;
+        }
+        plan->kernels = 0;
+    }
+    return SE2N_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,254 @@
+// Pixel-wise stages of the path: orientation (smoothing and gradient in the
+// DFT domain), lift, static restoration and projection. All HBM-bound:
+// consecutive threads own consecutive pixel pairs, so every access of a
+// plane is a coalesced 16-byte (two complex) or 8-byte (two float) access.
+// H and W are even, so a pixel pair never straddles a plane and every plane
+// starts 16-byte aligned.
+#include "se2n_internal.h"
+
+namespace {
+
+constexpr int kBlock = 256;
+
+inline int grid_for(long long n, int per_block = kBlock) {
+    long long g = (n + per_block - 1) / per_block;
+    if (g > 1048576) g = 1048576;  // grid-stride beyond this
+    return (int)(g < 1 ? 1 : g);
+}
+
+// spec = f * (mask != 0) as complex, two pixels per thread.
+__global__ void k_orient_prep(const float2 *__restrict__ f, const uchar2 *__restrict__ mask,
+                              float4 *__restrict__ spec, long long npairs) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npairs;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float2 v = f[i];
+        const uchar2 m = mask[i];
+        spec[i] = make_float4(m.x ? v.x : 0.0f, 0.0f, m.y ? v.y : 0.0f, 0.0f);
+    }
+}
+
+// From the image spectrum F, write the spectra of the smoothed x and y
+// derivatives: F * g * (i 2 pi l~/W) and F * g * (i 2 pi k~/H), with
+// g = exp(-2 pi^2 sigma^2 ((k~/H)^2 + (l~/W)^2)), k~, l~ the signed
+// frequencies and the Nyquist derivative term set to zero.
+__global__ void k_grad_spec(const float2 *__restrict__ F, float2 *__restrict__ gx, float2 *__restrict__ gy,
+                            int H, int W, float sigma) {
+    const long long HW = (long long)H * W;
+    const float two_pi = 6.28318530717958647692f;
+    const float c = -2.0f * 9.86960440108935861883f * sigma * sigma;  // -2 pi^2 sigma^2
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < HW;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(i / W), l = (int)(i - (long long)k * W);
+        const int ks = (2 * k >= H) ? k - H : k;
+        const int ls = (2 * l >= W) ? l - W : l;
+        const float fy = (float)ks / (float)H, fx = (float)ls / (float)W;
+        const float g = expf(c * (fx * fx + fy * fy));
+        const float dx = (2 * ls == -W) ? 0.0f : two_pi * fx * g;
+        const float dy = (2 * ks == -H) ? 0.0f : two_pi * fy * g;
+        const float2 v = F[i];
+        gx[i] = make_float2(-v.y * dx, v.x * dx);  // i * dx * F
+        gy[i] = make_float2(-v.y * dy, v.x * dy);
+    }
+}
+
+// max over pixels of |grad|^2 (real parts of the inverse transforms); the
+// scale of the unnormalised inverse cancels in every later use.
+__global__ void k_grad_max(const float2 *__restrict__ gx, const float2 *__restrict__ gy, long long HW,
+                           unsigned int *__restrict__ gmax) {
+    float m = 0.0f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < HW;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float x = gx[i].x, y = gy[i].x;
+        m = fmaxf(m, fmaf(x, x, y * y));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __shared__ float wm[kBlock / 32];
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = (threadIdx.x < blockDim.x / 32) ? wm[threadIdx.x] : 0.0f;
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        // non-negative floats order like their bit patterns
+        if (threadIdx.x == 0) atomicMax(gmax, __float_as_uint(m));
+    }
+}
+
+// bin = floor(phi / dth + 1/2) mod N with phi = atan2(gy, gx) + pi/2 in
+// [0, pi); flat pixels (|grad|^2 <= flat_tol^2 max|grad|^2) get SE2N_BIN_FLAT.
+__global__ void k_bins(const float2 *__restrict__ gx, const float2 *__restrict__ gy, long long HW,
+                       const unsigned int *__restrict__ gmax, float flat_tol2, int N, float inv_dth,
+                       uint8_t *__restrict__ bins) {
+    const float pi = 3.14159265358979323846f;
+    const float thresh = flat_tol2 * __uint_as_float(*gmax);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < HW;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float x = gx[i].x, y = gy[i].x;
+        const float m2 = fmaf(x, x, y * y);
+        uint8_t b = SE2N_BIN_FLAT;
+        if (!(m2 <= thresh)) {
+            float phi = atan2f(y, x) + 0.5f * pi;
+            if (phi >= pi) phi -= pi;
+            if (phi < 0.0f) phi += pi;
+            const float u = fmaf(phi, inv_dth, 0.5f);
+            int r = (int)floorf(u);
+            r %= N;
+            if (r < 0) r += N;
+            b = (uint8_t)r;
+        }
+        bins[i] = b;
+    }
+}
+
+// vol[r][y][x] = f0 on the pixel's bin (all bins if flat), 0 elsewhere.
+__global__ void k_lift(const float2 *__restrict__ f, const uchar2 *__restrict__ mask,
+                       const uchar2 *__restrict__ bins, float4 *__restrict__ vol, long long npairs, int N) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npairs;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float2 v = f[i];
+        const uchar2 m = mask[i];
+        const uchar2 b = bins[i];
+        const float a0 = m.x ? v.x : 0.0f, a1 = m.y ? v.y : 0.0f;
+        for (int r = 0; r < N; ++r) {
+            const bool on0 = (b.x == r) || (b.x == SE2N_BIN_FLAT);
+            const bool on1 = (b.y == r) || (b.y == SE2N_BIN_FLAT);
+            vol[(long long)r * npairs + i] = make_float4(on0 ? a0 : 0.0f, 0.0f, on1 ? a1 : 0.0f, 0.0f);
+        }
+    }
+}
+
+// Static restoration. h(t) = max_r scale*Re vol, h(0) = max_r of the lift.
+__device__ __forceinline__ float sr_value(float re, float h0, float ht, float lift_r, bool good, float eps,
+                                          float guard) {
+    if (!good) return re;
+    if (ht > guard) {
+        const float sig = (eps * h0 + (1.0f - eps) * ht) / ht;
+        return re * sig;
+    }
+    return eps * lift_r + (1.0f - eps) * re;
+}
+
+__global__ void k_mix(float4 *__restrict__ vol, const float2 *__restrict__ f, const uchar2 *__restrict__ mask,
+                      const uchar2 *__restrict__ bins, long long npairs, int N, float scale, float eps,
+                      float guard) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npairs;
+         i += (long long)gridDim.x * blockDim.x) {
+        float ht0 = -INFINITY, ht1 = -INFINITY;
+        for (int r = 0; r < N; ++r) {
+            const float4 v = vol[(long long)r * npairs + i];
+            ht0 = fmaxf(ht0, v.x * scale);
+            ht1 = fmaxf(ht1, v.z * scale);
+        }
+        const float2 fv = f[i];
+        const uchar2 m = mask[i];
+        const uchar2 b = bins[i];
+        const float a0 = m.x ? fv.x : 0.0f, a1 = m.y ? fv.y : 0.0f;
+        // max over angles of the lift: the value itself if it sits on every
+        // angle or is not negative (N >= 2 leaves zeros on the other angles)
+        const float h00 = (b.x == SE2N_BIN_FLAT) ? a0 : fmaxf(a0, 0.0f);
+        const float h01 = (b.y == SE2N_BIN_FLAT) ? a1 : fmaxf(a1, 0.0f);
+        for (int r = 0; r < N; ++r) {
+            const long long o = (long long)r * npairs + i;
+            const float4 v = vol[o];
+            const float l0 = ((b.x == r) || (b.x == SE2N_BIN_FLAT)) ? a0 : 0.0f;
+            const float l1 = ((b.y == r) || (b.y == SE2N_BIN_FLAT)) ? a1 : 0.0f;
+            vol[o] = make_float4(sr_value(v.x * scale, h00, ht0, l0, m.x != 0, eps, guard), 0.0f,
+                                 sr_value(v.z * scale, h01, ht1, l1, m.y != 0, eps, guard), 0.0f);
+        }
+    }
+}
+
+__global__ void k_project(const float4 *__restrict__ vol, long long npairs, int N, float scale, int proj,
+                          float2 *__restrict__ out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npairs;
+         i += (long long)gridDim.x * blockDim.x) {
+        float a0, a1;
+        if (proj == SE2N_PROJ_MAX) {
+            a0 = -INFINITY;
+            a1 = -INFINITY;
+            for (int r = 0; r < N; ++r) {
+                const float4 v = vol[(long long)r * npairs + i];
+                a0 = fmaxf(a0, v.x * scale);
+                a1 = fmaxf(a1, v.z * scale);
+            }
+        } else {
+            a0 = 0.0f;
+            a1 = 0.0f;
+            for (int r = 0; r < N; ++r) {
+                const float4 v = vol[(long long)r * npairs + i];
+                a0 += v.x * scale;
+                a1 += v.z * scale;
+            }
+            a0 /= (float)N;
+            a1 /= (float)N;
+        }
+        out[i] = make_float2(a0, a1);
+    }
+}
+
+__global__ void k_scale(float4 *__restrict__ v, long long n4, float s) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4;
+         i += (long long)gridDim.x * blockDim.x) {
+        float4 a = v[i];
+        a.x *= s; a.y *= s; a.z *= s; a.w *= s;
+        v[i] = a;
+    }
+}
+
+}  // namespace
+
+cudaError_t se2n_launch_orient_prep(const float *f, const uint8_t *mask, float2 *spec, long long HW,
+                                    cudaStream_t s) {
+    const long long n = HW / 2;
+    k_orient_prep<<<grid_for(n), kBlock, 0, s>>>((const float2 *)f, (const uchar2 *)mask, (float4 *)spec, n);
+    return cudaGetLastError();
+}
+
+cudaError_t se2n_launch_grad_spec(float2 *spec, int H, int W, float sigma, cudaStream_t s) {
+    const long long HW = (long long)H * W;
+    k_grad_spec<<<grid_for(HW), kBlock, 0, s>>>(spec, spec + HW, spec + 2 * HW, H, W, sigma);
+    return cudaGetLastError();
+}
+
+cudaError_t se2n_launch_grad_max(const float2 *gx, const float2 *gy, long long HW, unsigned int *gmax,
+                                 cudaStream_t s) {
+    int g = grid_for(HW);
+    if (g > 4096) g = 4096;
+    k_grad_max<<<g, kBlock, 0, s>>>(gx, gy, HW, gmax);
+    return cudaGetLastError();
+}
+
+cudaError_t se2n_launch_bins(const float2 *gx, const float2 *gy, long long HW, const unsigned int *gmax,
+                             float flat_tol2, int N, int angle_conv, uint8_t *bins, cudaStream_t s) {
+    const float dth = (angle_conv ? 2.0f : 1.0f) * 3.14159265358979323846f / (float)N;
+    k_bins<<<grid_for(HW), kBlock, 0, s>>>(gx, gy, HW, gmax, flat_tol2, N, 1.0f / dth, bins);
+    return cudaGetLastError();
+}
+
+cudaError_t se2n_launch_lift(const float *f, const uint8_t *mask, const uint8_t *bins, float2 *vol,
+                             long long HW, int N, cudaStream_t s) {
+    const long long n = HW / 2;
+    k_lift<<<grid_for(n), kBlock, 0, s>>>((const float2 *)f, (const uchar2 *)mask, (const uchar2 *)bins,
+                                          (float4 *)vol, n, N);
+    return cudaGetLastError();
+}
+
+cudaError_t se2n_launch_mix(float2 *vol, const float *f, const uint8_t *mask, const uint8_t *bins,
+                            long long HW, int N, float scale, float eps, float guard, cudaStream_t s) {
+    const long long n = HW / 2;
+    k_mix<<<grid_for(n), kBlock, 0, s>>>((float4 *)vol, (const float2 *)f, (const uchar2 *)mask,
+                                         (const uchar2 *)bins, n, N, scale, eps, guard);
+    return cudaGetLastError();
+}
+
+cudaError_t se2n_launch_project(const float2 *vol, long long HW, int N, float scale, int proj, float *out,
+                                cudaStream_t s) {
+    const long long n = HW / 2;
+    k_project<<<grid_for(n), kBlock, 0, s>>>((const float4 *)vol, n, N, scale, proj, (float2 *)out);
+    return cudaGetLastError();
+}
+
+cudaError_t se2n_launch_scale(float2 *vol, long long count, float scale, cudaStream_t s) {
+    const long long n4 = count / 2;
+    k_scale<<<grid_for(n4), kBlock, 0, s>>>((float4 *)vol, n4, scale);
+    return cudaGetLastError();
+}

@@ -1,0 +1,81 @@
+// Internal declarations shared by the CUDA translation units of libse2n.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "se2n.h"
+
+struct se2n_plan {
+    int H, W, N, angle_conv;
+    long long HW;
+    int device;
+    cudaStream_t stream;
+    cufftHandle fft_vol;   // batch N, [H][W], C2C, in place
+    cufftHandle fft_one;   // one plane
+    cufftHandle fft_two;   // batch 2 (gradient components)
+    float2 *spec;          // [3][H][W]: image spectrum, x and y gradient
+    unsigned int *gmax;    // one word: max |grad|^2 as float bits
+    uint8_t *bins;         // [H][W] bins computed by se2n_inpaint
+    // se2n_inpaint_host buffers (allocated on first use)
+    float *h_f, *h_out;
+    uint8_t *h_mask;
+    float2 *h_vol;
+    // diffusion launch configuration
+    int diffuse_P;         // threads per frequency
+    int diffuse_block;     // threads per block
+    int diffuse_blocks;    // 0 = fill the device
+    int num_sms;
+    int last_cuda_error;
+    // stage timing (se2n_plan_profile): event pairs per stage, reused
+    bool profiling;
+    std::vector<cudaEvent_t> stage_ev[SE2N_NUM_STAGES];
+    int stage_used[SE2N_NUM_STAGES];
+    double prof_ms[SE2N_NUM_STAGES];
+    long long prof_calls[SE2N_NUM_STAGES];
+    long long kernels;  // own kernel launches
+};
+
+// Parameters of one diffusion launch (kernel parameter space: read through
+// the constant bank, so the angle tables cost no loads in the hot loop).
+struct DiffuseArgs {
+    float2 *vol;
+    long long HW;
+    int H, W;
+    int steps;
+    float inv_c;      // 2 / (beta dt): the left CN matrix divided by beta dt / 2
+    float inv_beta;
+    double inv_c_d;   // the same in FP64 (Sherman-Morrison scalars in FP64)
+    double inv_beta_d;
+    float cs[SE2N_MAX_N];
+    float sn[SE2N_MAX_N];
+};
+
+// Launch the diffusion kernel for (N, P, fp64 correction) on `stream`.
+// Returns cudaErrorInvalidValue if no instantiation exists.
+cudaError_t se2n_launch_diffuse(int N, int P, bool sm_fp64, const DiffuseArgs &a, int block, int blocks,
+                                cudaStream_t stream);
+// Occupancy query for the same kernel: blocks per SM and registers per thread.
+cudaError_t se2n_diffuse_occupancy(int N, int P, bool sm_fp64, int block, int *blocks_per_sm, int *regs);
+// Whether an instantiation exists for (N, P).
+bool se2n_diffuse_has(int N, int P);
+int se2n_diffuse_default_P(int N);
+
+// Pixel kernels (pixel.cu).
+cudaError_t se2n_launch_orient_prep(const float *f, const uint8_t *mask, float2 *spec, long long HW,
+                                    cudaStream_t s);
+cudaError_t se2n_launch_grad_spec(float2 *spec, int H, int W, float sigma, cudaStream_t s);
+cudaError_t se2n_launch_grad_max(const float2 *gx, const float2 *gy, long long HW, unsigned int *gmax,
+                                 cudaStream_t s);
+cudaError_t se2n_launch_bins(const float2 *gx, const float2 *gy, long long HW, const unsigned int *gmax,
+                             float flat_tol2, int N, int angle_conv, uint8_t *bins, cudaStream_t s);
+cudaError_t se2n_launch_lift(const float *f, const uint8_t *mask, const uint8_t *bins, float2 *vol,
+                             long long HW, int N, cudaStream_t s);
+cudaError_t se2n_launch_mix(float2 *vol, const float *f, const uint8_t *mask, const uint8_t *bins,
+                            long long HW, int N, float scale, float eps, float guard, cudaStream_t s);
+cudaError_t se2n_launch_project(const float2 *vol, long long HW, int N, float scale, int proj, float *out,
+                                cudaStream_t s);
+cudaError_t se2n_launch_scale(float2 *vol, long long count, float scale, cudaStream_t s);

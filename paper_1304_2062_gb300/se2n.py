@@ -1,0 +1,256 @@
+"""Python binding of libse2n, the C ABI declared in include/se2n.h.
+
+Argument marshalling only: every function here has the name of the C entry
+point it calls, turns torch CUDA tensors into device pointers and streams
+into cudaStream_t handles, and raises Se2nError on a non-OK status. All
+computation happens in the CUDA library; if the library is missing, loading
+this module fails (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libse2n.so")
+
+SE2N_OK = 0
+SE2N_EINVAL = 1
+SE2N_ENOMEM = 2
+SE2N_ECUDA = 3
+SE2N_ECUFFT = 4
+SE2N_EUNSUPPORTED = 5
+SE2N_ENUMERIC = 6
+SE2N_BIN_FLAT = 255
+SE2N_PROJ_MAX = 0
+SE2N_PROJ_MEAN = 1
+SE2N_DIFFUSE_SM_FP64 = 1
+SE2N_MAX_N = 64
+
+
+class Se2nError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {se2n_status_string(status)} (status {status})")
+
+
+SE2N_STAGES = ("orient", "lift", "fft", "diffuse", "mix", "project")
+
+
+class se2n_profile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 6), ("calls", ctypes.c_longlong * 6), ("kernels", ctypes.c_longlong)]
+
+
+class se2n_params(ctypes.Structure):
+    _fields_ = [
+        ("N", ctypes.c_int),
+        ("beta", ctypes.c_double),
+        ("T", ctypes.c_double),
+        ("steps", ctypes.c_int),
+        ("rounds", ctypes.c_int),
+        ("eps", ctypes.c_double),
+        ("sigma_smooth", ctypes.c_double),
+        ("flat_tol", ctypes.c_double),
+        ("proj", ctypes.c_int),
+        ("final_mix", ctypes.c_int),
+        ("guard", ctypes.c_double),
+        ("diffuse_flags", ctypes.c_int),
+    ]
+
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "se2n_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "se2n_params_default": (ctypes.c_int, [ctypes.POINTER(se2n_params)]),
+    "se2n_params_from_paper": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "se2n_plan_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, _P]),
+    "se2n_plan_destroy": (ctypes.c_int, [_P]),
+    "se2n_plan_set_stream": (ctypes.c_int, [_P, _P]),
+    "se2n_plan_last_cuda_error": (ctypes.c_int, [_P]),
+    "se2n_orient": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_double, _P]),
+    "se2n_lift": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "se2n_forward": (ctypes.c_int, [_P, _P]),
+    "se2n_inverse": (ctypes.c_int, [_P, _P]),
+    "se2n_diffuse": (ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int]),
+    "se2n_mix": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_double, ctypes.c_double]),
+    "se2n_project": (ctypes.c_int, [_P, _P, ctypes.c_int, _P]),
+    "se2n_inpaint": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(se2n_params), _P, _P]),
+    "se2n_inpaint_host": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(se2n_params), _P]),
+    "se2n_plan_tune_diffuse": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "se2n_plan_profile": (ctypes.c_int, [_P, ctypes.c_int]),
+    "se2n_plan_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(se2n_profile), ctypes.c_int]),
+    "se2n_plan_diffuse_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                              ctypes.POINTER(ctypes.c_int)]),
+}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libse2n.so is not built ({LIB_PATH}); run __graft_entry__.build() "
+                          "or python paper_1304_2062_gb300/build.py")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def _check(status, where):
+    if status != SE2N_OK:
+        raise Se2nError(status, where)
+
+
+def _ptr(x):
+    """Device (or host) address of a tensor, a numpy array or a raw int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)!r}")
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def se2n_status_string(status):
+    return lib.se2n_status_string(int(status)).decode()
+
+
+def se2n_params_default(**overrides):
+    p = se2n_params()
+    _check(lib.se2n_params_default(ctypes.byref(p)), "se2n_params_default")
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+def se2n_params_from_paper(alpha, T_paper, M, N):
+    b = ctypes.c_double()
+    t = ctypes.c_double()
+    _check(lib.se2n_params_from_paper(alpha, T_paper, M, N, ctypes.byref(b), ctypes.byref(t)),
+           "se2n_params_from_paper")
+    return b.value, t.value
+
+
+class Plan:
+    """Owns an se2n_plan*; destroyed on close() or garbage collection."""
+
+    def __init__(self, handle, H, W, N, angle_conv):
+        self.handle = handle
+        self.H, self.W, self.N, self.angle_conv = H, W, N, angle_conv
+
+    def close(self):
+        if self.handle:
+            lib.se2n_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def _as_parameter_(self):
+        return self.handle
+
+
+def se2n_plan_create(H, W, N, angle_conv=0, stream=None):
+    h = _P()
+    _check(lib.se2n_plan_create(ctypes.byref(h), H, W, N, angle_conv, _stream(stream)), "se2n_plan_create")
+    return Plan(h.value, H, W, N, angle_conv)
+
+
+def se2n_plan_destroy(plan):
+    plan.close()
+
+
+def se2n_plan_set_stream(plan, stream):
+    _check(lib.se2n_plan_set_stream(plan.handle, _stream(stream)), "se2n_plan_set_stream")
+
+
+def se2n_plan_last_cuda_error(plan):
+    return lib.se2n_plan_last_cuda_error(plan.handle)
+
+
+def se2n_orient(plan, f, mask, sigma, flat_tol, bins):
+    _check(lib.se2n_orient(plan.handle, _ptr(f), _ptr(mask), sigma, flat_tol, _ptr(bins)), "se2n_orient")
+
+
+def se2n_lift(plan, f, mask, bins, vol):
+    _check(lib.se2n_lift(plan.handle, _ptr(f), _ptr(mask), _ptr(bins), _ptr(vol)), "se2n_lift")
+
+
+def se2n_forward(plan, vol):
+    _check(lib.se2n_forward(plan.handle, _ptr(vol)), "se2n_forward")
+
+
+def se2n_inverse(plan, vol):
+    _check(lib.se2n_inverse(plan.handle, _ptr(vol)), "se2n_inverse")
+
+
+def se2n_diffuse(plan, vol_hat, beta, T, steps, flags=0):
+    _check(lib.se2n_diffuse(plan.handle, _ptr(vol_hat), beta, T, steps, flags), "se2n_diffuse")
+
+
+def se2n_mix(plan, vol, f, mask, bins, eps, guard=1e-12):
+    _check(lib.se2n_mix(plan.handle, _ptr(vol), _ptr(f), _ptr(mask), _ptr(bins), eps, guard), "se2n_mix")
+
+
+def se2n_project(plan, vol, proj, out):
+    _check(lib.se2n_project(plan.handle, _ptr(vol), proj, _ptr(out)), "se2n_project")
+
+
+def se2n_inpaint(plan, f, mask, bins_in, params, vol, out):
+    _check(lib.se2n_inpaint(plan.handle, _ptr(f), _ptr(mask), _ptr(bins_in), ctypes.byref(params), _ptr(vol),
+                            _ptr(out)), "se2n_inpaint")
+
+
+def se2n_inpaint_host(plan, f_host, mask_host, params, out_host):
+    _check(lib.se2n_inpaint_host(plan.handle, _ptr(f_host), _ptr(mask_host), ctypes.byref(params),
+                                 _ptr(out_host)), "se2n_inpaint_host")
+
+
+def se2n_plan_tune_diffuse(plan, threads_per_freq=0, block_threads=0, blocks=0):
+    _check(lib.se2n_plan_tune_diffuse(plan.handle, threads_per_freq, block_threads, blocks),
+           "se2n_plan_tune_diffuse")
+
+
+def se2n_plan_diffuse_info(plan):
+    r, b, p = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib.se2n_plan_diffuse_info(plan.handle, ctypes.byref(r), ctypes.byref(b), ctypes.byref(p)),
+           "se2n_plan_diffuse_info")
+    return dict(regs_per_thread=r.value, blocks_per_sm=b.value, threads_per_freq=p.value)
+
+
+def se2n_plan_profile(plan, enable=True):
+    _check(lib.se2n_plan_profile(plan.handle, 1 if enable else 0), "se2n_plan_profile")
+
+
+def se2n_plan_profile_read(plan, reset=False):
+    """Accumulated stage times: {stage: (ms, calls)} plus the own-kernel launch count."""
+    prof = se2n_profile()
+    _check(lib.se2n_plan_profile_read(plan.handle, ctypes.byref(prof), 1 if reset else 0), "se2n_plan_profile_read")
+    out = {name: (prof.ms[i], prof.calls[i]) for i, name in enumerate(SE2N_STAGES)}
+    out["kernels"] = prof.kernels
+    return out

@@ -249,8 +249,15 @@ def workload_2048(stress=False, seed=4):
 
 
 def random_volume(N, H, W, seed, dtype=np.complex128):
-    """Random complex volume [N][H][W] with unit-variance Gaussian parts."""
+    """Random complex volume [N][H][W] with unit-variance Gaussian parts
+    (drawn directly in float32 when dtype is complex64, to keep large
+    volumes cheap)."""
     rng = np.random.default_rng(seed)
+    if np.dtype(dtype) == np.complex64:
+        v = np.empty((N, H, W), np.complex64)
+        v.real = rng.standard_normal((N, H, W), dtype=np.float32)
+        v.imag = rng.standard_normal((N, H, W), dtype=np.float32)
+        return v
     v = rng.standard_normal((N, H, W)) + 1j * rng.standard_normal((N, H, W))
     return v.astype(dtype)
 

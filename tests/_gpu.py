@@ -1,0 +1,41 @@
+"""Helpers shared by the GPU parity tests: device tensors from numpy inputs
+and the comparison metrics with their tolerances.
+
+Tolerances (the diffusion runs in FP32 against the FP64 oracle):
+  * REL_L2 = 1e-5: relative L2 error over a whole volume or image;
+  * MAX_REL = 1e-5: max-abs error of a projected image relative to max|f|.
+Both are the stated accuracy target of the path; the measured errors are
+typically 1e-7 .. 2e-6 (see the test output).
+"""
+import numpy as np
+import torch
+
+REL_L2 = 1e-5
+MAX_REL = 1e-5
+
+
+def dev():
+    return torch.device("cuda:0")
+
+
+def t_f32(a):
+    return torch.tensor(np.ascontiguousarray(a, dtype=np.float32), device=dev())
+
+
+def t_u8(a):
+    return torch.tensor(np.ascontiguousarray(a, dtype=np.uint8), device=dev())
+
+
+def t_c64(a):
+    return torch.tensor(np.ascontiguousarray(a, dtype=np.complex64), device=dev())
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def rel_l2(x, ref):
+    x = np.asarray(x, dtype=np.complex128 if np.iscomplexobj(x) else np.float64)
+    ref = np.asarray(ref)
+    return float(np.linalg.norm((x - ref).ravel()) / max(np.linalg.norm(np.asarray(ref).ravel()), 1e-300))

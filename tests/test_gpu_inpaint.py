@@ -1,0 +1,189 @@
+"""End-to-end parity of se2n_inpaint (lift, DFT, fused CN diffusion, static
+restoration between intervals, inverse DFT, projection) against the FP64
+oracle through the C ABI.
+
+The orientation bins are a floating-point decision (tested on their own in
+test_gpu_stages.py); here both sides get the oracle's bins so the rest of
+the path is compared at the FP32 tolerance. The GPU's own-bins path is
+checked to be the same computation (bitwise) as orient + inpaint.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from _gpu import MAX_REL, REL_L2, host, rel_l2, t_f32, t_u8
+
+pytestmark = pytest.mark.gpu
+
+se2n = pytest.importorskip("paper_1304_2062_gb300.se2n")
+
+import torch  # noqa: E402
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "curves_noise_512_N32.npz")
+
+
+def _gpu_inpaint(f32, mask, bins, prm, conv=0, tune=None):
+    H, W = f32.shape
+    plan = se2n.se2n_plan_create(H, W, prm.N, conv)
+    if tune:
+        se2n.se2n_plan_tune_diffuse(plan, *tune)
+    vol = torch.empty((prm.N, H, W), dtype=torch.complex64, device="cuda")
+    out = torch.empty((H, W), dtype=torch.float32, device="cuda")
+    se2n.se2n_inpaint(plan, t_f32(f32), t_u8(mask), None if bins is None else t_u8(bins), prm, vol, out)
+    got = host(out)
+    plan.close()
+    return got
+
+
+def _params(p: oracle.Params, flags=0):
+    return se2n.se2n_params_default(N=p.N, beta=p.beta, T=p.T, steps=p.steps, rounds=p.rounds, eps=p.eps,
+                                    sigma_smooth=p.sigma, flat_tol=p.flat_tol, proj=p.proj,
+                                    final_mix=p.final_mix, guard=p.guard, diffuse_flags=flags)
+
+
+def _compare(w, p, conv=0, flags=0, tune=None):
+    f32 = w.f.astype(np.float32)
+    f64 = f32.astype(np.float64)
+    bins = oracle.orient(f64, w.mask, p.N, p.sigma, conv, p.flat_tol)["bins"]
+    p.angle_conv = conv
+    ref = oracle.inpaint(f64, w.mask, p, bins=bins)["out"]
+    got = _gpu_inpaint(f32, w.mask, bins, _params(p, flags), conv, tune)
+    mx = np.abs(got - ref).max() / np.abs(f64).max()
+    r2 = rel_l2(got, ref)
+    print(f"{w.H}x{w.W} N={p.N} S={p.steps} R={p.rounds}: max-abs/max|f| {mx:.2e}, rel-L2 {r2:.2e}")
+    assert mx <= MAX_REL
+    assert r2 <= REL_L2
+    return got
+
+
+def test_small_workload_single_round():
+    """64x64 lines and circles, 50 % random mask, N=16, beta=0.5, T=1 in
+    100 steps, one round (the plain method)."""
+    w = synth.workload_small()
+    _compare(w, oracle.Params(N=16, beta=0.5, T=1.0, steps=100, rounds=1))
+
+
+def test_reduced_512_geometry_three_rounds():
+    w = synth.workload_512(H=128, W=128, steps=100, rounds=3)
+    _compare(w, oracle.Params(N=32, beta=0.25, T=6.0, steps=100, rounds=3))
+
+
+@pytest.mark.parametrize("variant", ["mean", "final_mix", "conv1", "fp64", "N64", "P4", "nonsquare"])
+def test_variants(variant):
+    w = synth.workload_512(H=96, W=96, steps=60, rounds=3)
+    p = oracle.Params(N=32, beta=0.25, T=6.0, steps=60, rounds=3)
+    conv, flags, tune = 0, 0, None
+    if variant == "mean":
+        p.proj = 1
+    elif variant == "final_mix":
+        p.final_mix = 1
+    elif variant == "conv1":
+        conv = 1
+    elif variant == "fp64":
+        flags = se2n.SE2N_DIFFUSE_SM_FP64
+    elif variant == "N64":
+        p.N = 64
+    elif variant == "P4":
+        tune = (4, 128, 0)
+    elif variant == "nonsquare":
+        w = synth.workload_512(H=64, W=160, steps=60, rounds=3)
+    _compare(w, p, conv, flags, tune)
+
+
+def test_table1_parameters_in_pixel_units():
+    """A Table 1 row (alpha=0.3, T=4, n=160 in the paper's units, M=256,
+    N=30) mapped to pixel units, on a bar-corrupted 64x64 image with a few
+    of its restoration intervals."""
+    beta, T = se2n.se2n_params_from_paper(0.30, 4.0, 256, 30)
+    ob, oT = oracle.params_from_paper(0.30, 4.0, 256, 30)
+    assert abs(beta - ob) < 1e-15 and abs(T - oT) < 1e-12
+    clean = synth.curves_noise_image(64, 64, 8, n_curves=12)
+    mask = synth.bar_mask(64, 64, 3, 10)
+    w = synth.Workload("table1", clean, mask, N=30, beta=beta, T=T / 160 * 4, steps=20, rounds=4)
+    _compare(w, oracle.Params(N=30, beta=beta, T=T / 160 * 4, steps=20, rounds=4))
+
+
+def test_full_512_N32_ten_rounds_against_stored_oracle():
+    """The full workload (512x512, N=32, beta=0.25, 10 intervals of 500
+    steps) against the FP64 oracle's result written by
+    tests/golden/make_references.py."""
+    if not os.path.exists(GOLDEN):
+        pytest.fail("missing tests/golden/curves_noise_512_N32.npz: run tests/golden/make_references.py")
+    g = np.load(GOLDEN)
+    w = synth.workload_512()
+    p = oracle.Params(N=32, beta=0.25, T=20.0, steps=500, rounds=10)
+    got = _gpu_inpaint(w.f.astype(np.float32), w.mask, g["bins"], _params(p))
+    ref = g["out"].astype(np.float64)
+    mx = np.abs(got - ref).max() / np.abs(w.f).max()
+    r2 = rel_l2(got, ref)
+    print(f"512^2 N=32 10x500: max-abs/max|f| {mx:.2e}, rel-L2 {r2:.2e}")
+    assert mx <= MAX_REL
+    assert r2 <= REL_L2
+
+
+def test_own_bins_path_is_orient_then_inpaint():
+    w = synth.workload_512(H=128, W=128, steps=20, rounds=2)
+    p = oracle.Params(N=32, beta=0.25, T=4.0, steps=20, rounds=2)
+    f32 = w.f.astype(np.float32)
+    plan = se2n.se2n_plan_create(w.H, w.W, 32)
+    b = torch.empty((w.H, w.W), dtype=torch.uint8, device="cuda")
+    se2n.se2n_orient(plan, t_f32(f32), t_u8(w.mask), 1.0, 1e-4, b)
+    bins = host(b)
+    plan.close()
+    a = _gpu_inpaint(f32, w.mask, None, _params(p))
+    c = _gpu_inpaint(f32, w.mask, bins, _params(p))
+    np.testing.assert_array_equal(a, c)
+
+
+def test_host_entry_point_matches_device_entry_point():
+    w = synth.workload_512(H=128, W=64, steps=20, rounds=2)
+    p = oracle.Params(N=32, beta=0.25, T=4.0, steps=20, rounds=2)
+    f32 = np.ascontiguousarray(w.f.astype(np.float32))
+    mask = np.ascontiguousarray(w.mask.astype(np.uint8))
+    dev = _gpu_inpaint(f32, mask, None, _params(p))
+    plan = se2n.se2n_plan_create(w.H, w.W, 32)
+    out = np.zeros((w.H, w.W), np.float32)
+    for _ in range(2):  # the second call reuses the plan's buffers
+        se2n.se2n_inpaint_host(plan, f32, mask, _params(p), out)
+        np.testing.assert_array_equal(out, dev)
+    plan.close()
+
+
+def test_rotation_equivariance_full_size():
+    """Property at the full 512x512 size: rotating the input by 90 degrees
+    rotates the output (bins rotated with their channel shift N/2)."""
+    w = synth.workload_512(steps=100, rounds=2)
+    N = 32
+    p = oracle.Params(N=N, beta=0.25, T=4.0, steps=100, rounds=2)
+    f32 = w.f.astype(np.float32)
+    bins = oracle.orient(f32.astype(np.float64), w.mask, N)["bins"]
+    rb = np.rot90(bins).copy()
+    single = rb != oracle.BIN_FLAT
+    rb[single] = (rb[single].astype(int) + N // 2) % N
+    a = _gpu_inpaint(f32, w.mask, bins, _params(p))
+    b = _gpu_inpaint(np.rot90(f32).copy(), np.rot90(w.mask).copy(), rb, _params(p))
+    assert rel_l2(b, np.rot90(a)) <= REL_L2
+
+
+def test_inpaint_rejects_bad_parameters():
+    plan = se2n.se2n_plan_create(16, 16, 16)
+    f = t_f32(np.ones((16, 16)))
+    m = t_u8(np.ones((16, 16)))
+    vol = torch.empty((16, 16, 16), dtype=torch.complex64, device="cuda")
+    out = torch.empty((16, 16), dtype=torch.float32, device="cuda")
+    bad = [dict(N=32), dict(eps=1.5), dict(rounds=0), dict(steps=0), dict(beta=0.0), dict(proj=3),
+           dict(sigma_smooth=0.0), dict(final_mix=2), dict(diffuse_flags=8)]
+    for b in bad:
+        prm = se2n.se2n_params_default(N=16)
+        for k, v in b.items():
+            setattr(prm, k, v)
+        with pytest.raises(se2n.Se2nError) as e:
+            se2n.se2n_inpaint(plan, f, m, None, prm, vol, out)
+        assert e.value.status == se2n.SE2N_EINVAL, b
+    prm = se2n.se2n_params_default(N=16)
+    with pytest.raises(se2n.Se2nError):
+        se2n.se2n_inpaint(plan, np.ones((16, 16), np.float32), m, None, prm, vol, out)   # host image
+    plan.close()
