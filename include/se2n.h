@@ -69,7 +69,9 @@ typedef enum se2n_status {
 #define SE2N_PROJ_MEAN 1
 
 /* se2n_diffuse flags. */
-#define SE2N_DIFFUSE_SM_FP64 1  /* Sherman-Morrison correction scalars in FP64 */
+#define SE2N_DIFFUSE_SM_FP64 1     /* Sherman-Morrison correction scalars in FP64 */
+#define SE2N_DIFFUSE_SPLIT_DIAG 2  /* keep a_r^2/beta apart from the angular second difference
+                                      (always on when beta * T > 8, see se2n_diffuse) */
 
 /* Largest N this build has kernels for, and the N it supports. */
 #define SE2N_MAX_N 64
@@ -172,7 +174,11 @@ SE2N_API se2n_status se2n_inverse(se2n_plan *plan, void *vol);
  * once. beta > 0 (the jump rate of Section 2), T >= 0 (T = 0 is a no-op),
  * steps >= 1, beta*dt >= 1e-30 and beta*dt <= 1e3 (else SE2N_ENUMERIC).
  * flags: SE2N_DIFFUSE_SM_FP64 computes the corner (Sherman-Morrison)
- * correction scalars in FP64. */
+ * correction scalars in FP64. SE2N_DIFFUSE_SPLIT_DIAG forms the right-hand
+ * side as (psi_{r-1} + psi_{r+1} - 2 psi_r) - (a_r^2/beta) psi_r instead of
+ * with the fused coefficient 2 + a_r^2/beta, whose FP32 rounding perturbs
+ * decay rates by ~1.2e-7 beta per unit time; it costs one FMA more per angle
+ * and is selected automatically when beta * T > 8. */
 SE2N_API se2n_status se2n_diffuse(se2n_plan *plan, void *vol_hat, double beta, double T, int steps, int flags);
 
 /* Static restoration (Section 5, SR) on the real volume, in place: with

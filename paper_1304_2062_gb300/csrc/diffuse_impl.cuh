@@ -28,6 +28,13 @@
 //
 // Per step and per real component each angle costs 6 FP32 instructions
 // (add, 5 FMA; 7 when Q = 2), plus a few shuffles per thread.
+//
+// Split diagonal (SPLIT). E_r = 2 + a_r^2/beta held in one FP32 number
+// quantises a_r^2/beta to ulp(2) = 2.4e-7, i.e. perturbs the decay rate of
+// every mode by up to 1.2e-7 beta per unit time: negligible unless beta * T
+// is large (the error grows as 1.2e-7 beta T on modes that survive). The
+// SPLIT variant keeps e_r = a_r^2/beta alone and forms
+// y_r = (psi_{r-1} + psi_{r+1} - 2 psi_r) - e_r psi_r, one more FMA per angle.
 #pragma once
 
 #include "se2n_internal.h"
@@ -177,7 +184,7 @@ __device__ __forceinline__ void tear_setup(const TearInfo<P> &ti, const T (&diag
     }
 }
 
-template <int N, int P, bool FP64>
+template <int N, int P, bool FP64, bool SPLIT>
 __global__ void __launch_bounds__(256) k_diffuse(const DiffuseArgs a) {
     constexpr int K = N / P;
     constexpr int Q = TearInfo<P>::Q;
@@ -225,8 +232,13 @@ __global__ void __launch_bounds__(256) k_diffuse(const DiffuseArgs a) {
         for (int j = 0; j < K; ++j) {
             const int r = row0 + rstep * j;
             const float ar = fmaf(wx, a.cs[r], wy * a.sn[r]);
-            E[j] = fmaf(ar * ar, a.inv_beta, 2.0f);
-            dmod[j] = a.inv_c + E[j];
+            if constexpr (SPLIT) {
+                E[j] = ar * ar * a.inv_beta;
+                dmod[j] = (a.inv_c + 2.0f) + E[j];
+            } else {
+                E[j] = fmaf(ar * ar, a.inv_beta, 2.0f);
+                dmod[j] = a.inv_c + E[j];
+            }
         }
         const float d_loc0 = dmod[0];
         const float d_part = (P == 1) ? d_loc0 : xshfl(d_loc0, P - 1);  // the i row across my tear
@@ -291,8 +303,14 @@ __global__ void __launch_bounds__(256) k_diffuse(const DiffuseArgs a) {
                 const float Li = (j == 0) ? li : pim[j - 1];
                 const float Rr = (j == K - 1) ? rr : pr[j + 1];
                 const float Ri = (j == K - 1) ? ri : pim[j + 1];
-                const float yr = fmaf(-E[j], pr[j], Lr + Rr);
-                const float yi = fmaf(-E[j], pim[j], Li + Ri);
+                float yr, yi;
+                if constexpr (SPLIT) {
+                    yr = fmaf(-E[j], pr[j], fmaf(-2.0f, pr[j], Lr + Rr));
+                    yi = fmaf(-E[j], pim[j], fmaf(-2.0f, pim[j], Li + Ri));
+                } else {
+                    yr = fmaf(-E[j], pr[j], Lr + Rr);
+                    yi = fmaf(-E[j], pim[j], Li + Ri);
+                }
                 if (j == 0) {
                     zr[0] = yr;
                     zi[0] = yi;
@@ -361,13 +379,16 @@ __global__ void __launch_bounds__(256) k_diffuse(const DiffuseArgs a) {
 
 }  // namespace se2n
 
-// One instantiation per (N, P, fp64): a table entry with the kernel pointer.
-#define SE2N_DIFFUSE_ENTRY(N_, P_)                                            \
-    {N_, P_, false, (const void *)&se2n::k_diffuse<N_, P_, false>},           \
-    {N_, P_, true, (const void *)&se2n::k_diffuse<N_, P_, true>}
+// One instantiation per (N, P, fp64 correction, split diagonal): a table
+// entry with the kernel pointer.
+#define SE2N_DIFFUSE_ENTRY(N_, P_)                                                  \
+    {N_, P_, false, false, (const void *)&se2n::k_diffuse<N_, P_, false, false>},   \
+    {N_, P_, true, false, (const void *)&se2n::k_diffuse<N_, P_, true, false>},     \
+    {N_, P_, false, true, (const void *)&se2n::k_diffuse<N_, P_, false, true>},     \
+    {N_, P_, true, true, (const void *)&se2n::k_diffuse<N_, P_, true, true>}
 
 struct DiffuseEntry {
     int N, P;
-    bool fp64;
+    bool fp64, split;
     const void *fn;
 };

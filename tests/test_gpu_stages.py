@@ -37,6 +37,9 @@ def _gpu_bins(f32, mask, N, conv=0, sigma=1.0, flat_tol=1e-4):
 
 
 def _check_bins(got, o, N, flat_tol):
+    """Exact agreement where the oracle's decision is far from a boundary
+    (in units of the FP32 gradient error), a valid neighbouring choice
+    elsewhere. Returns the fraction of pixels where the two differ."""
     rel = o["rel"]
     # angle uncertainty in bins: (N/pi) * (grad error / |grad|)
     ang = (N / np.pi) * FP32_GRAD_ERR / np.maximum(rel, 1e-30)
@@ -44,7 +47,7 @@ def _check_bins(got, o, N, flat_tol):
     ambiguous_bin = (o["bins"] != oracle.BIN_FLAT) & (o["margin"] <= ang)
     sure = ~(ambiguous_flat | ambiguous_bin)
     np.testing.assert_array_equal(got[sure], o["bins"][sure])
-    # ambiguous pixels: the GPU's bin must be one of the two nearest bins, or flat near the threshold
+    # elsewhere the GPU's bin must be one of the two nearest bins, or flat near the threshold
     u = o["phi"] * N / np.pi + 0.5
     lo = np.mod(np.floor(u - 0.5), N).astype(int)
     hi = np.mod(lo + 1, N)
@@ -52,7 +55,7 @@ def _check_bins(got, o, N, flat_tol):
     ok = (got[amb] == lo[amb]) | (got[amb] == hi[amb]) | (got[amb] == o["bins"][amb])
     ok |= ambiguous_flat[amb] & (got[amb] == oracle.BIN_FLAT)
     assert ok.all()
-    return amb.mean()
+    return (got != o["bins"]).mean(), amb.mean()
 
 
 @pytest.mark.parametrize("maker,N", [(lambda: synth.workload_small(64, 64), 16),
@@ -63,9 +66,9 @@ def test_orientation_bins(maker, N):
     f32 = w.f.astype(np.float32)
     o = oracle.orient(f32.astype(np.float64), w.mask, N)
     got = _gpu_bins(f32, w.mask, N)
-    frac = _check_bins(got, o, N, 1e-4)
-    print(f"{w.H}x{w.W} N={N}: ambiguous fraction {frac:.2e}")
-    assert frac < 5e-3
+    diff, amb = _check_bins(got, o, N, 1e-4)
+    print(f"{w.H}x{w.W} N={N}: differing bins {diff:.2e}, near-tie pixels {amb:.2e}")
+    assert diff < 1e-3
 
 
 def test_orientation_flat_regions_and_2pi_convention():
@@ -76,7 +79,7 @@ def test_orientation_flat_regions_and_2pi_convention():
     f32 = f.astype(np.float32)
     o = oracle.orient(f32.astype(np.float64), mask, N, angle_conv=1)
     got = _gpu_bins(f32, mask, N, conv=1)
-    assert (o["bins"] == oracle.BIN_FLAT).mean() > 0.2
+    assert (o["bins"] == oracle.BIN_FLAT).mean() > 0.1
     sure_flat = (o["bins"] == oracle.BIN_FLAT) & (o["rel"] < 1e-4 - FP32_GRAD_ERR)
     assert (got[sure_flat] == oracle.BIN_FLAT).all()
     # 2 pi / N grid: directions mod pi land on bins 0 .. N/2
