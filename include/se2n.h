@@ -88,7 +88,8 @@ typedef struct se2n_plan se2n_plan;
  *            lifted to every angle.
  *   proj     SE2N_PROJ_MAX or SE2N_PROJ_MEAN.
  *   final_mix  1: restore once more after the last interval (not in the paper).
- *   guard    restoration divides by h(t_i) only where h(t_i) > guard.
+ *   guard    restoration divides by h(t_i) only where h(t_i) > guard * h(0)
+ *            (relative; 0.1 keeps sigma <= 5.5 at eps = 0.5).
  *   diffuse_flags  SE2N_DIFFUSE_* flags passed to every diffusion. */
 typedef struct se2n_params {
     int N;
@@ -107,7 +108,7 @@ typedef struct se2n_params {
 
 /* Fill p with the defaults: N=32, beta=0.25, T=2, steps=100, rounds=1,
  * eps=0.5, sigma_smooth=1, flat_tol=1e-4, proj=max, final_mix=0,
- * guard=1e-12, diffuse_flags=0. SE2N_EINVAL if p is NULL. */
+ * guard=0.1, diffuse_flags=0. SE2N_EINVAL if p is NULL. */
 SE2N_API se2n_status se2n_params_default(se2n_params *p);
 
 /* Map the paper's weighting alpha and time T_paper on an M x M image with N
@@ -183,9 +184,11 @@ SE2N_API se2n_status se2n_diffuse(se2n_plan *plan, void *vol_hat, double beta, d
 
 /* Static restoration (Section 5, SR) on the real volume, in place: with
  * h(t) = max_r Re vol_r and h(0) = max_r of the lift of (f, mask, bins), a
- * known pixel (mask != 0) with h(t) > guard has every angle scaled by
- * sigma = (eps h(0) + (1-eps) h(t)) / h(t); a known pixel with h(t) <= guard
- * becomes eps * lift + (1-eps) * Re vol. Imaginary parts are set to 0
+ * known pixel (mask != 0) with h(t) > guard h(0) has every angle scaled by
+ * sigma = (eps h(0) + (1-eps) h(t)) / h(t); a known pixel with
+ * h(t) <= guard h(0) (or h(t) <= 0) becomes eps * lift + (1-eps) * Re vol,
+ * which moves its maximum to about the same value without dividing by a
+ * near-zero h(t). Imaginary parts are set to 0
  * everywhere. 0 <= eps <= 1. */
 SE2N_API se2n_status se2n_mix(se2n_plan *plan, void *vol, const float *f, const uint8_t *mask,
                      const uint8_t *bins, double eps, double guard);

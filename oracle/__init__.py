@@ -36,8 +36,9 @@ Readings taken where the paper is silent (all listed in the design doc):
   * a pixel whose smoothed gradient is below flat_tol * max|grad| is "flat"
     and is lifted to every angle;
   * the image is zero on the corrupted set B (f = f * mask);
-  * restoration divides by h(t_i) only where h(t_i) > guard; elsewhere the
-    good pixel is mixed linearly with its lift.
+  * restoration divides by h(t_i) only where h(t_i) > guard * h(0) (guard =
+    0.1, so sigma <= 5.5 for eps = 0.5); elsewhere the good pixel is mixed
+    linearly with its lift.
 
 Parity status of each function is recorded in the design doc; every function here
 is pinned by a test under tests/ against a closed form, a dense brute-force
@@ -80,7 +81,7 @@ class Params:
     angle_conv: int = 0      # 0: th_r = pi r/N, 1: th_r = 2 pi r/N
     flat_tol: float = 1e-4
     final_mix: int = 0       # 1: restore once more after the last interval
-    guard: float = 1e-12
+    guard: float = 0.1       # relative: sigma only where h(t) > guard * h(0)
 
 
 # ----------------------------------------------------------------------------
@@ -287,22 +288,24 @@ def diffuse_dense(vol_hat, beta, T, steps, angle_conv=0):
 # static restoration
 # ----------------------------------------------------------------------------
 
-def mix(vol, f, mask, bins, eps, guard=1e-12):
+def mix(vol, f, mask, bins, eps, guard=0.1):
     """Static restoration at the good pixels (Section 5, SR).
 
     h(t) = max over angles of the current volume, h(0) = max over angles of
     the lift; on G every angle is scaled by
-    sigma = (eps h(0) + (1-eps) h(t)) / h(t). Where h(t) <= guard the good
-    pixel is instead set to eps * lift + (1-eps) * psi. The volume is real
-    (the imaginary part is dropped everywhere); B pixels are otherwise
-    unchanged."""
+    sigma = (eps h(0) + (1-eps) h(t)) / h(t). Where h(t) <= guard * h(0) (or
+    h(t) <= 0) the division would amplify the small residual by more than
+    eps/guard, and the good pixel is instead set to eps * lift + (1-eps) * psi,
+    which moves its maximum to about the same eps h(0) + (1-eps) h(t). The
+    volume is real (the imaginary part is dropped everywhere); B pixels are
+    otherwise unchanged."""
     re = np.asarray(vol).real.copy()
     N = re.shape[0]
     psi0 = lift(f, mask, bins, N).real
     h0 = psi0.max(axis=0)
     ht = re.max(axis=0)
     good = np.asarray(mask) != 0
-    scaled = good & (ht > guard)
+    scaled = good & (ht > guard * h0) & (ht > 0.0)
     lin = good & ~scaled
     sig = np.ones_like(ht)
     sig[scaled] = (eps * h0[scaled] + (1.0 - eps) * ht[scaled]) / ht[scaled]

@@ -255,7 +255,7 @@ se2n_status se2n_params_default(se2n_params *p) {
     p->flat_tol = 1e-4;
     p->proj = SE2N_PROJ_MAX;
     p->final_mix = 0;
-    p->guard = 1e-12;
+    p->guard = 0.1;
     p->diffuse_flags = 0;
     return SE2N_OK;
 }

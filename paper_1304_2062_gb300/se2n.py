@@ -213,7 +213,7 @@ def se2n_diffuse(plan, vol_hat, beta, T, steps, flags=0):
     _check(lib.se2n_diffuse(plan.handle, _ptr(vol_hat), beta, T, steps, flags), "se2n_diffuse")
 
 
-def se2n_mix(plan, vol, f, mask, bins, eps, guard=1e-12):
+def se2n_mix(plan, vol, f, mask, bins, eps, guard=0.1):
     _check(lib.se2n_mix(plan.handle, _ptr(vol), _ptr(f), _ptr(mask), _ptr(bins), eps, guard), "se2n_mix")
 
 

@@ -128,10 +128,11 @@ def test_static_restoration(eps):
     o = oracle.orient(f32.astype(np.float64), w.mask, N)
     rng = np.random.default_rng(2)
     vol = (rng.uniform(0.05, 1.0, (N, w.H, w.W)) + 1j * rng.standard_normal((N, w.H, w.W)) * 1e-3).astype(np.complex64)
-    vol[:, 3, 5] = -0.25  # a known pixel (if known) with h(t) <= guard takes the linear branch
+    vol[:, 3, 5] = -0.25  # h(t) <= 0: the linear branch (if the pixel is known)
+    vol[:, 7, 9] = 0.01   # h(t) = 0.01 <= 0.1 h(0) when f > 0.1: the linear branch
     plan = se2n.se2n_plan_create(w.H, w.W, N)
     v = t_c64(vol)
-    se2n.se2n_mix(plan, v, t_f32(f32), t_u8(w.mask), t_u8(o["bins"]), eps, 1e-12)
+    se2n.se2n_mix(plan, v, t_f32(f32), t_u8(w.mask), t_u8(o["bins"]), eps, 0.1)
     got = host(v)
     plan.close()
     ref = oracle.mix(vol.astype(np.complex128), f32.astype(np.float64), w.mask, o["bins"], eps)

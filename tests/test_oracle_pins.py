@@ -364,6 +364,24 @@ def test_mix_scales_good_pixels_by_sigma(oracle_mod):
     np.testing.assert_allclose(out.real.ravel(), sigma * vol.real.ravel(), rtol=1e-15)
 
 
+def test_mix_relative_guard_blends_linearly(oracle_mod):
+    """h(t) = 0.04 <= 0.1 h(0) = 0.08: the division would amplify by ~10,
+    so the pixel is blended with its lift instead."""
+    N = 4
+    f = np.array([[0.8]])
+    mask = np.array([[1]], np.uint8)
+    bins = np.array([[3]], np.uint8)
+    vol = np.array([0.01, 0.04, 0.02, 0.03]).reshape(N, 1, 1).astype(complex)
+    out = oracle_mod.mix(vol, f, mask, bins, 0.5, guard=0.1)
+    lift = np.array([0.0, 0.0, 0.0, 0.8])
+    np.testing.assert_allclose(out.real.ravel(), 0.5 * lift + 0.5 * vol.real.ravel(), rtol=1e-15)
+    # just above the threshold the sigma rescaling applies
+    vol2 = vol * 2.5   # h(t) = 0.1 > 0.08
+    out2 = oracle_mod.mix(vol2, f, mask, bins, 0.5, guard=0.1)
+    sigma = (0.5 * 0.8 + 0.5 * 0.1) / 0.1
+    np.testing.assert_allclose(out2.real.ravel(), sigma * vol2.real.ravel(), rtol=1e-14)
+
+
 def test_mix_guard_blends_linearly(oracle_mod):
     N = 4
     f = np.array([[0.8]])
