@@ -72,6 +72,7 @@ typedef enum se2n_status {
 #define SE2N_DIFFUSE_SM_FP64 1     /* Sherman-Morrison correction scalars in FP64 */
 #define SE2N_DIFFUSE_SPLIT_DIAG 2  /* keep a_r^2/beta apart from the angular second difference
                                       (always on when beta * T > 8, see se2n_diffuse) */
+#define SE2N_DIFFUSE_FULL_CORRECTION 4  /* apply the corner correction on every angle (no truncation) */
 
 /* Largest N this build has kernels for, and the N it supports. */
 #define SE2N_MAX_N 64
@@ -179,7 +180,11 @@ SE2N_API se2n_status se2n_inverse(se2n_plan *plan, void *vol);
  * side as (psi_{r-1} + psi_{r+1} - 2 psi_r) - (a_r^2/beta) psi_r instead of
  * with the fused coefficient 2 + a_r^2/beta, whose FP32 rounding perturbs
  * decay rates by ~1.2e-7 beta per unit time; it costs one FMA more per angle
- * and is selected automatically when beta * T > 8. */
+ * and is selected automatically when beta * T > 8.
+ * When beta*dt <= ~0.067 (no FP64 flag), a packed fast path runs: the corner
+ * correction vector decays by a factor <= 1e-9 within 6 angles of the tear,
+ * so it is applied on those angles only (below FP32 resolution elsewhere);
+ * SE2N_DIFFUSE_FULL_CORRECTION forces the general kernel. */
 SE2N_API se2n_status se2n_diffuse(se2n_plan *plan, void *vol_hat, double beta, double T, int steps, int flags);
 
 /* Static restoration (Section 5, SR) on the real volume, in place: with

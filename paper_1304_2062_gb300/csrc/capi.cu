@@ -76,7 +76,7 @@ se2n_status check_plan(se2n_plan *plan) {
 
 se2n_status diffuse_impl(se2n_plan *plan, float2 *vol, double beta, double T, int steps, int flags) {
     if (!(beta > 0.0) || !(T >= 0.0) || steps < 1 || !isfinite(beta) || !isfinite(T)) return SE2N_EINVAL;
-    if (flags & ~(SE2N_DIFFUSE_SM_FP64 | SE2N_DIFFUSE_SPLIT_DIAG)) return SE2N_EINVAL;
+    if (flags & ~(SE2N_DIFFUSE_SM_FP64 | SE2N_DIFFUSE_SPLIT_DIAG | SE2N_DIFFUSE_FULL_CORRECTION)) return SE2N_EINVAL;
     if (T == 0.0) return SE2N_OK;
     const double dt = T / steps;
     const double bdt = beta * dt;
@@ -85,6 +85,7 @@ se2n_status diffuse_impl(se2n_plan *plan, float2 *vol, double beta, double T, in
     // The fused diagonal 2 + a^2/beta perturbs decay rates by ~1.2e-7 beta per
     // unit time; past beta T = 8 that exceeds 1e-6 and the split form is used.
     const bool split = (flags & SE2N_DIFFUSE_SPLIT_DIAG) != 0 || beta * T > 8.0;
+    const bool fast = !(flags & SE2N_DIFFUSE_FULL_CORRECTION) && se2n_diffuse_truncation_ok(bdt);
 
     DiffuseArgs a;
     a.vol = vol;
@@ -106,7 +107,7 @@ se2n_status diffuse_impl(se2n_plan *plan, float2 *vol, double beta, double T, in
     int blocks = plan->diffuse_blocks;
     if (blocks <= 0) {
         int per_sm = 0;
-        cudaError_t e = se2n_diffuse_occupancy(plan->N, P, fp64, split, block, &per_sm, nullptr);
+        cudaError_t e = se2n_diffuse_occupancy(plan->N, P, fp64, split, fast, block, &per_sm, nullptr);
         if (e != cudaSuccess) return cuda_status(plan, e);
         if (per_sm < 1) per_sm = 1;
         blocks = plan->num_sms * per_sm;
@@ -116,7 +117,7 @@ se2n_status diffuse_impl(se2n_plan *plan, float2 *vol, double beta, double T, in
     if (blocks < 1) blocks = 1;
     StageTimer timer(plan, SE2N_STAGE_DIFFUSE);
     plan->kernels += 1;
-    cudaError_t e = se2n_launch_diffuse(plan->N, P, fp64, split, a, block, blocks, plan->stream);
+    cudaError_t e = se2n_launch_diffuse(plan->N, P, fp64, split, fast, a, block, blocks, plan->stream);
     if (e == cudaErrorInvalidValue && !se2n_diffuse_has(plan->N, P)) return SE2N_EUNSUPPORTED;
     return cuda_status(plan, e);
 }
@@ -169,7 +170,8 @@ se2n_status check_params(const se2n_plan *plan, const se2n_params *p) {
     if (!(p->eps >= 0.0 && p->eps <= 1.0) || !(p->sigma_smooth > 0.0) || !(p->flat_tol >= 0.0)) return SE2N_EINVAL;
     if ((p->proj != SE2N_PROJ_MAX && p->proj != SE2N_PROJ_MEAN) || (p->final_mix != 0 && p->final_mix != 1))
         return SE2N_EINVAL;
-    if (!(p->guard >= 0.0) || (p->diffuse_flags & ~(SE2N_DIFFUSE_SM_FP64 | SE2N_DIFFUSE_SPLIT_DIAG)))
+    if (!(p->guard >= 0.0) ||
+        (p->diffuse_flags & ~(SE2N_DIFFUSE_SM_FP64 | SE2N_DIFFUSE_SPLIT_DIAG | SE2N_DIFFUSE_FULL_CORRECTION)))
         return SE2N_EINVAL;
     if (!isfinite(p->beta) || !isfinite(p->T) || !isfinite(p->sigma_smooth) || !isfinite(p->guard))
         return SE2N_EINVAL;
@@ -447,7 +449,7 @@ se2n_status se2n_plan_diffuse_info(se2n_plan *plan, int *regs_per_thread, int *b
     SE2N_TRY(check_plan(plan));
     int regs = 0, per_sm = 0;
     cudaError_t e =
-        se2n_diffuse_occupancy(plan->N, plan->diffuse_P, false, false, plan->diffuse_block, &per_sm, &regs);
+        se2n_diffuse_occupancy(plan->N, plan->diffuse_P, false, false, true, plan->diffuse_block, &per_sm, &regs);
     if (e != cudaSuccess) return cuda_status(plan, e);
     if (regs_per_thread) *regs_per_thread = regs;
     if (blocks_per_sm) *blocks_per_sm = per_sm;

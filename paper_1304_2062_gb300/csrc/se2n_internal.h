@@ -56,11 +56,15 @@ struct DiffuseArgs {
 
 // Launch the diffusion kernel for (N, P, fp64 correction) on `stream`.
 // Returns cudaErrorInvalidValue if no instantiation exists.
-cudaError_t se2n_launch_diffuse(int N, int P, bool sm_fp64, bool split, const DiffuseArgs &a, int block,
-                                int blocks, cudaStream_t stream);
+// `fast` asks for the packed fast path (truncated tear correction); it is
+// used when an instantiation exists and sm_fp64 is off.
+cudaError_t se2n_launch_diffuse(int N, int P, bool sm_fp64, bool split, bool fast, const DiffuseArgs &a,
+                                int block, int blocks, cudaStream_t stream);
 // Occupancy query for the same kernel: blocks per SM and registers per thread.
-cudaError_t se2n_diffuse_occupancy(int N, int P, bool sm_fp64, bool split, int block, int *blocks_per_sm,
-                                   int *regs);
+cudaError_t se2n_diffuse_occupancy(int N, int P, bool sm_fp64, bool split, bool fast, int block,
+                                   int *blocks_per_sm, int *regs);
+// Whether the tear corrections may be truncated for this beta * dt.
+bool se2n_diffuse_truncation_ok(double beta_dt);
 // Whether an instantiation exists for (N, P).
 bool se2n_diffuse_has(int N, int P);
 int se2n_diffuse_default_P(int N);

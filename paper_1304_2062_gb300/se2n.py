@@ -25,6 +25,8 @@ SE2N_BIN_FLAT = 255
 SE2N_PROJ_MAX = 0
 SE2N_PROJ_MEAN = 1
 SE2N_DIFFUSE_SM_FP64 = 1
+SE2N_DIFFUSE_SPLIT_DIAG = 2
+SE2N_DIFFUSE_FULL_CORRECTION = 4
 SE2N_MAX_N = 64
 
 

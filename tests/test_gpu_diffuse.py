@@ -210,3 +210,20 @@ def test_unsupported_and_invalid_plans():
         se2n.se2n_plan_tune_diffuse(plan, 2, 100, 0)
     assert e.value.status == se2n.SE2N_EINVAL
     plan.close()
+
+
+@pytest.mark.parametrize("N,P", [(16, 1), (16, 2), (32, 2), (32, 4), (64, 4), (30, 2)])
+@pytest.mark.parametrize("beta,T,S", [(0.25, 2.0, 500), (0.5, 2.0, 14), (1.0, 1.3, 20)])
+def test_fast_path_equals_general_path_and_oracle(N, P, beta, T, S):
+    """The packed fast path (truncated corner correction) against the
+    general kernel (full correction) and the oracle. beta*dt = 1e-3, 0.0714
+    (just past the truncation threshold, 0.0675: general kernel on both
+    sides) and 0.065 (just inside it)."""
+    vol = synth.random_volume(N, 26, 34, seed=N + P, dtype=np.complex64)
+    ref = oracle.diffuse(vol.astype(np.complex128), beta, T, S)
+    fast = _run(vol, N, beta, T, S, tune=(P, 128, 0))
+    full = _run(vol, N, beta, T, S, flags=se2n.SE2N_DIFFUSE_FULL_CORRECTION, tune=(P, 128, 0))
+    ef, eg = rel_l2(fast, ref), rel_l2(full, ref)
+    print(f"N={N} P={P} beta*dt={beta * T / S:.4f}: fast {ef:.2e} general {eg:.2e}")
+    assert ef <= REL_L2 and eg <= REL_L2
+    assert rel_l2(fast, full) <= 2e-6
