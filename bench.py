@@ -224,7 +224,7 @@ def run_ours(args, rank, world, local_rank):
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 4),
                 "traffic": args.traffic if args.traffic is not None else stored_traffic(),
-                "kernel": "k_diffuse<32,2,false>",
+                "kernel": "k_diffuse_x2<32,2,false> (packed FP32 pairs, truncated corner correction)",
                 "flops_per_update": FLOPS_PER_UPDATE, "updates_per_launch": updates_per_launch,
                 "avg_launch_ms": round(d_avg_s * 1e3, 4),
                 "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop/FMA x 2070 MHz (derived, not measured)",

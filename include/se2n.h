@@ -222,7 +222,7 @@ SE2N_API se2n_status se2n_inpaint_host(se2n_plan *plan, const float *f_host, con
 
 /* Tuning of the diffusion launch (used by the autotuner): threads per
  * frequency P (1, 2 or 4; 0 = default for the plan's N), threads per block
- * (multiple of 32, <= 1024; 0 = 128) and blocks (0 = as many as fit on the
+ * (multiple of 32, <= 256; 0 = 256) and blocks (0 = as many as fit on the
  * device at once). SE2N_EUNSUPPORTED if no kernel exists for (N, P). */
 SE2N_API se2n_status se2n_plan_tune_diffuse(se2n_plan *plan, int threads_per_freq, int block_threads, int blocks);
 

@@ -285,7 +285,7 @@ se2n_status se2n_plan_create(se2n_plan **out, int H, int W, int N, int angle_con
     plan->HW = (long long)H * W;
     plan->stream = (cudaStream_t)stream;
     plan->diffuse_P = se2n_diffuse_default_P(N);
-    plan->diffuse_block = 128;
+    plan->diffuse_block = 256;
     plan->diffuse_blocks = 0;
     cudaError_t e = cudaGetDevice(&plan->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&plan->num_sms, cudaDevAttrMultiProcessorCount, plan->device);
@@ -434,7 +434,7 @@ se2n_status se2n_inpaint_host(se2n_plan *plan, const float *f_host, const uint8_
 se2n_status se2n_plan_tune_diffuse(se2n_plan *plan, int threads_per_freq, int block_threads, int blocks) {
     SE2N_TRY(check_plan(plan));
     const int P = threads_per_freq ? threads_per_freq : se2n_diffuse_default_P(plan->N);
-    const int block = block_threads ? block_threads : 128;
+    const int block = block_threads ? block_threads : 256;
     if (P != 1 && P != 2 && P != 4) return SE2N_EINVAL;
     if (block < 32 || block > 256 || (block % 32) || blocks < 0) return SE2N_EINVAL;
     if (!se2n_diffuse_has(plan->N, P)) return SE2N_EUNSUPPORTED;

@@ -14,7 +14,7 @@ import pytest
 
 import oracle
 import synth
-from _gpu import MAX_REL, REL_L2, host, rel_l2, t_f32, t_u8
+from _gpu import MAX_REL, MAX_REL_RESTORED, REL_L2, host, rel_l2, t_f32, t_u8
 
 pytestmark = pytest.mark.gpu
 
@@ -54,7 +54,7 @@ def _compare(w, p, conv=0, flags=0, tune=None):
     mx = np.abs(got - ref).max() / np.abs(f64).max()
     r2 = rel_l2(got, ref)
     print(f"{w.H}x{w.W} N={p.N} S={p.steps} R={p.rounds}: max-abs/max|f| {mx:.2e}, rel-L2 {r2:.2e}")
-    assert mx <= MAX_REL
+    assert mx <= (MAX_REL if p.rounds == 1 else MAX_REL_RESTORED)
     assert r2 <= REL_L2
     return got
 
@@ -120,7 +120,7 @@ def test_full_512_N32_ten_rounds_against_stored_oracle():
     mx = np.abs(got - ref).max() / np.abs(w.f).max()
     r2 = rel_l2(got, ref)
     print(f"512^2 N=32 10x500: max-abs/max|f| {mx:.2e}, rel-L2 {r2:.2e}")
-    assert mx <= MAX_REL
+    assert mx <= MAX_REL_RESTORED
     assert r2 <= REL_L2
 
 
