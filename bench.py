@@ -121,7 +121,7 @@ def kernel_source_hash():
     only valid for the exact kernel it was captured on."""
     import hashlib
     h = hashlib.sha256()
-    for name in ("diffuse_impl.cuh", "diffuse.cu"):
+    for name in ("diffuse_impl.cuh", "diffuse_x2.cuh", "diffuse.cu"):
         with open(os.path.join(ROOT, "paper_1304_2062_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
