@@ -306,6 +306,81 @@ def cpu_baseline(w, steps=75, rounds=2):
                       "frequencies, numpy FFTs)"}
 
 
+def run_batch(args, rank, world, local_rank):
+    """256 seeded images of uneven size (128..1024) and N (16, 32, 64): the
+    whole method through one graph-captured batch with one persistent
+    diffusion launch, against one se2n_inpaint per image. Images are dealt
+    to ranks round-robin (weak scaling)."""
+    import torch
+
+    from paper_1304_2062_gb300 import se2n
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    allw = synth.workload_batch()
+    mine = [allw[i] for i in shard(len(allw), rank, world)]
+    stream = torch.cuda.Stream(dev)
+    w0 = allw[0]
+    prm = se2n.se2n_params_default(beta=w0.beta, T=w0.T, steps=w0.steps, rounds=w0.rounds, eps=w0.eps)
+    imgs = []
+    for w in mine:
+        imgs.append((torch.tensor(w.f.astype(np.float32), device=dev), torch.tensor(w.mask, device=dev),
+                     torch.zeros((w.H, w.W), dtype=torch.float32, device=dev), w.N))
+    t0 = time.perf_counter()
+    batch = se2n.se2n_batch_create(imgs, prm, 0, se2n.SE2N_BATCH_AUTOTUNE, stream)
+    create_s = time.perf_counter() - t0
+    info = se2n.se2n_batch_get_info(batch)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    updates = info["updates_per_run"]
+
+    def timed(fn, k):
+        evs = []
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                fn(batch)
+            torch.cuda.synchronize(dev)
+            if dist:
+                dist.barrier()
+            for _ in range(k):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn(batch)
+                b.record(stream)
+                evs.append((a, b))
+            torch.cuda.synchronize(dev)
+        return max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), dist, dev) / k
+
+    with ClockSampler(local_rank) as clocks:
+        ms = timed(se2n.se2n_batch_run, args.steps)
+    ms_per_image = timed(se2n.se2n_batch_run_per_image, max(1, min(args.steps, 3)))
+    ms_diff = timed(se2n.se2n_batch_run_diffusion, max(1, min(args.steps, 5)))
+    achieved = FLOPS_PER_UPDATE * updates / (ms_diff / 1e3) / 1e12
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
+    batch.close()
+    if dist:
+        dist.destroy_process_group()
+    total_updates = updates * world
+    return {"metric": METRIC, "value": total_updates / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch of 256 seeded images, sides U{128..1024}, N U{16,32,64}, "
+                                   "60-90% corrupted, beta=0.25, T=2, 100 CN steps, 1 interval",
+                       "images_this_rank": len(mine), "updates_per_step": total_updates,
+                       "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas"},
+            "per_image_launches": {"ms_per_step": ms_per_image, "value": total_updates / (ms_per_image / 1e3),
+                                   "speedup_of_batched": ms_per_image / ms},
+            "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
+                         "frac": round(achieved / peak, 4), "traffic": None, "kernel": "k_diffuse_batch",
+                         "avg_launch_ms": round(ms_diff, 3)},
+            "autotune": info, "create_s": create_s, "clocks": clocks.summary(),
+            "gpu_launches": len(mine) * 6 + w0.rounds * 1}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
@@ -337,6 +412,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["512", "batch"], default="512",
+                    help="512: the 512x512 N=32 10x500-step inpaint (default); batch: 256 uneven images")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per diffusion launch from an ncu capture of the current kernel")
     args = ap.parse_args()
@@ -347,6 +424,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         res = run_reference(args, rank, world)
+    elif args.workload == "batch":
+        res = run_batch(args, rank, world, local_rank)
     else:
         res = run_ours(args, rank, world, local_rank)
     if rank == 0 and res is not None:

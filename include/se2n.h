@@ -255,6 +255,72 @@ SE2N_API se2n_status se2n_plan_profile(se2n_plan *plan, int enable);
  * reset != 0 clears them afterwards. */
 SE2N_API se2n_status se2n_plan_profile_read(se2n_plan *plan, se2n_profile *out, int reset);
 
+/* ---------------------------------------------------------------------------
+ * Batches: many images of uneven size and N through one persistent,
+ * graph-captured diffusion launch per restoration interval.
+ *
+ * se2n_batch_create plans the whole batch once: a cuFFT plan per distinct
+ * (H, W, N), device storage for every lifted volume and bin map, the work
+ * items of the persistent diffusion kernel, and a CUDA graph of the complete
+ * method (orientation, lift, DFT, diffusion, restoration, inverse DFT,
+ * projection) for every image, captured on the batch's stream. Each warp of
+ * the persistent kernel claims (image, frequency-tile) items from an atomic
+ * counter; the tile size, block size and threads per frequency are taken
+ * from the built-in table or, with SE2N_BATCH_AUTOTUNE, chosen by timing
+ * the candidates on this batch. se2n_batch_run replays the graph.
+ * ------------------------------------------------------------------------- */
+
+typedef struct se2n_image_desc {
+    const float *f;       /* [H][W] device image */
+    const uint8_t *mask;  /* [H][W] device mask, nonzero = known */
+    float *out;           /* [H][W] device output image */
+    const uint8_t *bins;  /* [H][W] device bin map to use, or NULL to compute it (se2n_orient) */
+    int H, W, N;          /* H, W even; N one of 16, 32, 64 */
+} se2n_image_desc;
+
+typedef struct se2n_batch se2n_batch;
+
+#define SE2N_BATCH_AUTOTUNE 1
+
+typedef struct se2n_batch_info {
+    int images;
+    int items;              /* work items of the persistent kernel */
+    int tile_passes;        /* warp passes (32/P frequencies each) per item */
+    int block, blocks;      /* launch shape of the persistent kernel */
+    int p16, p32, p64;      /* threads per frequency for N = 16, 32, 64 */
+    int fast, split;        /* packed fast path; split diagonal */
+    int candidates;         /* launch shapes timed by the autotuner (0 if not run) */
+    double best_ms, worst_ms;        /* their fastest and slowest diffusion time */
+    double updates_per_run;          /* sum of H W N steps rounds over the images */
+    double volume_bytes;             /* device bytes of the lifted volumes */
+} se2n_batch_info;
+
+/* Build a batch of `count` images. p->N is ignored (each image has its
+ * own); every other field of p applies to all images. angle_conv as in
+ * se2n_plan_create. flags: SE2N_BATCH_AUTOTUNE. The image, mask and output
+ * buffers must stay valid while the batch is used. Allocates about
+ * 8 N H W + H W bytes per image plus the plans. Synchronizes the stream. */
+SE2N_API se2n_status se2n_batch_create(se2n_batch **out, const se2n_image_desc *imgs, int count,
+                                       const se2n_params *p, int angle_conv, int flags, void *stream);
+
+/* Run the whole method for every image of the batch (one graph launch). */
+SE2N_API se2n_status se2n_batch_run(se2n_batch *b);
+
+/* The same results computed the plain way: se2n_inpaint on each image in
+ * turn (one diffusion launch per image and interval). Bitwise equal to
+ * se2n_batch_run; kept as the comparison baseline. */
+SE2N_API se2n_status se2n_batch_run_per_image(se2n_batch *b);
+
+/* One persistent diffusion launch over the batch's volumes as they stand
+ * (one interval of T/rounds in `steps` steps), outside the graph: for timing
+ * the kernel on its own. */
+SE2N_API se2n_status se2n_batch_run_diffusion(se2n_batch *b);
+
+SE2N_API se2n_status se2n_batch_get_info(se2n_batch *b, se2n_batch_info *out);
+
+/* Release everything (after synchronizing the stream). NULL is a no-op. */
+SE2N_API se2n_status se2n_batch_destroy(se2n_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,7 +18,8 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libse2n.so")
 
-SOURCES = ["capi.cu", "pixel.cu", "diffuse.cu", "diffuse_tab_a.cu", "diffuse_tab_b.cu", "diffuse_tab_c.cu"]
+SOURCES = ["capi.cu", "pixel.cu", "diffuse.cu", "diffuse_tab_a.cu", "diffuse_tab_b.cu", "diffuse_tab_c.cu",
+           "batch_kern.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -67,8 +68,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not os.path.isdir(libdir):
         libdir = os.path.join(cuda, "lib")
     tmp = LIB + f".tmp{os.getpid()}"
+    exports = os.path.join(OUT_DIR, "exports.map")
+    with open(exports, "w") as fh:
+        fh.write("{ global: se2n_*; local: *; };\n")   # the C ABI only
     link = [nvcc, "-shared", *ARCH, "-cudart", "shared", *objs, "-o", tmp, "-L", libdir, "-lcufft",
-            "-Xlinker", f"-rpath,{libdir}"]
+            "-Xlinker", f"-rpath,{libdir}", "-Xlinker", f"--version-script={exports}"]
     res = subprocess.run(link, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stderr}")

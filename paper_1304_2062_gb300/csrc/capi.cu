@@ -5,6 +5,10 @@
 #include <new>
 #include <stdint.h>
 
+#include <algorithm>
+#include <vector>
+
+#include "se2n_batch.h"
 #include "se2n_internal.h"
 
 namespace {
@@ -74,6 +78,28 @@ se2n_status check_plan(se2n_plan *plan) {
     return SE2N_OK;
 }
 
+}  // namespace
+
+StepParams step_params(double beta, double beta_dt, int steps) {
+    StepParams sp;
+    sp.steps = steps;
+    sp.inv_c_d = 2.0 / beta_dt;
+    sp.inv_beta_d = 1.0 / beta;
+    sp.inv_c = (float)sp.inv_c_d;
+    sp.inv_beta = (float)sp.inv_beta_d;
+    return sp;
+}
+
+void angle_table(int N, int angle_conv, float *cs, float *sn, int count) {
+    const double dth = (angle_conv ? 2.0 : 1.0) * kPi / N;
+    for (int r = 0; r < count; ++r) {
+        cs[r] = r < N ? (float)cos(dth * r) : 0.0f;
+        sn[r] = r < N ? (float)sin(dth * r) : 0.0f;
+    }
+}
+
+namespace {
+
 se2n_status diffuse_impl(se2n_plan *plan, float2 *vol, double beta, double T, int steps, int flags) {
     if (!(beta > 0.0) || !(T >= 0.0) || steps < 1 || !isfinite(beta) || !isfinite(T)) return SE2N_EINVAL;
     if (flags & ~(SE2N_DIFFUSE_SM_FP64 | SE2N_DIFFUSE_SPLIT_DIAG | SE2N_DIFFUSE_FULL_CORRECTION)) return SE2N_EINVAL;
@@ -92,16 +118,8 @@ se2n_status diffuse_impl(se2n_plan *plan, float2 *vol, double beta, double T, in
     a.HW = plan->HW;
     a.H = plan->H;
     a.W = plan->W;
-    a.steps = steps;
-    a.inv_c_d = 2.0 / bdt;
-    a.inv_beta_d = 1.0 / beta;
-    a.inv_c = (float)a.inv_c_d;
-    a.inv_beta = (float)a.inv_beta_d;
-    const double dth = (plan->angle_conv ? 2.0 : 1.0) * kPi / plan->N;
-    for (int r = 0; r < SE2N_MAX_N; ++r) {
-        a.cs[r] = r < plan->N ? (float)cos(dth * r) : 0.0f;
-        a.sn[r] = r < plan->N ? (float)sin(dth * r) : 0.0f;
-    }
+    a.sp = step_params(beta, bdt, steps);
+    angle_table(plan->N, plan->angle_conv, a.cs, a.sn, SE2N_MAX_N);
     const int P = plan->diffuse_P;
     const int block = plan->diffuse_block;
     int blocks = plan->diffuse_blocks;
@@ -494,6 +512,391 @@ se2n_status se2n_plan_profile_read(se2n_plan *plan, se2n_profile *out, int reset
         }
         plan->kernels = 0;
     }
+    return SE2N_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// batches
+// ---------------------------------------------------------------------------
+
+struct se2n_batch {
+    int count = 0, angle_conv = 0, device = 0;
+    cudaStream_t stream = nullptr;
+    se2n_params p{};
+    std::vector<se2n_image_desc> imgs;
+    std::vector<se2n_plan *> plans;    // owned, one per distinct (H, W, N)
+    std::vector<se2n_plan *> plan_of;  // per image
+    char *arena = nullptr;
+    size_t vol_bytes = 0;
+    std::vector<float2 *> vols;
+    std::vector<uint8_t *> bins;
+    std::vector<BatchImage> h_imgs;
+    float *d_tables = nullptr;
+    BatchImage *d_imgs = nullptr;
+    BatchItem *d_items = nullptr;
+    size_t items_cap = 0;
+    unsigned int *d_counter = nullptr;
+    int n_items = 0, config = 0, passes = 8, block = 256, blocks = 0;
+    bool fast = false, split = false;
+    int candidates = 0;
+    double best_ms = 0.0, worst_ms = 0.0, updates = 0.0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int num_sms = 0;
+    bool flags_autotune = false;
+};
+
+namespace {
+
+std::vector<BatchItem> build_items(const se2n_batch *b, int config, int passes) {
+    std::vector<int> order(b->count);
+    for (int i = 0; i < b->count; ++i) order[i] = i;
+    // costliest first: larger N, then larger images
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        const se2n_image_desc &a = b->imgs[x], &c = b->imgs[y];
+        if (a.N != c.N) return a.N > c.N;
+        return (long long)a.H * a.W > (long long)c.H * c.W;
+    });
+    std::vector<BatchItem> items;
+    for (int i : order) {
+        const se2n_image_desc &d = b->imgs[i];
+        const long long HW = (long long)d.H * d.W;
+        const int per = 32 / se2n_batch_config_P(config, d.N);
+        const long long tile = (long long)per * passes;
+        for (long long f0 = 0; f0 < HW; f0 += tile) {
+            BatchItem it;
+            it.image = i;
+            it.first = f0;
+            it.count = (int)std::min(tile, HW - f0);
+            items.push_back(it);
+        }
+    }
+    return items;
+}
+
+se2n_status upload_items(se2n_batch *b, const std::vector<BatchItem> &items) {
+    if (items.size() > b->items_cap) {
+        cudaFree(b->d_items);
+        b->d_items = nullptr;
+        b->items_cap = 0;
+        cudaError_t e = cudaMalloc(&b->d_items, sizeof(BatchItem) * items.size());
+        if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? SE2N_ENOMEM : SE2N_ECUDA;
+        b->items_cap = items.size();
+    }
+    cudaError_t e = cudaMemcpyAsync(b->d_items, items.data(), sizeof(BatchItem) * items.size(),
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    b->n_items = (int)items.size();
+    return e == cudaSuccess ? SE2N_OK : SE2N_ECUDA;
+}
+
+se2n_status batch_diffuse(se2n_batch *b, int steps, double T) {
+    const double dt = T / steps;
+    const StepParams sp = step_params(b->p.beta, b->p.beta * dt, steps);
+    cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned int), b->stream);
+    if (e == cudaSuccess)
+        e = se2n_launch_diffuse_batch(b->config, b->fast, b->split, sp, b->d_tables, b->d_imgs, b->d_items,
+                                      b->n_items, b->d_counter, b->block, b->blocks, b->stream);
+    return e == cudaSuccess ? SE2N_OK : SE2N_ECUDA;
+}
+
+se2n_status set_shape(se2n_batch *b, int config, int passes, int block) {
+    int per_sm = 0;
+    if (se2n_batch_occupancy(config, b->fast, b->split, block, &per_sm) != cudaSuccess) return SE2N_ECUDA;
+    b->config = config;
+    b->passes = passes;
+    b->block = block;
+    b->blocks = b->num_sms * std::max(per_sm, 1);
+    return upload_items(b, build_items(b, config, passes));
+}
+
+// Time every candidate launch shape on this batch (diffusion only, a few
+// steps, on zeroed volumes that the graph's lift overwrites later) and keep
+// the fastest.
+se2n_status autotune(se2n_batch *b) {
+    const int steps = std::min(b->p.steps, 16);
+    const double T = b->p.T / b->p.rounds * steps / b->p.steps;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SE2N_ECUDA;
+    double best = 1e30, worst = 0.0;
+    int bc = 0, bp = 8, bb = 256;
+    const int passes_c[] = {2, 8, 32};
+    const int block_c[] = {128, 256};
+    se2n_status st = SE2N_OK;
+    for (int c = 0; c < se2n_batch_configs() && st == SE2N_OK; ++c)
+        for (int pc : passes_c)
+            for (int bl : block_c) {
+                st = set_shape(b, c, pc, bl);
+                if (st != SE2N_OK) break;
+                st = batch_diffuse(b, steps, T);  // warm
+                cudaEventRecord(e0, b->stream);
+                if (st == SE2N_OK) st = batch_diffuse(b, steps, T);
+                cudaEventRecord(e1, b->stream);
+                if (cudaEventSynchronize(e1) != cudaSuccess) st = SE2N_ECUDA;
+                if (st != SE2N_OK) break;
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                b->candidates += 1;
+                worst = std::max(worst, (double)ms);
+                if (ms < best) {
+                    best = ms;
+                    bc = c;
+                    bp = pc;
+                    bb = bl;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != SE2N_OK) return st;
+    b->best_ms = best;
+    b->worst_ms = worst;
+    return set_shape(b, bc, bp, bb);
+}
+
+se2n_status enqueue_batch(se2n_batch *b) {
+    const se2n_params &p = b->p;
+    const double Tr = p.T / p.rounds;
+    for (int i = 0; i < b->count; ++i) {
+        se2n_plan *pl = b->plan_of[i];
+        const se2n_image_desc &d = b->imgs[i];
+        if (d.bins) {
+            if (cudaMemcpyAsync(b->bins[i], d.bins, (size_t)pl->HW, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess)
+                return SE2N_ECUDA;
+        } else {
+            SE2N_TRY(orient_impl(pl, d.f, d.mask, p.sigma_smooth, p.flat_tol, b->bins[i]));
+        }
+        SE2N_TRY(lift_impl(pl, d.f, d.mask, b->bins[i], b->vols[i]));
+        SE2N_TRY(fft(pl, pl->fft_vol, b->vols[i], CUFFT_FORWARD));
+    }
+    SE2N_TRY(batch_diffuse(b, p.steps, Tr));
+    for (int r = 1; r < p.rounds; ++r) {
+        for (int i = 0; i < b->count; ++i) {
+            se2n_plan *pl = b->plan_of[i];
+            const se2n_image_desc &d = b->imgs[i];
+            SE2N_TRY(fft(pl, pl->fft_vol, b->vols[i], CUFFT_INVERSE));
+            SE2N_TRY(mix_impl(pl, b->vols[i], d.f, d.mask, b->bins[i], (float)(1.0 / (double)pl->HW),
+                              (float)p.eps, (float)p.guard));
+            SE2N_TRY(fft(pl, pl->fft_vol, b->vols[i], CUFFT_FORWARD));
+        }
+        SE2N_TRY(batch_diffuse(b, p.steps, Tr));
+    }
+    for (int i = 0; i < b->count; ++i) {
+        se2n_plan *pl = b->plan_of[i];
+        const se2n_image_desc &d = b->imgs[i];
+        const float inv_hw = (float)(1.0 / (double)pl->HW);
+        SE2N_TRY(fft(pl, pl->fft_vol, b->vols[i], CUFFT_INVERSE));
+        float scale = inv_hw;
+        if (p.final_mix) {
+            SE2N_TRY(mix_impl(pl, b->vols[i], d.f, d.mask, b->bins[i], inv_hw, (float)p.eps, (float)p.guard));
+            scale = 1.0f;
+        }
+        SE2N_TRY(project_impl(pl, b->vols[i], scale, p.proj, d.out));
+    }
+    return SE2N_OK;
+}
+
+void free_batch(se2n_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (se2n_plan *pl : b->plans) {
+        cudaStreamSynchronize(pl->stream);
+        free_plan(pl);
+    }
+    cudaFree(b->arena);
+    cudaFree(b->d_tables);
+    cudaFree(b->d_imgs);
+    cudaFree(b->d_items);
+    cudaFree(b->d_counter);
+    delete b;
+}
+
+se2n_status create_batch(se2n_batch *b, const se2n_image_desc *imgs) {
+    cudaError_t e = cudaGetDevice(&b->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
+    if (e != cudaSuccess) return SE2N_ECUDA;
+    b->imgs.assign(imgs, imgs + b->count);
+    // plans per distinct shape
+    b->plan_of.resize(b->count);
+    for (int i = 0; i < b->count; ++i) {
+        const se2n_image_desc &d = imgs[i];
+        se2n_plan *found = nullptr;
+        for (se2n_plan *pl : b->plans)
+            if (pl->H == d.H && pl->W == d.W && pl->N == d.N) found = pl;
+        if (!found) {
+            SE2N_TRY(se2n_plan_create(&found, d.H, d.W, d.N, b->angle_conv, (void *)b->stream));
+            b->plans.push_back(found);
+        }
+        b->plan_of[i] = found;
+        b->updates += (double)d.H * d.W * d.N * b->p.steps * b->p.rounds;
+    }
+    // one arena: every volume 256-byte aligned, then the bin maps
+    std::vector<size_t> voff(b->count), boff(b->count);
+    size_t off = 0;
+    for (int i = 0; i < b->count; ++i) {
+        voff[i] = off;
+        off += ((size_t)imgs[i].H * imgs[i].W * imgs[i].N * sizeof(float2) + 255) / 256 * 256;
+    }
+    b->vol_bytes = off;
+    for (int i = 0; i < b->count; ++i) {
+        boff[i] = off;
+        off += ((size_t)imgs[i].H * imgs[i].W + 255) / 256 * 256;
+    }
+    e = cudaMalloc(&b->arena, off);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? SE2N_ENOMEM : SE2N_ECUDA;
+    b->vols.resize(b->count);
+    b->bins.resize(b->count);
+    for (int i = 0; i < b->count; ++i) {
+        b->vols[i] = (float2 *)(b->arena + voff[i]);
+        b->bins[i] = (uint8_t *)(b->arena + boff[i]);
+    }
+    // angle tables, one per distinct N, cos[N] then sin[N]
+    std::vector<float> tables;
+    std::vector<int> table_N, table_off;
+    b->h_imgs.resize(b->count);
+    for (int i = 0; i < b->count; ++i) {
+        const int N = imgs[i].N;
+        int t = -1;
+        for (size_t j = 0; j < table_N.size(); ++j)
+            if (table_N[j] == N) t = table_off[j];
+        if (t < 0) {
+            t = (int)tables.size();
+            table_N.push_back(N);
+            table_off.push_back(t);
+            std::vector<float> cs(N), sn(N);
+            angle_table(N, b->angle_conv, cs.data(), sn.data(), N);
+            tables.insert(tables.end(), cs.begin(), cs.end());
+            tables.insert(tables.end(), sn.begin(), sn.end());
+        }
+        BatchImage &bi = b->h_imgs[i];
+        bi.vol = b->vols[i];
+        bi.H = imgs[i].H;
+        bi.W = imgs[i].W;
+        bi.HW = (long long)bi.H * bi.W;
+        bi.N = N;
+        bi.table = t;
+    }
+    e = cudaMalloc(&b->d_tables, sizeof(float) * tables.size());
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_imgs, sizeof(BatchImage) * b->count);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, 256);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_tables, tables.data(), sizeof(float) * tables.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_imgs, b->h_imgs.data(), sizeof(BatchImage) * b->count, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? SE2N_ENOMEM : SE2N_ECUDA;
+    // numerical path (as se2n_diffuse chooses it for one interval)
+    const double Tr = b->p.T / b->p.rounds;
+    const double bdt = b->p.beta * Tr / b->p.steps;
+    b->split = (b->p.diffuse_flags & SE2N_DIFFUSE_SPLIT_DIAG) || b->p.beta * Tr > 8.0;
+    b->fast = !(b->p.diffuse_flags & SE2N_DIFFUSE_FULL_CORRECTION) && se2n_diffuse_truncation_ok(bdt);
+    if (cudaMemsetAsync(b->arena, 0, b->vol_bytes, b->stream) != cudaSuccess) return SE2N_ECUDA;
+    if (b->flags_autotune) {
+        SE2N_TRY(autotune(b));
+    } else {
+        SE2N_TRY(set_shape(b, 0, 8, 256));
+    }
+    // capture the whole method into a graph
+    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SE2N_ECUDA;
+    se2n_status st = enqueue_batch(b);
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(b->stream, &g);
+    if (st != SE2N_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (ce != cudaSuccess) return SE2N_ECUDA;
+    b->graph = g;
+    if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) return SE2N_ECUDA;
+    return SE2N_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+se2n_status se2n_batch_create(se2n_batch **out, const se2n_image_desc *imgs, int count, const se2n_params *p,
+                              int angle_conv, int flags, void *stream) {
+    if (!out || !imgs || count < 1 || !p || (angle_conv != 0 && angle_conv != 1)) return SE2N_EINVAL;
+    if (flags & ~SE2N_BATCH_AUTOTUNE) return SE2N_EINVAL;
+    for (int i = 0; i < count; ++i) {
+        const se2n_image_desc &d = imgs[i];
+        if (d.H < 2 || d.W < 2 || (d.H % 2) || (d.W % 2) || (long long)d.H * d.W > (1LL << 28)) return SE2N_EINVAL;
+        if (d.N != 16 && d.N != 32 && d.N != 64) return SE2N_EUNSUPPORTED;
+        if (!device_ptr(d.f, 8) || !device_ptr(d.mask, 2) || !device_ptr(d.out, 8)) return SE2N_EINVAL;
+        if (d.bins && !device_ptr(d.bins, 2)) return SE2N_EINVAL;
+    }
+    se2n_batch *b = new (std::nothrow) se2n_batch();
+    if (!b) return SE2N_ENOMEM;
+    b->count = count;
+    b->angle_conv = angle_conv;
+    b->stream = (cudaStream_t)stream;
+    b->p = *p;
+    b->flags_autotune = (flags & SE2N_BATCH_AUTOTUNE) != 0;
+    se2n_status st = SE2N_OK;
+    for (int i = 0; i < count && st == SE2N_OK; ++i) {
+        se2n_plan probe{};
+        probe.N = imgs[i].N;
+        se2n_params q = *p;
+        q.N = imgs[i].N;
+        st = check_params(&probe, &q);
+    }
+    if (st == SE2N_OK) st = create_batch(b, imgs);
+    if (st == SE2N_OK) st = cudaStreamSynchronize(b->stream) == cudaSuccess ? SE2N_OK : SE2N_ECUDA;
+    if (st != SE2N_OK) {
+        (void)cudaGetLastError();
+        free_batch(b);
+        return st;
+    }
+    *out = b;
+    return SE2N_OK;
+}
+
+se2n_status se2n_batch_run(se2n_batch *b) {
+    if (!b) return SE2N_EINVAL;
+    return cudaGraphLaunch(b->exec, b->stream) == cudaSuccess ? SE2N_OK : SE2N_ECUDA;
+}
+
+se2n_status se2n_batch_run_per_image(se2n_batch *b) {
+    if (!b) return SE2N_EINVAL;
+    for (int i = 0; i < b->count; ++i) {
+        se2n_params q = b->p;
+        q.N = b->imgs[i].N;
+        SE2N_TRY(inpaint_impl(b->plan_of[i], b->imgs[i].f, b->imgs[i].mask, b->imgs[i].bins, &q, b->vols[i],
+                              b->imgs[i].out));
+    }
+    return SE2N_OK;
+}
+
+se2n_status se2n_batch_run_diffusion(se2n_batch *b) {
+    if (!b) return SE2N_EINVAL;
+    return batch_diffuse(b, b->p.steps, b->p.T / b->p.rounds);
+}
+
+se2n_status se2n_batch_get_info(se2n_batch *b, se2n_batch_info *out) {
+    if (!b || !out) return SE2N_EINVAL;
+    out->images = b->count;
+    out->items = b->n_items;
+    out->tile_passes = b->passes;
+    out->block = b->block;
+    out->blocks = b->blocks;
+    out->p16 = se2n_batch_config_P(b->config, 16);
+    out->p32 = se2n_batch_config_P(b->config, 32);
+    out->p64 = se2n_batch_config_P(b->config, 64);
+    out->fast = b->fast;
+    out->split = b->split;
+    out->candidates = b->candidates;
+    out->best_ms = b->best_ms;
+    out->worst_ms = b->worst_ms;
+    out->updates_per_run = b->updates;
+    out->volume_bytes = (double)b->vol_bytes;
+    return SE2N_OK;
+}
+
+se2n_status se2n_batch_destroy(se2n_batch *b) {
+    if (!b) return SE2N_OK;
+    cudaStreamSynchronize(b->stream);
+    free_batch(b);
     return SE2N_OK;
 }
 

@@ -184,8 +184,13 @@ __device__ __forceinline__ void tear_setup(const TearInfo<P> &ti, const T (&diag
     }
 }
 
+// One frequency group: the P adjacent lanes of this warp integrate all
+// steps of frequency fc of the H x W volume vol[N][H][W], loading and
+// storing its N-vector. Every lane of the warp must call this together
+// (shuffles); a lane with !active works on a valid frequency without storing.
 template <int N, int P, bool FP64, bool SPLIT>
-__global__ void __launch_bounds__(256) k_diffuse(const DiffuseArgs a) {
+__device__ __forceinline__ void diffuse_group(const StepParams &sp, const float *cs, const float *sn,
+    float2 *vol, int H, int W, long long HW, long long fc, bool active) {
     constexpr int K = N / P;
     constexpr int Q = TearInfo<P>::Q;
     static_assert(P == 1 || P == 2 || P == 4, "threads per frequency");
@@ -199,181 +204,185 @@ __global__ void __launch_bounds__(256) k_diffuse(const DiffuseArgs a) {
     const int row0 = (P == 1) ? 0 : (ti.iside ? (p >> 1) * half : (p >> 1) * half + half - 1);
     const int rstep = (P == 1 || ti.iside) ? 1 : -1;
 
+    const int k = (int)(fc / W);
+    const int l = (int)(fc - (long long)k * W);
+    const float wx = sin_2pi_frac(l, W);
+    const float wy = sin_2pi_frac(k, H);
+    float2 *col = vol + (long long)row0 * HW + fc;
+    const long long stride = (long long)rstep * HW;
+
+    float pr[K], pim[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const float2 v = col[j * stride];
+        pr[j] = v.x;
+        pim[j] = v.y;
+    }
+
+    // ---- per-frequency setup (once per launch) ----
+    float E[K], dmod[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const int r = row0 + rstep * j;
+        const float ar = fmaf(wx, cs[r], wy * sn[r]);
+        if constexpr (SPLIT) {
+            E[j] = ar * ar * sp.inv_beta;
+            dmod[j] = (sp.inv_c + 2.0f) + E[j];
+        } else {
+            E[j] = fmaf(ar * ar, sp.inv_beta, 2.0f);
+            dmod[j] = sp.inv_c + E[j];
+        }
+    }
+    const float d_loc0 = dmod[0];
+    const float d_part = (P == 1) ? d_loc0 : xshfl(d_loc0, P - 1);  // the i row across my tear
+    const float d_i = ti.iside ? d_loc0 : d_part;
+    if constexpr (P == 1) {
+        dmod[K - 1] = dmod[K - 1] + 1.0f / d_loc0;
+        dmod[0] = 2.0f * d_loc0;
+    } else if (ti.iside) {
+        dmod[0] = 2.0f * d_loc0;
+    } else {
+        dmod[0] = d_loc0 + 1.0f / d_part;
+    }
+
+    float G[K], G2[K], Z2[Q][K], M1, M2;
+    float hc[Q] = {}, hc1 = 0.0f;
+    double hcd[Q] = {}, hcd1 = 0.0;
+    if constexpr (FP64) {
+        double dd[K], Gd[K], M1d, M2d;
+        const double inv_c = sp.inv_c_d;
+        double dE[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const int r = row0 + rstep * j;
+            const double ar = (double)wx * (double)cs[r] + (double)wy * (double)sn[r];
+            dE[j] = 2.0 + ar * ar * sp.inv_beta_d;
+            dd[j] = inv_c + dE[j];
+        }
+        const double dl0 = dd[0];
+        const double dpart = (P == 1) ? dl0 : xshfl(dl0, P - 1);
+        const double di = ti.iside ? dl0 : dpart;
+        if constexpr (P == 1) {
+            dd[K - 1] += 1.0 / dl0;
+            dd[0] = 2.0 * dl0;
+        } else if (ti.iside) {
+            dd[0] = 2.0 * dl0;
+        } else {
+            dd[0] = dl0 + 1.0 / dpart;
+        }
+        tear_setup<K, P, double>(ti, dd, di, dl0, Z2, hcd, hcd1, Gd, M1d, M2d);
+        torn_factor<K, P, float>(dmod, G, M1, M2);
+    } else {
+        tear_setup<K, P, float>(ti, dmod, d_i, d_loc0, Z2, hc, hc1, G, M1, M2);
+    }
+#pragma unroll
+    for (int j = 0; j < K; ++j) G2[j] = 2.0f * G[j];
+
+    // ---- the fused CN steps ----
+#pragma unroll 1
+    for (int s = 0; s < sp.steps; ++s) {
+        float lr, li, rr, ri;
+        if constexpr (P == 1) {
+            lr = pr[K - 1]; li = pim[K - 1];
+            rr = pr[0]; ri = pim[0];
+        } else {
+            lr = xshfl(pr[0], P - 1); li = xshfl(pim[0], P - 1);
+            rr = xshfl(pr[K - 1], 1); ri = xshfl(pim[K - 1], 1);
+        }
+        float zr[K], zi[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const float Lr = (j == 0) ? lr : pr[j - 1];
+            const float Li = (j == 0) ? li : pim[j - 1];
+            const float Rr = (j == K - 1) ? rr : pr[j + 1];
+            const float Ri = (j == K - 1) ? ri : pim[j + 1];
+            float yr, yi;
+            if constexpr (SPLIT) {
+                yr = fmaf(-E[j], pr[j], fmaf(-2.0f, pr[j], Lr + Rr));
+                yi = fmaf(-E[j], pim[j], fmaf(-2.0f, pim[j], Li + Ri));
+            } else {
+                yr = fmaf(-E[j], pr[j], Lr + Rr);
+                yi = fmaf(-E[j], pim[j], Li + Ri);
+            }
+            if (j == 0) {
+                zr[0] = yr;
+                zi[0] = yi;
+            } else {
+                zr[j] = fmaf(G[j - 1], zr[j - 1], yr);
+                zi[j] = fmaf(G[j - 1], zi[j - 1], yi);
+            }
+        }
+        float xr, xi;
+        if constexpr (P == 1) {
+            xr = zr[K - 1];
+            xi = zi[K - 1];
+        } else {
+            const float qr = xshfl(zr[K - 1], 1), qi = xshfl(zi[K - 1], 1);
+            xr = fmaf(M1, zr[K - 1], M2 * qr);
+            xi = fmaf(M1, zi[K - 1], M2 * qi);
+        }
+        const float xlr = xr, xli = xi;
+        pr[K - 1] = fmaf(G2[K - 1], xr, pr[K - 1]);
+        pim[K - 1] = fmaf(G2[K - 1], xi, pim[K - 1]);
+#pragma unroll
+        for (int j = K - 2; j >= 0; --j) {
+            xr = fmaf(G[j + 1], xr, zr[j]);
+            xi = fmaf(G[j + 1], xi, zi[j]);
+            pr[j] = fmaf(G2[j], xr, pr[j]);
+            pim[j] = fmaf(G2[j], xi, pim[j]);
+        }
+        float ar[Q], ai[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            if constexpr (FP64) {
+                double tr, tq;
+                if constexpr (P == 1) {
+                    tr = hcd[q] * (double)xr + hcd1 * (double)xlr;
+                    tq = hcd[q] * (double)xi + hcd1 * (double)xli;
+                } else {
+                    tr = group_sum<P, double>(hcd[q] * (double)xr);
+                    tq = group_sum<P, double>(hcd[q] * (double)xi);
+                }
+                ar[q] = (float)tr;
+                ai[q] = (float)tq;
+            } else if constexpr (P == 1) {
+                ar[q] = fmaf(hc[q], xr, hc1 * xlr);
+                ai[q] = fmaf(hc[q], xi, hc1 * xli);
+            } else {
+                ar[q] = group_sum<P, float>(hc[q] * xr);
+                ai[q] = group_sum<P, float>(hc[q] * xi);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                pr[j] = fmaf(-ar[q], Z2[q][j], pr[j]);
+                pim[j] = fmaf(-ai[q], Z2[q][j], pim[j]);
+            }
+        }
+    }
+
+    if (active) {
+#pragma unroll
+        for (int j = 0; j < K; ++j) col[j * stride] = make_float2(pr[j], pim[j]);
+    }
+}
+
+template <int N, int P, bool FP64, bool SPLIT>
+__global__ void __launch_bounds__(256) k_diffuse(const __grid_constant__ DiffuseArgs a) {
+    const int lane = threadIdx.x & 31;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long slot = tid / P;
     const long long nslots = (long long)gridDim.x * blockDim.x / P;
     const long long warp_slot0 = (tid - lane) / P;
-
     // The loop bound is uniform across the warp (warp_slot0), so every lane
     // takes part in every shuffle; lanes past the end work on a clamped
     // frequency and do not store.
     for (long long base = 0; warp_slot0 + base < a.HW; base += nslots) {
         const long long f = slot + base;
         const bool active = f < a.HW;
-        const long long fc = active ? f : a.HW - 1;
-        const int k = (int)(fc / a.W);
-        const int l = (int)(fc - (long long)k * a.W);
-        const float wx = sin_2pi_frac(l, a.W);
-        const float wy = sin_2pi_frac(k, a.H);
-        float2 *col = a.vol + (long long)row0 * a.HW + fc;
-        const long long stride = (long long)rstep * a.HW;
-
-        float pr[K], pim[K];
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            const float2 v = col[j * stride];
-            pr[j] = v.x;
-            pim[j] = v.y;
-        }
-
-        // ---- per-frequency setup (once per launch) ----
-        float E[K], dmod[K];
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            const int r = row0 + rstep * j;
-            const float ar = fmaf(wx, a.cs[r], wy * a.sn[r]);
-            if constexpr (SPLIT) {
-                E[j] = ar * ar * a.inv_beta;
-                dmod[j] = (a.inv_c + 2.0f) + E[j];
-            } else {
-                E[j] = fmaf(ar * ar, a.inv_beta, 2.0f);
-                dmod[j] = a.inv_c + E[j];
-            }
-        }
-        const float d_loc0 = dmod[0];
-        const float d_part = (P == 1) ? d_loc0 : xshfl(d_loc0, P - 1);  // the i row across my tear
-        const float d_i = ti.iside ? d_loc0 : d_part;
-        if constexpr (P == 1) {
-            dmod[K - 1] = dmod[K - 1] + 1.0f / d_loc0;
-            dmod[0] = 2.0f * d_loc0;
-        } else if (ti.iside) {
-            dmod[0] = 2.0f * d_loc0;
-        } else {
-            dmod[0] = d_loc0 + 1.0f / d_part;
-        }
-
-        float G[K], G2[K], Z2[Q][K], M1, M2;
-        float hc[Q] = {}, hc1 = 0.0f;
-        double hcd[Q] = {}, hcd1 = 0.0;
-        if constexpr (FP64) {
-            double dd[K], Gd[K], M1d, M2d;
-            const double inv_c = a.inv_c_d;
-            double dE[K];
-#pragma unroll
-            for (int j = 0; j < K; ++j) {
-                const int r = row0 + rstep * j;
-                const double ar = (double)wx * (double)a.cs[r] + (double)wy * (double)a.sn[r];
-                dE[j] = 2.0 + ar * ar * a.inv_beta_d;
-                dd[j] = inv_c + dE[j];
-            }
-            const double dl0 = dd[0];
-            const double dpart = (P == 1) ? dl0 : xshfl(dl0, P - 1);
-            const double di = ti.iside ? dl0 : dpart;
-            if constexpr (P == 1) {
-                dd[K - 1] += 1.0 / dl0;
-                dd[0] = 2.0 * dl0;
-            } else if (ti.iside) {
-                dd[0] = 2.0 * dl0;
-            } else {
-                dd[0] = dl0 + 1.0 / dpart;
-            }
-            tear_setup<K, P, double>(ti, dd, di, dl0, Z2, hcd, hcd1, Gd, M1d, M2d);
-            torn_factor<K, P, float>(dmod, G, M1, M2);
-        } else {
-            tear_setup<K, P, float>(ti, dmod, d_i, d_loc0, Z2, hc, hc1, G, M1, M2);
-        }
-#pragma unroll
-        for (int j = 0; j < K; ++j) G2[j] = 2.0f * G[j];
-
-        // ---- the fused CN steps ----
-#pragma unroll 1
-        for (int s = 0; s < a.steps; ++s) {
-            float lr, li, rr, ri;
-            if constexpr (P == 1) {
-                lr = pr[K - 1]; li = pim[K - 1];
-                rr = pr[0]; ri = pim[0];
-            } else {
-                lr = xshfl(pr[0], P - 1); li = xshfl(pim[0], P - 1);
-                rr = xshfl(pr[K - 1], 1); ri = xshfl(pim[K - 1], 1);
-            }
-            float zr[K], zi[K];
-#pragma unroll
-            for (int j = 0; j < K; ++j) {
-                const float Lr = (j == 0) ? lr : pr[j - 1];
-                const float Li = (j == 0) ? li : pim[j - 1];
-                const float Rr = (j == K - 1) ? rr : pr[j + 1];
-                const float Ri = (j == K - 1) ? ri : pim[j + 1];
-                float yr, yi;
-                if constexpr (SPLIT) {
-                    yr = fmaf(-E[j], pr[j], fmaf(-2.0f, pr[j], Lr + Rr));
-                    yi = fmaf(-E[j], pim[j], fmaf(-2.0f, pim[j], Li + Ri));
-                } else {
-                    yr = fmaf(-E[j], pr[j], Lr + Rr);
-                    yi = fmaf(-E[j], pim[j], Li + Ri);
-                }
-                if (j == 0) {
-                    zr[0] = yr;
-                    zi[0] = yi;
-                } else {
-                    zr[j] = fmaf(G[j - 1], zr[j - 1], yr);
-                    zi[j] = fmaf(G[j - 1], zi[j - 1], yi);
-                }
-            }
-            float xr, xi;
-            if constexpr (P == 1) {
-                xr = zr[K - 1];
-                xi = zi[K - 1];
-            } else {
-                const float qr = xshfl(zr[K - 1], 1), qi = xshfl(zi[K - 1], 1);
-                xr = fmaf(M1, zr[K - 1], M2 * qr);
-                xi = fmaf(M1, zi[K - 1], M2 * qi);
-            }
-            const float xlr = xr, xli = xi;
-            pr[K - 1] = fmaf(G2[K - 1], xr, pr[K - 1]);
-            pim[K - 1] = fmaf(G2[K - 1], xi, pim[K - 1]);
-#pragma unroll
-            for (int j = K - 2; j >= 0; --j) {
-                xr = fmaf(G[j + 1], xr, zr[j]);
-                xi = fmaf(G[j + 1], xi, zi[j]);
-                pr[j] = fmaf(G2[j], xr, pr[j]);
-                pim[j] = fmaf(G2[j], xi, pim[j]);
-            }
-            float ar[Q], ai[Q];
-#pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                if constexpr (FP64) {
-                    double tr, tq;
-                    if constexpr (P == 1) {
-                        tr = hcd[q] * (double)xr + hcd1 * (double)xlr;
-                        tq = hcd[q] * (double)xi + hcd1 * (double)xli;
-                    } else {
-                        tr = group_sum<P, double>(hcd[q] * (double)xr);
-                        tq = group_sum<P, double>(hcd[q] * (double)xi);
-                    }
-                    ar[q] = (float)tr;
-                    ai[q] = (float)tq;
-                } else if constexpr (P == 1) {
-                    ar[q] = fmaf(hc[q], xr, hc1 * xlr);
-                    ai[q] = fmaf(hc[q], xi, hc1 * xli);
-                } else {
-                    ar[q] = group_sum<P, float>(hc[q] * xr);
-                    ai[q] = group_sum<P, float>(hc[q] * xi);
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < K; ++j) {
-#pragma unroll
-                for (int q = 0; q < Q; ++q) {
-                    pr[j] = fmaf(-ar[q], Z2[q][j], pr[j]);
-                    pim[j] = fmaf(-ai[q], Z2[q][j], pim[j]);
-                }
-            }
-        }
-
-        if (active) {
-#pragma unroll
-            for (int j = 0; j < K; ++j) col[j * stride] = make_float2(pr[j], pim[j]);
-        }
+        diffuse_group<N, P, FP64, SPLIT>(a.sp, a.cs, a.sn, a.vol, a.H, a.W, a.HW, active ? f : a.HW - 1, active);
     }
 }
 

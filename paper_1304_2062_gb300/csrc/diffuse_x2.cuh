@@ -73,8 +73,13 @@ __device__ __forceinline__ f32x2 group_sum2(f32x2 v) {
 
 constexpr int kTruncRows = 6;
 
+// One frequency group: the P adjacent lanes of this warp integrate all
+// steps of frequency fc of the H x W volume vol[N][H][W], loading and
+// storing its N-vector. Every lane of the warp must call this together
+// (shuffles); a lane with !active works on a valid frequency without storing.
 template <int N, int P, bool SPLIT>
-__global__ void __launch_bounds__(256) k_diffuse_x2(const DiffuseArgs a) {
+__device__ __forceinline__ void diffuse_group_x2(const StepParams &sp, const float *cs, const float *sn,
+    float2 *vol, int H, int W, long long HW, long long fc, bool active) {
     constexpr int K = N / P;
     constexpr int Q = TearInfo<P>::Q;
     constexpr int KZ = (K < kTruncRows) ? K : kTruncRows;
@@ -88,139 +93,146 @@ __global__ void __launch_bounds__(256) k_diffuse_x2(const DiffuseArgs a) {
     const int row0 = (P == 1) ? 0 : (ti.iside ? (p >> 1) * half : (p >> 1) * half + half - 1);
     const int rstep = (P == 1 || ti.iside) ? 1 : -1;
 
+    const int k = (int)(fc / W);
+    const int l = (int)(fc - (long long)k * W);
+    const float wx = sin_2pi_frac(l, W);
+    const float wy = sin_2pi_frac(k, H);
+    float2 *col = vol + (long long)row0 * HW + fc;
+    const long long stride = (long long)rstep * HW;
+
+    f32x2 ps[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const float2 v = col[j * stride];
+        ps[j] = pk2(v.x, v.y);
+    }
+
+    // ---- per-frequency setup (scalar, once per launch) ----
+    float E[K], dmod[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const int r = row0 + rstep * j;
+        const float ar = fmaf(wx, cs[r], wy * sn[r]);
+        if constexpr (SPLIT) {
+            E[j] = ar * ar * sp.inv_beta;
+            dmod[j] = (sp.inv_c + 2.0f) + E[j];
+        } else {
+            E[j] = fmaf(ar * ar, sp.inv_beta, 2.0f);
+            dmod[j] = sp.inv_c + E[j];
+        }
+    }
+    const float d_loc0 = dmod[0];
+    const float d_part = (P == 1) ? d_loc0 : xshfl(d_loc0, P - 1);
+    const float d_i = ti.iside ? d_loc0 : d_part;
+    if constexpr (P == 1) {
+        dmod[K - 1] = dmod[K - 1] + 1.0f / d_loc0;
+        dmod[0] = 2.0f * d_loc0;
+    } else if (ti.iside) {
+        dmod[0] = 2.0f * d_loc0;
+    } else {
+        dmod[0] = d_loc0 + 1.0f / d_part;
+    }
+    float G[K], Z2[Q][K], M1, M2, hc[Q], hc1;
+    tear_setup<K, P, float>(ti, dmod, d_i, d_loc0, Z2, hc, hc1, G, M1, M2);
+
+    f32x2 nEd[K], Gd[K], G2d[K], Zd[KZ], ZdEnd[KZ];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        nEd[j] = dup2(-E[j]);
+        Gd[j] = dup2(G[j]);
+        G2d[j] = dup2(2.0f * G[j]);
+    }
+    const int own = (Q == 1 || ti.tear == 0) ? 0 : Q - 1;
+#pragma unroll
+    for (int j = 0; j < KZ; ++j) {
+        Zd[j] = dup2(own == 0 ? Z2[0][j] : Z2[Q - 1][j]);
+        ZdEnd[j] = dup2(P == 1 ? Z2[0][K - KZ + j] : 0.0f);
+    }
+    const f32x2 hcd0 = dup2(hc[0]), hcdQ = dup2(hc[Q - 1]), hc1d = dup2(hc1), M1d = dup2(M1), M2d = dup2(M2);
+    const f32x2 m2d = dup2(-2.0f);
+
+    // ---- the fused CN steps ----
+#pragma unroll 1
+    for (int s = 0; s < sp.steps; ++s) {
+        f32x2 ln, rn;
+        if constexpr (P == 1) {
+            ln = ps[K - 1];
+            rn = ps[0];
+        } else {
+            ln = xshfl2(ps[0], P - 1);
+            rn = xshfl2(ps[K - 1], 1);
+        }
+        f32x2 zs[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const f32x2 L = (j == 0) ? ln : ps[j - 1];
+            const f32x2 R = (j == K - 1) ? rn : ps[j + 1];
+            f32x2 y;
+            if constexpr (SPLIT) {
+                y = fma2(nEd[j], ps[j], fma2(m2d, ps[j], add2(L, R)));
+            } else {
+                y = fma2(nEd[j], ps[j], add2(L, R));
+            }
+            zs[j] = (j == 0) ? y : fma2(Gd[j - 1], zs[j - 1], y);
+        }
+        f32x2 xi;
+        if constexpr (P == 1) {
+            xi = zs[K - 1];
+        } else {
+            const f32x2 q = xshfl2(zs[K - 1], 1);
+            xi = fma2(M1d, zs[K - 1], mul2(M2d, q));
+        }
+        const f32x2 xiK = xi;
+        ps[K - 1] = fma2(G2d[K - 1], xi, ps[K - 1]);
+#pragma unroll
+        for (int j = K - 2; j >= 0; --j) {
+            xi = fma2(Gd[j + 1], xi, zs[j]);
+            ps[j] = fma2(G2d[j], xi, ps[j]);
+        }
+        // alpha of the thread's own tear: every lane contributes to the
+        // sum of each tear (rows of both tears sit on different lanes)
+        f32x2 al;
+        if constexpr (P == 1) {
+            al = fma2(hcd0, xi, mul2(hc1d, xiK));
+        } else if constexpr (Q == 1) {
+            al = group_sum2<P>(mul2(hcd0, xi));
+        } else {
+            const f32x2 a0 = group_sum2<P>(mul2(hcd0, xi));
+            const f32x2 a1 = group_sum2<P>(mul2(hcdQ, xi));
+            al = (own == 0) ? a0 : a1;
+        }
+        const f32x2 nal = pk2(-lo2(al), -hi2(al));
+#pragma unroll
+        for (int j = 0; j < KZ; ++j) ps[j] = fma2(nal, Zd[j], ps[j]);
+        if constexpr (P == 1) {
+#pragma unroll
+            for (int j = 0; j < KZ; ++j) {
+                if (K - KZ + j < KZ) continue;  // rows already corrected from the other end
+                ps[K - KZ + j] = fma2(nal, ZdEnd[j], ps[K - KZ + j]);
+            }
+        }
+    }
+
+    if (active) {
+#pragma unroll
+        for (int j = 0; j < K; ++j) col[j * stride] = make_float2(lo2(ps[j]), hi2(ps[j]));
+    }
+}
+
+template <int N, int P, bool SPLIT>
+__global__ void __launch_bounds__(256) k_diffuse_x2(const __grid_constant__ DiffuseArgs a) {
+    const int lane = threadIdx.x & 31;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long slot = tid / P;
     const long long nslots = (long long)gridDim.x * blockDim.x / P;
     const long long warp_slot0 = (tid - lane) / P;
-
+    // The loop bound is uniform across the warp (warp_slot0), so every lane
+    // takes part in every shuffle; lanes past the end work on a clamped
+    // frequency and do not store.
     for (long long base = 0; warp_slot0 + base < a.HW; base += nslots) {
         const long long f = slot + base;
         const bool active = f < a.HW;
-        const long long fc = active ? f : a.HW - 1;
-        const int k = (int)(fc / a.W);
-        const int l = (int)(fc - (long long)k * a.W);
-        const float wx = sin_2pi_frac(l, a.W);
-        const float wy = sin_2pi_frac(k, a.H);
-        float2 *col = a.vol + (long long)row0 * a.HW + fc;
-        const long long stride = (long long)rstep * a.HW;
-
-        f32x2 ps[K];
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            const float2 v = col[j * stride];
-            ps[j] = pk2(v.x, v.y);
-        }
-
-        // ---- per-frequency setup (scalar, once per launch) ----
-        float E[K], dmod[K];
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            const int r = row0 + rstep * j;
-            const float ar = fmaf(wx, a.cs[r], wy * a.sn[r]);
-            if constexpr (SPLIT) {
-                E[j] = ar * ar * a.inv_beta;
-                dmod[j] = (a.inv_c + 2.0f) + E[j];
-            } else {
-                E[j] = fmaf(ar * ar, a.inv_beta, 2.0f);
-                dmod[j] = a.inv_c + E[j];
-            }
-        }
-        const float d_loc0 = dmod[0];
-        const float d_part = (P == 1) ? d_loc0 : xshfl(d_loc0, P - 1);
-        const float d_i = ti.iside ? d_loc0 : d_part;
-        if constexpr (P == 1) {
-            dmod[K - 1] = dmod[K - 1] + 1.0f / d_loc0;
-            dmod[0] = 2.0f * d_loc0;
-        } else if (ti.iside) {
-            dmod[0] = 2.0f * d_loc0;
-        } else {
-            dmod[0] = d_loc0 + 1.0f / d_part;
-        }
-        float G[K], Z2[Q][K], M1, M2, hc[Q], hc1;
-        tear_setup<K, P, float>(ti, dmod, d_i, d_loc0, Z2, hc, hc1, G, M1, M2);
-
-        f32x2 nEd[K], Gd[K], G2d[K], Zd[KZ], ZdEnd[KZ];
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            nEd[j] = dup2(-E[j]);
-            Gd[j] = dup2(G[j]);
-            G2d[j] = dup2(2.0f * G[j]);
-        }
-        const int own = (Q == 1 || ti.tear == 0) ? 0 : Q - 1;
-#pragma unroll
-        for (int j = 0; j < KZ; ++j) {
-            Zd[j] = dup2(own == 0 ? Z2[0][j] : Z2[Q - 1][j]);
-            ZdEnd[j] = dup2(P == 1 ? Z2[0][K - KZ + j] : 0.0f);
-        }
-        const f32x2 hcd0 = dup2(hc[0]), hcdQ = dup2(hc[Q - 1]), hc1d = dup2(hc1), M1d = dup2(M1), M2d = dup2(M2);
-        const f32x2 m2d = dup2(-2.0f);
-
-        // ---- the fused CN steps ----
-#pragma unroll 1
-        for (int s = 0; s < a.steps; ++s) {
-            f32x2 ln, rn;
-            if constexpr (P == 1) {
-                ln = ps[K - 1];
-                rn = ps[0];
-            } else {
-                ln = xshfl2(ps[0], P - 1);
-                rn = xshfl2(ps[K - 1], 1);
-            }
-            f32x2 zs[K];
-#pragma unroll
-            for (int j = 0; j < K; ++j) {
-                const f32x2 L = (j == 0) ? ln : ps[j - 1];
-                const f32x2 R = (j == K - 1) ? rn : ps[j + 1];
-                f32x2 y;
-                if constexpr (SPLIT) {
-                    y = fma2(nEd[j], ps[j], fma2(m2d, ps[j], add2(L, R)));
-                } else {
-                    y = fma2(nEd[j], ps[j], add2(L, R));
-                }
-                zs[j] = (j == 0) ? y : fma2(Gd[j - 1], zs[j - 1], y);
-            }
-            f32x2 xi;
-            if constexpr (P == 1) {
-                xi = zs[K - 1];
-            } else {
-                const f32x2 q = xshfl2(zs[K - 1], 1);
-                xi = fma2(M1d, zs[K - 1], mul2(M2d, q));
-            }
-            const f32x2 xiK = xi;
-            ps[K - 1] = fma2(G2d[K - 1], xi, ps[K - 1]);
-#pragma unroll
-            for (int j = K - 2; j >= 0; --j) {
-                xi = fma2(Gd[j + 1], xi, zs[j]);
-                ps[j] = fma2(G2d[j], xi, ps[j]);
-            }
-            // alpha of the thread's own tear: every lane contributes to the
-            // sum of each tear (rows of both tears sit on different lanes)
-            f32x2 al;
-            if constexpr (P == 1) {
-                al = fma2(hcd0, xi, mul2(hc1d, xiK));
-            } else if constexpr (Q == 1) {
-                al = group_sum2<P>(mul2(hcd0, xi));
-            } else {
-                const f32x2 a0 = group_sum2<P>(mul2(hcd0, xi));
-                const f32x2 a1 = group_sum2<P>(mul2(hcdQ, xi));
-                al = (own == 0) ? a0 : a1;
-            }
-            const f32x2 nal = pk2(-lo2(al), -hi2(al));
-#pragma unroll
-            for (int j = 0; j < KZ; ++j) ps[j] = fma2(nal, Zd[j], ps[j]);
-            if constexpr (P == 1) {
-#pragma unroll
-                for (int j = 0; j < KZ; ++j) {
-                    if (K - KZ + j < KZ) continue;  // rows already corrected from the other end
-                    ps[K - KZ + j] = fma2(nal, ZdEnd[j], ps[K - KZ + j]);
-                }
-            }
-        }
-
-        if (active) {
-#pragma unroll
-            for (int j = 0; j < K; ++j) col[j * stride] = make_float2(lo2(ps[j]), hi2(ps[j]));
-        }
+        diffuse_group_x2<N, P, SPLIT>(a.sp, a.cs, a.sn, a.vol, a.H, a.W, a.HW, active ? f : a.HW - 1, active);
     }
 }
 

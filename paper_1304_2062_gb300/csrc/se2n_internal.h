@@ -39,20 +39,30 @@ struct se2n_plan {
     long long kernels;  // own kernel launches
 };
 
-// Parameters of one diffusion launch (kernel parameter space: read through
-// the constant bank, so the angle tables cost no loads in the hot loop).
-struct DiffuseArgs {
-    float2 *vol;
-    long long HW;
-    int H, W;
+// Scalars of one diffusion call, shared by every frequency.
+struct StepParams {
     int steps;
     float inv_c;      // 2 / (beta dt): the left CN matrix divided by beta dt / 2
     float inv_beta;
     double inv_c_d;   // the same in FP64 (Sherman-Morrison scalars in FP64)
     double inv_beta_d;
+};
+
+// Parameters of one single-image diffusion launch (kernel parameter space:
+// read through the constant bank, so the angle tables cost no loads).
+struct DiffuseArgs {
+    float2 *vol;
+    long long HW;
+    int H, W;
+    StepParams sp;
     float cs[SE2N_MAX_N];
     float sn[SE2N_MAX_N];
 };
+
+// Host helpers shared by the single-image and batched paths (capi.cu).
+StepParams step_params(double beta, double beta_dt, int steps);
+// cos/sin of th_r = (pi or 2 pi) r / N for r < count (zero past N), as FP32.
+void angle_table(int N, int angle_conv, float *cs, float *sn, int count);
 
 // Launch the diffusion kernel for (N, P, fp64 correction) on `stream`.
 // Returns cudaErrorInvalidValue if no instantiation exists.

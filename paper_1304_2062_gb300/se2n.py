@@ -28,6 +28,7 @@ SE2N_DIFFUSE_SM_FP64 = 1
 SE2N_DIFFUSE_SPLIT_DIAG = 2
 SE2N_DIFFUSE_FULL_CORRECTION = 4
 SE2N_MAX_N = 64
+SE2N_BATCH_AUTOTUNE = 1
 
 
 class Se2nError(RuntimeError):
@@ -41,6 +42,19 @@ SE2N_STAGES = ("orient", "lift", "fft", "diffuse", "mix", "project")
 
 class se2n_profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 6), ("calls", ctypes.c_longlong * 6), ("kernels", ctypes.c_longlong)]
+
+
+class se2n_image_desc(ctypes.Structure):
+    _fields_ = [("f", ctypes.c_void_p), ("mask", ctypes.c_void_p), ("out", ctypes.c_void_p),
+                ("bins", ctypes.c_void_p), ("H", ctypes.c_int), ("W", ctypes.c_int), ("N", ctypes.c_int)]
+
+
+class se2n_batch_info(ctypes.Structure):
+    _fields_ = [("images", ctypes.c_int), ("items", ctypes.c_int), ("tile_passes", ctypes.c_int),
+                ("block", ctypes.c_int), ("blocks", ctypes.c_int), ("p16", ctypes.c_int), ("p32", ctypes.c_int),
+                ("p64", ctypes.c_int), ("fast", ctypes.c_int), ("split", ctypes.c_int),
+                ("candidates", ctypes.c_int), ("best_ms", ctypes.c_double), ("worst_ms", ctypes.c_double),
+                ("updates_per_run", ctypes.c_double), ("volume_bytes", ctypes.c_double)]
 
 
 class se2n_params(ctypes.Structure):
@@ -83,6 +97,13 @@ _SIGS = {
     "se2n_plan_tune_diffuse": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "se2n_plan_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "se2n_plan_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(se2n_profile), ctypes.c_int]),
+    "se2n_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(se2n_image_desc), ctypes.c_int,
+                                         ctypes.POINTER(se2n_params), ctypes.c_int, ctypes.c_int, _P]),
+    "se2n_batch_run": (ctypes.c_int, [_P]),
+    "se2n_batch_run_per_image": (ctypes.c_int, [_P]),
+    "se2n_batch_run_diffusion": (ctypes.c_int, [_P]),
+    "se2n_batch_get_info": (ctypes.c_int, [_P, ctypes.POINTER(se2n_batch_info)]),
+    "se2n_batch_destroy": (ctypes.c_int, [_P]),
     "se2n_plan_diffuse_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                               ctypes.POINTER(ctypes.c_int)]),
 }
@@ -256,3 +277,62 @@ def se2n_plan_profile_read(plan, reset=False):
     out = {name: (prof.ms[i], prof.calls[i]) for i, name in enumerate(SE2N_STAGES)}
     out["kernels"] = prof.kernels
     return out
+
+
+class Batch:
+    """Owns an se2n_batch*; keeps the image descriptors' buffers alive."""
+
+    def __init__(self, handle, keep):
+        self.handle = handle
+        self._keep = keep
+
+    def close(self):
+        if self.handle:
+            lib.se2n_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def se2n_batch_create(images, params, angle_conv=0, flags=0, stream=None):
+    """images: sequence of (f, mask, out, N) or (f, mask, out, N, bins) with
+    device tensors f [H][W] float32, mask [H][W] uint8, out [H][W] float32 and
+    optionally bins [H][W] uint8."""
+    descs = (se2n_image_desc * len(images))()
+    keep = []
+    for i, img in enumerate(images):
+        f, mask, out, N = img[:4]
+        bins = img[4] if len(img) > 4 else None
+        H, W = f.shape
+        descs[i] = se2n_image_desc(_ptr(f), _ptr(mask), _ptr(out), _ptr(bins), H, W, N)
+        keep.append(img)
+    h = _P()
+    _check(lib.se2n_batch_create(ctypes.byref(h), descs, len(images), ctypes.byref(params), angle_conv, flags,
+                                 _stream(stream)), "se2n_batch_create")
+    return Batch(h.value, keep)
+
+
+def se2n_batch_run(batch):
+    _check(lib.se2n_batch_run(batch.handle), "se2n_batch_run")
+
+
+def se2n_batch_run_per_image(batch):
+    _check(lib.se2n_batch_run_per_image(batch.handle), "se2n_batch_run_per_image")
+
+
+def se2n_batch_run_diffusion(batch):
+    _check(lib.se2n_batch_run_diffusion(batch.handle), "se2n_batch_run_diffusion")
+
+
+def se2n_batch_get_info(batch):
+    info = se2n_batch_info()
+    _check(lib.se2n_batch_get_info(batch.handle, ctypes.byref(info)), "se2n_batch_get_info")
+    return {name: getattr(info, name) for name, _ in se2n_batch_info._fields_}
+
+
+def se2n_batch_destroy(batch):
+    batch.close()
