@@ -299,7 +299,10 @@ typedef struct se2n_batch_info {
  * own); every other field of p applies to all images. angle_conv as in
  * se2n_plan_create. flags: SE2N_BATCH_AUTOTUNE. The image, mask and output
  * buffers must stay valid while the batch is used. Allocates about
- * 8 N H W + H W bytes per image plus the plans. Synchronizes the stream. */
+ * 8 N H W + H W bytes per image plus the plans. Synchronizes the stream.
+ * A NULL (legacy default) stream is replaced by a blocking stream the batch
+ * creates, since graphs cannot be captured on the legacy stream; it is
+ * ordered with the caller's legacy-stream work. */
 SE2N_API se2n_status se2n_batch_create(se2n_batch **out, const se2n_image_desc *imgs, int count,
                                        const se2n_params *p, int angle_conv, int flags, void *stream);
 

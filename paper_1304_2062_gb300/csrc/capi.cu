@@ -546,6 +546,7 @@ struct se2n_batch {
     cudaGraphExec_t exec = nullptr;
     int num_sms = 0;
     bool flags_autotune = false;
+    bool own_stream = false;  // created because the caller passed the legacy stream
 };
 
 namespace {
@@ -709,6 +710,7 @@ void free_batch(se2n_batch *b) {
     cudaFree(b->d_imgs);
     cudaFree(b->d_items);
     cudaFree(b->d_counter);
+    if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
 }
 
@@ -831,6 +833,16 @@ se2n_status se2n_batch_create(se2n_batch **out, const se2n_image_desc *imgs, int
     b->count = count;
     b->angle_conv = angle_conv;
     b->stream = (cudaStream_t)stream;
+    if (!b->stream) {
+        // Graphs cannot be captured on the legacy default stream. A blocking
+        // stream of our own is still ordered with the caller's legacy-stream
+        // work in both directions.
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamDefault) != cudaSuccess) {
+            delete b;
+            return SE2N_ECUDA;
+        }
+        b->own_stream = true;
+    }
     b->p = *p;
     b->flags_autotune = (flags & SE2N_BATCH_AUTOTUNE) != 0;
     se2n_status st = SE2N_OK;
