@@ -324,6 +324,46 @@ SE2N_API se2n_status se2n_batch_get_info(se2n_batch *b, se2n_batch_info *out);
 /* Release everything (after synchronizing the stream). NULL is a no-op. */
 SE2N_API se2n_status se2n_batch_destroy(se2n_batch *b);
 
+/* ---------------------------------------------------------------------------
+ * Diffusion that allocates nothing.
+ *
+ * The paper has no counterpart to this entry point. It exists for callers
+ * that cannot let a library call cudaMalloc: applications that own all
+ * device memory through their own pool or arena (a framework allocator, an
+ * embedded runtime with a fixed memory budget), and latency-critical loops
+ * that cannot afford the implicit device-wide synchronisation cudaMalloc and
+ * cudaFree may cause.
+ *
+ * It integrates eq. (deceq) exactly as se2n_diffuse does, for up to
+ * SE2N_NOALLOC_MAX_VOLUMES transformed volumes (N = 16, 32 or 64, H and W
+ * even) in one persistent launch, in place. The caller passes the volumes;
+ * the only other memory used is a fixed array of SE2N_NOALLOC_SCRATCH_BYTES
+ * bytes compiled into the library, which every GPU that loads the library
+ * holds until the process exits. No cudaMalloc, cudaFree or allocating
+ * library routine is called.
+ *
+ * All calls share that array and it keeps the last call's contents; each
+ * call resets what must start at zero. Calls that overlap on the GPU (on
+ * different streams, or from several threads without ordering) race on the
+ * array and give wrong results: order them. The first call on a device looks
+ * up the array's device address (once per device); make that first call
+ * before any stream capture. flags: SE2N_DIFFUSE_SPLIT_DIAG and
+ * SE2N_DIFFUSE_FULL_CORRECTION as for se2n_diffuse (the FP64 correction is
+ * not offered here). SE2N_EINVAL for count < 1 or count >
+ * SE2N_NOALLOC_MAX_VOLUMES, bad sizes, parameters or pointers;
+ * SE2N_EUNSUPPORTED for another N. The host copy of the call's records
+ * waits for earlier work on the stream to finish. */
+#define SE2N_NOALLOC_MAX_VOLUMES 64
+#define SE2N_NOALLOC_SCRATCH_BYTES 8192
+
+typedef struct se2n_volume_desc {
+    void *vol_hat;  /* [N][H][W] complex, 16-byte aligned device memory */
+    int H, W, N;
+} se2n_volume_desc;
+
+SE2N_API se2n_status se2n_diffuse_many_noalloc(const se2n_volume_desc *vols, int count, double beta, double T,
+                                               int steps, int angle_conv, int flags, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

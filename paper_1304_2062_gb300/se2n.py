@@ -29,6 +29,8 @@ SE2N_DIFFUSE_SPLIT_DIAG = 2
 SE2N_DIFFUSE_FULL_CORRECTION = 4
 SE2N_MAX_N = 64
 SE2N_BATCH_AUTOTUNE = 1
+SE2N_NOALLOC_MAX_VOLUMES = 64
+SE2N_NOALLOC_SCRATCH_BYTES = 8192
 
 
 class Se2nError(RuntimeError):
@@ -47,6 +49,10 @@ class se2n_profile(ctypes.Structure):
 class se2n_image_desc(ctypes.Structure):
     _fields_ = [("f", ctypes.c_void_p), ("mask", ctypes.c_void_p), ("out", ctypes.c_void_p),
                 ("bins", ctypes.c_void_p), ("H", ctypes.c_int), ("W", ctypes.c_int), ("N", ctypes.c_int)]
+
+
+class se2n_volume_desc(ctypes.Structure):
+    _fields_ = [("vol_hat", ctypes.c_void_p), ("H", ctypes.c_int), ("W", ctypes.c_int), ("N", ctypes.c_int)]
 
 
 class se2n_batch_info(ctypes.Structure):
@@ -104,6 +110,8 @@ _SIGS = {
     "se2n_batch_run_diffusion": (ctypes.c_int, [_P]),
     "se2n_batch_get_info": (ctypes.c_int, [_P, ctypes.POINTER(se2n_batch_info)]),
     "se2n_batch_destroy": (ctypes.c_int, [_P]),
+    "se2n_diffuse_many_noalloc": (ctypes.c_int, [ctypes.POINTER(se2n_volume_desc), ctypes.c_int, ctypes.c_double,
+                                                 ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
     "se2n_plan_diffuse_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                               ctypes.POINTER(ctypes.c_int)]),
 }
@@ -336,3 +344,14 @@ def se2n_batch_get_info(batch):
 
 def se2n_batch_destroy(batch):
     batch.close()
+
+
+def se2n_diffuse_many_noalloc(volumes, beta, T, steps, angle_conv=0, flags=0, stream=None):
+    """volumes: sequence of complex64 device tensors [N][H][W] (diffused in
+    place). Calls the entry point that allocates no device memory."""
+    descs = (se2n_volume_desc * max(len(volumes), 1))()
+    for i, v in enumerate(volumes):
+        N, H, W = v.shape
+        descs[i] = se2n_volume_desc(_ptr(v), H, W, N)
+    _check(lib.se2n_diffuse_many_noalloc(descs, len(volumes), beta, T, steps, angle_conv, flags, _stream(stream)),
+           "se2n_diffuse_many_noalloc")
