@@ -325,6 +325,59 @@ SE2N_API se2n_status se2n_batch_get_info(se2n_batch *b, se2n_batch_info *out);
 SE2N_API se2n_status se2n_batch_destroy(se2n_batch *b);
 
 /* ---------------------------------------------------------------------------
+ * Learned surrogate (not in the paper): a 4-level U-Net with 32-64-128-256
+ * channels, BF16 weights and activations with FP32 accumulation, trained by
+ * this library's own forward and backward kernels on (corrupted image,
+ * method output) pairs generated by se2n_inpaint / se2n_batch_run. The
+ * method stays the judge: se2n_surrogate_inpaint falls back to it for every
+ * image whose network output misses its own known pixels by more than a
+ * threshold (RMS over the known pixels).
+ *
+ * Layout: images are [count][H][W] float32 and uint8 masks on the device,
+ * H and W multiples of 8. Parameters form one flat FP32 vector: for each of
+ * the 14 3x3 conv layers (enc0a 8->32, enc0b 32->32, enc1a 32->64, enc1b,
+ * enc2a 64->128, enc2b, enc3a 128->256, enc3b, dec2a 384->128, dec2b,
+ * dec1a 192->64, dec1b, dec0a 96->32, dec0b) W[cout][9][cin] then b[cout],
+ * then the 1x1 head w[32], b[1]. All calls run on the stream given at
+ * creation.
+ * ------------------------------------------------------------------------- */
+
+typedef struct se2n_unet se2n_unet;
+
+/* Allocate a network for up to `batch` images of H x W (weights zero). */
+SE2N_API se2n_status se2n_unet_create(se2n_unet **out, int batch, int H, int W, void *stream);
+SE2N_API se2n_status se2n_unet_destroy(se2n_unet *u);
+SE2N_API se2n_status se2n_unet_param_count(const se2n_unet *u, long long *n);
+/* Deterministic He-normal initialisation from a seed (resets Adam). */
+SE2N_API se2n_status se2n_unet_init(se2n_unet *u, unsigned long long seed);
+/* Host copies of the flat FP32 parameters / gradients (synchronous). Setting
+ * the parameters also resets the Adam moments. */
+SE2N_API se2n_status se2n_unet_set_params(se2n_unet *u, const float *host);
+SE2N_API se2n_status se2n_unet_get_params(se2n_unet *u, float *host);
+SE2N_API se2n_status se2n_unet_get_grads(se2n_unet *u, float *host);
+/* out [count][H][W] = network(f, mask). */
+SE2N_API se2n_status se2n_unet_forward(se2n_unet *u, const float *f, const uint8_t *mask, int count, float *out);
+/* Forward, the loss mean((out - target)^2) (written to loss_device if not
+ * NULL) and the gradient of every parameter (kept inside for the optimizer,
+ * readable with se2n_unet_get_grads). */
+SE2N_API se2n_status se2n_unet_backward(se2n_unet *u, const float *f, const uint8_t *mask, const float *target,
+                                        int count, float *loss_device);
+/* One Adam step with the last gradients (bias-corrected). */
+SE2N_API se2n_status se2n_unet_adam(se2n_unet *u, double lr, double beta1, double beta2, double eps);
+/* se2n_unet_backward then se2n_unet_adam(lr, 0.9, 0.999, 1e-8). */
+SE2N_API se2n_status se2n_unet_train_step(se2n_unet *u, const float *f, const uint8_t *mask, const float *target,
+                                          int count, double lr, float *loss_device);
+/* Inpaint `count` images with the network; every image whose output differs
+ * from f on its known pixels by more than `threshold` (RMS) is redone by the
+ * method (se2n_inpaint with plan and p, vol_scratch [N][H][W] complex on the
+ * device, enqueued on the plan's stream). residual_host[count] (may be NULL)
+ * receives the per-image RMS, *fallbacks the number redone. The plan must be
+ * H x W. */
+SE2N_API se2n_status se2n_surrogate_inpaint(se2n_unet *u, se2n_plan *plan, const se2n_params *p, const float *f,
+                                            const uint8_t *mask, int count, double threshold, void *vol_scratch,
+                                            float *out, float *residual_host, int *fallbacks);
+
+/* ---------------------------------------------------------------------------
  * Diffusion that allocates nothing.
  *
  * The paper has no counterpart to this entry point. It exists for callers

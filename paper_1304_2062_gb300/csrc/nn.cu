@@ -1,0 +1,523 @@
+// Kernels of the learned surrogate: a 4-level U-Net (32-64-128-256
+// channels), BF16 weights and activations, FP32 accumulation, trained on
+// (corrupted image, method output) pairs that the inpainting method itself
+// generates.
+//
+// Activations are NHWC bf16 with the channel count a multiple of 8; a 3x3
+// convolution (padding 1) is the implicit GEMM of nn_gemm.cuh with
+// k = tap * C + channel, tap = (dy+1)*3 + (dx+1). Layer list and parameter
+// layout are in unet.cu.
+#include <cuda_bf16.h>
+
+#include "nn.h"
+#include "nn_gemm.cuh"
+
+using namespace se2n::nn;
+
+namespace {
+
+struct Geo {
+    int B, H, W;
+    __device__ __forceinline__ void pix(int m, int &b, int &y, int &x) const {
+        x = m % W;
+        const int t = m / W;
+        y = t % H;
+        b = t / H;
+    }
+};
+
+// A operand of a forward conv: the input activation, gathered per tap. The
+// input may be the concatenation [nearest-upsample(lo), skip] along
+// channels: channels < C1 come from `lo` at half resolution, the rest from
+// `skip` at full resolution.
+struct ConvInLoader {
+    Geo g;
+    const __nv_bfloat16 *src;   // full-resolution source (or the skip part)
+    const __nv_bfloat16 *lo;    // half-resolution upsampled part, or null
+    int C, C1, M, K;            // C = total input channels; C1 = channels from `lo`
+    int flip;                   // 1: taps mirrored (backward data)
+    __device__ __forceinline__ const void *chunk(int m, int k) const {
+        if (m >= M || k >= K) return nullptr;
+        const int tap = k / C, c = k - tap * C;
+        int dy = tap / 3 - 1, dx = tap % 3 - 1;
+        if (flip) {
+            dy = -dy;
+            dx = -dx;
+        }
+        int b, y, x;
+        g.pix(m, b, y, x);
+        const int yy = y + dy, xx = x + dx;
+        if (yy < 0 || yy >= g.H || xx < 0 || xx >= g.W) return nullptr;
+        if (lo && c < C1) {
+            const int Wl = g.W >> 1, Hl = g.H >> 1;
+            return lo + (((long long)b * Hl + (yy >> 1)) * Wl + (xx >> 1)) * C1 + c;
+        }
+        const int Cs = lo ? C - C1 : C;
+        const int cs = lo ? c - C1 : c;
+        return src + (((long long)b * g.H + yy) * g.W + xx) * Cs + cs;
+    }
+};
+
+// B operand of a forward conv: weights W[co][k], K-major.
+struct WeightKLoader {
+    const __nv_bfloat16 *w;
+    int N, K;
+    __device__ __forceinline__ const void *chunk(int n, int k) const {
+        return (n < N && k < K) ? (const void *)(w + (long long)n * K + k) : nullptr;
+    }
+};
+
+// B operand of backward data: B(k = tap*Cout + co, n = ci) = W[co][tap*Cin + ci],
+// N-major (8 consecutive ci of one (tap, co)).
+struct WeightNLoader {
+    const __nv_bfloat16 *w;
+    int Cout, Cin, K;  // K = 9 * Cout
+    __device__ __forceinline__ const void *chunk(int k, int n) const {
+        if (k >= K || n >= Cin) return nullptr;
+        const int tap = k / Cout, co = k - tap * Cout;
+        return w + (long long)co * 9 * Cin + tap * Cin + n;
+    }
+};
+
+// A operand of backward weight: dOut[pix][co], M(=co)-major.
+struct GradOutMLoader {
+    const __nv_bfloat16 *g;
+    int Cout, P;  // P = number of pixels (the GEMM's K)
+    __device__ __forceinline__ const void *chunk(int k, int m) const {
+        return (k < P && m < Cout) ? (const void *)(g + (long long)k * Cout + m) : nullptr;
+    }
+};
+
+// B operand of backward weight: B(k = pixel, n = tap*Cin + ci) = In[shift(pixel, tap)][ci].
+struct InNLoader {
+    ConvInLoader in;  // flip = 0; chunk(m = pixel, k = n) gives the gathered input
+    int P;
+    __device__ __forceinline__ const void *chunk(int k, int n) const {
+        if (k >= P) return nullptr;
+        return in.chunk(k, n);
+    }
+};
+
+template <int BM, int BN, bool AK, bool BK_, class LA, class LB>
+__device__ __forceinline__ void run_tile(const LA &la, const LB &lb, int m0, int n0, int kt0, int kt1,
+                                         float (&acc)[BM / 32][BN / 16][4]) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    gemm_mainloop<BM, BN, AK, BK_>(la, lb, m0, n0, kt0, kt1, (__nv_bfloat16 *)smem_raw, acc);
+}
+
+// Forward conv: out = relu(A W^T + bias) (relu optional), bf16 NHWC.
+template <int BM, int BN>
+__global__ void __launch_bounds__(128) k_conv_fwd(ConvInLoader la, WeightKLoader lb, const float *bias,
+                                                  __nv_bfloat16 *out, int relu) {
+    float acc[BM / 32][BN / 16][4];
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    run_tile<BM, BN, true, true>(la, lb, m0, n0, 0, (la.K + kBK - 1) / kBK, acc);
+#pragma unroll
+    for (int i = 0; i < BM / 32; ++i)
+#pragma unroll
+        for (int j = 0; j < BN / 16; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; q += 2) {
+                int m, n;
+                acc_pos<BM, BN>(i, j, q, m, n);
+                m += m0;
+                n += n0;
+                if (m < la.M && n < lb.N) {
+                    float v0 = acc[i][j][q] + bias[n], v1 = acc[i][j][q + 1] + bias[n + 1];
+                    if (relu) {
+                        v0 = fmaxf(v0, 0.0f);
+                        v1 = fmaxf(v1, 0.0f);
+                    }
+                    *(__nv_bfloat162 *)(out + (long long)m * lb.N + n) = __floats2bfloat162_rn(v0, v1);
+                }
+            }
+}
+
+// Backward data: dIn = dZ * W (flipped taps); multiplied by (act > 0) when
+// the input was a ReLU output; channels >= split go to a second buffer.
+template <int BM, int BN>
+__global__ void __launch_bounds__(128) k_conv_dgrad(ConvInLoader la, WeightNLoader lb, const __nv_bfloat16 *act,
+                                                    __nv_bfloat16 *din, __nv_bfloat16 *din2, int split) {
+    float acc[BM / 32][BN / 16][4];
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    run_tile<BM, BN, true, false>(la, lb, m0, n0, 0, (la.K + kBK - 1) / kBK, acc);
+    const int Cin = lb.Cin;
+#pragma unroll
+    for (int i = 0; i < BM / 32; ++i)
+#pragma unroll
+        for (int j = 0; j < BN / 16; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; q += 2) {
+                int m, n;
+                acc_pos<BM, BN>(i, j, q, m, n);
+                m += m0;
+                n += n0;
+                if (m >= la.M || n >= Cin) continue;
+                float v0 = acc[i][j][q], v1 = acc[i][j][q + 1];
+                if (n < split) {
+                    if (act) {
+                        const __nv_bfloat162 a = *(const __nv_bfloat162 *)(act + (long long)m * split + n);
+                        if (!(__bfloat162float(a.x) > 0.0f)) v0 = 0.0f;
+                        if (!(__bfloat162float(a.y) > 0.0f)) v1 = 0.0f;
+                    }
+                    *(__nv_bfloat162 *)(din + (long long)m * split + n) = __floats2bfloat162_rn(v0, v1);
+                } else {
+                    const int c2 = Cin - split;
+                    *(__nv_bfloat162 *)(din2 + (long long)m * c2 + (n - split)) = __floats2bfloat162_rn(v0, v1);
+                }
+            }
+}
+
+// Backward weight (split K over pixels): dW[co][tap*Cin+ci] += sum dZ * In.
+template <int BM, int BN>
+__global__ void __launch_bounds__(128) k_conv_wgrad(GradOutMLoader la, InNLoader lb, float *dw, int N, int ktiles_per) {
+    float acc[BM / 32][BN / 16][4];
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int kt_total = (lb.P + kBK - 1) / kBK;
+    const int kt0 = blockIdx.z * ktiles_per;
+    const int kt1 = min(kt_total, kt0 + ktiles_per);
+    run_tile<BM, BN, false, false>(la, lb, m0, n0, kt0, kt1, acc);
+    if (kt1 <= kt0) return;
+#pragma unroll
+    for (int i = 0; i < BM / 32; ++i)
+#pragma unroll
+        for (int j = 0; j < BN / 16; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                int m, n;
+                acc_pos<BM, BN>(i, j, q, m, n);
+                m += m0;
+                n += n0;
+                if (m < la.Cout && n < N) atomicAdd(dw + (long long)m * N + n, acc[i][j][q]);
+            }
+}
+
+// Column sums of a [P][C] bf16 matrix into db[C] (bias gradients).
+__global__ void k_colsum(const __nv_bfloat16 *g, long long P, int C, float *db) {
+    const int c = threadIdx.x;  // blockDim.x == C (<= 256)
+    float s = 0.0f;
+    for (long long p = blockIdx.x; p < P; p += gridDim.x) s += __bfloat162float(g[p * C + c]);
+    atomicAdd(db + c, s);
+}
+
+// Input packing: x[b][y][x][0] = f*(mask!=0), [1] = mask, [2..7] = 0.
+__global__ void k_pack_input(const float *f, const uint8_t *mask, __nv_bfloat16 *x, long long P) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+        const float m = mask[p] ? 1.0f : 0.0f;
+        __nv_bfloat16 v[8];
+        v[0] = __float2bfloat16_rn(f[p] * m);
+        v[1] = __float2bfloat16_rn(m);
+#pragma unroll
+        for (int c = 2; c < 8; ++c) v[c] = __float2bfloat16_rn(0.0f);
+        *(uint4 *)(x + p * 8) = *(uint4 *)v;
+    }
+}
+
+// 2x2 average pooling, NHWC.
+__global__ void k_pool(const __nv_bfloat16 *in, __nv_bfloat16 *out, int B, int H, int W, int C) {
+    const int Ho = H / 2, Wo = W / 2;
+    const long long total = (long long)B * Ho * Wo * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        long long t = i / C;
+        const int x = (int)(t % Wo);
+        t /= Wo;
+        const int y = (int)(t % Ho);
+        const int b = (int)(t / Ho);
+        const long long base = (((long long)b * H + 2 * y) * W + 2 * x) * C + c;
+        const float s = __bfloat162float(in[base]) + __bfloat162float(in[base + C]) +
+                        __bfloat162float(in[base + (long long)W * C]) + __bfloat162float(in[base + (long long)W * C + C]);
+        out[i] = __float2bfloat16_rn(0.25f * s);
+    }
+}
+
+// Gradient into an encoder output e: g_e = (pool_backward(g_pooled) + g_skip) * (e > 0).
+__global__ void k_pool_bwd_add_mask(const __nv_bfloat16 *gp, const __nv_bfloat16 *gskip, const __nv_bfloat16 *e,
+                                    __nv_bfloat16 *ge, int B, int H, int W, int C) {
+    const long long total = (long long)B * H * W * C;
+    const int Ho = H / 2, Wo = W / 2;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        long long t = i / C;
+        const int x = (int)(t % W);
+        t /= W;
+        const int y = (int)(t % H);
+        const int b = (int)(t / H);
+        float v = 0.25f * __bfloat162float(gp[(((long long)b * Ho + y / 2) * Wo + x / 2) * C + c]);
+        if (gskip) v += __bfloat162float(gskip[i]);
+        if (!(__bfloat162float(e[i]) > 0.0f)) v = 0.0f;
+        ge[i] = __float2bfloat16_rn(v);
+    }
+}
+
+// Gradient into a half-resolution tensor d that was upsampled (nearest):
+// g_d = (sum over the 2x2 block of g_up) * (d > 0).
+__global__ void k_up_bwd_mask(const __nv_bfloat16 *gup, const __nv_bfloat16 *d, __nv_bfloat16 *gd, int B, int Hl,
+                              int Wl, int C) {
+    const long long total = (long long)B * Hl * Wl * C;
+    const int H = 2 * Hl, W = 2 * Wl;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        long long t = i / C;
+        const int x = (int)(t % Wl);
+        t /= Wl;
+        const int y = (int)(t % Hl);
+        const int b = (int)(t / Hl);
+        const long long base = (((long long)b * H + 2 * y) * W + 2 * x) * C + c;
+        float v = __bfloat162float(gup[base]) + __bfloat162float(gup[base + C]) +
+                  __bfloat162float(gup[base + (long long)W * C]) + __bfloat162float(gup[base + (long long)W * C + C]);
+        if (!(__bfloat162float(d[i]) > 0.0f)) v = 0.0f;
+        gd[i] = __float2bfloat16_rn(v);
+    }
+}
+
+// Head: out[p] = sum_c w[c] d[p][c] + b (1x1 conv to one channel, FP32 out).
+__global__ void k_head(const __nv_bfloat16 *d, const float *w, const float *b, float *out, long long P, int C) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+        float s = b[0];
+        for (int c = 0; c < C; ++c) s = fmaf(w[c], __bfloat162float(d[p * C + c]), s);
+        out[p] = s;
+    }
+}
+
+// Loss L = mean over pixels of (out - target)^2 and its gradient at the
+// head, back into d: g_d[p][c] = g_out[p] w[c] (d > 0); also the head's
+// parameter gradients.
+__global__ void k_loss_head_bwd(const float *out, const float *target, const __nv_bfloat16 *d, const float *w,
+                                __nv_bfloat16 *gd, float *gw, float *gb, float *loss, long long P, int C, float inv_n) {
+    __shared__ float sgw[256];
+    __shared__ float sgb, sloss;
+    if (threadIdx.x < C) sgw[threadIdx.x] = 0.0f;
+    if (threadIdx.x == 0) {
+        sgb = 0.0f;
+        sloss = 0.0f;
+    }
+    __syncthreads();
+    float lg = 0.0f, lb = 0.0f;
+    float lw[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) lw[c] = 0.0f;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+        const float r = out[p] - target[p];
+        lg += r * r;
+        const float go = 2.0f * r * inv_n;
+        lb += go;
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+            const float dv = __bfloat162float(d[p * C + c]);
+            lw[c] = fmaf(go, dv, lw[c]);
+            gd[p * C + c] = __float2bfloat16_rn(dv > 0.0f ? go * w[c] : 0.0f);
+        }
+    }
+    atomicAdd(&sloss, lg);
+    atomicAdd(&sgb, lb);
+#pragma unroll
+    for (int c = 0; c < 32; ++c) atomicAdd(&sgw[c], lw[c]);
+    __syncthreads();
+    if (threadIdx.x < C) atomicAdd(gw + threadIdx.x, sgw[threadIdx.x]);
+    if (threadIdx.x == 0) {
+        atomicAdd(gb, sgb);
+        atomicAdd(loss, sloss * inv_n);
+    }
+}
+
+// Adam on the FP32 master parameters; refreshes the bf16 copy of the conv
+// weights (bf16 index map: for i < n_bf16_span the bf16 copy mirrors p).
+__global__ void k_adam(float *p, const float *g, float *m, float *v, __nv_bfloat16 *pb, long long n, float lr,
+                       float b1, float b2, float eps, float c1, float c2) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float upd = lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+        const float pi = p[i] - upd;
+        p[i] = pi;
+        pb[i] = __float2bfloat16_rn(pi);
+    }
+}
+
+__global__ void k_to_bf16(const float *p, __nv_bfloat16 *pb, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        pb[i] = __float2bfloat16_rn(p[i]);
+}
+
+// Per-image residual on the known pixels: r[b] = sqrt(mean over known
+// pixels of (out - f)^2) (the fallback criterion of the surrogate).
+__global__ void k_known_residual(const float *out, const float *f, const uint8_t *mask, int HW, float *r) {
+    const int b = blockIdx.x;
+    float s = 0.0f, n = 0.0f;
+    for (int i = threadIdx.x; i < HW; i += blockDim.x) {
+        const long long p = (long long)b * HW + i;
+        if (mask[p]) {
+            const float d = out[p] - f[p];
+            s += d * d;
+            n += 1.0f;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        n += __shfl_xor_sync(0xffffffffu, n, o);
+    }
+    __shared__ float ss[32], sn[32];
+    if ((threadIdx.x & 31) == 0) {
+        ss[threadIdx.x >> 5] = s;
+        sn[threadIdx.x >> 5] = n;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float ts = 0.0f, tn = 0.0f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            ts += ss[w];
+            tn += sn[w];
+        }
+        r[b] = tn > 0.0f ? sqrtf(ts / tn) : 0.0f;
+    }
+}
+
+int grid_for(long long n) {
+    long long g = (n + 255) / 256;
+    if (g > 65536) g = 65536;
+    return (int)(g < 1 ? 1 : g);
+}
+
+template <int BM, int BN>
+cudaError_t launch_fwd(const ConvInLoader &la, const WeightKLoader &lb, const float *bias, __nv_bfloat16 *out,
+                       int relu, cudaStream_t s) {
+    using S = Smem<BM, BN, true, true>;
+    auto *fn = &k_conv_fwd<BM, BN>;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, S::BYTES);
+    dim3 grid((la.M + BM - 1) / BM, (lb.N + BN - 1) / BN);
+    fn<<<grid, 128, S::BYTES, s>>>(la, lb, bias, out, relu);
+    return cudaGetLastError();
+}
+
+template <int BM, int BN>
+cudaError_t launch_dgrad(const ConvInLoader &la, const WeightNLoader &lb, const __nv_bfloat16 *act,
+                         __nv_bfloat16 *din, __nv_bfloat16 *din2, int split, cudaStream_t s) {
+    using S = Smem<BM, BN, true, false>;
+    auto *fn = &k_conv_dgrad<BM, BN>;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, S::BYTES);
+    dim3 grid((la.M + BM - 1) / BM, (lb.Cin + BN - 1) / BN);
+    fn<<<grid, 128, S::BYTES, s>>>(la, lb, act, din, din2, split);
+    return cudaGetLastError();
+}
+
+template <int BM, int BN>
+cudaError_t launch_wgrad(const GradOutMLoader &la, const InNLoader &lb, float *dw, int N, int splits, cudaStream_t s) {
+    using S = Smem<BM, BN, false, false>;
+    auto *fn = &k_conv_wgrad<BM, BN>;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, S::BYTES);
+    const int kt_total = (lb.P + kBK - 1) / kBK;
+    const int per = (kt_total + splits - 1) / splits;
+    dim3 grid((la.Cout + BM - 1) / BM, (N + BN - 1) / BN, (kt_total + per - 1) / per);
+    fn<<<grid, 128, S::BYTES, s>>>(la, lb, dw, N, per);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+namespace se2n {
+namespace nn {
+
+cudaError_t conv_forward(const __nv_bfloat16 *in, const __nv_bfloat16 *lo, int C1, int B, int H, int W, int Cin,
+                         const __nv_bfloat16 *w, const float *bias, int Cout, int relu, __nv_bfloat16 *out,
+                         cudaStream_t s) {
+    ConvInLoader la{{B, H, W}, in, lo, Cin, C1, B * H * W, 9 * Cin, 0};
+    WeightKLoader lb{w, Cout, 9 * Cin};
+    if (Cout <= 32) return launch_fwd<128, 32>(la, lb, bias, out, relu, s);
+    if (Cout <= 64) return launch_fwd<128, 64>(la, lb, bias, out, relu, s);
+    return launch_fwd<128, 128>(la, lb, bias, out, relu, s);
+}
+
+cudaError_t conv_backward_data(const __nv_bfloat16 *gz, int B, int H, int W, int Cout, const __nv_bfloat16 *w, int Cin,
+                               const __nv_bfloat16 *act, __nv_bfloat16 *din, __nv_bfloat16 *din2, int split,
+                               cudaStream_t s) {
+    ConvInLoader la{{B, H, W}, gz, nullptr, Cout, 0, B * H * W, 9 * Cout, 1};
+    WeightNLoader lb{w, Cout, Cin, 9 * Cout};
+    if (Cin <= 32) return launch_dgrad<128, 32>(la, lb, act, din, din2, split, s);
+    if (Cin <= 64) return launch_dgrad<128, 64>(la, lb, act, din, din2, split, s);
+    return launch_dgrad<128, 128>(la, lb, act, din, din2, split, s);
+}
+
+cudaError_t conv_backward_weight(const __nv_bfloat16 *gz, int B, int H, int W, int Cout, const __nv_bfloat16 *in,
+                                 const __nv_bfloat16 *lo, int C1, int Cin, float *dw, cudaStream_t s) {
+    const int P = B * H * W;
+    GradOutMLoader la{gz, Cout, P};
+    InNLoader lb{{{B, H, W}, in, lo, Cin, C1, P, 9 * Cin, 0}, P};
+    const int N = 9 * Cin;
+    const int kt_total = (P + kBK - 1) / kBK;
+    // enough CTAs to fill the GPU, each reducing a slab of pixels
+    const int tiles = ((Cout + 63) / 64) * ((N + 63) / 64);
+    int splits = (4 * 152 + tiles - 1) / tiles;
+    if (splits > kt_total) splits = kt_total;
+    if (splits < 1) splits = 1;
+    if (Cout <= 32) return launch_wgrad<32, 64>(la, lb, dw, N, splits, s);
+    if (Cout <= 64) return launch_wgrad<64, 64>(la, lb, dw, N, splits, s);
+    return launch_wgrad<128, 64>(la, lb, dw, N, splits, s);
+}
+
+cudaError_t colsum(const __nv_bfloat16 *g, long long P, int C, float *db, cudaStream_t s) {
+    k_colsum<<<1024, C, 0, s>>>(g, P, C, db);
+    return cudaGetLastError();
+}
+
+cudaError_t pack_input(const float *f, const uint8_t *mask, __nv_bfloat16 *x, long long P, cudaStream_t s) {
+    k_pack_input<<<grid_for(P), 256, 0, s>>>(f, mask, x, P);
+    return cudaGetLastError();
+}
+
+cudaError_t pool(const __nv_bfloat16 *in, __nv_bfloat16 *out, int B, int H, int W, int C, cudaStream_t s) {
+    k_pool<<<grid_for((long long)B * H * W * C / 4), 256, 0, s>>>(in, out, B, H, W, C);
+    return cudaGetLastError();
+}
+
+cudaError_t pool_backward_add_mask(const __nv_bfloat16 *gp, const __nv_bfloat16 *gskip, const __nv_bfloat16 *e,
+                                   __nv_bfloat16 *ge, int B, int H, int W, int C, cudaStream_t s) {
+    k_pool_bwd_add_mask<<<grid_for((long long)B * H * W * C), 256, 0, s>>>(gp, gskip, e, ge, B, H, W, C);
+    return cudaGetLastError();
+}
+
+cudaError_t up_backward_mask(const __nv_bfloat16 *gup, const __nv_bfloat16 *d, __nv_bfloat16 *gd, int B, int Hl,
+                             int Wl, int C, cudaStream_t s) {
+    k_up_bwd_mask<<<grid_for((long long)B * Hl * Wl * C), 256, 0, s>>>(gup, d, gd, B, Hl, Wl, C);
+    return cudaGetLastError();
+}
+
+cudaError_t head(const __nv_bfloat16 *d, const float *w, const float *b, float *out, long long P, int C,
+                 cudaStream_t s) {
+    k_head<<<grid_for(P), 256, 0, s>>>(d, w, b, out, P, C);
+    return cudaGetLastError();
+}
+
+cudaError_t loss_head_backward(const float *out, const float *target, const __nv_bfloat16 *d, const float *w,
+                               __nv_bfloat16 *gd, float *gw, float *gb, float *loss, long long P, int C,
+                               cudaStream_t s) {
+    int g = grid_for(P);
+    if (g > 2048) g = 2048;
+    k_loss_head_bwd<<<g, 256, 0, s>>>(out, target, d, w, gd, gw, gb, loss, P, C, 1.0f / (float)P);
+    return cudaGetLastError();
+}
+
+cudaError_t adam(float *p, const float *g, float *m, float *v, __nv_bfloat16 *pb, long long n, float lr, float b1,
+                 float b2, float eps, int t, cudaStream_t s) {
+    const float c1 = 1.0f / (1.0f - powf(b1, (float)t));
+    const float c2 = 1.0f / (1.0f - powf(b2, (float)t));
+    k_adam<<<grid_for(n), 256, 0, s>>>(p, g, m, v, pb, n, lr, b1, b2, eps, c1, c2);
+    return cudaGetLastError();
+}
+
+cudaError_t to_bf16(const float *p, __nv_bfloat16 *pb, long long n, cudaStream_t s) {
+    k_to_bf16<<<grid_for(n), 256, 0, s>>>(p, pb, n);
+    return cudaGetLastError();
+}
+
+cudaError_t known_residual(const float *out, const float *f, const uint8_t *mask, int B, int HW, float *r,
+                           cudaStream_t s) {
+    k_known_residual<<<B, 256, 0, s>>>(out, f, mask, HW, r);
+    return cudaGetLastError();
+}
+
+}  // namespace nn
+}  // namespace se2n

@@ -1,0 +1,45 @@
+// Kernels of the surrogate network (nn.cu).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace se2n {
+namespace nn {
+
+// 3x3 convolution, padding 1, NHWC bf16. The input is `in` (Cin channels),
+// or, when lo != null, the channel concatenation [nearest-upsample(lo) (C1
+// channels, half resolution), in (Cin - C1 channels)]. out = relu?(conv + bias).
+cudaError_t conv_forward(const __nv_bfloat16 *in, const __nv_bfloat16 *lo, int C1, int B, int H, int W, int Cin,
+                         const __nv_bfloat16 *w, const float *bias, int Cout, int relu, __nv_bfloat16 *out,
+                         cudaStream_t s);
+// Gradient w.r.t. the input from the pre-activation gradient gz [P][Cout];
+// channels < split go to din (multiplied by act > 0 when act != null),
+// channels >= split to din2.
+cudaError_t conv_backward_data(const __nv_bfloat16 *gz, int B, int H, int W, int Cout, const __nv_bfloat16 *w, int Cin,
+                               const __nv_bfloat16 *act, __nv_bfloat16 *din, __nv_bfloat16 *din2, int split,
+                               cudaStream_t s);
+// dw[Cout][9*Cin] += weight gradient (FP32, atomically accumulated).
+cudaError_t conv_backward_weight(const __nv_bfloat16 *gz, int B, int H, int W, int Cout, const __nv_bfloat16 *in,
+                                 const __nv_bfloat16 *lo, int C1, int Cin, float *dw, cudaStream_t s);
+cudaError_t colsum(const __nv_bfloat16 *g, long long P, int C, float *db, cudaStream_t s);
+cudaError_t pack_input(const float *f, const uint8_t *mask, __nv_bfloat16 *x, long long P, cudaStream_t s);
+cudaError_t pool(const __nv_bfloat16 *in, __nv_bfloat16 *out, int B, int H, int W, int C, cudaStream_t s);
+cudaError_t pool_backward_add_mask(const __nv_bfloat16 *gp, const __nv_bfloat16 *gskip, const __nv_bfloat16 *e,
+                                   __nv_bfloat16 *ge, int B, int H, int W, int C, cudaStream_t s);
+cudaError_t up_backward_mask(const __nv_bfloat16 *gup, const __nv_bfloat16 *d, __nv_bfloat16 *gd, int B, int Hl,
+                             int Wl, int C, cudaStream_t s);
+cudaError_t head(const __nv_bfloat16 *d, const float *w, const float *b, float *out, long long P, int C,
+                 cudaStream_t s);
+cudaError_t loss_head_backward(const float *out, const float *target, const __nv_bfloat16 *d, const float *w,
+                               __nv_bfloat16 *gd, float *gw, float *gb, float *loss, long long P, int C,
+                               cudaStream_t s);
+cudaError_t adam(float *p, const float *g, float *m, float *v, __nv_bfloat16 *pb, long long n, float lr, float b1,
+                 float b2, float eps, int t, cudaStream_t s);
+cudaError_t to_bf16(const float *p, __nv_bfloat16 *pb, long long n, cudaStream_t s);
+cudaError_t known_residual(const float *out, const float *f, const uint8_t *mask, int B, int HW, float *r,
+                           cudaStream_t s);
+
+}  // namespace nn
+}  // namespace se2n

@@ -112,6 +112,19 @@ _SIGS = {
     "se2n_batch_destroy": (ctypes.c_int, [_P]),
     "se2n_diffuse_many_noalloc": (ctypes.c_int, [ctypes.POINTER(se2n_volume_desc), ctypes.c_int, ctypes.c_double,
                                                  ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
+    "se2n_unet_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
+    "se2n_unet_destroy": (ctypes.c_int, [_P]),
+    "se2n_unet_param_count": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_longlong)]),
+    "se2n_unet_init": (ctypes.c_int, [_P, ctypes.c_ulonglong]),
+    "se2n_unet_set_params": (ctypes.c_int, [_P, _P]),
+    "se2n_unet_get_params": (ctypes.c_int, [_P, _P]),
+    "se2n_unet_get_grads": (ctypes.c_int, [_P, _P]),
+    "se2n_unet_forward": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
+    "se2n_unet_backward": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, _P]),
+    "se2n_unet_adam": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
+    "se2n_unet_train_step": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_double, _P]),
+    "se2n_surrogate_inpaint": (ctypes.c_int, [_P, _P, ctypes.POINTER(se2n_params), _P, _P, ctypes.c_int,
+                                              ctypes.c_double, _P, _P, _P, ctypes.POINTER(ctypes.c_int)]),
     "se2n_plan_diffuse_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                               ctypes.POINTER(ctypes.c_int)]),
 }
@@ -355,3 +368,80 @@ def se2n_diffuse_many_noalloc(volumes, beta, T, steps, angle_conv=0, flags=0, st
         descs[i] = se2n_volume_desc(_ptr(v), H, W, N)
     _check(lib.se2n_diffuse_many_noalloc(descs, len(volumes), beta, T, steps, angle_conv, flags, _stream(stream)),
            "se2n_diffuse_many_noalloc")
+
+
+class Unet:
+    """Owns an se2n_unet*."""
+
+    def __init__(self, handle, batch, H, W):
+        self.handle = handle
+        self.batch, self.H, self.W = batch, H, W
+
+    def close(self):
+        if self.handle:
+            lib.se2n_unet_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def se2n_unet_create(batch, H, W, stream=None):
+    h = _P()
+    _check(lib.se2n_unet_create(ctypes.byref(h), batch, H, W, _stream(stream)), "se2n_unet_create")
+    return Unet(h.value, batch, H, W)
+
+
+def se2n_unet_destroy(u):
+    u.close()
+
+
+def se2n_unet_param_count(u):
+    n = ctypes.c_longlong()
+    _check(lib.se2n_unet_param_count(u.handle, ctypes.byref(n)), "se2n_unet_param_count")
+    return n.value
+
+
+def se2n_unet_init(u, seed):
+    _check(lib.se2n_unet_init(u.handle, seed), "se2n_unet_init")
+
+
+def se2n_unet_set_params(u, host):
+    _check(lib.se2n_unet_set_params(u.handle, _ptr(host)), "se2n_unet_set_params")
+
+
+def se2n_unet_get_params(u, host):
+    _check(lib.se2n_unet_get_params(u.handle, _ptr(host)), "se2n_unet_get_params")
+
+
+def se2n_unet_get_grads(u, host):
+    _check(lib.se2n_unet_get_grads(u.handle, _ptr(host)), "se2n_unet_get_grads")
+
+
+def se2n_unet_forward(u, f, mask, count, out):
+    _check(lib.se2n_unet_forward(u.handle, _ptr(f), _ptr(mask), count, _ptr(out)), "se2n_unet_forward")
+
+
+def se2n_unet_backward(u, f, mask, target, count, loss=None):
+    _check(lib.se2n_unet_backward(u.handle, _ptr(f), _ptr(mask), _ptr(target), count, _ptr(loss)),
+           "se2n_unet_backward")
+
+
+def se2n_unet_adam(u, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    _check(lib.se2n_unet_adam(u.handle, lr, beta1, beta2, eps), "se2n_unet_adam")
+
+
+def se2n_unet_train_step(u, f, mask, target, count, lr, loss=None):
+    _check(lib.se2n_unet_train_step(u.handle, _ptr(f), _ptr(mask), _ptr(target), count, lr, _ptr(loss)),
+           "se2n_unet_train_step")
+
+
+def se2n_surrogate_inpaint(u, plan, params, f, mask, count, threshold, vol_scratch, out, residual_host=None):
+    nf = ctypes.c_int()
+    _check(lib.se2n_surrogate_inpaint(u.handle, plan.handle, ctypes.byref(params), _ptr(f), _ptr(mask), count,
+                                      threshold, _ptr(vol_scratch), _ptr(out), _ptr(residual_host), ctypes.byref(nf)),
+           "se2n_surrogate_inpaint")
+    return nf.value

@@ -1,0 +1,174 @@
+"""The surrogate network's own GPU kernels (forward, backward, Adam) against
+the FP64 reference in oracle/unet.py, its training on pairs the method
+generates, and the method fallback.
+
+Both sides get the same values: the reference uses the bfloat16-rounded
+conv weights and input the GPU computes with. The GPU also rounds every
+activation and activation gradient to bfloat16 (relative step 2^-8), which
+bounds the agreement: about 15 layers forward and back accumulate a few
+times 2^-9 in quadrature. The tolerances below (2e-2 on the output, 5e-2
+per parameter tensor on the gradients) leave a factor of two or more over
+the measured errors printed by the tests.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import unet as ou
+from _gpu import host, t_f32, t_u8
+
+pytestmark = pytest.mark.gpu
+
+se2n = pytest.importorskip("paper_1304_2062_gb300.se2n")
+
+import torch  # noqa: E402
+
+OUT_TOL = 2e-2
+GRAD_TOL = 5e-2
+
+
+def _gpu_view(p32):
+    """The parameters as the GPU computes with them: bf16 conv weights,
+    FP32 biases and head."""
+    q = p32.astype(np.float64).copy()
+    offs, hw, hb, n = ou.layout()
+    for (w, b), (cin, cout, _) in zip(offs, ou.LAYERS):
+        q[w:w + cout * 9 * cin] = ou.bf16_round(q[w:w + cout * 9 * cin])
+    return q
+
+
+def _inputs(B, H, W, seed):
+    rng = np.random.default_rng(seed)
+    f = rng.uniform(0.05, 1.0, (B, H, W)).astype(np.float32)
+    mask = (rng.random((B, H, W)) > 0.5).astype(np.uint8)
+    target = rng.uniform(0.0, 1.0, (B, H, W)).astype(np.float32)
+    return f, mask, target
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-30))
+
+
+@pytest.mark.parametrize("B,H,W", [(2, 16, 16), (1, 24, 40)])
+def test_forward_and_gradients_match_oracle(B, H, W):
+    p32 = ou.he_params(11).astype(np.float32)
+    f, mask, target = _inputs(B, H, W, 5)
+    u = se2n.se2n_unet_create(B, H, W)
+    se2n.se2n_unet_set_params(u, p32)
+    out = torch.zeros((B, H, W), dtype=torch.float32, device="cuda")
+    fd, md, td = t_f32(f), t_u8(mask), t_f32(target)
+    se2n.se2n_unet_forward(u, fd, md, B, out)
+    got = host(out)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    se2n.se2n_unet_backward(u, fd, md, td, B, loss)
+    g = np.zeros(se2n.se2n_unet_param_count(u), np.float32)
+    se2n.se2n_unet_get_grads(u, g)
+    u.close()
+
+    q = _gpu_view(p32)
+    f_in = ou.bf16_round(f * (mask != 0))
+    ref, _ = ou.forward(q, f_in, mask)
+    ref_loss, ref_g = ou.loss_and_grads(q, f_in, mask, target)
+    e_out = _rel(got, ref)
+    print(f"forward rel-L2 {e_out:.2e}; loss {host(loss)[0]:.6f} vs {ref_loss:.6f}")
+    assert e_out <= OUT_TOL
+    assert abs(host(loss)[0] - ref_loss) <= OUT_TOL * ref_loss
+    offs, hw, hb, n = ou.layout()
+    worst = 0.0
+    for i, ((w, b), (cin, cout, _)) in enumerate(zip(offs, ou.LAYERS)):
+        cw = 2 if cin == 8 else cin  # input channels 2..7 are always zero
+        gw = g[w:w + cout * 9 * cin].reshape(cout, 9, cin)[:, :, :cw]
+        rw = ref_g[w:w + cout * 9 * cin].reshape(cout, 9, cin)[:, :, :cw]
+        ew, eb = _rel(gw, rw), _rel(g[b:b + cout], ref_g[b:b + cout])
+        worst = max(worst, ew, eb)
+        print(f"layer {i:2d}: dW rel-L2 {ew:.2e}, db rel-L2 {eb:.2e}")
+        assert ew <= GRAD_TOL and eb <= GRAD_TOL
+    eh = _rel(g[hw:hb + 1], ref_g[hw:hb + 1])
+    print(f"head: rel-L2 {eh:.2e}; worst layer {worst:.2e}")
+    assert eh <= GRAD_TOL
+
+
+def _method_pairs(n, H, W, seed, N=32):
+    """(corrupted image, mask, method output) from the GPU method."""
+    fs, ms, outs = [], [], []
+    plan = se2n.se2n_plan_create(H, W, N)
+    prm = se2n.se2n_params_default(N=N, beta=0.5, T=1.0, steps=100, rounds=1)
+    vol = torch.empty((N, H, W), dtype=torch.complex64, device="cuda")
+    for i in range(n):
+        clean = synth.lines_circles_image(H, W, seed + i)
+        mask = synth.bernoulli_mask(H, W, seed + 10000 + i, 0.5)
+        f = (clean * mask).astype(np.float32)
+        out = torch.empty((H, W), dtype=torch.float32, device="cuda")
+        se2n.se2n_inpaint(plan, t_f32(f), t_u8(mask), None, prm, vol, out)
+        fs.append(f)
+        ms.append(mask)
+        outs.append(host(out).copy())
+    plan.close()
+    return np.stack(fs), np.stack(ms), np.stack(outs)
+
+
+def test_training_on_method_pairs_reduces_the_loss():
+    H = W = 32
+    f, m, t = _method_pairs(32, H, W, 500)
+    u = se2n.se2n_unet_create(16, H, W)
+    se2n.se2n_unet_init(u, 7)
+    fd, md, td = t_f32(f), t_u8(m), t_f32(t)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    losses = []
+    for step in range(300):
+        i = (step % 2) * 16
+        se2n.se2n_unet_train_step(u, fd[i:i + 16], md[i:i + 16], td[i:i + 16], 16, 2e-3, loss)
+        losses.append(float(host(loss)[0]))
+    out = torch.zeros((16, H, W), dtype=torch.float32, device="cuda")
+    se2n.se2n_unet_forward(u, fd[:16], md[:16], 16, out)
+    pred = host(out)
+    u.close()
+    first, last = np.mean(losses[:10]), np.mean(losses[-10:])
+    psnr = lambda a, b: 10 * np.log10(1.0 / np.mean((a - b) ** 2))
+    p_net, p_zero = psnr(pred, t[:16]), psnr(f[:16], t[:16])
+    print(f"loss {first:.4f} -> {last:.5f}; PSNR vs method: network {p_net:.2f} dB, zero-filled input {p_zero:.2f} dB")
+    assert last < first / 5
+    assert p_net > p_zero + 3.0
+
+
+def test_fallback_to_the_method():
+    H = W = 32
+    f, m, t = _method_pairs(4, H, W, 900)
+    u = se2n.se2n_unet_create(4, H, W)
+    se2n.se2n_unet_init(u, 1)
+    plan = se2n.se2n_plan_create(H, W, 32)
+    prm = se2n.se2n_params_default(N=32, beta=0.5, T=1.0, steps=100, rounds=1)
+    vol = torch.empty((32, H, W), dtype=torch.complex64, device="cuda")
+    fd, md = t_f32(f), t_u8(m)
+    out = torch.zeros((4, H, W), dtype=torch.float32, device="cuda")
+    r = np.zeros(4, np.float32)
+    # an untrained network misses the known pixels: every image is redone by the method
+    nf = se2n.se2n_surrogate_inpaint(u, plan, prm, fd, md, 4, 2e-2, vol, out, r)
+    torch.cuda.synchronize()
+    assert nf == 4 and (r > 2e-2).all()
+    np.testing.assert_array_equal(host(out), t)
+    # with no threshold, the network output is returned as it is
+    nf = se2n.se2n_surrogate_inpaint(u, plan, prm, fd, md, 4, 1e30, vol, out, r)
+    ref = torch.zeros_like(out)
+    se2n.se2n_unet_forward(u, fd, md, 4, ref)
+    assert nf == 0
+    np.testing.assert_array_equal(host(out), host(ref))
+    plan.close()
+    u.close()
+
+
+def test_network_rejects_bad_arguments():
+    with pytest.raises(se2n.Se2nError) as e:
+        se2n.se2n_unet_create(2, 12, 16)   # not a multiple of 8
+    assert e.value.status == se2n.SE2N_EINVAL
+    u = se2n.se2n_unet_create(2, 16, 16)
+    f = t_f32(np.zeros((2, 16, 16)))
+    m = t_u8(np.zeros((2, 16, 16)))
+    out = torch.zeros((2, 16, 16), dtype=torch.float32, device="cuda")
+    with pytest.raises(se2n.Se2nError):
+        se2n.se2n_unet_forward(u, f, m, 3, out)   # more images than the batch
+    with pytest.raises(se2n.Se2nError):
+        se2n.se2n_unet_forward(u, np.zeros((2, 16, 16), np.float32), m, 2, out)  # host buffer
+    with pytest.raises(se2n.Se2nError):
+        se2n.se2n_unet_adam(u, -1.0)
+    u.close()
