@@ -381,9 +381,360 @@ def run_batch(args, rank, world, local_rank):
             "gpu_launches": len(mine) * 6 + w0.rounds * 1}
 
 
+# ----------------------------------------------------------------------------
+# learned surrogate
+# ----------------------------------------------------------------------------
+
+SURR_METRIC = "surrogate inpaints/s (256x256, batch 64, method fallback at known-pixel RMS > 2e-2)"
+SURR_UNIT = "images/s"
+SURR_BATCH = 64
+SURR_THRESHOLD = 2e-2
+SURR_LAUNCHES_PER_CALL = 20
+# (input channels used, output channels, level) of the 14 3x3 convolutions;
+# the first layer reads 2 real channels (f, mask) of its 8-channel input
+SURR_CONVS = [(2, 32, 0), (32, 32, 0), (32, 64, 1), (64, 64, 1), (64, 128, 2), (128, 128, 2), (128, 256, 3),
+              (256, 256, 3), (384, 128, 2), (128, 128, 2), (192, 64, 1), (64, 64, 1), (96, 32, 0), (32, 32, 0)]
+
+
+def surrogate_flops(H, W):
+    """Algorithmic conv flops of one forward pass of one H x W image
+    (2 x 9 x Cin x Cout per output pixel, plus the 1x1 head)."""
+    fl = sum(2 * 9 * cin * cout * (H >> lvl) * (W >> lvl) for cin, cout, lvl in SURR_CONVS)
+    return fl + 2 * 32 * H * W
+
+
+def surrogate_train_flops(H, W):
+    """Forward + data gradient (not for the first layer) + weight gradient."""
+    first = 2 * 9 * 2 * 32 * H * W
+    f = surrogate_flops(H, W)
+    return 3 * f - first
+
+
+def _surrogate_chunk(job):
+    first, count = job
+    return first, synth.surrogate_examples(first, count)
+
+
+def _psnr(a, b):
+    return float(10 * np.log10(1.0 / max(np.mean((np.asarray(a, np.float64) - b) ** 2), 1e-30)))
+
+
+def run_surrogate(args, rank, world, local_rank):
+    """The learned surrogate end to end: 20000 seeded 256x256 pairs
+    (corrupted image, method-inpainted image) made by the GPU method, the
+    network trained on them by the library's own kernels, then timed
+    inference of batches of 64 with the method as fallback, against the
+    method on the same images. Reports PSNR against the clean images and
+    against the method's output on 512 held-out images."""
+    import multiprocessing as mp
+
+    pool = mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1))
+    import torch
+
+    from paper_1304_2062_gb300 import se2n
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    H = W = synth.SURROGATE_SIDE
+    mp_ = synth.surrogate_method_params()
+    N = mp_["N"]
+    stream = torch.cuda.Stream(dev)
+    plan = se2n.se2n_plan_create(H, W, N, 0, stream)
+    prm = se2n.se2n_params_default(reinject=1, **mp_)
+    vol = torch.empty((N, H, W), dtype=torch.complex64, device=dev)
+
+    def make_set(first, count):
+        F = torch.empty((count, H, W), dtype=torch.float32, device=dev)
+        M = torch.empty((count, H, W), dtype=torch.uint8, device=dev)
+        T = torch.empty((count, H, W), dtype=torch.float32, device=dev)
+        C = []
+        per = max(64, count // (4 * (os.cpu_count() or 1)))
+        jobs = [(s, min(per, first + count - s)) for s in range(first, first + count, per)]
+        gpu_ms = 0.0
+        for s, (clean, mask) in pool.imap(_surrogate_chunk, jobs):
+            i0, n = s - first, clean.shape[0]
+            with torch.cuda.stream(stream):
+                F[i0:i0 + n].copy_(torch.from_numpy(clean * mask))
+                M[i0:i0 + n].copy_(torch.from_numpy(mask))
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                for j in range(i0, i0 + n):
+                    se2n.se2n_inpaint(plan, F[j], M[j], None, prm, vol, T[j])
+                b.record(stream)
+            b.synchronize()
+            gpu_ms += a.elapsed_time(b)
+            C.append(clean)
+        return F, M, T, np.concatenate(C), gpu_ms
+
+    t0 = time.perf_counter()
+    first, count = synth.SURROGATE_TRAIN_SEEDS
+    count = args.train_pairs or count
+    Ftr, Mtr, Ttr, _, gen_ms = make_set(first, count)
+    gen_s = time.perf_counter() - t0
+    vfirst, vcount = synth.SURROGATE_VAL_SEEDS
+    Fv, Mv, Tv, Cv, _ = make_set(vfirst, vcount)
+    pool.close()
+
+    # training: Adam, cosine-decayed learning rate, blocks of 32 consecutive
+    # (independently seeded) examples in a fresh random order every epoch
+    u = se2n.se2n_unet_create(SURR_BATCH, H, W, stream)
+    se2n.se2n_unet_init(u, 7)
+    tb = 32
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    rng = np.random.default_rng(0)
+    starts = []
+
+    def next_start():
+        if not starts:
+            starts.extend(rng.permutation(np.arange(0, count - tb + 1, tb)).tolist())
+        return starts.pop()
+
+    lr0, lr_min, warm = 1e-3, 1e-5, 200
+
+    def train(nsteps, total, done):
+        for k in range(nsteps):
+            s = next_start()
+            i = done + k
+            x = i / max(total, 1)
+            lr = lr_min + 0.5 * (lr0 - lr_min) * (1 + np.cos(np.pi * min(x, 1.0)))
+            lr *= min(1.0, (i + 1) / warm)
+            se2n.se2n_unet_train_step(u, Ftr[s], Mtr[s], Ttr[s], tb, float(lr), loss)
+
+    with torch.cuda.stream(stream):
+        # time 30 steps of the warm-up ramp to size the run to the time budget
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        train(10, 10 ** 9, 0)
+        a.record(stream)
+        train(20, 10 ** 9, 10)
+        b.record(stream)
+        b.synchronize()
+        ms_step = a.elapsed_time(b) / 20
+        total = max(300, int(args.train_seconds * 1e3 / ms_step))
+        t1 = time.perf_counter()
+        losses = []
+        done = 30
+        while done < total:
+            n = min(500, total - done)
+            train(n, total, done)
+            done += n
+            losses.append(float(loss.item()))
+        torch.cuda.synchronize(dev)
+        train_s = time.perf_counter() - t1
+
+    # validation: network alone, network with fallback, method
+    net = torch.empty_like(Tv)
+    sur = torch.empty_like(Tv)
+    resid = np.zeros(vcount, np.float32)
+    fallbacks = 0
+    with torch.cuda.stream(stream):
+        for s in range(0, vcount, SURR_BATCH):
+            n = min(SURR_BATCH, vcount - s)
+            se2n.se2n_unet_forward(u, Fv[s:s + n], Mv[s:s + n], n, net[s:s + n])
+            r = np.zeros(n, np.float32)
+            fallbacks += se2n.se2n_surrogate_inpaint(u, plan, prm, Fv[s:s + n], Mv[s:s + n], n, SURR_THRESHOLD, vol,
+                                                     sur[s:s + n], r)
+            resid[s:s + n] = r
+        torch.cuda.synchronize(dev)
+    net_h, sur_h, meth_h = net.cpu().numpy(), sur.cpu().numpy(), Tv.cpu().numpy()
+    f_h = Fv.cpu().numpy()
+    quality = {
+        "validation_images": vcount,
+        "psnr_vs_clean_db": {"surrogate_with_fallback": _psnr(sur_h, Cv), "network_alone": _psnr(net_h, Cv),
+                             "method": _psnr(meth_h, Cv), "zero_filled_input": _psnr(f_h, Cv)},
+        "psnr_vs_method_db": {"surrogate_with_fallback": _psnr(sur_h, meth_h), "network_alone": _psnr(net_h, meth_h),
+                              "zero_filled_input": _psnr(f_h, meth_h)},
+        "fallbacks": int(fallbacks), "threshold": SURR_THRESHOLD,
+        "known_pixel_rms": {"median": float(np.median(resid)), "max": float(resid.max())},
+    }
+
+    # timed: surrogate inference of batches of 64 (held-out images), fallback included
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    nb = vcount // SURR_BATCH
+
+    def batch(i):
+        s = (i % nb) * SURR_BATCH
+        return s, s + SURR_BATCH
+
+    def timed(fn, k):
+        with torch.cuda.stream(stream):
+            for i in range(args.warmup):
+                fn(i)
+            torch.cuda.synchronize(dev)
+            if dist:
+                dist.barrier()
+            evs = []
+            for i in range(k):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn(i)
+                b.record(stream)
+                evs.append((a, b))
+            torch.cuda.synchronize(dev)
+        return max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), dist, dev) / k
+
+    nf = []
+
+    def surrogate_step(i):
+        s, e = batch(i)
+        nf.append(se2n.se2n_surrogate_inpaint(u, plan, prm, Fv[s:e], Mv[s:e], SURR_BATCH, SURR_THRESHOLD, vol,
+                                             sur[s:e], None))
+
+    def forward_step(i):
+        s, e = batch(i)
+        se2n.se2n_unet_forward(u, Fv[s:e], Mv[s:e], SURR_BATCH, net[s:e])
+
+    def method_step(i):
+        s, e = batch(i)
+        for j in range(s, e):
+            se2n.se2n_inpaint(plan, Fv[j], Mv[j], None, prm, vol, Tv[j])
+
+    se2n.se2n_plan_profile(plan, True)
+    with ClockSampler(local_rank) as clocks:
+        ms = timed(surrogate_step, args.steps)
+    method_kernels = int(se2n.se2n_plan_profile_read(plan, reset=True)["kernels"])
+    se2n.se2n_plan_profile(plan, False)
+    nf_timed = int(sum(nf[-args.steps:]))
+    kernels_per_fallback = method_kernels / max(1, sum(nf))
+    ms_fwd = timed(forward_step, max(3, min(args.steps, 10)))
+    ms_method = timed(method_step, max(3, min(args.steps, 5)))
+    fl = surrogate_flops(H, W) * SURR_BATCH
+    peaks = _peaks()
+    peak = peaks.get("bf16_tflops", 1900.0)
+    achieved = fl / (ms_fwd / 1e3) / 1e12
+    train_tflops = surrogate_train_flops(H, W) * tb / (ms_step / 1e3) / 1e12
+
+    # end to end: pinned host inputs in, result out, every step
+    fh = torch.from_numpy(f_h[:SURR_BATCH].copy()).pin_memory()
+    mh = torch.from_numpy(Mv[:SURR_BATCH].cpu().numpy()).pin_memory()
+    oh = torch.empty((SURR_BATCH, H, W), dtype=torch.float32).pin_memory()
+    Fd, Md, Od = torch.empty_like(Fv[:SURR_BATCH]), torch.empty_like(Mv[:SURR_BATCH]), torch.empty_like(Tv[:SURR_BATCH])
+
+    def e2e_step(i):
+        Fd.copy_(fh, non_blocking=True)
+        Md.copy_(mh, non_blocking=True)
+        se2n.se2n_surrogate_inpaint(u, plan, prm, Fd, Md, SURR_BATCH, SURR_THRESHOLD, vol, Od, None)
+        oh.copy_(Od, non_blocking=True)
+
+    ms_e2e = timed(e2e_step, max(3, min(args.steps, 10)))
+    u.close()
+    plan.close()
+    if dist:
+        dist.destroy_process_group()
+    res = {"metric": SURR_METRIC, "value": world * SURR_BATCH / (ms / 1e3), "unit": SURR_UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (FP32 accumulate)", "data": "synthetic",
+           "config": {"workload": f"surrogate_lines_circles_256: {count} training pairs (seeds {first}..), "
+                                  f"{vcount} held-out (seeds {vfirst}..), 50% random masks, targets from the GPU "
+                                  f"method (N={N}, beta={mp_['beta']}, T={mp_['T']}, {mp_['steps']} steps, "
+                                  "known pixels re-injected); 4-level U-Net 32-64-128-256",
+                      "batch": SURR_BATCH, "l2": "flushed between timed steps (256 MiB write)",
+                      "parallelism": "replicas"},
+           "method_same_images": {"ms_per_step": ms_method, "value": world * SURR_BATCH / (ms_method / 1e3),
+                                  "api": "se2n_inpaint per image", "speedup_of_surrogate": ms_method / ms},
+           "quality": quality,
+           "roofline": {"bound": "tensor", "achieved": round(achieved, 3), "peak": peak, "unit": "TFLOP/s",
+                        "frac": round(achieved / peak, 4), "traffic": None,
+                        "kernel": "se2n_unet_forward (k_conv_fwd: mma.sync m16n8k16 bf16, FP32 accumulate)",
+                        "flops_per_launch": fl, "avg_launch_ms": round(ms_fwd, 4),
+                        "peak_basis": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json bf16_tflops)"},
+           "training": {"pairs": count, "batch": tb, "steps": done, "seconds": round(train_s, 2),
+                        "lr": f"Adam, linear warm-up over {warm} steps to {lr0}, cosine to {lr_min}",
+                        "ms_per_step": round(ms_step, 3), "tflops": round(train_tflops, 2),
+                        "loss_every_500_steps": [float(f"{v:.3g}") for v in losses],
+                        "pair_generation_s": round(gen_s, 2), "method_gpu_s_for_pairs": round(gen_ms / 1e3, 2)},
+           "e2e": {"value": world * SURR_BATCH / (ms_e2e / 1e3), "unit": SURR_UNIT, "ms_per_step": ms_e2e,
+                   "h2d_bytes_per_step": int(fh.numel() * 4 + mh.numel()), "d2h_bytes_per_step": int(oh.numel() * 4),
+                   "api": "pinned host copies + se2n_surrogate_inpaint"},
+           "clocks": clocks.summary(),
+           # per surrogate call: input packing, 3 pools, 14 convolutions, head, residual; plus the
+           # method's kernels for the images that fell back (counted by the plan)
+           "gpu_launches": SURR_LAUNCHES_PER_CALL * args.steps + int(round(kernels_per_fallback * nf_timed)),
+           "fallbacks_in_timed_region": nf_timed}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = surrogate_cpu_baseline()
+    return res
+
+
+def surrogate_cpu_baseline(n=8):
+    """The FP64 oracle's method on n held-out surrogate images (images/s)."""
+    import oracle
+    first = synth.SURROGATE_VAL_SEEDS[0]
+    p = oracle.Params(reinject=1, **synth.surrogate_method_params())
+    t0 = time.perf_counter()
+    for i in range(n):
+        clean, mask = synth.surrogate_example(first + i)
+        oracle.inpaint(clean * mask, mask, p)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": SURR_UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"the FP64 oracle's method (the surrogate's fallback and teacher) on {n} held-out 256x256 "
+                      f"images, {dt:.1f} s, all host cores"}
+
+
+def _reference_line(args, world, metric, unit, value, ms, cfg, sample):
+    return {"impl": "reference", "metric": metric, "value": value, "unit": unit, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": unit, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
 def run_reference(args, rank, world):
+    """The oracle as the reference arm, on the same workload, metric and unit
+    as our arm, each step a bounded sample of it (rank 0 only)."""
     if rank != 0:
         return None
+    import oracle
+    if args.workload == "surrogate":
+        first = synth.SURROGATE_VAL_SEEDS[0]
+        p = oracle.Params(reinject=1, **synth.surrogate_method_params())
+        per = 2
+
+        def one(k):
+            for i in range(per):
+                clean, mask = synth.surrogate_example(first + (k * per + i) % synth.SURROGATE_VAL_SEEDS[1])
+                oracle.inpaint(clean * mask, mask, p)
+        for k in range(args.warmup):
+            one(k)
+        times = []
+        for k in range(args.steps):
+            t0 = time.perf_counter()
+            one(k)
+            times.append(time.perf_counter() - t0)
+        total = sum(times)
+        value = per * args.steps / total
+        return _reference_line(args, world, SURR_METRIC, SURR_UNIT, value, total / args.steps * 1e3,
+                               {"workload": "surrogate_lines_circles_256 (held-out images)",
+                                "reference_sample": f"{per} images per step"},
+                               f"each step: the FP64 oracle's method on {per} held-out 256x256 images (the surrogate's "
+                               "teacher and fallback), all host cores")
+    if args.workload == "batch":
+        allw = synth.workload_batch()
+        steps = 10
+
+        def one(k):
+            w = allw[k % len(allw)]
+            pp = oracle.Params(N=w.N, beta=w.beta, T=w.T * steps / w.steps, steps=steps, rounds=1, eps=w.eps)
+            t0 = time.perf_counter()
+            oracle.inpaint(w.f, w.mask, pp)
+            return w.H * w.W * w.N * steps, time.perf_counter() - t0
+        for k in range(args.warmup):
+            one(k)
+        upd, total = 0, 0.0
+        for k in range(args.steps):
+            u_, dt = one(args.warmup + k)
+            upd += u_
+            total += dt
+        return _reference_line(args, world, METRIC, UNIT, upd / total, total / args.steps * 1e3,
+                               {"workload": "batch of 256 seeded images (sampled one per step)",
+                                "reference_sample": f"one batch image per step, {steps} CN steps"},
+                               f"each step: the FP64 oracle's inpaint of the next image of the batch with {steps} "
+                               "CN steps (same dt), all host cores")
     w = _workload()
     steps, rounds = 20, 1
     for _ in range(args.warmup):
@@ -396,13 +747,8 @@ def run_reference(args, rank, world):
     value = upd * args.steps / total
     sample = (f"each step: the FP64 oracle's inpaint of the 512x512 N=32 image with {rounds} interval x {steps} "
               f"CN steps ({upd:.3g} updates), all host cores")
-    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": _config(w, {"reference_sample": f"{rounds} x {steps} steps per step"}),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": sample},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    return _reference_line(args, world, METRIC, UNIT, value, total / args.steps * 1e3,
+                           _config(w, {"reference_sample": f"{rounds} x {steps} steps per step"}), sample)
 
 
 def main():
@@ -412,8 +758,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["512", "batch"], default="512",
-                    help="512: the 512x512 N=32 10x500-step inpaint (default); batch: 256 uneven images")
+    ap.add_argument("--workload", choices=["512", "batch", "surrogate"], default="512",
+                    help="512: the 512x512 N=32 10x500-step inpaint (default); batch: 256 uneven images; "
+                         "surrogate: train the U-Net on method pairs, time its inference with fallback")
+    ap.add_argument("--train-seconds", type=float, default=150.0, help="surrogate training time budget")
+    ap.add_argument("--train-pairs", type=int, default=0, help="surrogate training pairs (0: all 20000)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per diffusion launch from an ncu capture of the current kernel")
     args = ap.parse_args()
@@ -426,6 +775,8 @@ def main():
         res = run_reference(args, rank, world)
     elif args.workload == "batch":
         res = run_batch(args, rank, world, local_rank)
+    elif args.workload == "surrogate":
+        res = run_surrogate(args, rank, world, local_rank)
     else:
         res = run_ours(args, rank, world, local_rank)
     if rank == 0 and res is not None:

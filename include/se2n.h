@@ -91,7 +91,10 @@ typedef struct se2n_plan se2n_plan;
  *   final_mix  1: restore once more after the last interval (not in the paper).
  *   guard    restoration divides by h(t_i) only where h(t_i) > guard * h(0)
  *            (relative; 0.1 keeps sigma <= 5.5 at eps = 0.5).
- *   diffuse_flags  SE2N_DIFFUSE_* flags passed to every diffusion. */
+ *   diffuse_flags  SE2N_DIFFUSE_* flags passed to every diffusion.
+ *   reinject 1: the result is the inpainted image, f on the known pixels
+ *            (mask != 0) and the projection only on the corrupted ones;
+ *            0: the projection everywhere (default). */
 typedef struct se2n_params {
     int N;
     double beta;
@@ -105,11 +108,12 @@ typedef struct se2n_params {
     int final_mix;
     double guard;
     int diffuse_flags;
+    int reinject;
 } se2n_params;
 
 /* Fill p with the defaults: N=32, beta=0.25, T=2, steps=100, rounds=1,
  * eps=0.5, sigma_smooth=1, flat_tol=1e-4, proj=max, final_mix=0,
- * guard=0.1, diffuse_flags=0. SE2N_EINVAL if p is NULL. */
+ * guard=0.1, diffuse_flags=0, reinject=0. SE2N_EINVAL if p is NULL. */
 SE2N_API se2n_status se2n_params_default(se2n_params *p);
 
 /* Map the paper's weighting alpha and time T_paper on an M x M image with N
@@ -329,9 +333,12 @@ SE2N_API se2n_status se2n_batch_destroy(se2n_batch *b);
  * channels, BF16 weights and activations with FP32 accumulation, trained by
  * this library's own forward and backward kernels on (corrupted image,
  * method output) pairs generated by se2n_inpaint / se2n_batch_run. The
- * method stays the judge: se2n_surrogate_inpaint falls back to it for every
- * image whose network output misses its own known pixels by more than a
- * threshold (RMS over the known pixels).
+ * output is the masked input plus the network's correction,
+ *     out = f (mask != 0) + head(decoder),
+ * so the network learns only what the method changes. The method stays the
+ * judge: se2n_surrogate_inpaint falls back to it for every image whose
+ * output misses its own known pixels by more than a threshold (RMS over the
+ * known pixels).
  *
  * Layout: images are [count][H][W] float32 and uint8 masks on the device,
  * H and W multiples of 8. Parameters form one flat FP32 vector: for each of
@@ -348,14 +355,16 @@ typedef struct se2n_unet se2n_unet;
 SE2N_API se2n_status se2n_unet_create(se2n_unet **out, int batch, int H, int W, void *stream);
 SE2N_API se2n_status se2n_unet_destroy(se2n_unet *u);
 SE2N_API se2n_status se2n_unet_param_count(const se2n_unet *u, long long *n);
-/* Deterministic He-normal initialisation from a seed (resets Adam). */
+/* Deterministic initialisation from a seed (resets Adam): He-normal conv
+ * weights, zero biases and a zero head, so that the untrained output is the
+ * masked input itself. */
 SE2N_API se2n_status se2n_unet_init(se2n_unet *u, unsigned long long seed);
 /* Host copies of the flat FP32 parameters / gradients (synchronous). Setting
  * the parameters also resets the Adam moments. */
 SE2N_API se2n_status se2n_unet_set_params(se2n_unet *u, const float *host);
 SE2N_API se2n_status se2n_unet_get_params(se2n_unet *u, float *host);
 SE2N_API se2n_status se2n_unet_get_grads(se2n_unet *u, float *host);
-/* out [count][H][W] = network(f, mask). */
+/* out [count][H][W] = f (mask != 0) + network(f, mask). */
 SE2N_API se2n_status se2n_unet_forward(se2n_unet *u, const float *f, const uint8_t *mask, int count, float *out);
 /* Forward, the loss mean((out - target)^2) (written to loss_device if not
  * NULL) and the gradient of every parameter (kept inside for the optimizer,

@@ -82,6 +82,7 @@ class Params:
     flat_tol: float = 1e-4
     final_mix: int = 0       # 1: restore once more after the last interval
     guard: float = 0.1       # relative: sigma only where h(t) > guard * h(0)
+    reinject: int = 0        # 1: the result keeps f on the known pixels (the inpainted image)
 
 
 # ----------------------------------------------------------------------------
@@ -322,7 +323,9 @@ def inpaint(f, mask, p: Params, bins=None, nthreads=0, keep=False):
     """Lift, then `rounds` intervals of length T/rounds: the first starts
     from the lift; each later one starts from the statically restored state
     (the mix at t_0 is the identity, sigma = 1). The state at T is inverted
-    and projected (mixed once more first if final_mix).
+    and projected (mixed once more first if final_mix). With reinject the
+    known pixels of the result are f itself: the method only fills the
+    corrupted ones.
 
     Returns a dict with out (the image), bins and, if keep, the final volume."""
     if bins is None:
@@ -336,7 +339,10 @@ def inpaint(f, mask, p: Params, bins=None, nthreads=0, keep=False):
     v = inverse(v)
     if p.final_mix:
         v = mix(v, f, mask, bins, p.eps, p.guard)
-    res = dict(out=project(v, p.proj), bins=bins)
+    out = project(v, p.proj)
+    if p.reinject:
+        out = np.where(np.asarray(mask) != 0, np.asarray(f, dtype=np.float64), out)
+    res = dict(out=out, bins=bins)
     if keep:
         res["vol"] = v
     return res

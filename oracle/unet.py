@@ -4,7 +4,8 @@ tests may import it; the CUDA library never does).
 The network the library trains (not part of the paper): 3x3 convolutions
 with padding 1 and ReLU, 2x2 average pooling, nearest upsampling,
 channel concatenation of the upsampled lower level and the skip
-connection, a 1x1 head to one channel, and the loss mean((out - target)^2).
+connection, a 1x1 head to one channel added to the masked input
+(out = f (mask != 0) + head), and the loss mean((out - target)^2).
 Layers and the flat parameter layout are those of the C ABI (se2n_unet_*):
 for each of the 14 conv layers W[cout][9][cin] then b[cout], then the head
 w[32], b[1]; tap = (dy+1)*3 + (dx+1).
@@ -111,21 +112,28 @@ def pack_input(f, mask):
     return x
 
 
-def forward(params, f, mask):
+def forward(params, f, mask, bf16=False):
+    """Forward pass. With bf16=True every stored activation is rounded to
+    bfloat16 where a bfloat16 implementation stores it (conv outputs after
+    bias and ReLU, pooled outputs, the packed input); arithmetic stays FP64.
+    The ReLU masks are then taken on the rounded outputs."""
     Ws, bs, hw, hb = unpack(np.asarray(params, dtype=np.float64))
-    x0 = pack_input(f, mask)
-    cache = {"x0": x0, "z": [None] * 14, "in": [None] * 14}
+    q = bf16_round if bf16 else (lambda v: v)
+    x0 = q(pack_input(f, mask))
+    cache = {"x0": x0, "z": [None] * 14, "in": [None] * 14, "act": [None] * 14, "bf16": bf16}
     relu = lambda z: np.maximum(z, 0.0)
     e, h = [], x0
     for l in range(4):
         if l > 0:
-            h = pool(e[l - 1])
+            h = q(pool(e[l - 1]))
         cache["in"][2 * l] = h
         cache["z"][2 * l] = conv3x3(h, Ws[2 * l], bs[2 * l])
-        a = relu(cache["z"][2 * l])
+        a = q(relu(cache["z"][2 * l]))
+        cache["act"][2 * l] = a
         cache["in"][2 * l + 1] = a
         cache["z"][2 * l + 1] = conv3x3(a, Ws[2 * l + 1], bs[2 * l + 1])
-        e.append(relu(cache["z"][2 * l + 1]))
+        e.append(q(relu(cache["z"][2 * l + 1])))
+        cache["act"][2 * l + 1] = e[-1]
     below = e[3]
     for k in range(3):
         level = 2 - k
@@ -133,22 +141,29 @@ def forward(params, f, mask):
         xin = np.concatenate([up(below), e[level]], axis=-1)
         cache["in"][la] = xin
         cache["z"][la] = conv3x3(xin, Ws[la], bs[la])
-        c = relu(cache["z"][la])
+        c = q(relu(cache["z"][la]))
+        cache["act"][la] = c
         cache["in"][lb] = c
         cache["z"][lb] = conv3x3(c, Ws[lb], bs[lb])
-        below = relu(cache["z"][lb])
+        below = q(relu(cache["z"][lb]))
+        cache["act"][lb] = below
     d0 = below
-    out = d0 @ hw + hb
+    out = d0 @ hw + hb + np.asarray(f, dtype=np.float64) * (np.asarray(mask) != 0)
     cache["d0"] = d0
     cache["e"] = e
     return out, cache
 
 
-def loss_and_grads(params, f, mask, target):
-    """mean((out - target)^2) and its gradient w.r.t. the flat parameters."""
+def loss_and_grads(params, f, mask, target, bf16=False):
+    """mean((out - target)^2) and its gradient w.r.t. the flat parameters.
+    With bf16=True the activation gradients are also rounded to bfloat16
+    where a bfloat16 implementation stores them (after each masking, each
+    data-gradient, each pooling/upsampling adjoint), and the ReLU masks use
+    the rounded activations."""
     params = np.asarray(params, dtype=np.float64)
     Ws, bs, hw, hb = unpack(params)
-    out, cache = forward(params, f, mask)
+    out, cache = forward(params, f, mask, bf16)
+    q = bf16_round if bf16 else (lambda v: v)
     r = out - np.asarray(target, dtype=np.float64)
     loss = np.mean(r ** 2)
     gout = 2.0 * r / r.size
@@ -156,7 +171,8 @@ def loss_and_grads(params, f, mask, target):
     g = np.zeros(n)
     g[o_hw:o_hw + 32] = np.einsum("bhw,bhwc->c", gout, cache["d0"])
     g[o_hb] = gout.sum()
-    relu_mask = lambda z: (z > 0).astype(np.float64)
+    act = cache["act"]
+    relu_mask = lambda layer: (act[layer] > 0).astype(np.float64) if bf16 else (cache["z"][layer] > 0).astype(np.float64)
 
     def conv_back(layer, gz):
         gx, gW, gb = conv3x3_backward(cache["in"][layer], Ws[layer], gz)
@@ -165,28 +181,23 @@ def loss_and_grads(params, f, mask, target):
         g[b:b + gb.size] = gb
         return gx
 
-    gd = gout[..., None] * hw[None, None, None, :]
+    gz = q(gout[..., None] * hw[None, None, None, :] * relu_mask(13))
     gskip = [None] * 3
-    ge3 = None
     for k in (2, 1, 0):
         la, lb = 8 + 2 * k, 9 + 2 * k
-        gz = gd * relu_mask(cache["z"][lb])
         gc = conv_back(lb, gz)
-        gz = gc * relu_mask(cache["z"][la])
+        gz = q(gc * relu_mask(la))
         gin = conv_back(la, gz)
         lo = LAYERS[la][2]
-        gup, gskip[k] = gin[..., :lo], gin[..., lo:]
-        gd = up_backward(gup)
-        if k == 0:
-            ge3 = gd
-    ge = ge3
+        gup, gskip[k] = q(gin[..., :lo]), q(gin[..., lo:])
+        below_layer = 9 + 2 * (k - 1) if k > 0 else 7
+        gz = q(up_backward(gup) * relu_mask(below_layer))
     for l in (3, 2, 1, 0):
         if l < 3:
-            ge = pool_backward(gp) + gskip[2 - l]
-        gz = ge * relu_mask(cache["z"][2 * l + 1])
+            gz = q((pool_backward(gp) + gskip[2 - l]) * relu_mask(2 * l + 1))
         ga = conv_back(2 * l + 1, gz)
-        gz = ga * relu_mask(cache["z"][2 * l])
-        gp = conv_back(2 * l, gz)
+        gz = q(ga * relu_mask(2 * l))
+        gp = q(conv_back(2 * l, gz))
     return loss, g
 
 

@@ -176,17 +176,19 @@ se2n_status mix_impl(se2n_plan *plan, float2 *vol, const float *f, const uint8_t
     return cuda_status(plan, se2n_launch_mix(vol, f, mask, bins, plan->HW, plan->N, scale, eps, guard, plan->stream));
 }
 
-se2n_status project_impl(se2n_plan *plan, const float2 *vol, float scale, int proj, float *out) {
+se2n_status project_impl(se2n_plan *plan, const float2 *vol, float scale, int proj, const float *f,
+                         const uint8_t *mask, float *out) {
     StageTimer timer(plan, SE2N_STAGE_PROJECT);
     plan->kernels += 1;
-    return cuda_status(plan, se2n_launch_project(vol, plan->HW, plan->N, scale, proj, out, plan->stream));
+    return cuda_status(plan, se2n_launch_project(vol, plan->HW, plan->N, scale, proj, f, mask, out, plan->stream));
 }
 
 se2n_status check_params(const se2n_plan *plan, const se2n_params *p) {
     if (!p) return SE2N_EINVAL;
     if (p->N != plan->N || !(p->beta > 0.0) || !(p->T >= 0.0) || p->steps < 1 || p->rounds < 1) return SE2N_EINVAL;
     if (!(p->eps >= 0.0 && p->eps <= 1.0) || !(p->sigma_smooth > 0.0) || !(p->flat_tol >= 0.0)) return SE2N_EINVAL;
-    if ((p->proj != SE2N_PROJ_MAX && p->proj != SE2N_PROJ_MEAN) || (p->final_mix != 0 && p->final_mix != 1))
+    if ((p->proj != SE2N_PROJ_MAX && p->proj != SE2N_PROJ_MEAN) || (p->final_mix != 0 && p->final_mix != 1) ||
+        (p->reinject != 0 && p->reinject != 1))
         return SE2N_EINVAL;
     if (!(p->guard >= 0.0) ||
         (p->diffuse_flags & ~(SE2N_DIFFUSE_SM_FP64 | SE2N_DIFFUSE_SPLIT_DIAG | SE2N_DIFFUSE_FULL_CORRECTION)))
@@ -227,7 +229,7 @@ se2n_status inpaint_impl(se2n_plan *plan, const float *f, const uint8_t *mask, c
         SE2N_TRY(mix_impl(plan, vol, f, mask, bins, inv_hw, (float)p->eps, (float)p->guard));
         scale = 1.0f;
     }
-    return project_impl(plan, vol, scale, p->proj, out);
+    return project_impl(plan, vol, scale, p->proj, p->reinject ? f : nullptr, p->reinject ? mask : nullptr, out);
 }
 
 void free_plan(se2n_plan *plan) {
@@ -277,6 +279,7 @@ se2n_status se2n_params_default(se2n_params *p) {
     p->final_mix = 0;
     p->guard = 0.1;
     p->diffuse_flags = 0;
+    p->reinject = 0;
     return SE2N_OK;
 }
 
@@ -406,7 +409,7 @@ se2n_status se2n_project(se2n_plan *plan, const void *vol, int proj, float *out)
     SE2N_TRY(check_plan(plan));
     if (!device_ptr(vol, 16) || !device_ptr(out, 8)) return SE2N_EINVAL;
     if (proj != SE2N_PROJ_MAX && proj != SE2N_PROJ_MEAN) return SE2N_EINVAL;
-    return project_impl(plan, (const float2 *)vol, 1.0f, proj, out);
+    return project_impl(plan, (const float2 *)vol, 1.0f, proj, nullptr, nullptr, out);
 }
 
 se2n_status se2n_inpaint(se2n_plan *plan, const float *f, const uint8_t *mask, const uint8_t *bins_in,
@@ -693,7 +696,8 @@ se2n_status enqueue_batch(se2n_batch *b) {
             SE2N_TRY(mix_impl(pl, b->vols[i], d.f, d.mask, b->bins[i], inv_hw, (float)p.eps, (float)p.guard));
             scale = 1.0f;
         }
-        SE2N_TRY(project_impl(pl, b->vols[i], scale, p.proj, d.out));
+        SE2N_TRY(project_impl(pl, b->vols[i], scale, p.proj, p.reinject ? d.f : nullptr,
+                              p.reinject ? d.mask : nullptr, d.out));
     }
     return SE2N_OK;
 }

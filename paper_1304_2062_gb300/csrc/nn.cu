@@ -272,11 +272,12 @@ __global__ void k_up_bwd_mask(const __nv_bfloat16 *gup, const __nv_bfloat16 *d, 
 }
 
 // Head: out[p] = sum_c w[c] d[p][c] + b (1x1 conv to one channel, FP32 out).
-__global__ void k_head(const __nv_bfloat16 *d, const float *w, const float *b, float *out, long long P, int C) {
+__global__ void k_head(const __nv_bfloat16 *d, const float *w, const float *b, const float *f, const uint8_t *mask,
+                       float *out, long long P, int C) {
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
         float s = b[0];
         for (int c = 0; c < C; ++c) s = fmaf(w[c], __bfloat162float(d[p * C + c]), s);
-        out[p] = s;
+        out[p] = (mask[p] ? f[p] : 0.0f) + s;
     }
 }
 
@@ -485,9 +486,9 @@ cudaError_t up_backward_mask(const __nv_bfloat16 *gup, const __nv_bfloat16 *d, _
     return cudaGetLastError();
 }
 
-cudaError_t head(const __nv_bfloat16 *d, const float *w, const float *b, float *out, long long P, int C,
-                 cudaStream_t s) {
-    k_head<<<grid_for(P), 256, 0, s>>>(d, w, b, out, P, C);
+cudaError_t head(const __nv_bfloat16 *d, const float *w, const float *b, const float *f, const uint8_t *mask,
+                 float *out, long long P, int C, cudaStream_t s) {
+    k_head<<<grid_for(P), 256, 0, s>>>(d, w, b, f, mask, out, P, C);
     return cudaGetLastError();
 }
 

@@ -30,8 +30,10 @@ cudaError_t pool_backward_add_mask(const __nv_bfloat16 *gp, const __nv_bfloat16 
                                    __nv_bfloat16 *ge, int B, int H, int W, int C, cudaStream_t s);
 cudaError_t up_backward_mask(const __nv_bfloat16 *gup, const __nv_bfloat16 *d, __nv_bfloat16 *gd, int B, int Hl,
                              int Wl, int C, cudaStream_t s);
-cudaError_t head(const __nv_bfloat16 *d, const float *w, const float *b, float *out, long long P, int C,
-                 cudaStream_t s);
+// out[p] = f[p] (mask[p] != 0) + sum_c w[c] d[p][c] + b: the 1x1 head plus
+// the input skip (FP32 f, not its bf16 copy).
+cudaError_t head(const __nv_bfloat16 *d, const float *w, const float *b, const float *f, const uint8_t *mask,
+                 float *out, long long P, int C, cudaStream_t s);
 cudaError_t loss_head_backward(const float *out, const float *target, const __nv_bfloat16 *d, const float *w,
                                __nv_bfloat16 *gd, float *gw, float *gb, float *loss, long long P, int C,
                                cudaStream_t s);

@@ -160,7 +160,7 @@ __global__ void k_mix(float4 *__restrict__ vol, const float2 *__restrict__ f, co
 }
 
 __global__ void k_project(const float4 *__restrict__ vol, long long npairs, int N, float scale, int proj,
-                          float2 *__restrict__ out) {
+                          const float2 *__restrict__ f, const uchar2 *__restrict__ mask, float2 *__restrict__ out) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npairs;
          i += (long long)gridDim.x * blockDim.x) {
         float a0, a1;
@@ -182,6 +182,12 @@ __global__ void k_project(const float4 *__restrict__ vol, long long npairs, int 
             }
             a0 /= (float)N;
             a1 /= (float)N;
+        }
+        if (mask) {
+            const uchar2 m = mask[i];
+            const float2 fv = f[i];
+            if (m.x) a0 = fv.x;
+            if (m.y) a1 = fv.y;
         }
         out[i] = make_float2(a0, a1);
     }
@@ -242,10 +248,11 @@ cudaError_t se2n_launch_mix(float2 *vol, const float *f, const uint8_t *mask, co
     return cudaGetLastError();
 }
 
-cudaError_t se2n_launch_project(const float2 *vol, long long HW, int N, float scale, int proj, float *out,
-                                cudaStream_t s) {
+cudaError_t se2n_launch_project(const float2 *vol, long long HW, int N, float scale, int proj, const float *f,
+                                const uint8_t *mask, float *out, cudaStream_t s) {
     const long long n = HW / 2;
-    k_project<<<grid_for(n), kBlock, 0, s>>>((const float4 *)vol, n, N, scale, proj, (float2 *)out);
+    k_project<<<grid_for(n), kBlock, 0, s>>>((const float4 *)vol, n, N, scale, proj, (const float2 *)f,
+                                             (const uchar2 *)mask, (float2 *)out);
     return cudaGetLastError();
 }
 

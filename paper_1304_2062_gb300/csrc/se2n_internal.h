@@ -91,6 +91,8 @@ cudaError_t se2n_launch_lift(const float *f, const uint8_t *mask, const uint8_t 
                              long long HW, int N, cudaStream_t s);
 cudaError_t se2n_launch_mix(float2 *vol, const float *f, const uint8_t *mask, const uint8_t *bins,
                             long long HW, int N, float scale, float eps, float guard, cudaStream_t s);
-cudaError_t se2n_launch_project(const float2 *vol, long long HW, int N, float scale, int proj, float *out,
-                                cudaStream_t s);
+// out = max_r (or mean_r) of scale * Re vol[r]; where mask != null, pixels
+// with mask != 0 take f instead (the inpainted image).
+cudaError_t se2n_launch_project(const float2 *vol, long long HW, int N, float scale, int proj, const float *f,
+                                const uint8_t *mask, float *out, cudaStream_t s);
 cudaError_t se2n_launch_scale(float2 *vol, long long count, float scale, cudaStream_t s);

@@ -115,7 +115,7 @@ se2n_status forward(se2n_unet *u, const float *f, const uint8_t *mask, int n) {
         TRYC(conv_forward(u->c[k], nullptr, 0, n, Hl, Wl, Bb.cin, Wt(lb), Bi(lb), Bb.cout, 1, u->d[k], s));
         below = u->d[k];
     }
-    TRYC(head(u->d[2], u->p + u->hw_off, u->p + u->hb_off, u->out, (long long)n * H * W, 32, s));
+    TRYC(head(u->d[2], u->p + u->hw_off, u->p + u->hb_off, f, mask, u->out, (long long)n * H * W, 32, s));
     return SE2N_OK;
 }
 
@@ -335,10 +335,9 @@ se2n_status se2n_unet_init(se2n_unet *u, unsigned long long seed) {
             h[u->w_off[l] + i] = (float)(sd * sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2));
         }
     }
-    for (int c = 0; c < 32; ++c) {
-        const double u1 = unit(st), u2 = unit(st);
-        h[u->hw_off + c] = (float)(sqrt(1.0 / 32.0) * sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2));
-    }
+    // the head starts at zero: the untrained network is the identity on the
+    // masked input (out = f on known pixels, 0 elsewhere), and training
+    // grows the correction from there
     return se2n_unet_set_params(u, h.data());
 }
 

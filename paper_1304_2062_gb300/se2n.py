@@ -77,6 +77,7 @@ class se2n_params(ctypes.Structure):
         ("final_mix", ctypes.c_int),
         ("guard", ctypes.c_double),
         ("diffuse_flags", ctypes.c_int),
+        ("reinject", ctypes.c_int),
     ]
 
 

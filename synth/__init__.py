@@ -248,6 +248,37 @@ def workload_2048(stress=False, seed=4):
     return Workload("lines_patches_2048_N64", clean, mask, N=64, beta=0.25, T=50.0, steps=1000, rounds=1)
 
 
+# the surrogate's data: the 64x64 generator at 256x256, half of the pixels
+# corrupted; training seeds 10000..29999, validation seeds 30000..30511
+SURROGATE_SIDE = 256
+SURROGATE_TRAIN_SEEDS = (10000, 20000)   # first seed, count
+SURROGATE_VAL_SEEDS = (30000, 512)
+
+
+def surrogate_example(seed, H=SURROGATE_SIDE, W=SURROGATE_SIDE):
+    """(clean, mask) of one surrogate example: the lines-and-circles image at
+    this seed and a 50 % random mask drawn from seed + 1_000_000."""
+    return lines_circles_image(H, W, seed), bernoulli_mask(H, W, seed + 1_000_000, 0.5)
+
+
+def surrogate_examples(first, count, H=SURROGATE_SIDE, W=SURROGATE_SIDE):
+    """Stacked (clean float32 [count][H][W], mask uint8 [count][H][W]) for
+    seeds first .. first + count - 1."""
+    clean = np.empty((count, H, W), np.float32)
+    mask = np.empty((count, H, W), np.uint8)
+    for i in range(count):
+        c, m = surrogate_example(first + i, H, W)
+        clean[i] = c
+        mask[i] = m
+    return clean, mask
+
+
+def surrogate_method_params():
+    """Method parameters the surrogate's targets are made with: N=32 and the
+    64x64 workload's beta=0.5, T=1 in 100 steps, one round."""
+    return dict(N=32, beta=0.5, T=1.0, steps=100, rounds=1)
+
+
 def random_volume(N, H, W, seed, dtype=np.complex128):
     """Random complex volume [N][H][W] with unit-variance Gaussian parts
     (drawn directly in float32 when dtype is complex64, to keep large

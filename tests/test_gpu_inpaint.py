@@ -41,7 +41,8 @@ def _gpu_inpaint(f32, mask, bins, prm, conv=0, tune=None):
 def _params(p: oracle.Params, flags=0):
     return se2n.se2n_params_default(N=p.N, beta=p.beta, T=p.T, steps=p.steps, rounds=p.rounds, eps=p.eps,
                                     sigma_smooth=p.sigma, flat_tol=p.flat_tol, proj=p.proj,
-                                    final_mix=p.final_mix, guard=p.guard, diffuse_flags=flags)
+                                    final_mix=p.final_mix, guard=p.guard, diffuse_flags=flags,
+                                    reinject=p.reinject)
 
 
 def _compare(w, p, conv=0, flags=0, tune=None):
@@ -71,7 +72,7 @@ def test_reduced_512_geometry_three_rounds():
     _compare(w, oracle.Params(N=32, beta=0.25, T=6.0, steps=100, rounds=3))
 
 
-@pytest.mark.parametrize("variant", ["mean", "final_mix", "conv1", "fp64", "N64", "P4", "nonsquare"])
+@pytest.mark.parametrize("variant", ["mean", "final_mix", "conv1", "fp64", "N64", "P4", "nonsquare", "reinject"])
 def test_variants(variant):
     w = synth.workload_512(H=96, W=96, steps=60, rounds=3)
     p = oracle.Params(N=32, beta=0.25, T=6.0, steps=60, rounds=3)
@@ -90,7 +91,12 @@ def test_variants(variant):
         tune = (4, 128, 0)
     elif variant == "nonsquare":
         w = synth.workload_512(H=64, W=160, steps=60, rounds=3)
-    _compare(w, p, conv, flags, tune)
+    elif variant == "reinject":
+        p.reinject = 1
+    got = _compare(w, p, conv, flags, tune)
+    if variant == "reinject":
+        k = w.mask != 0
+        np.testing.assert_array_equal(got[k], w.f.astype(np.float32)[k])
 
 
 def test_table1_parameters_in_pixel_units():
@@ -175,7 +181,7 @@ def test_inpaint_rejects_bad_parameters():
     vol = torch.empty((16, 16, 16), dtype=torch.complex64, device="cuda")
     out = torch.empty((16, 16), dtype=torch.float32, device="cuda")
     bad = [dict(N=32), dict(eps=1.5), dict(rounds=0), dict(steps=0), dict(beta=0.0), dict(proj=3),
-           dict(sigma_smooth=0.0), dict(final_mix=2), dict(diffuse_flags=8)]
+           dict(sigma_smooth=0.0), dict(final_mix=2), dict(diffuse_flags=8), dict(reinject=2)]
     for b in bad:
         prm = se2n.se2n_params_default(N=16)
         for k, v in b.items():

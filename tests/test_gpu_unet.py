@@ -3,12 +3,22 @@ the FP64 reference in oracle/unet.py, its training on pairs the method
 generates, and the method fallback.
 
 Both sides get the same values: the reference uses the bfloat16-rounded
-conv weights and input the GPU computes with. The GPU also rounds every
-activation and activation gradient to bfloat16 (relative step 2^-8), which
-bounds the agreement: about 15 layers forward and back accumulate a few
-times 2^-9 in quadrature. The tolerances below (2e-2 on the output, 5e-2
-per parameter tensor on the gradients) leave a factor of two or more over
-the measured errors printed by the tests.
+conv weights the GPU computes with, and its bf16 mode rounds every stored
+activation and activation gradient to bfloat16 where the GPU stores them
+(FP64 arithmetic in between). What is left is the accumulation: the GPU's
+tensor-core sums differ from FP64 sums in the last FP32 bits, and one such
+difference that moves a stored value across a bfloat16 rounding boundary
+(one step, 2^-8 relative) perturbs everything downstream of it, so that
+after a few layers a large share of the stored values differ by one step.
+tests/test_oracle_unet.py shows this on the CPU: the same bf16 network with
+FP32 instead of FP64 sums differs from the FP64-summed one by up to 6-7 %
+rel-L2 in the middle layers' gradients on the 1x24x40 case below, from a
+single flipped value in layer 1. Two equally valid bfloat16 evaluations
+are therefore this far apart, and the tolerances are set above that
+spread: 0.1 per parameter tensor against the bf16-emulating reference,
+0.15 against the unrounded FP64 one, 2e-2 on the forward output. A wrong
+index, a dropped skip or upsampling gradient or a transposed operand moves
+a gradient by tens of percent or more.
 """
 import numpy as np
 import pytest
@@ -23,8 +33,9 @@ se2n = pytest.importorskip("paper_1304_2062_gb300.se2n")
 
 import torch  # noqa: E402
 
-OUT_TOL = 2e-2
-GRAD_TOL = 5e-2
+OUT_TOL = 2e-2        # forward output against the bf16-emulating reference
+GRAD_TOL = 0.1        # each parameter gradient against the bf16-emulating reference
+FP64_GRAD_TOL = 0.15  # each parameter gradient against the unrounded FP64 reference
 
 
 def _gpu_view(p32):
@@ -66,33 +77,36 @@ def test_forward_and_gradients_match_oracle(B, H, W):
     u.close()
 
     q = _gpu_view(p32)
-    f_in = ou.bf16_round(f * (mask != 0))
-    ref, _ = ou.forward(q, f_in, mask)
-    ref_loss, ref_g = ou.loss_and_grads(q, f_in, mask, target)
+    ref, _ = ou.forward(q, f, mask, bf16=True)
+    ref_loss, ref_g = ou.loss_and_grads(q, f, mask, target, bf16=True)
+    _, g64 = ou.loss_and_grads(q, f, mask, target)
     e_out = _rel(got, ref)
     print(f"forward rel-L2 {e_out:.2e}; loss {host(loss)[0]:.6f} vs {ref_loss:.6f}")
-    assert e_out <= OUT_TOL
-    assert abs(host(loss)[0] - ref_loss) <= OUT_TOL * ref_loss
     offs, hw, hb, n = ou.layout()
-    worst = 0.0
+    rows = []
     for i, ((w, b), (cin, cout, _)) in enumerate(zip(offs, ou.LAYERS)):
         cw = 2 if cin == 8 else cin  # input channels 2..7 are always zero
-        gw = g[w:w + cout * 9 * cin].reshape(cout, 9, cin)[:, :, :cw]
-        rw = ref_g[w:w + cout * 9 * cin].reshape(cout, 9, cin)[:, :, :cw]
-        ew, eb = _rel(gw, rw), _rel(g[b:b + cout], ref_g[b:b + cout])
-        worst = max(worst, ew, eb)
-        print(f"layer {i:2d}: dW rel-L2 {ew:.2e}, db rel-L2 {eb:.2e}")
-        assert ew <= GRAD_TOL and eb <= GRAD_TOL
+        pick = lambda v: v[w:w + cout * 9 * cin].reshape(cout, 9, cin)[:, :, :cw]
+        ew, eb = _rel(pick(g), pick(ref_g)), _rel(g[b:b + cout], ref_g[b:b + cout])
+        e64 = _rel(pick(g), pick(g64))
+        rows.append((ew, eb, e64))
+        print(f"layer {i:2d}: dW rel-L2 {ew:.2e}, db rel-L2 {eb:.2e} (bf16-emulating); dW vs FP64 {e64:.2e}")
     eh = _rel(g[hw:hb + 1], ref_g[hw:hb + 1])
-    print(f"head: rel-L2 {eh:.2e}; worst layer {worst:.2e}")
+    print(f"head: rel-L2 {eh:.2e}")
+    assert e_out <= OUT_TOL
+    assert abs(host(loss)[0] - ref_loss) <= OUT_TOL * ref_loss
+    for ew, eb, e64 in rows:
+        assert ew <= GRAD_TOL and eb <= GRAD_TOL
+        assert e64 <= FP64_GRAD_TOL
     assert eh <= GRAD_TOL
 
 
 def _method_pairs(n, H, W, seed, N=32):
-    """(corrupted image, mask, method output) from the GPU method."""
+    """(corrupted image, mask, inpainted image) from the GPU method: f on the
+    known pixels, the method's value on the corrupted ones."""
     fs, ms, outs = [], [], []
     plan = se2n.se2n_plan_create(H, W, N)
-    prm = se2n.se2n_params_default(N=N, beta=0.5, T=1.0, steps=100, rounds=1)
+    prm = se2n.se2n_params_default(N=N, beta=0.5, T=1.0, steps=100, rounds=1, reinject=1)
     vol = torch.empty((N, H, W), dtype=torch.complex64, device="cuda")
     for i in range(n):
         clean = synth.lines_circles_image(H, W, seed + i)
@@ -125,9 +139,12 @@ def test_training_on_method_pairs_reduces_the_loss():
     u.close()
     first, last = np.mean(losses[:10]), np.mean(losses[-10:])
     psnr = lambda a, b: 10 * np.log10(1.0 / np.mean((a - b) ** 2))
-    p_net, p_zero = psnr(pred, t[:16]), psnr(f[:16], t[:16])
-    print(f"loss {first:.4f} -> {last:.5f}; PSNR vs method: network {p_net:.2f} dB, zero-filled input {p_zero:.2f} dB")
-    assert last < first / 5
+    p_net, p_zero = psnr(pred, t[:16]), psnr(f[:16], t[:16])  # the zero-filled input is the untrained skip
+    k = m[:16] != 0
+    resid = np.sqrt(np.mean((pred[k] - f[:16][k]) ** 2))
+    print(f"loss {first:.4f} -> {last:.5f}; PSNR vs method: network {p_net:.2f} dB, zero-filled input {p_zero:.2f} dB; "
+          f"RMS on known pixels {resid:.4f}")
+    assert last < first / 2
     assert p_net > p_zero + 3.0
 
 
@@ -135,14 +152,14 @@ def test_fallback_to_the_method():
     H = W = 32
     f, m, t = _method_pairs(4, H, W, 900)
     u = se2n.se2n_unet_create(4, H, W)
-    se2n.se2n_unet_init(u, 1)
+    se2n.se2n_unet_set_params(u, ou.he_params(1).astype(np.float32))  # random, head included
     plan = se2n.se2n_plan_create(H, W, 32)
-    prm = se2n.se2n_params_default(N=32, beta=0.5, T=1.0, steps=100, rounds=1)
+    prm = se2n.se2n_params_default(N=32, beta=0.5, T=1.0, steps=100, rounds=1, reinject=1)
     vol = torch.empty((32, H, W), dtype=torch.complex64, device="cuda")
     fd, md = t_f32(f), t_u8(m)
     out = torch.zeros((4, H, W), dtype=torch.float32, device="cuda")
     r = np.zeros(4, np.float32)
-    # an untrained network misses the known pixels: every image is redone by the method
+    # a random network misses the known pixels: every image is redone by the method
     nf = se2n.se2n_surrogate_inpaint(u, plan, prm, fd, md, 4, 2e-2, vol, out, r)
     torch.cuda.synchronize()
     assert nf == 4 and (r > 2e-2).all()
@@ -155,6 +172,20 @@ def test_fallback_to_the_method():
     np.testing.assert_array_equal(host(out), host(ref))
     plan.close()
     u.close()
+
+
+def test_initialisation_is_the_identity_on_the_masked_input():
+    """se2n_unet_init zeroes the head: the untrained output is f on the known
+    pixels and 0 on the others, exactly."""
+    rng = np.random.default_rng(2)
+    f = rng.uniform(0.05, 1.0, (2, 16, 24)).astype(np.float32)
+    m = (rng.random((2, 16, 24)) > 0.5).astype(np.uint8)
+    u = se2n.se2n_unet_create(2, 16, 24)
+    se2n.se2n_unet_init(u, 3)
+    out = torch.zeros((2, 16, 24), dtype=torch.float32, device="cuda")
+    se2n.se2n_unet_forward(u, t_f32(f), t_u8(m), 2, out)
+    u.close()
+    np.testing.assert_array_equal(host(out), f * (m != 0))
 
 
 def test_network_rejects_bad_arguments():

@@ -406,6 +406,20 @@ def test_single_round_inpaint_is_lift_diffuse_project(oracle_mod):
     np.testing.assert_array_equal(res["out"], manual)
 
 
+def test_reinject_keeps_known_pixels_and_fills_the_rest(oracle_mod):
+    """The inpainted image (reinject): f itself on every known pixel, and
+    on the corrupted ones exactly the plain projection."""
+    w = synth.workload_small(32, 32)
+    p = oracle_mod.Params(N=8, beta=0.5, T=1.0, steps=10, rounds=2)
+    plain = oracle_mod.inpaint(w.f, w.mask, p)["out"]
+    p.reinject = 1
+    out = oracle_mod.inpaint(w.f, w.mask, p)["out"]
+    k = w.mask != 0
+    np.testing.assert_array_equal(out[k], w.f[k])
+    np.testing.assert_array_equal(out[~k], plain[~k])
+    assert np.abs(plain[k] - w.f[k]).max() > 1e-3  # the plain result does move the known pixels
+
+
 def test_restoration_improves_on_zero_fill_and_beats_downstairs(oracle_mod):
     """Sanity, not parity: on bar-corrupted synthetic data, static
     restoration on the lifted volume brings the corrupted pixels closer to
