@@ -1,0 +1,285 @@
+// 3x3 convolution (padding 1, NHWC bf16) as a persistent, warp-specialised
+// implicit GEMM on the tcgen05 tensor cores with TMA operand loads:
+//
+//   D[m][n] = sum_k A(m, k) B(n, k),  m = output pixel, n = output channel,
+//   k = tap * C + c,  A(m, tap * C + c) = In[pixel m shifted by tap][c],
+//   B = a K-major [N][9 C] weight matrix.
+//
+// Tiles of D are 128 pixels (a bw x bh rectangle of one image, bw * bh = 128)
+// by BN channels. The K loop runs over (tap, CK-channel chunk) blocks; for
+// each block one TMA box load brings the tile's 128 pixels shifted by the
+// tap (the tensor map's out-of-bounds zero fill is the convolution's
+// padding) and one brings the matching BN x CK weights, both in the
+// swizzled K-major layout the tensor core reads (CK = 64: 128-byte swizzle;
+// CK = 32: 64-byte swizzle).
+//
+// Roles (192 threads, one CTA per SM, tiles strided over CTAs):
+//   warp 0, one thread   TMA producer: fills a ring of STAGES stages, each
+//                        guarded by a "full" (transaction bytes) and an
+//                        "empty" (tensor core done) mbarrier;
+//   warp 1               allocates 2 x BN tensor-memory columns; one thread
+//                        issues tcgen05.mma (M = 128, N = BN, K = 16) into
+//                        one of two accumulators and commits to "empty" per
+//                        stage and to "acc full" per tile;
+//   warps 2-5            epilogue: tcgen05.ld of the accumulator rows their
+//                        lane quarter may access, then the functor EPI, then
+//                        "acc empty", so the next tile's MMAs overlap it.
+//
+// Every wait is bounded (about 2 s at the full clock). One that runs out sets *err and the
+// shared abort flag; the CTA then stops, lets what it issued complete
+// (bounded), releases its tensor memory and returns. CTAs that find *err
+// set do nothing.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "conv_tc.cuh"
+
+namespace se2n {
+namespace nn {
+namespace tma {
+
+// Geometry of one convolution launch (passed by value).
+struct ConvGeo {
+    int B, H, W, C;      // A tensor: B images of H x W pixels, C channels
+    int bw, bh;          // tile shape in pixels (bw * bh == 128)
+    int tiles_x, tiles_y, mtiles, ntiles, tiles;
+    int nchunk;          // C / CK
+    int KB;              // 9 * nchunk
+    int flip;            // 1: taps mirrored (data gradient)
+};
+
+template <int BN, int CK>
+struct Cfg {
+    static_assert(CK == 32 || CK == 64, "channel chunk of 32 (64-byte swizzle) or 64 (128-byte swizzle)");
+    static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "tcgen05 M=128 needs N in [16, 256], N % 16 == 0");
+    static constexpr int A_BYTES = 128 * CK * 2;
+    static constexpr int B_BYTES = BN * CK * 2;
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int STAGES = (196608 / STAGE) > 12 ? 12 : (196608 / STAGE);
+    // two accumulators, each at a power-of-two column offset
+    static constexpr int ACC_COLS = BN <= 16 ? 16 : BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+    static constexpr int TMEM_COLS = 2 * ACC_COLS < 32 ? 32 : 2 * ACC_COLS;
+    static constexpr int SMEM = 1024 + STAGES * STAGE + 256;
+    static constexpr uint32_t SBO = 8 * CK * 2;              // 8-row atom
+    static constexpr uint64_t LAYOUT = CK == 64 ? 2 : 4;     // SWIZZLE_128B / SWIZZLE_64B
+};
+
+template <int BN, int CK>
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    using C = Cfg<BN, CK>;
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(16u >> 4) << 16;
+    d |= (uint64_t)(C::SBO >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= C::LAYOUT << 61;
+    return d;
+}
+
+__device__ __forceinline__ void arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];\n" ::"r"(dst),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int c0, int c1, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+            dst),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tile_origin(const ConvGeo &g, int t, int &b, int &x0, int &y0, int &nt) {
+    const int mt = t % g.mtiles;
+    nt = t / g.mtiles;
+    const int per_img = g.tiles_x * g.tiles_y;
+    b = mt / per_img;
+    const int r = mt - b * per_img;
+    y0 = (r / g.tiles_x) * g.bh;
+    x0 = (r % g.tiles_x) * g.bw;
+}
+
+// EPI provides
+//   store(m, n, v[16], float &state)  the 16 outputs of pixel m, columns n..n+15
+//   finish(m, float state)            after the last column group of pixel m
+template <int BN, int CK, class EPI>
+__global__ void __launch_bounds__(192, 1)
+    k_conv_tma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, const ConvGeo g,
+               const EPI epi, int *err) {
+    using Cf = Cfg<BN, CK>;
+    constexpr int S = Cf::STAGES;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    const uint32_t bar_full = base + S * Cf::STAGE;
+    const uint32_t bar_empty = bar_full + 8 * S;
+    const uint32_t bar_afull = bar_empty + 8 * S;   // 2
+    const uint32_t bar_aempty = bar_afull + 16;     // 2
+    const uint32_t tmem_slot = bar_aempty + 16;
+    volatile int *abort = (volatile int *)(smem_raw + (tmem_slot + 4 - raw));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        *abort = *(volatile int *)err;
+        for (int s = 0; s < S; ++s) {
+            tc::mbar_init(bar_full + 8 * s, 1);
+            tc::mbar_init(bar_empty + 8 * s, 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            tc::mbar_init(bar_afull + 8 * a, 1);
+            tc::mbar_init(bar_aempty + 8 * a, 4);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"((uint64_t)&mapA) : "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"((uint64_t)&mapB) : "memory");
+    }
+    __syncthreads();
+    if (*abort) return;
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(tmem_slot),
+                     "r"((uint32_t)Cf::TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    uint32_t tmem_base;
+    asm volatile("ld.shared.u32 %0, [%1];\n" : "=r"(tmem_base) : "r"(tmem_slot));
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer ----------------
+            int s = 0;
+            uint32_t ph = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < g.tiles && ok; t += gridDim.x) {
+                int b, x0, y0, nt;
+                tile_origin(g, t, b, x0, y0, nt);
+                for (int kb = 0; kb < g.KB; ++kb) {
+                    const int tap = kb / g.nchunk, ch = kb - tap * g.nchunk;
+                    int dy = tap / 3 - 1, dx = tap % 3 - 1;
+                    if (g.flip) {
+                        dy = -dy;
+                        dx = -dx;
+                    }
+                    if (!tc::mbar_wait(bar_empty + 8 * s, ph ^ 1u, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t sa = base + s * Cf::STAGE, sb = sa + Cf::A_BYTES;
+                    arrive_expect_tx(bar_full + 8 * s, Cf::STAGE);
+                    tma_load_4d(sa, &mapA, ch * CK, x0 + dx, y0 + dy, b, bar_full + 8 * s);
+                    tma_load_2d(sb, &mapB, tap * g.C + ch * CK, nt * BN, bar_full + 8 * s);
+                    if (++s == S) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
+                }
+            }
+            if (!ok) {
+                // loads already issued finish on their own within microseconds
+                const long long t0 = clock64();
+                while (clock64() - t0 < 200000LL) {
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer ----------------
+            constexpr uint32_t IDESC = tc::idesc_bf16_f32<BN>();
+            int s = 0, acc = 0;
+            uint32_t ph = 0, aph = 0;
+            bool ok = true;
+            uint32_t last_bar = 0, last_par = 0;
+            for (int t = blockIdx.x; t < g.tiles && ok; t += gridDim.x) {
+                if (!tc::mbar_wait(bar_aempty + 8 * acc, aph ^ 1u, abort)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const uint32_t d = tmem_base + (uint32_t)(acc * Cf::ACC_COLS);
+                for (int kb = 0; kb < g.KB; ++kb) {
+                    if (!tc::mbar_wait(bar_full + 8 * s, ph, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                    const uint32_t sa = base + s * Cf::STAGE, sb = sa + Cf::A_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < CK / 16; ++kk)
+                        tc::mma_f16(d, sdesc<BN, CK>(sa + kk * 32), sdesc<BN, CK>(sb + kk * 32), IDESC,
+                                    (kb > 0 || kk > 0) ? 1u : 0u);
+                    tc::mma_commit(bar_empty + 8 * s);
+                    last_bar = bar_empty + 8 * s;
+                    last_par = ph;
+                    if (++s == S) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                tc::mma_commit(bar_afull + 8 * acc);
+                if (++acc == 2) {
+                    acc = 0;
+                    aph ^= 1u;
+                }
+            }
+            if (!ok && last_bar) tc::mbar_wait(last_bar, last_par, nullptr);  // tensor core idle before release
+        }
+    } else {
+        // ---------------- epilogue (warps 2..5) ----------------
+        const int q = warp & 3;  // lane quarter this warp may read
+        int acc = 0;
+        uint32_t aph = 0;
+        for (int t = blockIdx.x; t < g.tiles; t += gridDim.x) {
+            if (!tc::mbar_wait(bar_afull + 8 * acc, aph, abort)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            int b, x0, y0, nt;
+            tile_origin(g, t, b, x0, y0, nt);
+            const int r = q * 32 + lane;
+            const int y = y0 + r / g.bw, x = x0 + r % g.bw;
+            const int m = (b * g.H + y) * g.W + x;
+            const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * Cf::ACC_COLS);
+            float state = 0.0f;
+#pragma unroll 1
+            for (int j0 = 0; j0 < BN; j0 += 16) {
+                uint32_t v[16];
+                tc::tmem_ld16(taddr + (uint32_t)j0, v);
+                float f[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) f[i] = __uint_as_float(v[i]);
+                epi.store(m, nt * BN + j0, f, state);
+            }
+            epi.finish(m, state);
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            __syncwarp();
+            if (lane == 0) arrive(bar_aempty + 8 * acc);
+            if (++acc == 2) {
+                acc = 0;
+                aph ^= 1u;
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && *abort) atomicExch(err, 1);
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem_base),
+                     "r"((uint32_t)Cf::TMEM_COLS));
+    }
+}
+
+}  // namespace tma
+}  // namespace nn
+}  // namespace se2n

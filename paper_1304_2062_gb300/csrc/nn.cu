@@ -9,63 +9,18 @@
 // layout are in unet.cu.
 #include <cuda_bf16.h>
 
+#include "conv_loaders.cuh"
+#include "conv_tc.cuh"
 #include "nn.h"
 #include "nn_gemm.cuh"
 
 using namespace se2n::nn;
 
+// Set by a tensor-core convolution whose bounded wait ran out (never expected;
+// it would mean the device stopped making progress). Read by tc_fault().
+__device__ int g_tc_fault;
+
 namespace {
-
-struct Geo {
-    int B, H, W;
-    __device__ __forceinline__ void pix(int m, int &b, int &y, int &x) const {
-        x = m % W;
-        const int t = m / W;
-        y = t % H;
-        b = t / H;
-    }
-};
-
-// A operand of a forward conv: the input activation, gathered per tap. The
-// input may be the concatenation [nearest-upsample(lo), skip] along
-// channels: channels < C1 come from `lo` at half resolution, the rest from
-// `skip` at full resolution.
-struct ConvInLoader {
-    Geo g;
-    const __nv_bfloat16 *src;   // full-resolution source (or the skip part)
-    const __nv_bfloat16 *lo;    // half-resolution upsampled part, or null
-    int C, C1, M, K;            // C = total input channels; C1 = channels from `lo`
-    int flip;                   // 1: taps mirrored (backward data)
-    __device__ __forceinline__ const void *chunk(int m, int k) const {
-        if (m >= M || k >= K) return nullptr;
-        const int tap = k / C, c = k - tap * C;
-        int dy = tap / 3 - 1, dx = tap % 3 - 1;
-        if (flip) {
-            dy = -dy;
-            dx = -dx;
-        }
-        int b, y, x;
-        g.pix(m, b, y, x);
-        const int yy = y + dy, xx = x + dx;
-        if (yy < 0 || yy >= g.H || xx < 0 || xx >= g.W) return nullptr;
-        if (lo && c < C1) {
-            const int Wl = g.W >> 1, Hl = g.H >> 1;
-            return lo + (((long long)b * Hl + (yy >> 1)) * Wl + (xx >> 1)) * C1 + c;
-        }
-        const int Cs = lo ? C - C1 : C;
-        const int cs = lo ? c - C1 : c;
-        return src + (((long long)b * g.H + yy) * g.W + xx) * Cs + cs;
-    }
-};
-
-// B operand of a forward conv: weights W[co][k], K-major.
-struct WeightKLoader {
-    const __nv_bfloat16 *w;
-    int N, K;
-    __device__ __forceinline__ const void *chunk(int n, int k) const {
-        return (n < N && k < K) ? (const void *)(w + (long long)n * K + k) : nullptr;
-    }
-};
 
 // B operand of backward data: B(k = tap*Cout + co, n = ci) = W[co][tap*Cin + ci],
 // N-major (8 consecutive ci of one (tap, co)).
@@ -192,6 +147,95 @@ __global__ void __launch_bounds__(128) k_conv_wgrad(GradOutMLoader la, InNLoader
             }
 }
 
+// ---------------------------------------------------------------------------
+// tcgen05 convolutions (conv_tc.cuh): forward and backward data
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *(const uint32_t *)&h;
+}
+
+// out[m][n..n+15] = relu?(v + bias), bf16; out has N channels per pixel.
+struct FwdEpi {
+    const float *bias;
+    __nv_bfloat16 *out;
+    int N, relu;
+    __device__ __forceinline__ void operator()(int m, int n, const float (&v)[16]) const {
+        uint32_t p[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            float a = v[2 * q] + bias[n + 2 * q], b = v[2 * q + 1] + bias[n + 2 * q + 1];
+            if (relu) {
+                a = fmaxf(a, 0.0f);
+                b = fmaxf(b, 0.0f);
+            }
+            p[q] = pack_bf16(a, b);
+        }
+        uint4 *dst = (uint4 *)(out + (long long)m * N + n);
+        dst[0] = make_uint4(p[0], p[1], p[2], p[3]);
+        dst[1] = make_uint4(p[4], p[5], p[6], p[7]);
+    }
+};
+
+// Backward data: columns < split go to din (times (act > 0) when act is
+// given), the others to din2; N = total columns. split % 16 == 0.
+struct DgradEpi {
+    const __nv_bfloat16 *act;
+    __nv_bfloat16 *din, *din2;
+    int split, N;
+    __device__ __forceinline__ void operator()(int m, int n, const float (&v)[16]) const {
+        float w[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) w[q] = v[q];
+        __nv_bfloat16 *dst;
+        if (n < split) {
+            if (act) {
+                const uint4 *a4 = (const uint4 *)(act + (long long)m * split + n);
+                const uint4 a0 = a4[0], a1 = a4[1];
+                const uint32_t aw[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const __nv_bfloat162 h = *(const __nv_bfloat162 *)&aw[q];
+                    if (!(__bfloat162float(h.x) > 0.0f)) w[2 * q] = 0.0f;
+                    if (!(__bfloat162float(h.y) > 0.0f)) w[2 * q + 1] = 0.0f;
+                }
+            }
+            dst = din + (long long)m * split + n;
+        } else {
+            dst = din2 + (long long)m * (N - split) + (n - split);
+        }
+        uint32_t p[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) p[q] = pack_bf16(w[2 * q], w[2 * q + 1]);
+        uint4 *d4 = (uint4 *)dst;
+        d4[0] = make_uint4(p[0], p[1], p[2], p[3]);
+        d4[1] = make_uint4(p[4], p[5], p[6], p[7]);
+    }
+};
+
+template <int BN, int STAGES, int LAG>
+__global__ void __launch_bounds__(128) k_conv_fwd_tc(ConvInLoader la, WeightKLoader lb, FwdEpi epi) {
+    tc::conv_tile<BN, STAGES, LAG>(la, lb, epi, &g_tc_fault);
+}
+
+template <int BN, int STAGES, int LAG>
+__global__ void __launch_bounds__(128) k_conv_dgrad_tc(ConvInLoader la, WeightKLoader lb, DgradEpi epi) {
+    tc::conv_tile<BN, STAGES, LAG>(la, lb, epi, &g_tc_fault);
+}
+
+// Weights rearranged for the data gradient, K-major in the output channel:
+// wt[ci][tap * Cout + co] = w[co][tap * Cin + ci].
+__global__ void k_transpose_dgrad(const __nv_bfloat16 *w, __nv_bfloat16 *wt, int Cout, int Cin) {
+    const long long total = (long long)Cout * 9 * Cin;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int co = (int)(i % Cout);
+        const long long t = i / Cout;
+        const int tap = (int)(t % 9), ci = (int)(t / 9);
+        wt[i] = w[((long long)co * 9 + tap) * Cin + ci];
+    }
+}
+
 // Column sums of a [P][C] bf16 matrix into db[C] (bias gradients).
 __global__ void k_colsum(const __nv_bfloat16 *g, long long P, int C, float *db) {
     const int c = threadIdx.x;  // blockDim.x == C (<= 256)
@@ -213,21 +257,97 @@ __global__ void k_pack_input(const float *f, const uint8_t *mask, __nv_bfloat16 
     }
 }
 
-// 2x2 average pooling, NHWC.
+// 2x2 average pooling, NHWC, 8 channels (16 bytes) per thread.
 __global__ void k_pool(const __nv_bfloat16 *in, __nv_bfloat16 *out, int B, int H, int W, int C) {
-    const int Ho = H / 2, Wo = W / 2;
-    const long long total = (long long)B * Ho * Wo * C;
+    const int Ho = H / 2, Wo = W / 2, C8 = C / 8;
+    const long long total = (long long)B * Ho * Wo * C8;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        long long t = i / C;
+        const int c = (int)(i % C8) * 8;
+        long long t = i / C8;
         const int x = (int)(t % Wo);
         t /= Wo;
         const int y = (int)(t % Ho);
         const int b = (int)(t / Ho);
         const long long base = (((long long)b * H + 2 * y) * W + 2 * x) * C + c;
-        const float s = __bfloat162float(in[base]) + __bfloat162float(in[base + C]) +
-                        __bfloat162float(in[base + (long long)W * C]) + __bfloat162float(in[base + (long long)W * C + C]);
-        out[i] = __float2bfloat16_rn(0.25f * s);
+        const uint4 q0 = *(const uint4 *)(in + base), q1 = *(const uint4 *)(in + base + C);
+        const uint4 q2 = *(const uint4 *)(in + base + (long long)W * C), q3 = *(const uint4 *)(in + base + (long long)W * C + C);
+        const __nv_bfloat16 *a = (const __nv_bfloat16 *)&q0, *b1 = (const __nv_bfloat16 *)&q1;
+        const __nv_bfloat16 *c2 = (const __nv_bfloat16 *)&q2, *d3 = (const __nv_bfloat16 *)&q3;
+        __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const float s = __bfloat162float(a[k]) + __bfloat162float(b1[k]) + __bfloat162float(c2[k]) +
+                            __bfloat162float(d3[k]);
+            o[k] = __float2bfloat16_rn(0.25f * s);
+        }
+        *(uint4 *)(out + (((long long)b * Ho + y) * Wo + x) * C + c) = *(const uint4 *)o;
+    }
+}
+
+// out[p] = [nearest-upsample(lo) (C1 channels), skip (Cs channels)], 16 bytes per thread.
+__global__ void k_upcat(const __nv_bfloat16 *lo, int C1, const __nv_bfloat16 *skip, int Cs, __nv_bfloat16 *out, int B,
+                        int H, int W) {
+    const int C = C1 + Cs, C8 = C / 8;
+    const long long total = (long long)B * H * W * C8;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C8) * 8;
+        const long long p = i / C8;
+        uint4 v;
+        if (c < C1) {
+            const int x = (int)(p % W);
+            const long long t = p / W;
+            const int y = (int)(t % H);
+            const long long b = t / H;
+            v = *(const uint4 *)(lo + ((b * (H / 2) + y / 2) * (W / 2) + x / 2) * C1 + c);
+        } else {
+            v = *(const uint4 *)(skip + p * Cs + (c - C1));
+        }
+        *(uint4 *)(out + p * C + c) = v;
+    }
+}
+
+// First convolution straight from the image: the input channels are
+// bf16(f m) and m (the other six are zero), so each of the 32 outputs is a
+// sum over 9 taps x 2 channels, done in FP32 on the CUDA cores.
+__global__ void __launch_bounds__(256) k_conv0(const float *f, const uint8_t *mask, const __nv_bfloat16 *w,
+                                               const float *bias, __nv_bfloat16 *out, int B, int H, int W) {
+    __shared__ float sw[32][9][2];
+    __shared__ float sb[32];
+    for (int i = threadIdx.x; i < 32 * 9 * 2; i += blockDim.x) {
+        const int co = i / 18, r = i % 18, tap = r / 2, ci = r % 2;
+        sw[co][tap][ci] = __bfloat162float(w[(co * 9 + tap) * 8 + ci]);
+    }
+    if (threadIdx.x < 32) sb[threadIdx.x] = bias[threadIdx.x];
+    __syncthreads();
+    const long long P = (long long)B * H * W;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(p % W);
+        const long long t = p / W;
+        const int y = (int)(t % H);
+        const long long b = t / H;
+        float v0[9], v1[9];
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+            const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+            v0[tap] = v1[tap] = 0.0f;
+            if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
+                const long long q = (b * H + yy) * W + xx;
+                const float m = mask[q] ? 1.0f : 0.0f;
+                v0[tap] = __bfloat162float(__float2bfloat16_rn(f[q] * m));
+                v1[tap] = m;
+            }
+        }
+        __align__(16) __nv_bfloat16 o[32];
+#pragma unroll
+        for (int co = 0; co < 32; ++co) {
+            float s = 0.0f;
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap) s = fmaf(sw[co][tap][1], v1[tap], fmaf(sw[co][tap][0], v0[tap], s));
+            o[co] = __float2bfloat16_rn(fmaxf(s + sb[co], 0.0f));
+        }
+        uint4 *dst = (uint4 *)(out + p * 32);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dst[k] = ((const uint4 *)o)[k];
     }
 }
 
@@ -417,16 +537,60 @@ cudaError_t launch_wgrad(const GradOutMLoader &la, const InNLoader &lb, float *d
     return cudaGetLastError();
 }
 
+template <int BN, int STAGES, int LAG>
+cudaError_t launch_fwd_tc(const ConvInLoader &la, const WeightKLoader &lb, const FwdEpi &epi, cudaStream_t s) {
+    constexpr int bytes = tc::smem_bytes<BN, STAGES>();
+    auto *fn = &k_conv_fwd_tc<BN, STAGES, LAG>;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    dim3 grid((la.M + tc::BM - 1) / tc::BM, lb.N / BN);
+    fn<<<grid, 128, bytes, s>>>(la, lb, epi);
+    return cudaGetLastError();
+}
+
+template <int BN, int STAGES, int LAG>
+cudaError_t launch_dgrad_tc(const ConvInLoader &la, const WeightKLoader &lb, const DgradEpi &epi, cudaStream_t s) {
+    constexpr int bytes = tc::smem_bytes<BN, STAGES>();
+    auto *fn = &k_conv_dgrad_tc<BN, STAGES, LAG>;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    dim3 grid((la.M + tc::BM - 1) / tc::BM, lb.N / BN);
+    fn<<<grid, 128, bytes, s>>>(la, lb, epi);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 namespace se2n {
 namespace nn {
 
+cudaError_t tc_fault(int *host_flag, bool reset) {
+    cudaError_t e = cudaMemcpyFromSymbol(host_flag, g_tc_fault, sizeof(int));
+    if (e == cudaSuccess && reset && *host_flag) {
+        const int zero = 0;
+        e = cudaMemcpyToSymbol(g_tc_fault, &zero, sizeof(int));
+    }
+    int t = 0;
+    if (e == cudaSuccess) e = tma_fault(&t, reset);
+    if (e == cudaSuccess) *host_flag |= t;
+    return e;
+}
+
 cudaError_t conv_forward(const __nv_bfloat16 *in, const __nv_bfloat16 *lo, int C1, int B, int H, int W, int Cin,
                          const __nv_bfloat16 *w, const float *bias, int Cout, int relu, __nv_bfloat16 *out,
                          cudaStream_t s) {
+    if (!lo) {
+        const cudaError_t e = conv_forward_tma(in, B, H, W, Cin, w, bias, Cout, relu, out, nullptr, s);
+        if (e != cudaErrorNotSupported) return e;
+    }
     ConvInLoader la{{B, H, W}, in, lo, Cin, C1, B * H * W, 9 * Cin, 0};
     WeightKLoader lb{w, Cout, 9 * Cin};
+    const FwdEpi epi{bias, out, Cout, relu};
+    switch (Cout) {
+        case 32: return launch_fwd_tc<32, 4, 2>(la, lb, epi, s);
+        case 64: return launch_fwd_tc<64, 4, 2>(la, lb, epi, s);
+        case 128: return launch_fwd_tc<128, 4, 2>(la, lb, epi, s);
+        case 256: return launch_fwd_tc<256, 4, 2>(la, lb, epi, s);
+        default: break;
+    }
     if (Cout <= 32) return launch_fwd<128, 32>(la, lb, bias, out, relu, s);
     if (Cout <= 64) return launch_fwd<128, 64>(la, lb, bias, out, relu, s);
     return launch_fwd<128, 128>(la, lb, bias, out, relu, s);
@@ -434,8 +598,26 @@ cudaError_t conv_forward(const __nv_bfloat16 *in, const __nv_bfloat16 *lo, int C
 
 cudaError_t conv_backward_data(const __nv_bfloat16 *gz, int B, int H, int W, int Cout, const __nv_bfloat16 *w, int Cin,
                                const __nv_bfloat16 *act, __nv_bfloat16 *din, __nv_bfloat16 *din2, int split,
-                               cudaStream_t s) {
+                               __nv_bfloat16 *wt_scratch, cudaStream_t s) {
     ConvInLoader la{{B, H, W}, gz, nullptr, Cout, 0, B * H * W, 9 * Cout, 1};
+    if (wt_scratch && Cin % 32 == 0 && split % 16 == 0) {
+        const long long nw = (long long)Cout * 9 * Cin;
+        k_transpose_dgrad<<<grid_for(nw), 256, 0, s>>>(w, wt_scratch, Cout, Cin);
+        const cudaError_t e = conv_dgrad_tma(gz, B, H, W, Cout, wt_scratch, Cin, act, din, din2, split, s);
+        if (e != cudaErrorNotSupported) return e;
+        const WeightKLoader lt{wt_scratch, Cin, 9 * Cout};
+        const DgradEpi epi{act, din, din2, split, Cin};
+        switch (Cin) {
+            case 32: return launch_dgrad_tc<32, 4, 2>(la, lt, epi, s);
+            case 64: return launch_dgrad_tc<64, 4, 2>(la, lt, epi, s);
+            case 96: return launch_dgrad_tc<96, 4, 2>(la, lt, epi, s);
+            case 128: return launch_dgrad_tc<128, 4, 2>(la, lt, epi, s);
+            case 192: return launch_dgrad_tc<192, 4, 2>(la, lt, epi, s);
+            case 256: return launch_dgrad_tc<256, 4, 2>(la, lt, epi, s);
+            case 384: return launch_dgrad_tc<192, 4, 2>(la, lt, epi, s);
+            default: break;
+        }
+    }
     WeightNLoader lb{w, Cout, Cin, 9 * Cout};
     if (Cin <= 32) return launch_dgrad<128, 32>(la, lb, act, din, din2, split, s);
     if (Cin <= 64) return launch_dgrad<128, 64>(la, lb, act, din, din2, split, s);
@@ -470,7 +652,19 @@ cudaError_t pack_input(const float *f, const uint8_t *mask, __nv_bfloat16 *x, lo
 }
 
 cudaError_t pool(const __nv_bfloat16 *in, __nv_bfloat16 *out, int B, int H, int W, int C, cudaStream_t s) {
-    k_pool<<<grid_for((long long)B * H * W * C / 4), 256, 0, s>>>(in, out, B, H, W, C);
+    k_pool<<<grid_for((long long)B * H * W * C / 32), 256, 0, s>>>(in, out, B, H, W, C);
+    return cudaGetLastError();
+}
+
+cudaError_t upcat(const __nv_bfloat16 *lo, int C1, const __nv_bfloat16 *skip, int Cs, __nv_bfloat16 *out, int B, int H,
+                  int W, cudaStream_t s) {
+    k_upcat<<<grid_for((long long)B * H * W * (C1 + Cs) / 8), 256, 0, s>>>(lo, C1, skip, Cs, out, B, H, W);
+    return cudaGetLastError();
+}
+
+cudaError_t conv0_direct(const float *f, const uint8_t *mask, const __nv_bfloat16 *w, const float *bias,
+                         __nv_bfloat16 *out, int B, int H, int W, cudaStream_t s) {
+    k_conv0<<<grid_for((long long)B * H * W), 256, 0, s>>>(f, mask, w, bias, out, B, H, W);
     return cudaGetLastError();
 }
 

@@ -16,10 +16,39 @@ cudaError_t conv_forward(const __nv_bfloat16 *in, const __nv_bfloat16 *lo, int C
                          cudaStream_t s);
 // Gradient w.r.t. the input from the pre-activation gradient gz [P][Cout];
 // channels < split go to din (multiplied by act > 0 when act != null),
-// channels >= split to din2.
+// channels >= split to din2. wt_scratch (Cout*9*Cin elements) receives the
+// rearranged weights of the tensor-core path.
 cudaError_t conv_backward_data(const __nv_bfloat16 *gz, int B, int H, int W, int Cout, const __nv_bfloat16 *w, int Cin,
                                const __nv_bfloat16 *act, __nv_bfloat16 *din, __nv_bfloat16 *din2, int split,
-                               cudaStream_t s);
+                               __nv_bfloat16 *wt_scratch, cudaStream_t s);
+// 1 in *host_flag if a tensor-core convolution gave up on a wait (never
+// expected); reset clears it. Synchronous.
+cudaError_t tc_fault(int *host_flag, bool reset);
+
+// The network's 1x1 head and input skip, fused into the last convolution:
+// y[p] = f[p] (mask[p] != 0) + hb + sum_c hw[c] d[p][c].
+struct HeadArgs {
+    const float *hw, *hb, *f;
+    const uint8_t *mask;
+    float *y;
+};
+// TMA tensor-core paths (conv_tma.cu); cudaErrorNotSupported when the shape
+// is outside them (tiles of 128 pixels of one image, channel counts in
+// multiples of 32), and the caller uses the general kernels.
+cudaError_t conv_forward_tma(const __nv_bfloat16 *in, int B, int H, int W, int Cin, const __nv_bfloat16 *w,
+                             const float *bias, int Cout, int relu, __nv_bfloat16 *out, const HeadArgs *head,
+                             cudaStream_t s);
+cudaError_t conv_dgrad_tma(const __nv_bfloat16 *gz, int B, int H, int W, int Cout, const __nv_bfloat16 *wt, int Cin,
+                           const __nv_bfloat16 *act, __nv_bfloat16 *din, __nv_bfloat16 *din2, int split,
+                           cudaStream_t s);
+cudaError_t tma_fault(int *host_flag, bool reset);
+// out[p] = [nearest-upsample(lo) (C1 channels), skip (Cs channels)].
+cudaError_t upcat(const __nv_bfloat16 *lo, int C1, const __nv_bfloat16 *skip, int Cs, __nv_bfloat16 *out, int B, int H,
+                  int W, cudaStream_t s);
+// First layer straight from the image: out = relu(conv3x3([bf16(f m), m]) + b)
+// with w the layer's bf16 weights [32][9][8] (input channels 0 and 1 used).
+cudaError_t conv0_direct(const float *f, const uint8_t *mask, const __nv_bfloat16 *w, const float *bias,
+                         __nv_bfloat16 *out, int B, int H, int W, cudaStream_t s);
 // dw[Cout][9*Cin] += weight gradient (FP32, atomically accumulated).
 cudaError_t conv_backward_weight(const __nv_bfloat16 *gz, int B, int H, int W, int Cout, const __nv_bfloat16 *in,
                                  const __nv_bfloat16 *lo, int C1, int Cin, float *dw, cudaStream_t s);

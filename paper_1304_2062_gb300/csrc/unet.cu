@@ -55,7 +55,9 @@ struct se2n_unet {
     __nv_bfloat16 *arena = nullptr;
     __nv_bfloat16 *x0, *a[4], *e[4], *pl[4], *c[3], *d[3];
     __nv_bfloat16 *gd[3], *gc[3], *gup[3], *gskip[3], *ge[4], *ga[4], *gp[4];
+    __nv_bfloat16 *cat[3];  // decoder inputs [up(below), skip], materialised
     float *out = nullptr, *target = nullptr, *loss = nullptr, *resid = nullptr;
+    __nv_bfloat16 *wt = nullptr;  // one layer's weights rearranged for the data gradient
 };
 
 namespace {
@@ -71,6 +73,14 @@ se2n_status cuda_st(cudaError_t e) {
         if (_s != SE2N_OK) return _s;          \
     } while (0)
 #define TRYC(expr) TRY(cuda_st(expr))
+
+// A tensor-core convolution that gave up on a bounded wait (never expected)
+// is reported by the next synchronous call as SE2N_ECUDA.
+se2n_status check_tc() {
+    int f = 0;
+    TRYC(se2n::nn::tc_fault(&f, true));
+    return f ? SE2N_ECUDA : SE2N_OK;
+}
 
 long long level_pixels(const se2n_unet *u, int count, int level) {
     return (long long)count * (u->H >> level) * (u->W >> level);
@@ -92,16 +102,16 @@ se2n_status forward(se2n_unet *u, const float *f, const uint8_t *mask, int n) {
     const int H = u->H, W = u->W;
     auto Wt = [&](int l) { return u->pb + u->w_off[l]; };
     auto Bi = [&](int l) { return u->p + u->b_off[l]; };
-    TRYC(pack_input(f, mask, u->x0, (long long)n * H * W, s));
-    const __nv_bfloat16 *in = u->x0;
     for (int l = 0; l < 4; ++l) {
         const int Hl = H >> l, Wl = W >> l;
         const LayerSpec &A = kLayers[2 * l], &Bb = kLayers[2 * l + 1];
-        if (l > 0) {
+        if (l == 0) {
+            // the first layer reads the image and mask directly (2 meaningful input channels)
+            TRYC(conv0_direct(f, mask, Wt(0), Bi(0), u->a[0], n, H, W, s));
+        } else {
             TRYC(pool(u->e[l - 1], u->pl[l], n, H >> (l - 1), W >> (l - 1), kLayers[2 * l - 1].cout, s));
-            in = u->pl[l];
+            TRYC(conv_forward(u->pl[l], nullptr, 0, n, Hl, Wl, A.cin, Wt(2 * l), Bi(2 * l), A.cout, 1, u->a[l], s));
         }
-        TRYC(conv_forward(in, nullptr, 0, n, Hl, Wl, A.cin, Wt(2 * l), Bi(2 * l), A.cout, 1, u->a[l], s));
         TRYC(conv_forward(u->a[l], nullptr, 0, n, Hl, Wl, Bb.cin, Wt(2 * l + 1), Bi(2 * l + 1), Bb.cout, 1, u->e[l], s));
     }
     // decoder levels 2, 1, 0 (layer indices 8..13)
@@ -111,21 +121,35 @@ se2n_status forward(se2n_unet *u, const float *f, const uint8_t *mask, int n) {
         const int la = 8 + 2 * k, lb = 9 + 2 * k;
         const LayerSpec &A = kLayers[la], &Bb = kLayers[lb];
         const int Hl = H >> level, Wl = W >> level;
-        TRYC(conv_forward(u->e[level], below, A.lo_ch, n, Hl, Wl, A.cin, Wt(la), Bi(la), A.cout, 1, u->c[k], s));
+        // the concatenation [up(below), skip] is written out once, so that the
+        // convolution reads one NHWC tensor with tensor-memory-access boxes
+        TRYC(upcat(below, A.lo_ch, u->e[level], A.cin - A.lo_ch, u->cat[k], n, Hl, Wl, s));
+        TRYC(conv_forward(u->cat[k], nullptr, 0, n, Hl, Wl, A.cin, Wt(la), Bi(la), A.cout, 1, u->c[k], s));
+        if (k == 2) {
+            // last convolution with the head and the input skip fused, when the tile shape allows
+            const HeadArgs h{u->p + u->hw_off, u->p + u->hb_off, f, mask, u->out};
+            const cudaError_t e =
+                conv_forward_tma(u->c[k], n, Hl, Wl, Bb.cin, Wt(lb), Bi(lb), Bb.cout, 1, u->d[k], &h, s);
+            if (e == cudaSuccess) break;
+            if (e != cudaErrorNotSupported) return cuda_st(e);
+        }
         TRYC(conv_forward(u->c[k], nullptr, 0, n, Hl, Wl, Bb.cin, Wt(lb), Bi(lb), Bb.cout, 1, u->d[k], s));
         below = u->d[k];
+        if (k == 2)
+            TRYC(head(u->d[2], u->p + u->hw_off, u->p + u->hb_off, f, mask, u->out, (long long)n * H * W, 32, s));
     }
-    TRYC(head(u->d[2], u->p + u->hw_off, u->p + u->hb_off, f, mask, u->out, (long long)n * H * W, 32, s));
     return SE2N_OK;
 }
 
-se2n_status backward(se2n_unet *u, int n) {
+se2n_status backward(se2n_unet *u, const float *f, const uint8_t *mask, int n) {
     using namespace se2n::nn;
     cudaStream_t s = u->stream;
     const int H = u->H, W = u->W;
     auto Wt = [&](int l) { return u->pb + u->w_off[l]; };
     auto dW = [&](int l) { return u->g + u->w_off[l]; };
     auto dB = [&](int l) { return u->g + u->b_off[l]; };
+    // the first layer's input as the weight gradient reads it (8 channels: f m, m, zeros)
+    TRYC(pack_input(f, mask, u->x0, (long long)n * H * W, s));
     TRYC(cudaMemsetAsync(u->g, 0, sizeof(float) * u->n_params, s));
     TRYC(cudaMemsetAsync(u->loss, 0, sizeof(float), s));
     TRYC(loss_head_backward(u->out, u->target, u->d[2], u->p + u->hw_off, u->gd[2], u->g + u->hw_off,
@@ -137,16 +161,15 @@ se2n_status backward(se2n_unet *u, int n) {
         const LayerSpec &A = kLayers[la], &Bb = kLayers[lb];
         const int Hl = H >> level, Wl = W >> level;
         const long long P = level_pixels(u, n, level);
-        const __nv_bfloat16 *below = (k == 0) ? u->e[3] : u->d[k - 1];
         // second conv: c[k] -> d[k]
         TRYC(conv_backward_weight(u->gd[k], n, Hl, Wl, Bb.cout, u->c[k], nullptr, 0, Bb.cin, dW(lb), s));
         TRYC(colsum(u->gd[k], P, Bb.cout, dB(lb), s));
-        TRYC(conv_backward_data(u->gd[k], n, Hl, Wl, Bb.cout, Wt(lb), Bb.cin, u->c[k], u->gc[k], nullptr, Bb.cin, s));
+        TRYC(conv_backward_data(u->gd[k], n, Hl, Wl, Bb.cout, Wt(lb), Bb.cin, u->c[k], u->gc[k], nullptr, Bb.cin, u->wt, s));
         // first conv: [up(below), e[level]] -> c[k]
-        TRYC(conv_backward_weight(u->gc[k], n, Hl, Wl, A.cout, u->e[level], below, A.lo_ch, A.cin, dW(la), s));
+        TRYC(conv_backward_weight(u->gc[k], n, Hl, Wl, A.cout, u->cat[k], nullptr, 0, A.cin, dW(la), s));
         TRYC(colsum(u->gc[k], P, A.cout, dB(la), s));
         TRYC(conv_backward_data(u->gc[k], n, Hl, Wl, A.cout, Wt(la), A.cin, nullptr, u->gup[k], u->gskip[k],
-                                A.lo_ch, s));
+                                A.lo_ch, u->wt, s));
         // gradient into the tensor below (half resolution), through the upsampling
         if (k > 0) {
             TRYC(up_backward_mask(u->gup[k], u->d[k - 1], u->gd[k - 1], n, Hl / 2, Wl / 2, A.lo_ch, s));
@@ -167,12 +190,11 @@ se2n_status backward(se2n_unet *u, int n) {
         TRYC(conv_backward_weight(u->ge[l], n, Hl, Wl, Bb.cout, u->a[l], nullptr, 0, Bb.cin, dW(2 * l + 1), s));
         TRYC(colsum(u->ge[l], P, Bb.cout, dB(2 * l + 1), s));
         TRYC(conv_backward_data(u->ge[l], n, Hl, Wl, Bb.cout, Wt(2 * l + 1), Bb.cin, u->a[l], u->ga[l], nullptr,
-                                Bb.cin, s));
+                                Bb.cin, u->wt, s));
         TRYC(conv_backward_weight(u->ga[l], n, Hl, Wl, A.cout, in, nullptr, 0, A.cin, dW(2 * l), s));
         TRYC(colsum(u->ga[l], P, A.cout, dB(2 * l), s));
         if (l > 0) {
-            TRYC(conv_backward_data(u->ga[l], n, Hl, Wl, A.cout, Wt(2 * l), A.cin, nullptr, u->gp[l], nullptr, A.cin,
-                                    s));
+            TRYC(conv_backward_data(u->ga[l], n, Hl, Wl, A.cout, Wt(2 * l), A.cin, nullptr, u->gp[l], nullptr, A.cin, u->wt, s));
         }
     }
     return SE2N_OK;
@@ -234,6 +256,7 @@ se2n_status se2n_unet_create(se2n_unet **out, int batch, int H, int W, void *str
         bufs.push_back({&u->gd[k], P(level) * A.cout});
         bufs.push_back({&u->gup[k], P(level) * A.lo_ch});
         bufs.push_back({&u->gskip[k], P(level) * (A.cin - A.lo_ch)});
+        bufs.push_back({&u->cat[k], P(level) * A.cin});
     }
     long long total = 0;
     for (auto &b : bufs) total += (b.second + 127) / 128 * 128;
@@ -254,6 +277,12 @@ se2n_status se2n_unet_create(se2n_unet **out, int batch, int H, int W, void *str
     if (e == cudaSuccess) e = cudaMalloc(&u->target, sizeof(float) * P0);
     if (e == cudaSuccess) e = cudaMalloc(&u->loss, 256);
     if (e == cudaSuccess) e = cudaMalloc(&u->resid, sizeof(float) * batch);
+    size_t wmax = 0;
+    for (int l = 0; l < 14; ++l) {
+        const size_t nw = (size_t)kLayers[l].cout * 9 * kLayers[l].cin;
+        if (nw > wmax) wmax = nw;
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&u->wt, sizeof(__nv_bfloat16) * wmax);
     if (e == cudaSuccess) e = cudaMemsetAsync(u->p, 0, sizeof(float) * np, u->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(u->m, 0, sizeof(float) * np, u->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(u->v, 0, sizeof(float) * np, u->stream);
@@ -270,6 +299,7 @@ se2n_status se2n_unet_create(se2n_unet **out, int batch, int H, int W, void *str
         cudaFree(u->target);
         cudaFree(u->loss);
         cudaFree(u->resid);
+        cudaFree(u->wt);
         delete u;
         return cuda_st(e);
     }
@@ -290,6 +320,7 @@ se2n_status se2n_unet_destroy(se2n_unet *u) {
     cudaFree(u->target);
     cudaFree(u->loss);
     cudaFree(u->resid);
+    cudaFree(u->wt);
     delete u;
     return SE2N_OK;
 }
@@ -313,13 +344,15 @@ se2n_status se2n_unet_set_params(se2n_unet *u, const float *host) {
 se2n_status se2n_unet_get_params(se2n_unet *u, float *host) {
     if (!u || !host) return SE2N_EINVAL;
     TRYC(cudaMemcpyAsync(host, u->p, sizeof(float) * u->n_params, cudaMemcpyDeviceToHost, u->stream));
-    return cuda_st(cudaStreamSynchronize(u->stream));
+    TRYC(cudaStreamSynchronize(u->stream));
+    return check_tc();
 }
 
 se2n_status se2n_unet_get_grads(se2n_unet *u, float *host) {
     if (!u || !host) return SE2N_EINVAL;
     TRYC(cudaMemcpyAsync(host, u->g, sizeof(float) * u->n_params, cudaMemcpyDeviceToHost, u->stream));
-    return cuda_st(cudaStreamSynchronize(u->stream));
+    TRYC(cudaStreamSynchronize(u->stream));
+    return check_tc();
 }
 
 se2n_status se2n_unet_init(se2n_unet *u, unsigned long long seed) {
@@ -357,7 +390,7 @@ se2n_status se2n_unet_backward(se2n_unet *u, const float *f, const uint8_t *mask
     TRYC(cudaMemcpyAsync(u->target, target, sizeof(float) * count * u->H * u->W, cudaMemcpyDeviceToDevice,
                          u->stream));
     TRY(forward(u, f, mask, count));
-    TRY(backward(u, count));
+    TRY(backward(u, f, mask, count));
     if (loss_device) TRYC(cudaMemcpyAsync(loss_device, u->loss, sizeof(float), cudaMemcpyDeviceToDevice, u->stream));
     return SE2N_OK;
 }
@@ -387,6 +420,7 @@ se2n_status se2n_surrogate_inpaint(se2n_unet *u, se2n_plan *plan, const se2n_par
     std::vector<float> r(count);
     TRYC(cudaMemcpyAsync(r.data(), u->resid, sizeof(float) * count, cudaMemcpyDeviceToHost, u->stream));
     TRYC(cudaStreamSynchronize(u->stream));
+    TRY(check_tc());
     int nf = 0;
     for (int i = 0; i < count; ++i) {
         if (residual_host) residual_host[i] = r[i];

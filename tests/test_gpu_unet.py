@@ -60,7 +60,7 @@ def _rel(a, b):
     return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-30))
 
 
-@pytest.mark.parametrize("B,H,W", [(2, 16, 16), (1, 24, 40)])
+@pytest.mark.parametrize("B,H,W", [(2, 16, 16), (1, 24, 40), (1, 64, 128), (2, 32, 64)])
 def test_forward_and_gradients_match_oracle(B, H, W):
     p32 = ou.he_params(11).astype(np.float32)
     f, mask, target = _inputs(B, H, W, 5)
