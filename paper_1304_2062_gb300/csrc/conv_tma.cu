@@ -33,7 +33,7 @@ __device__ __forceinline__ void store16(__nv_bfloat16 *dst, const float (&w)[16]
     d4[1] = make_uint4(p[4], p[5], p[6], p[7]);
 }
 
-// out[m][n..n+15] = relu?(v + bias) as bf16.
+// out[m][n..n+15] = relu?(v + bias) as bf16; pixel m's channels at out + m * N.
 struct FwdEpi {
     const float *bias;
     __nv_bfloat16 *out;
@@ -191,6 +191,66 @@ cudaError_t launch(const __nv_bfloat16 *A, int B, int H, int W, int C, const __n
     return cudaGetLastError();
 }
 
+// Narrow layers: 16 x 8 tiles, halo boxes, weights resident in shared memory.
+template <int BN, int CK, class EPI>
+cudaError_t launch_halo(const __nv_bfloat16 *A, int B, int H, int W, int C, const __nv_bfloat16 *wmat, int N, int flip,
+                        const EPI &epi, cudaStream_t s) {
+    using Cf = tma::HaloCfg<BN, CK>;
+    if (W % tma::HBW || H % tma::HBH || C % CK || N != BN) return cudaErrorNotSupported;
+    const int nblk = 9 * (C / CK);
+    const int wbytes = nblk * Cf::BBLK;
+    int S = (Cf::SMEM_BUDGET - wbytes) / Cf::A_BYTES;
+    if (S > 8) S = 8;
+    if (S < 3) return cudaErrorNotSupported;
+    auto enc = encoder();
+    const int nsm = sm_count();
+    int *err = fault_ptr();
+    if (!enc || nsm <= 0 || !err) return cudaErrorNotSupported;
+    CUtensorMap ma, mb;
+    {
+        const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+        const cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2, (cuuint64_t)H * W * C * 2};
+        const cuuint32_t box[4] = {(cuuint32_t)CK, (cuuint32_t)tma::HBW, (cuuint32_t)(tma::HBH + 2), 1};
+        const cuuint32_t es[4] = {1, 1, 1, 1};
+        if (enc(&ma, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)A, dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CK == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    {
+        const cuuint64_t dims[2] = {(cuuint64_t)9 * C, (cuuint64_t)N};
+        const cuuint64_t strides[1] = {(cuuint64_t)9 * C * 2};
+        const cuuint32_t box[2] = {(cuuint32_t)CK, (cuuint32_t)BN};
+        const cuuint32_t es[2] = {1, 1};
+        if (enc(&mb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)wmat, dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CK == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    tma::ConvGeo g;
+    g.B = B;
+    g.H = H;
+    g.W = W;
+    g.C = C;
+    g.bw = tma::HBW;
+    g.bh = tma::HBH;
+    g.tiles_x = W / tma::HBW;
+    g.tiles_y = H / tma::HBH;
+    g.mtiles = B * g.tiles_x * g.tiles_y;
+    g.ntiles = 1;
+    g.tiles = g.mtiles;
+    g.nchunk = C / CK;
+    g.KB = 3 * g.nchunk;
+    g.flip = flip;
+    const int smem = 1024 + wbytes + S * Cf::A_BYTES + 256;
+    auto *fn = &tma::k_conv_halo<BN, CK, EPI>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const int grid = g.tiles < nsm ? g.tiles : nsm;
+    fn<<<grid, 192, smem, s>>>(ma, mb, g, epi, S, err);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 namespace se2n {
@@ -206,16 +266,29 @@ cudaError_t tma_fault(int *host_flag, bool reset) {
 }
 
 cudaError_t conv_forward_tma(const __nv_bfloat16 *in, int B, int H, int W, int Cin, const __nv_bfloat16 *w,
-                             const float *bias, int Cout, int relu, __nv_bfloat16 *out, const HeadArgs *head,
+                             const float *bias, int Cout, int relu, __nv_bfloat16 *out, int ldo, const HeadArgs *head,
                              cudaStream_t s) {
     const bool ck64 = Cin % 64 == 0;
     if (head) {
-        if (Cout != 32 || !relu) return cudaErrorNotSupported;
+        if (Cout != 32 || !relu || ldo != 32) return cudaErrorNotSupported;
         const HeadEpi epi{bias, out, head->hw, head->hb, head->f, head->mask, head->y};
+        cudaError_t e = ck64 ? launch_halo<32, 64>(in, B, H, W, Cin, w, Cout, 0, epi, s)
+                             : launch_halo<32, 32>(in, B, H, W, Cin, w, Cout, 0, epi, s);
+        if (e != cudaErrorNotSupported) return e;
         return ck64 ? launch<32, 64>(in, B, H, W, Cin, w, Cout, 0, epi, s)
                     : launch<32, 32>(in, B, H, W, Cin, w, Cout, 0, epi, s);
     }
-    const FwdEpi epi{bias, out, Cout, relu};
+    const FwdEpi epi{bias, out, ldo, relu};
+    if (Cout == 32 || Cout == 64) {
+        cudaError_t e;
+        if (Cout == 32)
+            e = ck64 ? launch_halo<32, 64>(in, B, H, W, Cin, w, Cout, 0, epi, s)
+                     : launch_halo<32, 32>(in, B, H, W, Cin, w, Cout, 0, epi, s);
+        else
+            e = ck64 ? launch_halo<64, 64>(in, B, H, W, Cin, w, Cout, 0, epi, s)
+                     : launch_halo<64, 32>(in, B, H, W, Cin, w, Cout, 0, epi, s);
+        if (e != cudaErrorNotSupported) return e;
+    }
     switch (Cout) {
         case 32: return ck64 ? launch<32, 64>(in, B, H, W, Cin, w, Cout, 0, epi, s)
                              : launch<32, 32>(in, B, H, W, Cin, w, Cout, 0, epi, s);
@@ -234,6 +307,18 @@ cudaError_t conv_dgrad_tma(const __nv_bfloat16 *gz, int B, int H, int W, int Cou
     const bool ck64 = Cout % 64 == 0;
     const DgradEpi epi{act, din, din2, split, Cin};
     // A = gz (Cout channels, taps mirrored), B = wt [Cin][9 Cout]
+    if (Cin == 32 || Cin == 64 || Cin == 96) {
+        cudaError_t e = cudaErrorNotSupported;
+        if (Cin == 32)
+            e = ck64 ? launch_halo<32, 64>(gz, B, H, W, Cout, wt, Cin, 1, epi, s)
+                     : launch_halo<32, 32>(gz, B, H, W, Cout, wt, Cin, 1, epi, s);
+        else if (Cin == 64)
+            e = ck64 ? launch_halo<64, 64>(gz, B, H, W, Cout, wt, Cin, 1, epi, s)
+                     : launch_halo<64, 32>(gz, B, H, W, Cout, wt, Cin, 1, epi, s);
+        else if (!ck64)
+            e = launch_halo<96, 32>(gz, B, H, W, Cout, wt, Cin, 1, epi, s);
+        if (e != cudaErrorNotSupported) return e;
+    }
     if (!ck64) {
         if (Cin == 32) return launch<32, 32>(gz, B, H, W, Cout, wt, Cin, 1, epi, s);
         if (Cin == 96) return launch<96, 32>(gz, B, H, W, Cout, wt, Cin, 1, epi, s);

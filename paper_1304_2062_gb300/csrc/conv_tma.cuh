@@ -280,6 +280,213 @@ __global__ void __launch_bounds__(192, 1)
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Narrow layers (BN <= 64): halo boxes and resident weights.
+//
+// Tiles are 16 x 8 pixels. For each channel block and each horizontal
+// offset sx in {-1, 0, 1} one TMA box brings the 16 x 10 pixels (rows
+// y0 - 1 .. y0 + 8) shifted by sx; the three vertical offsets sy are the
+// same box read from row (sy + 1) * 16, a whole number of swizzle atoms, so
+// one box feeds three taps (160 box rows instead of 3 x 128). All weights of
+// the layer (9 C x BN) are loaded into shared memory once per CTA, so the
+// K loop moves no weight rows at all.
+// ---------------------------------------------------------------------------
+
+constexpr int HBW = 16, HBH = 8;             // tile 16 x 8 pixels
+constexpr int HROWS = HBW * (HBH + 2);        // 160 box rows
+
+template <int BN, int CK>
+struct HaloCfg {
+    static_assert(BN % 16 == 0 && BN >= 16 && BN <= 128, "narrow layers");
+    static constexpr int A_BYTES = HROWS * CK * 2;
+    static constexpr int BBLK = BN * CK * 2;   // one (tap, channel block) of weights
+    static constexpr int ACC_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : 128;
+    static constexpr int TMEM_COLS = 2 * ACC_COLS;
+    static constexpr int SMEM_BUDGET = 196608;
+};
+
+template <int BN, int CK, class EPI>
+__global__ void __launch_bounds__(192, 1)
+    k_conv_halo(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, const ConvGeo g,
+                const EPI epi, int S, int *err) {
+    using Cf = HaloCfg<BN, CK>;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    const int nblk = 9 * g.nchunk;                       // resident weight blocks
+    const uint32_t wres = base;                          // nblk x BBLK
+    const uint32_t stages = wres + nblk * Cf::BBLK;      // S x A_BYTES
+    const uint32_t bar_w = stages + S * Cf::A_BYTES;
+    const uint32_t bar_full = bar_w + 8;
+    const uint32_t bar_empty = bar_full + 8 * S;
+    const uint32_t bar_afull = bar_empty + 8 * S;
+    const uint32_t bar_aempty = bar_afull + 16;
+    const uint32_t tmem_slot = bar_aempty + 16;
+    volatile int *abort = (volatile int *)(smem_raw + (tmem_slot + 4 - raw));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        *abort = *(volatile int *)err;
+        tc::mbar_init(bar_w, 1);
+        for (int s = 0; s < S; ++s) {
+            tc::mbar_init(bar_full + 8 * s, 1);
+            tc::mbar_init(bar_empty + 8 * s, 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            tc::mbar_init(bar_afull + 8 * a, 1);
+            tc::mbar_init(bar_aempty + 8 * a, 4);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"((uint64_t)&mapA) : "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"((uint64_t)&mapB) : "memory");
+    }
+    __syncthreads();
+    if (*abort) return;
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(tmem_slot),
+                     "r"((uint32_t)Cf::TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    uint32_t tmem_base;
+    asm volatile("ld.shared.u32 %0, [%1];\n" : "=r"(tmem_base) : "r"(tmem_slot));
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer ----------------
+            const int nt0 = blockIdx.x < g.tiles ? (blockIdx.x / g.mtiles) : 0;
+            // this CTA's tiles all have the same n tile when ntiles == 1 (the narrow layers)
+            arrive_expect_tx(bar_w, (uint32_t)(nblk * Cf::BBLK));
+            for (int tap = 0; tap < 9; ++tap)
+                for (int ch = 0; ch < g.nchunk; ++ch)
+                    tma_load_2d(wres + (tap * g.nchunk + ch) * Cf::BBLK, &mapB, tap * g.C + ch * CK, nt0 * BN, bar_w);
+            int s = 0;
+            uint32_t ph = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < g.tiles && ok; t += gridDim.x) {
+                int b, x0, y0, nt;
+                tile_origin(g, t, b, x0, y0, nt);
+                for (int ch = 0; ch < g.nchunk && ok; ++ch)
+                    for (int sxi = 0; sxi < 3; ++sxi) {
+                        if (!tc::mbar_wait(bar_empty + 8 * s, ph ^ 1u, abort)) {
+                            ok = false;
+                            break;
+                        }
+                        arrive_expect_tx(bar_full + 8 * s, Cf::A_BYTES);
+                        tma_load_4d(stages + s * Cf::A_BYTES, &mapA, ch * CK, x0 + sxi - 1, y0 - 1, b,
+                                    bar_full + 8 * s);
+                        if (++s == S) {
+                            s = 0;
+                            ph ^= 1u;
+                        }
+                    }
+            }
+            if (!ok) {
+                const long long t0 = clock64();
+                while (clock64() - t0 < 200000LL) {
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer ----------------
+            constexpr uint32_t IDESC = tc::idesc_bf16_f32<BN>();
+            int s = 0, acc = 0;
+            uint32_t ph = 0, aph = 0;
+            bool ok = tc::mbar_wait(bar_w, 0, abort);
+            uint32_t last_bar = 0, last_par = 0;
+            for (int t = blockIdx.x; t < g.tiles && ok; t += gridDim.x) {
+                if (!tc::mbar_wait(bar_aempty + 8 * acc, aph ^ 1u, abort)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const uint32_t d = tmem_base + (uint32_t)(acc * Cf::ACC_COLS);
+                bool first = true;
+                for (int ch = 0; ch < g.nchunk && ok; ++ch)
+                    for (int sxi = 0; sxi < 3; ++sxi) {
+                        if (!tc::mbar_wait(bar_full + 8 * s, ph, abort)) {
+                            ok = false;
+                            break;
+                        }
+                        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                        const uint32_t sa = stages + s * Cf::A_BYTES;
+#pragma unroll
+                        for (int syi = 0; syi < 3; ++syi) {
+                            // source offset (sy, sx) = (syi - 1, sxi - 1); the weight tap reads it
+                            const int tap = g.flip ? (2 - syi) * 3 + (2 - sxi) : syi * 3 + sxi;
+                            const uint32_t wa = wres + (tap * g.nchunk + ch) * Cf::BBLK;
+                            const uint32_t aa = sa + syi * HBW * CK * 2;
+#pragma unroll
+                            for (int kk = 0; kk < CK / 16; ++kk) {
+                                tc::mma_f16(d, sdesc<BN, CK>(aa + kk * 32), sdesc<BN, CK>(wa + kk * 32), IDESC,
+                                            first ? 0u : 1u);
+                                first = false;
+                            }
+                        }
+                        tc::mma_commit(bar_empty + 8 * s);
+                        last_bar = bar_empty + 8 * s;
+                        last_par = ph;
+                        if (++s == S) {
+                            s = 0;
+                            ph ^= 1u;
+                        }
+                    }
+                if (!ok) break;
+                tc::mma_commit(bar_afull + 8 * acc);
+                if (++acc == 2) {
+                    acc = 0;
+                    aph ^= 1u;
+                }
+            }
+            if (!ok && last_bar) tc::mbar_wait(last_bar, last_par, nullptr);
+        }
+    } else {
+        // ---------------- epilogue (warps 2..5) ----------------
+        const int q = warp & 3;
+        int acc = 0;
+        uint32_t aph = 0;
+        for (int t = blockIdx.x; t < g.tiles; t += gridDim.x) {
+            if (!tc::mbar_wait(bar_afull + 8 * acc, aph, abort)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            int b, x0, y0, nt;
+            tile_origin(g, t, b, x0, y0, nt);
+            const int r = q * 32 + lane;
+            const int y = y0 + r / HBW, x = x0 + r % HBW;
+            const int m = (b * g.H + y) * g.W + x;
+            const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * Cf::ACC_COLS);
+            float state = 0.0f;
+#pragma unroll 1
+            for (int j0 = 0; j0 < BN; j0 += 16) {
+                uint32_t v[16];
+                tc::tmem_ld16(taddr + (uint32_t)j0, v);
+                float f[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) f[i] = __uint_as_float(v[i]);
+                epi.store(m, nt * BN + j0, f, state);
+            }
+            epi.finish(m, state);
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            __syncwarp();
+            if (lane == 0) arrive(bar_aempty + 8 * acc);
+            if (++acc == 2) {
+                acc = 0;
+                aph ^= 1u;
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && *abort) atomicExch(err, 1);
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem_base),
+                     "r"((uint32_t)Cf::TMEM_COLS));
+    }
+}
+
 }  // namespace tma
 }  // namespace nn
 }  // namespace se2n

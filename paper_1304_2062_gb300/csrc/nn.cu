@@ -257,8 +257,8 @@ __global__ void k_pack_input(const float *f, const uint8_t *mask, __nv_bfloat16 
     }
 }
 
-// 2x2 average pooling, NHWC, 8 channels (16 bytes) per thread.
-__global__ void k_pool(const __nv_bfloat16 *in, __nv_bfloat16 *out, int B, int H, int W, int C) {
+// 2x2 average pooling, NHWC (input row stride ldi), 8 channels (16 bytes) per thread.
+__global__ void k_pool(const __nv_bfloat16 *in, int ldi, __nv_bfloat16 *out, int B, int H, int W, int C) {
     const int Ho = H / 2, Wo = W / 2, C8 = C / 8;
     const long long total = (long long)B * Ho * Wo * C8;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
@@ -268,9 +268,10 @@ __global__ void k_pool(const __nv_bfloat16 *in, __nv_bfloat16 *out, int B, int H
         t /= Wo;
         const int y = (int)(t % Ho);
         const int b = (int)(t / Ho);
-        const long long base = (((long long)b * H + 2 * y) * W + 2 * x) * C + c;
-        const uint4 q0 = *(const uint4 *)(in + base), q1 = *(const uint4 *)(in + base + C);
-        const uint4 q2 = *(const uint4 *)(in + base + (long long)W * C), q3 = *(const uint4 *)(in + base + (long long)W * C + C);
+        const long long base = (((long long)b * H + 2 * y) * W + 2 * x) * ldi + c;
+        const uint4 q0 = *(const uint4 *)(in + base), q1 = *(const uint4 *)(in + base + ldi);
+        const uint4 q2 = *(const uint4 *)(in + base + (long long)W * ldi);
+        const uint4 q3 = *(const uint4 *)(in + base + (long long)W * ldi + ldi);
         const __nv_bfloat16 *a = (const __nv_bfloat16 *)&q0, *b1 = (const __nv_bfloat16 *)&q1;
         const __nv_bfloat16 *c2 = (const __nv_bfloat16 *)&q2, *d3 = (const __nv_bfloat16 *)&q3;
         __align__(16) __nv_bfloat16 o[8];
@@ -284,68 +285,82 @@ __global__ void k_pool(const __nv_bfloat16 *in, __nv_bfloat16 *out, int B, int H
     }
 }
 
-// out[p] = [nearest-upsample(lo) (C1 channels), skip (Cs channels)], 16 bytes per thread.
-__global__ void k_upcat(const __nv_bfloat16 *lo, int C1, const __nv_bfloat16 *skip, int Cs, __nv_bfloat16 *out, int B,
-                        int H, int W) {
-    const int C = C1 + Cs, C8 = C / 8;
-    const long long total = (long long)B * H * W * C8;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C8) * 8;
-        const long long p = i / C8;
-        uint4 v;
-        if (c < C1) {
-            const int x = (int)(p % W);
-            const long long t = p / W;
-            const int y = (int)(t % H);
-            const long long b = t / H;
-            v = *(const uint4 *)(lo + ((b * (H / 2) + y / 2) * (W / 2) + x / 2) * C1 + c);
-        } else {
-            v = *(const uint4 *)(skip + p * Cs + (c - C1));
-        }
-        *(uint4 *)(out + p * C + c) = v;
+// Nearest upsampling into the first C1 channels of a wider tensor: one
+// block per output row (b, y), 16 bytes per thread.
+__global__ void k_upsample_into(const __nv_bfloat16 *lo, int C1, __nv_bfloat16 *out, int ldo, int H, int W) {
+    const int y = blockIdx.x % H;
+    const long long b = blockIdx.x / H;
+    const int C8 = C1 / 8, Wl = W / 2;
+    const __nv_bfloat16 *src = lo + ((b * (H / 2) + y / 2) * Wl) * C1;
+    __nv_bfloat16 *dst = out + ((b * H + y) * W) * (long long)ldo;
+    for (int i = threadIdx.x; i < W * C8; i += blockDim.x) {
+        const int x = i / C8, c = (i - x * C8) * 8;
+        *(uint4 *)(dst + (long long)x * ldo + c) = *(const uint4 *)(src + (x / 2) * C1 + c);
     }
 }
 
 // First convolution straight from the image: the input channels are
 // bf16(f m) and m (the other six are zero), so each of the 32 outputs is a
-// sum over 9 taps x 2 channels, done in FP32 on the CUDA cores.
+// sum over 9 taps x 2 channels, done in FP32 on the CUDA cores. A block
+// takes 32 x 8 pixel tiles; the tile and its 1-pixel halo of (bf16(f m), m)
+// are staged in shared memory with coalesced loads, and the weights sit
+// there as [tap][channel][4 outputs] float4 (one 16-byte load per 4 FMAs).
+constexpr int C0_TW = 32, C0_TH = 8;
 __global__ void __launch_bounds__(256) k_conv0(const float *f, const uint8_t *mask, const __nv_bfloat16 *w,
                                                const float *bias, __nv_bfloat16 *out, int B, int H, int W) {
-    __shared__ float sw[32][9][2];
+    __shared__ float4 sw[9][2][8];
     __shared__ float sb[32];
-    for (int i = threadIdx.x; i < 32 * 9 * 2; i += blockDim.x) {
-        const int co = i / 18, r = i % 18, tap = r / 2, ci = r % 2;
-        sw[co][tap][ci] = __bfloat162float(w[(co * 9 + tap) * 8 + ci]);
+    __shared__ float2 tile[C0_TH + 2][C0_TW + 2];
+    for (int i = threadIdx.x; i < 9 * 2 * 8; i += blockDim.x) {
+        const int tap = i / 16, ci = (i / 8) % 2, q = i % 8;
+        const __nv_bfloat16 *wq = w + tap * 8 + ci;  // w[co][tap][ci], 72 per output channel
+        sw[tap][ci][q] = make_float4(__bfloat162float(wq[(4 * q + 0) * 72]), __bfloat162float(wq[(4 * q + 1) * 72]),
+                                     __bfloat162float(wq[(4 * q + 2) * 72]), __bfloat162float(wq[(4 * q + 3) * 72]));
     }
     if (threadIdx.x < 32) sb[threadIdx.x] = bias[threadIdx.x];
-    __syncthreads();
-    const long long P = (long long)B * H * W;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(p % W);
-        const long long t = p / W;
-        const int y = (int)(t % H);
-        const long long b = t / H;
-        float v0[9], v1[9];
-#pragma unroll
-        for (int tap = 0; tap < 9; ++tap) {
-            const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
-            v0[tap] = v1[tap] = 0.0f;
+    const int tx = threadIdx.x % C0_TW, ty = threadIdx.x / C0_TW;
+    const int ntx = (W + C0_TW - 1) / C0_TW, nty = (H + C0_TH - 1) / C0_TH;
+    const long long ntiles = (long long)B * ntx * nty;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int bx = (int)(t % ntx);
+        const long long r = t / ntx;
+        const int by = (int)(r % nty);
+        const long long b = r / nty;
+        const int x0 = bx * C0_TW, y0 = by * C0_TH;
+        __syncthreads();  // the previous tile is consumed (and the tables are ready)
+        for (int i = threadIdx.x; i < (C0_TH + 2) * (C0_TW + 2); i += blockDim.x) {
+            const int ly = i / (C0_TW + 2), lx = i % (C0_TW + 2);
+            const int yy = y0 + ly - 1, xx = x0 + lx - 1;
+            float2 v = make_float2(0.0f, 0.0f);
             if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
                 const long long q = (b * H + yy) * W + xx;
                 const float m = mask[q] ? 1.0f : 0.0f;
-                v0[tap] = __bfloat162float(__float2bfloat16_rn(f[q] * m));
-                v1[tap] = m;
+                v = make_float2(__bfloat162float(__float2bfloat16_rn(f[q] * m)), m);
+            }
+            tile[ly][lx] = v;
+        }
+        __syncthreads();
+        const int x = x0 + tx, y = y0 + ty;
+        if (x >= W || y >= H) continue;
+        float acc[32];
+#pragma unroll
+        for (int co = 0; co < 32; ++co) acc[co] = 0.0f;
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+            const float2 v = tile[ty + tap / 3][tx + tap % 3];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float4 a = sw[tap][0][q], c = sw[tap][1][q];
+                acc[4 * q + 0] = fmaf(c.x, v.y, fmaf(a.x, v.x, acc[4 * q + 0]));
+                acc[4 * q + 1] = fmaf(c.y, v.y, fmaf(a.y, v.x, acc[4 * q + 1]));
+                acc[4 * q + 2] = fmaf(c.z, v.y, fmaf(a.z, v.x, acc[4 * q + 2]));
+                acc[4 * q + 3] = fmaf(c.w, v.y, fmaf(a.w, v.x, acc[4 * q + 3]));
             }
         }
         __align__(16) __nv_bfloat16 o[32];
 #pragma unroll
-        for (int co = 0; co < 32; ++co) {
-            float s = 0.0f;
-#pragma unroll
-            for (int tap = 0; tap < 9; ++tap) s = fmaf(sw[co][tap][1], v1[tap], fmaf(sw[co][tap][0], v0[tap], s));
-            o[co] = __float2bfloat16_rn(fmaxf(s + sb[co], 0.0f));
-        }
-        uint4 *dst = (uint4 *)(out + p * 32);
+        for (int co = 0; co < 32; ++co) o[co] = __float2bfloat16_rn(fmaxf(acc[co] + sb[co], 0.0f));
+        uint4 *dst = (uint4 *)(out + ((b * H + y) * W + x) * 32);
 #pragma unroll
         for (int k = 0; k < 4; ++k) dst[k] = ((const uint4 *)o)[k];
     }
@@ -353,7 +368,7 @@ __global__ void __launch_bounds__(256) k_conv0(const float *f, const uint8_t *ma
 
 // Gradient into an encoder output e: g_e = (pool_backward(g_pooled) + g_skip) * (e > 0).
 __global__ void k_pool_bwd_add_mask(const __nv_bfloat16 *gp, const __nv_bfloat16 *gskip, const __nv_bfloat16 *e,
-                                    __nv_bfloat16 *ge, int B, int H, int W, int C) {
+                                    int lde, __nv_bfloat16 *ge, int B, int H, int W, int C) {
     const long long total = (long long)B * H * W * C;
     const int Ho = H / 2, Wo = W / 2;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
@@ -365,7 +380,7 @@ __global__ void k_pool_bwd_add_mask(const __nv_bfloat16 *gp, const __nv_bfloat16
         const int b = (int)(t / H);
         float v = 0.25f * __bfloat162float(gp[(((long long)b * Ho + y / 2) * Wo + x / 2) * C + c]);
         if (gskip) v += __bfloat162float(gskip[i]);
-        if (!(__bfloat162float(e[i]) > 0.0f)) v = 0.0f;
+        if (!(__bfloat162float(e[(i / C) * lde + c]) > 0.0f)) v = 0.0f;
         ge[i] = __float2bfloat16_rn(v);
     }
 }
@@ -575,15 +590,15 @@ cudaError_t tc_fault(int *host_flag, bool reset) {
 }
 
 cudaError_t conv_forward(const __nv_bfloat16 *in, const __nv_bfloat16 *lo, int C1, int B, int H, int W, int Cin,
-                         const __nv_bfloat16 *w, const float *bias, int Cout, int relu, __nv_bfloat16 *out,
+                         const __nv_bfloat16 *w, const float *bias, int Cout, int relu, __nv_bfloat16 *out, int ldo,
                          cudaStream_t s) {
     if (!lo) {
-        const cudaError_t e = conv_forward_tma(in, B, H, W, Cin, w, bias, Cout, relu, out, nullptr, s);
+        const cudaError_t e = conv_forward_tma(in, B, H, W, Cin, w, bias, Cout, relu, out, ldo, nullptr, s);
         if (e != cudaErrorNotSupported) return e;
     }
     ConvInLoader la{{B, H, W}, in, lo, Cin, C1, B * H * W, 9 * Cin, 0};
     WeightKLoader lb{w, Cout, 9 * Cin};
-    const FwdEpi epi{bias, out, Cout, relu};
+    const FwdEpi epi{bias, out, ldo, relu};
     switch (Cout) {
         case 32: return launch_fwd_tc<32, 4, 2>(la, lb, epi, s);
         case 64: return launch_fwd_tc<64, 4, 2>(la, lb, epi, s);
@@ -591,6 +606,7 @@ cudaError_t conv_forward(const __nv_bfloat16 *in, const __nv_bfloat16 *lo, int C
         case 256: return launch_fwd_tc<256, 4, 2>(la, lb, epi, s);
         default: break;
     }
+    if (ldo != Cout) return cudaErrorNotSupported;
     if (Cout <= 32) return launch_fwd<128, 32>(la, lb, bias, out, relu, s);
     if (Cout <= 64) return launch_fwd<128, 64>(la, lb, bias, out, relu, s);
     return launch_fwd<128, 128>(la, lb, bias, out, relu, s);
@@ -651,26 +667,32 @@ cudaError_t pack_input(const float *f, const uint8_t *mask, __nv_bfloat16 *x, lo
     return cudaGetLastError();
 }
 
-cudaError_t pool(const __nv_bfloat16 *in, __nv_bfloat16 *out, int B, int H, int W, int C, cudaStream_t s) {
-    k_pool<<<grid_for((long long)B * H * W * C / 32), 256, 0, s>>>(in, out, B, H, W, C);
+cudaError_t pool(const __nv_bfloat16 *in, int ldi, __nv_bfloat16 *out, int B, int H, int W, int C, cudaStream_t s) {
+    k_pool<<<grid_for((long long)B * H * W * C / 32), 256, 0, s>>>(in, ldi, out, B, H, W, C);
     return cudaGetLastError();
 }
 
-cudaError_t upcat(const __nv_bfloat16 *lo, int C1, const __nv_bfloat16 *skip, int Cs, __nv_bfloat16 *out, int B, int H,
-                  int W, cudaStream_t s) {
-    k_upcat<<<grid_for((long long)B * H * W * (C1 + Cs) / 8), 256, 0, s>>>(lo, C1, skip, Cs, out, B, H, W);
+cudaError_t upsample_into(const __nv_bfloat16 *lo, int C1, __nv_bfloat16 *out, int ldo, int B, int H, int W,
+                          cudaStream_t s) {
+    k_upsample_into<<<B * H, 256, 0, s>>>(lo, C1, out, ldo, H, W);
     return cudaGetLastError();
 }
 
 cudaError_t conv0_direct(const float *f, const uint8_t *mask, const __nv_bfloat16 *w, const float *bias,
                          __nv_bfloat16 *out, int B, int H, int W, cudaStream_t s) {
-    k_conv0<<<grid_for((long long)B * H * W), 256, 0, s>>>(f, mask, w, bias, out, B, H, W);
+    // a few blocks per SM, each over many pixels: the weight table is built once per block
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int g = grid_for((long long)B * H * W);
+    if (nsm > 0 && g > 8 * nsm) g = 8 * nsm;
+    k_conv0<<<g, 256, 0, s>>>(f, mask, w, bias, out, B, H, W);
     return cudaGetLastError();
 }
 
-cudaError_t pool_backward_add_mask(const __nv_bfloat16 *gp, const __nv_bfloat16 *gskip, const __nv_bfloat16 *e,
+cudaError_t pool_backward_add_mask(const __nv_bfloat16 *gp, const __nv_bfloat16 *gskip, const __nv_bfloat16 *e, int lde,
                                    __nv_bfloat16 *ge, int B, int H, int W, int C, cudaStream_t s) {
-    k_pool_bwd_add_mask<<<grid_for((long long)B * H * W * C), 256, 0, s>>>(gp, gskip, e, ge, B, H, W, C);
+    k_pool_bwd_add_mask<<<grid_for((long long)B * H * W * C), 256, 0, s>>>(gp, gskip, e, lde, ge, B, H, W, C);
     return cudaGetLastError();
 }
 

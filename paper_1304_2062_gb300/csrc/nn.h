@@ -10,9 +10,10 @@ namespace nn {
 
 // 3x3 convolution, padding 1, NHWC bf16. The input is `in` (Cin channels),
 // or, when lo != null, the channel concatenation [nearest-upsample(lo) (C1
-// channels, half resolution), in (Cin - C1 channels)]. out = relu?(conv + bias).
+// channels, half resolution), in (Cin - C1 channels)]. out = relu?(conv + bias),
+// pixel p's Cout channels at out + p * ldo (ldo >= Cout, a multiple of 8).
 cudaError_t conv_forward(const __nv_bfloat16 *in, const __nv_bfloat16 *lo, int C1, int B, int H, int W, int Cin,
-                         const __nv_bfloat16 *w, const float *bias, int Cout, int relu, __nv_bfloat16 *out,
+                         const __nv_bfloat16 *w, const float *bias, int Cout, int relu, __nv_bfloat16 *out, int ldo,
                          cudaStream_t s);
 // Gradient w.r.t. the input from the pre-activation gradient gz [P][Cout];
 // channels < split go to din (multiplied by act > 0 when act != null),
@@ -36,15 +37,16 @@ struct HeadArgs {
 // is outside them (tiles of 128 pixels of one image, channel counts in
 // multiples of 32), and the caller uses the general kernels.
 cudaError_t conv_forward_tma(const __nv_bfloat16 *in, int B, int H, int W, int Cin, const __nv_bfloat16 *w,
-                             const float *bias, int Cout, int relu, __nv_bfloat16 *out, const HeadArgs *head,
+                             const float *bias, int Cout, int relu, __nv_bfloat16 *out, int ldo, const HeadArgs *head,
                              cudaStream_t s);
 cudaError_t conv_dgrad_tma(const __nv_bfloat16 *gz, int B, int H, int W, int Cout, const __nv_bfloat16 *wt, int Cin,
                            const __nv_bfloat16 *act, __nv_bfloat16 *din, __nv_bfloat16 *din2, int split,
                            cudaStream_t s);
 cudaError_t tma_fault(int *host_flag, bool reset);
-// out[p] = [nearest-upsample(lo) (C1 channels), skip (Cs channels)].
-cudaError_t upcat(const __nv_bfloat16 *lo, int C1, const __nv_bfloat16 *skip, int Cs, __nv_bfloat16 *out, int B, int H,
-                  int W, cudaStream_t s);
+// Channels 0..C1-1 of out (ldo channels per pixel, H x W) = nearest-upsample(lo)
+// (C1 channels, H/2 x W/2).
+cudaError_t upsample_into(const __nv_bfloat16 *lo, int C1, __nv_bfloat16 *out, int ldo, int B, int H, int W,
+                          cudaStream_t s);
 // First layer straight from the image: out = relu(conv3x3([bf16(f m), m]) + b)
 // with w the layer's bf16 weights [32][9][8] (input channels 0 and 1 used).
 cudaError_t conv0_direct(const float *f, const uint8_t *mask, const __nv_bfloat16 *w, const float *bias,
@@ -54,8 +56,10 @@ cudaError_t conv_backward_weight(const __nv_bfloat16 *gz, int B, int H, int W, i
                                  const __nv_bfloat16 *lo, int C1, int Cin, float *dw, cudaStream_t s);
 cudaError_t colsum(const __nv_bfloat16 *g, long long P, int C, float *db, cudaStream_t s);
 cudaError_t pack_input(const float *f, const uint8_t *mask, __nv_bfloat16 *x, long long P, cudaStream_t s);
-cudaError_t pool(const __nv_bfloat16 *in, __nv_bfloat16 *out, int B, int H, int W, int C, cudaStream_t s);
-cudaError_t pool_backward_add_mask(const __nv_bfloat16 *gp, const __nv_bfloat16 *gskip, const __nv_bfloat16 *e,
+// in: C channels per pixel at in + p * ldi; out dense (C per pixel).
+cudaError_t pool(const __nv_bfloat16 *in, int ldi, __nv_bfloat16 *out, int B, int H, int W, int C, cudaStream_t s);
+// e: C channels per pixel at e + p * lde.
+cudaError_t pool_backward_add_mask(const __nv_bfloat16 *gp, const __nv_bfloat16 *gskip, const __nv_bfloat16 *e, int lde,
                                    __nv_bfloat16 *ge, int B, int H, int W, int C, cudaStream_t s);
 cudaError_t up_backward_mask(const __nv_bfloat16 *gup, const __nv_bfloat16 *d, __nv_bfloat16 *gd, int B, int Hl,
                              int Wl, int C, cudaStream_t s);

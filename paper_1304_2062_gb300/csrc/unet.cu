@@ -55,7 +55,8 @@ struct se2n_unet {
     __nv_bfloat16 *arena = nullptr;
     __nv_bfloat16 *x0, *a[4], *e[4], *pl[4], *c[3], *d[3];
     __nv_bfloat16 *gd[3], *gc[3], *gup[3], *gskip[3], *ge[4], *ga[4], *gp[4];
-    __nv_bfloat16 *cat[3];  // decoder inputs [up(below), skip], materialised
+    __nv_bfloat16 *cat[3];  // decoder inputs [up(below), skip]; e[0..2] live inside them
+    int e_ld[4];            // channels per pixel of the tensor e[l] lives in
     float *out = nullptr, *target = nullptr, *loss = nullptr, *resid = nullptr;
     __nv_bfloat16 *wt = nullptr;  // one layer's weights rearranged for the data gradient
 };
@@ -109,10 +110,13 @@ se2n_status forward(se2n_unet *u, const float *f, const uint8_t *mask, int n) {
             // the first layer reads the image and mask directly (2 meaningful input channels)
             TRYC(conv0_direct(f, mask, Wt(0), Bi(0), u->a[0], n, H, W, s));
         } else {
-            TRYC(pool(u->e[l - 1], u->pl[l], n, H >> (l - 1), W >> (l - 1), kLayers[2 * l - 1].cout, s));
-            TRYC(conv_forward(u->pl[l], nullptr, 0, n, Hl, Wl, A.cin, Wt(2 * l), Bi(2 * l), A.cout, 1, u->a[l], s));
+            TRYC(pool(u->e[l - 1], u->e_ld[l - 1], u->pl[l], n, H >> (l - 1), W >> (l - 1), kLayers[2 * l - 1].cout, s));
+            TRYC(conv_forward(u->pl[l], nullptr, 0, n, Hl, Wl, A.cin, Wt(2 * l), Bi(2 * l), A.cout, 1, u->a[l], A.cout,
+                              s));
         }
-        TRYC(conv_forward(u->a[l], nullptr, 0, n, Hl, Wl, Bb.cin, Wt(2 * l + 1), Bi(2 * l + 1), Bb.cout, 1, u->e[l], s));
+        // e[l] (l < 3) is written straight into the skip channels of decoder level l's input
+        TRYC(conv_forward(u->a[l], nullptr, 0, n, Hl, Wl, Bb.cin, Wt(2 * l + 1), Bi(2 * l + 1), Bb.cout, 1, u->e[l],
+                          u->e_ld[l], s));
     }
     // decoder levels 2, 1, 0 (layer indices 8..13)
     const __nv_bfloat16 *below = u->e[3];
@@ -121,19 +125,19 @@ se2n_status forward(se2n_unet *u, const float *f, const uint8_t *mask, int n) {
         const int la = 8 + 2 * k, lb = 9 + 2 * k;
         const LayerSpec &A = kLayers[la], &Bb = kLayers[lb];
         const int Hl = H >> level, Wl = W >> level;
-        // the concatenation [up(below), skip] is written out once, so that the
-        // convolution reads one NHWC tensor with tensor-memory-access boxes
-        TRYC(upcat(below, A.lo_ch, u->e[level], A.cin - A.lo_ch, u->cat[k], n, Hl, Wl, s));
-        TRYC(conv_forward(u->cat[k], nullptr, 0, n, Hl, Wl, A.cin, Wt(la), Bi(la), A.cout, 1, u->c[k], s));
+        // the input [up(below), e[level]] is one NHWC tensor (read with TMA boxes):
+        // e[level] is already in it, the upsampled half is written here
+        TRYC(upsample_into(below, A.lo_ch, u->cat[k], A.cin, n, Hl, Wl, s));
+        TRYC(conv_forward(u->cat[k], nullptr, 0, n, Hl, Wl, A.cin, Wt(la), Bi(la), A.cout, 1, u->c[k], A.cout, s));
         if (k == 2) {
             // last convolution with the head and the input skip fused, when the tile shape allows
             const HeadArgs h{u->p + u->hw_off, u->p + u->hb_off, f, mask, u->out};
             const cudaError_t e =
-                conv_forward_tma(u->c[k], n, Hl, Wl, Bb.cin, Wt(lb), Bi(lb), Bb.cout, 1, u->d[k], &h, s);
+                conv_forward_tma(u->c[k], n, Hl, Wl, Bb.cin, Wt(lb), Bi(lb), Bb.cout, 1, u->d[k], Bb.cout, &h, s);
             if (e == cudaSuccess) break;
             if (e != cudaErrorNotSupported) return cuda_st(e);
         }
-        TRYC(conv_forward(u->c[k], nullptr, 0, n, Hl, Wl, Bb.cin, Wt(lb), Bi(lb), Bb.cout, 1, u->d[k], s));
+        TRYC(conv_forward(u->c[k], nullptr, 0, n, Hl, Wl, Bb.cin, Wt(lb), Bi(lb), Bb.cout, 1, u->d[k], Bb.cout, s));
         below = u->d[k];
         if (k == 2)
             TRYC(head(u->d[2], u->p + u->hw_off, u->p + u->hb_off, f, mask, u->out, (long long)n * H * W, 32, s));
@@ -184,7 +188,8 @@ se2n_status backward(se2n_unet *u, const float *f, const uint8_t *mask, int n) {
         const LayerSpec &A = kLayers[2 * l], &Bb = kLayers[2 * l + 1];
         if (l < 3) {
             // e[l] feeds the pool of level l+1 (gradient gp[l+1]) and the skip of decoder level l
-            TRYC(pool_backward_add_mask(u->gp[l + 1], u->gskip[2 - l], u->e[l], u->ge[l], n, Hl, Wl, Bb.cout, s));
+            TRYC(pool_backward_add_mask(u->gp[l + 1], u->gskip[2 - l], u->e[l], u->e_ld[l], u->ge[l], n, Hl, Wl,
+                                        Bb.cout, s));
         }
         const __nv_bfloat16 *in = (l == 0) ? u->x0 : u->pl[l];
         TRYC(conv_backward_weight(u->ge[l], n, Hl, Wl, Bb.cout, u->a[l], nullptr, 0, Bb.cin, dW(2 * l + 1), s));
@@ -241,7 +246,7 @@ se2n_status se2n_unet_create(se2n_unet **out, int batch, int H, int W, void *str
     bufs.push_back({&u->x0, P(0) * 8});
     for (int l = 0; l < 4; ++l) {
         bufs.push_back({&u->a[l], P(l) * kLayers[2 * l].cout});
-        bufs.push_back({&u->e[l], P(l) * kLayers[2 * l + 1].cout});
+        if (l == 3) bufs.push_back({&u->e[l], P(l) * kLayers[2 * l + 1].cout});
         bufs.push_back({&u->ga[l], P(l) * kLayers[2 * l].cout});
         bufs.push_back({&u->ge[l], P(l) * kLayers[2 * l + 1].cout});
         bufs.push_back({&u->pl[l], l > 0 ? P(l) * kLayers[2 * l - 1].cout : 8});
@@ -266,6 +271,14 @@ se2n_status se2n_unet_create(se2n_unet **out, int batch, int H, int W, void *str
         for (auto &b : bufs) {
             *b.first = u->arena + o;
             o += (b.second + 127) / 128 * 128;
+        }
+    // e[l], l < 3: the skip channels of decoder level l's input (after the upsampled ones)
+    for (int l = 0; l < 4; ++l) u->e_ld[l] = kLayers[2 * l + 1].cout;
+    if (e == cudaSuccess)
+        for (int l = 0; l < 3; ++l) {
+            const LayerSpec &D = kLayers[8 + 2 * (2 - l)];
+            u->e[l] = u->cat[2 - l] + D.lo_ch;
+            u->e_ld[l] = D.cin;
         }
     const size_t np = (size_t)u->n_params;
     if (e == cudaSuccess) e = cudaMalloc(&u->p, sizeof(float) * np);
