@@ -33,21 +33,26 @@ __device__ __forceinline__ void store16(__nv_bfloat16 *dst, const float (&w)[16]
     d4[1] = make_uint4(p[4], p[5], p[6], p[7]);
 }
 
-// out[m][n..n+15] = relu?(v + bias) as bf16; pixel m's channels at out + m * N.
+// out[m][n..n+15] = relu?(v + bias) as bf16; pixel m's channels at out + m * N;
+// nb bias values (the output channels).
 struct FwdEpi {
     const float *bias;
     __nv_bfloat16 *out;
-    int N, relu;
-    __device__ __forceinline__ void store(int m, int n, const float (&v)[16], float &) const {
+    int N, relu, nb;
+    static constexpr int SMEM_FLOATS = 256;
+    __device__ __forceinline__ void prepare(float *sm, int i, int n) const {
+        for (int k = i; k < nb; k += n) sm[k] = bias[k];
+    }
+    __device__ __forceinline__ void store(int m, int n, const float (&v)[16], float &, const float *sm) const {
         float w[16];
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
-            w[q] = v[q] + bias[n + q];
+            w[q] = v[q] + sm[n + q];
             if (relu) w[q] = fmaxf(w[q], 0.0f);
         }
         store16(out + (long long)m * N + n, w);
     }
-    __device__ __forceinline__ void finish(int, float) const {}
+    __device__ __forceinline__ void finish(int, float, const float *) const {}
 };
 
 // The last convolution (32 channels, ReLU) with the 1x1 head and the input
@@ -59,18 +64,24 @@ struct HeadEpi {
     const float *hw, *hb, *f;
     const uint8_t *mask;
     float *y;
-    __device__ __forceinline__ void store(int m, int n, const float (&v)[16], float &st) const {
+    static constexpr int SMEM_FLOATS = 65;  // bias[32], hw[32], hb
+    __device__ __forceinline__ void prepare(float *sm, int i, int n) const {
+        for (int k = i; k < 65; k += n) sm[k] = k < 32 ? bias[k] : k < 64 ? hw[k - 32] : hb[0];
+    }
+    __device__ __forceinline__ void store(int m, int n, const float (&v)[16], float &st, const float *sm) const {
         float w[16];
-        if (n == 0) st = hb[0];
+        if (n == 0) st = sm[64];
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
-            w[q] = fmaxf(v[q] + bias[n + q], 0.0f);
+            w[q] = fmaxf(v[q] + sm[n + q], 0.0f);
             w[q] = __bfloat162float(__float2bfloat16_rn(w[q]));
-            st = fmaf(hw[n + q], w[q], st);
+            st = fmaf(sm[32 + n + q], w[q], st);
         }
         store16(out + (long long)m * 32 + n, w);
     }
-    __device__ __forceinline__ void finish(int m, float st) const { y[m] = (mask[m] ? f[m] : 0.0f) + st; }
+    __device__ __forceinline__ void finish(int m, float st, const float *) const {
+        y[m] = (mask[m] ? f[m] : 0.0f) + st;
+    }
 };
 
 // Data gradient: columns < split go to din (times (act > 0) when act is
@@ -79,7 +90,9 @@ struct DgradEpi {
     const __nv_bfloat16 *act;
     __nv_bfloat16 *din, *din2;
     int split, N;
-    __device__ __forceinline__ void store(int m, int n, const float (&v)[16], float &) const {
+    static constexpr int SMEM_FLOATS = 1;
+    __device__ __forceinline__ void prepare(float *, int, int) const {}
+    __device__ __forceinline__ void store(int m, int n, const float (&v)[16], float &, const float *) const {
         float w[16];
 #pragma unroll
         for (int q = 0; q < 16; ++q) w[q] = v[q];
@@ -100,7 +113,7 @@ struct DgradEpi {
             store16(din2 + (long long)m * (N - split) + (n - split), w);
         }
     }
-    __device__ __forceinline__ void finish(int, float) const {}
+    __device__ __forceinline__ void finish(int, float, const float *) const {}
 };
 
 PFN_cuTensorMapEncodeTiled_v12000 encoder() {
@@ -196,7 +209,7 @@ template <int BN, int CK, class EPI>
 cudaError_t launch_halo(const __nv_bfloat16 *A, int B, int H, int W, int C, const __nv_bfloat16 *wmat, int N, int flip,
                         const EPI &epi, cudaStream_t s) {
     using Cf = tma::HaloCfg<BN, CK>;
-    if (W % tma::HBW || H % tma::HBH || C % CK || N != BN) return cudaErrorNotSupported;
+    if (W % tma::HBW || H % tma::HBH || C % CK || N % BN) return cudaErrorNotSupported;
     const int nblk = 9 * (C / CK);
     const int wbytes = nblk * Cf::BBLK;
     int S = (Cf::SMEM_BUDGET - wbytes) / Cf::A_BYTES;
@@ -237,8 +250,8 @@ cudaError_t launch_halo(const __nv_bfloat16 *A, int B, int H, int W, int C, cons
     g.tiles_x = W / tma::HBW;
     g.tiles_y = H / tma::HBH;
     g.mtiles = B * g.tiles_x * g.tiles_y;
-    g.ntiles = 1;
-    g.tiles = g.mtiles;
+    g.ntiles = N / BN;
+    g.tiles = g.mtiles * g.ntiles;
     g.nchunk = C / CK;
     g.KB = 3 * g.nchunk;
     g.flip = flip;
@@ -246,7 +259,10 @@ cudaError_t launch_halo(const __nv_bfloat16 *A, int B, int H, int W, int C, cons
     auto *fn = &tma::k_conv_halo<BN, CK, EPI>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    const int grid = g.tiles < nsm ? g.tiles : nsm;
+    // each CTA keeps one n tile's weights: a whole number of CTAs per n tile
+    const int per = nsm / g.ntiles;
+    if (per < 1) return cudaErrorNotSupported;
+    const int grid = (g.mtiles < per ? g.mtiles : per) * g.ntiles;
     fn<<<grid, 192, smem, s>>>(ma, mb, g, epi, S, err);
     return cudaGetLastError();
 }
@@ -278,7 +294,7 @@ cudaError_t conv_forward_tma(const __nv_bfloat16 *in, int B, int H, int W, int C
         return ck64 ? launch<32, 64>(in, B, H, W, Cin, w, Cout, 0, epi, s)
                     : launch<32, 32>(in, B, H, W, Cin, w, Cout, 0, epi, s);
     }
-    const FwdEpi epi{bias, out, ldo, relu};
+    const FwdEpi epi{bias, out, ldo, relu, Cout};
     if (Cout == 32 || Cout == 64) {
         cudaError_t e;
         if (Cout == 32)

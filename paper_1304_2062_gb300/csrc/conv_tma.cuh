@@ -111,8 +111,10 @@ __device__ __forceinline__ void tile_origin(const ConvGeo &g, int t, int &b, int
 }
 
 // EPI provides
-//   store(m, n, v[16], float &state)  the 16 outputs of pixel m, columns n..n+15
-//   finish(m, float state)            after the last column group of pixel m
+//   SMEM_FLOATS, prepare(sm, i, n)    constants copied to shared memory by the
+//                                      epilogue threads i = 0..n-1 once per CTA
+//   store(m, n, v[16], float &state, sm)  the 16 outputs of pixel m, columns n..n+15
+//   finish(m, float state, sm)        after the last column group of pixel m
 template <int BN, int CK, class EPI>
 __global__ void __launch_bounds__(192, 1)
     k_conv_tma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, const ConvGeo g,
@@ -239,6 +241,9 @@ __global__ void __launch_bounds__(192, 1)
         }
     } else {
         // ---------------- epilogue (warps 2..5) ----------------
+        __shared__ float epi_const[EPI::SMEM_FLOATS];
+        epi.prepare(epi_const, threadIdx.x - 64, 128);
+        asm volatile("bar.sync 1, 128;\n" ::: "memory");  // the four epilogue warps only
         const int q = warp & 3;  // lane quarter this warp may read
         int acc = 0;
         uint32_t aph = 0;
@@ -259,9 +264,9 @@ __global__ void __launch_bounds__(192, 1)
                 float f[16];
 #pragma unroll
                 for (int i = 0; i < 16; ++i) f[i] = __uint_as_float(v[i]);
-                epi.store(m, nt * BN + j0, f, state);
+                epi.store(m, nt * BN + j0, f, state, epi_const);
             }
-            epi.finish(m, state);
+            epi.finish(m, state, epi_const);
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
             __syncwarp();
             if (lane == 0) arrive(bar_aempty + 8 * acc);
@@ -325,6 +330,11 @@ __global__ void __launch_bounds__(192, 1)
     const uint32_t tmem_slot = bar_aempty + 16;
     volatile int *abort = (volatile int *)(smem_raw + (tmem_slot + 4 - raw));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // tiles t = nt * mtiles + mt; CTA c takes n tile c % ntiles and every
+    // (gridDim.x / ntiles)-th m tile from c / ntiles (gridDim.x % ntiles == 0)
+    const int first_tile = (blockIdx.x % g.ntiles) * g.mtiles + blockIdx.x / g.ntiles;
+    const int end_tile = (blockIdx.x % g.ntiles + 1) * g.mtiles;
+    const int tile_step = gridDim.x / g.ntiles;
 
     if (threadIdx.x == 0) {
         *abort = *(volatile int *)err;
@@ -357,8 +367,8 @@ __global__ void __launch_bounds__(192, 1)
     if (warp == 0) {
         if (lane == 0) {
             // ---------------- TMA producer ----------------
-            const int nt0 = blockIdx.x < g.tiles ? (blockIdx.x / g.mtiles) : 0;
-            // this CTA's tiles all have the same n tile when ntiles == 1 (the narrow layers)
+            // this CTA's tiles all have the n tile blockIdx.x % ntiles: its weights stay resident
+            const int nt0 = blockIdx.x % g.ntiles;
             arrive_expect_tx(bar_w, (uint32_t)(nblk * Cf::BBLK));
             for (int tap = 0; tap < 9; ++tap)
                 for (int ch = 0; ch < g.nchunk; ++ch)
@@ -366,7 +376,7 @@ __global__ void __launch_bounds__(192, 1)
             int s = 0;
             uint32_t ph = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < g.tiles && ok; t += gridDim.x) {
+            for (int t = first_tile; t < end_tile && ok; t += tile_step) {
                 int b, x0, y0, nt;
                 tile_origin(g, t, b, x0, y0, nt);
                 for (int ch = 0; ch < g.nchunk && ok; ++ch)
@@ -398,7 +408,7 @@ __global__ void __launch_bounds__(192, 1)
             uint32_t ph = 0, aph = 0;
             bool ok = tc::mbar_wait(bar_w, 0, abort);
             uint32_t last_bar = 0, last_par = 0;
-            for (int t = blockIdx.x; t < g.tiles && ok; t += gridDim.x) {
+            for (int t = first_tile; t < end_tile && ok; t += tile_step) {
                 if (!tc::mbar_wait(bar_aempty + 8 * acc, aph ^ 1u, abort)) {
                     ok = false;
                     break;
@@ -446,10 +456,13 @@ __global__ void __launch_bounds__(192, 1)
         }
     } else {
         // ---------------- epilogue (warps 2..5) ----------------
+        __shared__ float epi_const[EPI::SMEM_FLOATS];
+        epi.prepare(epi_const, threadIdx.x - 64, 128);
+        asm volatile("bar.sync 1, 128;\n" ::: "memory");  // the four epilogue warps only
         const int q = warp & 3;
         int acc = 0;
         uint32_t aph = 0;
-        for (int t = blockIdx.x; t < g.tiles; t += gridDim.x) {
+        for (int t = first_tile; t < end_tile; t += tile_step) {
             if (!tc::mbar_wait(bar_afull + 8 * acc, aph, abort)) break;
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             int b, x0, y0, nt;
@@ -466,9 +479,9 @@ __global__ void __launch_bounds__(192, 1)
                 float f[16];
 #pragma unroll
                 for (int i = 0; i < 16; ++i) f[i] = __uint_as_float(v[i]);
-                epi.store(m, nt * BN + j0, f, state);
+                epi.store(m, nt * BN + j0, f, state, epi_const);
             }
-            epi.finish(m, state);
+            epi.finish(m, state, epi_const);
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
             __syncwarp();
             if (lane == 0) arrive(bar_aempty + 8 * acc);
