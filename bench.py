@@ -639,7 +639,7 @@ def run_surrogate(args, rank, world, local_rank):
            "quality": quality,
            "roofline": {"bound": "tensor", "achieved": round(achieved, 3), "peak": peak, "unit": "TFLOP/s",
                         "frac": round(achieved / peak, 4), "traffic": None,
-                        "kernel": "se2n_unet_forward (k_conv_fwd: mma.sync m16n8k16 bf16, FP32 accumulate)",
+                        "kernel": "se2n_unet_forward: 13 tcgen05 convolutions (TMA) + first layer on CUDA cores",
                         "flops_per_launch": fl, "avg_launch_ms": round(ms_fwd, 4),
                         "peak_basis": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json bf16_tflops)"},
            "training": {"pairs": count, "batch": tb, "steps": done, "seconds": round(train_s, 2),
@@ -658,6 +658,84 @@ def run_surrogate(args, rank, world, local_rank):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = surrogate_cpu_baseline()
     return res
+
+
+def run_unet_forward(args, rank, world, local_rank):
+    """The network's inference kernels alone: batches of 64 seeded 256x256
+    inputs (the surrogate workload's images and masks) through
+    se2n_unet_forward, initialised weights (the kernels' cost does not depend
+    on their values). Roofline: the forward's algorithmic conv flops against
+    the measured dense bf16 peak."""
+    import torch
+
+    from paper_1304_2062_gb300 import se2n
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    H = W = synth.SURROGATE_SIDE
+    clean, mask = synth.surrogate_examples(synth.SURROGATE_VAL_SEEDS[0] + 64 * rank, SURR_BATCH)
+    stream = torch.cuda.Stream(dev)
+    F = torch.tensor(clean * mask, device=dev)
+    M = torch.tensor(mask, device=dev)
+    out = torch.empty((SURR_BATCH, H, W), dtype=torch.float32, device=dev)
+    u = se2n.se2n_unet_create(SURR_BATCH, H, W, stream)
+    se2n.se2n_unet_init(u, 7)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            se2n.se2n_unet_forward(u, F, M, SURR_BATCH, out)
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        evs = []
+        with ClockSampler(local_rank) as clocks:
+            for _ in range(args.steps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                se2n.se2n_unet_forward(u, F, M, SURR_BATCH, out)
+                b.record(stream)
+                evs.append((a, b))
+            torch.cuda.synchronize(dev)
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), dist, dev) / args.steps
+    u.close()
+    if dist:
+        dist.destroy_process_group()
+    fl = surrogate_flops(H, W) * SURR_BATCH
+    peak = _peaks().get("bf16_tflops", 1890.1)
+    achieved = fl / (ms / 1e3) / 1e12
+    res = {"metric": "surrogate network forward images/s (256x256, batch 64)", "value": world * SURR_BATCH / (ms / 1e3),
+           "unit": SURR_UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (FP32 accumulate)",
+           "data": "synthetic", "config": {"workload": "unet_forward_256_b64: 64 seeded lines-and-circles images, "
+                                                      "50% masks, 4-level U-Net 32-64-128-256",
+                                           "l2": "flushed between timed steps (256 MiB write)",
+                                           "parallelism": "replicas"},
+           "roofline": {"bound": "tensor", "achieved": round(achieved, 3), "peak": peak, "unit": "TFLOP/s",
+                        "frac": round(achieved / peak, 4), "traffic": None,
+                        "kernel": "se2n_unet_forward: 13 tcgen05 convolutions (TMA) + first layer on CUDA cores",
+                        "flops_per_launch": fl, "avg_launch_ms": round(ms, 4),
+                        "peak_basis": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json bf16_tflops)"},
+           "clocks": clocks.summary(), "gpu_launches": 20 * args.steps}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = unet_cpu_baseline()
+    return res
+
+
+def unet_cpu_baseline():
+    """The FP64 reference network (oracle/unet.py) forward on one image."""
+    from oracle import unet as ou
+    clean, mask = synth.surrogate_example(synth.SURROGATE_VAL_SEEDS[0])
+    p = ou.he_params(7)
+    t0 = time.perf_counter()
+    ou.forward(p, (clean * mask)[None], mask[None])
+    dt = time.perf_counter() - t0
+    return {"value": 1 / dt, "unit": SURR_UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"the FP64 reference network's forward of one 256x256 image ({dt:.1f} s, numpy)"}
 
 
 def surrogate_cpu_baseline(n=8):
@@ -758,7 +836,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["512", "batch", "surrogate"], default="512",
+    ap.add_argument("--workload", choices=["512", "batch", "surrogate", "unet-forward"], default="512",
                     help="512: the 512x512 N=32 10x500-step inpaint (default); batch: 256 uneven images; "
                          "surrogate: train the U-Net on method pairs, time its inference with fallback")
     ap.add_argument("--train-seconds", type=float, default=150.0, help="surrogate training time budget")
@@ -777,6 +855,8 @@ def main():
         res = run_batch(args, rank, world, local_rank)
     elif args.workload == "surrogate":
         res = run_surrogate(args, rank, world, local_rank)
+    elif args.workload == "unet-forward":
+        res = run_unet_forward(args, rank, world, local_rank)
     else:
         res = run_ours(args, rank, world, local_rank)
     if rank == 0 and res is not None:
