@@ -8,9 +8,11 @@ interval): orientation, lift, forward DFT, 10 x fused diffusion, 9 x
 all through se2n_inpaint with the inputs resident in HBM.
 
 Metric: Mathieu updates per second, updates = frequencies x N x steps per
-interval x intervals = 512^2 * 32 * 500 * 10 per inpaint, over the whole
-inpaint time (value), plus ms per inpaint, the FP32 error against the FP64
-oracle, the diffusion kernel's roofline (FP32 ALU bound), the end-to-end
+interval x intervals = 512^2 * 32 * 500 * 10 per inpaint (the method's
+work on all M^2 frequencies), over the whole inpaint time (value), plus ms
+per inpaint, the FP32 error against the FP64 oracle, the diffusion kernel's
+roofline (FP32 ALU bound; its flops are those of the frequencies the launch
+integrates, the Hermitian half 512 x 257 of the spectrum), the end-to-end
 number from host buffers (se2n_inpaint_host) and the oracle's CPU rate.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -218,7 +220,8 @@ def run_ours(args, rank, world, local_rank):
     # diffusion kernel roofline (FP32 ALU bound), from the live event timings
     d_ms, d_calls = prof["diffuse"]
     d_avg_s = d_ms / d_calls / 1e3
-    updates_per_launch = w.H * w.W * w.N * w.steps
+    # the launch integrates the Hermitian half of the spectrum: H x (W/2 + 1) frequencies
+    updates_per_launch = w.H * (w.W // 2 + 1) * w.N * w.steps
     achieved = FLOPS_PER_UPDATE * updates_per_launch / d_avg_s / 1e12
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
@@ -229,7 +232,8 @@ def run_ours(args, rank, world, local_rank):
                 "avg_launch_ms": round(d_avg_s * 1e3, 4),
                 "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop/FMA x 2070 MHz (derived, not measured)",
                 "diffuse_updates_per_s": updates_per_launch / d_avg_s,
-                "hbm_gbs_of_diffuse": round(16 * w.H * w.W * w.N / d_avg_s / 1e9, 1)}
+                "hbm_gbs_of_diffuse": round(16 * w.H * (w.W // 2 + 1) * w.N / d_avg_s / 1e9, 1),
+                "frequencies_integrated": "Hermitian half, H x (W/2 + 1) (value counts all M^2 frequencies)"}
     stages = {k: {"ms_per_step": round(v[0] / args.steps, 4), "calls_per_step": v[1] / args.steps}
               for k, v in prof.items() if k != "kernels"}
     launches = int(prof["kernels"])
@@ -359,7 +363,9 @@ def run_batch(args, rank, world, local_rank):
         ms = timed(se2n.se2n_batch_run, args.steps)
     ms_per_image = timed(se2n.se2n_batch_run_per_image, max(1, min(args.steps, 3)))
     ms_diff = timed(se2n.se2n_batch_run_diffusion, max(1, min(args.steps, 5)))
-    achieved = FLOPS_PER_UPDATE * updates / (ms_diff / 1e3) / 1e12
+    # the diffusion launch integrates the Hermitian half of each spectrum
+    half_updates = sum(w.H * (w.W // 2 + 1) * w.N * w.steps * w.rounds for w in mine)
+    achieved = FLOPS_PER_UPDATE * half_updates / (ms_diff / 1e3) / 1e12
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
     batch.close()
     if dist:

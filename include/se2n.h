@@ -94,7 +94,14 @@ typedef struct se2n_plan se2n_plan;
  *   diffuse_flags  SE2N_DIFFUSE_* flags passed to every diffusion.
  *   reinject 1: the result is the inpainted image, f on the known pixels
  *            (mask != 0) and the projection only on the corrupted ones;
- *            0: the projection everywhere (default). */
+ *            0: the projection everywhere (default).
+ *   full_spectrum  0 (default): the lifted volume is real, so its spectrum
+ *            is Hermitian and the system of frequency (-k, -l) is that of
+ *            (k, l) conjugated (a_r^2 is even in the frequency; Theorem 2):
+ *            se2n_inpaint integrates the H (W/2 + 1) frequencies l <= W/2
+ *            with real-to-complex transforms. 1: all H W frequencies with
+ *            complex transforms. Same result up to rounding. The volume
+ *            argument of se2n_inpaint is [N][H][W] complex in both cases. */
 typedef struct se2n_params {
     int N;
     double beta;
@@ -109,11 +116,12 @@ typedef struct se2n_params {
     double guard;
     int diffuse_flags;
     int reinject;
+    int full_spectrum;
 } se2n_params;
 
 /* Fill p with the defaults: N=32, beta=0.25, T=2, steps=100, rounds=1,
  * eps=0.5, sigma_smooth=1, flat_tol=1e-4, proj=max, final_mix=0,
- * guard=0.1, diffuse_flags=0, reinject=0. SE2N_EINVAL if p is NULL. */
+ * guard=0.1, diffuse_flags=0, reinject=0, full_spectrum=0. SE2N_EINVAL if p is NULL. */
 SE2N_API se2n_status se2n_params_default(se2n_params *p);
 
 /* Map the paper's weighting alpha and time T_paper on an M x M image with N

@@ -28,9 +28,9 @@ __device__ __forceinline__ void batch_item(const StepParams &sp, const float *ta
         const bool active = o < item.count;
         const long long fc = item.first + (active ? o : 0);
         if constexpr (FAST) {
-            diffuse_group_x2<N, P, SPLIT>(sp, cs, sn, im.vol, im.H, im.W, im.HW, fc, active);
+            diffuse_group_x2<N, P, SPLIT>(sp, cs, sn, im.vol, im.H, im.W, im.Wc, im.HW, fc, active);
         } else {
-            diffuse_group<N, P, false, SPLIT>(sp, cs, sn, im.vol, im.H, im.W, im.HW, fc, active);
+            diffuse_group<N, P, false, SPLIT>(sp, cs, sn, im.vol, im.H, im.W, im.Wc, im.HW, fc, active);
         }
     }
 }

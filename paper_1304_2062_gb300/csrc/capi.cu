@@ -100,7 +100,8 @@ void angle_table(int N, int angle_conv, float *cs, float *sn, int count) {
 
 namespace {
 
-se2n_status diffuse_impl(se2n_plan *plan, float2 *vol, double beta, double T, int steps, int flags) {
+// half: vol holds the Hermitian half [N][H][W/2 + 1] of the spectrum.
+se2n_status diffuse_impl(se2n_plan *plan, float2 *vol, double beta, double T, int steps, int flags, bool half = false) {
     if (!(beta > 0.0) || !(T >= 0.0) || steps < 1 || !isfinite(beta) || !isfinite(T)) return SE2N_EINVAL;
     if (flags & ~(SE2N_DIFFUSE_SM_FP64 | SE2N_DIFFUSE_SPLIT_DIAG | SE2N_DIFFUSE_FULL_CORRECTION)) return SE2N_EINVAL;
     if (T == 0.0) return SE2N_OK;
@@ -115,7 +116,8 @@ se2n_status diffuse_impl(se2n_plan *plan, float2 *vol, double beta, double T, in
 
     DiffuseArgs a;
     a.vol = vol;
-    a.HW = plan->HW;
+    a.Wc = half ? plan->Wc : plan->W;
+    a.HW = (long long)plan->H * a.Wc;
     a.H = plan->H;
     a.W = plan->W;
     a.sp = step_params(beta, bdt, steps);
@@ -130,7 +132,7 @@ se2n_status diffuse_impl(se2n_plan *plan, float2 *vol, double beta, double T, in
         if (per_sm < 1) per_sm = 1;
         blocks = plan->num_sms * per_sm;
     }
-    const long long need = (plan->HW * P + block - 1) / block;
+    const long long need = (a.HW * P + block - 1) / block;
     if (blocks > need) blocks = (int)need;
     if (blocks < 1) blocks = 1;
     StageTimer timer(plan, SE2N_STAGE_DIFFUSE);
@@ -143,6 +145,31 @@ se2n_status diffuse_impl(se2n_plan *plan, float2 *vol, double beta, double T, in
 se2n_status fft(se2n_plan *plan, cufftHandle h, float2 *data, int dir) {
     StageTimer timer(plan, SE2N_STAGE_FFT);
     return cufft_status(cufftExecC2C(h, (cufftComplex *)data, (cufftComplex *)data, dir));
+}
+
+// The Hermitian-half transforms (in place; the inverse is unnormalised).
+se2n_status ensure_half(se2n_plan *plan) {
+    if (plan->half_ready) return SE2N_OK;
+    int n2[2] = {plan->H, plan->W};
+    int real_embed[2] = {plan->H, 2 * plan->Wc};
+    int cplx_embed[2] = {plan->H, plan->Wc};
+    const int real_dist = plan->H * 2 * plan->Wc, cplx_dist = plan->H * plan->Wc;
+    cufftResult r = cufftPlanMany(&plan->fft_r2c, 2, n2, real_embed, 1, real_dist, cplx_embed, 1, cplx_dist, CUFFT_R2C,
+                                  plan->N);
+    if (r == CUFFT_SUCCESS)
+        r = cufftPlanMany(&plan->fft_c2r, 2, n2, cplx_embed, 1, cplx_dist, real_embed, 1, real_dist, CUFFT_C2R,
+                          plan->N);
+    if (r == CUFFT_SUCCESS) r = cufftSetStream(plan->fft_r2c, plan->stream);
+    if (r == CUFFT_SUCCESS) r = cufftSetStream(plan->fft_c2r, plan->stream);
+    if (r != CUFFT_SUCCESS) return cufft_status(r);
+    plan->half_ready = true;
+    return SE2N_OK;
+}
+
+se2n_status fft_half(se2n_plan *plan, float2 *data, bool forward) {
+    StageTimer timer(plan, SE2N_STAGE_FFT);
+    if (forward) return cufft_status(cufftExecR2C(plan->fft_r2c, (cufftReal *)data, (cufftComplex *)data));
+    return cufft_status(cufftExecC2R(plan->fft_c2r, (cufftComplex *)data, (cufftReal *)data));
 }
 
 se2n_status orient_impl(se2n_plan *plan, const float *f, const uint8_t *mask, double sigma, double flat_tol,
@@ -176,6 +203,28 @@ se2n_status mix_impl(se2n_plan *plan, float2 *vol, const float *f, const uint8_t
     return cuda_status(plan, se2n_launch_mix(vol, f, mask, bins, plan->HW, plan->N, scale, eps, guard, plan->stream));
 }
 
+se2n_status lift_half_impl(se2n_plan *plan, const float *f, const uint8_t *mask, const uint8_t *bins, float2 *vol) {
+    StageTimer timer(plan, SE2N_STAGE_LIFT);
+    plan->kernels += 1;
+    return cuda_status(plan, se2n_launch_lift_r(f, mask, bins, (float *)vol, plan->H, plan->W, plan->N, plan->stream));
+}
+
+se2n_status mix_half_impl(se2n_plan *plan, float2 *vol, const float *f, const uint8_t *mask, const uint8_t *bins,
+                          float scale, float eps, float guard) {
+    StageTimer timer(plan, SE2N_STAGE_MIX);
+    plan->kernels += 1;
+    return cuda_status(plan, se2n_launch_mix_r((float *)vol, f, mask, bins, plan->H, plan->W, plan->N, scale, eps,
+                                               guard, plan->stream));
+}
+
+se2n_status project_half_impl(se2n_plan *plan, const float2 *vol, float scale, int proj, const float *f,
+                              const uint8_t *mask, float *out) {
+    StageTimer timer(plan, SE2N_STAGE_PROJECT);
+    plan->kernels += 1;
+    return cuda_status(plan, se2n_launch_project_r((const float *)vol, plan->H, plan->W, plan->N, scale, proj, f, mask,
+                                                   out, plan->stream));
+}
+
 se2n_status project_impl(se2n_plan *plan, const float2 *vol, float scale, int proj, const float *f,
                          const uint8_t *mask, float *out) {
     StageTimer timer(plan, SE2N_STAGE_PROJECT);
@@ -188,7 +237,7 @@ se2n_status check_params(const se2n_plan *plan, const se2n_params *p) {
     if (p->N != plan->N || !(p->beta > 0.0) || !(p->T >= 0.0) || p->steps < 1 || p->rounds < 1) return SE2N_EINVAL;
     if (!(p->eps >= 0.0 && p->eps <= 1.0) || !(p->sigma_smooth > 0.0) || !(p->flat_tol >= 0.0)) return SE2N_EINVAL;
     if ((p->proj != SE2N_PROJ_MAX && p->proj != SE2N_PROJ_MEAN) || (p->final_mix != 0 && p->final_mix != 1) ||
-        (p->reinject != 0 && p->reinject != 1))
+        (p->reinject != 0 && p->reinject != 1) || (p->full_spectrum != 0 && p->full_spectrum != 1))
         return SE2N_EINVAL;
     if (!(p->guard >= 0.0) ||
         (p->diffuse_flags & ~(SE2N_DIFFUSE_SM_FP64 | SE2N_DIFFUSE_SPLIT_DIAG | SE2N_DIFFUSE_FULL_CORRECTION)))
@@ -213,6 +262,31 @@ se2n_status inpaint_impl(se2n_plan *plan, const float *f, const uint8_t *mask, c
     }
     const double Tr = p->T / p->rounds;
     const float inv_hw = (float)(1.0 / (double)HW);
+    if (!p->full_spectrum) {
+        // The lifted volume is real, so its spectrum is Hermitian and the
+        // system of frequency (-k, -l) is that of (k, l) conjugated (a_r^2 is
+        // even in the frequency): integrate the half l = 0 .. W/2 only, with
+        // real-to-complex transforms, and let the inverse transform rebuild
+        // the rest.
+        SE2N_TRY(ensure_half(plan));
+        SE2N_TRY(lift_half_impl(plan, f, mask, bins, vol));
+        SE2N_TRY(fft_half(plan, vol, true));
+        SE2N_TRY(diffuse_impl(plan, vol, p->beta, Tr, p->steps, p->diffuse_flags, true));
+        for (int i = 1; i < p->rounds; ++i) {
+            SE2N_TRY(fft_half(plan, vol, false));
+            SE2N_TRY(mix_half_impl(plan, vol, f, mask, bins, inv_hw, (float)p->eps, (float)p->guard));
+            SE2N_TRY(fft_half(plan, vol, true));
+            SE2N_TRY(diffuse_impl(plan, vol, p->beta, Tr, p->steps, p->diffuse_flags, true));
+        }
+        SE2N_TRY(fft_half(plan, vol, false));
+        float scale = inv_hw;
+        if (p->final_mix) {
+            SE2N_TRY(mix_half_impl(plan, vol, f, mask, bins, inv_hw, (float)p->eps, (float)p->guard));
+            scale = 1.0f;
+        }
+        return project_half_impl(plan, vol, scale, p->proj, p->reinject ? f : nullptr, p->reinject ? mask : nullptr,
+                                 out);
+    }
     SE2N_TRY(lift_impl(plan, f, mask, bins, vol));
     SE2N_TRY(fft(plan, plan->fft_vol, vol, CUFFT_FORWARD));
     SE2N_TRY(diffuse_impl(plan, vol, p->beta, Tr, p->steps, p->diffuse_flags));
@@ -236,6 +310,8 @@ void free_plan(se2n_plan *plan) {
     if (plan->fft_vol) cufftDestroy(plan->fft_vol);
     if (plan->fft_one) cufftDestroy(plan->fft_one);
     if (plan->fft_two) cufftDestroy(plan->fft_two);
+    if (plan->fft_r2c) cufftDestroy(plan->fft_r2c);
+    if (plan->fft_c2r) cufftDestroy(plan->fft_c2r);
     cudaFree(plan->spec);
     cudaFree(plan->gmax);
     cudaFree(plan->bins);
@@ -280,6 +356,7 @@ se2n_status se2n_params_default(se2n_params *p) {
     p->guard = 0.1;
     p->diffuse_flags = 0;
     p->reinject = 0;
+    p->full_spectrum = 0;
     return SE2N_OK;
 }
 
@@ -304,6 +381,10 @@ se2n_status se2n_plan_create(se2n_plan **out, int H, int W, int N, int angle_con
     plan->N = N;
     plan->angle_conv = angle_conv;
     plan->HW = (long long)H * W;
+    plan->Wc = W / 2 + 1;
+    plan->fft_r2c = 0;
+    plan->fft_c2r = 0;
+    plan->half_ready = false;
     plan->stream = (cudaStream_t)stream;
     plan->diffuse_P = se2n_diffuse_default_P(N);
     plan->diffuse_block = 256;
@@ -353,6 +434,9 @@ se2n_status se2n_plan_set_stream(se2n_plan *plan, void *stream) {
     cudaStream_t s = (cudaStream_t)stream;
     if (cufftSetStream(plan->fft_vol, s) != CUFFT_SUCCESS || cufftSetStream(plan->fft_one, s) != CUFFT_SUCCESS ||
         cufftSetStream(plan->fft_two, s) != CUFFT_SUCCESS)
+        return SE2N_ECUFFT;
+    if (plan->half_ready &&
+        (cufftSetStream(plan->fft_r2c, s) != CUFFT_SUCCESS || cufftSetStream(plan->fft_c2r, s) != CUFFT_SUCCESS))
         return SE2N_ECUFFT;
     plan->stream = s;
     return SE2N_OK;
@@ -566,7 +650,7 @@ std::vector<BatchItem> build_items(const se2n_batch *b, int config, int passes) 
     std::vector<BatchItem> items;
     for (int i : order) {
         const se2n_image_desc &d = b->imgs[i];
-        const long long HW = (long long)d.H * d.W;
+        const long long HW = b->h_imgs[i].HW;  // frequencies integrated (the Hermitian half by default)
         const int per = 32 / se2n_batch_config_P(config, d.N);
         const long long tile = (long long)per * passes;
         for (long long f0 = 0; f0 < HW; f0 += tile) {
@@ -659,8 +743,52 @@ se2n_status autotune(se2n_batch *b) {
     return set_shape(b, bc, bp, bb);
 }
 
+se2n_status enqueue_batch_half(se2n_batch *b) {
+    const se2n_params &p = b->p;
+    const double Tr = p.T / p.rounds;
+    for (int i = 0; i < b->count; ++i) {
+        se2n_plan *pl = b->plan_of[i];
+        const se2n_image_desc &d = b->imgs[i];
+        if (d.bins) {
+            if (cudaMemcpyAsync(b->bins[i], d.bins, (size_t)pl->HW, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess)
+                return SE2N_ECUDA;
+        } else {
+            SE2N_TRY(orient_impl(pl, d.f, d.mask, p.sigma_smooth, p.flat_tol, b->bins[i]));
+        }
+        SE2N_TRY(lift_half_impl(pl, d.f, d.mask, b->bins[i], b->vols[i]));
+        SE2N_TRY(fft_half(pl, b->vols[i], true));
+    }
+    SE2N_TRY(batch_diffuse(b, p.steps, Tr));
+    for (int r = 1; r < p.rounds; ++r) {
+        for (int i = 0; i < b->count; ++i) {
+            se2n_plan *pl = b->plan_of[i];
+            const se2n_image_desc &d = b->imgs[i];
+            SE2N_TRY(fft_half(pl, b->vols[i], false));
+            SE2N_TRY(mix_half_impl(pl, b->vols[i], d.f, d.mask, b->bins[i], (float)(1.0 / (double)pl->HW),
+                                   (float)p.eps, (float)p.guard));
+            SE2N_TRY(fft_half(pl, b->vols[i], true));
+        }
+        SE2N_TRY(batch_diffuse(b, p.steps, Tr));
+    }
+    for (int i = 0; i < b->count; ++i) {
+        se2n_plan *pl = b->plan_of[i];
+        const se2n_image_desc &d = b->imgs[i];
+        const float inv_hw = (float)(1.0 / (double)pl->HW);
+        SE2N_TRY(fft_half(pl, b->vols[i], false));
+        float scale = inv_hw;
+        if (p.final_mix) {
+            SE2N_TRY(mix_half_impl(pl, b->vols[i], d.f, d.mask, b->bins[i], inv_hw, (float)p.eps, (float)p.guard));
+            scale = 1.0f;
+        }
+        SE2N_TRY(project_half_impl(pl, b->vols[i], scale, p.proj, p.reinject ? d.f : nullptr,
+                                   p.reinject ? d.mask : nullptr, d.out));
+    }
+    return SE2N_OK;
+}
+
 se2n_status enqueue_batch(se2n_batch *b) {
     const se2n_params &p = b->p;
+    if (!p.full_spectrum) return enqueue_batch_half(b);
     const double Tr = p.T / p.rounds;
     for (int i = 0; i < b->count; ++i) {
         se2n_plan *pl = b->plan_of[i];
@@ -779,7 +907,8 @@ se2n_status create_batch(se2n_batch *b, const se2n_image_desc *imgs) {
         bi.vol = b->vols[i];
         bi.H = imgs[i].H;
         bi.W = imgs[i].W;
-        bi.HW = (long long)bi.H * bi.W;
+        bi.Wc = b->p.full_spectrum ? bi.W : bi.W / 2 + 1;
+        bi.HW = (long long)bi.H * bi.Wc;
         bi.N = N;
         bi.table = t;
     }
@@ -797,6 +926,9 @@ se2n_status create_batch(se2n_batch *b, const se2n_image_desc *imgs) {
     b->split = (b->p.diffuse_flags & SE2N_DIFFUSE_SPLIT_DIAG) || b->p.beta * Tr > 8.0;
     b->fast = !(b->p.diffuse_flags & SE2N_DIFFUSE_FULL_CORRECTION) && se2n_diffuse_truncation_ok(bdt);
     if (cudaMemsetAsync(b->arena, 0, b->vol_bytes, b->stream) != cudaSuccess) return SE2N_ECUDA;
+    // transforms of the Hermitian-half path are planned before the capture
+    if (!b->p.full_spectrum)
+        for (se2n_plan *pl : b->plans) SE2N_TRY(ensure_half(pl));
     if (b->flags_autotune) {
         SE2N_TRY(autotune(b));
     } else {

@@ -79,7 +79,7 @@ constexpr int kTruncRows = 6;
 // (shuffles); a lane with !active works on a valid frequency without storing.
 template <int N, int P, bool SPLIT>
 __device__ __forceinline__ void diffuse_group_x2(const StepParams &sp, const float *cs, const float *sn,
-    float2 *vol, int H, int W, long long HW, long long fc, bool active) {
+    float2 *vol, int H, int W, int Wc, long long HW, long long fc, bool active) {
     constexpr int K = N / P;
     constexpr int Q = TearInfo<P>::Q;
     constexpr int KZ = (K < kTruncRows) ? K : kTruncRows;
@@ -93,8 +93,9 @@ __device__ __forceinline__ void diffuse_group_x2(const StepParams &sp, const flo
     const int row0 = (P == 1) ? 0 : (ti.iside ? (p >> 1) * half : (p >> 1) * half + half - 1);
     const int rstep = (P == 1 || ti.iside) ? 1 : -1;
 
-    const int k = (int)(fc / W);
-    const int l = (int)(fc - (long long)k * W);
+    // fc = k * Wc + l: Wc stored columns (W, or W/2 + 1 for the Hermitian half)
+    const int k = (int)(fc / Wc);
+    const int l = (int)(fc - (long long)k * Wc);
     const float wx = sin_2pi_frac(l, W);
     const float wy = sin_2pi_frac(k, H);
     float2 *col = vol + (long long)row0 * HW + fc;
@@ -232,7 +233,7 @@ __global__ void __launch_bounds__(256) k_diffuse_x2(const __grid_constant__ Diff
     for (long long base = 0; warp_slot0 + base < a.HW; base += nslots) {
         const long long f = slot + base;
         const bool active = f < a.HW;
-        diffuse_group_x2<N, P, SPLIT>(a.sp, a.cs, a.sn, a.vol, a.H, a.W, a.HW, active ? f : a.HW - 1, active);
+        diffuse_group_x2<N, P, SPLIT>(a.sp, a.cs, a.sn, a.vol, a.H, a.W, a.Wc, a.HW, active ? f : a.HW - 1, active);
     }
 }
 

@@ -54,9 +54,9 @@ __device__ __forceinline__ void static_item(const StepParams &sp, const float *t
         const bool active = o < count;
         const long long fc = first + (active ? o : 0);
         if constexpr (FAST) {
-            se2n::diffuse_group_x2<N, P, SPLIT>(sp, cs, sn, im.vol, im.H, im.W, im.HW, fc, active);
+            se2n::diffuse_group_x2<N, P, SPLIT>(sp, cs, sn, im.vol, im.H, im.W, im.W, im.HW, fc, active);
         } else {
-            se2n::diffuse_group<N, P, false, SPLIT>(sp, cs, sn, im.vol, im.H, im.W, im.HW, fc, active);
+            se2n::diffuse_group<N, P, false, SPLIT>(sp, cs, sn, im.vol, im.H, im.W, im.W, im.HW, fc, active);
         }
     }
 }

@@ -193,6 +193,102 @@ __global__ void k_project(const float4 *__restrict__ vol, long long npairs, int 
     }
 }
 
+// ---------------------------------------------------------------------------
+// The same stages on the real volume of the Hermitian-half path: planes of
+// H rows of Wp = W + 2 floats (the in-place R2C layout), pixel (y, x) of
+// plane r at r * H * Wp + y * Wp + x. Two pixels per thread (W even).
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ long long real_off(long long i, int W, int Wp) {
+    const long long p = 2 * i;
+    const long long y = p / W;
+    return y * Wp + (p - y * W);
+}
+
+__global__ void k_lift_r(const float2 *__restrict__ f, const uchar2 *__restrict__ mask,
+                         const uchar2 *__restrict__ bins, float *__restrict__ vol, long long npairs, int W, int Wp,
+                         long long plane, int N) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npairs;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float2 v = f[i];
+        const uchar2 m = mask[i];
+        const uchar2 b = bins[i];
+        const float a0 = m.x ? v.x : 0.0f, a1 = m.y ? v.y : 0.0f;
+        float2 *out = (float2 *)(vol + real_off(i, W, Wp));
+        for (int r = 0; r < N; ++r) {
+            const bool on0 = (b.x == r) || (b.x == SE2N_BIN_FLAT);
+            const bool on1 = (b.y == r) || (b.y == SE2N_BIN_FLAT);
+            out[(long long)r * (plane / 2)] = make_float2(on0 ? a0 : 0.0f, on1 ? a1 : 0.0f);
+        }
+    }
+}
+
+__global__ void k_mix_r(float *__restrict__ vol, const float2 *__restrict__ f, const uchar2 *__restrict__ mask,
+                        const uchar2 *__restrict__ bins, long long npairs, int W, int Wp, long long plane, int N,
+                        float scale, float eps, float guard) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npairs;
+         i += (long long)gridDim.x * blockDim.x) {
+        float2 *col = (float2 *)(vol + real_off(i, W, Wp));
+        const long long ps = plane / 2;
+        float ht0 = -INFINITY, ht1 = -INFINITY;
+        for (int r = 0; r < N; ++r) {
+            const float2 v = col[(long long)r * ps];
+            ht0 = fmaxf(ht0, v.x * scale);
+            ht1 = fmaxf(ht1, v.y * scale);
+        }
+        const float2 fv = f[i];
+        const uchar2 m = mask[i];
+        const uchar2 b = bins[i];
+        const float a0 = m.x ? fv.x : 0.0f, a1 = m.y ? fv.y : 0.0f;
+        const float h00 = (b.x == SE2N_BIN_FLAT) ? a0 : fmaxf(a0, 0.0f);
+        const float h01 = (b.y == SE2N_BIN_FLAT) ? a1 : fmaxf(a1, 0.0f);
+        for (int r = 0; r < N; ++r) {
+            const float2 v = col[(long long)r * ps];
+            const float l0 = ((b.x == r) || (b.x == SE2N_BIN_FLAT)) ? a0 : 0.0f;
+            const float l1 = ((b.y == r) || (b.y == SE2N_BIN_FLAT)) ? a1 : 0.0f;
+            col[(long long)r * ps] = make_float2(sr_value(v.x * scale, h00, ht0, l0, m.x != 0, eps, guard),
+                                                 sr_value(v.y * scale, h01, ht1, l1, m.y != 0, eps, guard));
+        }
+    }
+}
+
+__global__ void k_project_r(const float *__restrict__ vol, long long npairs, int W, int Wp, long long plane, int N,
+                            float scale, int proj, const float2 *__restrict__ f, const uchar2 *__restrict__ mask,
+                            float2 *__restrict__ out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npairs;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float2 *col = (const float2 *)(vol + real_off(i, W, Wp));
+        const long long ps = plane / 2;
+        float a0, a1;
+        if (proj == SE2N_PROJ_MAX) {
+            a0 = -INFINITY;
+            a1 = -INFINITY;
+            for (int r = 0; r < N; ++r) {
+                const float2 v = col[(long long)r * ps];
+                a0 = fmaxf(a0, v.x * scale);
+                a1 = fmaxf(a1, v.y * scale);
+            }
+        } else {
+            a0 = 0.0f;
+            a1 = 0.0f;
+            for (int r = 0; r < N; ++r) {
+                const float2 v = col[(long long)r * ps];
+                a0 += v.x * scale;
+                a1 += v.y * scale;
+            }
+            a0 /= (float)N;
+            a1 /= (float)N;
+        }
+        if (mask) {
+            const uchar2 m = mask[i];
+            const float2 fv = f[i];
+            if (m.x) a0 = fv.x;
+            if (m.y) a1 = fv.y;
+        }
+        out[i] = make_float2(a0, a1);
+    }
+}
+
 __global__ void k_scale(float4 *__restrict__ v, long long n4, float s) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4;
          i += (long long)gridDim.x * blockDim.x) {
@@ -253,6 +349,33 @@ cudaError_t se2n_launch_project(const float2 *vol, long long HW, int N, float sc
     const long long n = HW / 2;
     k_project<<<grid_for(n), kBlock, 0, s>>>((const float4 *)vol, n, N, scale, proj, (const float2 *)f,
                                              (const uchar2 *)mask, (float2 *)out);
+    return cudaGetLastError();
+}
+
+cudaError_t se2n_launch_lift_r(const float *f, const uint8_t *mask, const uint8_t *bins, float *vol, int H, int W,
+                               int N, cudaStream_t s) {
+    const long long n = (long long)H * W / 2;
+    const int Wp = W + 2;
+    k_lift_r<<<grid_for(n), kBlock, 0, s>>>((const float2 *)f, (const uchar2 *)mask, (const uchar2 *)bins, vol, n, W,
+                                            Wp, (long long)H * Wp, N);
+    return cudaGetLastError();
+}
+
+cudaError_t se2n_launch_mix_r(float *vol, const float *f, const uint8_t *mask, const uint8_t *bins, int H, int W,
+                              int N, float scale, float eps, float guard, cudaStream_t s) {
+    const long long n = (long long)H * W / 2;
+    const int Wp = W + 2;
+    k_mix_r<<<grid_for(n), kBlock, 0, s>>>(vol, (const float2 *)f, (const uchar2 *)mask, (const uchar2 *)bins, n, W, Wp,
+                                           (long long)H * Wp, N, scale, eps, guard);
+    return cudaGetLastError();
+}
+
+cudaError_t se2n_launch_project_r(const float *vol, int H, int W, int N, float scale, int proj, const float *f,
+                                  const uint8_t *mask, float *out, cudaStream_t s) {
+    const long long n = (long long)H * W / 2;
+    const int Wp = W + 2;
+    k_project_r<<<grid_for(n), kBlock, 0, s>>>(vol, n, W, Wp, (long long)H * Wp, N, scale, proj, (const float2 *)f,
+                                               (const uchar2 *)mask, (float2 *)out);
     return cudaGetLastError();
 }
 

@@ -5,16 +5,17 @@
 #include "se2n_internal.h"
 
 struct BatchImage {
-    float2 *vol;       // [N][H][W] complex, the image's transformed volume
-    long long HW;
+    float2 *vol;       // [N][H][Wc] complex, the image's transformed volume
+    long long HW;      // H * Wc frequencies per plane
     int H, W, N;
+    int Wc;            // stored columns: W, or W/2 + 1 for the Hermitian half
     int table;         // offset of the image's angle table (cos[N] then sin[N]) in the table array
 };
 
 struct BatchItem {
     int image;         // index into the BatchImage array
     int count;         // frequencies in this item
-    long long first;   // first frequency index k*W + l
+    long long first;   // first frequency index k*Wc + l
 };
 
 int se2n_batch_configs();

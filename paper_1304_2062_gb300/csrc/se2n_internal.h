@@ -17,6 +17,12 @@ struct se2n_plan {
     cufftHandle fft_vol;   // batch N, [H][W], C2C, in place
     cufftHandle fft_one;   // one plane
     cufftHandle fft_two;   // batch 2 (gradient components)
+    // Hermitian-half path (created on first use): the real volume is [N][H][W+2]
+    // floats, its spectrum [N][H][Wc] complex in the same memory, Wc = W/2 + 1
+    int Wc;
+    cufftHandle fft_r2c;   // batch N, R2C, in place
+    cufftHandle fft_c2r;   // batch N, C2R, in place
+    bool half_ready;
     float2 *spec;          // [3][H][W]: image spectrum, x and y gradient
     unsigned int *gmax;    // one word: max |grad|^2 as float bits
     uint8_t *bins;         // [H][W] bins computed by se2n_inpaint
@@ -52,8 +58,9 @@ struct StepParams {
 // read through the constant bank, so the angle tables cost no loads).
 struct DiffuseArgs {
     float2 *vol;
-    long long HW;
+    long long HW;  // frequencies per plane (the plane's stride in complex elements)
     int H, W;
+    int Wc;        // stored columns per row: W, or W/2 + 1 for the Hermitian half
     StepParams sp;
     float cs[SE2N_MAX_N];
     float sn[SE2N_MAX_N];
@@ -93,6 +100,14 @@ cudaError_t se2n_launch_mix(float2 *vol, const float *f, const uint8_t *mask, co
                             long long HW, int N, float scale, float eps, float guard, cudaStream_t s);
 // out = max_r (or mean_r) of scale * Re vol[r]; where mask != null, pixels
 // with mask != 0 take f instead (the inpainted image).
+// The same stages on the real volume of the Hermitian-half path: planes of H
+// rows of W + 2 floats (in-place R2C layout).
+cudaError_t se2n_launch_lift_r(const float *f, const uint8_t *mask, const uint8_t *bins, float *vol, int H, int W,
+                               int N, cudaStream_t s);
+cudaError_t se2n_launch_mix_r(float *vol, const float *f, const uint8_t *mask, const uint8_t *bins, int H, int W,
+                              int N, float scale, float eps, float guard, cudaStream_t s);
+cudaError_t se2n_launch_project_r(const float *vol, int H, int W, int N, float scale, int proj, const float *f,
+                                  const uint8_t *mask, float *out, cudaStream_t s);
 cudaError_t se2n_launch_project(const float2 *vol, long long HW, int N, float scale, int proj, const float *f,
                                 const uint8_t *mask, float *out, cudaStream_t s);
 cudaError_t se2n_launch_scale(float2 *vol, long long count, float scale, cudaStream_t s);

@@ -78,6 +78,7 @@ class se2n_params(ctypes.Structure):
         ("guard", ctypes.c_double),
         ("diffuse_flags", ctypes.c_int),
         ("reinject", ctypes.c_int),
+        ("full_spectrum", ctypes.c_int),
     ]
 
 

@@ -38,20 +38,20 @@ def _gpu_inpaint(f32, mask, bins, prm, conv=0, tune=None):
     return got
 
 
-def _params(p: oracle.Params, flags=0):
+def _params(p: oracle.Params, flags=0, full=0):
     return se2n.se2n_params_default(N=p.N, beta=p.beta, T=p.T, steps=p.steps, rounds=p.rounds, eps=p.eps,
                                     sigma_smooth=p.sigma, flat_tol=p.flat_tol, proj=p.proj,
                                     final_mix=p.final_mix, guard=p.guard, diffuse_flags=flags,
-                                    reinject=p.reinject)
+                                    reinject=p.reinject, full_spectrum=full)
 
 
-def _compare(w, p, conv=0, flags=0, tune=None):
+def _compare(w, p, conv=0, flags=0, tune=None, full=0):
     f32 = w.f.astype(np.float32)
     f64 = f32.astype(np.float64)
     bins = oracle.orient(f64, w.mask, p.N, p.sigma, conv, p.flat_tol)["bins"]
     p.angle_conv = conv
     ref = oracle.inpaint(f64, w.mask, p, bins=bins)["out"]
-    got = _gpu_inpaint(f32, w.mask, bins, _params(p, flags), conv, tune)
+    got = _gpu_inpaint(f32, w.mask, bins, _params(p, flags, full), conv, tune)
     mx = np.abs(got - ref).max() / np.abs(f64).max()
     r2 = rel_l2(got, ref)
     print(f"{w.H}x{w.W} N={p.N} S={p.steps} R={p.rounds}: max-abs/max|f| {mx:.2e}, rel-L2 {r2:.2e}")
@@ -72,7 +72,8 @@ def test_reduced_512_geometry_three_rounds():
     _compare(w, oracle.Params(N=32, beta=0.25, T=6.0, steps=100, rounds=3))
 
 
-@pytest.mark.parametrize("variant", ["mean", "final_mix", "conv1", "fp64", "N64", "P4", "nonsquare", "reinject"])
+@pytest.mark.parametrize("variant", ["mean", "final_mix", "conv1", "fp64", "N64", "P4", "nonsquare", "reinject",
+                                     "full_spectrum", "full_spectrum_nonsquare"])
 def test_variants(variant):
     w = synth.workload_512(H=96, W=96, steps=60, rounds=3)
     p = oracle.Params(N=32, beta=0.25, T=6.0, steps=60, rounds=3)
@@ -93,10 +94,29 @@ def test_variants(variant):
         w = synth.workload_512(H=64, W=160, steps=60, rounds=3)
     elif variant == "reinject":
         p.reinject = 1
-    got = _compare(w, p, conv, flags, tune)
+    full = 1 if variant.startswith("full_spectrum") else 0
+    if variant == "full_spectrum_nonsquare":
+        w = synth.workload_512(H=64, W=160, steps=60, rounds=3)
+    got = _compare(w, p, conv, flags, tune, full)
     if variant == "reinject":
         k = w.mask != 0
         np.testing.assert_array_equal(got[k], w.f.astype(np.float32)[k])
+
+
+@pytest.mark.parametrize("H,W,conv", [(96, 96, 0), (64, 160, 0), (128, 66, 1)])
+def test_hermitian_half_equals_full_spectrum(H, W, conv):
+    """The Hermitian-half path (R2C transforms, frequencies l <= W/2) and the
+    full complex path are the same method: they agree to FP32 rounding of the
+    transforms, far inside the oracle tolerance."""
+    w = synth.workload_512(H=H, W=W, steps=60, rounds=3)
+    p = oracle.Params(N=32, beta=0.25, T=6.0, steps=60, rounds=3)
+    bins = oracle.orient(w.f.astype(np.float32).astype(np.float64), w.mask, p.N, p.sigma, conv, p.flat_tol)["bins"]
+    f32 = w.f.astype(np.float32)
+    half = _gpu_inpaint(f32, w.mask, bins, _params(p, 0, 0), conv)
+    full = _gpu_inpaint(f32, w.mask, bins, _params(p, 0, 1), conv)
+    r = rel_l2(half, full)
+    print(f"{H}x{W} conv {conv}: half vs full rel-L2 {r:.2e}")
+    assert r <= 1e-6
 
 
 def test_table1_parameters_in_pixel_units():
