@@ -267,10 +267,82 @@ cudaError_t launch_halo(const __nv_bfloat16 *A, int B, int H, int W, int C, cons
     return cudaGetLastError();
 }
 
+// Weight gradient (k_wgrad_tma): x [B][H][W][C] and gz [B][H][W][Cout] NHWC, dw
+// [Cout][9 C] FP32 (accumulated).
+template <int BN, int MG, int NG>
+cudaError_t launch_wgrad(const __nv_bfloat16 *x, int B, int H, int W, int C, const __nv_bfloat16 *gz, float *dw,
+                         cudaStream_t s) {
+    const int bkx = W >= 64 ? 64 : W;
+    if (bkx < 16 || bkx % 16 || W % bkx || C % MG) return cudaErrorNotSupported;
+    auto enc = encoder();
+    const int nsm = sm_count();
+    int *err = fault_ptr();
+    if (!enc || nsm <= 0 || !err) return cudaErrorNotSupported;
+    CUtensorMap mx, mg;
+    {
+        const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+        const cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2, (cuuint64_t)H * W * C * 2};
+        const cuuint32_t box[4] = {(cuuint32_t)MG, (cuuint32_t)bkx, 1, 1};
+        const cuuint32_t es[4] = {1, 1, 1, 1};
+        if (enc(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)x, dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, MG == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    {
+        const cuuint64_t dims[4] = {(cuuint64_t)BN, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+        const cuuint64_t strides[3] = {(cuuint64_t)BN * 2, (cuuint64_t)W * BN * 2, (cuuint64_t)H * W * BN * 2};
+        const cuuint32_t box[4] = {(cuuint32_t)NG, (cuuint32_t)bkx, 1, 1};
+        const cuuint32_t es[4] = {1, 1, 1, 1};
+        if (enc(&mg, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)gz, dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, NG == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    tma::WgradGeo g;
+    g.B = B;
+    g.H = H;
+    g.W = W;
+    g.C = C;
+    g.Cout = BN;
+    g.bkx = bkx;
+    g.xblocks = W / bkx;
+    g.kblocks = B * H * g.xblocks;
+    g.mtiles = (9 * C + 127) / 128;
+    int ks = (2 * nsm + g.mtiles - 1) / g.mtiles;
+    if (ks > g.kblocks) ks = g.kblocks;
+    if (ks < 1) ks = 1;
+    g.ksplit = ks;
+    g.units = g.mtiles * ks;
+    const int stage = (128 + BN) * bkx * 2;
+    int S = 196608 / stage;
+    if (S > 8) S = 8;
+    const int smem = 1024 + S * stage + 256;
+    auto *fn = &tma::k_wgrad_tma<BN, MG, NG>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const int grid = g.units < nsm ? g.units : nsm;
+    fn<<<grid, 192, smem, s>>>(mx, mg, g, dw, S, err);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 namespace se2n {
 namespace nn {
+
+cudaError_t conv_wgrad_tma(const __nv_bfloat16 *x, int B, int H, int W, int C, const __nv_bfloat16 *gz, int Cout,
+                           float *dw, cudaStream_t s) {
+    const bool m64 = C % 64 == 0;
+    switch (Cout) {
+        case 32: return m64 ? cudaErrorNotSupported : launch_wgrad<32, 32, 32>(x, B, H, W, C, gz, dw, s);
+        case 64: return m64 ? launch_wgrad<64, 64, 64>(x, B, H, W, C, gz, dw, s)
+                            : launch_wgrad<64, 32, 64>(x, B, H, W, C, gz, dw, s);
+        case 128: return m64 ? launch_wgrad<128, 64, 64>(x, B, H, W, C, gz, dw, s) : cudaErrorNotSupported;
+        case 256: return m64 ? launch_wgrad<256, 64, 64>(x, B, H, W, C, gz, dw, s) : cudaErrorNotSupported;
+        default: return cudaErrorNotSupported;
+    }
+}
 
 cudaError_t tma_fault(int *host_flag, bool reset) {
     cudaError_t e = cudaMemcpyFromSymbol(host_flag, g_tma_fault, sizeof(int));

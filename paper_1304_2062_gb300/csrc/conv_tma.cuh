@@ -500,6 +500,251 @@ __global__ void __launch_bounds__(192, 1)
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Weight gradient: dW[co][tap * C + ci] += sum over pixels p of
+// In[p shifted by tap][ci] * gz[p][co], as D[m][n] with m = tap * C + ci
+// (rows, M = 128 per tile), n = co (N = Cout), K = pixels. Both operands come
+// from NHWC tensors, so they are MN-major in shared memory: a TMA box of MG
+// channels x BKX pixels of one image row lands as BKX rows (one per pixel,
+// the K index) of MG contiguous channels, the MN-major swizzled layout
+// (MG = 64: 128-byte rows and swizzle; MG = 32: 64-byte). The tap shift
+// moves the pixel coordinates, never the innermost (channel) one; rows of
+// the M tile past 9 C are zero-filled by a box that starts out of range.
+// A unit of work is (M tile, a range of pixel blocks); its partial D is
+// added to dW with FP32 atomics by the epilogue, which overlaps the next
+// unit's MMAs (two accumulators).
+// ---------------------------------------------------------------------------
+
+struct WgradGeo {
+    int B, H, W, C, Cout;
+    int bkx;            // pixels per K block (one image row segment), 16 / 32 / 64
+    int xblocks;        // W / bkx
+    int kblocks;        // B * H * xblocks
+    int mtiles;         // ceil(9 C / 128)
+    int ksplit;         // pixel ranges per M tile
+    int units;          // mtiles * ksplit
+};
+
+template <int MG, int NG>
+struct WgCfg {
+    static_assert((MG == 32 || MG == 64) && (NG == 32 || NG == 64), "32- or 64-channel groups");
+    static constexpr uint64_t LAYOUT_A = MG == 64 ? 2 : 4, LAYOUT_B = NG == 64 ? 2 : 4;
+    static constexpr uint32_t SBO_A = 8 * MG * 2, SBO_B = 8 * NG * 2;
+};
+
+// MN-major matrix descriptor: leading byte offset = stride between MN groups,
+// stride byte offset = stride between 8-row groups along K.
+__device__ __forceinline__ uint64_t sdesc_mn(uint32_t saddr, uint32_t lbo, uint32_t sbo, uint64_t layout) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= layout << 61;
+    return d;
+}
+
+// kind::f16, D FP32, A and B BF16, both MN-major.
+template <int N>
+__device__ __forceinline__ constexpr uint32_t idesc_bf16_mn() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(128 >> 4) << 24);
+}
+
+template <int BN, int MG, int NG>
+__global__ void __launch_bounds__(192, 1)
+    k_wgrad_tma(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapG, const WgradGeo g,
+                float *dw, int S, int *err) {
+    using Cf = WgCfg<MG, NG>;
+    constexpr int ACC = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+    constexpr int TMEM_COLS = 2 * ACC;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    const int bkx = g.bkx;
+    const uint32_t A_BYTES = 128u * bkx * 2, B_BYTES = (uint32_t)BN * bkx * 2, STAGE = A_BYTES + B_BYTES;
+    const uint32_t bar_full = base + S * STAGE;
+    const uint32_t bar_empty = bar_full + 8 * S;
+    const uint32_t bar_afull = bar_empty + 8 * S;
+    const uint32_t bar_aempty = bar_afull + 16;
+    const uint32_t tmem_slot = bar_aempty + 16;
+    volatile int *abort = (volatile int *)(smem_raw + (tmem_slot + 4 - raw));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m_total = 9 * g.C;
+
+    if (threadIdx.x == 0) {
+        *abort = *(volatile int *)err;
+        for (int s = 0; s < S; ++s) {
+            tc::mbar_init(bar_full + 8 * s, 1);
+            tc::mbar_init(bar_empty + 8 * s, 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            tc::mbar_init(bar_afull + 8 * a, 1);
+            tc::mbar_init(bar_aempty + 8 * a, 4);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"((uint64_t)&mapX) : "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"((uint64_t)&mapG) : "memory");
+    }
+    __syncthreads();
+    if (*abort) return;
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(tmem_slot),
+                     "r"((uint32_t)TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    uint32_t tmem_base;
+    asm volatile("ld.shared.u32 %0, [%1];\n" : "=r"(tmem_base) : "r"(tmem_slot));
+
+    // unit u = mt * ksplit + ks covers pixel blocks [kb0, kb1) of M tile mt
+    auto unit_range = [&](int u, int &mt, int &kb0, int &kb1) {
+        mt = u / g.ksplit;
+        const int ks = u - mt * g.ksplit;
+        const int per = (g.kblocks + g.ksplit - 1) / g.ksplit;
+        kb0 = ks * per;
+        kb1 = min(g.kblocks, kb0 + per);
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer ----------------
+            int s = 0;
+            uint32_t ph = 0;
+            bool ok = true;
+            for (int u = blockIdx.x; u < g.units && ok; u += gridDim.x) {
+                int mt, kb0, kb1;
+                unit_range(u, mt, kb0, kb1);
+                for (int kb = kb0; kb < kb1; ++kb) {
+                    const int xb = kb % g.xblocks;
+                    const int r = kb / g.xblocks;
+                    const int y = r % g.H, b = r / g.H;
+                    const int x0 = xb * bkx;
+                    if (!tc::mbar_wait(bar_empty + 8 * s, ph ^ 1u, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t sa = base + s * STAGE, sb = sa + A_BYTES;
+                    arrive_expect_tx(bar_full + 8 * s, STAGE);
+#pragma unroll
+                    for (int gi = 0; gi < 128 / MG; ++gi) {
+                        const int m0 = mt * 128 + gi * MG;
+                        int c0 = g.C, dy = 0, dx = 0;  // past the last row: a box entirely out of range (zeros)
+                        if (m0 < m_total) {
+                            const int tap = m0 / g.C;
+                            c0 = m0 - tap * g.C;
+                            dy = tap / 3 - 1;
+                            dx = tap % 3 - 1;
+                        }
+                        tma_load_4d(sa + gi * (uint32_t)(bkx * MG * 2), &mapX, c0, x0 + dx, y + dy, b,
+                                    bar_full + 8 * s);
+                    }
+#pragma unroll
+                    for (int gi = 0; gi < BN / NG; ++gi)
+                        tma_load_4d(sb + gi * (uint32_t)(bkx * NG * 2), &mapG, gi * NG, x0, y, b, bar_full + 8 * s);
+                    if (++s == S) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
+                }
+            }
+            if (!ok) {
+                const long long t0 = clock64();
+                while (clock64() - t0 < 200000LL) {
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer ----------------
+            constexpr uint32_t IDESC = idesc_bf16_mn<BN>();
+            const uint32_t lbo_a = (uint32_t)(bkx * MG * 2), lbo_b = (uint32_t)(bkx * NG * 2);
+            int s = 0, acc = 0;
+            uint32_t ph = 0, aph = 0;
+            bool ok = true;
+            uint32_t last_bar = 0, last_par = 0;
+            for (int u = blockIdx.x; u < g.units && ok; u += gridDim.x) {
+                int mt, kb0, kb1;
+                unit_range(u, mt, kb0, kb1);
+                if (!tc::mbar_wait(bar_aempty + 8 * acc, aph ^ 1u, abort)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const uint32_t d = tmem_base + (uint32_t)(acc * ACC);
+                bool first = true;
+                for (int kb = kb0; kb < kb1; ++kb) {
+                    if (!tc::mbar_wait(bar_full + 8 * s, ph, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                    const uint32_t sa = base + s * STAGE, sb = sa + A_BYTES;
+                    for (int kk = 0; kk < bkx / 16; ++kk) {
+                        // 16 pixels = two 8-row groups along K
+                        tc::mma_f16(d, sdesc_mn(sa + kk * 2 * Cf::SBO_A, lbo_a, Cf::SBO_A, Cf::LAYOUT_A),
+                                    sdesc_mn(sb + kk * 2 * Cf::SBO_B, lbo_b, Cf::SBO_B, Cf::LAYOUT_B), IDESC,
+                                    first ? 0u : 1u);
+                        first = false;
+                    }
+                    tc::mma_commit(bar_empty + 8 * s);
+                    last_bar = bar_empty + 8 * s;
+                    last_par = ph;
+                    if (++s == S) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                tc::mma_commit(bar_afull + 8 * acc);
+                if (++acc == 2) {
+                    acc = 0;
+                    aph ^= 1u;
+                }
+            }
+            if (!ok && last_bar) tc::mbar_wait(last_bar, last_par, nullptr);
+        }
+    } else {
+        // ---------------- epilogue (warps 2..5): atomic adds into dW ----------------
+        const int q = warp & 3;
+        int acc = 0;
+        uint32_t aph = 0;
+        for (int u = blockIdx.x; u < g.units; u += gridDim.x) {
+            int mt, kb0, kb1;
+            unit_range(u, mt, kb0, kb1);
+            if (!tc::mbar_wait(bar_afull + 8 * acc, aph, abort)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const int m = mt * 128 + q * 32 + lane;
+            const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * ACC);
+#pragma unroll 1
+            for (int j0 = 0; j0 < BN; j0 += 16) {
+                uint32_t v[16];
+                tc::tmem_ld16(taddr + (uint32_t)j0, v);
+                if (m < m_total && kb1 > kb0) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) atomicAdd(dw + (long long)(j0 + i) * m_total + m, __uint_as_float(v[i]));
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            __syncwarp();
+            if (lane == 0) arrive(bar_aempty + 8 * acc);
+            if (++acc == 2) {
+                acc = 0;
+                aph ^= 1u;
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && *abort) atomicExch(err, 1);
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem_base),
+                     "r"((uint32_t)TMEM_COLS));
+    }
+}
+
 }  // namespace tma
 }  // namespace nn
 }  // namespace se2n

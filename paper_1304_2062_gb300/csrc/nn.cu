@@ -236,12 +236,33 @@ __global__ void k_transpose_dgrad(const __nv_bfloat16 *w, __nv_bfloat16 *wt, int
     }
 }
 
-// Column sums of a [P][C] bf16 matrix into db[C] (bias gradients).
-__global__ void k_colsum(const __nv_bfloat16 *g, long long P, int C, float *db) {
-    const int c = threadIdx.x;  // blockDim.x == C (<= 256)
-    float s = 0.0f;
-    for (long long p = blockIdx.x; p < P; p += gridDim.x) s += __bfloat162float(g[p * C + c]);
-    atomicAdd(db + c, s);
+// Column sums of a [P][C] bf16 matrix into db[C] (bias gradients): each
+// thread sums 8 channels (one 16-byte load) of every (256 / (C/8))-th row,
+// the block combines its partial sums in shared memory, one atomic per
+// channel per block.
+__global__ void __launch_bounds__(256) k_colsum(const __nv_bfloat16 *g, long long P, int C, float *db) {
+    __shared__ float part[256][8];
+    const int groups = C / 8;                 // 4..32
+    const int rows = blockDim.x / groups;     // rows per block step
+    const int cg = threadIdx.x % groups, rr = threadIdx.x / groups;
+    float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (rr < rows) {
+        for (long long p = (long long)blockIdx.x * rows + rr; p < P; p += (long long)gridDim.x * rows) {
+            const uint4 v = *(const uint4 *)(g + p * C + cg * 8);
+            const __nv_bfloat16 *h = (const __nv_bfloat16 *)&v;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) s[k] += __bfloat162float(h[k]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) part[threadIdx.x][k] = s[k];
+    __syncthreads();
+    if (threadIdx.x < C) {
+        const int c8 = threadIdx.x / 8, k = threadIdx.x % 8;
+        float t = 0.0f;
+        for (int r = 0; r < rows; ++r) t += part[r * groups + c8][k];
+        atomicAdd(db + threadIdx.x, t);
+    }
 }
 
 // Input packing: x[b][y][x][0] = f*(mask!=0), [1] = mask, [2..7] = 0.
@@ -366,43 +387,67 @@ __global__ void __launch_bounds__(256) k_conv0(const float *f, const uint8_t *ma
     }
 }
 
-// Gradient into an encoder output e: g_e = (pool_backward(g_pooled) + g_skip) * (e > 0).
+// Gradient into an encoder output e: g_e = (pool_backward(g_pooled) + g_skip) * (e > 0),
+// 8 channels (16 bytes) per thread; e has lde channels per pixel.
 __global__ void k_pool_bwd_add_mask(const __nv_bfloat16 *gp, const __nv_bfloat16 *gskip, const __nv_bfloat16 *e,
                                     int lde, __nv_bfloat16 *ge, int B, int H, int W, int C) {
-    const long long total = (long long)B * H * W * C;
-    const int Ho = H / 2, Wo = W / 2;
+    const int C8 = C / 8, Ho = H / 2, Wo = W / 2;
+    const long long total = (long long)B * H * W * C8;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        long long t = i / C;
-        const int x = (int)(t % W);
-        t /= W;
+        const int c = (int)(i % C8) * 8;
+        const long long pix = i / C8;
+        const int x = (int)(pix % W);
+        const long long t = pix / W;
         const int y = (int)(t % H);
-        const int b = (int)(t / H);
-        float v = 0.25f * __bfloat162float(gp[(((long long)b * Ho + y / 2) * Wo + x / 2) * C + c]);
-        if (gskip) v += __bfloat162float(gskip[i]);
-        if (!(__bfloat162float(e[(i / C) * lde + c]) > 0.0f)) v = 0.0f;
-        ge[i] = __float2bfloat16_rn(v);
+        const long long b = t / H;
+        const uint4 vp = *(const uint4 *)(gp + ((b * Ho + y / 2) * Wo + x / 2) * C + c);
+        const uint4 ve = *(const uint4 *)(e + pix * lde + c);
+        uint4 vs = make_uint4(0, 0, 0, 0);
+        if (gskip) vs = *(const uint4 *)(gskip + pix * C + c);
+        const __nv_bfloat16 *hp = (const __nv_bfloat16 *)&vp, *he = (const __nv_bfloat16 *)&ve,
+                            *hs = (const __nv_bfloat16 *)&vs;
+        __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            float v = 0.25f * __bfloat162float(hp[k]);
+            if (gskip) v += __bfloat162float(hs[k]);
+            if (!(__bfloat162float(he[k]) > 0.0f)) v = 0.0f;
+            o[k] = __float2bfloat16_rn(v);
+        }
+        *(uint4 *)(ge + pix * C + c) = *(const uint4 *)o;
     }
 }
 
 // Gradient into a half-resolution tensor d that was upsampled (nearest):
-// g_d = (sum over the 2x2 block of g_up) * (d > 0).
+// g_d = (sum over the 2x2 block of g_up) * (d > 0), 8 channels per thread.
 __global__ void k_up_bwd_mask(const __nv_bfloat16 *gup, const __nv_bfloat16 *d, __nv_bfloat16 *gd, int B, int Hl,
                               int Wl, int C) {
-    const long long total = (long long)B * Hl * Wl * C;
-    const int H = 2 * Hl, W = 2 * Wl;
+    const int C8 = C / 8, H = 2 * Hl, W = 2 * Wl;
+    const long long total = (long long)B * Hl * Wl * C8;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        long long t = i / C;
-        const int x = (int)(t % Wl);
-        t /= Wl;
+        const int c = (int)(i % C8) * 8;
+        const long long pix = i / C8;
+        const int x = (int)(pix % Wl);
+        const long long t = pix / Wl;
         const int y = (int)(t % Hl);
-        const int b = (int)(t / Hl);
-        const long long base = (((long long)b * H + 2 * y) * W + 2 * x) * C + c;
-        float v = __bfloat162float(gup[base]) + __bfloat162float(gup[base + C]) +
-                  __bfloat162float(gup[base + (long long)W * C]) + __bfloat162float(gup[base + (long long)W * C + C]);
-        if (!(__bfloat162float(d[i]) > 0.0f)) v = 0.0f;
-        gd[i] = __float2bfloat16_rn(v);
+        const long long b = t / Hl;
+        const long long base = ((b * H + 2 * y) * W + 2 * x) * C + c;
+        const uint4 q0 = *(const uint4 *)(gup + base), q1 = *(const uint4 *)(gup + base + C);
+        const uint4 q2 = *(const uint4 *)(gup + base + (long long)W * C);
+        const uint4 q3 = *(const uint4 *)(gup + base + (long long)W * C + C);
+        const uint4 vd = *(const uint4 *)(d + pix * C + c);
+        const __nv_bfloat16 *a = (const __nv_bfloat16 *)&q0, *b1 = (const __nv_bfloat16 *)&q1,
+                            *c2 = (const __nv_bfloat16 *)&q2, *d3 = (const __nv_bfloat16 *)&q3,
+                            *hd = (const __nv_bfloat16 *)&vd;
+        __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            float v = __bfloat162float(a[k]) + __bfloat162float(b1[k]) + __bfloat162float(c2[k]) +
+                      __bfloat162float(d3[k]);
+            if (!(__bfloat162float(hd[k]) > 0.0f)) v = 0.0f;
+            o[k] = __float2bfloat16_rn(v);
+        }
+        *(uint4 *)(gd + pix * C + c) = *(const uint4 *)o;
     }
 }
 
@@ -418,42 +463,61 @@ __global__ void k_head(const __nv_bfloat16 *d, const float *w, const float *b, c
 
 // Loss L = mean over pixels of (out - target)^2 and its gradient at the
 // head, back into d: g_d[p][c] = g_out[p] w[c] (d > 0); also the head's
-// parameter gradients.
-__global__ void k_loss_head_bwd(const float *out, const float *target, const __nv_bfloat16 *d, const float *w,
-                                __nv_bfloat16 *gd, float *gw, float *gb, float *loss, long long P, int C, float inv_n) {
-    __shared__ float sgw[256];
-    __shared__ float sgb, sloss;
-    if (threadIdx.x < C) sgw[threadIdx.x] = 0.0f;
-    if (threadIdx.x == 0) {
-        sgb = 0.0f;
-        sloss = 0.0f;
-    }
-    __syncthreads();
+// parameter gradients. One pixel's 32 channels per thread (four 16-byte
+// loads and stores); the partial sums are reduced across the warp with
+// shuffles, then across the block in shared memory, one atomic each.
+__global__ void __launch_bounds__(256) k_loss_head_bwd(const float *out, const float *target,
+                                                       const __nv_bfloat16 *d, const float *w, __nv_bfloat16 *gd,
+                                                       float *gw, float *gb, float *loss, long long P, int C,
+                                                       float inv_n) {
+    __shared__ float sgw[8][33];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     float lg = 0.0f, lb = 0.0f;
-    float lw[32];
+    float lw[32], wc[32];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) lw[c] = 0.0f;
+    for (int c = 0; c < 32; ++c) {
+        lw[c] = 0.0f;
+        wc[c] = w[c];
+    }
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
         const float r = out[p] - target[p];
         lg += r * r;
         const float go = 2.0f * r * inv_n;
         lb += go;
 #pragma unroll
-        for (int c = 0; c < 32; ++c) {
-            const float dv = __bfloat162float(d[p * C + c]);
-            lw[c] = fmaf(go, dv, lw[c]);
-            gd[p * C + c] = __float2bfloat16_rn(dv > 0.0f ? go * w[c] : 0.0f);
+        for (int q = 0; q < 4; ++q) {
+            const uint4 v = *(const uint4 *)(d + p * C + 8 * q);
+            const __nv_bfloat16 *h = (const __nv_bfloat16 *)&v;
+            __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const float dv = __bfloat162float(h[k]);
+                lw[8 * q + k] = fmaf(go, dv, lw[8 * q + k]);
+                o[k] = __float2bfloat16_rn(dv > 0.0f ? go * wc[8 * q + k] : 0.0f);
+            }
+            *(uint4 *)(gd + p * C + 8 * q) = *(const uint4 *)o;
         }
     }
-    atomicAdd(&sloss, lg);
-    atomicAdd(&sgb, lb);
 #pragma unroll
-    for (int c = 0; c < 32; ++c) atomicAdd(&sgw[c], lw[c]);
+    for (int c = 0; c < 32; ++c) {
+        float v = lw[c];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sgw[wid][c] = v;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lg += __shfl_xor_sync(0xffffffffu, lg, o);
+        lb += __shfl_xor_sync(0xffffffffu, lb, o);
+    }
+    if (lane == 0) {
+        sgw[wid][32] = lb;
+        atomicAdd(loss, lg * inv_n);
+    }
     __syncthreads();
-    if (threadIdx.x < C) atomicAdd(gw + threadIdx.x, sgw[threadIdx.x]);
-    if (threadIdx.x == 0) {
-        atomicAdd(gb, sgb);
-        atomicAdd(loss, sloss * inv_n);
+    if (threadIdx.x < 33) {
+        float t = 0.0f;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sgw[k][threadIdx.x];
+        if (threadIdx.x < 32) atomicAdd(gw + threadIdx.x, t);
+        else atomicAdd(gb, t);
     }
 }
 
@@ -642,6 +706,10 @@ cudaError_t conv_backward_data(const __nv_bfloat16 *gz, int B, int H, int W, int
 
 cudaError_t conv_backward_weight(const __nv_bfloat16 *gz, int B, int H, int W, int Cout, const __nv_bfloat16 *in,
                                  const __nv_bfloat16 *lo, int C1, int Cin, float *dw, cudaStream_t s) {
+    if (!lo) {
+        const cudaError_t e = conv_wgrad_tma(in, B, H, W, Cin, gz, Cout, dw, s);
+        if (e != cudaErrorNotSupported) return e;
+    }
     const int P = B * H * W;
     GradOutMLoader la{gz, Cout, P};
     InNLoader lb{{{B, H, W}, in, lo, Cin, C1, P, 9 * Cin, 0}, P};
@@ -658,7 +726,7 @@ cudaError_t conv_backward_weight(const __nv_bfloat16 *gz, int B, int H, int W, i
 }
 
 cudaError_t colsum(const __nv_bfloat16 *g, long long P, int C, float *db, cudaStream_t s) {
-    k_colsum<<<1024, C, 0, s>>>(g, P, C, db);
+    k_colsum<<<1024, 256, 0, s>>>(g, P, C, db);
     return cudaGetLastError();
 }
 
@@ -692,13 +760,13 @@ cudaError_t conv0_direct(const float *f, const uint8_t *mask, const __nv_bfloat1
 
 cudaError_t pool_backward_add_mask(const __nv_bfloat16 *gp, const __nv_bfloat16 *gskip, const __nv_bfloat16 *e, int lde,
                                    __nv_bfloat16 *ge, int B, int H, int W, int C, cudaStream_t s) {
-    k_pool_bwd_add_mask<<<grid_for((long long)B * H * W * C), 256, 0, s>>>(gp, gskip, e, lde, ge, B, H, W, C);
+    k_pool_bwd_add_mask<<<grid_for((long long)B * H * W * C / 8), 256, 0, s>>>(gp, gskip, e, lde, ge, B, H, W, C);
     return cudaGetLastError();
 }
 
 cudaError_t up_backward_mask(const __nv_bfloat16 *gup, const __nv_bfloat16 *d, __nv_bfloat16 *gd, int B, int Hl,
                              int Wl, int C, cudaStream_t s) {
-    k_up_bwd_mask<<<grid_for((long long)B * Hl * Wl * C), 256, 0, s>>>(gup, d, gd, B, Hl, Wl, C);
+    k_up_bwd_mask<<<grid_for((long long)B * Hl * Wl * C / 8), 256, 0, s>>>(gup, d, gd, B, Hl, Wl, C);
     return cudaGetLastError();
 }
 

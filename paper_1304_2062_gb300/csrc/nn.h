@@ -43,6 +43,10 @@ cudaError_t conv_dgrad_tma(const __nv_bfloat16 *gz, int B, int H, int W, int Cou
                            const __nv_bfloat16 *act, __nv_bfloat16 *din, __nv_bfloat16 *din2, int split,
                            cudaStream_t s);
 cudaError_t tma_fault(int *host_flag, bool reset);
+// Weight gradient on the tensor cores (MN-major TMA operands): dw [Cout][9 C] +=
+// sum over pixels of x[p shifted by tap][ci] gz[p][co]; x, gz dense NHWC.
+cudaError_t conv_wgrad_tma(const __nv_bfloat16 *x, int B, int H, int W, int C, const __nv_bfloat16 *gz, int Cout,
+                           float *dw, cudaStream_t s);
 // Channels 0..C1-1 of out (ldo channels per pixel, H x W) = nearest-upsample(lo)
 // (C1 channels, H/2 x W/2).
 cudaError_t upsample_into(const __nv_bfloat16 *lo, int C1, __nv_bfloat16 *out, int ldo, int B, int H, int W,
