@@ -57,7 +57,7 @@ typedef enum se2n_status {
     SE2N_ENOMEM = 2,        /* a device or host allocation failed */
     SE2N_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
     SE2N_ECUFFT = 4,        /* a cuFFT call failed */
-    SE2N_EUNSUPPORTED = 5,  /* valid request this build has no kernel for (e.g. an N without an instantiation) */
+    SE2N_EUNSUPPORTED = 5,  /* valid request the library has no kernel for (e.g. an N without an instantiation) */
     SE2N_ENUMERIC = 6       /* parameters outside the range the FP32 scheme resolves */
 } se2n_status;
 
@@ -74,7 +74,7 @@ typedef enum se2n_status {
                                       (always on when beta * T > 8, see se2n_diffuse) */
 #define SE2N_DIFFUSE_FULL_CORRECTION 4  /* apply the corner correction on every angle (no truncation) */
 
-/* Largest N this build has kernels for, and the N it supports. */
+/* Largest N the library has kernels for. */
 #define SE2N_MAX_N 64
 
 typedef struct se2n_plan se2n_plan;

@@ -28,7 +28,7 @@ wx = sin(2 pi l/W), wy = sin(2 pi k/H). The paper's eq. (FTE) uses the mesh
 step 1/sqrt(M) and a factor 1/2; params_from_paper maps its (alpha, T) onto
 this form exactly.
 
-Readings taken where the paper is silent (all listed in the design doc):
+Readings taken where the paper is silent:
   * th_r = pi r / N (directions, the projectivised picture) by default,
     2 pi r / N on request (angle_conv=1);
   * the lift goes to the level-line tangent (gradient angle + pi/2), the
@@ -40,9 +40,8 @@ Readings taken where the paper is silent (all listed in the design doc):
     0.1, so sigma <= 5.5 for eps = 0.5); elsewhere the good pixel is mixed
     linearly with its lift.
 
-Parity status of each function is recorded in the design doc; every function here
-is pinned by a test under tests/ against a closed form, a dense brute-force
-computation, an invariant or a textbook routine.
+Every function here is pinned by a test under tests/ against a closed form,
+a dense brute-force computation, an invariant or a textbook routine.
 """
 from __future__ import annotations
 
