@@ -200,6 +200,7 @@ __global__ void __launch_bounds__(192, 1)
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
             constexpr uint32_t IDESC = tc::idesc_bf16_f32<BN>();
+            const uint64_t base_desc = sdesc<BN, CK>(base);
             int s = 0, acc = 0;
             uint32_t ph = 0, aph = 0;
             bool ok = true;
@@ -218,10 +219,10 @@ __global__ void __launch_bounds__(192, 1)
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                     const uint32_t sa = base + s * Cf::STAGE, sb = sa + Cf::A_BYTES;
+                    const uint64_t da = base_desc + ((sa - base) >> 4), db = base_desc + ((sb - base) >> 4);
 #pragma unroll
                     for (int kk = 0; kk < CK / 16; ++kk)
-                        tc::mma_f16(d, sdesc<BN, CK>(sa + kk * 32), sdesc<BN, CK>(sb + kk * 32), IDESC,
-                                    (kb > 0 || kk > 0) ? 1u : 0u);
+                        tc::mma_f16(d, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), IDESC, (kb > 0 || kk > 0) ? 1u : 0u);
                     tc::mma_commit(bar_empty + 8 * s);
                     last_bar = bar_empty + 8 * s;
                     last_par = ph;
@@ -404,6 +405,7 @@ __global__ void __launch_bounds__(192, 1)
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
             constexpr uint32_t IDESC = tc::idesc_bf16_f32<BN>();
+            const uint64_t a_desc0 = sdesc<BN, CK>(stages), w_desc0 = sdesc<BN, CK>(wres);
             int s = 0, acc = 0;
             uint32_t ph = 0, aph = 0;
             bool ok = tc::mbar_wait(bar_w, 0, abort);
@@ -428,11 +430,12 @@ __global__ void __launch_bounds__(192, 1)
                         for (int syi = 0; syi < 3; ++syi) {
                             // source offset (sy, sx) = (syi - 1, sxi - 1); the weight tap reads it
                             const int tap = g.flip ? (2 - syi) * 3 + (2 - sxi) : syi * 3 + sxi;
-                            const uint32_t wa = wres + (tap * g.nchunk + ch) * Cf::BBLK;
-                            const uint32_t aa = sa + syi * HBW * CK * 2;
+                            // descriptors = the base descriptors plus the offset in 16-byte units
+                            const uint64_t da = a_desc0 + ((sa - stages + syi * HBW * CK * 2) >> 4);
+                            const uint64_t dw = w_desc0 + (((tap * g.nchunk + ch) * Cf::BBLK) >> 4);
 #pragma unroll
                             for (int kk = 0; kk < CK / 16; ++kk) {
-                                tc::mma_f16(d, sdesc<BN, CK>(aa + kk * 32), sdesc<BN, CK>(wa + kk * 32), IDESC,
+                                tc::mma_f16(d, da + (uint64_t)(kk * 2), dw + (uint64_t)(kk * 2), IDESC,
                                             first ? 0u : 1u);
                                 first = false;
                             }
