@@ -234,8 +234,14 @@ SE2N_API se2n_status se2n_inpaint_host(se2n_plan *plan, const float *f_host, con
 
 /* Tuning of the diffusion launch (used by the autotuner): threads per
  * frequency P (1, 2 or 4; 0 = default for the plan's N), threads per block
- * (multiple of 32, <= 256; 0 = 256) and blocks (0 = as many as fit on the
- * device at once). SE2N_EUNSUPPORTED if no kernel exists for (N, P). */
+ * (multiple of 32, <= 384; the packed FP32 kernels take up to 256 below
+ * N = 48 and 384 from N = 48 on, the others 256, and a larger value is
+ * lowered to that) and blocks (0 = as many as fit on the device at once).
+ * block_threads = 0 restores the default shape, which ignores blocks: 128
+ * threads a block and one frequency group a thread for the packed kernels
+ * below N = 48, one resident 384-thread block an SM for them from N = 48 on,
+ * and 256-thread resident blocks for the others. SE2N_EUNSUPPORTED if no
+ * kernel exists for (N, P). */
 SE2N_API se2n_status se2n_plan_tune_diffuse(se2n_plan *plan, int threads_per_freq, int block_threads, int blocks);
 
 /* Resource use of the current diffusion kernel choice: registers per thread,

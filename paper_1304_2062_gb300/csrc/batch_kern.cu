@@ -36,7 +36,7 @@ __device__ __forceinline__ void batch_item(const StepParams &sp, const float *ta
 }
 
 template <int P16, int P32, int P64, bool FAST, bool SPLIT>
-__global__ void __launch_bounds__(256) k_diffuse_batch(const StepParams sp, const float *__restrict__ tables,
+__global__ void __launch_bounds__(FAST ? kDiffuseMaxBlock : 256, 1) k_diffuse_batch(const StepParams sp, const float *__restrict__ tables,
                                                        const BatchImage *__restrict__ imgs,
                                                        const BatchItem *__restrict__ items, int n_items,
                                                        unsigned int *counter) {

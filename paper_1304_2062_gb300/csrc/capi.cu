@@ -123,18 +123,13 @@ se2n_status diffuse_impl(se2n_plan *plan, float2 *vol, double beta, double T, in
     a.sp = step_params(beta, bdt, steps);
     angle_table(plan->N, plan->angle_conv, a.cs, a.sn, SE2N_MAX_N);
     const int P = plan->diffuse_P;
-    const int block = plan->diffuse_block;
-    int blocks = plan->diffuse_blocks;
-    if (blocks <= 0) {
-        int per_sm = 0;
-        cudaError_t e = se2n_diffuse_occupancy(plan->N, P, fp64, split, fast, block, &per_sm, nullptr);
-        if (e != cudaSuccess) return cuda_status(plan, e);
-        if (per_sm < 1) per_sm = 1;
-        blocks = plan->num_sms * per_sm;
+    int block = 0, blocks = 0;
+    cudaError_t es = se2n_diffuse_shape(plan->N, P, fp64, split, fast, plan->diffuse_block, plan->diffuse_blocks,
+                                        plan->num_sms, a.HW, &block, &blocks);
+    if (es != cudaSuccess) {
+        if (es == cudaErrorInvalidValue && !se2n_diffuse_has(plan->N, P)) return SE2N_EUNSUPPORTED;
+        return cuda_status(plan, es);
     }
-    const long long need = (a.HW * P + block - 1) / block;
-    if (blocks > need) blocks = (int)need;
-    if (blocks < 1) blocks = 1;
     StageTimer timer(plan, SE2N_STAGE_DIFFUSE);
     plan->kernels += 1;
     cudaError_t e = se2n_launch_diffuse(plan->N, P, fp64, split, fast, a, block, blocks, plan->stream);
@@ -387,7 +382,7 @@ se2n_status se2n_plan_create(se2n_plan **out, int H, int W, int N, int angle_con
     plan->half_ready = false;
     plan->stream = (cudaStream_t)stream;
     plan->diffuse_P = se2n_diffuse_default_P(N);
-    plan->diffuse_block = 256;
+    plan->diffuse_block = 0;
     plan->diffuse_blocks = 0;
     cudaError_t e = cudaGetDevice(&plan->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&plan->num_sms, cudaDevAttrMultiProcessorCount, plan->device);
@@ -539,9 +534,9 @@ se2n_status se2n_inpaint_host(se2n_plan *plan, const float *f_host, const uint8_
 se2n_status se2n_plan_tune_diffuse(se2n_plan *plan, int threads_per_freq, int block_threads, int blocks) {
     SE2N_TRY(check_plan(plan));
     const int P = threads_per_freq ? threads_per_freq : se2n_diffuse_default_P(plan->N);
-    const int block = block_threads ? block_threads : 256;
+    const int block = block_threads;
     if (P != 1 && P != 2 && P != 4) return SE2N_EINVAL;
-    if (block < 32 || block > 256 || (block % 32) || blocks < 0) return SE2N_EINVAL;
+    if (block < 0 || block > 384 || (block % 32) || blocks < 0) return SE2N_EINVAL;
     if (!se2n_diffuse_has(plan->N, P)) return SE2N_EUNSUPPORTED;
     plan->diffuse_P = P;
     plan->diffuse_block = block;
@@ -552,9 +547,11 @@ se2n_status se2n_plan_tune_diffuse(se2n_plan *plan, int threads_per_freq, int bl
 se2n_status se2n_plan_diffuse_info(se2n_plan *plan, int *regs_per_thread, int *blocks_per_sm,
                                    int *threads_per_freq) {
     SE2N_TRY(check_plan(plan));
-    int regs = 0, per_sm = 0;
-    cudaError_t e =
-        se2n_diffuse_occupancy(plan->N, plan->diffuse_P, false, false, true, plan->diffuse_block, &per_sm, &regs);
+    int regs = 0, per_sm = 0, block = 0, blocks = 0;
+    cudaError_t e = se2n_diffuse_shape(plan->N, plan->diffuse_P, false, false, true, plan->diffuse_block,
+                                       plan->diffuse_blocks, plan->num_sms, plan->HW, &block, &blocks);
+    if (e == cudaSuccess)
+        e = se2n_diffuse_occupancy(plan->N, plan->diffuse_P, false, false, true, block, &per_sm, &regs);
     if (e != cudaSuccess) return cuda_status(plan, e);
     if (regs_per_thread) *regs_per_thread = regs;
     if (blocks_per_sm) *blocks_per_sm = per_sm;

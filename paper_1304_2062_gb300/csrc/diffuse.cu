@@ -3,6 +3,9 @@
 
 #include <math.h>
 
+#include <algorithm>
+#include <climits>
+
 extern const DiffuseEntry se2n_diffuse_tab_a[];
 extern const int se2n_diffuse_tab_a_len;
 extern const DiffuseEntry se2n_diffuse_tab_b[];
@@ -74,6 +77,43 @@ cudaError_t se2n_diffuse_occupancy(int N, int P, bool sm_fp64, bool split, bool 
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, 0);
     if (e != cudaSuccess) return e;
     if (blocks_per_sm) *blocks_per_sm = n;
+    return cudaSuccess;
+}
+
+int se2n_diffuse_block_limit(int N, int P, bool sm_fp64, bool split, bool fast) {
+    const void *fn = choose(N, P, sm_fp64, split, fast);
+    cudaFuncAttributes attr;
+    if (!fn || cudaFuncGetAttributes(&attr, fn) != cudaSuccess) return 256;
+    return attr.maxThreadsPerBlock;
+}
+
+cudaError_t se2n_diffuse_shape(int N, int P, bool sm_fp64, bool split, bool fast, int tuned_block,
+                               int tuned_blocks, int num_sms, long long freqs, int *block, int *blocks) {
+    const bool packed = fast && !sm_fp64 && find_x2(N, P, split) != nullptr;
+    int b = tuned_block, nb = tuned_blocks;
+    bool all = false;
+    if (b == 0) {
+        if (packed && N < 48) {
+            b = 128;
+            all = true;
+        } else {
+            b = packed ? 384 : 256;
+        }
+        nb = 0;
+    }
+    b = std::min(b, se2n_diffuse_block_limit(N, P, sm_fp64, split, fast));
+    const long long need = std::max((freqs * P + b - 1) / b, 1LL);
+    if (all) {
+        nb = (int)std::min(need, (long long)INT_MAX);
+    } else if (nb <= 0) {
+        int per_sm = 0;
+        cudaError_t e = se2n_diffuse_occupancy(N, P, sm_fp64, split, fast, b, &per_sm, nullptr);
+        if (e != cudaSuccess) return e;
+        nb = num_sms * std::max(per_sm, 1);
+    }
+    if (nb > need) nb = (int)need;
+    *block = b;
+    *blocks = std::max(nb, 1);
     return cudaSuccess;
 }
 

@@ -73,6 +73,13 @@ __device__ __forceinline__ f32x2 group_sum2(f32x2 v) {
 
 constexpr int kTruncRows = 6;
 
+// Launch bound of the packed kernels. Below N = 48 a thread holds at most 16
+// angles and runs fastest with all the registers it wants (<= 200 at a
+// 256-thread bound, 8 warps an SM); from N = 48 on the 384-thread bound caps
+// it at 170 registers so that 12 warps stay resident, which measured faster.
+constexpr int kDiffuseMaxBlock = 384;
+constexpr int x2_max_block(int N) { return N >= 48 ? kDiffuseMaxBlock : 256; }
+
 // One frequency group: the P adjacent lanes of this warp integrate all
 // steps of frequency fc of the H x W volume vol[N][H][W], loading and
 // storing its N-vector. Every lane of the warp must call this together
@@ -136,7 +143,8 @@ __device__ __forceinline__ void diffuse_group_x2(const StepParams &sp, const flo
     float G[K], Z2[Q][K], M1, M2, hc[Q], hc1;
     tear_setup<K, P, float>(ti, dmod, d_i, d_loc0, Z2, hc, hc1, G, M1, M2);
 
-    f32x2 nEd[K], Gd[K], G2d[K], Zd[KZ], ZdEnd[KZ];
+    // the tear vectors are kept negated, so the correction is one FMA by alpha
+    f32x2 nEd[K], Gd[K], G2d[K], nZd[KZ], nZdEnd[KZ];
 #pragma unroll
     for (int j = 0; j < K; ++j) {
         nEd[j] = dup2(-E[j]);
@@ -146,22 +154,31 @@ __device__ __forceinline__ void diffuse_group_x2(const StepParams &sp, const flo
     const int own = (Q == 1 || ti.tear == 0) ? 0 : Q - 1;
 #pragma unroll
     for (int j = 0; j < KZ; ++j) {
-        Zd[j] = dup2(own == 0 ? Z2[0][j] : Z2[Q - 1][j]);
-        ZdEnd[j] = dup2(P == 1 ? Z2[0][K - KZ + j] : 0.0f);
+        nZd[j] = dup2(-(own == 0 ? Z2[0][j] : Z2[Q - 1][j]));
+        nZdEnd[j] = dup2(P == 1 ? -Z2[0][K - KZ + j] : 0.0f);
     }
     const f32x2 hcd0 = dup2(hc[0]), hcdQ = dup2(hc[Q - 1]), hc1d = dup2(hc1), M1d = dup2(M1), M2d = dup2(M2);
     const f32x2 m2d = dup2(-2.0f);
+    // Row 0 of the partner across the tear is corrected by the same alpha
+    // (both sit on one tear), so a lane rebuilds the corrected value from the
+    // partner's uncorrected row and the partner's nZd[0]: the two exchanges
+    // that end a step overlap instead of following one another. Row K-1 is
+    // outside the corrected rows when K > KZ and is exchanged as soon as the
+    // back substitution has produced it.
+    constexpr bool kEarlyRn = K > KZ;
+    const f32x2 nZp0 = (P == 1) ? nZd[0] : xshfl2(nZd[0], P - 1);
+    f32x2 ln, rn;
+    if constexpr (P > 1) {
+        ln = xshfl2(ps[0], P - 1);
+        rn = xshfl2(ps[K - 1], 1);
+    }
 
     // ---- the fused CN steps ----
 #pragma unroll 1
     for (int s = 0; s < sp.steps; ++s) {
-        f32x2 ln, rn;
         if constexpr (P == 1) {
             ln = ps[K - 1];
             rn = ps[0];
-        } else {
-            ln = xshfl2(ps[0], P - 1);
-            rn = xshfl2(ps[K - 1], 1);
         }
         f32x2 zs[K];
 #pragma unroll
@@ -185,6 +202,8 @@ __device__ __forceinline__ void diffuse_group_x2(const StepParams &sp, const flo
         }
         const f32x2 xiK = xi;
         ps[K - 1] = fma2(G2d[K - 1], xi, ps[K - 1]);
+        f32x2 rn_next;
+        if constexpr (P > 1 && kEarlyRn) rn_next = xshfl2(ps[K - 1], 1);
 #pragma unroll
         for (int j = K - 2; j >= 0; --j) {
             xi = fma2(Gd[j + 1], xi, zs[j]);
@@ -192,7 +211,8 @@ __device__ __forceinline__ void diffuse_group_x2(const StepParams &sp, const flo
         }
         // alpha of the thread's own tear: every lane contributes to the
         // sum of each tear (rows of both tears sit on different lanes)
-        f32x2 al;
+        f32x2 al, ps0_partner;
+        if constexpr (P > 1) ps0_partner = xshfl2(ps[0], P - 1);
         if constexpr (P == 1) {
             al = fma2(hcd0, xi, mul2(hc1d, xiK));
         } else if constexpr (Q == 1) {
@@ -202,14 +222,20 @@ __device__ __forceinline__ void diffuse_group_x2(const StepParams &sp, const flo
             const f32x2 a1 = group_sum2<P>(mul2(hcdQ, xi));
             al = (own == 0) ? a0 : a1;
         }
-        const f32x2 nal = pk2(-lo2(al), -hi2(al));
 #pragma unroll
-        for (int j = 0; j < KZ; ++j) ps[j] = fma2(nal, Zd[j], ps[j]);
+        for (int j = 0; j < KZ; ++j) ps[j] = fma2(al, nZd[j], ps[j]);
         if constexpr (P == 1) {
 #pragma unroll
             for (int j = 0; j < KZ; ++j) {
                 if (K - KZ + j < KZ) continue;  // rows already corrected from the other end
-                ps[K - KZ + j] = fma2(nal, ZdEnd[j], ps[K - KZ + j]);
+                ps[K - KZ + j] = fma2(al, nZdEnd[j], ps[K - KZ + j]);
+            }
+        } else {
+            ln = fma2(al, nZp0, ps0_partner);
+            if constexpr (kEarlyRn) {
+                rn = rn_next;
+            } else {
+                rn = xshfl2(ps[K - 1], 1);
             }
         }
     }
@@ -221,7 +247,7 @@ __device__ __forceinline__ void diffuse_group_x2(const StepParams &sp, const flo
 }
 
 template <int N, int P, bool SPLIT>
-__global__ void __launch_bounds__(256) k_diffuse_x2(const __grid_constant__ DiffuseArgs a) {
+__global__ void __launch_bounds__(x2_max_block(N), 1) k_diffuse_x2(const __grid_constant__ DiffuseArgs a) {
     const int lane = threadIdx.x & 31;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long slot = tid / P;

@@ -32,7 +32,7 @@ struct se2n_plan {
     float2 *h_vol;
     // diffusion launch configuration
     int diffuse_P;         // threads per frequency
-    int diffuse_block;     // threads per block
+    int diffuse_block;     // threads per block; 0 = the default shape for N
     int diffuse_blocks;    // 0 = fill the device
     int num_sms;
     int last_cuda_error;
@@ -80,6 +80,14 @@ cudaError_t se2n_launch_diffuse(int N, int P, bool sm_fp64, bool split, bool fas
 // Occupancy query for the same kernel: blocks per SM and registers per thread.
 cudaError_t se2n_diffuse_occupancy(int N, int P, bool sm_fp64, bool split, bool fast, int block,
                                    int *blocks_per_sm, int *regs);
+// Largest block the chosen kernel accepts (its launch bound).
+int se2n_diffuse_block_limit(int N, int P, bool sm_fp64, bool split, bool fast);
+// Launch shape of one diffusion launch over `freqs` frequencies: the plan's
+// tuned block and grid, or by default 128-thread blocks with one frequency
+// group per thread (N < 48, packed kernel) or one resident 384-thread block
+// an SM (N >= 48, packed kernel), 256-thread resident blocks otherwise.
+cudaError_t se2n_diffuse_shape(int N, int P, bool sm_fp64, bool split, bool fast, int tuned_block,
+                               int tuned_blocks, int num_sms, long long freqs, int *block, int *blocks);
 // Whether the tear corrections may be truncated for this beta * dt.
 bool se2n_diffuse_truncation_ok(double beta_dt);
 // Whether an instantiation exists for (N, P).

@@ -46,7 +46,7 @@ def test_diffuse_matches_oracle_every_instantiation(N, P):
     assert err <= REL_L2
 
 
-@pytest.mark.parametrize("block,blocks", [(32, 1), (64, 3), (256, 0), (96, 7)])
+@pytest.mark.parametrize("block,blocks", [(32, 1), (64, 3), (256, 0), (96, 7), (384, 0), (0, 0)])
 def test_grid_stride_and_block_shapes(block, blocks):
     """Few blocks force many passes of the grid-stride loop; odd block
     counts leave partially filled warps at the tail."""
@@ -54,6 +54,20 @@ def test_grid_stride_and_block_shapes(block, blocks):
     ref = oracle.diffuse(vol.astype(np.complex128), 0.3, 2.0, 15)
     got = _run(vol, 32, 0.3, 2.0, 15, tune=(2, block, blocks))
     assert rel_l2(got, ref) <= REL_L2
+
+
+@pytest.mark.parametrize("N,P", [(16, 1), (32, 2), (64, 4)])
+def test_every_launch_shape_gives_the_same_bits(N, P):
+    """Each frequency's arithmetic does not depend on which thread or block
+    takes it: the default shape (128-thread blocks over all frequencies
+    below N = 48, resident 384-thread blocks from N = 48 on), resident and
+    one-pass grids, 384-thread blocks (lowered to 256 below N = 48) and a
+    few-block grid-stride launch give bitwise the same volume."""
+    vol = synth.random_volume(N, 36, 50, seed=N + 7).astype(np.complex64)
+    outs = [_run(vol, N, 0.25, 1.0, 50, tune=(P, block, blocks))
+            for block, blocks in [(0, 0), (128, 0), (128, 1 << 20), (256, 0), (384, 0), (384, 1 << 20), (64, 5)]]
+    for o in outs[1:]:
+        assert np.array_equal(o.view(np.uint64), outs[0].view(np.uint64))
 
 
 @pytest.mark.parametrize("conv", [0, 1])
@@ -206,9 +220,10 @@ def test_unsupported_and_invalid_plans():
     with pytest.raises(se2n.Se2nError) as e:
         se2n.se2n_plan_tune_diffuse(plan, 4, 128, 0)
     assert e.value.status == se2n.SE2N_EUNSUPPORTED
-    with pytest.raises(se2n.Se2nError) as e:
-        se2n.se2n_plan_tune_diffuse(plan, 2, 100, 0)
-    assert e.value.status == se2n.SE2N_EINVAL
+    for block in (100, 416, -32):
+        with pytest.raises(se2n.Se2nError) as e:
+            se2n.se2n_plan_tune_diffuse(plan, 2, block, 0)
+        assert e.value.status == se2n.SE2N_EINVAL
     plan.close()
 
 
