@@ -16,6 +16,8 @@ diffusion and human vision: a semi-discrete new twist"):
                      remark after Theorem 2), see se2n_oracle.c;
 * mix             -- static restoration (Section 5, "Static restoration"):
                      sigma = (eps h(0) + (1-eps) h(t_i)) / h(t_i) on the good set;
+* dr_grow         -- dynamic restoration (Section 5.3): the good set grows
+                     into the corrupted one from its boundary;
 * project         -- Section 1.2.4 (second item): maximum (default) or mean
                      over the angles;
 * inpaint         -- the whole method: lift, then n restoration intervals.
@@ -38,7 +40,14 @@ Readings taken where the paper is silent:
   * the image is zero on the corrupted set B (f = f * mask);
   * restoration divides by h(t_i) only where h(t_i) > guard * h(0) (guard =
     0.1, so sigma <= 5.5 for eps = 0.5); elsewhere the good pixel is mixed
-    linearly with its lift.
+    linearly with its lift;
+  * dynamic restoration tests the current image h(t_i) = max over angles
+    before the restoration at t_i; the boundary of B is the set of bad pixels
+    with a good 8-neighbour; the mean runs over the bad pixels of the 3x3
+    block inside the image (the pixel included); the comparison is strict;
+    every pixel decides on the sets before the step; a pixel that joins is
+    restored from then on like a known pixel of value h(t_i) lifted to the
+    angle of its largest value (the first one on ties).
 
 Every function here is pinned by a test under tests/ against a closed form,
 a dense brute-force computation, an invariant or a textbook routine.
@@ -58,7 +67,7 @@ BIN_FLAT = 255
 __all__ = [
     "BIN_FLAT", "Params", "angles", "omegas", "symbol", "params_from_paper",
     "orient", "lift", "lift_from_image", "forward", "inverse", "diffuse",
-    "diffuse_dense", "cyclic_solve", "mix", "project", "inpaint",
+    "diffuse_dense", "cyclic_solve", "mix", "dr_grow", "project", "inpaint",
     "downstairs_restore", "dense_operator", "dense_paper_operator", "rel_l2",
 ]
 
@@ -82,6 +91,7 @@ class Params:
     final_mix: int = 0       # 1: restore once more after the last interval
     guard: float = 0.1       # relative: sigma only where h(t) > guard * h(0)
     reinject: int = 0        # 1: the result keeps f on the known pixels (the inpainted image)
+    dynamic: int = 0         # 1: dynamic restoration (Section 5.3): the good set grows each round
 
 
 # ----------------------------------------------------------------------------
@@ -314,6 +324,55 @@ def mix(vol, f, mask, bins, eps, guard=0.1):
     return out.astype(np.complex128)
 
 
+def dr_grow(vol, mask, fref, bins, dtype=np.float64):
+    """One step of dynamic restoration (Section 5.3): the good set G_i is
+    G_{i-1} plus every pixel of the boundary of B_{i-1} whose image value
+    exceeds the mean of the image over the pixels of B_{i-1} in its 3x3
+    neighbourhood.
+
+    vol: the volume at the restoration time (its real part is used); mask,
+    fref, bins: the good set (nonzero = good) and, for its pixels, the
+    reference value and orientation bin that the restoration pulls them to.
+    The image is h = max over angles. A bad pixel is on the boundary when one
+    of its 8 neighbours is good; its mean runs over the bad pixels of its 3x3
+    block (itself included) that lie inside the image, summed row by row,
+    top to bottom and left to right, and it joins when h > sum / count.
+    Decisions use the sets before the step. A joining pixel gets fref = h and
+    bins = the angle of its largest value (the first on ties).
+
+    dtype: precision of h, the sums and the comparison; float32 takes the
+    decision the way an FP32 kernel summing in the same order does.
+
+    Returns (mask, fref, bins) of G_i as new arrays."""
+    re = np.asarray(vol).real.astype(dtype)
+    h = re.max(axis=0)
+    amax = np.argmax(re, axis=0).astype(np.uint8)
+    good = np.asarray(mask) != 0
+    bad = ~good
+    H, W = h.shape
+    acc = np.zeros((H, W), dtype=dtype)
+    cnt = np.zeros((H, W), dtype=np.int64)
+    boundary = np.zeros((H, W), dtype=bool)
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            # neighbour (y + dy, x + dx) of every pixel (y, x) that has one
+            ys = slice(max(0, -dy), H - max(0, dy))
+            xs = slice(max(0, -dx), W - max(0, dx))
+            ny = slice(max(0, dy), H + min(0, dy))
+            nx = slice(max(0, dx), W + min(0, dx))
+            nb_bad = bad[ny, nx]
+            acc[ys, xs] = np.where(nb_bad, acc[ys, xs] + h[ny, nx], acc[ys, xs])
+            cnt[ys, xs] += nb_bad
+            if dy or dx:
+                boundary[ys, xs] |= good[ny, nx]
+    mean = np.divide(acc, cnt.astype(dtype), out=np.zeros_like(acc), where=cnt > 0)
+    join = bad & boundary & (h > mean)
+    new_mask = np.where(join, 1, good.astype(np.uint8)).astype(np.uint8)
+    new_fref = np.where(join, h.astype(np.float64), np.asarray(fref, dtype=np.float64))
+    new_bins = np.where(join, amax, np.asarray(bins)).astype(np.uint8)
+    return new_mask, new_fref, new_bins
+
+
 # ----------------------------------------------------------------------------
 # the whole method
 # ----------------------------------------------------------------------------
@@ -326,22 +385,36 @@ def inpaint(f, mask, p: Params, bins=None, nthreads=0, keep=False):
     known pixels of the result are f itself: the method only fills the
     corrupted ones.
 
-    Returns a dict with out (the image), bins and, if keep, the final volume."""
+    With dynamic, every restoration is preceded by one growth step of the
+    good set (dr_grow); reinject still keeps only the given known pixels.
+
+    Returns a dict with out (the image), bins, the final good set (mask_final,
+    equal to the given one without dynamic) and, if keep, the final volume."""
     if bins is None:
         bins = orient(f, mask, p.N, p.sigma, p.angle_conv, p.flat_tol)["bins"]
+    g_mask = (np.asarray(mask) != 0).astype(np.uint8)
+    g_fref = np.asarray(f, dtype=np.float64) * g_mask
+    g_bins = np.asarray(bins).astype(np.uint8)
+
+    def restore(v):
+        nonlocal g_mask, g_fref, g_bins
+        if p.dynamic:
+            g_mask, g_fref, g_bins = dr_grow(v, g_mask, g_fref, g_bins)
+        return mix(v, g_fref, g_mask, g_bins, p.eps, p.guard)
+
     Tr = p.T / p.rounds
     v = forward(lift(f, mask, bins, p.N))
     v = diffuse(v, p.beta, Tr, p.steps, p.angle_conv, nthreads=nthreads)
     for _ in range(1, p.rounds):
-        v = mix(inverse(v), f, mask, bins, p.eps, p.guard)
+        v = restore(inverse(v))
         v = diffuse(forward(v), p.beta, Tr, p.steps, p.angle_conv, nthreads=nthreads)
     v = inverse(v)
     if p.final_mix:
-        v = mix(v, f, mask, bins, p.eps, p.guard)
+        v = restore(v)
     out = project(v, p.proj)
     if p.reinject:
         out = np.where(np.asarray(mask) != 0, np.asarray(f, dtype=np.float64), out)
-    res = dict(out=out, bins=bins)
+    res = dict(out=out, bins=bins, mask_final=g_mask)
     if keep:
         res["vol"] = v
     return res
