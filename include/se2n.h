@@ -101,7 +101,13 @@ typedef struct se2n_plan se2n_plan;
  *            se2n_inpaint integrates the H (W/2 + 1) frequencies l <= W/2
  *            with real-to-complex transforms. 1: all H W frequencies with
  *            complex transforms. Same result up to rounding. The volume
- *            argument of se2n_inpaint is [N][H][W] complex in both cases. */
+ *            argument of se2n_inpaint is [N][H][W] complex in both cases.
+ *   dynamic  1: dynamic restoration (Section 5.3): before every restoration
+ *            the good set grows by one step of se2n_dr_grow (starting from
+ *            the known pixels), and the restoration pulls every good pixel to
+ *            its reference (f for a known pixel, its value when it joined for
+ *            the others); reinject still keeps f on the known pixels only.
+ *            0: static restoration on the known pixels (default). */
 typedef struct se2n_params {
     int N;
     double beta;
@@ -117,11 +123,13 @@ typedef struct se2n_params {
     int diffuse_flags;
     int reinject;
     int full_spectrum;
+    int dynamic;
 } se2n_params;
 
 /* Fill p with the defaults: N=32, beta=0.25, T=2, steps=100, rounds=1,
  * eps=0.5, sigma_smooth=1, flat_tol=1e-4, proj=max, final_mix=0,
- * guard=0.1, diffuse_flags=0, reinject=0, full_spectrum=0. SE2N_EINVAL if p is NULL. */
+ * guard=0.1, diffuse_flags=0, reinject=0, full_spectrum=0, dynamic=0.
+ * SE2N_EINVAL if p is NULL. */
 SE2N_API se2n_status se2n_params_default(se2n_params *p);
 
 /* Map the paper's weighting alpha and time T_paper on an M x M image with N
@@ -198,6 +206,21 @@ SE2N_API se2n_status se2n_inverse(se2n_plan *plan, void *vol);
  * so it is applied on those angles only (below FP32 resolution elsewhere);
  * SE2N_DIFFUSE_FULL_CORRECTION forces the general kernel. */
 SE2N_API se2n_status se2n_diffuse(se2n_plan *plan, void *vol_hat, double beta, double T, int steps, int flags);
+
+/* One step of dynamic restoration (Section 5.3) on the real part of the
+ * (normalised) complex volume vol [N][H][W]: with h = max_r Re vol_r, a pixel
+ * that is bad in mask_in (0) and has a good 8-neighbour becomes good when h
+ * exceeds the mean of h over the bad pixels of its 3x3 block inside the image
+ * (the pixel included; summed in FP32 row by row, then one division). Every
+ * decision uses mask_in. mask_out [H][W] receives the new set (1 good, 0 bad)
+ * and must not overlap mask_in; fref [H][W] floats and bins [H][W] bytes, the
+ * reference value and orientation bin the restoration pulls a good pixel to,
+ * are set for the pixels that join (fref = h, bins = the first angle with the
+ * largest value) and left alone elsewhere. Device memory, enqueued on the
+ * plan's stream; the plan allocates 12 H W bytes of state on first use.
+ * se2n_inpaint does this before every restoration when params.dynamic = 1. */
+SE2N_API se2n_status se2n_dr_grow(se2n_plan *plan, const void *vol, const uint8_t *mask_in, uint8_t *mask_out,
+                                  float *fref, uint8_t *bins);
 
 /* Static restoration (Section 5, SR) on the real volume, in place: with
  * h(t) = max_r Re vol_r and h(0) = max_r of the lift of (f, mask, bins), a

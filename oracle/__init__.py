@@ -324,7 +324,7 @@ def mix(vol, f, mask, bins, eps, guard=0.1):
     return out.astype(np.complex128)
 
 
-def dr_grow(vol, mask, fref, bins, dtype=np.float64):
+def dr_grow(vol, mask, fref, bins, dtype=np.float64, return_margin=False):
     """One step of dynamic restoration (Section 5.3): the good set G_i is
     G_{i-1} plus every pixel of the boundary of B_{i-1} whose image value
     exceeds the mean of the image over the pixels of B_{i-1} in its 3x3
@@ -343,7 +343,11 @@ def dr_grow(vol, mask, fref, bins, dtype=np.float64):
     dtype: precision of h, the sums and the comparison; float32 takes the
     decision the way an FP32 kernel summing in the same order does.
 
-    Returns (mask, fref, bins) of G_i as new arrays."""
+    Returns (mask, fref, bins) of G_i as new arrays, and with return_margin
+    also the smallest |h - mean| over the boundary pixels whose block holds
+    another bad pixel (inf if none): how far the closest decision that
+    rounding could change is from a tie. A pixel whose 8 neighbours are all
+    good compares h with itself and never joins, in any precision."""
     re = np.asarray(vol).real.astype(dtype)
     h = re.max(axis=0)
     amax = np.argmax(re, axis=0).astype(np.uint8)
@@ -370,6 +374,10 @@ def dr_grow(vol, mask, fref, bins, dtype=np.float64):
     new_mask = np.where(join, 1, good.astype(np.uint8)).astype(np.uint8)
     new_fref = np.where(join, h.astype(np.float64), np.asarray(fref, dtype=np.float64))
     new_bins = np.where(join, amax, np.asarray(bins)).astype(np.uint8)
+    if return_margin:
+        cand = bad & boundary & (cnt >= 2)
+        margin = float(np.abs(h - mean)[cand].min()) if cand.any() else float("inf")
+        return new_mask, new_fref, new_bins, margin
     return new_mask, new_fref, new_bins
 
 
@@ -389,17 +397,21 @@ def inpaint(f, mask, p: Params, bins=None, nthreads=0, keep=False):
     good set (dr_grow); reinject still keeps only the given known pixels.
 
     Returns a dict with out (the image), bins, the final good set (mask_final,
-    equal to the given one without dynamic) and, if keep, the final volume."""
+    equal to the given one without dynamic), the smallest decision margin of
+    the growth steps (dr_margin, inf without dynamic) and, if keep, the final
+    volume."""
     if bins is None:
         bins = orient(f, mask, p.N, p.sigma, p.angle_conv, p.flat_tol)["bins"]
     g_mask = (np.asarray(mask) != 0).astype(np.uint8)
     g_fref = np.asarray(f, dtype=np.float64) * g_mask
     g_bins = np.asarray(bins).astype(np.uint8)
+    margin = float("inf")
 
     def restore(v):
-        nonlocal g_mask, g_fref, g_bins
+        nonlocal g_mask, g_fref, g_bins, margin
         if p.dynamic:
-            g_mask, g_fref, g_bins = dr_grow(v, g_mask, g_fref, g_bins)
+            g_mask, g_fref, g_bins, m = dr_grow(v, g_mask, g_fref, g_bins, return_margin=True)
+            margin = min(margin, m)
         return mix(v, g_fref, g_mask, g_bins, p.eps, p.guard)
 
     Tr = p.T / p.rounds
@@ -414,7 +426,7 @@ def inpaint(f, mask, p: Params, bins=None, nthreads=0, keep=False):
     out = project(v, p.proj)
     if p.reinject:
         out = np.where(np.asarray(mask) != 0, np.asarray(f, dtype=np.float64), out)
-    res = dict(out=out, bins=bins, mask_final=g_mask)
+    res = dict(out=out, bins=bins, mask_final=g_mask, dr_margin=margin)
     if keep:
         res["vol"] = v
     return res

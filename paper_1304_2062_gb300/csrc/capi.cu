@@ -227,12 +227,81 @@ se2n_status project_impl(se2n_plan *plan, const float2 *vol, float scale, int pr
     return cuda_status(plan, se2n_launch_project(vol, plan->HW, plan->N, scale, proj, f, mask, out, plan->stream));
 }
 
+// ---- dynamic restoration (Section 5.3) ----
+
+// One allocation of 12 H W bytes: fref and h (floats), the two good-set
+// buffers, bins and the argmax angles (bytes). H W is a multiple of 4, so
+// every array is 16-byte aligned.
+se2n_status dr_alloc(DrState &d, long long HW) {
+    if (d.buf) return SE2N_OK;
+    cudaError_t e = cudaMalloc(&d.buf, (size_t)12 * (size_t)HW);
+    if (e != cudaSuccess) {
+        d.buf = nullptr;
+        (void)cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? SE2N_ENOMEM : SE2N_ECUDA;
+    }
+    d.fref = (float *)d.buf;
+    d.h = (float *)(d.buf + 4 * HW);
+    d.mask[0] = d.buf + 8 * HW;
+    d.mask[1] = d.buf + 9 * HW;
+    d.bins = d.buf + 10 * HW;
+    d.amax = d.buf + 11 * HW;
+    d.cur = 0;
+    return SE2N_OK;
+}
+
+void dr_free(DrState &d) {
+    cudaFree(d.buf);
+    d = DrState();
+}
+
+// Start of an inpaint: the good set is the known pixels, each referenced to
+// its value in f at its orientation bin.
+se2n_status dr_begin(se2n_plan *plan, DrState &d, const float *f, const uint8_t *mask, const uint8_t *bins) {
+    const size_t HW = (size_t)plan->HW;
+    cudaError_t e = cudaMemcpyAsync(d.fref, f, 4 * HW, cudaMemcpyDeviceToDevice, plan->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d.mask[0], mask, HW, cudaMemcpyDeviceToDevice, plan->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d.bins, bins, HW, cudaMemcpyDeviceToDevice, plan->stream);
+    d.cur = 0;
+    return cuda_status(plan, e);
+}
+
+// One growth step from the (unnormalised, times scale) volume.
+se2n_status dr_step(se2n_plan *plan, DrState &d, const float2 *vol, float scale, bool half) {
+    StageTimer timer(plan, SE2N_STAGE_MIX);
+    plan->kernels += 2;
+    cudaError_t e = half ? se2n_launch_dr_max_r((const float *)vol, plan->H, plan->W, plan->N, scale, d.h, d.amax,
+                                                plan->stream)
+                         : se2n_launch_dr_max(vol, plan->HW, plan->N, scale, d.h, d.amax, plan->stream);
+    if (e == cudaSuccess)
+        e = se2n_launch_dr_grow(d.h, d.amax, d.mask[d.cur], d.mask[d.cur ^ 1], d.fref, d.bins, plan->H, plan->W,
+                                plan->stream);
+    d.cur ^= 1;
+    return cuda_status(plan, e);
+}
+
+// The restoration at the end of an interval: static on (f, mask, bins), or,
+// with dr, one growth step of the good set and then the static restoration
+// towards the references of the grown set.
+se2n_status restore_impl(se2n_plan *plan, DrState *dr, float2 *vol, const float *f, const uint8_t *mask,
+                         const uint8_t *bins, float scale, float eps, float guard, bool half) {
+    if (dr) {
+        SE2N_TRY(dr_step(plan, *dr, vol, scale, half));
+        f = dr->fref;
+        mask = dr->mask[dr->cur];
+        bins = dr->bins;
+    }
+    return half ? mix_half_impl(plan, vol, f, mask, bins, scale, eps, guard)
+                : mix_impl(plan, vol, f, mask, bins, scale, eps, guard);
+}
+
 se2n_status check_params(const se2n_plan *plan, const se2n_params *p) {
     if (!p) return SE2N_EINVAL;
     if (p->N != plan->N || !(p->beta > 0.0) || !(p->T >= 0.0) || p->steps < 1 || p->rounds < 1) return SE2N_EINVAL;
     if (!(p->eps >= 0.0 && p->eps <= 1.0) || !(p->sigma_smooth > 0.0) || !(p->flat_tol >= 0.0)) return SE2N_EINVAL;
     if ((p->proj != SE2N_PROJ_MAX && p->proj != SE2N_PROJ_MEAN) || (p->final_mix != 0 && p->final_mix != 1) ||
-        (p->reinject != 0 && p->reinject != 1) || (p->full_spectrum != 0 && p->full_spectrum != 1))
+        (p->reinject != 0 && p->reinject != 1) || (p->full_spectrum != 0 && p->full_spectrum != 1) ||
+        (p->dynamic != 0 && p->dynamic != 1))
         return SE2N_EINVAL;
     if (!(p->guard >= 0.0) ||
         (p->diffuse_flags & ~(SE2N_DIFFUSE_SM_FP64 | SE2N_DIFFUSE_SPLIT_DIAG | SE2N_DIFFUSE_FULL_CORRECTION)))
@@ -257,6 +326,13 @@ se2n_status inpaint_impl(se2n_plan *plan, const float *f, const uint8_t *mask, c
     }
     const double Tr = p->T / p->rounds;
     const float inv_hw = (float)(1.0 / (double)HW);
+    const float eps = (float)p->eps, guard = (float)p->guard;
+    DrState *dr = nullptr;
+    if (p->dynamic) {
+        SE2N_TRY(dr_alloc(plan->dr, HW));
+        dr = &plan->dr;
+        SE2N_TRY(dr_begin(plan, *dr, f, mask, bins));
+    }
     if (!p->full_spectrum) {
         // The lifted volume is real, so its spectrum is Hermitian and the
         // system of frequency (-k, -l) is that of (k, l) conjugated (a_r^2 is
@@ -269,14 +345,14 @@ se2n_status inpaint_impl(se2n_plan *plan, const float *f, const uint8_t *mask, c
         SE2N_TRY(diffuse_impl(plan, vol, p->beta, Tr, p->steps, p->diffuse_flags, true));
         for (int i = 1; i < p->rounds; ++i) {
             SE2N_TRY(fft_half(plan, vol, false));
-            SE2N_TRY(mix_half_impl(plan, vol, f, mask, bins, inv_hw, (float)p->eps, (float)p->guard));
+            SE2N_TRY(restore_impl(plan, dr, vol, f, mask, bins, inv_hw, eps, guard, true));
             SE2N_TRY(fft_half(plan, vol, true));
             SE2N_TRY(diffuse_impl(plan, vol, p->beta, Tr, p->steps, p->diffuse_flags, true));
         }
         SE2N_TRY(fft_half(plan, vol, false));
         float scale = inv_hw;
         if (p->final_mix) {
-            SE2N_TRY(mix_half_impl(plan, vol, f, mask, bins, inv_hw, (float)p->eps, (float)p->guard));
+            SE2N_TRY(restore_impl(plan, dr, vol, f, mask, bins, inv_hw, eps, guard, true));
             scale = 1.0f;
         }
         return project_half_impl(plan, vol, scale, p->proj, p->reinject ? f : nullptr, p->reinject ? mask : nullptr,
@@ -288,14 +364,14 @@ se2n_status inpaint_impl(se2n_plan *plan, const float *f, const uint8_t *mask, c
     for (int i = 1; i < p->rounds; ++i) {
         // inverse DFT; its 1/(H W) is folded into the restoration kernel
         SE2N_TRY(fft(plan, plan->fft_vol, vol, CUFFT_INVERSE));
-        SE2N_TRY(mix_impl(plan, vol, f, mask, bins, inv_hw, (float)p->eps, (float)p->guard));
+        SE2N_TRY(restore_impl(plan, dr, vol, f, mask, bins, inv_hw, eps, guard, false));
         SE2N_TRY(fft(plan, plan->fft_vol, vol, CUFFT_FORWARD));
         SE2N_TRY(diffuse_impl(plan, vol, p->beta, Tr, p->steps, p->diffuse_flags));
     }
     SE2N_TRY(fft(plan, plan->fft_vol, vol, CUFFT_INVERSE));
     float scale = inv_hw;
     if (p->final_mix) {
-        SE2N_TRY(mix_impl(plan, vol, f, mask, bins, inv_hw, (float)p->eps, (float)p->guard));
+        SE2N_TRY(restore_impl(plan, dr, vol, f, mask, bins, inv_hw, eps, guard, false));
         scale = 1.0f;
     }
     return project_impl(plan, vol, scale, p->proj, p->reinject ? f : nullptr, p->reinject ? mask : nullptr, out);
@@ -314,6 +390,7 @@ void free_plan(se2n_plan *plan) {
     cudaFree(plan->h_out);
     cudaFree(plan->h_mask);
     cudaFree(plan->h_vol);
+    dr_free(plan->dr);
     for (int st = 0; st < SE2N_NUM_STAGES; ++st)
         for (cudaEvent_t e : plan->stage_ev[st]) cudaEventDestroy(e);
     delete plan;
@@ -352,6 +429,7 @@ se2n_status se2n_params_default(se2n_params *p) {
     p->diffuse_flags = 0;
     p->reinject = 0;
     p->full_spectrum = 0;
+    p->dynamic = 0;
     return SE2N_OK;
 }
 
@@ -473,6 +551,24 @@ se2n_status se2n_diffuse(se2n_plan *plan, void *vol_hat, double beta, double T, 
     SE2N_TRY(check_plan(plan));
     if (!device_ptr(vol_hat, 16)) return SE2N_EINVAL;
     return diffuse_impl(plan, (float2 *)vol_hat, beta, T, steps, flags);
+}
+
+se2n_status se2n_dr_grow(se2n_plan *plan, const void *vol, const uint8_t *mask_in, uint8_t *mask_out, float *fref,
+                         uint8_t *bins) {
+    SE2N_TRY(check_plan(plan));
+    if (!device_ptr(vol, 16) || !device_ptr(mask_in, 1) || !device_ptr(mask_out, 1) || !device_ptr(fref, 4) ||
+        !device_ptr(bins, 1))
+        return SE2N_EINVAL;
+    const uintptr_t a = (uintptr_t)mask_in, o = (uintptr_t)mask_out, HW = (uintptr_t)plan->HW;
+    if (a < o + HW && o < a + HW) return SE2N_EINVAL;  // the step reads the old set while writing the new one
+    SE2N_TRY(dr_alloc(plan->dr, plan->HW));  // h and the argmax angles
+    DrState &d = plan->dr;
+    StageTimer timer(plan, SE2N_STAGE_MIX);
+    plan->kernels += 2;
+    cudaError_t e = se2n_launch_dr_max((const float2 *)vol, plan->HW, plan->N, 1.0f, d.h, d.amax, plan->stream);
+    if (e == cudaSuccess)
+        e = se2n_launch_dr_grow(d.h, d.amax, mask_in, mask_out, fref, bins, plan->H, plan->W, plan->stream);
+    return cuda_status(plan, e);
 }
 
 se2n_status se2n_mix(se2n_plan *plan, void *vol, const float *f, const uint8_t *mask, const uint8_t *bins,
@@ -616,6 +712,7 @@ struct se2n_batch {
     size_t vol_bytes = 0;
     std::vector<float2 *> vols;
     std::vector<uint8_t *> bins;
+    std::vector<DrState> dr;  // per image, with dynamic restoration
     std::vector<BatchImage> h_imgs;
     float *d_tables = nullptr;
     BatchImage *d_imgs = nullptr;
@@ -754,6 +851,7 @@ se2n_status enqueue_batch_half(se2n_batch *b) {
         }
         SE2N_TRY(lift_half_impl(pl, d.f, d.mask, b->bins[i], b->vols[i]));
         SE2N_TRY(fft_half(pl, b->vols[i], true));
+        if (p.dynamic) SE2N_TRY(dr_begin(pl, b->dr[i], d.f, d.mask, b->bins[i]));
     }
     SE2N_TRY(batch_diffuse(b, p.steps, Tr));
     for (int r = 1; r < p.rounds; ++r) {
@@ -761,8 +859,8 @@ se2n_status enqueue_batch_half(se2n_batch *b) {
             se2n_plan *pl = b->plan_of[i];
             const se2n_image_desc &d = b->imgs[i];
             SE2N_TRY(fft_half(pl, b->vols[i], false));
-            SE2N_TRY(mix_half_impl(pl, b->vols[i], d.f, d.mask, b->bins[i], (float)(1.0 / (double)pl->HW),
-                                   (float)p.eps, (float)p.guard));
+            SE2N_TRY(restore_impl(pl, p.dynamic ? &b->dr[i] : nullptr, b->vols[i], d.f, d.mask, b->bins[i],
+                                  (float)(1.0 / (double)pl->HW), (float)p.eps, (float)p.guard, true));
             SE2N_TRY(fft_half(pl, b->vols[i], true));
         }
         SE2N_TRY(batch_diffuse(b, p.steps, Tr));
@@ -774,7 +872,8 @@ se2n_status enqueue_batch_half(se2n_batch *b) {
         SE2N_TRY(fft_half(pl, b->vols[i], false));
         float scale = inv_hw;
         if (p.final_mix) {
-            SE2N_TRY(mix_half_impl(pl, b->vols[i], d.f, d.mask, b->bins[i], inv_hw, (float)p.eps, (float)p.guard));
+            SE2N_TRY(restore_impl(pl, p.dynamic ? &b->dr[i] : nullptr, b->vols[i], d.f, d.mask, b->bins[i], inv_hw,
+                                  (float)p.eps, (float)p.guard, true));
             scale = 1.0f;
         }
         SE2N_TRY(project_half_impl(pl, b->vols[i], scale, p.proj, p.reinject ? d.f : nullptr,
@@ -798,6 +897,7 @@ se2n_status enqueue_batch(se2n_batch *b) {
         }
         SE2N_TRY(lift_impl(pl, d.f, d.mask, b->bins[i], b->vols[i]));
         SE2N_TRY(fft(pl, pl->fft_vol, b->vols[i], CUFFT_FORWARD));
+        if (p.dynamic) SE2N_TRY(dr_begin(pl, b->dr[i], d.f, d.mask, b->bins[i]));
     }
     SE2N_TRY(batch_diffuse(b, p.steps, Tr));
     for (int r = 1; r < p.rounds; ++r) {
@@ -805,8 +905,8 @@ se2n_status enqueue_batch(se2n_batch *b) {
             se2n_plan *pl = b->plan_of[i];
             const se2n_image_desc &d = b->imgs[i];
             SE2N_TRY(fft(pl, pl->fft_vol, b->vols[i], CUFFT_INVERSE));
-            SE2N_TRY(mix_impl(pl, b->vols[i], d.f, d.mask, b->bins[i], (float)(1.0 / (double)pl->HW),
-                              (float)p.eps, (float)p.guard));
+            SE2N_TRY(restore_impl(pl, p.dynamic ? &b->dr[i] : nullptr, b->vols[i], d.f, d.mask, b->bins[i],
+                                  (float)(1.0 / (double)pl->HW), (float)p.eps, (float)p.guard, false));
             SE2N_TRY(fft(pl, pl->fft_vol, b->vols[i], CUFFT_FORWARD));
         }
         SE2N_TRY(batch_diffuse(b, p.steps, Tr));
@@ -818,7 +918,8 @@ se2n_status enqueue_batch(se2n_batch *b) {
         SE2N_TRY(fft(pl, pl->fft_vol, b->vols[i], CUFFT_INVERSE));
         float scale = inv_hw;
         if (p.final_mix) {
-            SE2N_TRY(mix_impl(pl, b->vols[i], d.f, d.mask, b->bins[i], inv_hw, (float)p.eps, (float)p.guard));
+            SE2N_TRY(restore_impl(pl, p.dynamic ? &b->dr[i] : nullptr, b->vols[i], d.f, d.mask, b->bins[i], inv_hw,
+                                  (float)p.eps, (float)p.guard, false));
             scale = 1.0f;
         }
         SE2N_TRY(project_impl(pl, b->vols[i], scale, p.proj, p.reinject ? d.f : nullptr,
@@ -830,6 +931,7 @@ se2n_status enqueue_batch(se2n_batch *b) {
 void free_batch(se2n_batch *b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
+    for (DrState &d : b->dr) dr_free(d);
     for (se2n_plan *pl : b->plans) {
         cudaStreamSynchronize(pl->stream);
         free_plan(pl);
@@ -881,6 +983,10 @@ se2n_status create_batch(se2n_batch *b, const se2n_image_desc *imgs) {
     for (int i = 0; i < b->count; ++i) {
         b->vols[i] = (float2 *)(b->arena + voff[i]);
         b->bins[i] = (uint8_t *)(b->arena + boff[i]);
+    }
+    if (b->p.dynamic) {
+        b->dr.resize(b->count);
+        for (int i = 0; i < b->count; ++i) SE2N_TRY(dr_alloc(b->dr[i], (long long)imgs[i].H * imgs[i].W));
     }
     // angle tables, one per distinct N, cos[N] then sin[N]
     std::vector<float> tables;

@@ -289,6 +289,98 @@ __global__ void k_project_r(const float *__restrict__ vol, long long npairs, int
     }
 }
 
+// ---------------------------------------------------------------------------
+// Dynamic restoration (Section 5.3): the good set grows before a restoration.
+// ---------------------------------------------------------------------------
+
+// Image value h = max over angles of scale * Re psi and the angle of its
+// first maximum, one pixel a thread; vol is the complex volume [N][HW].
+__global__ void k_dr_max(const float2 *__restrict__ vol, long long HW, int N, float scale, float *__restrict__ h,
+                         uint8_t *__restrict__ amax) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < HW;
+         i += (long long)gridDim.x * blockDim.x) {
+        float best = -INFINITY;
+        int arg = 0;
+        for (int r = 0; r < N; ++r) {
+            const float v = vol[(long long)r * HW + i].x * scale;
+            if (v > best) {
+                best = v;
+                arg = r;
+            }
+        }
+        h[i] = best;
+        amax[i] = (uint8_t)arg;
+    }
+}
+
+// The same on the real volume of the Hermitian-half path (planes of H rows
+// of Wp = W + 2 floats).
+__global__ void k_dr_max_r(const float *__restrict__ vol, long long HW, int W, int Wp, long long plane, int N,
+                           float scale, float *__restrict__ h, uint8_t *__restrict__ amax) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < HW;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long y = i / W;
+        const float *col = vol + y * Wp + (i - y * W);
+        float best = -INFINITY;
+        int arg = 0;
+        for (int r = 0; r < N; ++r) {
+            const float v = col[(long long)r * plane] * scale;
+            if (v > best) {
+                best = v;
+                arg = r;
+            }
+        }
+        h[i] = best;
+        amax[i] = (uint8_t)arg;
+    }
+}
+
+// One growth step of the good set. A bad pixel with a good 8-neighbour joins
+// when h exceeds the mean of h over the bad pixels of its 3x3 block inside
+// the image: summed in FP32 row by row, top to bottom and left to right,
+// then one IEEE division. Every decision reads mask_in only (the sets before
+// the step); a joining pixel takes fref = h and bins = amax, which no other
+// thread reads here. mask_out holds 1 for good, 0 for bad.
+__global__ void k_dr_grow(const float *__restrict__ h, const uint8_t *__restrict__ amax,
+                          const uint8_t *__restrict__ mask_in, uint8_t *__restrict__ mask_out, float *__restrict__ fref,
+                          uint8_t *__restrict__ bins, int H, int W) {
+    const long long HW = (long long)H * W;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < HW;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (mask_in[i]) {
+            mask_out[i] = 1;
+            continue;
+        }
+        const int y = (int)(i / W);
+        const int x = (int)(i - (long long)y * W);
+        float sum = 0.0f;
+        int cnt = 0;
+        bool touches = false;
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int yy = y + dy;
+            if (yy < 0 || yy >= H) continue;
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int xx = x + dx;
+                if (xx < 0 || xx >= W) continue;
+                const long long q = (long long)yy * W + xx;
+                if (mask_in[q]) {
+                    touches = true;
+                } else {
+                    sum += h[q];
+                    ++cnt;
+                }
+            }
+        }
+        const float hv = h[i];
+        const bool join = touches && hv > sum / (float)cnt;  // cnt >= 1: the pixel itself
+        mask_out[i] = join ? 1 : 0;
+        if (join) {
+            fref[i] = hv;
+            bins[i] = amax[i];
+        }
+    }
+}
+
 __global__ void k_scale(float4 *__restrict__ v, long long n4, float s) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4;
          i += (long long)gridDim.x * blockDim.x) {
@@ -376,6 +468,26 @@ cudaError_t se2n_launch_project_r(const float *vol, int H, int W, int N, float s
     const int Wp = W + 2;
     k_project_r<<<grid_for(n), kBlock, 0, s>>>(vol, n, W, Wp, (long long)H * Wp, N, scale, proj, (const float2 *)f,
                                                (const uchar2 *)mask, (float2 *)out);
+    return cudaGetLastError();
+}
+
+cudaError_t se2n_launch_dr_max(const float2 *vol, long long HW, int N, float scale, float *h, uint8_t *amax,
+                               cudaStream_t s) {
+    k_dr_max<<<grid_for(HW), kBlock, 0, s>>>(vol, HW, N, scale, h, amax);
+    return cudaGetLastError();
+}
+
+cudaError_t se2n_launch_dr_max_r(const float *vol, int H, int W, int N, float scale, float *h, uint8_t *amax,
+                                 cudaStream_t s) {
+    const long long HW = (long long)H * W;
+    const int Wp = W + 2;
+    k_dr_max_r<<<grid_for(HW), kBlock, 0, s>>>(vol, HW, W, Wp, (long long)H * Wp, N, scale, h, amax);
+    return cudaGetLastError();
+}
+
+cudaError_t se2n_launch_dr_grow(const float *h, const uint8_t *amax, const uint8_t *mask_in, uint8_t *mask_out,
+                                float *fref, uint8_t *bins, int H, int W, cudaStream_t s) {
+    k_dr_grow<<<grid_for((long long)H * W), kBlock, 0, s>>>(h, amax, mask_in, mask_out, fref, bins, H, W);
     return cudaGetLastError();
 }
 

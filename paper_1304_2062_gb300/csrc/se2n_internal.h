@@ -9,6 +9,14 @@
 
 #include "se2n.h"
 
+struct DrState {
+    uint8_t *buf = nullptr;  // one allocation of 12 H W bytes holding the arrays below
+    float *fref = nullptr, *h = nullptr;
+    uint8_t *mask[2] = {nullptr, nullptr};
+    uint8_t *bins = nullptr, *amax = nullptr;
+    int cur = 0;  // mask[cur] is the current good set
+};
+
 struct se2n_plan {
     int H, W, N, angle_conv;
     long long HW;
@@ -30,6 +38,10 @@ struct se2n_plan {
     float *h_f, *h_out;
     uint8_t *h_mask;
     float2 *h_vol;
+    // dynamic restoration state (allocated on first use): the good set
+    // (ping-pong), the reference values and bins the restoration pulls the
+    // good pixels to, and the image value and argmax angle of the last step
+    DrState dr;
     // diffusion launch configuration
     int diffuse_P;         // threads per frequency
     int diffuse_block;     // threads per block; 0 = the default shape for N
@@ -119,3 +131,13 @@ cudaError_t se2n_launch_project_r(const float *vol, int H, int W, int N, float s
 cudaError_t se2n_launch_project(const float2 *vol, long long HW, int N, float scale, int proj, const float *f,
                                 const uint8_t *mask, float *out, cudaStream_t s);
 cudaError_t se2n_launch_scale(float2 *vol, long long count, float scale, cudaStream_t s);
+// Dynamic restoration: h = max_r scale * Re vol[r] and the angle of its first
+// maximum (complex [N][HW] volume, or the real half-path layout), then one
+// growth step of the good set from mask_in to mask_out (updating fref and bins
+// of the pixels that join).
+cudaError_t se2n_launch_dr_max(const float2 *vol, long long HW, int N, float scale, float *h, uint8_t *amax,
+                               cudaStream_t s);
+cudaError_t se2n_launch_dr_max_r(const float *vol, int H, int W, int N, float scale, float *h, uint8_t *amax,
+                                 cudaStream_t s);
+cudaError_t se2n_launch_dr_grow(const float *h, const uint8_t *amax, const uint8_t *mask_in, uint8_t *mask_out,
+                                float *fref, uint8_t *bins, int H, int W, cudaStream_t s);

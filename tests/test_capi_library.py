@@ -29,7 +29,7 @@ def lib():
 def test_header_declares_the_boundary():
     names = _declared()
     for required in ["se2n_plan_create", "se2n_plan_destroy", "se2n_orient", "se2n_lift", "se2n_forward",
-                     "se2n_diffuse", "se2n_inverse", "se2n_mix", "se2n_project", "se2n_inpaint",
+                     "se2n_diffuse", "se2n_inverse", "se2n_mix", "se2n_dr_grow", "se2n_project", "se2n_inpaint",
                      "se2n_inpaint_host", "se2n_params_from_paper", "se2n_status_string"]:
         assert required in names
 
@@ -71,9 +71,11 @@ def test_params_from_paper_matches_oracle(lib):
 def test_params_default(lib):
     from paper_1304_2062_gb300.se2n import se2n_params
     p = se2n_params()
+    p.reinject = p.full_spectrum = p.dynamic = 7      # the C side must reach the last field
     lib.se2n_params_default.argtypes = [ctypes.POINTER(se2n_params)]
     assert lib.se2n_params_default(ctypes.byref(p)) == 0
     assert (p.N, p.steps, p.rounds, p.proj, p.final_mix) == (32, 100, 1, 0, 0)
+    assert (p.reinject, p.full_spectrum, p.dynamic) == (0, 0, 0)
     assert (p.beta, p.eps, p.sigma_smooth, p.flat_tol) == (0.25, 0.5, 1.0, 1e-4)
     assert lib.se2n_params_default(None) == 1
 

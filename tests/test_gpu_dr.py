@@ -1,0 +1,162 @@
+"""Dynamic restoration (Section 5.3) on the GPU against the FP64 oracle
+through the C ABI.
+
+The growth step is an integer decision taken on floating-point values, so
+the step on its own is compared bit for bit with the oracle taking the same
+decision in FP32 on the same inputs (ragged sizes, exact ties, masks with
+any nonzero value, no boundary at all). In the whole method the GPU decides
+on FP32 images and the oracle on FP64 ones, which differ by ~1e-7; a decision
+closer than that to a tie could go either way and both results would be
+correct. The oracle reports its closest decision (1e-8 .. 1e-6 on these
+inputs: thousands of decisions a run); on these seeded inputs no decision
+flips, and the whole result is compared at the restored-result tolerance."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from _gpu import MAX_REL_RESTORED, REL_L2, host, rel_l2, t_c64, t_f32, t_u8
+
+pytestmark = pytest.mark.gpu
+
+se2n = pytest.importorskip("paper_1304_2062_gb300.se2n")
+
+import torch  # noqa: E402
+
+
+def _gpu_step(vol, mask, fref, bins):
+    N, H, W = vol.shape
+    plan = se2n.se2n_plan_create(H, W, N)
+    v = t_c64(vol)
+    m_in = t_u8(mask)
+    m_out = torch.full((H, W), 77, dtype=torch.uint8, device="cuda")
+    f = t_f32(fref)
+    b = t_u8(bins)
+    se2n.se2n_dr_grow(plan, v, m_in, m_out, f, b)
+    out = host(m_out), host(f), host(b)
+    plan.close()
+    return out
+
+
+def _inputs(N, H, W, seed, quantised=False, good_value=1):
+    rng = np.random.default_rng(seed)
+    if quantised:
+        # values on a coarse grid: many exact ties between h and the mean
+        re = rng.integers(0, 4, size=(N, H, W)).astype(np.float32) * 0.25
+    else:
+        re = rng.normal(size=(N, H, W)).astype(np.float32)
+    vol = (re + 1j * rng.normal(size=(N, H, W)).astype(np.float32)).astype(np.complex64)
+    mask = np.where(rng.random((H, W)) < 0.45, good_value, 0).astype(np.uint8)
+    fref = rng.random((H, W)).astype(np.float32)
+    bins = rng.integers(0, N, size=(H, W)).astype(np.uint8)
+    return vol, mask, fref, bins
+
+
+@pytest.mark.parametrize("N,H,W,seed,quantised,good", [
+    (16, 6, 10, 1, False, 1), (32, 34, 22, 2, False, 1), (16, 64, 96, 3, False, 255),
+    (32, 2, 2, 4, False, 1), (16, 30, 30, 5, True, 1), (64, 18, 40, 6, True, 3)])
+def test_growth_step_is_bit_exact(N, H, W, seed, quantised, good):
+    vol, mask, fref, bins = _inputs(N, H, W, seed, quantised, good)
+    m_gpu, f_gpu, b_gpu = _gpu_step(vol, mask, fref, bins)
+    m_ref, f_ref, b_ref = oracle.dr_grow(vol.astype(np.complex128), mask, fref, bins, dtype=np.float32)
+    np.testing.assert_array_equal(m_gpu, m_ref)
+    np.testing.assert_array_equal(f_gpu, f_ref.astype(np.float32))
+    np.testing.assert_array_equal(b_gpu, b_ref)
+    joined = (m_ref != 0) & (mask == 0)
+    print(f"{H}x{W} N={N}: {joined.sum()} of {(mask == 0).sum()} bad pixels join")
+
+
+@pytest.mark.parametrize("fill", [0, 1])
+def test_growth_step_without_a_boundary(fill):
+    """All good: nothing changes. All bad: no pixel touches G, none joins."""
+    vol, _, fref, bins = _inputs(16, 12, 14, 9)
+    mask = np.full((12, 14), fill, dtype=np.uint8)
+    m_gpu, f_gpu, b_gpu = _gpu_step(vol, mask, fref, bins)
+    np.testing.assert_array_equal(m_gpu, mask)
+    np.testing.assert_array_equal(f_gpu, fref)
+    np.testing.assert_array_equal(b_gpu, bins)
+
+
+def test_overlapping_masks_are_rejected():
+    vol, mask, fref, bins = _inputs(16, 8, 8, 10)
+    plan = se2n.se2n_plan_create(8, 8, 16)
+    m = t_u8(mask)
+    with pytest.raises(se2n.Se2nError) as e:
+        se2n.se2n_dr_grow(plan, t_c64(vol), m, m, t_f32(fref), t_u8(bins))
+    assert e.value.status == se2n.SE2N_EINVAL
+    plan.close()
+
+
+def _params(p, full=0, dynamic=1):
+    return se2n.se2n_params_default(N=p.N, beta=p.beta, T=p.T, steps=p.steps, rounds=p.rounds, eps=p.eps,
+                                    sigma_smooth=p.sigma, flat_tol=p.flat_tol, proj=p.proj,
+                                    final_mix=p.final_mix, guard=p.guard, reinject=p.reinject,
+                                    full_spectrum=full, dynamic=dynamic)
+
+
+def _gpu_inpaint(f32, mask, bins, prm):
+    H, W = f32.shape
+    plan = se2n.se2n_plan_create(H, W, prm.N)
+    vol = torch.empty((prm.N, H, W), dtype=torch.complex64, device="cuda")
+    out = torch.empty((H, W), dtype=torch.float32, device="cuda")
+    se2n.se2n_inpaint(plan, t_f32(f32), t_u8(mask), t_u8(bins), prm, vol, out)
+    got = host(out)
+    plan.close()
+    return got
+
+
+@pytest.mark.parametrize("H,W,full,final_mix", [(96, 96, 0, 0), (64, 160, 0, 1), (96, 96, 1, 0), (128, 66, 1, 1)])
+def test_inpaint_with_dynamic_restoration_matches_oracle(H, W, full, final_mix):
+    w = synth.workload_512(H=H, W=W, steps=60, rounds=4)
+    p = oracle.Params(N=32, beta=0.25, T=8.0, steps=60, rounds=4, final_mix=final_mix, dynamic=1)
+    f32 = w.f.astype(np.float32)
+    f64 = f32.astype(np.float64)
+    bins = oracle.orient(f64, w.mask, p.N, p.sigma, 0, p.flat_tol)["bins"]
+    ref = oracle.inpaint(f64, w.mask, p, bins=bins)
+    grown = int(ref["mask_final"].sum() - (w.mask != 0).sum())
+    assert grown > 0
+    got = _gpu_inpaint(f32, w.mask, bins, _params(p, full))
+    mx = np.abs(got - ref["out"]).max() / np.abs(f64).max()
+    r2 = rel_l2(got, ref["out"])
+    static = oracle.inpaint(f64, w.mask, oracle.Params(**{**p.__dict__, "dynamic": 0}), bins=bins)["out"]
+    print(f"{H}x{W} full={full}: {grown} pixels joined, margin {ref['dr_margin']:.2e}, max-abs/max|f| {mx:.2e}, "
+          f"rel-L2 {r2:.2e} (dynamic vs static differ by {rel_l2(ref['out'], static):.2e})")
+    assert mx <= MAX_REL_RESTORED
+    assert r2 <= REL_L2
+
+
+def test_dynamic_equals_static_when_eps_is_zero():
+    w = synth.workload_512(H=64, W=64, steps=40, rounds=3)
+    p = oracle.Params(N=16, beta=0.25, T=6.0, steps=40, rounds=3, eps=0.0)
+    bins = oracle.orient(w.f.astype(np.float64), w.mask, p.N, p.sigma, 0, p.flat_tol)["bins"]
+    f32 = w.f.astype(np.float32)
+    a = _gpu_inpaint(f32, w.mask, bins, _params(p, dynamic=0))
+    b = _gpu_inpaint(f32, w.mask, bins, _params(p, dynamic=1))
+    np.testing.assert_array_equal(a, b)
+
+
+def test_batch_with_dynamic_restoration_is_bitwise_per_image():
+    rng = np.random.default_rng(11)
+    imgs = []
+    for i, (H, W, N) in enumerate([(64, 64, 16), (96, 64, 32), (64, 64, 16), (128, 96, 64)]):
+        clean = synth.curves_noise_image(H, W, seed=50 + i)
+        mask = (rng.random((H, W)) > 0.6).astype(np.uint8)
+        f = t_f32(clean * mask)
+        m = t_u8(mask)
+        out = torch.zeros((H, W), dtype=torch.float32, device="cuda")
+        imgs.append((f, m, out, N))
+    prm = se2n.se2n_params_default(beta=0.25, T=4.0, steps=30, rounds=3, dynamic=1)
+    batch = se2n.se2n_batch_create(imgs, prm, 0, 0, None)
+    se2n.se2n_batch_run(batch)
+    a = [host(o).copy() for _, _, o, _ in imgs]
+    se2n.se2n_batch_run_per_image(batch)
+    b = [host(o).copy() for _, _, o, _ in imgs]
+    prm0 = se2n.se2n_params_default(beta=0.25, T=4.0, steps=30, rounds=3, dynamic=0)
+    batch0 = se2n.se2n_batch_create(imgs, prm0, 0, 0, None)
+    se2n.se2n_batch_run(batch0)
+    c = [host(o).copy() for _, _, o, _ in imgs]
+    batch.close()
+    batch0.close()
+    for x, y, z in zip(a, b, c):
+        np.testing.assert_array_equal(x, y)
+        assert not np.array_equal(x, z)       # the dynamic run is a different result

@@ -45,6 +45,9 @@ def test_hand_worked_step_on_a_vertical_edge():
     unchanged = want == mask
     assert np.array_equal(f1[unchanged], fref[unchanged])
     assert np.array_equal(b1[unchanged], bins[unchanged])
+    # the closest decision: (2,2) at |0.1 - 1/6|
+    *_, margin = oracle.dr_grow(vol, mask, fref, bins, return_margin=True)
+    assert margin == pytest.approx(1.0 / 6.0 - 0.1, rel=1e-12)
 
 
 def test_diagonal_neighbour_counts_and_good_values_are_excluded():
@@ -76,6 +79,17 @@ def test_comparison_is_strict():
     vol, _ = _vol_from_image(h, seed=2)
     m1, _, _ = oracle.dr_grow(vol, mask, np.zeros(h.shape), np.zeros(h.shape, np.uint8))
     assert m1.sum() == mask.sum() + 1 and m1[2, 2] == 1
+
+
+def test_a_lone_bad_pixel_never_joins_and_has_no_margin():
+    """Every neighbour good: the mean is h itself and h > h is false."""
+    mask = np.ones((3, 3), dtype=np.uint8)
+    mask[1, 1] = 0
+    h = np.full((3, 3), 0.1)
+    h[1, 1] = 9.0
+    vol, _ = _vol_from_image(h, seed=3)
+    m1, _, _, margin = oracle.dr_grow(vol, mask, np.zeros((3, 3)), np.zeros((3, 3), np.uint8), return_margin=True)
+    assert np.array_equal(m1, mask) and margin == float("inf")
 
 
 def test_first_maximum_gives_the_bin():
