@@ -49,11 +49,15 @@ def _workload():
     return synth.workload_512()
 
 
-def _config(w, extra=None):
+GOLDEN_DYNAMIC = os.path.join(ROOT, "tests", "golden", "curves_noise_512_N32_dynamic.npz")
+
+
+def _config(w, extra=None, dynamic=False):
     cfg = {
-        "workload": f"curves_noise_512_N32: {w.H}x{w.W} image, N={w.N}, beta={w.beta}, "
-                    f"{w.rounds} restoration intervals x {w.steps} CN steps, T={w.T}, eps={w.eps}, "
-                    "80% random mask + 4-px bars every 32 px",
+        "workload": f"curves_noise_512_N32{'_dynamic' if dynamic else ''}: {w.H}x{w.W} image, N={w.N}, "
+                    f"beta={w.beta}, {w.rounds} restoration intervals x {w.steps} CN steps, T={w.T}, eps={w.eps}, "
+                    "80% random mask + 4-px bars every 32 px"
+                    + (", dynamic restoration (Section 5.3)" if dynamic else ""),
         "updates_per_step": w.updates(),
         "l2": "flushed between timed steps (256 MiB write)",
         "parallelism": "replicas",
@@ -180,8 +184,9 @@ def run_ours(args, rank, world, local_rank):
     f32 = w.f.astype(np.float32)
     stream = torch.cuda.Stream(dev)
     plan = se2n.se2n_plan_create(w.H, w.W, w.N, 0, stream)
+    dynamic = args.workload == "dr"
     prm = se2n.se2n_params_default(N=w.N, beta=w.beta, T=w.T, steps=w.steps, rounds=w.rounds, eps=w.eps,
-                                   sigma_smooth=w.sigma)
+                                   sigma_smooth=w.sigma, dynamic=int(dynamic))
     f_d = torch.tensor(f32, device=dev)
     m_d = torch.tensor(w.mask, device=dev)
     vol = torch.empty((w.N, w.H, w.W), dtype=torch.complex64, device=dev)
@@ -240,8 +245,20 @@ def run_ours(args, rank, world, local_rank):
 
     result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-              "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config(w),
+              "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config(w, dynamic=dynamic),
               "roofline": roofline, "gpu_launches": launches, "stages_ms": stages}
+    if dynamic:
+        # one growth step reads the real volume once (max and argmax over the
+        # angles) and a few bytes a pixel of image and set state
+        dr_ms, dr_calls = prof["dr"]
+        per_px = 4 * w.N + 16
+        dr_s = dr_ms / dr_calls / 1e3
+        result["dynamic_restoration"] = {
+            "growth_steps_per_inpaint": dr_calls / args.steps,
+            "ms_per_growth_step": round(dr_s * 1e3, 4),
+            "algorithmic_bytes_per_growth_step": per_px * w.H * w.W,
+            "hbm_gbs": round(per_px * w.H * w.W / dr_s / 1e9, 1),
+            "bytes_basis": "4 N bytes a pixel (the real volume, read once) + 16 (h, argmax, set, reference)"}
     result["clocks"] = clocks.summary()
 
     # end to end from pinned host buffers through se2n_inpaint_host
@@ -263,8 +280,9 @@ def run_ours(args, rank, world, local_rank):
                      "d2h_bytes_per_step": o_h.numel() * 4, "api": "se2n_inpaint_host (pinned host buffers)"}
 
     # error of this result against the FP64 oracle (stored reference, same inputs)
-    if rank == 0 and os.path.exists(GOLDEN):
-        g = np.load(GOLDEN)
+    golden = GOLDEN_DYNAMIC if dynamic else GOLDEN
+    if rank == 0 and os.path.exists(golden):
+        g = np.load(golden)
         b_d = torch.tensor(g["bins"], device=dev)
         with torch.cuda.stream(stream):
             se2n.se2n_inpaint(plan, f_d, m_d, b_d, prm, vol, out)
@@ -281,7 +299,7 @@ def run_ours(args, rank, world, local_rank):
             "oracle_seconds_for_this_result": float(g["oracle_seconds"][0])}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        result["cpu_baseline"] = cpu_baseline(w)
+        result["cpu_baseline"] = cpu_baseline(w, dynamic=dynamic)
     plan.close()
     if dist:
         dist.destroy_process_group()
@@ -292,9 +310,10 @@ def run_ours(args, rank, world, local_rank):
 # the oracle as CPU baseline / reference arm
 # ----------------------------------------------------------------------------
 
-def _oracle_sample(w, steps, rounds):
+def _oracle_sample(w, steps, rounds, dynamic=False):
     import oracle
-    p = oracle.Params(N=w.N, beta=w.beta, T=w.T / w.rounds * rounds, steps=steps, rounds=rounds, eps=w.eps)
+    p = oracle.Params(N=w.N, beta=w.beta, T=w.T / w.rounds * rounds, steps=steps, rounds=rounds, eps=w.eps,
+                      dynamic=int(dynamic))
     f = w.f.astype(np.float32).astype(np.float64)
     t0 = time.perf_counter()
     oracle.inpaint(f, w.mask, p)
@@ -302,12 +321,13 @@ def _oracle_sample(w, steps, rounds):
     return w.H * w.W * w.N * steps * rounds, dt
 
 
-def cpu_baseline(w, steps=75, rounds=2):
-    upd, dt = _oracle_sample(w, steps, rounds)
+def cpu_baseline(w, steps=75, rounds=2, dynamic=False):
+    upd, dt = _oracle_sample(w, steps, rounds, dynamic)
     return {"value": upd / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"the FP64 oracle's whole inpaint of the same 512x512 N=32 image with {rounds} intervals "
-                      f"x {steps} CN steps ({upd:.3g} updates, {dt:.1f} s), all host cores (OpenMP over "
-                      "frequencies, numpy FFTs)"}
+                      f"x {steps} CN steps ({upd:.3g} updates, {dt:.1f} s)"
+                      + (", dynamic restoration" if dynamic else "")
+                      + ", all host cores (OpenMP over frequencies, numpy FFTs)"}
 
 
 def run_batch(args, rank, world, local_rank):
@@ -854,19 +874,22 @@ def run_reference(args, rank, world):
                                f"each step: the FP64 oracle's inpaint of the next image of the batch with {steps} "
                                "CN steps (same dt), all host cores")
     w = _workload()
-    steps, rounds = 20, 1
+    dynamic = args.workload == "dr"
+    # with dynamic restoration two intervals, so that the sample holds a growth step
+    steps, rounds = (10, 2) if dynamic else (20, 1)
     for _ in range(args.warmup):
-        _oracle_sample(w, steps, rounds)
+        _oracle_sample(w, steps, rounds, dynamic)
     times, upd = [], 0
     for _ in range(args.steps):
-        upd, dt = _oracle_sample(w, steps, rounds)
+        upd, dt = _oracle_sample(w, steps, rounds, dynamic)
         times.append(dt)
     total = sum(times)
     value = upd * args.steps / total
-    sample = (f"each step: the FP64 oracle's inpaint of the 512x512 N=32 image with {rounds} interval x {steps} "
-              f"CN steps ({upd:.3g} updates), all host cores")
+    sample = (f"each step: the FP64 oracle's inpaint of the 512x512 N=32 image with {rounds} interval(s) x {steps} "
+              f"CN steps ({upd:.3g} updates){', dynamic restoration' if dynamic else ''}, all host cores")
     return _reference_line(args, world, METRIC, UNIT, value, total / args.steps * 1e3,
-                           _config(w, {"reference_sample": f"{rounds} x {steps} steps per step"}), sample)
+                           _config(w, {"reference_sample": f"{rounds} x {steps} steps per step"}, dynamic=dynamic),
+                           sample)
 
 
 def main():
@@ -876,9 +899,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["512", "batch", "surrogate", "unet-forward"], default="512",
-                    help="512: the 512x512 N=32 10x500-step inpaint (default); batch: 256 uneven images; "
-                         "surrogate: train the U-Net on method pairs, time its inference with fallback")
+    ap.add_argument("--workload", choices=["512", "dr", "batch", "surrogate", "unet-forward"], default="512",
+                    help="512: the 512x512 N=32 10x500-step inpaint (default); dr: the same with dynamic "
+                         "restoration; batch: 256 uneven images; surrogate: train the U-Net on method pairs, "
+                         "time its inference with fallback")
     ap.add_argument("--train-seconds", type=float, default=150.0, help="surrogate training time budget")
     ap.add_argument("--train-pairs", type=int, default=0, help="surrogate training pairs (0: all 20000)")
     ap.add_argument("--traffic", type=float, default=None,

@@ -281,7 +281,8 @@ SE2N_API se2n_status se2n_plan_diffuse_info(se2n_plan *plan, int *regs_per_threa
 #define SE2N_STAGE_DIFFUSE 3
 #define SE2N_STAGE_MIX 4
 #define SE2N_STAGE_PROJECT 5
-#define SE2N_NUM_STAGES 6
+#define SE2N_STAGE_DR 6       /* growth steps of dynamic restoration */
+#define SE2N_NUM_STAGES 7
 
 typedef struct se2n_profile {
     double ms[SE2N_NUM_STAGES];       /* device time accumulated per stage, milliseconds */

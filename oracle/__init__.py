@@ -344,10 +344,10 @@ def dr_grow(vol, mask, fref, bins, dtype=np.float64, return_margin=False):
     decision the way an FP32 kernel summing in the same order does.
 
     Returns (mask, fref, bins) of G_i as new arrays, and with return_margin
-    also the smallest |h - mean| over the boundary pixels whose block holds
-    another bad pixel (inf if none): how far the closest decision that
-    rounding could change is from a tie. A pixel whose 8 neighbours are all
-    good compares h with itself and never joins, in any precision."""
+    also the map of |h - mean| over the boundary pixels whose block holds
+    another bad pixel (inf elsewhere): how far each decision that rounding
+    could change is from a tie. A pixel whose 8 neighbours are all good
+    compares h with itself and never joins, in any precision."""
     re = np.asarray(vol).real.astype(dtype)
     h = re.max(axis=0)
     amax = np.argmax(re, axis=0).astype(np.uint8)
@@ -376,7 +376,7 @@ def dr_grow(vol, mask, fref, bins, dtype=np.float64, return_margin=False):
     new_bins = np.where(join, amax, np.asarray(bins)).astype(np.uint8)
     if return_margin:
         cand = bad & boundary & (cnt >= 2)
-        margin = float(np.abs(h - mean)[cand].min()) if cand.any() else float("inf")
+        margin = np.where(cand, np.abs(h - mean).astype(np.float64), np.inf)
         return new_mask, new_fref, new_bins, margin
     return new_mask, new_fref, new_bins
 
@@ -385,7 +385,7 @@ def dr_grow(vol, mask, fref, bins, dtype=np.float64, return_margin=False):
 # the whole method
 # ----------------------------------------------------------------------------
 
-def inpaint(f, mask, p: Params, bins=None, nthreads=0, keep=False):
+def inpaint(f, mask, p: Params, bins=None, nthreads=0, keep=False, tie_tol=0.0):
     """Lift, then `rounds` intervals of length T/rounds: the first starts
     from the lift; each later one starts from the statically restored state
     (the mix at t_0 is the identity, sigma = 1). The state at T is inverted
@@ -398,20 +398,23 @@ def inpaint(f, mask, p: Params, bins=None, nthreads=0, keep=False):
 
     Returns a dict with out (the image), bins, the final good set (mask_final,
     equal to the given one without dynamic), the smallest decision margin of
-    the growth steps (dr_margin, inf without dynamic) and, if keep, the final
-    volume."""
+    the growth steps (dr_margin, inf without dynamic), the pixels whose
+    decision came within tie_tol of a tie in some growth step (dr_ties) and,
+    if keep, the final volume."""
     if bins is None:
         bins = orient(f, mask, p.N, p.sigma, p.angle_conv, p.flat_tol)["bins"]
     g_mask = (np.asarray(mask) != 0).astype(np.uint8)
     g_fref = np.asarray(f, dtype=np.float64) * g_mask
     g_bins = np.asarray(bins).astype(np.uint8)
     margin = float("inf")
+    ties = np.zeros(g_mask.shape, dtype=bool)
 
     def restore(v):
-        nonlocal g_mask, g_fref, g_bins, margin
+        nonlocal g_mask, g_fref, g_bins, margin, ties
         if p.dynamic:
             g_mask, g_fref, g_bins, m = dr_grow(v, g_mask, g_fref, g_bins, return_margin=True)
-            margin = min(margin, m)
+            margin = min(margin, float(m.min()))
+            ties |= m < tie_tol
         return mix(v, g_fref, g_mask, g_bins, p.eps, p.guard)
 
     Tr = p.T / p.rounds
@@ -426,7 +429,7 @@ def inpaint(f, mask, p: Params, bins=None, nthreads=0, keep=False):
     out = project(v, p.proj)
     if p.reinject:
         out = np.where(np.asarray(mask) != 0, np.asarray(f, dtype=np.float64), out)
-    res = dict(out=out, bins=bins, mask_final=g_mask, dr_margin=margin)
+    res = dict(out=out, bins=bins, mask_final=g_mask, dr_margin=margin, dr_ties=ties)
     if keep:
         res["vol"] = v
     return res

@@ -268,7 +268,7 @@ se2n_status dr_begin(se2n_plan *plan, DrState &d, const float *f, const uint8_t 
 
 // One growth step from the (unnormalised, times scale) volume.
 se2n_status dr_step(se2n_plan *plan, DrState &d, const float2 *vol, float scale, bool half) {
-    StageTimer timer(plan, SE2N_STAGE_MIX);
+    StageTimer timer(plan, SE2N_STAGE_DR);
     plan->kernels += 2;
     cudaError_t e = half ? se2n_launch_dr_max_r((const float *)vol, plan->H, plan->W, plan->N, scale, d.h, d.amax,
                                                 plan->stream)
@@ -563,7 +563,7 @@ se2n_status se2n_dr_grow(se2n_plan *plan, const void *vol, const uint8_t *mask_i
     if (a < o + HW && o < a + HW) return SE2N_EINVAL;  // the step reads the old set while writing the new one
     SE2N_TRY(dr_alloc(plan->dr, plan->HW));  // h and the argmax angles
     DrState &d = plan->dr;
-    StageTimer timer(plan, SE2N_STAGE_MIX);
+    StageTimer timer(plan, SE2N_STAGE_DR);
     plan->kernels += 2;
     cudaError_t e = se2n_launch_dr_max((const float2 *)vol, plan->HW, plan->N, 1.0f, d.h, d.amax, plan->stream);
     if (e == cudaSuccess)

@@ -39,11 +39,12 @@ class Se2nError(RuntimeError):
         super().__init__(f"{where}: {se2n_status_string(status)} (status {status})")
 
 
-SE2N_STAGES = ("orient", "lift", "fft", "diffuse", "mix", "project")
+SE2N_STAGES = ("orient", "lift", "fft", "diffuse", "mix", "project", "dr")
 
 
 class se2n_profile(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double * 6), ("calls", ctypes.c_longlong * 6), ("kernels", ctypes.c_longlong)]
+    _fields_ = [("ms", ctypes.c_double * len(SE2N_STAGES)), ("calls", ctypes.c_longlong * len(SE2N_STAGES)),
+                ("kernels", ctypes.c_longlong)]
 
 
 class se2n_image_desc(ctypes.Structure):

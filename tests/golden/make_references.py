@@ -1,12 +1,16 @@
 """Write the FP64 oracle's result for the full 512x512, N=32 workload
 (beta = 0.25, 10 restoration intervals of 500 Crank-Nicolson steps, T = 2
-per interval, eps = 0.5) to curves_noise_512_N32.npz.
+per interval, eps = 0.5) to curves_noise_512_N32.npz, and the same with
+dynamic restoration (Section 5.3) to curves_noise_512_N32_dynamic.npz
+(which also holds the final good set, the smallest decision margin and
+the pixels whose decision came within 1e-5 of a tie in some growth step).
 
 Calls only oracle/ and synth/. The orientation bins are the oracle's own
 (FP64 decision on the FP32-rounded image the GPU also receives); the stored
 image is the oracle's projected output, rounded to float32 (its 6e-8
 relative resolution is far below the 1e-5 comparison tolerance).
-Takes about 3 minutes on 8 cores.
+Takes about 3 minutes on 8 cores per file; `python make_references.py
+dynamic` writes only the second.
 """
 import os
 import sys
@@ -21,20 +25,34 @@ import oracle  # noqa: E402
 import synth  # noqa: E402
 
 OUT = os.path.join(HERE, "curves_noise_512_N32.npz")
+OUT_DYNAMIC = os.path.join(HERE, "curves_noise_512_N32_dynamic.npz")
+# a growth decision this close to a tie may go either way in FP32 (the GPU's
+# images differ from the oracle's by ~1e-7 of max|f|)
+TIE_TOL = 1e-5
+
+
+def write(path, dynamic):
+    w = synth.workload_512()
+    f = w.f.astype(np.float32).astype(np.float64)
+    p = oracle.Params(N=w.N, beta=w.beta, T=w.T, steps=w.steps, rounds=w.rounds, eps=w.eps, dynamic=dynamic)
+    bins = oracle.orient(f, w.mask, p.N)["bins"]
+    t0 = time.time()
+    res = oracle.inpaint(f, w.mask, p, bins=bins, tie_tol=TIE_TOL)
+    secs = time.time() - t0
+    extra = {}
+    if dynamic:
+        extra = dict(mask_final=res["mask_final"], dr_margin=np.array([res["dr_margin"]]),
+                     dr_ties=res["dr_ties"], tie_tol=np.array([TIE_TOL]))
+    np.savez_compressed(path, out=res["out"].astype(np.float32), bins=bins,
+                        params=np.array([p.N, p.beta, p.T, p.steps, p.rounds, p.eps]),
+                        oracle_seconds=np.array([secs]), **extra)
+    print(f"wrote {path} in {secs:.1f} s")
 
 
 def main():
-    w = synth.workload_512()
-    f = w.f.astype(np.float32).astype(np.float64)
-    p = oracle.Params(N=w.N, beta=w.beta, T=w.T, steps=w.steps, rounds=w.rounds, eps=w.eps)
-    bins = oracle.orient(f, w.mask, p.N)["bins"]
-    t0 = time.time()
-    out = oracle.inpaint(f, w.mask, p, bins=bins)["out"]
-    secs = time.time() - t0
-    np.savez_compressed(OUT, out=out.astype(np.float32), bins=bins,
-                        params=np.array([p.N, p.beta, p.T, p.steps, p.rounds, p.eps]),
-                        oracle_seconds=np.array([secs]))
-    print(f"wrote {OUT} in {secs:.1f} s")
+    if sys.argv[1:] != ["dynamic"]:
+        write(OUT, 0)
+    write(OUT_DYNAMIC, 1)
 
 
 if __name__ == "__main__":

@@ -91,8 +91,15 @@ def test_autotuned_shape_gives_the_same_result():
     b1.close()
     assert info["candidates"] == 12 and info["best_ms"] <= info["worst_ms"]
     assert info["tile_passes"] in (2, 8, 32) and info["block"] in (128, 256)
+    # tile and block do not change any frequency's arithmetic; another table
+    # of threads per frequency splits the angles differently (another torn
+    # elimination), which is the same method to FP32 rounding
+    same_split = (info["p16"], info["p32"], info["p64"]) == (1, 2, 4)
     for a, c in zip(ref, got):
-        np.testing.assert_array_equal(a, c)
+        if same_split:
+            np.testing.assert_array_equal(a, c)
+        else:
+            assert rel_l2(c, a) <= REL_L2
 
 
 def test_general_kernel_batch_large_beta_dt():

@@ -47,7 +47,8 @@ def test_hand_worked_step_on_a_vertical_edge():
     assert np.array_equal(b1[unchanged], bins[unchanged])
     # the closest decision: (2,2) at |0.1 - 1/6|
     *_, margin = oracle.dr_grow(vol, mask, fref, bins, return_margin=True)
-    assert margin == pytest.approx(1.0 / 6.0 - 0.1, rel=1e-12)
+    assert margin.min() == pytest.approx(1.0 / 6.0 - 0.1, rel=1e-12)
+    assert np.isfinite(margin).sum() == 4 and np.all(np.isfinite(margin[:, 2]))
 
 
 def test_diagonal_neighbour_counts_and_good_values_are_excluded():
@@ -89,7 +90,7 @@ def test_a_lone_bad_pixel_never_joins_and_has_no_margin():
     h[1, 1] = 9.0
     vol, _ = _vol_from_image(h, seed=3)
     m1, _, _, margin = oracle.dr_grow(vol, mask, np.zeros((3, 3)), np.zeros((3, 3), np.uint8), return_margin=True)
-    assert np.array_equal(m1, mask) and margin == float("inf")
+    assert np.array_equal(m1, mask) and np.all(np.isinf(margin))
 
 
 def test_first_maximum_gives_the_bin():
