@@ -73,6 +73,17 @@ typedef enum se2n_status {
 #define SE2N_DIFFUSE_SPLIT_DIAG 2  /* keep a_r^2/beta apart from the angular second difference
                                       (always on when beta * T > 8, see se2n_diffuse) */
 #define SE2N_DIFFUSE_FULL_CORRECTION 4  /* apply the corner correction on every angle (no truncation) */
+/* Integrate by the S-step propagator: for every class of frequencies with
+ * equal coefficients (rows k and (H/2 - k) mod H, columns l and (W/2 - l)
+ * mod W) the matrix (B-^{-1} B+)^S - I is built once in FP32 by binary
+ * powering in increment form and applied as one N x N product per frequency
+ * (Section 4: the integration over an interval is one linear map). The same
+ * result as S Crank-Nicolson steps up to rounding. The plan keeps the
+ * matrices (4 N^2 bytes a class, about H W N^2 bytes in all) and reuses them
+ * while beta dt, S and the spectrum half stay the same, so the intervals of
+ * one inpaint build them once. N = 16, 32 or 64 (else SE2N_EUNSUPPORTED);
+ * the other flags do not apply. */
+#define SE2N_DIFFUSE_PROPAGATOR 8
 
 /* Largest N the library has kernels for. */
 #define SE2N_MAX_N 64
@@ -282,7 +293,8 @@ SE2N_API se2n_status se2n_plan_diffuse_info(se2n_plan *plan, int *regs_per_threa
 #define SE2N_STAGE_MIX 4
 #define SE2N_STAGE_PROJECT 5
 #define SE2N_STAGE_DR 6       /* growth steps of dynamic restoration */
-#define SE2N_NUM_STAGES 7
+#define SE2N_STAGE_PROPAGATOR 7  /* building S-step propagators (applying them counts as diffusion) */
+#define SE2N_NUM_STAGES 8
 
 typedef struct se2n_profile {
     double ms[SE2N_NUM_STAGES];       /* device time accumulated per stage, milliseconds */

@@ -100,14 +100,66 @@ void angle_table(int N, int angle_conv, float *cs, float *sn, int count) {
 
 namespace {
 
+// The S-step propagators of every class of equal-coefficient frequencies,
+// built when beta dt, S or the spectrum half changed, then applied once.
+se2n_status propagate_impl(se2n_plan *plan, float2 *vol, double beta, double bdt, int steps, bool half) {
+    if (!se2n_prop_supported(plan->N)) return SE2N_EUNSUPPORTED;
+    PropArgs a;
+    a.vol = vol;
+    a.H = plan->H;
+    a.W = plan->W;
+    a.Wc = half ? plan->Wc : plan->W;
+    a.HW = (long long)a.H * a.Wc;
+    a.half = half ? 1 : 0;
+    a.col_slots = se2n_prop_col_slots(plan->W, half);
+    a.classes = se2n_prop_classes(plan->H, plan->W, half);
+    a.steps = steps;
+    a.inv_c = (float)(2.0 / bdt);
+    a.inv_beta = (float)(1.0 / beta);
+    angle_table(plan->N, plan->angle_conv, a.cs, a.sn, SE2N_MAX_N);
+    const size_t need = (size_t)a.classes * plan->N * plan->N * sizeof(float);
+    if (plan->prop_bytes < need) {
+        cudaFree(plan->prop_D);
+        plan->prop_D = nullptr;
+        plan->prop_bytes = 0;
+        plan->prop_valid = false;
+        cudaError_t e = cudaMalloc(&plan->prop_D, need);
+        if (e != cudaSuccess) {
+            plan->prop_D = nullptr;
+            (void)cudaGetLastError();
+            return e == cudaErrorMemoryAllocation ? SE2N_ENOMEM : SE2N_ECUDA;
+        }
+        plan->prop_bytes = need;
+    }
+    a.D = plan->prop_D;
+    if (!(plan->prop_valid && plan->prop_beta == beta && plan->prop_bdt == bdt && plan->prop_steps == steps &&
+          plan->prop_half == half)) {
+        plan->prop_valid = false;
+        StageTimer timer(plan, SE2N_STAGE_PROPAGATOR);
+        plan->kernels += 1;
+        SE2N_TRY(cuda_status(plan, se2n_launch_prop_build(plan->N, a, plan->num_sms, plan->stream)));
+        plan->prop_valid = true;
+        plan->prop_beta = beta;
+        plan->prop_bdt = bdt;
+        plan->prop_steps = steps;
+        plan->prop_half = half;
+    }
+    StageTimer timer(plan, SE2N_STAGE_DIFFUSE);
+    plan->kernels += 1;
+    return cuda_status(plan, se2n_launch_prop_apply(plan->N, a, plan->num_sms, plan->stream));
+}
+
 // half: vol holds the Hermitian half [N][H][W/2 + 1] of the spectrum.
 se2n_status diffuse_impl(se2n_plan *plan, float2 *vol, double beta, double T, int steps, int flags, bool half = false) {
     if (!(beta > 0.0) || !(T >= 0.0) || steps < 1 || !isfinite(beta) || !isfinite(T)) return SE2N_EINVAL;
-    if (flags & ~(SE2N_DIFFUSE_SM_FP64 | SE2N_DIFFUSE_SPLIT_DIAG | SE2N_DIFFUSE_FULL_CORRECTION)) return SE2N_EINVAL;
+    if (flags & ~(SE2N_DIFFUSE_SM_FP64 | SE2N_DIFFUSE_SPLIT_DIAG | SE2N_DIFFUSE_FULL_CORRECTION |
+                  SE2N_DIFFUSE_PROPAGATOR))
+        return SE2N_EINVAL;
     if (T == 0.0) return SE2N_OK;
     const double dt = T / steps;
     const double bdt = beta * dt;
     if (!(bdt >= 1e-30 && bdt <= 1e3)) return SE2N_ENUMERIC;
+    if (flags & SE2N_DIFFUSE_PROPAGATOR) return propagate_impl(plan, vol, beta, bdt, steps, half);
     const bool fp64 = (flags & SE2N_DIFFUSE_SM_FP64) != 0;
     // The fused diagonal 2 + a^2/beta perturbs decay rates by ~1.2e-7 beta per
     // unit time; past beta T = 8 that exceeds 1e-6 and the split form is used.
@@ -303,8 +355,8 @@ se2n_status check_params(const se2n_plan *plan, const se2n_params *p) {
         (p->reinject != 0 && p->reinject != 1) || (p->full_spectrum != 0 && p->full_spectrum != 1) ||
         (p->dynamic != 0 && p->dynamic != 1))
         return SE2N_EINVAL;
-    if (!(p->guard >= 0.0) ||
-        (p->diffuse_flags & ~(SE2N_DIFFUSE_SM_FP64 | SE2N_DIFFUSE_SPLIT_DIAG | SE2N_DIFFUSE_FULL_CORRECTION)))
+    if (!(p->guard >= 0.0) || (p->diffuse_flags & ~(SE2N_DIFFUSE_SM_FP64 | SE2N_DIFFUSE_SPLIT_DIAG |
+                                                    SE2N_DIFFUSE_FULL_CORRECTION | SE2N_DIFFUSE_PROPAGATOR)))
         return SE2N_EINVAL;
     if (!isfinite(p->beta) || !isfinite(p->T) || !isfinite(p->sigma_smooth) || !isfinite(p->guard))
         return SE2N_EINVAL;
@@ -391,6 +443,7 @@ void free_plan(se2n_plan *plan) {
     cudaFree(plan->h_mask);
     cudaFree(plan->h_vol);
     dr_free(plan->dr);
+    cudaFree(plan->prop_D);
     for (int st = 0; st < SE2N_NUM_STAGES; ++st)
         for (cudaEvent_t e : plan->stage_ev[st]) cudaEventDestroy(e);
     delete plan;

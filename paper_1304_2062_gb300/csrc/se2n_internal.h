@@ -42,6 +42,14 @@ struct se2n_plan {
     // (ping-pong), the reference values and bins the restoration pulls the
     // good pixels to, and the image value and argmax angle of the last step
     DrState dr;
+    // S-step propagators (SE2N_DIFFUSE_PROPAGATOR), kept for the next call
+    // with the same beta dt, S and spectrum half
+    float *prop_D;
+    size_t prop_bytes;
+    bool prop_valid;
+    double prop_beta, prop_bdt;
+    int prop_steps;
+    bool prop_half;
     // diffusion launch configuration
     int diffuse_P;         // threads per frequency
     int diffuse_block;     // threads per block; 0 = the default shape for N
@@ -77,6 +85,28 @@ struct DiffuseArgs {
     float cs[SE2N_MAX_N];
     float sn[SE2N_MAX_N];
 };
+
+// Parameters of the propagator kernels (propagator.cu): build D_S for every
+// class of frequencies with equal coefficients, or apply it to the volume.
+struct PropArgs {
+    float *D;          // [classes][N][N] row-major, D_S = (B-^{-1} B+)^S - I
+    float2 *vol;       // [N][H][Wc] complex (apply only)
+    int H, W, Wc;
+    long long HW;      // H * Wc
+    int col_slots;     // column classes a row class
+    long long classes;
+    int steps;         // S
+    float inv_c;       // 2 / (beta dt)
+    float inv_beta;
+    int half;          // 1: the Hermitian half (columns l <= W/2), 0: all W columns
+    float cs[SE2N_MAX_N];
+    float sn[SE2N_MAX_N];
+};
+bool se2n_prop_supported(int N);
+int se2n_prop_col_slots(int W, bool half);
+long long se2n_prop_classes(int H, int W, bool half);
+cudaError_t se2n_launch_prop_build(int N, const PropArgs &a, int num_sms, cudaStream_t s);
+cudaError_t se2n_launch_prop_apply(int N, const PropArgs &a, int num_sms, cudaStream_t s);
 
 // Host helpers shared by the single-image and batched paths (capi.cu).
 StepParams step_params(double beta, double beta_dt, int steps);

@@ -27,6 +27,7 @@ SE2N_PROJ_MEAN = 1
 SE2N_DIFFUSE_SM_FP64 = 1
 SE2N_DIFFUSE_SPLIT_DIAG = 2
 SE2N_DIFFUSE_FULL_CORRECTION = 4
+SE2N_DIFFUSE_PROPAGATOR = 8
 SE2N_MAX_N = 64
 SE2N_BATCH_AUTOTUNE = 1
 SE2N_NOALLOC_MAX_VOLUMES = 64
@@ -39,7 +40,7 @@ class Se2nError(RuntimeError):
         super().__init__(f"{where}: {se2n_status_string(status)} (status {status})")
 
 
-SE2N_STAGES = ("orient", "lift", "fft", "diffuse", "mix", "project", "dr")
+SE2N_STAGES = ("orient", "lift", "fft", "diffuse", "mix", "project", "dr", "propagator")
 
 
 class se2n_profile(ctypes.Structure):

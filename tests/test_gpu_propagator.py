@@ -1,0 +1,144 @@
+"""The S-step propagator path (SE2N_DIFFUSE_PROPAGATOR) against the FP64
+oracle's step-by-step Crank-Nicolson integration, through the C ABI.
+
+The propagator is the same linear map as S steps, built in FP32 by binary
+powering in increment form, so it is held to the step kernel's tolerance:
+single calls over every supported N, S from 1 to 500 (powers of two and
+not), beta dt from 1e-3 to 10, odd-sized and non-square planes; whole
+inpaints on both spectrum layouts; the full 512x512, N=32 workload against
+the stored oracle result; and the plan's reuse of the matrices."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from _gpu import MAX_REL_RESTORED, REL_L2, host, rel_l2, t_c64, t_f32, t_u8
+
+pytestmark = pytest.mark.gpu
+
+se2n = pytest.importorskip("paper_1304_2062_gb300.se2n")
+
+import torch  # noqa: E402
+
+PROP = se2n.SE2N_DIFFUSE_PROPAGATOR
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "curves_noise_512_N32.npz")
+
+
+def _run(vol, N, beta, T, S, flags):
+    _, H, W = vol.shape
+    plan = se2n.se2n_plan_create(H, W, N)
+    v = t_c64(vol)
+    se2n.se2n_diffuse(plan, v, beta, T, S, flags)
+    out = host(v)
+    plan.close()
+    return out
+
+
+@pytest.mark.parametrize("N,H,W,beta,T,S", [
+    (16, 34, 22, 0.5, 1.0, 20), (32, 30, 26, 0.3, 2.0, 15), (64, 18, 14, 0.25, 2.0, 37),
+    (32, 40, 40, 0.25, 2.0, 500), (32, 20, 24, 0.25, 2.0, 1), (32, 20, 24, 0.25, 2.0, 2),
+    (16, 12, 64, 0.25, 2.0, 256), (64, 22, 30, 0.7, 3.0, 100),
+    (32, 18, 14, 10.0, 20.0, 20), (64, 18, 14, 10.0, 20.0, 20), (16, 2, 6, 0.5, 1.0, 9)])
+def test_propagator_matches_oracle(N, H, W, beta, T, S):
+    vol = synth.random_volume(N, H, W, seed=N + H + S).astype(np.complex64)
+    ref = oracle.diffuse(vol.astype(np.complex128), beta, T, S)
+    got = _run(vol, N, beta, T, S, PROP)
+    steps = _run(vol, N, beta, T, S, 0)
+    e_ref, e_steps = rel_l2(got, ref), rel_l2(got, steps)
+    print(f"N={N} {H}x{W} beta*dt={beta * T / S:.3g} S={S}: rel-L2 vs oracle {e_ref:.2e}, "
+          f"vs the step kernel {e_steps:.2e}")
+    assert e_ref <= REL_L2
+    assert e_steps <= 2 * REL_L2
+
+
+def test_lifted_image_spectrum():
+    """The workload's shape: the DFT of a lifted image, dominated by the low
+    frequencies, 500 steps."""
+    w = synth.workload_512(H=64, W=96, steps=500, rounds=1)
+    bins = oracle.orient(w.f, w.mask, 32)["bins"]
+    vol = oracle.forward(oracle.lift(w.f, w.mask, bins, 32))
+    ref = oracle.diffuse(vol, 0.25, 2.0, 500)
+    got = _run(vol.astype(np.complex64), 32, 0.25, 2.0, 500, PROP)
+    err = rel_l2(got, ref)
+    print(f"lifted 64x96 N=32 500 steps: rel-L2 {err:.2e}")
+    assert err <= REL_L2
+
+
+def test_unsupported_angle_count():
+    plan = se2n.se2n_plan_create(8, 8, 30)
+    v = torch.zeros((30, 8, 8), dtype=torch.complex64, device="cuda")
+    with pytest.raises(se2n.Se2nError) as e:
+        se2n.se2n_diffuse(plan, v, 0.25, 1.0, 10, PROP)
+    assert e.value.status == se2n.SE2N_EUNSUPPORTED
+    plan.close()
+
+
+def test_matrices_are_rebuilt_only_when_the_step_changes():
+    vol = synth.random_volume(32, 16, 20, seed=4).astype(np.complex64)
+    plan = se2n.se2n_plan_create(16, 20, 32)
+    se2n.se2n_plan_profile(plan, True)
+    outs = []
+    for beta, T, S in [(0.25, 2.0, 50), (0.25, 2.0, 50), (0.5, 2.0, 50), (0.5, 2.0, 60), (0.5, 2.0, 60)]:
+        v = t_c64(vol)
+        se2n.se2n_diffuse(plan, v, beta, T, S, PROP)
+        outs.append((host(v), oracle.diffuse(vol.astype(np.complex128), beta, T, S)))
+    prof = se2n.se2n_plan_profile_read(plan)
+    plan.close()
+    assert prof["propagator"][1] == 3 and prof["diffuse"][1] == 5
+    for got, ref in outs:
+        assert rel_l2(got, ref) <= REL_L2
+
+
+def _params(p, full=0):
+    return se2n.se2n_params_default(N=p.N, beta=p.beta, T=p.T, steps=p.steps, rounds=p.rounds, eps=p.eps,
+                                    sigma_smooth=p.sigma, flat_tol=p.flat_tol, proj=p.proj,
+                                    final_mix=p.final_mix, guard=p.guard, reinject=p.reinject,
+                                    full_spectrum=full, diffuse_flags=PROP)
+
+
+def _gpu_inpaint(f32, mask, bins, prm, profile=False):
+    H, W = f32.shape
+    plan = se2n.se2n_plan_create(H, W, prm.N)
+    vol = torch.empty((prm.N, H, W), dtype=torch.complex64, device="cuda")
+    out = torch.empty((H, W), dtype=torch.float32, device="cuda")
+    if profile:
+        se2n.se2n_plan_profile(plan, True)
+    se2n.se2n_inpaint(plan, t_f32(f32), t_u8(mask), t_u8(bins), prm, vol, out)
+    got = host(out)
+    prof = se2n.se2n_plan_profile_read(plan) if profile else None
+    plan.close()
+    return got, prof
+
+
+@pytest.mark.parametrize("H,W,N,full", [(96, 96, 32, 0), (64, 160, 32, 1), (64, 64, 16, 0), (48, 80, 64, 0)])
+def test_inpaint_with_propagators_matches_oracle(H, W, N, full):
+    w = synth.workload_512(H=H, W=W, steps=60, rounds=3)
+    p = oracle.Params(N=N, beta=0.25, T=6.0, steps=60, rounds=3)
+    f32 = w.f.astype(np.float32)
+    f64 = f32.astype(np.float64)
+    bins = oracle.orient(f64, w.mask, p.N, p.sigma, 0, p.flat_tol)["bins"]
+    ref = oracle.inpaint(f64, w.mask, p, bins=bins)["out"]
+    got, prof = _gpu_inpaint(f32, w.mask, bins, _params(p, full), profile=True)
+    mx = np.abs(got - ref).max() / np.abs(f64).max()
+    r2 = rel_l2(got, ref)
+    print(f"{H}x{W} N={N} full={full}: max-abs/max|f| {mx:.2e}, rel-L2 {r2:.2e}")
+    assert prof["propagator"][1] == 1 and prof["diffuse"][1] == 3   # built once, applied every interval
+    assert mx <= MAX_REL_RESTORED
+    assert r2 <= REL_L2
+
+
+def test_full_512_N32_ten_rounds_against_stored_oracle():
+    if not os.path.exists(GOLDEN):
+        pytest.fail("missing tests/golden/curves_noise_512_N32.npz: run tests/golden/make_references.py")
+    g = np.load(GOLDEN)
+    w = synth.workload_512()
+    p = oracle.Params(N=32, beta=0.25, T=20.0, steps=500, rounds=10)
+    got, _ = _gpu_inpaint(w.f.astype(np.float32), w.mask, g["bins"], _params(p))
+    ref = g["out"].astype(np.float64)
+    mx = np.abs(got - ref).max() / np.abs(w.f).max()
+    r2 = rel_l2(got, ref)
+    print(f"512x512 propagators: max-abs/max|f| {mx:.2e}, rel-L2 {r2:.2e}")
+    assert mx <= MAX_REL_RESTORED
+    assert r2 <= REL_L2
