@@ -79,7 +79,8 @@ typedef enum se2n_status {
  * powering in increment form and applied as one N x N product per frequency
  * (Section 4: the integration over an interval is one linear map). The same
  * result as S Crank-Nicolson steps up to rounding. The plan keeps the
- * matrices (4 N^2 bytes a class, about H W N^2 bytes in all) and reuses them
+ * matrices (symmetric, stored by cyclic diagonals: 4 N (N/2 + 1) bytes a
+ * class, about H W N^2 / 2 bytes in all) and reuses them
  * while beta dt, S and the spectrum half stay the same, so the intervals of
  * one inpaint build them once. N = 16, 32 or 64 (else SE2N_EUNSUPPORTED);
  * the other flags do not apply. */
@@ -265,6 +266,12 @@ SE2N_API se2n_status se2n_inpaint(se2n_plan *plan, const float *f, const uint8_t
  * and out_host are host memory (pinned memory makes the copies faster). */
 SE2N_API se2n_status se2n_inpaint_host(se2n_plan *plan, const float *f_host, const uint8_t *mask_host,
                               const se2n_params *p, float *out_host);
+
+/* Forget the S-step propagators the plan keeps for SE2N_DIFFUSE_PROPAGATOR:
+ * the next such call builds them again. free_memory != 0 also releases their
+ * device memory (allocated again on next use). Enqueues nothing; waits for
+ * the plan's stream first when it frees. */
+SE2N_API se2n_status se2n_plan_drop_propagators(se2n_plan *plan, int free_memory);
 
 /* Tuning of the diffusion launch (used by the autotuner): threads per
  * frequency P (1, 2 or 4; 0 = default for the plan's N), threads per block

@@ -117,7 +117,7 @@ se2n_status propagate_impl(se2n_plan *plan, float2 *vol, double beta, double bdt
     a.inv_c = (float)(2.0 / bdt);
     a.inv_beta = (float)(1.0 / beta);
     angle_table(plan->N, plan->angle_conv, a.cs, a.sn, SE2N_MAX_N);
-    const size_t need = (size_t)a.classes * plan->N * plan->N * sizeof(float);
+    const size_t need = (size_t)a.classes * (size_t)se2n_prop_floats(plan->N) * sizeof(float);
     if (plan->prop_bytes < need) {
         cudaFree(plan->prop_D);
         plan->prop_D = nullptr;
@@ -678,6 +678,18 @@ se2n_status se2n_inpaint_host(se2n_plan *plan, const float *f_host, const uint8_
     SE2N_TRY(cuda_status(plan, cudaMemcpyAsync(out_host, plan->h_out, sizeof(float) * HW, cudaMemcpyDeviceToHost,
                                                plan->stream)));
     return cuda_status(plan, cudaStreamSynchronize(plan->stream));
+}
+
+se2n_status se2n_plan_drop_propagators(se2n_plan *plan, int free_memory) {
+    SE2N_TRY(check_plan(plan));
+    plan->prop_valid = false;
+    if (free_memory && plan->prop_D) {
+        SE2N_TRY(cuda_status(plan, cudaStreamSynchronize(plan->stream)));
+        cudaFree(plan->prop_D);
+        plan->prop_D = nullptr;
+        plan->prop_bytes = 0;
+    }
+    return SE2N_OK;
 }
 
 se2n_status se2n_plan_tune_diffuse(se2n_plan *plan, int threads_per_freq, int block_threads, int blocks) {

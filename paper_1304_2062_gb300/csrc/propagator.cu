@@ -22,6 +22,12 @@
 // and the propagator is applied as x <- x + D_S x, so rounding is relative to
 // the change of x, as in the step-by-step integration.
 //
+// Storage. B+ and B- are polynomials in one symmetric matrix, so M and D_S
+// are symmetric. D_S is kept by cyclic diagonals, S_m[i] = D[i, (i + m) mod N]
+// for m = 0 .. N/2 (the mean of the two mirrored FP32 entries): N (N/2 + 1)
+// floats a class instead of N^2, and a lane i of the apply reads S_m[i] and
+// S_m[i - m], both coalesced across the warp.
+//
 // One step in scaled form: A' = (1/c) I - L, c = beta dt / 2, L the operator
 // divided by beta (diagonal -2 - a_r^2/beta, off-diagonals and corners 1);
 // x_{n+1} = x_n + 2 A'^{-1} L x_n. D_1 is built column by column: column i
@@ -48,18 +54,22 @@ __device__ __forceinline__ void pair_row(int s, int H, int &k, int &kb) {
 
 namespace {
 
-constexpr int kPropWarps = 4;   // warps a block in the build kernel
 constexpr int kApplyWarps = 8;  // warps a block in the apply kernel
 
+// Build kernel: one lane a column (N = 64: two), a tile of TR x TC entries of
+// every product a lane.
 template <int N>
 struct PropCfg {
-    static constexpr int LPC = N < 32 ? N : 32;  // lanes a class
-    static constexpr int CPW = 32 / LPC;         // classes a warp
-    static constexpr int CPL = N / LPC;          // columns (or rows) a lane
-    static constexpr int LD = N + 4;             // column stride in shared memory, floats
-    static constexpr int MAT = N * LD;           // floats a matrix
-    static constexpr int CLASS_FLOATS = 3 * MAT + 2 * N + 4;
-    static constexpr int SMEM = kPropWarps * CPW * CLASS_FLOATS * 4;
+    static constexpr int WARPS = N == 64 ? 2 : 4;  // warps a block
+    static constexpr int LPC = N < 32 ? N : 32;    // lanes a class
+    static constexpr int CPW = 32 / LPC;           // classes a warp
+    static constexpr int CPL = N / LPC;            // columns a lane in the column-wise steps
+    static constexpr int LD = N + 4;               // column (or row) stride in shared memory, floats
+    static constexpr int MAT = N * LD;             // floats a matrix
+    // P column- and row-major, R, and the product's two layouts; pivots, q, scalars
+    static constexpr int CLASS_FLOATS = 5 * MAT + 2 * N + 4;
+    static constexpr int SBLK = (N / 2 + 1) * N;   // stored floats a class
+    static constexpr int SMEM = WARPS * CPW * CLASS_FLOATS * 4;
     static_assert(N % 4 == 0 && LD % 4 == 0, "16-byte shared-memory vectors");
 };
 
@@ -75,78 +85,124 @@ __device__ __forceinline__ void class_members(const PropArgs &a, long long u, in
     }
 }
 
-// out[:, c] = acc0[:, c] + A B[:, c] for this lane's columns, all in shared
-// memory (column-major, stride LD); acc0 = two * X[:, c] + Y[:, c] (Y may be
-// null). out differs from every input.
+// out = two * X + Y + A B for one class, N x N in shared memory: A, X, Y and
+// out column-major, B row-major (stride LD), Y may be null, out_row (if not
+// null) receives the result row-major too; outputs differ from every input.
+// Register-blocked: lane t owns the TR x TC tile at rows (t % RB) TR, columns
+// (t / RB) TC, and per k loads the tile's slice of column k of A and of row k
+// of B with 16-byte loads (one or a few distinct addresses a warp).
 template <int N>
-__device__ __forceinline__ void prop_gemm(const float *A, const float *B, const float *X, float two, const float *Y,
-                                          float *out, int t) {
+struct GemmTile {
+    static constexpr int TR = N == 16 ? 4 : (N == 32 ? 8 : 16);
+    static constexpr int TC = N == 16 ? 4 : (N == 32 ? 4 : 8);
+    static constexpr int RB = N / TR;
+    static_assert((N / TR) * (N / TC) == PropCfg<N>::LPC, "one tile a lane");
+    static_assert(TR % 4 == 0 && TC % 4 == 0, "16-byte vectors");
+};
+
+template <int N>
+__device__ __forceinline__ void prop_gemm(const float *A, const float *Brow, const float *X, float two, const float *Y,
+                                          float *out, float *out_row, int t) {
     using C = PropCfg<N>;
-#pragma unroll 1
-    for (int cc = 0; cc < C::CPL; ++cc) {
-        const int c = t + cc * C::LPC;
-        f32x2 acc[N / 2];
+    using Tl = GemmTile<N>;
+    const int r0 = (t % Tl::RB) * Tl::TR, c0 = (t / Tl::RB) * Tl::TC;
+    f32x2 acc[Tl::TC][Tl::TR / 2];
 #pragma unroll
-        for (int i = 0; i < N; i += 4) {
-            const float4 xv = *reinterpret_cast<const float4 *>(X + c * C::LD + i);
+    for (int c = 0; c < Tl::TC; ++c)
+#pragma unroll
+        for (int i = 0; i < Tl::TR; i += 4) {
+            const float4 xv = *reinterpret_cast<const float4 *>(X + (c0 + c) * C::LD + r0 + i);
             float4 yv = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (Y) yv = *reinterpret_cast<const float4 *>(Y + c * C::LD + i);
-            acc[i / 2] = pk2(fmaf(two, xv.x, yv.x), fmaf(two, xv.y, yv.y));
-            acc[i / 2 + 1] = pk2(fmaf(two, xv.z, yv.z), fmaf(two, xv.w, yv.w));
+            if (Y) yv = *reinterpret_cast<const float4 *>(Y + (c0 + c) * C::LD + r0 + i);
+            acc[c][i / 2] = pk2(fmaf(two, xv.x, yv.x), fmaf(two, xv.y, yv.y));
+            acc[c][i / 2 + 1] = pk2(fmaf(two, xv.z, yv.z), fmaf(two, xv.w, yv.w));
         }
-        // B[kk, c] four at a time (this lane's own column, no bank conflict with
-        // the padded stride); A[:, kk] is the same address in every lane
-#pragma unroll 1
-        for (int k4 = 0; k4 < N; k4 += 4) {
-            const float4 bv = *reinterpret_cast<const float4 *>(B + c * C::LD + k4);
-            const float bk[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll 2
+    for (int kk = 0; kk < N; ++kk) {
+        f32x2 av[Tl::TR / 2];
 #pragma unroll
-            for (int kq = 0; kq < 4; ++kq) {
-                const f32x2 s = dup2(bk[kq]);
-                const float *col = A + (k4 + kq) * C::LD;
+        for (int i = 0; i < Tl::TR; i += 4) {
+            const float4 v = *reinterpret_cast<const float4 *>(A + kk * C::LD + r0 + i);
+            av[i / 2] = pk2(v.x, v.y);
+            av[i / 2 + 1] = pk2(v.z, v.w);
+        }
+        float bv[Tl::TC];
 #pragma unroll
-                for (int i = 0; i < N; i += 4) {
-                    const float4 av = *reinterpret_cast<const float4 *>(col + i);
-                    acc[i / 2] = fma2(pk2(av.x, av.y), s, acc[i / 2]);
-                    acc[i / 2 + 1] = fma2(pk2(av.z, av.w), s, acc[i / 2 + 1]);
-                }
+        for (int c = 0; c < Tl::TC; c += 4) {
+            const float4 v = *reinterpret_cast<const float4 *>(Brow + kk * C::LD + c0 + c);
+            bv[c] = v.x;
+            bv[c + 1] = v.y;
+            bv[c + 2] = v.z;
+            bv[c + 3] = v.w;
+        }
+#pragma unroll
+        for (int c = 0; c < Tl::TC; ++c) {
+            const f32x2 s = dup2(bv[c]);
+#pragma unroll
+            for (int i = 0; i < Tl::TR / 2; ++i) acc[c][i] = fma2(av[i], s, acc[c][i]);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < Tl::TC; ++c)
+#pragma unroll
+        for (int i = 0; i < Tl::TR; i += 4)
+            *reinterpret_cast<float4 *>(out + (c0 + c) * C::LD + r0 + i) =
+                make_float4(lo2(acc[c][i / 2]), hi2(acc[c][i / 2]), lo2(acc[c][i / 2 + 1]), hi2(acc[c][i / 2 + 1]));
+    if (out_row) {
+#pragma unroll
+        for (int i = 0; i < Tl::TR; i += 2)
+#pragma unroll
+            for (int c = 0; c < Tl::TC; c += 4) {
+                *reinterpret_cast<float4 *>(out_row + (r0 + i) * C::LD + c0 + c) =
+                    make_float4(lo2(acc[c][i / 2]), lo2(acc[c + 1][i / 2]), lo2(acc[c + 2][i / 2]),
+                                lo2(acc[c + 3][i / 2]));
+                *reinterpret_cast<float4 *>(out_row + (r0 + i + 1) * C::LD + c0 + c) =
+                    make_float4(hi2(acc[c][i / 2]), hi2(acc[c + 1][i / 2]), hi2(acc[c + 2][i / 2]),
+                                hi2(acc[c + 3][i / 2]));
             }
-        }
-#pragma unroll
-        for (int i = 0; i < N; i += 4)
-            *reinterpret_cast<float4 *>(out + c * C::LD + i) =
-                make_float4(lo2(acc[i / 2]), hi2(acc[i / 2]), lo2(acc[i / 2 + 1]), hi2(acc[i / 2 + 1]));
     }
 }
 
-// x = A'^{-1} r in place (r: N values), with the torn factor's reciprocal
-// pivots G and the Sherman-Morrison vector q = T^{-1} u in shared memory.
+// x = A'^{-1} r and y = A'^{-1} s in place (N values each), with the torn
+// factor's reciprocal pivots G and the Sherman-Morrison vector q = T^{-1} u:
+// the two right-hand sides run through the same sweeps as independent chains.
 template <int N>
-__device__ __forceinline__ void prop_solve(float (&x)[N], const float *G, const float *q, float inv_d0,
-                                           float inv_den) {
+__device__ __forceinline__ void prop_solve2(float (&x)[N], float (&y)[N], const float *G, const float *q,
+                                            float inv_d0, float inv_den) {
 #pragma unroll
-    for (int j = 1; j < N; ++j) x[j] = fmaf(G[j - 1], x[j - 1], x[j]);
+    for (int j = 1; j < N; ++j) {
+        x[j] = fmaf(G[j - 1], x[j - 1], x[j]);
+        y[j] = fmaf(G[j - 1], y[j - 1], y[j]);
+    }
     x[N - 1] *= G[N - 1];
+    y[N - 1] *= G[N - 1];
 #pragma unroll
-    for (int j = N - 2; j >= 0; --j) x[j] = (x[j] + x[j + 1]) * G[j];
-    const float w = fmaf(x[N - 1], inv_d0, x[0]) * inv_den;
+    for (int j = N - 2; j >= 0; --j) {
+        x[j] = (x[j] + x[j + 1]) * G[j];
+        y[j] = (y[j] + y[j + 1]) * G[j];
+    }
+    const float wx = fmaf(x[N - 1], inv_d0, x[0]) * inv_den;
+    const float wy = fmaf(y[N - 1], inv_d0, y[0]) * inv_den;
 #pragma unroll
-    for (int j = 0; j < N; ++j) x[j] = fmaf(-w, q[j], x[j]);
+    for (int j = 0; j < N; ++j) {
+        x[j] = fmaf(-wx, q[j], x[j]);
+        y[j] = fmaf(-wy, q[j], y[j]);
+    }
 }
 
 template <int N>
-__global__ void __launch_bounds__(kPropWarps * 32) k_prop_build(const __grid_constant__ PropArgs a) {
+__global__ void __launch_bounds__(PropCfg<N>::WARPS * 32) k_prop_build(const __grid_constant__ PropArgs a) {
     using C = PropCfg<N>;
     extern __shared__ __align__(16) float psm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane / C::LPC, t = lane - g * C::LPC;
     float *base = psm + (warp * C::CPW + g) * C::CLASS_FLOATS;
-    float *G = base + 3 * C::MAT;
+    float *G = base + 5 * C::MAT;
     float *q = G + N;
     float *scal = q + N;  // 1/d0, 1/(1 + v.q)
-    const long long stride = (long long)gridDim.x * kPropWarps * C::CPW;
+    const long long stride = (long long)gridDim.x * C::WARPS * C::CPW;
     // classes are taken warp-uniformly so that every lane reaches each __syncwarp
-    for (long long u0 = ((long long)blockIdx.x * kPropWarps + warp) * C::CPW; u0 < a.classes; u0 += stride) {
+    for (long long u0 = ((long long)blockIdx.x * C::WARPS + warp) * C::CPW; u0 < a.classes; u0 += stride) {
         const long long u = u0 + g;
         const bool live = u < a.classes;
         int k, kb, l, lb;
@@ -188,44 +244,64 @@ __global__ void __launch_bounds__(kPropWarps * 32) k_prop_build(const __grid_con
         }
         __syncwarp();
         const float inv_d0 = scal[0], inv_den = scal[1];
-        // D_1, column by column: 2 A'^{-1} Lap e_c - 2 (a_c^2/beta) A'^{-1} e_c
+        // D_1, column by column: 2 A'^{-1} Lap e_c - 2 (a_c^2/beta) A'^{-1} e_c;
+        // pivots and q are read into registers once (broadcast loads)
+        // (N = 64 reads them from shared memory: four 64-entry arrays exceed the registers)
         float *D1 = base;
+        constexpr int NR = N <= 32 ? N : 1;
+        float Gr[NR], qr[NR];
+        if constexpr (N <= 32) {
+#pragma unroll
+            for (int j = 0; j < N; j += 4) {
+                const float4 gv = *reinterpret_cast<const float4 *>(G + j);
+                const float4 qv = *reinterpret_cast<const float4 *>(q + j);
+                Gr[j] = gv.x; Gr[j + 1] = gv.y; Gr[j + 2] = gv.z; Gr[j + 3] = gv.w;
+                qr[j] = qv.x; qr[j + 1] = qv.y; qr[j + 2] = qv.z; qr[j + 3] = qv.w;
+            }
+        }
+        const float *Gs = N <= 32 ? Gr : G;
+        const float *qs = N <= 32 ? qr : q;
 #pragma unroll 1
         for (int cc = 0; cc < C::CPL; ++cc) {
             const int c = t + cc * C::LPC;
             const float ar = fmaf(wx, a.cs[c], wy * a.sn[c]);
             const float e2 = ar * ar * a.inv_beta;
-            float x[N];
+            const int cm = (c == 0) ? N - 1 : c - 1, cp = (c == N - 1) ? 0 : c + 1;
+            float x[N], y[N];
 #pragma unroll
-            for (int j = 0; j < N; ++j) x[j] = (j == c) ? 1.0f : 0.0f;
-            prop_solve<N>(x, G, q, inv_d0, inv_den);
-            float *dc = D1 + c * C::LD;  // this lane's column: first -2 (a_c^2/beta) A'^{-1} e_c
+            for (int j = 0; j < N; ++j) {
+                x[j] = (j == c) ? 1.0f : 0.0f;
+                y[j] = (j == c) ? -2.0f : ((j == cm || j == cp) ? 1.0f : 0.0f);
+            }
+            prop_solve2<N>(x, y, Gs, qs, inv_d0, inv_den);
+            float *dc = D1 + c * C::LD;
 #pragma unroll
             for (int j = 0; j < N; j += 4)
-                *reinterpret_cast<float4 *>(dc + j) = make_float4(-2.0f * e2 * x[j], -2.0f * e2 * x[j + 1],
-                                                                  -2.0f * e2 * x[j + 2], -2.0f * e2 * x[j + 3]);
-            const int cm = (c == 0) ? N - 1 : c - 1, cp = (c == N - 1) ? 0 : c + 1;
-#pragma unroll
-            for (int j = 0; j < N; ++j) x[j] = (j == c) ? -2.0f : ((j == cm || j == cp) ? 1.0f : 0.0f);
-            prop_solve<N>(x, G, q, inv_d0, inv_den);
-#pragma unroll
-            for (int j = 0; j < N; j += 4) {
-                const float4 v = *reinterpret_cast<const float4 *>(dc + j);
-                *reinterpret_cast<float4 *>(dc + j) = make_float4(fmaf(2.0f, x[j], v.x), fmaf(2.0f, x[j + 1], v.y),
-                                                                  fmaf(2.0f, x[j + 2], v.z), fmaf(2.0f, x[j + 3], v.w));
-            }
+                *reinterpret_cast<float4 *>(dc + j) =
+                    make_float4(fmaf(2.0f, y[j], -2.0f * e2 * x[j]), fmaf(2.0f, y[j + 1], -2.0f * e2 * x[j + 1]),
+                                fmaf(2.0f, y[j + 2], -2.0f * e2 * x[j + 2]), fmaf(2.0f, y[j + 3], -2.0f * e2 * x[j + 3]));
         }
         __syncwarp();
-        // binary powering: P runs through D_1, D_2, D_4, ...; R collects the set
-        // bits of S; Tm is the free third buffer every product is written to
-        float *P = base, *R = nullptr, *Tm = base + C::MAT, *spare = base + 2 * C::MAT;
+        // and row-major (this lane's column c becomes entries c of every row)
+        float *D1r = base + C::MAT;
+#pragma unroll 1
+        for (int cc = 0; cc < C::CPL; ++cc) {
+            const int c = t + cc * C::LPC;
+#pragma unroll
+            for (int j = 0; j < N; ++j) D1r[j * C::LD + c] = D1[c * C::LD + j];
+        }
+        __syncwarp();
+        // binary powering: P (column- and row-major) runs through D_1, D_2,
+        // D_4, ...; R collects the set bits of S; products go to Tc (and Tr)
+        float *P = base, *Pr = base + C::MAT, *R = base + 2 * C::MAT, *Tc = base + 3 * C::MAT,
+              *Tr = base + 4 * C::MAT;
+        bool have_r = false;
         int s = a.steps;
 #pragma unroll 1
         while (true) {
             if (s & 1) {
-                if (!R) {
-                    // R = P: copy this lane's columns into the spare buffer
-                    R = spare;
+                if (!have_r) {
+                    // R = P: copy this lane's columns
 #pragma unroll 1
                     for (int cc = 0; cc < C::CPL; ++cc) {
                         const int c = t + cc * C::LPC;
@@ -234,48 +310,78 @@ __global__ void __launch_bounds__(kPropWarps * 32) k_prop_build(const __grid_con
                             *reinterpret_cast<float4 *>(R + c * C::LD + j) =
                                 *reinterpret_cast<const float4 *>(P + c * C::LD + j);
                     }
+                    have_r = true;
                 } else {
-                    prop_gemm<N>(R, P, R, 1.0f, P, Tm, t);  // R + P + R P
+                    prop_gemm<N>(R, Pr, R, 1.0f, P, Tc, nullptr, t);  // R + P + R P
                     float *tmp = R;
-                    R = Tm;
-                    Tm = tmp;
+                    R = Tc;
+                    Tc = tmp;
                 }
                 __syncwarp();
             }
             s >>= 1;
             if (!s) break;
-            prop_gemm<N>(P, P, P, 2.0f, nullptr, Tm, t);  // 2 P + P P
+            prop_gemm<N>(P, Pr, P, 2.0f, nullptr, Tc, Tr, t);  // 2 P + P P
             float *tmp = P;
-            P = Tm;
-            Tm = tmp;
+            P = Tc;
+            Tc = tmp;
+            tmp = Pr;
+            Pr = Tr;
+            Tr = tmp;
             __syncwarp();
         }
-        // D_S, row-major: this lane writes rows t, t + LPC, ...
+        // D_S by cyclic diagonals: this lane writes S_m[i] for i = t, t + LPC, ...
+        // (R is column-major: D[i, j] = R[j LD + i]; both reads run at stride
+        // LD + 1 across the lanes, free of bank conflicts)
         if (live) {
-            float *out = a.D + u * (long long)N * N;
+            float *out = a.D + u * (long long)C::SBLK;
 #pragma unroll 1
             for (int cc = 0; cc < C::CPL; ++cc) {
-                const int r = t + cc * C::LPC;
-#pragma unroll
-                for (int j = 0; j < N; j += 4)
-                    *reinterpret_cast<float4 *>(out + (long long)r * N + j) =
-                        make_float4(R[j * C::LD + r], R[(j + 1) * C::LD + r], R[(j + 2) * C::LD + r],
-                                    R[(j + 3) * C::LD + r]);
+                const int i = t + cc * C::LPC;
+#pragma unroll 4
+                for (int m = 0; m <= N / 2; ++m) {
+                    const int j = (i + m) & (N - 1);
+                    out[m * N + i] = 0.5f * (R[j * C::LD + i] + R[i * C::LD + j]);
+                }
             }
         }
         __syncwarp();
     }
 }
 
-// x <- x + D_S x for the (up to four) frequencies of every class.
+// x <- x + D_S x for the (up to four) frequencies of every class. The warp
+// first fetches the class's whole diagonal block with 16-byte loads into
+// shared memory, together with the frequencies' N-vectors, so a class costs
+// one round trip to memory; lane r then forms row r from the block.
+template <int N>
+struct ApplyCfg {
+    static constexpr int LPC = N < 32 ? N : 32;  // lanes a class: one row (N = 64: two) a lane
+    static constexpr int CPW = 32 / LPC;
+    static constexpr int CPL = N / LPC;
+    static constexpr int SBLK = PropCfg<N>::SBLK;
+    static constexpr int S_FLOATS = CPW * SBLK;               // diagonal blocks a warp
+    static constexpr int X_FLOATS = CPW * 4 * N * 2;          // the classes' vectors a warp
+    static constexpr int WARP_FLOATS = S_FLOATS + X_FLOATS;
+    static constexpr int SMEM = kApplyWarps * WARP_FLOATS * 4;
+    static_assert(SBLK % 4 == 0, "16-byte blocks");
+};
+
 template <int N>
 __global__ void __launch_bounds__(kApplyWarps * 32) k_prop_apply(const __grid_constant__ PropArgs a) {
-    using C = PropCfg<N>;
-    __shared__ __align__(16) float2 xs[kApplyWarps][C::CPW][4][N];
+    using C = ApplyCfg<N>;
+    using AC = ApplyCfg<N>;
+    extern __shared__ __align__(16) float asm_[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane / C::LPC, t = lane - g * C::LPC;
+    float *sblk = asm_ + warp * AC::WARP_FLOATS;                 // [CPW][SBLK]
+    float2 *xs = reinterpret_cast<float2 *>(sblk + AC::S_FLOATS);  // [CPW][4][N]
     const long long stride = (long long)gridDim.x * kApplyWarps * C::CPW;
     for (long long u0 = ((long long)blockIdx.x * kApplyWarps + warp) * C::CPW; u0 < a.classes; u0 += stride) {
+        // the warp's CPW consecutive classes are contiguous in D: one block copy
+        const long long nlive = (a.classes - u0 < C::CPW) ? a.classes - u0 : C::CPW;
+        const float4 *src = reinterpret_cast<const float4 *>(a.D + u0 * (long long)C::SBLK);
+        const int n4 = (int)(nlive * C::SBLK / 4);
+        for (int i = lane; i < n4; i += 32) reinterpret_cast<float4 *>(sblk)[i] = __ldg(src + i);
         const long long u = u0 + g;
         const bool live = u < a.classes;
         int k, kb, l, lb;
@@ -283,6 +389,7 @@ __global__ void __launch_bounds__(kApplyWarps * 32) k_prop_apply(const __grid_co
         const long long f[4] = {(long long)k * a.Wc + l, (long long)k * a.Wc + lb, (long long)kb * a.Wc + l,
                                 (long long)kb * a.Wc + lb};
         const bool on[4] = {live, live && lb != l, live && kb != k, live && kb != k && lb != l};
+        float2 *xg = xs + g * 4 * N;
         float2 mine[4][C::CPL];
 #pragma unroll
         for (int m = 0; m < 4; ++m)
@@ -290,28 +397,33 @@ __global__ void __launch_bounds__(kApplyWarps * 32) k_prop_apply(const __grid_co
             for (int cc = 0; cc < C::CPL; ++cc) {
                 const int j = t + cc * C::LPC;
                 mine[m][cc] = on[m] ? a.vol[(long long)j * a.HW + f[m]] : make_float2(0.f, 0.f);
-                xs[warp][g][m][j] = mine[m][cc];
+                xg[m * N + j] = mine[m][cc];
             }
         __syncwarp();
-        const float *Dc = a.D + (live ? u : 0) * (long long)N * N;
+        const float *Sc = sblk + g * C::SBLK;
 #pragma unroll
         for (int cc = 0; cc < C::CPL; ++cc) {
             const int r = t + cc * C::LPC;
-            const float *row = Dc + (long long)r * N;
             f32x2 acc[4];
 #pragma unroll
             for (int m = 0; m < 4; ++m) acc[m] = pk2(0.f, 0.f);
+            // y_r = sum_{d=0}^{N/2} S_d[r] x_{r+d} + sum_{d=1}^{N/2-1} S_d[r-d] x_{r-d}
 #pragma unroll 4
-            for (int j = 0; j < N; j += 4) {
-                const float4 dv = *reinterpret_cast<const float4 *>(row + j);
-                const float dd[4] = {dv.x, dv.y, dv.z, dv.w};
+            for (int d = 0; d <= N / 2; ++d) {
+                const int jp = (r + d) & (N - 1);
+                const f32x2 s = dup2(Sc[d * N + r]);
 #pragma unroll
-                for (int jj = 0; jj < 4; ++jj) {
-                    const f32x2 s = dup2(dd[jj]);
+                for (int m = 0; m < 4; ++m) {
+                    const float2 xv = xg[m * N + jp];
+                    acc[m] = fma2(s, pk2(xv.x, xv.y), acc[m]);
+                }
+                if (d >= 1 && d < N / 2) {
+                    const int jm = (r - d) & (N - 1);
+                    const f32x2 s2 = dup2(Sc[d * N + jm]);
 #pragma unroll
                     for (int m = 0; m < 4; ++m) {
-                        const float2 xv = xs[warp][g][m][j + jj];
-                        acc[m] = fma2(s, pk2(xv.x, xv.y), acc[m]);
+                        const float2 xv = xg[m * N + jm];
+                        acc[m] = fma2(s2, pk2(xv.x, xv.y), acc[m]);
                     }
                 }
             }
@@ -331,24 +443,27 @@ cudaError_t launch_build(const PropArgs &a, int num_sms, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(k_prop_build<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_prop_build<N>, kPropWarps * 32, C::SMEM);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_prop_build<N>, C::WARPS * 32, C::SMEM);
     if (e != cudaSuccess) return e;
-    const long long per_block = (long long)kPropWarps * C::CPW;
+    const long long per_block = (long long)C::WARPS * C::CPW;
     long long blocks = (a.classes + per_block - 1) / per_block;
     const long long cap = (long long)num_sms * (per_sm > 0 ? per_sm : 1);
     if (blocks > cap) blocks = cap;
-    k_prop_build<N><<<(unsigned)blocks, kPropWarps * 32, C::SMEM, s>>>(a);
+    k_prop_build<N><<<(unsigned)blocks, C::WARPS * 32, C::SMEM, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int N>
 cudaError_t launch_apply(const PropArgs &a, int num_sms, cudaStream_t s) {
-    using C = PropCfg<N>;
+    using C = ApplyCfg<N>;
+    using AC = ApplyCfg<N>;
+    cudaError_t e = cudaFuncSetAttribute(k_prop_apply<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, AC::SMEM);
+    if (e != cudaSuccess) return e;
     const long long per_block = (long long)kApplyWarps * C::CPW;
     long long blocks = (a.classes + per_block - 1) / per_block;
     const long long cap = (long long)num_sms * 64;
     if (blocks > cap) blocks = cap;
-    k_prop_apply<N><<<(unsigned)blocks, kApplyWarps * 32, 0, s>>>(a);
+    k_prop_apply<N><<<(unsigned)blocks, kApplyWarps * 32, AC::SMEM, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -357,6 +472,8 @@ cudaError_t launch_apply(const PropArgs &a, int num_sms, cudaStream_t s) {
 }  // namespace se2n
 
 bool se2n_prop_supported(int N) { return N == 16 || N == 32 || N == 64; }
+
+long long se2n_prop_floats(int N) { return (long long)(N / 2 + 1) * N; }
 
 int se2n_prop_col_slots(int W, bool half) { return half ? W / 4 + 1 : se2n::pair_rows(W); }
 

@@ -89,7 +89,7 @@ struct DiffuseArgs {
 // Parameters of the propagator kernels (propagator.cu): build D_S for every
 // class of frequencies with equal coefficients, or apply it to the volume.
 struct PropArgs {
-    float *D;          // [classes][N][N] row-major, D_S = (B-^{-1} B+)^S - I
+    float *D;          // [classes][N/2 + 1][N]: cyclic diagonals of D_S = (B-^{-1} B+)^S - I
     float2 *vol;       // [N][H][Wc] complex (apply only)
     int H, W, Wc;
     long long HW;      // H * Wc
@@ -103,6 +103,7 @@ struct PropArgs {
     float sn[SE2N_MAX_N];
 };
 bool se2n_prop_supported(int N);
+long long se2n_prop_floats(int N);  // stored floats a class
 int se2n_prop_col_slots(int W, bool half);
 long long se2n_prop_classes(int H, int W, bool half);
 cudaError_t se2n_launch_prop_build(int N, const PropArgs &a, int num_sms, cudaStream_t s);

@@ -103,6 +103,7 @@ _SIGS = {
     "se2n_diffuse": (ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int]),
     "se2n_mix": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_double, ctypes.c_double]),
     "se2n_dr_grow": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "se2n_plan_drop_propagators": (ctypes.c_int, [_P, ctypes.c_int]),
     "se2n_project": (ctypes.c_int, [_P, _P, ctypes.c_int, _P]),
     "se2n_inpaint": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(se2n_params), _P, _P]),
     "se2n_inpaint_host": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(se2n_params), _P]),
@@ -265,6 +266,10 @@ def se2n_diffuse(plan, vol_hat, beta, T, steps, flags=0):
 
 def se2n_mix(plan, vol, f, mask, bins, eps, guard=0.1):
     _check(lib.se2n_mix(plan.handle, _ptr(vol), _ptr(f), _ptr(mask), _ptr(bins), eps, guard), "se2n_mix")
+
+
+def se2n_plan_drop_propagators(plan, free_memory=False):
+    _check(lib.se2n_plan_drop_propagators(plan.handle, 1 if free_memory else 0), "se2n_plan_drop_propagators")
 
 
 def se2n_dr_grow(plan, vol, mask_in, mask_out, fref, bins):

@@ -84,11 +84,17 @@ def test_matrices_are_rebuilt_only_when_the_step_changes():
         v = t_c64(vol)
         se2n.se2n_diffuse(plan, v, beta, T, S, PROP)
         outs.append((host(v), oracle.diffuse(vol.astype(np.complex128), beta, T, S)))
+    for free in (False, True):   # dropped matrices are built again, with or without their memory
+        se2n.se2n_plan_drop_propagators(plan, free)
+        v = t_c64(vol)
+        se2n.se2n_diffuse(plan, v, 0.5, 2.0, 60, PROP)
+        outs.append((host(v), outs[-1][1]))
     prof = se2n.se2n_plan_profile_read(plan)
     plan.close()
-    assert prof["propagator"][1] == 3 and prof["diffuse"][1] == 5
+    assert prof["propagator"][1] == 5 and prof["diffuse"][1] == 7
     for got, ref in outs:
         assert rel_l2(got, ref) <= REL_L2
+    np.testing.assert_array_equal(outs[-1][0], outs[-3][0])
 
 
 def _params(p, full=0):
