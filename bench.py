@@ -3,17 +3,22 @@
 One step = one whole inpaint of the 512x512, N=32 workload (seeded
 piecewise-smooth image, 80 % random mask plus 4-px bars every 32 px,
 beta = 0.25, 10 restoration intervals of 500 Crank-Nicolson steps, T = 2 per
-interval): orientation, lift, forward DFT, 10 x fused diffusion, 9 x
-(inverse DFT, static restoration, forward DFT), inverse DFT, projection,
-all through se2n_inpaint with the inputs resident in HBM.
+interval): orientation, lift, forward DFT, 10 x diffusion, 9 x (inverse
+DFT, static restoration, forward DFT), inverse DFT, projection, all through
+se2n_inpaint with the inputs resident in HBM. By default each interval's
+500 steps are applied as one precomputed S-step propagator per class of
+equal-coefficient frequencies, built inside every timed inpaint
+(--diffusion propagator); --diffusion steps runs the fused step-by-step
+kernel instead, and the default line reports that path too.
 
 Metric: Mathieu updates per second, updates = frequencies x N x steps per
 interval x intervals = 512^2 * 32 * 500 * 10 per inpaint (the method's
 work on all M^2 frequencies), over the whole inpaint time (value), plus ms
-per inpaint, the FP32 error against the FP64 oracle, the diffusion kernel's
-roofline (FP32 ALU bound; its flops are those of the frequencies the launch
-integrates, the Hermitian half 512 x 257 of the spectrum), the end-to-end
-number from host buffers (se2n_inpaint_host) and the oracle's CPU rate.
+per inpaint, the FP32 error against the FP64 oracle, the roofline of the
+dominant kernel (the propagator build, FP32 ALU bound; or the step kernel,
+whose flops are those of the frequencies it integrates, the Hermitian half
+512 x 257 of the spectrum), the end-to-end number from host buffers
+(se2n_inpaint_host) and the oracle's CPU rate.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Multi-GPU (torchrun): every rank inpaints its own image (replicas, weak
@@ -122,27 +127,48 @@ class ClockSampler:
 # our arm
 # ----------------------------------------------------------------------------
 
-def kernel_source_hash():
-    """Hash of the diffusion kernel's source: a stored DRAM-traffic figure is
-    only valid for the exact kernel it was captured on."""
+KERNEL_SOURCES = {"diffuse": ("diffuse_impl.cuh", "diffuse_x2.cuh", "diffuse.cu"),
+                  "prop_build": ("propagator.cu", "diffuse_x2.cuh", "diffuse_impl.cuh")}
+TRAFFIC_FILES = {"diffuse": "diffuse_traffic.json", "prop_build": "prop_build_traffic.json"}
+
+
+def kernel_source_hash(kind="diffuse"):
+    """Hash of a kernel's source files: a stored DRAM-traffic figure is only
+    valid for the exact kernel it was captured on."""
     import hashlib
     h = hashlib.sha256()
-    for name in ("diffuse_impl.cuh", "diffuse_x2.cuh", "diffuse.cu"):
+    for name in KERNEL_SOURCES[kind]:
         with open(os.path.join(ROOT, "paper_1304_2062_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def stored_traffic():
-    """DRAM bytes per diffusion launch from the committed ncu summary, or
+def stored_traffic(kind="diffuse"):
+    """DRAM bytes per launch of the kernel from the committed ncu summary, or
     None if it was taken on a different kernel source."""
     try:
-        rec = json.load(open(os.path.join(ROOT, "profiles", "diffuse_traffic.json")))
+        rec = json.load(open(os.path.join(ROOT, "profiles", TRAFFIC_FILES[kind])))
     except (OSError, ValueError):
         return None
-    if rec.get("kernel_source_hash") != kernel_source_hash():
+    if rec.get("kernel_source_hash") != kernel_source_hash(kind):
         return None
     return rec.get("dram_bytes_per_launch")
+
+
+def propagator_gemm_flops(classes, N, S):
+    """FP32 flops of building the S-step propagators: binary powering takes
+    floor(log2 S) squarings and popcount(S) - 1 combinations, each one N x N x N
+    product (2 N^3 flops); the O(N^2) solves of the first step are not counted."""
+    products = S.bit_length() - 1 + bin(S).count("1") - 1
+    return classes * products * 2 * N ** 3
+
+
+def propagator_classes(H, W, half=True):
+    """Classes of equal-coefficient frequencies: rows k and (H/2 - k) mod H,
+    columns l and (W/2 - l) (Hermitian half: l <= W/2)."""
+    pair_rows = H // 4 + 1 + (3 * H) // 4 - H // 2
+    cols = W // 4 + 1 if half else W // 4 + 1 + (3 * W) // 4 - W // 2
+    return pair_rows * cols
 
 
 def max_over_ranks(value, dist=None, device="cpu"):
@@ -185,8 +211,10 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.Stream(dev)
     plan = se2n.se2n_plan_create(w.H, w.W, w.N, 0, stream)
     dynamic = args.workload == "dr"
+    prop = args.diffusion == "propagator"
+    flags = se2n.SE2N_DIFFUSE_PROPAGATOR if prop else 0
     prm = se2n.se2n_params_default(N=w.N, beta=w.beta, T=w.T, steps=w.steps, rounds=w.rounds, eps=w.eps,
-                                   sigma_smooth=w.sigma, dynamic=int(dynamic))
+                                   sigma_smooth=w.sigma, dynamic=int(dynamic), diffuse_flags=flags)
     f_d = torch.tensor(f32, device=dev)
     m_d = torch.tensor(w.mask, device=dev)
     vol = torch.empty((w.N, w.H, w.W), dtype=torch.complex64, device=dev)
@@ -194,6 +222,10 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def step():
+        # every step builds its propagators again: the timed inpaint is one
+        # whole problem, nothing carried over from the previous step
+        if prop:
+            se2n.se2n_plan_drop_propagators(plan)
         se2n.se2n_inpaint(plan, f_d, m_d, None, prm, vol, out)
 
     with torch.cuda.stream(stream):
@@ -222,31 +254,94 @@ def run_ours(args, rank, world, local_rank):
     ms_per_step = total_ms / args.steps
     value = world * w.updates() * args.steps / (total_ms / 1e3)
 
-    # diffusion kernel roofline (FP32 ALU bound), from the live event timings
-    d_ms, d_calls = prof["diffuse"]
-    d_avg_s = d_ms / d_calls / 1e3
-    # the launch integrates the Hermitian half of the spectrum: H x (W/2 + 1) frequencies
-    updates_per_launch = w.H * (w.W // 2 + 1) * w.N * w.steps
-    achieved = FLOPS_PER_UPDATE * updates_per_launch / d_avg_s / 1e12
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
-    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
-                "frac": round(achieved / peak, 4),
-                "traffic": args.traffic if args.traffic is not None else stored_traffic(),
-                "kernel": "k_diffuse_x2<32,2,false> (packed FP32 pairs, truncated corner correction)",
-                "flops_per_update": FLOPS_PER_UPDATE, "updates_per_launch": updates_per_launch,
-                "avg_launch_ms": round(d_avg_s * 1e3, 4),
-                "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop/FMA x 2070 MHz (derived, not measured)",
-                "diffuse_updates_per_s": updates_per_launch / d_avg_s,
-                "hbm_gbs_of_diffuse": round(16 * w.H * (w.W // 2 + 1) * w.N / d_avg_s / 1e9, 1),
-                "frequencies_integrated": "Hermitian half, H x (W/2 + 1) (value counts all M^2 frequencies)"}
+    peak_basis = "152 SMs x 128 FP32 lanes x 2 flop/FMA x 2070 MHz (derived, not measured)"
+    # the path integrates the Hermitian half of the spectrum: H x (W/2 + 1) frequencies
+    updates_per_launch = w.H * (w.W // 2 + 1) * w.N * w.steps
+    if prop:
+        # the dominant kernel of ours is the propagator build (FP32 products)
+        b_ms, b_calls = prof["propagator"]
+        b_s = b_ms / b_calls / 1e3
+        classes = propagator_classes(w.H, w.W)
+        flops = propagator_gemm_flops(classes, w.N, w.steps)
+        achieved = flops / b_s / 1e12
+        a_ms, a_calls = prof["diffuse"]
+        a_s = a_ms / a_calls / 1e3
+        apply_bytes = classes * (w.N // 2 + 1) * w.N * 4 + 16 * w.H * (w.W // 2 + 1) * w.N
+        hbm = _peaks().get("hbm_gbs")
+        roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
+                    "frac": round(achieved / peak, 4),
+                    "traffic": args.traffic if args.traffic is not None else stored_traffic("prop_build"),
+                    "kernel": "k_prop_build<32> (S-step propagators of 33,153 frequency classes, FP32 products)",
+                    "flops_per_launch": flops, "flops_basis": "classes x (squarings + combinations) x 2 N^3, "
+                    f"S = {w.steps}: {w.steps.bit_length() - 1} squarings, {bin(w.steps).count('1') - 1} combinations",
+                    "avg_launch_ms": round(b_s * 1e3, 4), "peak_basis": peak_basis,
+                    "apply_kernel": {"kernel": "k_prop_apply<32>", "bound": "hbm", "avg_launch_ms": round(a_s * 1e3, 4),
+                                     "bytes_per_launch": apply_bytes,
+                                     "bytes_basis": "the classes' stored diagonals (4 N (N/2+1) bytes a class) + "
+                                                    "one read and one write of the half spectrum",
+                                     "achieved_gbs": round(apply_bytes / a_s / 1e9, 1), "peak_gbs": hbm,
+                                     "frac": round(apply_bytes / a_s / 1e9 / hbm, 4) if hbm else None,
+                                     "peak_basis": "MEASURED_PEAKS.json hbm_gbs"},
+                    "frequencies_integrated": "Hermitian half, H x (W/2 + 1) (value counts all M^2 frequencies)"}
+    else:
+        d_ms, d_calls = prof["diffuse"]
+        d_avg_s = d_ms / d_calls / 1e3
+        achieved = FLOPS_PER_UPDATE * updates_per_launch / d_avg_s / 1e12
+        roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
+                    "frac": round(achieved / peak, 4),
+                    "traffic": args.traffic if args.traffic is not None else stored_traffic(),
+                    "kernel": "k_diffuse_x2<32,2,false> (packed FP32 pairs, truncated corner correction)",
+                    "flops_per_update": FLOPS_PER_UPDATE, "updates_per_launch": updates_per_launch,
+                    "avg_launch_ms": round(d_avg_s * 1e3, 4), "peak_basis": peak_basis,
+                    "diffuse_updates_per_s": updates_per_launch / d_avg_s,
+                    "hbm_gbs_of_diffuse": round(16 * w.H * (w.W // 2 + 1) * w.N / d_avg_s / 1e9, 1),
+                    "frequencies_integrated": "Hermitian half, H x (W/2 + 1) (value counts all M^2 frequencies)"}
     stages = {k: {"ms_per_step": round(v[0] / args.steps, 4), "calls_per_step": v[1] / args.steps}
               for k, v in prof.items() if k != "kernels"}
     launches = int(prof["kernels"])
 
+    cfg = _config(w, {"diffusion": "S-step propagators built every inpaint (SE2N_DIFFUSE_PROPAGATOR)" if prop
+                      else "step by step, the fused Crank-Nicolson kernel"}, dynamic=dynamic)
     result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-              "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config(w, dynamic=dynamic),
+              "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
               "roofline": roofline, "gpu_launches": launches, "stages_ms": stages}
+    if prop:
+        # the other two ways to run the same inpaint, on the same plan and inputs:
+        # propagators kept from the previous call (serving one beta dt and S),
+        # and the step-by-step kernel with its own roofline
+        with torch.cuda.stream(stream):
+            def timed3(fn):
+                evs = []
+                for _ in range(3):
+                    flush.zero_()
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    fn()
+                    b.record(stream)
+                    evs.append((a, b))
+                torch.cuda.synchronize(dev)
+                return sum(a.elapsed_time(b) for a, b in evs) / 3
+            se2n.se2n_inpaint(plan, f_d, m_d, None, prm, vol, out)
+            kept = timed3(lambda: se2n.se2n_inpaint(plan, f_d, m_d, None, prm, vol, out))
+            prm_s = se2n.se2n_params_default(N=w.N, beta=w.beta, T=w.T, steps=w.steps, rounds=w.rounds, eps=w.eps,
+                                             sigma_smooth=w.sigma, dynamic=int(dynamic))
+            se2n.se2n_inpaint(plan, f_d, m_d, None, prm_s, vol, out)
+            torch.cuda.synchronize(dev)
+            se2n.se2n_plan_profile(plan, True)
+            stepwise = timed3(lambda: se2n.se2n_inpaint(plan, f_d, m_d, None, prm_s, vol, out))
+            sprof = se2n.se2n_plan_profile_read(plan, reset=True)
+            se2n.se2n_plan_profile(plan, False)
+        sd_s = sprof["diffuse"][0] / sprof["diffuse"][1] / 1e3
+        s_ach = FLOPS_PER_UPDATE * updates_per_launch / sd_s / 1e12
+        result["propagators_kept"] = {"ms_per_step": round(kept, 4), "value": world * w.updates() / (kept / 1e3)}
+        result["step_by_step"] = {
+            "ms_per_step": round(stepwise, 4), "value": world * w.updates() / (stepwise / 1e3),
+            "roofline": {"bound": "alu", "kernel": "k_diffuse_x2<32,2,false>", "avg_launch_ms": round(sd_s * 1e3, 4),
+                         "achieved": round(s_ach, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
+                         "frac": round(s_ach / peak, 4), "traffic": stored_traffic(),
+                         "flops_per_update": FLOPS_PER_UPDATE, "updates_per_launch": updates_per_launch}}
     if dynamic:
         # one growth step reads the real volume once (max and argmax over the
         # angles) and a few bytes a pixel of image and set state
@@ -270,6 +365,8 @@ def run_ours(args, rank, world, local_rank):
     e2e_ms = []
     for _ in range(max(3, min(args.steps, 10))):
         flush.zero_()
+        if prop:
+            se2n.se2n_plan_drop_propagators(plan)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         se2n.se2n_inpaint_host(plan, f_h.data_ptr(), m_h.data_ptr(), prm, o_h.data_ptr())
@@ -903,6 +1000,9 @@ def main():
                     help="512: the 512x512 N=32 10x500-step inpaint (default); dr: the same with dynamic "
                          "restoration; batch: 256 uneven images; surrogate: train the U-Net on method pairs, "
                          "time its inference with fallback")
+    ap.add_argument("--diffusion", choices=["propagator", "steps"], default="propagator",
+                    help="512 / dr: integrate each interval by S-step propagators built every inpaint (default) "
+                         "or step by step with the fused Crank-Nicolson kernel")
     ap.add_argument("--train-seconds", type=float, default=150.0, help="surrogate training time budget")
     ap.add_argument("--train-pairs", type=int, default=0, help="surrogate training pairs (0: all 20000)")
     ap.add_argument("--traffic", type=float, default=None,

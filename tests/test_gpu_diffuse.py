@@ -203,7 +203,7 @@ def test_rejects_bad_arguments():
         se2n.se2n_diffuse(plan, v.data_ptr() + 8, 0.5, 1.0, 10)   # misaligned
     assert e.value.status == se2n.SE2N_EINVAL
     with pytest.raises(se2n.Se2nError) as e:
-        se2n.se2n_diffuse(plan, v, 0.5, 1.0, 10, 8)   # unknown flag
+        se2n.se2n_diffuse(plan, v, 0.5, 1.0, 10, 16)   # unknown flag
     assert e.value.status == se2n.SE2N_EINVAL
     # nothing was enqueued: the volume is untouched and the context healthy
     assert (host(v) == 0).all()

@@ -201,7 +201,7 @@ def test_inpaint_rejects_bad_parameters():
     vol = torch.empty((16, 16, 16), dtype=torch.complex64, device="cuda")
     out = torch.empty((16, 16), dtype=torch.float32, device="cuda")
     bad = [dict(N=32), dict(eps=1.5), dict(rounds=0), dict(steps=0), dict(beta=0.0), dict(proj=3),
-           dict(sigma_smooth=0.0), dict(final_mix=2), dict(diffuse_flags=8), dict(reinject=2)]
+           dict(sigma_smooth=0.0), dict(final_mix=2), dict(diffuse_flags=16), dict(reinject=2), dict(dynamic=2)]
     for b in bad:
         prm = se2n.se2n_params_default(N=16)
         for k, v in b.items():
