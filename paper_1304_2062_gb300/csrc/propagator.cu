@@ -56,18 +56,19 @@ namespace {
 
 constexpr int kApplyWarps = 8;  // warps a block in the apply kernel
 
-// Build kernel: one lane a column (N = 64: two), a tile of TR x TC entries of
-// every product a lane.
+// Build kernel: a lane owns a TR x TC tile of every product (4 x 4 at N = 16,
+// 8 x 8 at N = 32, 16 x 8 at N = 64: 16, 16 and 32 lanes a class) and, in the
+// column-wise steps, N / LPC columns.
 template <int N>
 struct PropCfg {
     static constexpr int WARPS = N == 64 ? 2 : 4;  // warps a block
-    static constexpr int LPC = N < 32 ? N : 32;    // lanes a class
+    static constexpr int LPC = N == 64 ? 32 : 16;  // lanes a class
     static constexpr int CPW = 32 / LPC;           // classes a warp
     static constexpr int CPL = N / LPC;            // columns a lane in the column-wise steps
     static constexpr int LD = N + 4;               // column (or row) stride in shared memory, floats
     static constexpr int MAT = N * LD;             // floats a matrix
-    // P column- and row-major, R, and the product's two layouts; pivots, q, scalars
-    static constexpr int CLASS_FLOATS = 5 * MAT + 2 * N + 4;
+    // P column- and row-major and R (products are formed in place); pivots, q, scalars
+    static constexpr int CLASS_FLOATS = 3 * MAT + 2 * N + 4;
     static constexpr int SBLK = (N / 2 + 1) * N;   // stored floats a class
     static constexpr int SMEM = WARPS * CPW * CLASS_FLOATS * 4;
     static_assert(N % 4 == 0 && LD % 4 == 0, "16-byte shared-memory vectors");
@@ -87,14 +88,16 @@ __device__ __forceinline__ void class_members(const PropArgs &a, long long u, in
 
 // out = two * X + Y + A B for one class, N x N in shared memory: A, X, Y and
 // out column-major, B row-major (stride LD), Y may be null, out_row (if not
-// null) receives the result row-major too; outputs differ from every input.
+// null) receives the result row-major too. Every lane of the warp calls this
+// together: the warp synchronises between the last read of the inputs and
+// the first write, so out and out_row may be inputs (products in place).
 // Register-blocked: lane t owns the TR x TC tile at rows (t % RB) TR, columns
 // (t / RB) TC, and per k loads the tile's slice of column k of A and of row k
 // of B with 16-byte loads (one or a few distinct addresses a warp).
 template <int N>
 struct GemmTile {
     static constexpr int TR = N == 16 ? 4 : (N == 32 ? 8 : 16);
-    static constexpr int TC = N == 16 ? 4 : (N == 32 ? 4 : 8);
+    static constexpr int TC = N == 16 ? 4 : 8;
     static constexpr int RB = N / TR;
     static_assert((N / TR) * (N / TC) == PropCfg<N>::LPC, "one tile a lane");
     static_assert(TR % 4 == 0 && TC % 4 == 0, "16-byte vectors");
@@ -142,6 +145,7 @@ __device__ __forceinline__ void prop_gemm(const float *A, const float *Brow, con
             for (int i = 0; i < Tl::TR / 2; ++i) acc[c][i] = fma2(av[i], s, acc[c][i]);
         }
     }
+    __syncwarp();
 #pragma unroll
     for (int c = 0; c < Tl::TC; ++c)
 #pragma unroll
@@ -197,7 +201,7 @@ __global__ void __launch_bounds__(PropCfg<N>::WARPS * 32) k_prop_build(const __g
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane / C::LPC, t = lane - g * C::LPC;
     float *base = psm + (warp * C::CPW + g) * C::CLASS_FLOATS;
-    float *G = base + 5 * C::MAT;
+    float *G = base + 3 * C::MAT;
     float *q = G + N;
     float *scal = q + N;  // 1/d0, 1/(1 + v.q)
     const long long stride = (long long)gridDim.x * C::WARPS * C::CPW;
@@ -292,9 +296,8 @@ __global__ void __launch_bounds__(PropCfg<N>::WARPS * 32) k_prop_build(const __g
         }
         __syncwarp();
         // binary powering: P (column- and row-major) runs through D_1, D_2,
-        // D_4, ...; R collects the set bits of S; products go to Tc (and Tr)
-        float *P = base, *Pr = base + C::MAT, *R = base + 2 * C::MAT, *Tc = base + 3 * C::MAT,
-              *Tr = base + 4 * C::MAT;
+        // D_4, ...; R collects the set bits of S; products in place
+        float *P = base, *Pr = base + C::MAT, *R = base + 2 * C::MAT;
         bool have_r = false;
         int s = a.steps;
 #pragma unroll 1
@@ -312,22 +315,13 @@ __global__ void __launch_bounds__(PropCfg<N>::WARPS * 32) k_prop_build(const __g
                     }
                     have_r = true;
                 } else {
-                    prop_gemm<N>(R, Pr, R, 1.0f, P, Tc, nullptr, t);  // R + P + R P
-                    float *tmp = R;
-                    R = Tc;
-                    Tc = tmp;
+                    prop_gemm<N>(R, Pr, R, 1.0f, P, R, nullptr, t);  // R + P + R P
                 }
                 __syncwarp();
             }
             s >>= 1;
             if (!s) break;
-            prop_gemm<N>(P, Pr, P, 2.0f, nullptr, Tc, Tr, t);  // 2 P + P P
-            float *tmp = P;
-            P = Tc;
-            Tc = tmp;
-            tmp = Pr;
-            Pr = Tr;
-            Tr = tmp;
+            prop_gemm<N>(P, Pr, P, 2.0f, nullptr, P, Pr, t);  // 2 P + P P
             __syncwarp();
         }
         // D_S by cyclic diagonals: this lane writes S_m[i] for i = t, t + LPC, ...
