@@ -54,8 +54,6 @@ __device__ __forceinline__ void pair_row(int s, int H, int &k, int &kb) {
 
 namespace {
 
-constexpr int kApplyWarps = 8;  // warps a block in the apply kernel
-
 // Build kernel: a lane owns a TR x TC tile of every product (4 x 4 at N = 16,
 // 8 x 8 at N = 32, 16 x 8 at N = 64: 16, 16 and 32 lanes a class) and, in the
 // column-wise steps, N / LPC columns.
@@ -343,89 +341,104 @@ __global__ void __launch_bounds__(PropCfg<N>::WARPS * 32) k_prop_build(const __g
     }
 }
 
-// x <- x + D_S x for the (up to four) frequencies of every class. The warp
-// first fetches the class's whole diagonal block with 16-byte loads into
-// shared memory, together with the frequencies' N-vectors, so a class costs
-// one round trip to memory; lane r then forms row r from the block.
+// x <- x + D_S x for the (up to four) frequencies of every class. A lane owns
+// RPL rows of a class. It issues every global load it needs at once (its
+// rows' diagonal entries, coalesced across the lanes of the class, and its
+// rows of the four frequencies' vectors), then expands the rows into a padded
+// N x (N + 1) matrix in shared memory, reads them back into registers in
+// column order, and for every column j loads x_j of the four frequencies
+// once (a shared-memory broadcast for all its rows) for RPL x 4 packed FMAs.
 template <int N>
 struct ApplyCfg {
-    static constexpr int LPC = N < 32 ? N : 32;  // lanes a class: one row (N = 64: two) a lane
-    static constexpr int CPW = 32 / LPC;
-    static constexpr int CPL = N / LPC;
+    static constexpr int WARPS = 4;
+    static constexpr int RPL = N == 16 ? 1 : 2;  // rows a lane
+    static constexpr int LPC = N / RPL;          // lanes a class: 16, 16 or 32
+    static constexpr int CPW = 32 / LPC;         // classes a warp
+    static constexpr int DLD = N + 1;            // row stride of the expanded matrix
+    static constexpr int DF = N * DLD;
+    static constexpr int XF = 8 * N;             // x_j of the four frequencies, (re, im) each
+    // class regions 8 floats apart modulo 32 so that the classes of a warp
+    // fall on different banks
+    static constexpr int CLASS_FLOATS = ((DF + XF + 31) / 32) * 32 + 8;
     static constexpr int SBLK = PropCfg<N>::SBLK;
-    static constexpr int S_FLOATS = CPW * SBLK;               // diagonal blocks a warp
-    static constexpr int X_FLOATS = CPW * 4 * N * 2;          // the classes' vectors a warp
-    static constexpr int WARP_FLOATS = S_FLOATS + X_FLOATS;
-    static constexpr int SMEM = kApplyWarps * WARP_FLOATS * 4;
-    static_assert(SBLK % 4 == 0, "16-byte blocks");
+    static constexpr int SMEM = WARPS * CPW * CLASS_FLOATS * 4;
+    static_assert(XF % 4 == 0 && (CLASS_FLOATS % 4) == 0, "16-byte vectors");
 };
 
 template <int N>
-__global__ void __launch_bounds__(kApplyWarps * 32) k_prop_apply(const __grid_constant__ PropArgs a) {
+__global__ void __launch_bounds__(ApplyCfg<N>::WARPS * 32) k_prop_apply(const __grid_constant__ PropArgs a) {
     using C = ApplyCfg<N>;
-    using AC = ApplyCfg<N>;
     extern __shared__ __align__(16) float asm_[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane / C::LPC, t = lane - g * C::LPC;
-    float *sblk = asm_ + warp * AC::WARP_FLOATS;                 // [CPW][SBLK]
-    float2 *xs = reinterpret_cast<float2 *>(sblk + AC::S_FLOATS);  // [CPW][4][N]
-    const long long stride = (long long)gridDim.x * kApplyWarps * C::CPW;
-    for (long long u0 = ((long long)blockIdx.x * kApplyWarps + warp) * C::CPW; u0 < a.classes; u0 += stride) {
-        // the warp's CPW consecutive classes are contiguous in D: one block copy
-        const long long nlive = (a.classes - u0 < C::CPW) ? a.classes - u0 : C::CPW;
-        const float4 *src = reinterpret_cast<const float4 *>(a.D + u0 * (long long)C::SBLK);
-        const int n4 = (int)(nlive * C::SBLK / 4);
-        for (int i = lane; i < n4; i += 32) reinterpret_cast<float4 *>(sblk)[i] = __ldg(src + i);
+    float *xs = asm_ + (warp * C::CPW + g) * C::CLASS_FLOATS;  // [N][8], 16-byte aligned
+    float *Df = xs + C::XF;                                     // [N][DLD]
+    const long long stride = (long long)gridDim.x * C::WARPS * C::CPW;
+    for (long long u0 = ((long long)blockIdx.x * C::WARPS + warp) * C::CPW; u0 < a.classes; u0 += stride) {
         const long long u = u0 + g;
         const bool live = u < a.classes;
+        const long long uc = live ? u : a.classes - 1;
         int k, kb, l, lb;
-        class_members(a, live ? u : a.classes - 1, k, kb, l, lb);
+        class_members(a, uc, k, kb, l, lb);
         const long long f[4] = {(long long)k * a.Wc + l, (long long)k * a.Wc + lb, (long long)kb * a.Wc + l,
                                 (long long)kb * a.Wc + lb};
         const bool on[4] = {live, live && lb != l, live && kb != k, live && kb != k && lb != l};
-        float2 *xg = xs + g * 4 * N;
-        float2 mine[4][C::CPL];
+        const float *Sc = a.D + uc * (long long)C::SBLK;
+        // row r: D[r, r + d] = S_d[r] (d = 0 .. N/2), D[r, r - d] = S_d[r - d]
+        // (d = 1 .. N/2 - 1); dv[i][d] and dv[i][N/2 + d] hold them
+        float dv[C::RPL][N];
+        float2 mine[4][C::RPL];
 #pragma unroll
-        for (int m = 0; m < 4; ++m)
+        for (int i = 0; i < C::RPL; ++i) {
+            const int r = t + i * C::LPC;
 #pragma unroll
-            for (int cc = 0; cc < C::CPL; ++cc) {
-                const int j = t + cc * C::LPC;
-                mine[m][cc] = on[m] ? a.vol[(long long)j * a.HW + f[m]] : make_float2(0.f, 0.f);
-                xg[m * N + j] = mine[m][cc];
-            }
+            for (int d = 0; d <= N / 2; ++d) dv[i][d] = __ldg(Sc + d * N + r);
+#pragma unroll
+            for (int d = 1; d < N / 2; ++d) dv[i][N / 2 + d] = __ldg(Sc + d * N + ((r - d) & (N - 1)));
+#pragma unroll
+            for (int m = 0; m < 4; ++m) mine[m][i] = on[m] ? a.vol[(long long)r * a.HW + f[m]] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int i = 0; i < C::RPL; ++i) {
+            const int r = t + i * C::LPC;
+#pragma unroll
+            for (int d = 0; d <= N / 2; ++d) Df[r * C::DLD + ((r + d) & (N - 1))] = dv[i][d];
+#pragma unroll
+            for (int d = 1; d < N / 2; ++d) Df[r * C::DLD + ((r - d) & (N - 1))] = dv[i][N / 2 + d];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) *reinterpret_cast<float2 *>(xs + r * 8 + 2 * m) = mine[m][i];
+        }
         __syncwarp();
-        const float *Sc = sblk + g * C::SBLK;
+        float drow[C::RPL][N];
 #pragma unroll
-        for (int cc = 0; cc < C::CPL; ++cc) {
-            const int r = t + cc * C::LPC;
-            f32x2 acc[4];
+        for (int i = 0; i < C::RPL; ++i)
 #pragma unroll
-            for (int m = 0; m < 4; ++m) acc[m] = pk2(0.f, 0.f);
-            // y_r = sum_{d=0}^{N/2} S_d[r] x_{r+d} + sum_{d=1}^{N/2-1} S_d[r-d] x_{r-d}
-#pragma unroll 4
-            for (int d = 0; d <= N / 2; ++d) {
-                const int jp = (r + d) & (N - 1);
-                const f32x2 s = dup2(Sc[d * N + r]);
+            for (int j = 0; j < N; ++j) drow[i][j] = Df[(t + i * C::LPC) * C::DLD + j];
+        f32x2 acc[C::RPL][4];
 #pragma unroll
-                for (int m = 0; m < 4; ++m) {
-                    const float2 xv = xg[m * N + jp];
-                    acc[m] = fma2(s, pk2(xv.x, xv.y), acc[m]);
-                }
-                if (d >= 1 && d < N / 2) {
-                    const int jm = (r - d) & (N - 1);
-                    const f32x2 s2 = dup2(Sc[d * N + jm]);
+        for (int i = 0; i < C::RPL; ++i)
 #pragma unroll
-                    for (int m = 0; m < 4; ++m) {
-                        const float2 xv = xg[m * N + jm];
-                        acc[m] = fma2(s2, pk2(xv.x, xv.y), acc[m]);
-                    }
-                }
+            for (int m = 0; m < 4; ++m) acc[i][m] = pk2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            const float4 xa = *reinterpret_cast<const float4 *>(xs + j * 8);
+            const float4 xb = *reinterpret_cast<const float4 *>(xs + j * 8 + 4);
+            const f32x2 xm[4] = {pk2(xa.x, xa.y), pk2(xa.z, xa.w), pk2(xb.x, xb.y), pk2(xb.z, xb.w)};
+#pragma unroll
+            for (int i = 0; i < C::RPL; ++i) {
+                const f32x2 sd = dup2(drow[i][j]);
+#pragma unroll
+                for (int m = 0; m < 4; ++m) acc[i][m] = fma2(sd, xm[m], acc[i][m]);
             }
+        }
+#pragma unroll
+        for (int i = 0; i < C::RPL; ++i) {
+            const int r = t + i * C::LPC;
 #pragma unroll
             for (int m = 0; m < 4; ++m)
                 if (on[m])
                     a.vol[(long long)r * a.HW + f[m]] =
-                        make_float2(mine[m][cc].x + lo2(acc[m]), mine[m][cc].y + hi2(acc[m]));
+                        make_float2(mine[m][i].x + lo2(acc[i][m]), mine[m][i].y + hi2(acc[i][m]));
         }
         __syncwarp();
     }
@@ -450,14 +463,13 @@ cudaError_t launch_build(const PropArgs &a, int num_sms, cudaStream_t s) {
 template <int N>
 cudaError_t launch_apply(const PropArgs &a, int num_sms, cudaStream_t s) {
     using C = ApplyCfg<N>;
-    using AC = ApplyCfg<N>;
-    cudaError_t e = cudaFuncSetAttribute(k_prop_apply<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, AC::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_prop_apply<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
-    const long long per_block = (long long)kApplyWarps * C::CPW;
+    const long long per_block = (long long)C::WARPS * C::CPW;
     long long blocks = (a.classes + per_block - 1) / per_block;
     const long long cap = (long long)num_sms * 64;
     if (blocks > cap) blocks = cap;
-    k_prop_apply<N><<<(unsigned)blocks, kApplyWarps * 32, AC::SMEM, s>>>(a);
+    k_prop_apply<N><<<(unsigned)blocks, C::WARPS * 32, C::SMEM, s>>>(a);
     return cudaGetLastError();
 }
 
