@@ -354,6 +354,7 @@ typedef struct se2n_batch_info {
     double best_ms, worst_ms;        /* their fastest and slowest diffusion time */
     double updates_per_run;          /* sum of H W N steps rounds over the images */
     double volume_bytes;             /* device bytes of the lifted volumes */
+    int prop_images;                 /* images integrated by their shape's propagators */
 } se2n_batch_info;
 
 /* Build a batch of `count` images. p->N is ignored (each image has its
@@ -363,7 +364,11 @@ typedef struct se2n_batch_info {
  * 8 N H W + H W bytes per image plus the plans. Synchronizes the stream.
  * A NULL (legacy default) stream is replaced by a blocking stream the batch
  * creates, since graphs cannot be captured on the legacy stream; it is
- * ordered with the caller's legacy-stream work. */
+ * ordered with the caller's legacy-stream work. With SE2N_DIFFUSE_PROPAGATOR
+ * in p->diffuse_flags, the images of each distinct (H, W, N) are integrated
+ * by that shape's S-step propagators (built once a run, shared by the images)
+ * when that is estimated to cost less than stepping them, the others by the
+ * persistent step-by-step kernel; se2n_batch_get_info reports how many. */
 SE2N_API se2n_status se2n_batch_create(se2n_batch **out, const se2n_image_desc *imgs, int count,
                                        const se2n_params *p, int angle_conv, int flags, void *stream);
 

@@ -100,6 +100,26 @@ void angle_table(int N, int angle_conv, float *cs, float *sn, int count) {
 
 namespace {
 
+// Device memory for the plan's propagators (grown when too small, which
+// invalidates them).
+se2n_status prop_reserve(se2n_plan *plan, bool half) {
+    const size_t need =
+        (size_t)se2n_prop_classes(plan->H, plan->W, half) * (size_t)se2n_prop_floats(plan->N) * sizeof(float);
+    if (plan->prop_bytes >= need) return SE2N_OK;
+    cudaFree(plan->prop_D);
+    plan->prop_D = nullptr;
+    plan->prop_bytes = 0;
+    plan->prop_valid = false;
+    cudaError_t e = cudaMalloc(&plan->prop_D, need);
+    if (e != cudaSuccess) {
+        plan->prop_D = nullptr;
+        (void)cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? SE2N_ENOMEM : SE2N_ECUDA;
+    }
+    plan->prop_bytes = need;
+    return SE2N_OK;
+}
+
 // The S-step propagators of every class of equal-coefficient frequencies,
 // built when beta dt, S or the spectrum half changed, then applied once.
 se2n_status propagate_impl(se2n_plan *plan, float2 *vol, double beta, double bdt, int steps, bool half) {
@@ -117,20 +137,7 @@ se2n_status propagate_impl(se2n_plan *plan, float2 *vol, double beta, double bdt
     a.inv_c = (float)(2.0 / bdt);
     a.inv_beta = (float)(1.0 / beta);
     angle_table(plan->N, plan->angle_conv, a.cs, a.sn, SE2N_MAX_N);
-    const size_t need = (size_t)a.classes * (size_t)se2n_prop_floats(plan->N) * sizeof(float);
-    if (plan->prop_bytes < need) {
-        cudaFree(plan->prop_D);
-        plan->prop_D = nullptr;
-        plan->prop_bytes = 0;
-        plan->prop_valid = false;
-        cudaError_t e = cudaMalloc(&plan->prop_D, need);
-        if (e != cudaSuccess) {
-            plan->prop_D = nullptr;
-            (void)cudaGetLastError();
-            return e == cudaErrorMemoryAllocation ? SE2N_ENOMEM : SE2N_ECUDA;
-        }
-        plan->prop_bytes = need;
-    }
+    SE2N_TRY(prop_reserve(plan, half));
     a.D = plan->prop_D;
     if (!(plan->prop_valid && plan->prop_beta == beta && plan->prop_bdt == bdt && plan->prop_steps == steps &&
           plan->prop_half == half)) {
@@ -778,6 +785,8 @@ struct se2n_batch {
     std::vector<float2 *> vols;
     std::vector<uint8_t *> bins;
     std::vector<DrState> dr;  // per image, with dynamic restoration
+    std::vector<char> img_prop;   // per image: integrated by its shape's propagators
+    int prop_images = 0;
     std::vector<BatchImage> h_imgs;
     float *d_tables = nullptr;
     BatchImage *d_imgs = nullptr;
@@ -808,6 +817,7 @@ std::vector<BatchItem> build_items(const se2n_batch *b, int config, int passes) 
     });
     std::vector<BatchItem> items;
     for (int i : order) {
+        if (!b->img_prop.empty() && b->img_prop[i]) continue;  // integrated by propagators
         const se2n_image_desc &d = b->imgs[i];
         const long long HW = b->h_imgs[i].HW;  // frequencies integrated (the Hermitian half by default)
         const int per = 32 / se2n_batch_config_P(config, d.N);
@@ -847,6 +857,53 @@ se2n_status batch_diffuse(se2n_batch *b, int steps, double T) {
         e = se2n_launch_diffuse_batch(b->config, b->fast, b->split, sp, b->d_tables, b->d_imgs, b->d_items,
                                       b->n_items, b->d_counter, b->block, b->blocks, b->stream);
     return e == cudaSuccess ? SE2N_OK : SE2N_ECUDA;
+}
+
+// One interval of every image: the persistent step-by-step launch over the
+// whole batch, or, with SE2N_DIFFUSE_PROPAGATOR, each image's propagators
+// (built once per distinct plan shape, which the images of that shape share).
+se2n_status batch_interval(se2n_batch *b, double Tr, bool half) {
+    const se2n_params &p = b->p;
+    if (b->prop_images < b->count) SE2N_TRY(batch_diffuse(b, p.steps, Tr));
+    if (b->prop_images > 0)
+        for (int i = 0; i < b->count; ++i)
+            if (b->img_prop[i])
+                SE2N_TRY(diffuse_impl(b->plan_of[i], b->vols[i], p.beta, Tr, p.steps, p.diffuse_flags, half));
+    return SE2N_OK;
+}
+
+// With SE2N_DIFFUSE_PROPAGATOR, the images of one shape are integrated by
+// that shape's propagators when building them once and applying them to every
+// image and interval is estimated to cost less than the step-by-step kernel on
+// those images. The estimate uses this library's measured rates on a GB300
+// (512^2, N = 32): step kernel about 54 TFLOP/s at 22 flops an update, build
+// about 30 TFLOP/s at 2 N^3 flops a product, apply about 2 TB/s.
+void choose_propagators(se2n_batch *b) {
+    const se2n_params &p = b->p;
+    b->img_prop.assign(b->count, 0);
+    b->prop_images = 0;
+    if (!(p.diffuse_flags & SE2N_DIFFUSE_PROPAGATOR)) return;
+    const bool half = !p.full_spectrum;
+    const int S = p.steps;
+    int products = -1;
+    for (int s = S; s; s >>= 1) products += 1 + (s & 1);  // squarings + combinations
+    products -= 1;
+    for (se2n_plan *pl : b->plans) {
+        int n_img = 0;
+        for (int i = 0; i < b->count; ++i) n_img += b->plan_of[i] == pl;
+        const double freqs = (double)pl->H * (half ? pl->W / 2 + 1 : pl->W);
+        const double N = pl->N;
+        const double steps_s = n_img * (double)p.rounds * freqs * N * S * 22.0 / 54e12;
+        const double classes = (double)se2n_prop_classes(pl->H, pl->W, half);
+        const double build_s = classes * products * 2.0 * N * N * N / 30e12;
+        const double apply_s = n_img * (double)p.rounds * (classes * 4.0 * N * (N / 2 + 1) + 16.0 * freqs * N) / 2e12;
+        if (build_s + apply_s < steps_s)
+            for (int i = 0; i < b->count; ++i)
+                if (b->plan_of[i] == pl) {
+                    b->img_prop[i] = 1;
+                    b->prop_images += 1;
+                }
+    }
 }
 
 se2n_status set_shape(se2n_batch *b, int config, int passes, int block) {
@@ -918,7 +975,7 @@ se2n_status enqueue_batch_half(se2n_batch *b) {
         SE2N_TRY(fft_half(pl, b->vols[i], true));
         if (p.dynamic) SE2N_TRY(dr_begin(pl, b->dr[i], d.f, d.mask, b->bins[i]));
     }
-    SE2N_TRY(batch_diffuse(b, p.steps, Tr));
+    SE2N_TRY(batch_interval(b, Tr, true));
     for (int r = 1; r < p.rounds; ++r) {
         for (int i = 0; i < b->count; ++i) {
             se2n_plan *pl = b->plan_of[i];
@@ -928,7 +985,7 @@ se2n_status enqueue_batch_half(se2n_batch *b) {
                                   (float)(1.0 / (double)pl->HW), (float)p.eps, (float)p.guard, true));
             SE2N_TRY(fft_half(pl, b->vols[i], true));
         }
-        SE2N_TRY(batch_diffuse(b, p.steps, Tr));
+        SE2N_TRY(batch_interval(b, Tr, true));
     }
     for (int i = 0; i < b->count; ++i) {
         se2n_plan *pl = b->plan_of[i];
@@ -964,7 +1021,7 @@ se2n_status enqueue_batch(se2n_batch *b) {
         SE2N_TRY(fft(pl, pl->fft_vol, b->vols[i], CUFFT_FORWARD));
         if (p.dynamic) SE2N_TRY(dr_begin(pl, b->dr[i], d.f, d.mask, b->bins[i]));
     }
-    SE2N_TRY(batch_diffuse(b, p.steps, Tr));
+    SE2N_TRY(batch_interval(b, Tr, false));
     for (int r = 1; r < p.rounds; ++r) {
         for (int i = 0; i < b->count; ++i) {
             se2n_plan *pl = b->plan_of[i];
@@ -974,7 +1031,7 @@ se2n_status enqueue_batch(se2n_batch *b) {
                                   (float)(1.0 / (double)pl->HW), (float)p.eps, (float)p.guard, false));
             SE2N_TRY(fft(pl, pl->fft_vol, b->vols[i], CUFFT_FORWARD));
         }
-        SE2N_TRY(batch_diffuse(b, p.steps, Tr));
+        SE2N_TRY(batch_interval(b, Tr, false));
     }
     for (int i = 0; i < b->count; ++i) {
         se2n_plan *pl = b->plan_of[i];
@@ -1097,6 +1154,16 @@ se2n_status create_batch(se2n_batch *b, const se2n_image_desc *imgs) {
     // transforms of the Hermitian-half path are planned before the capture
     if (!b->p.full_spectrum)
         for (se2n_plan *pl : b->plans) SE2N_TRY(ensure_half(pl));
+    // so is the propagators' memory; the graph builds them (once per shape)
+    choose_propagators(b);
+    for (se2n_plan *pl : b->plans) {
+        bool used = false;
+        for (int i = 0; i < b->count; ++i) used = used || (b->img_prop[i] && b->plan_of[i] == pl);
+        if (!used) continue;
+        SE2N_TRY(prop_reserve(pl, !b->p.full_spectrum));
+        if (se2n_prop_prepare(pl->N) != cudaSuccess) return SE2N_ECUDA;
+        pl->prop_valid = false;
+    }
     if (b->flags_autotune) {
         SE2N_TRY(autotune(b));
     } else {
@@ -1178,6 +1245,8 @@ se2n_status se2n_batch_run_per_image(se2n_batch *b) {
     for (int i = 0; i < b->count; ++i) {
         se2n_params q = b->p;
         q.N = b->imgs[i].N;
+        // the same integration the batch chose for this image's shape
+        if (b->img_prop.empty() || !b->img_prop[i]) q.diffuse_flags &= ~SE2N_DIFFUSE_PROPAGATOR;
         SE2N_TRY(inpaint_impl(b->plan_of[i], b->imgs[i].f, b->imgs[i].mask, b->imgs[i].bins, &q, b->vols[i],
                               b->imgs[i].out));
     }
@@ -1206,6 +1275,7 @@ se2n_status se2n_batch_get_info(se2n_batch *b, se2n_batch_info *out) {
     out->worst_ms = b->worst_ms;
     out->updates_per_run = b->updates;
     out->volume_bytes = (double)b->vol_bytes;
+    out->prop_images = b->prop_images;
     return SE2N_OK;
 }
 

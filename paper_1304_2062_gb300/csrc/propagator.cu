@@ -487,6 +487,30 @@ long long se2n_prop_classes(int H, int W, bool half) {
     return (long long)se2n::pair_rows(H) * se2n_prop_col_slots(W, half);
 }
 
+cudaError_t se2n_prop_prepare(int N) {
+    switch (N) {
+        case 16:
+            return cudaFuncSetAttribute(se2n::k_prop_build<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        se2n::PropCfg<16>::SMEM) == cudaSuccess
+                       ? cudaFuncSetAttribute(se2n::k_prop_apply<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              se2n::ApplyCfg<16>::SMEM)
+                       : cudaGetLastError();
+        case 32:
+            return cudaFuncSetAttribute(se2n::k_prop_build<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        se2n::PropCfg<32>::SMEM) == cudaSuccess
+                       ? cudaFuncSetAttribute(se2n::k_prop_apply<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              se2n::ApplyCfg<32>::SMEM)
+                       : cudaGetLastError();
+        case 64:
+            return cudaFuncSetAttribute(se2n::k_prop_build<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        se2n::PropCfg<64>::SMEM) == cudaSuccess
+                       ? cudaFuncSetAttribute(se2n::k_prop_apply<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              se2n::ApplyCfg<64>::SMEM)
+                       : cudaGetLastError();
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t se2n_launch_prop_build(int N, const PropArgs &a, int num_sms, cudaStream_t s) {
     switch (N) {
         case 16: return se2n::launch_build<16>(a, num_sms, s);

@@ -106,6 +106,8 @@ bool se2n_prop_supported(int N);
 long long se2n_prop_floats(int N);  // stored floats a class
 int se2n_prop_col_slots(int W, bool half);
 long long se2n_prop_classes(int H, int W, bool half);
+// Set the kernels' shared-memory attributes for N (before a graph capture).
+cudaError_t se2n_prop_prepare(int N);
 cudaError_t se2n_launch_prop_build(int N, const PropArgs &a, int num_sms, cudaStream_t s);
 cudaError_t se2n_launch_prop_apply(int N, const PropArgs &a, int num_sms, cudaStream_t s);
 

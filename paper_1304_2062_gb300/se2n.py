@@ -62,7 +62,8 @@ class se2n_batch_info(ctypes.Structure):
                 ("block", ctypes.c_int), ("blocks", ctypes.c_int), ("p16", ctypes.c_int), ("p32", ctypes.c_int),
                 ("p64", ctypes.c_int), ("fast", ctypes.c_int), ("split", ctypes.c_int),
                 ("candidates", ctypes.c_int), ("best_ms", ctypes.c_double), ("worst_ms", ctypes.c_double),
-                ("updates_per_run", ctypes.c_double), ("volume_bytes", ctypes.c_double)]
+                ("updates_per_run", ctypes.c_double), ("volume_bytes", ctypes.c_double),
+                ("prop_images", ctypes.c_int)]
 
 
 class se2n_params(ctypes.Structure):

@@ -135,3 +135,40 @@ def test_batch_rejects_bad_input():
     with pytest.raises(se2n.Se2nError) as e:
         se2n.se2n_batch_create([(f, m, o, 16)], _params(), flags=2)
     assert e.value.status == se2n.SE2N_EINVAL
+
+
+@pytest.mark.parametrize("full", [0, 1])
+def test_batch_with_propagators(full):
+    """SE2N_DIFFUSE_PROPAGATOR in a batch: each distinct shape's propagators
+    are built once in the graph and shared by its images (repeated shapes
+    here); the graph replays bitwise, equals the per-image path bitwise and
+    matches the oracle."""
+    shapes = SHAPES + [(16, 24, 32), (32, 32, 16), (40, 64, 64)]
+    inputs = _inputs(shapes, seed=70)
+    T, S, R = 4.0, 100, 4
+    bins = [oracle.orient(f.astype(np.float32).astype(np.float64), m, N)["bins"] for f, m, N in inputs]
+    prm = se2n.se2n_params_default(beta=0.25, T=T, steps=S, rounds=R, eps=0.5,
+                                   diffuse_flags=se2n.SE2N_DIFFUSE_PROPAGATOR, full_spectrum=full)
+    b, outs = _batch(inputs, prm, bins=bins)
+    info = se2n.se2n_batch_get_info(b)
+    se2n.se2n_batch_run(b)
+    first = [host(o).copy() for o in outs]
+    se2n.se2n_batch_run(b)
+    second = [host(o).copy() for o in outs]
+    for o in outs:
+        o.zero_()
+    se2n.se2n_batch_run_per_image(b)
+    per = [host(o).copy() for o in outs]
+    b.close()
+    # 4 intervals of 100 steps: the cost estimate sends the N = 16 shapes and
+    # the twice-repeated 16 x 24, N = 32 one to propagators (6 images), the
+    # rest to the persistent step-by-step kernel
+    print(f"{info['prop_images']} of {info['images']} images by propagators")
+    assert info["prop_images"] == 6
+    for (f, m, N), bb, a, c, d in zip(inputs, bins, first, second, per):
+        np.testing.assert_array_equal(a, c)
+        np.testing.assert_array_equal(a, d)
+        f64 = f.astype(np.float32).astype(np.float64)
+        ref = oracle.inpaint(f64, m, oracle.Params(N=N, beta=0.25, T=T, steps=S, rounds=R), bins=bb)["out"]
+        assert rel_l2(a, ref) <= REL_L2
+        assert np.abs(a - ref).max() <= MAX_REL_RESTORED * np.abs(f64).max()
