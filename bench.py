@@ -446,7 +446,9 @@ def run_batch(args, rank, world, local_rank):
     mine = [allw[i] for i in shard(len(allw), rank, world)]
     stream = torch.cuda.Stream(dev)
     w0 = allw[0]
-    prm = se2n.se2n_params_default(beta=w0.beta, T=w0.T, steps=w0.steps, rounds=w0.rounds, eps=w0.eps)
+    prop = args.diffusion == "propagator"
+    prm = se2n.se2n_params_default(beta=w0.beta, T=w0.T, steps=w0.steps, rounds=w0.rounds, eps=w0.eps,
+                                   diffuse_flags=se2n.SE2N_DIFFUSE_PROPAGATOR if prop else 0)
     imgs = []
     for w in mine:
         imgs.append((torch.tensor(w.f.astype(np.float32), device=dev), torch.tensor(w.mask, device=dev),
@@ -511,8 +513,10 @@ def run_batch(args, rank, world, local_rank):
     ms_e2e = max_over_ranks(statistics.median(e2e_ms), dist, dev)
     h2d = sum(hf.nbytes + hm.nbytes for hf, hm in host_in)
     d2h = sum(ho.nbytes for ho in host_out)
-    # the diffusion launch integrates the Hermitian half of each spectrum
-    half_updates = sum(w.H * (w.W // 2 + 1) * w.N * w.steps * w.rounds for w in mine)
+    # the persistent launch integrates the Hermitian half of the spectra of the
+    # images it keeps (all of them step by step; with propagators, the shapes
+    # the batch left to it), one interval
+    half_updates = info["step_updates"]
     achieved = FLOPS_PER_UPDATE * half_updates / (ms_diff / 1e3) / 1e12
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
     batch.close()
@@ -525,6 +529,9 @@ def run_batch(args, rank, world, local_rank):
             "config": {"workload": "batch of 256 seeded images, sides U{128..1024}, N U{16,32,64}, "
                                    "60-90% corrupted, beta=0.25, T=2, 100 CN steps, 1 interval",
                        "images_this_rank": len(mine), "updates_per_step": total_updates,
+                       "diffusion": ("S-step propagators for the shapes where they are estimated cheaper "
+                                     f"({info['prop_images']} images), the persistent step kernel for the rest")
+                       if prop else "the persistent step-by-step kernel for every image",
                        "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas"},
             "per_image_launches": {"ms_per_step": ms_per_image, "value": total_updates / (ms_per_image / 1e3),
                                    "speedup_of_batched": ms_per_image / ms},

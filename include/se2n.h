@@ -355,6 +355,7 @@ typedef struct se2n_batch_info {
     double updates_per_run;          /* sum of H W N steps rounds over the images */
     double volume_bytes;             /* device bytes of the lifted volumes */
     int prop_images;                 /* images integrated by their shape's propagators */
+    double step_updates;             /* frequencies x N x steps of one interval the persistent kernel integrates */
 } se2n_batch_info;
 
 /* Build a batch of `count` images. p->N is ignored (each image has its

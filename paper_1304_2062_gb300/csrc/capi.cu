@@ -1276,6 +1276,10 @@ se2n_status se2n_batch_get_info(se2n_batch *b, se2n_batch_info *out) {
     out->updates_per_run = b->updates;
     out->volume_bytes = (double)b->vol_bytes;
     out->prop_images = b->prop_images;
+    out->step_updates = 0.0;
+    for (int i = 0; i < b->count; ++i)
+        if (b->img_prop.empty() || !b->img_prop[i])
+            out->step_updates += (double)b->h_imgs[i].HW * b->imgs[i].N * b->p.steps;
     return SE2N_OK;
 }
 
