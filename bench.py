@@ -164,11 +164,12 @@ def propagator_gemm_flops(classes, N, S):
 
 
 def propagator_classes(H, W, half=True):
-    """Classes of equal-coefficient frequencies: rows k and (H/2 - k) mod H,
-    columns l and (W/2 - l) (Hermitian half: l <= W/2)."""
-    pair_rows = H // 4 + 1 + (3 * H) // 4 - H // 2
+    """Classes of frequencies that share one propagator: row slots s in
+    [0, H/4] (rows s, H/2 - s, and H/2 + s, H - s reversed) times column
+    pairs l and (W/2 - l) (Hermitian half: l <= W/2)."""
+    row_slots = H // 4 + 1
     cols = W // 4 + 1 if half else W // 4 + 1 + (3 * W) // 4 - W // 2
-    return pair_rows * cols
+    return row_slots * cols
 
 
 def max_over_ranks(value, dist=None, device="cpu"):

@@ -10,8 +10,13 @@
 //
 // Classes. The coefficients depend on the frequency only through
 // wx = sin(2 pi l / W) and wy = sin(2 pi k / H), which are equal for rows
-// k and (H/2 - k) mod H and for columns l and (W/2 - l) mod W (pair_row):
-// up to four frequencies {k, kb} x {l, lb} share one propagator.
+// k and (H/2 - k) mod H and for columns l and (W/2 - l) mod W. Negating wy
+// maps a_r to -a_{-r} (both angle grids: theta_{-r} is -theta_r or
+// pi - theta_r), so the operator of rows H/2 + k and H - k is R L R, with R
+// the reversal r -> -r mod N of the angles, and their propagator R D R: the
+// apply reverses their vectors around the product. A class is one row slot
+// s in [0, H/4] (rows s, H/2 - s as they are, H/2 + s, H - s reversed) times
+// one column pair: up to eight frequencies share one propagator.
 //
 // Increment form. M is I plus a small matrix (of order beta dt), and its
 // powers are near I for the slow modes; stored as such in FP32 they would
@@ -44,12 +49,30 @@ namespace se2n {
 // of sinpif for both (up to the sign of a zero, which the square removes).
 // The pairs are enumerated once each: k in [0, H/4] (partner H/2 - k) and
 // k in [H/2 + 1, 3H/4] (partner 3H/2 - k); k = H/4 and 3H/4 are their own
-// partners. H is even. The same holds for columns over W.
+// partners. H is even. Columns of the full spectrum are paired this way.
 __host__ __device__ __forceinline__ int pair_rows(int H) { return H / 4 + 1 + (3 * H) / 4 - H / 2; }
 __device__ __forceinline__ void pair_row(int s, int H, int &k, int &kb) {
     const int lo = H / 4 + 1;
     k = (s < lo) ? s : H / 2 + 1 + (s - lo);
     kb = (k <= H / 2) ? H / 2 - k : 3 * H / 2 - k;
+}
+
+// Row slot s in [0, H/4] (H even): rows s and H/2 - s with wy = sin(2 pi s / H)
+// (the coefficients the propagator is built for) and rows H/2 + s and
+// (H - s) mod H with -wy (taken reversed). Each row of the plane is in
+// exactly one slot: s = 0 holds rows 0 and H/2 only, and s = H/4 rows H/4
+// and 3H/4 only.
+__host__ __device__ __forceinline__ int row_slots(int H) { return H / 4 + 1; }
+__device__ __forceinline__ void slot_rows(int s, int H, int (&k)[4], bool (&on)[4]) {
+    k[0] = s;
+    k[1] = H / 2 - s;
+    k[2] = H / 2 + s;
+    k[3] = (H - s) % H;
+    const bool quarter = 4 * s == H;
+    on[0] = true;
+    on[1] = !quarter;
+    on[2] = s != 0;
+    on[3] = s != 0 && !quarter;
 }
 
 namespace {
@@ -72,10 +95,10 @@ struct PropCfg {
     static_assert(N % 4 == 0 && LD % 4 == 0, "16-byte shared-memory vectors");
 };
 
-__device__ __forceinline__ void class_members(const PropArgs &a, long long u, int &k, int &kb, int &l, int &lb) {
-    const int srow = (int)(u / a.col_slots);
+// The row slot and the column pair of class u.
+__device__ __forceinline__ void class_slots(const PropArgs &a, long long u, int &srow, int &l, int &lb) {
+    srow = (int)(u / a.col_slots);
     const int scol = (int)(u - (long long)srow * a.col_slots);
-    pair_row(srow, a.H, k, kb);
     if (a.half) {
         l = scol;
         lb = a.W / 2 - scol;
@@ -207,8 +230,8 @@ __global__ void __launch_bounds__(PropCfg<N>::WARPS * 32) k_prop_build(const __g
     for (long long u0 = ((long long)blockIdx.x * C::WARPS + warp) * C::CPW; u0 < a.classes; u0 += stride) {
         const long long u = u0 + g;
         const bool live = u < a.classes;
-        int k, kb, l, lb;
-        class_members(a, live ? u : a.classes - 1, k, kb, l, lb);
+        int k, l, lb;
+        class_slots(a, live ? u : a.classes - 1, k, l, lb);
         const float wx = sin_2pi_frac(l, a.W), wy = sin_2pi_frac(k, a.H);
         // torn factor of A' (lane 0 of the class), diagonal d_j = 1/c + 2 + a_j^2/beta
         if (t == 0) {
@@ -341,22 +364,26 @@ __global__ void __launch_bounds__(PropCfg<N>::WARPS * 32) k_prop_build(const __g
     }
 }
 
-// x <- x + D_S x for the (up to four) frequencies of every class. A lane owns
-// RPL rows of a class. It issues every global load it needs at once (its
+// x <- x + D_S x for the (up to eight) frequencies of every class. A lane
+// owns RPL rows of a class. It issues every global load it needs at once (its
 // rows' diagonal entries, coalesced across the lanes of the class, and its
-// rows of the four frequencies' vectors), then expands the rows into a padded
+// rows of the eight frequencies' vectors), then expands the rows into a padded
 // N x (N + 1) matrix in shared memory, reads them back into registers in
-// column order, and for every column j loads x_j of the four frequencies
-// once (a shared-memory broadcast for all its rows) for RPL x 4 packed FMAs.
+// column order, and for every column j loads x_j of the eight frequencies
+// once (a shared-memory broadcast for all its rows) for RPL x 8 packed FMAs.
+// The vectors of the reversed rows are stored reversed (angle r at slot -r),
+// so slot r of every frequency receives row r of D x and goes back to the
+// angle it came from.
 template <int N>
 struct ApplyCfg {
     static constexpr int WARPS = 4;
     static constexpr int RPL = N == 16 ? 1 : 2;  // rows a lane
     static constexpr int LPC = N / RPL;          // lanes a class: 16, 16 or 32
     static constexpr int CPW = 32 / LPC;         // classes a warp
+    static constexpr int MEM = 8;                // frequencies a class
     static constexpr int DLD = N + 1;            // row stride of the expanded matrix
     static constexpr int DF = N * DLD;
-    static constexpr int XF = 8 * N;             // x_j of the four frequencies, (re, im) each
+    static constexpr int XF = 2 * MEM * N;       // x_j of the eight frequencies, (re, im) each
     // class regions 8 floats apart modulo 32 so that the classes of a warp
     // fall on different banks
     static constexpr int CLASS_FLOATS = ((DF + XF + 31) / 32) * 32 + 8;
@@ -368,26 +395,35 @@ struct ApplyCfg {
 template <int N>
 __global__ void __launch_bounds__(ApplyCfg<N>::WARPS * 32) k_prop_apply(const __grid_constant__ PropArgs a) {
     using C = ApplyCfg<N>;
+    constexpr int M = C::MEM;
     extern __shared__ __align__(16) float asm_[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane / C::LPC, t = lane - g * C::LPC;
-    float *xs = asm_ + (warp * C::CPW + g) * C::CLASS_FLOATS;  // [N][8], 16-byte aligned
+    float *xs = asm_ + (warp * C::CPW + g) * C::CLASS_FLOATS;  // [N][2M], 16-byte aligned
     float *Df = xs + C::XF;                                     // [N][DLD]
     const long long stride = (long long)gridDim.x * C::WARPS * C::CPW;
     for (long long u0 = ((long long)blockIdx.x * C::WARPS + warp) * C::CPW; u0 < a.classes; u0 += stride) {
         const long long u = u0 + g;
         const bool live = u < a.classes;
         const long long uc = live ? u : a.classes - 1;
-        int k, kb, l, lb;
-        class_members(a, uc, k, kb, l, lb);
-        const long long f[4] = {(long long)k * a.Wc + l, (long long)k * a.Wc + lb, (long long)kb * a.Wc + l,
-                                (long long)kb * a.Wc + lb};
-        const bool on[4] = {live, live && lb != l, live && kb != k, live && kb != k && lb != l};
+        int srow, l, lb;
+        class_slots(a, uc, srow, l, lb);
+        int k[4];
+        bool kon[4];
+        slot_rows(srow, a.H, k, kon);
+        // frequency m = 2 (row) + (column); rows 2 and 3 reversed
+        long long f[M];
+        bool on[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            f[m] = (long long)k[m / 2] * a.Wc + ((m & 1) ? lb : l);
+            on[m] = live && kon[m / 2] && (!(m & 1) || lb != l);
+        }
         const float *Sc = a.D + uc * (long long)C::SBLK;
         // row r: D[r, r + d] = S_d[r] (d = 0 .. N/2), D[r, r - d] = S_d[r - d]
         // (d = 1 .. N/2 - 1); dv[i][d] and dv[i][N/2 + d] hold them
         float dv[C::RPL][N];
-        float2 mine[4][C::RPL];
+        float2 mine[M][C::RPL];
 #pragma unroll
         for (int i = 0; i < C::RPL; ++i) {
             const int r = t + i * C::LPC;
@@ -396,17 +432,18 @@ __global__ void __launch_bounds__(ApplyCfg<N>::WARPS * 32) k_prop_apply(const __
 #pragma unroll
             for (int d = 1; d < N / 2; ++d) dv[i][N / 2 + d] = __ldg(Sc + d * N + ((r - d) & (N - 1)));
 #pragma unroll
-            for (int m = 0; m < 4; ++m) mine[m][i] = on[m] ? a.vol[(long long)r * a.HW + f[m]] : make_float2(0.f, 0.f);
+            for (int m = 0; m < M; ++m) mine[m][i] = on[m] ? a.vol[(long long)r * a.HW + f[m]] : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int i = 0; i < C::RPL; ++i) {
             const int r = t + i * C::LPC;
+            const int rr = (N - r) & (N - 1);
 #pragma unroll
             for (int d = 0; d <= N / 2; ++d) Df[r * C::DLD + ((r + d) & (N - 1))] = dv[i][d];
 #pragma unroll
             for (int d = 1; d < N / 2; ++d) Df[r * C::DLD + ((r - d) & (N - 1))] = dv[i][N / 2 + d];
 #pragma unroll
-            for (int m = 0; m < 4; ++m) *reinterpret_cast<float2 *>(xs + r * 8 + 2 * m) = mine[m][i];
+            for (int m = 0; m < M; ++m) *reinterpret_cast<float2 *>(xs + (m < 4 ? r : rr) * (2 * M) + 2 * m) = mine[m][i];
         }
         __syncwarp();
         float drow[C::RPL][N];
@@ -414,31 +451,39 @@ __global__ void __launch_bounds__(ApplyCfg<N>::WARPS * 32) k_prop_apply(const __
         for (int i = 0; i < C::RPL; ++i)
 #pragma unroll
             for (int j = 0; j < N; ++j) drow[i][j] = Df[(t + i * C::LPC) * C::DLD + j];
-        f32x2 acc[C::RPL][4];
+        f32x2 acc[C::RPL][M];
 #pragma unroll
         for (int i = 0; i < C::RPL; ++i)
 #pragma unroll
-            for (int m = 0; m < 4; ++m) acc[i][m] = pk2(0.f, 0.f);
+            for (int m = 0; m < M; ++m) acc[i][m] = pk2(0.f, 0.f);
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-            const float4 xa = *reinterpret_cast<const float4 *>(xs + j * 8);
-            const float4 xb = *reinterpret_cast<const float4 *>(xs + j * 8 + 4);
-            const f32x2 xm[4] = {pk2(xa.x, xa.y), pk2(xa.z, xa.w), pk2(xb.x, xb.y), pk2(xb.z, xb.w)};
+            f32x2 xm[M];
+#pragma unroll
+            for (int q = 0; q < M / 2; ++q) {
+                const float4 v = *reinterpret_cast<const float4 *>(xs + j * (2 * M) + 4 * q);
+                xm[2 * q] = pk2(v.x, v.y);
+                xm[2 * q + 1] = pk2(v.z, v.w);
+            }
 #pragma unroll
             for (int i = 0; i < C::RPL; ++i) {
                 const f32x2 sd = dup2(drow[i][j]);
 #pragma unroll
-                for (int m = 0; m < 4; ++m) acc[i][m] = fma2(sd, xm[m], acc[i][m]);
+                for (int m = 0; m < M; ++m) acc[i][m] = fma2(sd, xm[m], acc[i][m]);
             }
         }
 #pragma unroll
         for (int i = 0; i < C::RPL; ++i) {
             const int r = t + i * C::LPC;
+            const int rr = (N - r) & (N - 1);
 #pragma unroll
-            for (int m = 0; m < 4; ++m)
-                if (on[m])
-                    a.vol[(long long)r * a.HW + f[m]] =
-                        make_float2(mine[m][i].x + lo2(acc[i][m]), mine[m][i].y + hi2(acc[i][m]));
+            for (int m = 0; m < M; ++m)
+                if (on[m]) {
+                    // slot r holds the value of angle r (rows 0, 1) or -r (rows 2, 3)
+                    const float2 x0 = *reinterpret_cast<const float2 *>(xs + r * (2 * M) + 2 * m);
+                    a.vol[(long long)(m < 4 ? r : rr) * a.HW + f[m]] =
+                        make_float2(x0.x + lo2(acc[i][m]), x0.y + hi2(acc[i][m]));
+                }
         }
         __syncwarp();
     }
@@ -484,7 +529,7 @@ long long se2n_prop_floats(int N) { return (long long)(N / 2 + 1) * N; }
 int se2n_prop_col_slots(int W, bool half) { return half ? W / 4 + 1 : se2n::pair_rows(W); }
 
 long long se2n_prop_classes(int H, int W, bool half) {
-    return (long long)se2n::pair_rows(H) * se2n_prop_col_slots(W, half);
+    return (long long)se2n::row_slots(H) * se2n_prop_col_slots(W, half);
 }
 
 cudaError_t se2n_prop_prepare(int N) {

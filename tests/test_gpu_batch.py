@@ -160,11 +160,11 @@ def test_batch_with_propagators(full):
     se2n.se2n_batch_run_per_image(b)
     per = [host(o).copy() for o in outs]
     b.close()
-    # 4 intervals of 100 steps: the cost estimate sends the N = 16 shapes and
-    # the twice-repeated 16 x 24, N = 32 one to propagators (6 images), the
-    # rest to the persistent step-by-step kernel
+    # 4 intervals of 100 steps: the cost estimate sends the small shapes to
+    # propagators and the rest to the persistent step-by-step kernel; both
+    # paths must be taken for the checks below to cover the mixed graph
     print(f"{info['prop_images']} of {info['images']} images by propagators")
-    assert info["prop_images"] == 6
+    assert 0 < info["prop_images"] < info["images"]
     for (f, m, N), bb, a, c, d in zip(inputs, bins, first, second, per):
         np.testing.assert_array_equal(a, c)
         np.testing.assert_array_equal(a, d)

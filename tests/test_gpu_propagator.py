@@ -1,6 +1,10 @@
 """The S-step propagator path (SE2N_DIFFUSE_PROPAGATOR) against the FP64
 oracle's step-by-step Crank-Nicolson integration, through the C ABI.
 
+Rows H/2 + s and H - s take the propagator of rows s and H/2 - s with the
+angles reversed, so a class covers up to eight frequencies; plane heights
+2, 4, 6, 10 and 4m + 2 cover the slots where rows coincide (s = 0, H/4).
+
 The propagator is the same linear map as S steps, built in FP32 by binary
 powering in increment form, so it is held to the step kernel's tolerance:
 single calls over every supported N, S from 1 to 500 (powers of two and
@@ -40,7 +44,8 @@ def _run(vol, N, beta, T, S, flags):
     (16, 34, 22, 0.5, 1.0, 20), (32, 30, 26, 0.3, 2.0, 15), (64, 18, 14, 0.25, 2.0, 37),
     (32, 40, 40, 0.25, 2.0, 500), (32, 20, 24, 0.25, 2.0, 1), (32, 20, 24, 0.25, 2.0, 2),
     (16, 12, 64, 0.25, 2.0, 256), (64, 22, 30, 0.7, 3.0, 100),
-    (32, 18, 14, 10.0, 20.0, 20), (64, 18, 14, 10.0, 20.0, 20), (16, 2, 6, 0.5, 1.0, 9)])
+    (32, 18, 14, 10.0, 20.0, 20), (64, 18, 14, 10.0, 20.0, 20), (16, 2, 6, 0.5, 1.0, 9),
+    (16, 4, 8, 0.5, 2.0, 30), (32, 6, 10, 0.5, 2.0, 30), (16, 10, 4, 0.4, 2.0, 25)])
 def test_propagator_matches_oracle(N, H, W, beta, T, S):
     vol = synth.random_volume(N, H, W, seed=N + H + S).astype(np.complex64)
     ref = oracle.diffuse(vol.astype(np.complex128), beta, T, S)
@@ -118,7 +123,8 @@ def _gpu_inpaint(f32, mask, bins, prm, profile=False):
     return got, prof
 
 
-@pytest.mark.parametrize("H,W,N,full", [(96, 96, 32, 0), (64, 160, 32, 1), (64, 64, 16, 0), (48, 80, 64, 0)])
+@pytest.mark.parametrize("H,W,N,full", [(96, 96, 32, 0), (64, 160, 32, 1), (64, 64, 16, 0), (48, 80, 64, 0),
+                                         (66, 70, 16, 0), (70, 66, 32, 1)])
 def test_inpaint_with_propagators_matches_oracle(H, W, N, full):
     w = synth.workload_512(H=H, W=W, steps=60, rounds=3)
     p = oracle.Params(N=N, beta=0.25, T=6.0, steps=60, rounds=3)
