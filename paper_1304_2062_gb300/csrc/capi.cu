@@ -102,9 +102,9 @@ namespace {
 
 // Device memory for the plan's propagators (grown when too small, which
 // invalidates them).
-se2n_status prop_reserve(se2n_plan *plan, bool half) {
+se2n_status prop_reserve(se2n_plan *plan, bool half, bool rows = false) {
     const size_t need =
-        (size_t)se2n_prop_classes(plan->H, plan->W, half) * (size_t)se2n_prop_floats(plan->N) * sizeof(float);
+        (size_t)se2n_prop_classes(plan->H, plan->W, half) * (size_t)se2n_prop_floats(plan->N, rows) * sizeof(float);
     if (plan->prop_bytes >= need) return SE2N_OK;
     cudaFree(plan->prop_D);
     plan->prop_D = nullptr;
@@ -120,12 +120,10 @@ se2n_status prop_reserve(se2n_plan *plan, bool half) {
     return SE2N_OK;
 }
 
-// The S-step propagators of every class of equal-coefficient frequencies,
-// built when beta dt, S or the spectrum half changed, then applied once.
-se2n_status propagate_impl(se2n_plan *plan, float2 *vol, double beta, double bdt, int steps, bool half) {
-    if (!se2n_prop_supported(plan->N)) return SE2N_EUNSUPPORTED;
+PropArgs prop_args(se2n_plan *plan, float2 *vol, double beta, double bdt, int steps, bool half, bool rows) {
     PropArgs a;
     a.vol = vol;
+    a.rows = rows ? 1 : 0;
     a.H = plan->H;
     a.W = plan->W;
     a.Wc = half ? plan->Wc : plan->W;
@@ -137,23 +135,109 @@ se2n_status propagate_impl(se2n_plan *plan, float2 *vol, double beta, double bdt
     a.inv_c = (float)(2.0 / bdt);
     a.inv_beta = (float)(1.0 / beta);
     angle_table(plan->N, plan->angle_conv, a.cs, a.sn, SE2N_MAX_N);
-    SE2N_TRY(prop_reserve(plan, half));
     a.D = plan->prop_D;
-    if (!(plan->prop_valid && plan->prop_beta == beta && plan->prop_bdt == bdt && plan->prop_steps == steps &&
-          plan->prop_half == half)) {
-        plan->prop_valid = false;
-        StageTimer timer(plan, SE2N_STAGE_PROPAGATOR);
-        plan->kernels += 1;
-        SE2N_TRY(cuda_status(plan, se2n_launch_prop_build(plan->N, a, plan->num_sms, plan->stream)));
-        plan->prop_valid = true;
-        plan->prop_beta = beta;
-        plan->prop_bdt = bdt;
-        plan->prop_steps = steps;
-        plan->prop_half = half;
-    }
+    return a;
+}
+
+// The S-step propagators of every class of frequencies, built when beta dt,
+// S, the spectrum half or the storage changed.
+se2n_status prop_ensure(se2n_plan *plan, double beta, double bdt, int steps, bool half, bool rows) {
+    if (!se2n_prop_supported(plan->N)) return SE2N_EUNSUPPORTED;
+    SE2N_TRY(prop_reserve(plan, half, rows));
+    if (plan->prop_valid && plan->prop_beta == beta && plan->prop_bdt == bdt && plan->prop_steps == steps &&
+        plan->prop_half == half && plan->prop_rows == rows)
+        return SE2N_OK;
+    plan->prop_valid = false;
+    const PropArgs a = prop_args(plan, nullptr, beta, bdt, steps, half, rows);
+    StageTimer timer(plan, SE2N_STAGE_PROPAGATOR);
+    plan->kernels += 1;
+    SE2N_TRY(cuda_status(plan, se2n_launch_prop_build(plan->N, a, plan->num_sms, plan->stream)));
+    plan->prop_valid = true;
+    plan->prop_beta = beta;
+    plan->prop_bdt = bdt;
+    plan->prop_steps = steps;
+    plan->prop_half = half;
+    plan->prop_rows = rows;
+    return SE2N_OK;
+}
+
+// The propagators applied once to the spectrum vol (by diagonals).
+se2n_status propagate_impl(se2n_plan *plan, float2 *vol, double beta, double bdt, int steps, bool half) {
+    SE2N_TRY(prop_ensure(plan, beta, bdt, steps, half, false));
+    const PropArgs a = prop_args(plan, vol, beta, bdt, steps, half, false);
     StageTimer timer(plan, SE2N_STAGE_DIFFUSE);
     plan->kernels += 1;
     return cuda_status(plan, se2n_launch_prop_apply(plan->N, a, plan->num_sms, plan->stream));
+}
+
+// Column pass of the Hermitian half (colprop.cu): the row-transformed volume
+// [Wc][N][H] complex, its twiddle table and the row transforms into and out
+// of it (the real side is the in-place layout [N][H][W + 2]).
+bool col_path(const se2n_plan *plan, const se2n_params *p) {
+    return !p->full_spectrum && (p->diffuse_flags & SE2N_DIFFUSE_PROPAGATOR) &&
+           !(p->diffuse_flags & ~SE2N_DIFFUSE_PROPAGATOR) && se2n_col_supported(plan->N, plan->H);
+}
+
+se2n_status col_ensure(se2n_plan *plan) {
+    if (plan->col_ready) return SE2N_OK;
+    const int H = plan->H, W = plan->W, N = plan->N, Wc = plan->Wc;
+    const size_t col_bytes = (size_t)Wc * N * H * sizeof(float2);
+    if (!plan->colbuf) {
+        cudaError_t e = cudaMalloc(&plan->colbuf, col_bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&plan->col_tw, (size_t)H * sizeof(float2));
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            return e == cudaErrorMemoryAllocation ? SE2N_ENOMEM : SE2N_ECUDA;
+        }
+        std::vector<float2> tw(H);
+        for (int m = 0; m < H; ++m) {
+            // exp(-2 pi i m / H) from the exact fraction m / H
+            const double ang = -2.0 * M_PI * (double)m / (double)H;
+            tw[m] = make_float2((float)cos(ang), (float)sin(ang));
+        }
+        if (cudaMemcpy(plan->col_tw, tw.data(), (size_t)H * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess)
+            return SE2N_ECUDA;
+    }
+    // rows b = n H + k of the real volume (stride W + 2) <-> element l of row
+    // b at l N H + b
+    int n1[1] = {W}, real_embed[1] = {W + 2}, col_embed[1] = {Wc * N * H};
+    cufftResult r = CUFFT_SUCCESS;
+    if (!plan->fft_row_r2c)
+        r = cufftPlanMany(&plan->fft_row_r2c, 1, n1, real_embed, 1, W + 2, col_embed, N * H, 1, CUFFT_R2C, N * H);
+    if (r == CUFFT_SUCCESS && !plan->fft_row_c2r)
+        r = cufftPlanMany(&plan->fft_row_c2r, 1, n1, col_embed, N * H, 1, real_embed, 1, W + 2, CUFFT_C2R, N * H);
+    if (r == CUFFT_SUCCESS) r = cufftSetStream(plan->fft_row_r2c, plan->stream);
+    if (r == CUFFT_SUCCESS) r = cufftSetStream(plan->fft_row_c2r, plan->stream);
+    if (r != CUFFT_SUCCESS) return cufft_status(r);
+    if (cuda_status(plan, se2n_col_prepare(N, H)) != SE2N_OK) return SE2N_ECUDA;
+    plan->col_ready = true;
+    return SE2N_OK;
+}
+
+se2n_status col_rows(se2n_plan *plan, float2 *vol, bool forward) {
+    StageTimer timer(plan, SE2N_STAGE_FFT);
+    if (forward)
+        return cufft_status(cufftExecR2C(plan->fft_row_r2c, (cufftReal *)vol, (cufftComplex *)plan->colbuf));
+    return cufft_status(cufftExecC2R(plan->fft_row_c2r, (cufftComplex *)plan->colbuf, (cufftReal *)vol));
+}
+
+se2n_status col_diffuse(se2n_plan *plan, double beta, double T, int steps) {
+    if (!(beta > 0.0) || !(T >= 0.0) || steps < 1 || !isfinite(beta) || !isfinite(T)) return SE2N_EINVAL;
+    if (T == 0.0) return SE2N_OK;
+    const double bdt = beta * (T / steps);
+    if (!(bdt >= 1e-30 && bdt <= 1e3)) return SE2N_ENUMERIC;
+    SE2N_TRY(prop_ensure(plan, beta, bdt, steps, true, true));
+    ColArgs a;
+    a.col = plan->colbuf;
+    a.D = plan->prop_D;
+    a.tw = plan->col_tw;
+    a.H = plan->H;
+    a.W = plan->W;
+    a.Wc = plan->Wc;
+    a.col_slots = se2n_prop_col_slots(plan->W, true);
+    StageTimer timer(plan, SE2N_STAGE_DIFFUSE);
+    plan->kernels += 1;
+    return cuda_status(plan, se2n_launch_col_prop(plan->N, a, plan->stream));
 }
 
 // half: vol holds the Hermitian half [N][H][W/2 + 1] of the spectrum.
@@ -374,8 +458,10 @@ se2n_status check_params(const se2n_plan *plan, const se2n_params *p) {
     return SE2N_OK;
 }
 
+// allow_col = false keeps the separate transforms and propagator apply (the
+// path the batch graph takes, so that its per-image replay gives its bits).
 se2n_status inpaint_impl(se2n_plan *plan, const float *f, const uint8_t *mask, const uint8_t *bins_in,
-                         const se2n_params *p, float2 *vol, float *out) {
+                         const se2n_params *p, float2 *vol, float *out, bool allow_col = true) {
     const long long HW = plan->HW;
     const int N = plan->N;
     const uint8_t *bins = bins_in;
@@ -397,18 +483,30 @@ se2n_status inpaint_impl(se2n_plan *plan, const float *f, const uint8_t *mask, c
         // system of frequency (-k, -l) is that of (k, l) conjugated (a_r^2 is
         // even in the frequency): integrate the half l = 0 .. W/2 only, with
         // real-to-complex transforms, and let the inverse transform rebuild
-        // the rest.
-        SE2N_TRY(ensure_half(plan));
+        // the rest. With propagators on a supported shape, the transform
+        // along y and the propagators run fused in the column pass, between
+        // row transforms.
+        const bool col = allow_col && col_path(plan, p);
+        if (col)
+            SE2N_TRY(col_ensure(plan));
+        else
+            SE2N_TRY(ensure_half(plan));
+        auto to_spec = [&]() { return col ? col_rows(plan, vol, true) : fft_half(plan, vol, true); };
+        auto to_image = [&]() { return col ? col_rows(plan, vol, false) : fft_half(plan, vol, false); };
+        auto integrate = [&]() {
+            return col ? col_diffuse(plan, p->beta, Tr, p->steps)
+                       : diffuse_impl(plan, vol, p->beta, Tr, p->steps, p->diffuse_flags, true);
+        };
         SE2N_TRY(lift_half_impl(plan, f, mask, bins, vol));
-        SE2N_TRY(fft_half(plan, vol, true));
-        SE2N_TRY(diffuse_impl(plan, vol, p->beta, Tr, p->steps, p->diffuse_flags, true));
+        SE2N_TRY(to_spec());
+        SE2N_TRY(integrate());
         for (int i = 1; i < p->rounds; ++i) {
-            SE2N_TRY(fft_half(plan, vol, false));
+            SE2N_TRY(to_image());
             SE2N_TRY(restore_impl(plan, dr, vol, f, mask, bins, inv_hw, eps, guard, true));
-            SE2N_TRY(fft_half(plan, vol, true));
-            SE2N_TRY(diffuse_impl(plan, vol, p->beta, Tr, p->steps, p->diffuse_flags, true));
+            SE2N_TRY(to_spec());
+            SE2N_TRY(integrate());
         }
-        SE2N_TRY(fft_half(plan, vol, false));
+        SE2N_TRY(to_image());
         float scale = inv_hw;
         if (p->final_mix) {
             SE2N_TRY(restore_impl(plan, dr, vol, f, mask, bins, inv_hw, eps, guard, true));
@@ -442,6 +540,10 @@ void free_plan(se2n_plan *plan) {
     if (plan->fft_two) cufftDestroy(plan->fft_two);
     if (plan->fft_r2c) cufftDestroy(plan->fft_r2c);
     if (plan->fft_c2r) cufftDestroy(plan->fft_c2r);
+    if (plan->fft_row_r2c) cufftDestroy(plan->fft_row_r2c);
+    if (plan->fft_row_c2r) cufftDestroy(plan->fft_row_c2r);
+    cudaFree(plan->colbuf);
+    cudaFree(plan->col_tw);
     cudaFree(plan->spec);
     cudaFree(plan->gmax);
     cudaFree(plan->bins);
@@ -1248,7 +1350,7 @@ se2n_status se2n_batch_run_per_image(se2n_batch *b) {
         // the same integration the batch chose for this image's shape
         if (b->img_prop.empty() || !b->img_prop[i]) q.diffuse_flags &= ~SE2N_DIFFUSE_PROPAGATOR;
         SE2N_TRY(inpaint_impl(b->plan_of[i], b->imgs[i].f, b->imgs[i].mask, b->imgs[i].bins, &q, b->vols[i],
-                              b->imgs[i].out));
+                              b->imgs[i].out, false));
     }
     return SE2N_OK;
 }

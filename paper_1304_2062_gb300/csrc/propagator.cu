@@ -41,39 +41,9 @@
 // number. A' is cyclic tridiagonal: Thomas elimination of its torn part plus
 // one Sherman-Morrison correction.
 #include "diffuse_x2.cuh"
+#include "prop_classes.cuh"
 
 namespace se2n {
-
-// Rows k and (H/2 - k) mod H have bitwise the same coefficients:
-// sin_2pi_frac folds 2 pi k / H with integer arithmetic to the same argument
-// of sinpif for both (up to the sign of a zero, which the square removes).
-// The pairs are enumerated once each: k in [0, H/4] (partner H/2 - k) and
-// k in [H/2 + 1, 3H/4] (partner 3H/2 - k); k = H/4 and 3H/4 are their own
-// partners. H is even. Columns of the full spectrum are paired this way.
-__host__ __device__ __forceinline__ int pair_rows(int H) { return H / 4 + 1 + (3 * H) / 4 - H / 2; }
-__device__ __forceinline__ void pair_row(int s, int H, int &k, int &kb) {
-    const int lo = H / 4 + 1;
-    k = (s < lo) ? s : H / 2 + 1 + (s - lo);
-    kb = (k <= H / 2) ? H / 2 - k : 3 * H / 2 - k;
-}
-
-// Row slot s in [0, H/4] (H even): rows s and H/2 - s with wy = sin(2 pi s / H)
-// (the coefficients the propagator is built for) and rows H/2 + s and
-// (H - s) mod H with -wy (taken reversed). Each row of the plane is in
-// exactly one slot: s = 0 holds rows 0 and H/2 only, and s = H/4 rows H/4
-// and 3H/4 only.
-__host__ __device__ __forceinline__ int row_slots(int H) { return H / 4 + 1; }
-__device__ __forceinline__ void slot_rows(int s, int H, int (&k)[4], bool (&on)[4]) {
-    k[0] = s;
-    k[1] = H / 2 - s;
-    k[2] = H / 2 + s;
-    k[3] = (H - s) % H;
-    const bool quarter = 4 * s == H;
-    on[0] = true;
-    on[1] = !quarter;
-    on[2] = s != 0;
-    on[3] = s != 0 && !quarter;
-}
 
 namespace {
 
@@ -345,10 +315,30 @@ __global__ void __launch_bounds__(PropCfg<N>::WARPS * 32) k_prop_build(const __g
             prop_gemm<N>(P, Pr, P, 2.0f, nullptr, P, Pr, t);  // 2 P + P P
             __syncwarp();
         }
+        // D_S symmetrised, as rows in 16-byte chunks stored chunk-major
+        // (D[i][4c .. 4c + 3] at float4 c N + i): this lane writes rows i = t,
+        // t + LPC, ..., consecutive lanes consecutive chunks
+        if (live && a.rows) {
+            float4 *out = reinterpret_cast<float4 *>(a.D + u * (long long)(N * N));
+#pragma unroll 1
+            for (int cc = 0; cc < C::CPL; ++cc) {
+                const int i = t + cc * C::LPC;
+#pragma unroll 2
+                for (int c = 0; c < N / 4; ++c) {
+                    float d[4];
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        const int j = 4 * c + m;
+                        d[m] = 0.5f * (R[j * C::LD + i] + R[i * C::LD + j]);
+                    }
+                    out[c * N + i] = make_float4(d[0], d[1], d[2], d[3]);
+                }
+            }
+        }
         // D_S by cyclic diagonals: this lane writes S_m[i] for i = t, t + LPC, ...
         // (R is column-major: D[i, j] = R[j LD + i]; both reads run at stride
         // LD + 1 across the lanes, free of bank conflicts)
-        if (live) {
+        if (live && !a.rows) {
             float *out = a.D + u * (long long)C::SBLK;
 #pragma unroll 1
             for (int cc = 0; cc < C::CPL; ++cc) {
@@ -524,7 +514,7 @@ cudaError_t launch_apply(const PropArgs &a, int num_sms, cudaStream_t s) {
 
 bool se2n_prop_supported(int N) { return N == 16 || N == 32 || N == 64; }
 
-long long se2n_prop_floats(int N) { return (long long)(N / 2 + 1) * N; }
+long long se2n_prop_floats(int N, bool rows) { return rows ? (long long)N * N : (long long)(N / 2 + 1) * N; }
 
 int se2n_prop_col_slots(int W, bool half) { return half ? W / 4 + 1 : se2n::pair_rows(W); }
 

@@ -50,6 +50,13 @@ struct se2n_plan {
     double prop_beta, prop_bdt;
     int prop_steps;
     bool prop_half;
+    bool prop_rows;        // stored as full rows (the column pass) or by diagonals
+    // column pass of the Hermitian half (se2n_inpaint with propagators): the
+    // row-transformed volume [Wc][N][H] complex, row transforms to and from it
+    float2 *colbuf;
+    float2 *col_tw;        // exp(-2 pi i m / H), m < H
+    cufftHandle fft_row_r2c, fft_row_c2r;
+    bool col_ready;
     // diffusion launch configuration
     int diffuse_P;         // threads per frequency
     int diffuse_block;     // threads per block; 0 = the default shape for N
@@ -89,7 +96,10 @@ struct DiffuseArgs {
 // Parameters of the propagator kernels (propagator.cu): build D_S for every
 // class of frequencies with equal coefficients, or apply it to the volume.
 struct PropArgs {
-    float *D;          // [classes][N/2 + 1][N]: cyclic diagonals of D_S = (B-^{-1} B+)^S - I
+    float *D;          // D_S = (B-^{-1} B+)^S - I a class: [classes][N/2 + 1][N] cyclic
+                       // diagonals, or when rows != 0 [classes][N/4][N] float4:
+                       // row i's entries 4c .. 4c + 3 at float4 c N + i
+    int rows;          // storage of D (build only; the apply reads diagonals)
     float2 *vol;       // [N][H][Wc] complex (apply only)
     int H, W, Wc;
     long long HW;      // H * Wc
@@ -103,13 +113,26 @@ struct PropArgs {
     float sn[SE2N_MAX_N];
 };
 bool se2n_prop_supported(int N);
-long long se2n_prop_floats(int N);  // stored floats a class
+long long se2n_prop_floats(int N, bool rows = false);  // stored floats a class
 int se2n_prop_col_slots(int W, bool half);
 long long se2n_prop_classes(int H, int W, bool half);
 // Set the kernels' shared-memory attributes for N (before a graph capture).
 cudaError_t se2n_prop_prepare(int N);
 cudaError_t se2n_launch_prop_build(int N, const PropArgs &a, int num_sms, cudaStream_t s);
 cudaError_t se2n_launch_prop_apply(int N, const PropArgs &a, int num_sms, cudaStream_t s);
+
+// colprop.cu: the column pass of one interval on the row-transformed
+// Hermitian half [Wc][N][H] (forward DFT along k, x <- x + D_S x with D_S
+// stored as rows, inverse DFT along k), one block a column.
+struct ColArgs {
+    float2 *col;        // [Wc][N][H] complex, in place
+    const float *D;     // [classes][N/4][N] float4 (see PropArgs)
+    const float2 *tw;   // exp(-2 pi i m / H), m < H
+    int H, W, Wc, col_slots;
+};
+bool se2n_col_supported(int N, int H);
+cudaError_t se2n_col_prepare(int N, int H);
+cudaError_t se2n_launch_col_prop(int N, const ColArgs &a, cudaStream_t s);
 
 // Host helpers shared by the single-image and batched paths (capi.cu).
 StepParams step_params(double beta, double beta_dt, int steps);
