@@ -19,7 +19,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libse2n.so")
 
 SOURCES = ["capi.cu", "pixel.cu", "diffuse.cu", "diffuse_tab_a.cu", "diffuse_tab_b.cu", "diffuse_tab_c.cu",
-           "batch_kern.cu", "noalloc.cu", "nn.cu", "conv_tma.cu", "unet.cu", "propagator.cu", "colprop.cu"]
+           "batch_kern.cu", "noalloc.cu", "nn.cu", "conv_tma.cu", "unet.cu", "propagator.cu", "colprop.cu", "rowfft.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -170,55 +170,79 @@ se2n_status propagate_impl(se2n_plan *plan, float2 *vol, double beta, double bdt
     return cuda_status(plan, se2n_launch_prop_apply(plan->N, a, plan->num_sms, plan->stream));
 }
 
-// Column pass of the Hermitian half (colprop.cu): the row-transformed volume
-// [Wc][N][H] complex, its twiddle table and the row transforms into and out
-// of it (the real side is the in-place layout [N][H][W + 2]).
+// Row and column passes of the Hermitian half (rowfft.cu, colprop.cu): the
+// row-transformed volume [Wc][H][N] complex and the twiddle tables.
 bool col_path(const se2n_plan *plan, const se2n_params *p) {
-    return !p->full_spectrum && (p->diffuse_flags & SE2N_DIFFUSE_PROPAGATOR) &&
-           !(p->diffuse_flags & ~SE2N_DIFFUSE_PROPAGATOR) && se2n_col_supported(plan->N, plan->H);
+    return !p->full_spectrum && p->diffuse_flags == SE2N_DIFFUSE_PROPAGATOR &&
+           se2n_col_supported(plan->N, plan->H) && se2n_row_supported(plan->N, plan->W);
+}
+
+// exp(-2 pi i m / n), m < n, from the exact fraction m / n
+se2n_status upload_twiddles(float2 **dst, int n) {
+    cudaError_t e = cudaMalloc(dst, (size_t)n * sizeof(float2));
+    if (e != cudaSuccess) {
+        *dst = nullptr;
+        (void)cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? SE2N_ENOMEM : SE2N_ECUDA;
+    }
+    std::vector<float2> tw(n);
+    for (int m = 0; m < n; ++m) {
+        const double ang = -2.0 * M_PI * (double)m / (double)n;
+        tw[m] = make_float2((float)cos(ang), (float)sin(ang));
+    }
+    return cudaMemcpy(*dst, tw.data(), (size_t)n * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess
+               ? SE2N_OK
+               : SE2N_ECUDA;
 }
 
 se2n_status col_ensure(se2n_plan *plan) {
     if (plan->col_ready) return SE2N_OK;
-    const int H = plan->H, W = plan->W, N = plan->N, Wc = plan->Wc;
-    const size_t col_bytes = (size_t)Wc * N * H * sizeof(float2);
     if (!plan->colbuf) {
-        cudaError_t e = cudaMalloc(&plan->colbuf, col_bytes);
-        if (e == cudaSuccess) e = cudaMalloc(&plan->col_tw, (size_t)H * sizeof(float2));
+        cudaError_t e = cudaMalloc(&plan->colbuf, (size_t)plan->Wc * plan->N * plan->H * sizeof(float2));
         if (e != cudaSuccess) {
+            plan->colbuf = nullptr;
             (void)cudaGetLastError();
             return e == cudaErrorMemoryAllocation ? SE2N_ENOMEM : SE2N_ECUDA;
         }
-        std::vector<float2> tw(H);
-        for (int m = 0; m < H; ++m) {
-            // exp(-2 pi i m / H) from the exact fraction m / H
-            const double ang = -2.0 * M_PI * (double)m / (double)H;
-            tw[m] = make_float2((float)cos(ang), (float)sin(ang));
-        }
-        if (cudaMemcpy(plan->col_tw, tw.data(), (size_t)H * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess)
-            return SE2N_ECUDA;
     }
-    // rows b = n H + k of the real volume (stride W + 2) <-> element l of row
-    // b at l N H + b
-    int n1[1] = {W}, real_embed[1] = {W + 2}, col_embed[1] = {Wc * N * H};
-    cufftResult r = CUFFT_SUCCESS;
-    if (!plan->fft_row_r2c)
-        r = cufftPlanMany(&plan->fft_row_r2c, 1, n1, real_embed, 1, W + 2, col_embed, N * H, 1, CUFFT_R2C, N * H);
-    if (r == CUFFT_SUCCESS && !plan->fft_row_c2r)
-        r = cufftPlanMany(&plan->fft_row_c2r, 1, n1, col_embed, N * H, 1, real_embed, 1, W + 2, CUFFT_C2R, N * H);
-    if (r == CUFFT_SUCCESS) r = cufftSetStream(plan->fft_row_r2c, plan->stream);
-    if (r == CUFFT_SUCCESS) r = cufftSetStream(plan->fft_row_c2r, plan->stream);
-    if (r != CUFFT_SUCCESS) return cufft_status(r);
-    if (cuda_status(plan, se2n_col_prepare(N, H)) != SE2N_OK) return SE2N_ECUDA;
+    if (!plan->col_tw) SE2N_TRY(upload_twiddles(&plan->col_tw, plan->H));
+    if (!plan->row_tw) SE2N_TRY(upload_twiddles(&plan->row_tw, plan->W));
+    if (cuda_status(plan, se2n_col_prepare(plan->N, plan->H)) != SE2N_OK ||
+        cuda_status(plan, se2n_row_prepare(plan->N, plan->W)) != SE2N_OK)
+        return SE2N_ECUDA;
     plan->col_ready = true;
     return SE2N_OK;
 }
 
-se2n_status col_rows(se2n_plan *plan, float2 *vol, bool forward) {
+RowArgs row_args(se2n_plan *plan, const float *f, const uint8_t *mask, const uint8_t *bins, float scale, float eps,
+                 float guard) {
+    RowArgs r;
+    r.spec_in = plan->colbuf;
+    r.spec_out = plan->colbuf;
+    r.real_in = nullptr;
+    r.real_out = nullptr;
+    r.proj_out = nullptr;
+    r.f = f;
+    r.mask = mask;
+    r.bins = bins;
+    r.tw = plan->row_tw;
+    r.H = plan->H;
+    r.in_mode = SE2N_ROW_IN_SPEC;
+    r.out_mode = SE2N_ROW_OUT_SPEC;
+    r.mix = 0;
+    r.scale = scale;
+    r.eps = eps;
+    r.guard = guard;
+    r.proj = SE2N_PROJ_MAX;
+    r.reinject = 0;
+    r.scale_proj = 1.0f;
+    return r;
+}
+
+se2n_status row_pass(se2n_plan *plan, const RowArgs &r) {
     StageTimer timer(plan, SE2N_STAGE_FFT);
-    if (forward)
-        return cufft_status(cufftExecR2C(plan->fft_row_r2c, (cufftReal *)vol, (cufftComplex *)plan->colbuf));
-    return cufft_status(cufftExecC2R(plan->fft_row_c2r, (cufftComplex *)plan->colbuf, (cufftReal *)vol));
+    plan->kernels += 1;
+    return cuda_status(plan, se2n_launch_row(plan->N, plan->W, r, plan->stream));
 }
 
 se2n_status col_diffuse(se2n_plan *plan, double beta, double T, int steps) {
@@ -483,30 +507,59 @@ se2n_status inpaint_impl(se2n_plan *plan, const float *f, const uint8_t *mask, c
         // system of frequency (-k, -l) is that of (k, l) conjugated (a_r^2 is
         // even in the frequency): integrate the half l = 0 .. W/2 only, with
         // real-to-complex transforms, and let the inverse transform rebuild
-        // the rest. With propagators on a supported shape, the transform
-        // along y and the propagators run fused in the column pass, between
-        // row transforms.
-        const bool col = allow_col && col_path(plan, p);
-        if (col)
+        // the rest.
+        if (allow_col && col_path(plan, p)) {
+            // With propagators on a supported shape the volume stays
+            // row-transformed between intervals: a row pass (lift, or
+            // inverse DFT along x, restoration and forward DFT along x) and
+            // a column pass (DFT along y, propagators, inverse DFT along y)
+            // an interval, the projection fused into the last row pass.
+            // Dynamic restoration takes the real volume in vol between.
             SE2N_TRY(col_ensure(plan));
-        else
+            RowArgs r = row_args(plan, f, mask, bins, inv_hw, eps, guard);
+            r.in_mode = SE2N_ROW_IN_LIFT;
+            SE2N_TRY(row_pass(plan, r));
+            SE2N_TRY(col_diffuse(plan, p->beta, Tr, p->steps));
+            for (int i = 1; i <= p->rounds; ++i) {
+                const bool last = i == p->rounds;
+                r = row_args(plan, f, mask, bins, inv_hw, eps, guard);
+                if (dr) {
+                    r.out_mode = SE2N_ROW_OUT_REAL;
+                    r.real_out = (float *)vol;
+                    SE2N_TRY(row_pass(plan, r));
+                    if (last) break;
+                    SE2N_TRY(restore_impl(plan, dr, vol, f, mask, bins, inv_hw, eps, guard, true));
+                    r = row_args(plan, f, mask, bins, inv_hw, eps, guard);
+                    r.in_mode = SE2N_ROW_IN_REAL;
+                    r.real_in = (const float *)vol;
+                    SE2N_TRY(row_pass(plan, r));
+                } else if (last) {
+                    r.mix = p->final_mix;
+                    r.out_mode = SE2N_ROW_OUT_PROJ;
+                    r.proj_out = out;
+                    r.proj = p->proj;
+                    r.reinject = p->reinject;
+                    r.scale_proj = p->final_mix ? 1.0f : inv_hw;
+                    return row_pass(plan, r);
+                } else {
+                    r.mix = 1;
+                    SE2N_TRY(row_pass(plan, r));
+                }
+                SE2N_TRY(col_diffuse(plan, p->beta, Tr, p->steps));
+            }
+        } else {
             SE2N_TRY(ensure_half(plan));
-        auto to_spec = [&]() { return col ? col_rows(plan, vol, true) : fft_half(plan, vol, true); };
-        auto to_image = [&]() { return col ? col_rows(plan, vol, false) : fft_half(plan, vol, false); };
-        auto integrate = [&]() {
-            return col ? col_diffuse(plan, p->beta, Tr, p->steps)
-                       : diffuse_impl(plan, vol, p->beta, Tr, p->steps, p->diffuse_flags, true);
-        };
-        SE2N_TRY(lift_half_impl(plan, f, mask, bins, vol));
-        SE2N_TRY(to_spec());
-        SE2N_TRY(integrate());
-        for (int i = 1; i < p->rounds; ++i) {
-            SE2N_TRY(to_image());
-            SE2N_TRY(restore_impl(plan, dr, vol, f, mask, bins, inv_hw, eps, guard, true));
-            SE2N_TRY(to_spec());
-            SE2N_TRY(integrate());
+            SE2N_TRY(lift_half_impl(plan, f, mask, bins, vol));
+            SE2N_TRY(fft_half(plan, vol, true));
+            SE2N_TRY(diffuse_impl(plan, vol, p->beta, Tr, p->steps, p->diffuse_flags, true));
+            for (int i = 1; i < p->rounds; ++i) {
+                SE2N_TRY(fft_half(plan, vol, false));
+                SE2N_TRY(restore_impl(plan, dr, vol, f, mask, bins, inv_hw, eps, guard, true));
+                SE2N_TRY(fft_half(plan, vol, true));
+                SE2N_TRY(diffuse_impl(plan, vol, p->beta, Tr, p->steps, p->diffuse_flags, true));
+            }
+            SE2N_TRY(fft_half(plan, vol, false));
         }
-        SE2N_TRY(to_image());
         float scale = inv_hw;
         if (p->final_mix) {
             SE2N_TRY(restore_impl(plan, dr, vol, f, mask, bins, inv_hw, eps, guard, true));
@@ -540,10 +593,9 @@ void free_plan(se2n_plan *plan) {
     if (plan->fft_two) cufftDestroy(plan->fft_two);
     if (plan->fft_r2c) cufftDestroy(plan->fft_r2c);
     if (plan->fft_c2r) cufftDestroy(plan->fft_c2r);
-    if (plan->fft_row_r2c) cufftDestroy(plan->fft_row_r2c);
-    if (plan->fft_row_c2r) cufftDestroy(plan->fft_row_c2r);
     cudaFree(plan->colbuf);
     cudaFree(plan->col_tw);
+    cudaFree(plan->row_tw);
     cudaFree(plan->spec);
     cudaFree(plan->gmax);
     cudaFree(plan->bins);

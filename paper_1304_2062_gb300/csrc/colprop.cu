@@ -1,172 +1,28 @@
 // The column pass of one restoration interval on the Hermitian half of the
-// spectrum, fused. The volume between intervals is row-transformed: the DFT
-// along x (l) of every row, stored as complex [Wc][N][H] so that column l's
-// N x H block is contiguous (cuFFT writes and reads that layout). One block
-// a column l:
-//   1. takes the DFT along y (k) of every angle plane (unnormalised), which
-//      completes the two-dimensional DFT of the lifted volume;
+// spectrum, fused. Between intervals the volume is row-transformed: the DFT
+// along x (index l) of every row of every angle plane, stored as complex
+// [Wc][H][N] (rowfft.cu writes and reads it), so column l's H x N block is
+// contiguous and a frequency's N angles are adjacent. One block a column l:
+//   1. takes the DFT along y (index k) of every angle plane (unnormalised),
+//      which completes the two-dimensional DFT of the lifted volume;
 //   2. applies x <- x + D_S x to the N-vector of every frequency (k, l),
 //      D_S the S-step propagator of its class, stored by 16-byte chunks of
-//      its rows, chunk-major (eq. (deceq), Theorem 2,
-//      integrated by S Crank-Nicolson steps; see propagator.cu), with the
-//      angles reversed for rows H/2 + s and H - s;
+//      its rows, chunk-major (eq. (deceq), Theorem 2, integrated by S
+//      Crank-Nicolson steps; see propagator.cu), with the angles reversed
+//      for rows H/2 + s and H - s;
 //   3. takes the inverse DFT along k,
-// all in shared memory, so the spectrum of the interval never goes through
-// device memory.
-//
-// DFTs along k: mixed-radix Stockham (self-sorting) passes, radix 8 and then
-// one pass of radix 2 or 4 where H is not a power of 8, with the twiddles
-// exp(-/+ 2 pi i m / H) from a table. The first forward pass reads device
-// memory and the last inverse pass writes it; the others run in place in
-// shared memory (every read of a pass before its first write). The block
-// [N][H] is kept with planes H + 1 complex apart (so that the lanes of the
-// apply, one angle each, fall on different banks) and, inside a plane, each
-// run of 16 complex permuted by an XOR of its low bits with a function of the
-// run index: with it the three access patterns of the passes (consecutive,
-// stride 8, and runs of 8 that are 64 apart) take no bank conflicts.
+// in shared memory (smem_fft.cuh), so the spectrum of the interval never
+// goes through device memory.
 #include "diffuse_x2.cuh"
 #include "prop_classes.cuh"
 #include "se2n_internal.h"
+#include "smem_fft.cuh"
 
 namespace se2n {
 
 namespace {
 
 constexpr int kColThreads = 512;
-
-// shared-memory index of element e = n L + i of the block
-template <int L>
-__device__ __forceinline__ int xsm(int e) {
-    const int n = e / L, i = e & (L - 1), m = i >> 4;
-    return n * (L + 1) + (i ^ ((m & 7) | ((m << 1) & 8)));
-}
-
-// a * w (forward) or a * conj(w) (inverse)
-template <int DIR>
-__device__ __forceinline__ float2 twiddle(float2 a, float2 w) {
-    const float wy = DIR < 0 ? w.y : -w.y;
-    return make_float2(fmaf(a.x, w.x, -a.y * wy), fmaf(a.x, wy, a.y * w.x));
-}
-
-// z times exp(DIR i pi / 2): -i z forward, i z inverse
-template <int DIR>
-__device__ __forceinline__ float2 quarter(float2 z) {
-    return DIR < 0 ? make_float2(z.y, -z.x) : make_float2(-z.y, z.x);
-}
-
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-
-// V_k = sum_n v_n exp(DIR 2 pi i n k / R), in place, for R = 2, 4, 8.
-template <int R, int DIR>
-__device__ __forceinline__ void dft_small(float2 (&v)[R]) {
-    if constexpr (R == 2) {
-        const float2 a = v[0], b = v[1];
-        v[0] = cadd(a, b);
-        v[1] = csub(a, b);
-    } else if constexpr (R == 4) {
-        const float2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
-        const float2 t2 = cadd(v[1], v[3]), t3 = quarter<DIR>(csub(v[1], v[3]));
-        v[0] = cadd(t0, t2);
-        v[2] = csub(t0, t2);
-        v[1] = cadd(t1, t3);
-        v[3] = csub(t1, t3);
-    } else {
-        // even and odd halves, then V_k = E_k + w^k O_k, V_{k+4} = E_k - w^k O_k
-        float2 e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
-        dft_small<4, DIR>(e);
-        dft_small<4, DIR>(o);
-        constexpr float h = 0.70710678118654752f;  // cos(pi / 4)
-        // w = exp(DIR i pi / 4) = (1 + DIR i) / sqrt(2)
-        const float2 o1 = DIR < 0 ? make_float2(h * (o[1].x + o[1].y), h * (o[1].y - o[1].x))
-                                  : make_float2(h * (o[1].x - o[1].y), h * (o[1].y + o[1].x));
-        const float2 o2 = quarter<DIR>(o[2]);
-        const float2 o3 = quarter<DIR>(DIR < 0 ? make_float2(h * (o[3].x + o[3].y), h * (o[3].y - o[3].x))
-                                               : make_float2(h * (o[3].x - o[3].y), h * (o[3].y + o[3].x)));
-        v[0] = cadd(e[0], o[0]);
-        v[4] = csub(e[0], o[0]);
-        v[1] = cadd(e[1], o1);
-        v[5] = csub(e[1], o1);
-        v[2] = cadd(e[2], o2);
-        v[6] = csub(e[2], o2);
-        v[3] = cadd(e[3], o3);
-        v[7] = csub(e[3], o3);
-    }
-}
-
-// One Stockham pass of radix R over the N transforms of length L, whose
-// sub-transforms of length NS are done: butterfly j of a transform reads
-// elements j + r L / R, twiddles them by exp(DIR 2 pi i r (j mod NS) / (NS R)),
-// and writes its outputs to (j / NS) NS R + (j mod NS) + r NS.
-// SRC / DST: device memory (block of column l) instead of shared memory.
-template <int N, int L, int R, int NS, int DIR, bool SRC, bool DST>
-__device__ __forceinline__ void col_pass(const float2 *gin, float2 *gout, float2 *X, const float2 *tw, int tid) {
-    constexpr int M = L / R;  // butterflies a transform
-    constexpr int NB = N * M;
-    constexpr int BPT = (NB + kColThreads - 1) / kColThreads;
-    static_assert(kColThreads % M == 0, "j depends on the thread only");
-    // butterfly b = tid + q kColThreads: transform b / M, index j = tid mod M
-    // for every q, so the twiddles are read once
-    const int j = tid % M, k = j & (NS - 1);
-    float2 v[BPT][R];
-#pragma unroll
-    for (int q = 0; q < BPT; ++q) {
-        const int b = tid + q * kColThreads;
-        if (NB % kColThreads == 0 || b < NB) {
-            const int n = b / M;
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int e = n * L + j + r * M;
-                v[q][r] = SRC ? gin[e] : X[xsm<L>(e)];
-            }
-        }
-    }
-    float2 w[R];
-    if constexpr (NS > 1) {
-#pragma unroll
-        for (int r = 1; r < R; ++r) w[r] = tw[r * k * (L / (NS * R))];
-    }
-    if constexpr (!SRC && !DST) __syncthreads();  // in place
-#pragma unroll
-    for (int q = 0; q < BPT; ++q) {
-        const int b = tid + q * kColThreads;
-        if (NB % kColThreads == 0 || b < NB) {
-            const int n = b / M;
-            if constexpr (NS > 1) {
-#pragma unroll
-                for (int r = 1; r < R; ++r) v[q][r] = twiddle<DIR>(v[q][r], w[r]);
-            }
-            dft_small<R, DIR>(v[q]);
-            const int base = n * L + (j - k) * R + k;
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int e = base + r * NS;
-                if constexpr (DST)
-                    gout[e] = v[q][r];
-                else
-                    X[xsm<L>(e)] = v[q][r];
-            }
-        }
-    }
-}
-
-// The DFT along k of the N planes of the block (L = 64, 128, 256 or 512:
-// radix 8 x 8, 8 x 8 x 2, 8 x 8 x 4, 8 x 8 x 8). Ends with the block in
-// shared memory (LAST = false) or in device memory.
-template <int N, int L, int DIR, bool FIRST, bool LAST>
-__device__ __forceinline__ void col_dft(const float2 *gin, float2 *gout, float2 *X, const float2 *tw, int tid) {
-    static_assert(L == 64 || L == 128 || L == 256 || L == 512, "column length");
-    col_pass<N, L, 8, 1, DIR, FIRST, false>(gin, nullptr, X, tw, tid);
-    __syncthreads();
-    if constexpr (L == 64) {
-        col_pass<N, L, 8, 8, DIR, false, LAST>(nullptr, gout, X, tw, tid);
-    } else {
-        col_pass<N, L, 8, 8, DIR, false, false>(nullptr, nullptr, X, tw, tid);
-        __syncthreads();
-        constexpr int R = L == 128 ? 2 : (L == 256 ? 4 : 8);
-        col_pass<N, L, R, 64, DIR, false, LAST>(nullptr, gout, X, tw, tid);
-    }
-}
 
 // x <- x + D_S x for every frequency (k, l) of the column: one class (row
 // slot s, this column's slot) per N/2 lanes, two rows of D_S a lane, held in
@@ -243,7 +99,7 @@ __device__ __forceinline__ void col_apply(float2 *X, const float *D, int scol, i
 
 template <int N, int L>
 struct ColCfg {
-    static constexpr int XF = N * (L + 1);  // block with padded planes, complex
+    static constexpr int XF = SmemBlock<N, L>::COMPLEX;
     static constexpr int SMEM = (XF + L) * 8;
 };
 
@@ -259,12 +115,19 @@ __global__ void __launch_bounds__(kColThreads, 1) k_col_prop(const __grid_consta
     const int l = (b & 1) ? a.W / 2 - h : h;
     float2 *g = a.col + (long long)l * (N * L);
     for (int m = tid; m < L; m += kColThreads) tws[m] = a.tw[m];
+    // the column block [k][n] into transforms [n][k]: consecutive threads read
+    // consecutive angles of a frequency
+#pragma unroll 4
+    for (int e = tid; e < N * L; e += kColThreads) X[xsm<L>((e % N) * L + e / N)] = g[e];
     __syncthreads();
-    col_dft<N, L, -1, true, false>(g, nullptr, X, tws, tid);
+    fft_smem<kColThreads, N, L, -1, 1>(X, tws, tid);
     __syncthreads();
     col_apply<N, L>(X, a.D, half_col_slot(l, a.W), a.col_slots, tid);
     __syncthreads();
-    col_dft<N, L, 1, false, true>(nullptr, g, X, tws, tid);
+    fft_smem<kColThreads, N, L, 1, 1>(X, tws, tid);
+    __syncthreads();
+#pragma unroll 4
+    for (int e = tid; e < N * L; e += kColThreads) g[e] = X[xsm<L>((e % N) * L + e / N)];
 }
 
 template <int N, int L>

@@ -4,6 +4,7 @@
 // plane is a coalesced 16-byte (two complex) or 8-byte (two float) access.
 // H and W are even, so a pixel pair never straddles a plane and every plane
 // starts 16-byte aligned.
+#include "restore.cuh"
 #include "se2n_internal.h"
 
 namespace {
@@ -116,18 +117,7 @@ __global__ void k_lift(const float2 *__restrict__ f, const uchar2 *__restrict__ 
     }
 }
 
-// Static restoration. h(t) = max_r scale*Re vol, h(0) = max_r of the lift;
-// sigma = (eps h(0) + (1-eps) h(t)) / h(t) where h(t) > guard h(0) and
-// h(t) > 0, else the linear blend eps * lift + (1-eps) * psi.
-__device__ __forceinline__ float sr_value(float re, float h0, float ht, float lift_r, bool good, float eps,
-                                          float guard) {
-    if (!good) return re;
-    if (ht > guard * h0 && ht > 0.0f) {
-        const float sig = (eps * h0 + (1.0f - eps) * ht) / ht;
-        return re * sig;
-    }
-    return eps * lift_r + (1.0f - eps) * re;
-}
+using se2n::sr_value;
 
 __global__ void k_mix(float4 *__restrict__ vol, const float2 *__restrict__ f, const uchar2 *__restrict__ mask,
                       const uchar2 *__restrict__ bins, long long npairs, int N, float scale, float eps,

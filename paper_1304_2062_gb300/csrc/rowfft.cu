@@ -1,0 +1,211 @@
+// The row pass of the Hermitian-half path with propagators: one block a row
+// y, all N angles of it in shared memory. Between column passes (colprop.cu)
+// the volume is row-transformed, complex [Wc][H][N] (Wc = W/2 + 1); a row
+// pass
+//   1. reads the row: from the lift (f on the pixel's bin, all bins if
+//      flat), from the real volume, or from the row-transformed volume by
+//      the inverse real DFT along x;
+//   2. optionally applies the static restoration to every pixel (the rule of
+//      restore.cuh, with h(t) the maximum over the angles);
+//   3. writes the forward real DFT along x back to the row-transformed
+//      volume, or the real row, or the projection over the angles (max or
+//      mean, with the known pixels reinjected on request).
+// So the restoration between two intervals (Section 5.2) costs one read and
+// one write of the half spectrum, and the lift and the projection none.
+//
+// Real DFTs of length W by complex DFTs of length W/2 (smem_fft.cuh) on
+// z_m = x_2m + i x_2m+1. Forward: E_l = (Z_l + conj Z_{W/2-l}) / 2 and
+// O_l = -i (Z_l - conj Z_{W/2-l}) / 2 are the DFTs of the even and odd
+// samples, and X_l = E_l + w^l O_l, X_{W/2-l} = conj(E_l - w^l O_l) with
+// w = exp(-2 pi i / W). Inverse (unnormalised, as cuFFT's C2R, with the
+// imaginary parts of X_0 and X_{W/2} ignored): Z_l = P + i Q and
+// Z_{W/2-l} = conj P + i conj Q with P = X_l + conj X_{W/2-l} and
+// Q = conj(w^l) (X_l - conj X_{W/2-l}), then z = inverse DFT of Z.
+#include "restore.cuh"
+#include "se2n_internal.h"
+#include "smem_fft.cuh"
+
+namespace se2n {
+
+namespace {
+
+constexpr int kRowThreads = 256;
+
+template <int N, int W>
+struct RowCfg {
+    static constexpr int WH = W / 2;
+    static constexpr int XF = SmemBlock<N, WH>::COMPLEX;
+    static constexpr int SMEM = (XF + W) * 8;
+};
+
+template <int N, int W>
+__global__ void __launch_bounds__(kRowThreads) k_row(const __grid_constant__ RowArgs a) {
+    constexpr int WH = W / 2, T = kRowThreads;
+    extern __shared__ __align__(16) float2 rsm[];
+    float2 *Z = rsm;                       // [N][W/2]: z_m of every angle
+    float2 *tws = rsm + RowCfg<N, W>::XF;  // exp(-2 pi i m / W)
+    const int tid = threadIdx.x, y = blockIdx.x;
+    const long long H = a.H;
+    const long long row = (long long)y * W;  // first pixel of the row
+    for (int m = tid; m < W; m += T) tws[m] = a.tw[m];
+    // 1. the row
+    if (a.in_mode == SE2N_ROW_IN_LIFT) {
+        for (int m = tid; m < WH; m += T) {
+            const float2 fv = reinterpret_cast<const float2 *>(a.f + row)[m];
+            const uchar2 mk = reinterpret_cast<const uchar2 *>(a.mask + row)[m];
+            const uchar2 bn = reinterpret_cast<const uchar2 *>(a.bins + row)[m];
+            const float a0 = mk.x ? fv.x : 0.0f, a1 = mk.y ? fv.y : 0.0f;
+#pragma unroll 4
+            for (int n = 0; n < N; ++n) {
+                const bool on0 = (bn.x == n) || (bn.x == SE2N_BIN_FLAT);
+                const bool on1 = (bn.y == n) || (bn.y == SE2N_BIN_FLAT);
+                Z[xsm<WH>(n * WH + m)] = make_float2(on0 ? a0 : 0.0f, on1 ? a1 : 0.0f);
+            }
+        }
+    } else if (a.in_mode == SE2N_ROW_IN_REAL) {
+        for (int e = tid; e < N * WH; e += T) {
+            const int n = e / WH, m = e - n * WH;
+            Z[xsm<WH>(e)] = reinterpret_cast<const float2 *>(a.real_in + (n * H + y) * (W + 2))[m];
+        }
+    } else {
+        __syncthreads();  // twiddles
+        // pairs (l, W/2 - l), l = 0 .. W/4; consecutive threads take
+        // consecutive angles of one frequency
+        for (int e = tid; e < N * (WH / 2 + 1); e += T) {
+            const int l = e / N, n = e - l * N;
+            float2 xl = a.spec_in[((long long)l * H + y) * N + n];
+            float2 xb = a.spec_in[((long long)(WH - l) * H + y) * N + n];
+            if (l == 0) {
+                xl.y = 0.0f;
+                xb.y = 0.0f;
+            }
+            const float2 P = cadd(xl, cconj(xb));
+            const float2 Q = twiddle<1>(csub(xl, cconj(xb)), tws[l]);
+            Z[xsm<WH>(n * WH + l)] = make_float2(P.x - Q.y, P.y + Q.x);
+            if (l != 0 && 2 * l != WH) Z[xsm<WH>(n * WH + WH - l)] = make_float2(P.x + Q.y, Q.x - P.y);
+        }
+        __syncthreads();
+        fft_smem<T, N, WH, 1, 2>(Z, tws, tid);
+    }
+    __syncthreads();
+    // 2. the restoration, one pixel pair (2m, 2m + 1) a thread
+    if (a.mix) {
+        for (int m = tid; m < WH; m += T) {
+            float ht0 = -INFINITY, ht1 = -INFINITY;
+#pragma unroll 4
+            for (int n = 0; n < N; ++n) {
+                const float2 v = Z[xsm<WH>(n * WH + m)];
+                ht0 = fmaxf(ht0, v.x * a.scale);
+                ht1 = fmaxf(ht1, v.y * a.scale);
+            }
+            const float2 fv = reinterpret_cast<const float2 *>(a.f + row)[m];
+            const uchar2 mk = reinterpret_cast<const uchar2 *>(a.mask + row)[m];
+            const uchar2 bn = reinterpret_cast<const uchar2 *>(a.bins + row)[m];
+            const float a0 = mk.x ? fv.x : 0.0f, a1 = mk.y ? fv.y : 0.0f;
+            const float h00 = (bn.x == SE2N_BIN_FLAT) ? a0 : fmaxf(a0, 0.0f);
+            const float h01 = (bn.y == SE2N_BIN_FLAT) ? a1 : fmaxf(a1, 0.0f);
+#pragma unroll 4
+            for (int n = 0; n < N; ++n) {
+                float2 &v = Z[xsm<WH>(n * WH + m)];
+                const float l0 = ((bn.x == n) || (bn.x == SE2N_BIN_FLAT)) ? a0 : 0.0f;
+                const float l1 = ((bn.y == n) || (bn.y == SE2N_BIN_FLAT)) ? a1 : 0.0f;
+                v = make_float2(sr_value(v.x * a.scale, h00, ht0, l0, mk.x != 0, a.eps, a.guard),
+                                sr_value(v.y * a.scale, h01, ht1, l1, mk.y != 0, a.eps, a.guard));
+            }
+        }
+        __syncthreads();
+    }
+    // 3. the output
+    if (a.out_mode == SE2N_ROW_OUT_REAL) {
+        for (int e = tid; e < N * WH; e += T) {
+            const int n = e / WH, m = e - n * WH;
+            reinterpret_cast<float2 *>(a.real_out + (n * H + y) * (W + 2))[m] = Z[xsm<WH>(e)];
+        }
+    } else if (a.out_mode == SE2N_ROW_OUT_PROJ) {
+        for (int m = tid; m < WH; m += T) {
+            float a0, a1;
+            if (a.proj == SE2N_PROJ_MAX) {
+                a0 = -INFINITY;
+                a1 = -INFINITY;
+#pragma unroll 4
+                for (int n = 0; n < N; ++n) {
+                    const float2 v = Z[xsm<WH>(n * WH + m)];
+                    a0 = fmaxf(a0, v.x * a.scale_proj);
+                    a1 = fmaxf(a1, v.y * a.scale_proj);
+                }
+            } else {
+                a0 = 0.0f;
+                a1 = 0.0f;
+#pragma unroll 4
+                for (int n = 0; n < N; ++n) {
+                    const float2 v = Z[xsm<WH>(n * WH + m)];
+                    a0 += v.x * a.scale_proj;
+                    a1 += v.y * a.scale_proj;
+                }
+                a0 /= (float)N;
+                a1 /= (float)N;
+            }
+            if (a.reinject) {
+                const float2 fv = reinterpret_cast<const float2 *>(a.f + row)[m];
+                const uchar2 mk = reinterpret_cast<const uchar2 *>(a.mask + row)[m];
+                if (mk.x) a0 = fv.x;
+                if (mk.y) a1 = fv.y;
+            }
+            reinterpret_cast<float2 *>(a.proj_out + row)[m] = make_float2(a0, a1);
+        }
+    } else {
+        fft_smem<T, N, WH, -1, 2>(Z, tws, tid);
+        __syncthreads();
+        for (int e = tid; e < N * (WH / 2 + 1); e += T) {
+            const int l = e / N, n = e - l * N;
+            const float2 zl = Z[xsm<WH>(n * WH + l)];
+            const float2 zc = cconj(Z[xsm<WH>(n * WH + ((WH - l) & (WH - 1)))]);
+            const float2 s = cadd(zl, zc), d = csub(zl, zc);
+            const float2 E = make_float2(0.5f * s.x, 0.5f * s.y);
+            const float2 O = make_float2(0.5f * d.y, -0.5f * d.x);  // -i d / 2
+            const float2 B = twiddle<-1>(O, tws[l]);
+            a.spec_out[((long long)l * H + y) * N + n] = cadd(E, B);
+            if (2 * l != WH) a.spec_out[((long long)(WH - l) * H + y) * N + n] = cconj(csub(E, B));
+        }
+    }
+}
+
+template <int N, int W>
+cudaError_t row_attr() {
+    return cudaFuncSetAttribute(k_row<N, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowCfg<N, W>::SMEM);
+}
+
+template <int N, int W>
+cudaError_t row_launch(const RowArgs &a, cudaStream_t s) {
+    cudaError_t e = row_attr<N, W>();
+    if (e != cudaSuccess) return e;
+    k_row<N, W><<<a.H, kRowThreads, RowCfg<N, W>::SMEM, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t row_dispatch(int W, const RowArgs *a, cudaStream_t s) {
+    switch (W) {
+        case 64: return a ? row_launch<N, 64>(*a, s) : row_attr<N, 64>();
+        case 128: return a ? row_launch<N, 128>(*a, s) : row_attr<N, 128>();
+        case 256: return a ? row_launch<N, 256>(*a, s) : row_attr<N, 256>();
+        case 512: return a ? row_launch<N, 512>(*a, s) : row_attr<N, 512>();
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+}  // namespace se2n
+
+bool se2n_row_supported(int N, int W) { return (N == 16 || N == 32) && (W == 64 || W == 128 || W == 256 || W == 512); }
+
+cudaError_t se2n_row_prepare(int N, int W) {
+    if (!se2n_row_supported(N, W)) return cudaErrorInvalidValue;
+    return N == 16 ? se2n::row_dispatch<16>(W, nullptr, nullptr) : se2n::row_dispatch<32>(W, nullptr, nullptr);
+}
+
+cudaError_t se2n_launch_row(int N, int W, const RowArgs &a, cudaStream_t s) {
+    if (!se2n_row_supported(N, W)) return cudaErrorInvalidValue;
+    return N == 16 ? se2n::row_dispatch<16>(W, &a, s) : se2n::row_dispatch<32>(W, &a, s);
+}

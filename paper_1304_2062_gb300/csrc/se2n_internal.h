@@ -51,11 +51,11 @@ struct se2n_plan {
     int prop_steps;
     bool prop_half;
     bool prop_rows;        // stored as full rows (the column pass) or by diagonals
-    // column pass of the Hermitian half (se2n_inpaint with propagators): the
-    // row-transformed volume [Wc][N][H] complex, row transforms to and from it
+    // row and column passes of the Hermitian half (se2n_inpaint with
+    // propagators): the row-transformed volume [Wc][H][N] complex
     float2 *colbuf;
     float2 *col_tw;        // exp(-2 pi i m / H), m < H
-    cufftHandle fft_row_r2c, fft_row_c2r;
+    float2 *row_tw;        // exp(-2 pi i m / W), m < W
     bool col_ready;
     // diffusion launch configuration
     int diffuse_P;         // threads per frequency
@@ -122,10 +122,10 @@ cudaError_t se2n_launch_prop_build(int N, const PropArgs &a, int num_sms, cudaSt
 cudaError_t se2n_launch_prop_apply(int N, const PropArgs &a, int num_sms, cudaStream_t s);
 
 // colprop.cu: the column pass of one interval on the row-transformed
-// Hermitian half [Wc][N][H] (forward DFT along k, x <- x + D_S x with D_S
+// Hermitian half [Wc][H][N] (forward DFT along k, x <- x + D_S x with D_S
 // stored as rows, inverse DFT along k), one block a column.
 struct ColArgs {
-    float2 *col;        // [Wc][N][H] complex, in place
+    float2 *col;        // [Wc][H][N] complex, in place
     const float *D;     // [classes][N/4][N] float4 (see PropArgs)
     const float2 *tw;   // exp(-2 pi i m / H), m < H
     int H, W, Wc, col_slots;
@@ -133,6 +133,32 @@ struct ColArgs {
 bool se2n_col_supported(int N, int H);
 cudaError_t se2n_col_prepare(int N, int H);
 cudaError_t se2n_launch_col_prop(int N, const ColArgs &a, cudaStream_t s);
+
+// rowfft.cu: the row pass between column passes, one block a row y with all
+// its angles: the row-transformed volume [Wc][H][N] is taken back to the
+// image (inverse real DFT along x), restored, and transformed again, or the
+// row comes from the lift, or goes to the projection or to the real volume.
+enum { SE2N_ROW_IN_LIFT = 0, SE2N_ROW_IN_SPEC = 1, SE2N_ROW_IN_REAL = 2 };
+enum { SE2N_ROW_OUT_SPEC = 0, SE2N_ROW_OUT_REAL = 1, SE2N_ROW_OUT_PROJ = 2 };
+struct RowArgs {
+    const float2 *spec_in;  // [Wc][H][N] complex (IN_SPEC)
+    float2 *spec_out;       // [Wc][H][N] complex (OUT_SPEC); may be spec_in
+    const float *real_in;   // [N][H][W + 2] (IN_REAL)
+    float *real_out;        // [N][H][W + 2] (OUT_REAL), unnormalised
+    float *proj_out;        // [H][W] (OUT_PROJ)
+    const float *f;         // [H][W] image (lift, restoration, reinjection)
+    const uint8_t *mask;    // [H][W] known pixels
+    const uint8_t *bins;    // [H][W] orientation bins
+    const float2 *tw;       // exp(-2 pi i m / W), m < W
+    int H, in_mode, out_mode;
+    int mix;                // restore after the inverse DFT (IN_SPEC)
+    float scale, eps, guard;
+    int proj, reinject;     // OUT_PROJ: max or mean over the angles of scale_proj * value
+    float scale_proj;
+};
+bool se2n_row_supported(int N, int W);
+cudaError_t se2n_row_prepare(int N, int W);
+cudaError_t se2n_launch_row(int N, int W, const RowArgs &a, cudaStream_t s);
 
 // Host helpers shared by the single-image and batched paths (capi.cu).
 StepParams step_params(double beta, double beta_dt, int steps);

@@ -1,0 +1,150 @@
+// Batched complex DFTs in shared memory, the building block of the row and
+// column passes (rowfft.cu, colprop.cu): N transforms of length L (a power
+// of two, 32 .. 512) held as a block [N][L], transformed in place by
+// mixed-radix Stockham (self-sorting) passes, radix 8 and then one pass of
+// radix 2 or 4 where L is not a power of 8:
+//   pass with radix R over sub-transforms of length NS already done:
+//   butterfly j reads elements j + r L / R (r < R), multiplies them by
+//   exp(DIR 2 pi i r (j mod NS) / (NS R)), takes the R-point DFT, and writes
+//   output r to (j / NS) NS R + (j mod NS) + r NS.
+// Unnormalised; DIR = -1 forward, +1 inverse. Every read of a pass precedes
+// its first write (a barrier in between), so each thread holds its
+// butterflies' inputs in registers.
+//
+// Layout: element i of transform n at n (L + 1) + (i ^ s(i / 16)), with
+// s(m) = (m mod 8) + 8 (bit 2 of m): planes L + 1 apart put the N elements
+// of one index on different banks (the per-frequency work between the
+// transforms), and the XOR inside each run of 16 keeps the three access
+// patterns of the passes (consecutive; stride 8; runs of 8 that are 64
+// apart) free of bank conflicts.
+#pragma once
+
+namespace se2n {
+
+template <int L>
+__device__ __forceinline__ int xsm(int e) {
+    const int n = e / L, i = e & (L - 1), m = i >> 4;
+    return n * (L + 1) + (i ^ ((m & 7) | ((m << 1) & 8)));
+}
+
+template <int N, int L>
+struct SmemBlock {
+    static constexpr int COMPLEX = N * (L + 1);
+};
+
+// a * w (forward) or a * conj(w) (inverse)
+template <int DIR>
+__device__ __forceinline__ float2 twiddle(float2 a, float2 w) {
+    const float wy = DIR < 0 ? w.y : -w.y;
+    return make_float2(fmaf(a.x, w.x, -a.y * wy), fmaf(a.x, wy, a.y * w.x));
+}
+
+// z times exp(DIR i pi / 2): -i z forward, i z inverse
+template <int DIR>
+__device__ __forceinline__ float2 quarter(float2 z) {
+    return DIR < 0 ? make_float2(z.y, -z.x) : make_float2(-z.y, z.x);
+}
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+
+// V_k = sum_n v_n exp(DIR 2 pi i n k / R), in place, for R = 2, 4, 8.
+template <int R, int DIR>
+__device__ __forceinline__ void dft_small(float2 (&v)[R]) {
+    if constexpr (R == 2) {
+        const float2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else if constexpr (R == 4) {
+        const float2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+        const float2 t2 = cadd(v[1], v[3]), t3 = quarter<DIR>(csub(v[1], v[3]));
+        v[0] = cadd(t0, t2);
+        v[2] = csub(t0, t2);
+        v[1] = cadd(t1, t3);
+        v[3] = csub(t1, t3);
+    } else {
+        // even and odd halves, then V_k = E_k + w^k O_k, V_{k+4} = E_k - w^k O_k
+        float2 e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+        dft_small<4, DIR>(e);
+        dft_small<4, DIR>(o);
+        constexpr float h = 0.70710678118654752f;  // cos(pi / 4)
+        // w = exp(DIR i pi / 4) = (1 + DIR i) / sqrt(2)
+        const float2 o1 = DIR < 0 ? make_float2(h * (o[1].x + o[1].y), h * (o[1].y - o[1].x))
+                                  : make_float2(h * (o[1].x - o[1].y), h * (o[1].y + o[1].x));
+        const float2 o2 = quarter<DIR>(o[2]);
+        const float2 o3 = quarter<DIR>(DIR < 0 ? make_float2(h * (o[3].x + o[3].y), h * (o[3].y - o[3].x))
+                                               : make_float2(h * (o[3].x - o[3].y), h * (o[3].y + o[3].x)));
+        v[0] = cadd(e[0], o[0]);
+        v[4] = csub(e[0], o[0]);
+        v[1] = cadd(e[1], o1);
+        v[5] = csub(e[1], o1);
+        v[2] = cadd(e[2], o2);
+        v[6] = csub(e[2], o2);
+        v[3] = cadd(e[3], o3);
+        v[7] = csub(e[3], o3);
+    }
+}
+
+// One pass of T threads over the block X; tw[m * TS] = exp(-2 pi i m / L).
+template <int T, int N, int L, int R, int NS, int DIR, int TS>
+__device__ __forceinline__ void fft_pass(float2 *X, const float2 *tw, int tid) {
+    constexpr int M = L / R;  // butterflies a transform
+    constexpr int NB = N * M;
+    constexpr int BPT = (NB + T - 1) / T;
+    static_assert(T % M == 0, "j depends on the thread only");
+    // butterfly b = tid + q T: transform b / M, index j = tid mod M for every
+    // q, so the twiddles are read once
+    const int j = tid % M, k = j & (NS - 1);
+    float2 v[BPT][R];
+#pragma unroll
+    for (int q = 0; q < BPT; ++q) {
+        const int b = tid + q * T;
+        if (NB % T == 0 || b < NB) {
+            const int n = b / M;
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[q][r] = X[xsm<L>(n * L + j + r * M)];
+        }
+    }
+    float2 w[R];
+    if constexpr (NS > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) w[r] = tw[r * k * (L / (NS * R)) * TS];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < BPT; ++q) {
+        const int b = tid + q * T;
+        if (NB % T == 0 || b < NB) {
+            const int n = b / M;
+            if constexpr (NS > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[q][r] = twiddle<DIR>(v[q][r], w[r]);
+            }
+            dft_small<R, DIR>(v[q]);
+            const int base = n * L + (j - k) * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) X[xsm<L>(base + r * NS)] = v[q][r];
+        }
+    }
+}
+
+// The N DFTs of length L (32 = 8 x 4, 64 = 8 x 8, 128 = 8 x 8 x 2,
+// 256 = 8 x 8 x 4, 512 = 8 x 8 x 8). The caller synchronises before and after.
+template <int T, int N, int L, int DIR, int TS>
+__device__ __forceinline__ void fft_smem(float2 *X, const float2 *tw, int tid) {
+    static_assert(L == 32 || L == 64 || L == 128 || L == 256 || L == 512, "transform length");
+    fft_pass<T, N, L, 8, 1, DIR, TS>(X, tw, tid);
+    __syncthreads();
+    if constexpr (L == 32) {
+        fft_pass<T, N, L, 4, 8, DIR, TS>(X, tw, tid);
+    } else if constexpr (L == 64) {
+        fft_pass<T, N, L, 8, 8, DIR, TS>(X, tw, tid);
+    } else {
+        fft_pass<T, N, L, 8, 8, DIR, TS>(X, tw, tid);
+        __syncthreads();
+        fft_pass<T, N, L, L / 64, 64, DIR, TS>(X, tw, tid);
+    }
+}
+
+}  // namespace se2n

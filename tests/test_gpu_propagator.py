@@ -156,15 +156,19 @@ def test_full_512_N32_ten_rounds_against_stored_oracle():
     assert r2 <= REL_L2
 
 
-@pytest.mark.parametrize("H,W,N,dynamic", [(64, 96, 32, 0), (128, 70, 16, 0), (256, 40, 32, 0), (64, 64, 16, 1),
-                                           (128, 128, 32, 1)])
-def test_column_pass_matches_oracle(H, W, N, dynamic):
-    """Plane heights 64 to 512 with N = 16 or 32 run the fused column pass
-    (DFT along y, propagators, inverse DFT along y in shared memory, between
-    cuFFT row transforms): radix 8 x 8, 8 x 8 x 2 and 8 x 8 x 4, plane widths
-    with W/2 even and odd, and dynamic restoration on top."""
+@pytest.mark.parametrize("H,W,N,dynamic,final_mix,proj,reinject", [
+    (64, 128, 32, 0, 0, 0, 0), (128, 64, 16, 0, 1, 0, 0), (256, 64, 32, 0, 0, 1, 1), (64, 64, 16, 1, 0, 0, 0),
+    (128, 128, 32, 1, 1, 0, 1), (512, 256, 16, 0, 1, 1, 0)])
+def test_row_and_column_passes_match_oracle(H, W, N, dynamic, final_mix, proj, reinject):
+    """Plane sizes with H and W in 64 .. 512 and N = 16 or 32 run the fused
+    passes: a row pass (lift, or inverse DFT along x, restoration and forward
+    DFT along x, or projection) and a column pass (DFT along y, propagators,
+    inverse DFT along y) an interval. Cases cover every radix mix of both
+    lengths (8 x 4 .. 8 x 8 x 8), the final restoration, mean projection,
+    reinjection and dynamic restoration (the real volume between passes)."""
     w = synth.workload_512(H=H, W=W, steps=60, rounds=3)
-    p = oracle.Params(N=N, beta=0.25, T=6.0, steps=60, rounds=3, dynamic=dynamic)
+    p = oracle.Params(N=N, beta=0.25, T=6.0, steps=60, rounds=3, dynamic=dynamic, final_mix=final_mix, proj=proj,
+                      reinject=reinject)
     f32 = w.f.astype(np.float32)
     f64 = f32.astype(np.float64)
     bins = oracle.orient(f64, w.mask, p.N, p.sigma, 0, p.flat_tol)["bins"]
@@ -174,8 +178,11 @@ def test_column_pass_matches_oracle(H, W, N, dynamic):
     got, prof = _gpu_inpaint(f32, w.mask, bins, prm, profile=True)
     mx = np.abs(got - ref).max() / np.abs(f64).max()
     r2 = rel_l2(got, ref)
-    print(f"{H}x{W} N={N} dynamic={dynamic}: max-abs/max|f| {mx:.2e}, rel-L2 {r2:.2e}")
-    # one build; per interval one column pass and two row transforms
-    assert prof["propagator"][1] == 1 and prof["diffuse"][1] == 3 and prof["fft"][1] == 6
+    print(f"{H}x{W} N={N} dynamic={dynamic} final_mix={final_mix} proj={proj} reinject={reinject}: "
+          f"max-abs/max|f| {mx:.2e}, rel-L2 {r2:.2e}")
+    # one build; one column pass an interval; row passes: lift, one between
+    # intervals (two around the real volume with dynamic restoration), last
+    assert prof["propagator"][1] == 1 and prof["diffuse"][1] == 3
+    assert prof["fft"][1] == (6 if dynamic else 4)
     assert mx <= MAX_REL_RESTORED
     assert r2 <= REL_L2
