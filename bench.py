@@ -28,6 +28,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -128,8 +129,11 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 
 KERNEL_SOURCES = {"diffuse": ("diffuse_impl.cuh", "diffuse_x2.cuh", "diffuse.cu"),
-                  "prop_build": ("propagator.cu", "diffuse_x2.cuh", "diffuse_impl.cuh")}
-TRAFFIC_FILES = {"diffuse": "diffuse_traffic.json", "prop_build": "prop_build_traffic.json"}
+                  "prop_build": ("propagator.cu", "prop_classes.cuh", "diffuse_x2.cuh", "diffuse_impl.cuh"),
+                  "col_prop": ("colprop.cu", "smem_fft.cuh", "prop_classes.cuh", "diffuse_x2.cuh"),
+                  "row_pass": ("rowfft.cu", "smem_fft.cuh", "restore.cuh")}
+TRAFFIC_FILES = {"diffuse": "diffuse_traffic.json", "prop_build": "prop_build_traffic.json",
+                 "col_prop": "col_prop_traffic.json", "row_pass": "row_pass_traffic.json"}
 
 
 def kernel_source_hash(kind="diffuse"):
@@ -260,30 +264,52 @@ def run_ours(args, rank, world, local_rank):
     # the path integrates the Hermitian half of the spectrum: H x (W/2 + 1) frequencies
     updates_per_launch = w.H * (w.W // 2 + 1) * w.N * w.steps
     if prop:
-        # the dominant kernel of ours is the propagator build (FP32 products)
+        # every interval is one column pass (DFT along y, propagators, inverse
+        # DFT along y) and one row pass (inverse real DFT along x, restoration,
+        # forward real DFT along x); the propagators are built once. The
+        # column passes take the largest share of the inpaint.
+        c_ms, c_calls = prof["diffuse"]
+        c_s = c_ms / c_calls / 1e3
+        r_ms, r_calls = prof["fft"]
+        r_s = r_ms / r_calls / 1e3
         b_ms, b_calls = prof["propagator"]
         b_s = b_ms / b_calls / 1e3
         classes = propagator_classes(w.H, w.W)
+        wc = w.W // 2 + 1
+        spec_bytes = 8 * wc * w.H * w.N
+        col_bytes = 2 * spec_bytes + 4 * w.N * w.N * classes
+        row_bytes = 2 * spec_bytes + 6 * w.H * w.W
+        col_flops = 2 * wc * w.N * 5 * w.H * int(math.log2(w.H)) + 4 * w.N * w.N * w.H * wc
         flops = propagator_gemm_flops(classes, w.N, w.steps)
-        achieved = flops / b_s / 1e12
-        a_ms, a_calls = prof["diffuse"]
-        a_s = a_ms / a_calls / 1e3
-        apply_bytes = classes * (w.N // 2 + 1) * w.N * 4 + 16 * w.H * (w.W // 2 + 1) * w.N
         hbm = _peaks().get("hbm_gbs")
-        roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
-                    "frac": round(achieved / peak, 4),
-                    "traffic": args.traffic if args.traffic is not None else stored_traffic("prop_build"),
-                    "kernel": "k_prop_build<32> (S-step propagators of 33,153 frequency classes, FP32 products)",
-                    "flops_per_launch": flops, "flops_basis": "classes x (squarings + combinations) x 2 N^3, "
-                    f"S = {w.steps}: {w.steps.bit_length() - 1} squarings, {bin(w.steps).count('1') - 1} combinations",
-                    "avg_launch_ms": round(b_s * 1e3, 4), "peak_basis": peak_basis,
-                    "apply_kernel": {"kernel": "k_prop_apply<32>", "bound": "hbm", "avg_launch_ms": round(a_s * 1e3, 4),
-                                     "bytes_per_launch": apply_bytes,
-                                     "bytes_basis": "the classes' stored diagonals (4 N (N/2+1) bytes a class) + "
-                                                    "one read and one write of the half spectrum",
-                                     "achieved_gbs": round(apply_bytes / a_s / 1e9, 1), "peak_gbs": hbm,
-                                     "frac": round(apply_bytes / a_s / 1e9 / hbm, 4) if hbm else None,
-                                     "peak_basis": "MEASURED_PEAKS.json hbm_gbs"},
+        hbm_basis = "MEASURED_PEAKS.json hbm_gbs (copy, burst)"
+        roofline = {"bound": "hbm", "achieved": round(col_bytes / c_s / 1e9, 1), "peak": hbm, "unit": "GB/s",
+                    "frac": round(col_bytes / c_s / 1e9 / hbm, 4) if hbm else None,
+                    "traffic": args.traffic if args.traffic is not None else stored_traffic("col_prop"),
+                    "kernel": f"k_col_prop<{w.N},{w.H}> (column pass: DFT along y, x <- x + D_S x, inverse DFT; "
+                              "one block a column)",
+                    "bytes_per_launch": col_bytes,
+                    "bytes_basis": "one read and one write of the row-transformed half spectrum (8 (W/2+1) H N "
+                                   "bytes each) + the propagators as rows, read once (4 N^2 bytes a class)",
+                    "avg_launch_ms": round(c_s * 1e3, 4), "peak_basis": hbm_basis,
+                    "flops_per_launch": col_flops,
+                    "flops_basis": "2 (W/2+1) N complex DFTs of length H at 5 H log2 H + 4 N^2 a frequency",
+                    "frac_of_fp32_peak": round(col_flops / c_s / 1e12 / peak, 4),
+                    "row_pass": {"kernel": f"k_row<{w.N},{w.W}> (inverse real DFT along x, restoration, forward "
+                                           "real DFT; one block a row)", "bound": "hbm",
+                                 "avg_launch_ms": round(r_s * 1e3, 4), "bytes_per_launch": row_bytes,
+                                 "bytes_basis": "one read and one write of the half spectrum + f, mask, bins",
+                                 "achieved_gbs": round(row_bytes / r_s / 1e9, 1), "peak_gbs": hbm,
+                                 "frac": round(row_bytes / r_s / 1e9 / hbm, 4) if hbm else None,
+                                 "traffic": stored_traffic("row_pass")},
+                    "build": {"kernel": f"k_prop_build<{w.N}> ({classes} classes, FP32 products)", "bound": "alu",
+                              "avg_launch_ms": round(b_s * 1e3, 4), "flops_per_launch": flops,
+                              "flops_basis": "classes x (squarings + combinations) x 2 N^3, "
+                              f"S = {w.steps}: {w.steps.bit_length() - 1} squarings, "
+                              f"{bin(w.steps).count('1') - 1} combinations",
+                              "achieved_tflops": round(flops / b_s / 1e12, 3), "peak_tflops": round(peak, 3),
+                              "frac": round(flops / b_s / 1e12 / peak, 4), "peak_basis": peak_basis,
+                              "traffic": stored_traffic("prop_build")},
                     "frequencies_integrated": "Hermitian half, H x (W/2 + 1) (value counts all M^2 frequencies)"}
     else:
         d_ms, d_calls = prof["diffuse"]

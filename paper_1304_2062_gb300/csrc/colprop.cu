@@ -58,6 +58,15 @@ __device__ __forceinline__ void col_apply(float2 *X, const float *D, int scol, i
                 drow[i][4 * j + 3] = d.w;
             }
         }
+        // the class this lane takes next, into L1 while this one is applied
+        // (N^2 / 32 lines of 128 bytes a class, N / 16 a lane)
+        if (s + WARPS * CPW < SLOTS) {
+            const char *Dn = reinterpret_cast<const char *>(
+                D + ((long long)(s + WARPS * CPW) * col_slots + scol) * (N * N));
+#pragma unroll
+            for (int c = 0; c < N / 16; ++c)
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(Dn + (t + c * LPC) * 128));
+        }
         f32x2 acc[RPL][4];
 #pragma unroll
         for (int i = 0; i < RPL; ++i)
@@ -115,10 +124,22 @@ __global__ void __launch_bounds__(kColThreads, 1) k_col_prop(const __grid_consta
     const int l = (b & 1) ? a.W / 2 - h : h;
     float2 *g = a.col + (long long)l * (N * L);
     for (int m = tid; m < L; m += kColThreads) tws[m] = a.tw[m];
-    // the column block [k][n] into transforms [n][k]: consecutive threads read
-    // consecutive angles of a frequency
-#pragma unroll 4
-    for (int e = tid; e < N * L; e += kColThreads) X[xsm<L>((e % N) * L + e / N)] = g[e];
+    // the column block [k][n] into transforms [n][k], two angles a 16-byte
+    // load, every load of a thread issued before the first store
+    constexpr int NV = N * L / 2 / kColThreads;
+    static_assert(NV * 2 * kColThreads == N * L, "whole block");
+    {
+        float4 in[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) in[q] = reinterpret_cast<const float4 *>(g)[tid + q * kColThreads];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            const int e = 2 * (tid + q * kColThreads), k = e / N, n = e % N;
+            const int o = xoff<L>(k);
+            X[n * (L + 1) + o] = make_float2(in[q].x, in[q].y);
+            X[(n + 1) * (L + 1) + o] = make_float2(in[q].z, in[q].w);
+        }
+    }
     __syncthreads();
     fft_smem<kColThreads, N, L, -1, 1>(X, tws, tid);
     __syncthreads();
@@ -126,8 +147,13 @@ __global__ void __launch_bounds__(kColThreads, 1) k_col_prop(const __grid_consta
     __syncthreads();
     fft_smem<kColThreads, N, L, 1, 1>(X, tws, tid);
     __syncthreads();
-#pragma unroll 4
-    for (int e = tid; e < N * L; e += kColThreads) g[e] = X[xsm<L>((e % N) * L + e / N)];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        const int e = 2 * (tid + q * kColThreads), k = e / N, n = e % N;
+        const int o = xoff<L>(k);
+        const float2 a = X[n * (L + 1) + o], c = X[(n + 1) * (L + 1) + o];
+        reinterpret_cast<float4 *>(g)[tid + q * kColThreads] = make_float4(a.x, a.y, c.x, c.y);
+    }
 }
 
 template <int N, int L>
