@@ -55,11 +55,12 @@ __global__ void __launch_bounds__(kRowThreads) k_row(const __grid_constant__ Row
             const uchar2 mk = reinterpret_cast<const uchar2 *>(a.mask + row)[m];
             const uchar2 bn = reinterpret_cast<const uchar2 *>(a.bins + row)[m];
             const float a0 = mk.x ? fv.x : 0.0f, a1 = mk.y ? fv.y : 0.0f;
-#pragma unroll 4
+            float2 *Zm = Z + xoff<WH>(m);
+#pragma unroll 8
             for (int n = 0; n < N; ++n) {
                 const bool on0 = (bn.x == n) || (bn.x == SE2N_BIN_FLAT);
                 const bool on1 = (bn.y == n) || (bn.y == SE2N_BIN_FLAT);
-                Z[xsm<WH>(n * WH + m)] = make_float2(on0 ? a0 : 0.0f, on1 ? a1 : 0.0f);
+                Zm[n * (WH + 1)] = make_float2(on0 ? a0 : 0.0f, on1 ? a1 : 0.0f);
             }
         }
     } else if (a.in_mode == SE2N_ROW_IN_REAL) {
@@ -68,21 +69,36 @@ __global__ void __launch_bounds__(kRowThreads) k_row(const __grid_constant__ Row
             Z[xsm<WH>(e)] = reinterpret_cast<const float2 *>(a.real_in + (n * H + y) * (W + 2))[m];
         }
     } else {
-        __syncthreads();  // twiddles
-        // pairs (l, W/2 - l), l = 0 .. W/4; consecutive threads take
-        // consecutive angles of one frequency
-        for (int e = tid; e < N * (WH / 2 + 1); e += T) {
-            const int l = e / N, n = e - l * N;
-            float2 xl = a.spec_in[((long long)l * H + y) * N + n];
-            float2 xb = a.spec_in[((long long)(WH - l) * H + y) * N + n];
-            if (l == 0) {
-                xl.y = 0.0f;
-                xb.y = 0.0f;
+        // pairs (l, W/2 - l), l = 0 .. W/4: thread tid takes angle tid mod N
+        // of pairs tid / N + i T / N (consecutive threads, consecutive angles
+        // of one frequency), all its loads issued first
+        constexpr int LP = WH / 2 + 1, TL = T / N, IT = (LP + TL - 1) / TL;
+        static_assert(T % N == 0, "whole frequencies a block");
+        const int n = tid % N, l0 = tid / N;
+        float2 xl[IT], xb[IT];
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            const int l = l0 + i * TL;
+            if (LP % TL == 0 || l < LP) {
+                xl[i] = __ldg(a.spec_in + ((long long)l * H + y) * N + n);
+                xb[i] = __ldg(a.spec_in + ((long long)(WH - l) * H + y) * N + n);
             }
-            const float2 P = cadd(xl, cconj(xb));
-            const float2 Q = twiddle<1>(csub(xl, cconj(xb)), tws[l]);
-            Z[xsm<WH>(n * WH + l)] = make_float2(P.x - Q.y, P.y + Q.x);
-            if (l != 0 && 2 * l != WH) Z[xsm<WH>(n * WH + WH - l)] = make_float2(P.x + Q.y, Q.x - P.y);
+        }
+        __syncthreads();  // twiddles
+        float2 *Zn = Z + n * (WH + 1);
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            const int l = l0 + i * TL;
+            if (LP % TL == 0 || l < LP) {
+                if (l == 0) {
+                    xl[i].y = 0.0f;
+                    xb[i].y = 0.0f;
+                }
+                const float2 P = cadd(xl[i], cconj(xb[i]));
+                const float2 Q = twiddle<1>(csub(xl[i], cconj(xb[i])), tws[l]);
+                Zn[xoff<WH>(l)] = make_float2(P.x - Q.y, P.y + Q.x);
+                if (l != 0 && 2 * l != WH) Zn[xoff<WH>(WH - l)] = make_float2(P.x + Q.y, Q.x - P.y);
+            }
         }
         __syncthreads();
         fft_smem<T, N, WH, 1, 2>(Z, tws, tid);
@@ -91,10 +107,11 @@ __global__ void __launch_bounds__(kRowThreads) k_row(const __grid_constant__ Row
     // 2. the restoration, one pixel pair (2m, 2m + 1) a thread
     if (a.mix) {
         for (int m = tid; m < WH; m += T) {
+            float2 *Zm = Z + xoff<WH>(m);
             float ht0 = -INFINITY, ht1 = -INFINITY;
-#pragma unroll 4
+#pragma unroll 8
             for (int n = 0; n < N; ++n) {
-                const float2 v = Z[xsm<WH>(n * WH + m)];
+                const float2 v = Zm[n * (WH + 1)];
                 ht0 = fmaxf(ht0, v.x * a.scale);
                 ht1 = fmaxf(ht1, v.y * a.scale);
             }
@@ -104,9 +121,9 @@ __global__ void __launch_bounds__(kRowThreads) k_row(const __grid_constant__ Row
             const float a0 = mk.x ? fv.x : 0.0f, a1 = mk.y ? fv.y : 0.0f;
             const float h00 = (bn.x == SE2N_BIN_FLAT) ? a0 : fmaxf(a0, 0.0f);
             const float h01 = (bn.y == SE2N_BIN_FLAT) ? a1 : fmaxf(a1, 0.0f);
-#pragma unroll 4
+#pragma unroll 8
             for (int n = 0; n < N; ++n) {
-                float2 &v = Z[xsm<WH>(n * WH + m)];
+                float2 &v = Zm[n * (WH + 1)];
                 const float l0 = ((bn.x == n) || (bn.x == SE2N_BIN_FLAT)) ? a0 : 0.0f;
                 const float l1 = ((bn.y == n) || (bn.y == SE2N_BIN_FLAT)) ? a1 : 0.0f;
                 v = make_float2(sr_value(v.x * a.scale, h00, ht0, l0, mk.x != 0, a.eps, a.guard),
@@ -123,22 +140,23 @@ __global__ void __launch_bounds__(kRowThreads) k_row(const __grid_constant__ Row
         }
     } else if (a.out_mode == SE2N_ROW_OUT_PROJ) {
         for (int m = tid; m < WH; m += T) {
+            const float2 *Zm = Z + xoff<WH>(m);
             float a0, a1;
             if (a.proj == SE2N_PROJ_MAX) {
                 a0 = -INFINITY;
                 a1 = -INFINITY;
-#pragma unroll 4
+#pragma unroll 8
                 for (int n = 0; n < N; ++n) {
-                    const float2 v = Z[xsm<WH>(n * WH + m)];
+                    const float2 v = Zm[n * (WH + 1)];
                     a0 = fmaxf(a0, v.x * a.scale_proj);
                     a1 = fmaxf(a1, v.y * a.scale_proj);
                 }
             } else {
                 a0 = 0.0f;
                 a1 = 0.0f;
-#pragma unroll 4
+#pragma unroll 8
                 for (int n = 0; n < N; ++n) {
-                    const float2 v = Z[xsm<WH>(n * WH + m)];
+                    const float2 v = Zm[n * (WH + 1)];
                     a0 += v.x * a.scale_proj;
                     a1 += v.y * a.scale_proj;
                 }
@@ -156,16 +174,22 @@ __global__ void __launch_bounds__(kRowThreads) k_row(const __grid_constant__ Row
     } else {
         fft_smem<T, N, WH, -1, 2>(Z, tws, tid);
         __syncthreads();
-        for (int e = tid; e < N * (WH / 2 + 1); e += T) {
-            const int l = e / N, n = e - l * N;
-            const float2 zl = Z[xsm<WH>(n * WH + l)];
-            const float2 zc = cconj(Z[xsm<WH>(n * WH + ((WH - l) & (WH - 1)))]);
-            const float2 s = cadd(zl, zc), d = csub(zl, zc);
-            const float2 E = make_float2(0.5f * s.x, 0.5f * s.y);
-            const float2 O = make_float2(0.5f * d.y, -0.5f * d.x);  // -i d / 2
-            const float2 B = twiddle<-1>(O, tws[l]);
-            a.spec_out[((long long)l * H + y) * N + n] = cadd(E, B);
-            if (2 * l != WH) a.spec_out[((long long)(WH - l) * H + y) * N + n] = cconj(csub(E, B));
+        constexpr int LP = WH / 2 + 1, TL = T / N, IT = (LP + TL - 1) / TL;
+        const int n = tid % N, l0 = tid / N;
+        const float2 *Zn = Z + n * (WH + 1);
+#pragma unroll 4
+        for (int i = 0; i < IT; ++i) {
+            const int l = l0 + i * TL;
+            if (LP % TL == 0 || l < LP) {
+                const float2 zl = Zn[xoff<WH>(l)];
+                const float2 zc = cconj(Zn[xoff<WH>((WH - l) & (WH - 1))]);
+                const float2 s = cadd(zl, zc), d = csub(zl, zc);
+                const float2 E = make_float2(0.5f * s.x, 0.5f * s.y);
+                const float2 O = make_float2(0.5f * d.y, -0.5f * d.x);  // -i d / 2
+                const float2 B = twiddle<-1>(O, tws[l]);
+                a.spec_out[((long long)l * H + y) * N + n] = cadd(E, B);
+                if (2 * l != WH) a.spec_out[((long long)(WH - l) * H + y) * N + n] = cconj(csub(E, B));
+            }
         }
     }
 }

@@ -21,10 +21,15 @@
 
 namespace se2n {
 
+// position of element i inside a plane, and of element e = n L + i of the block
+template <int L>
+__device__ __forceinline__ int xoff(int i) {
+    const int m = i >> 4;
+    return i ^ ((m & 7) | ((m << 1) & 8));
+}
 template <int L>
 __device__ __forceinline__ int xsm(int e) {
-    const int n = e / L, i = e & (L - 1), m = i >> 4;
-    return n * (L + 1) + (i ^ ((m & 7) | ((m << 1) & 8)));
+    return (e / L) * (L + 1) + xoff<L>(e & (L - 1));
 }
 
 template <int N, int L>
@@ -96,14 +101,22 @@ __device__ __forceinline__ void fft_pass(float2 *X, const float2 *tw, int tid) {
     // butterfly b = tid + q T: transform b / M, index j = tid mod M for every
     // q, so the twiddles are read once
     const int j = tid % M, k = j & (NS - 1);
+    // positions inside the plane of this thread's inputs and outputs, the
+    // same for all its butterflies
+    int ro[R], wo[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        ro[r] = xoff<L>(j + r * M);
+        wo[r] = xoff<L>((j - k) * R + k + r * NS);
+    }
     float2 v[BPT][R];
 #pragma unroll
     for (int q = 0; q < BPT; ++q) {
         const int b = tid + q * T;
         if (NB % T == 0 || b < NB) {
-            const int n = b / M;
+            const float2 *Xn = X + (b / M) * (L + 1);
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[q][r] = X[xsm<L>(n * L + j + r * M)];
+            for (int r = 0; r < R; ++r) v[q][r] = Xn[ro[r]];
         }
     }
     float2 w[R];
@@ -116,15 +129,14 @@ __device__ __forceinline__ void fft_pass(float2 *X, const float2 *tw, int tid) {
     for (int q = 0; q < BPT; ++q) {
         const int b = tid + q * T;
         if (NB % T == 0 || b < NB) {
-            const int n = b / M;
             if constexpr (NS > 1) {
 #pragma unroll
                 for (int r = 1; r < R; ++r) v[q][r] = twiddle<DIR>(v[q][r], w[r]);
             }
             dft_small<R, DIR>(v[q]);
-            const int base = n * L + (j - k) * R + k;
+            float2 *Xn = X + (b / M) * (L + 1);
 #pragma unroll
-            for (int r = 0; r < R; ++r) X[xsm<L>(base + r * NS)] = v[q][r];
+            for (int r = 0; r < R; ++r) Xn[wo[r]] = v[q][r];
         }
     }
 }
