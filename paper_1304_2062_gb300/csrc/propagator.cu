@@ -185,6 +185,65 @@ __device__ __forceinline__ void prop_solve2(float (&x)[N], float (&y)[N], const 
     }
 }
 
+// Lane 0 of a class: the torn factor of A' (reciprocal pivots G, diagonal
+// d_j = 1/c + 2 + a_j^2/beta, with the corners folded into the first and last
+// pivots) and q = T^{-1} u, u = (-d0, 0, ..., 0, -1), for the Sherman-Morrison
+// correction; scal = (1/d0, 1/(1 + v.q)).
+template <int N>
+__device__ __forceinline__ void prop_factor(const PropArgs &a, float wx, float wy, float *G, float *q, float *scal) {
+    float d0 = 0.f;
+    float piv = 0.f;
+#pragma unroll 1
+    for (int j = 0; j < N; ++j) {
+        const float ar = fmaf(wx, a.cs[j], wy * a.sn[j]);
+        const float d = (a.inv_c + 2.0f) + ar * ar * a.inv_beta;
+        float tj = d;
+        if (j == 0) {
+            d0 = d;
+            tj = 2.0f * d;
+        }
+        if (j == N - 1) tj = d + 1.0f / d0;
+        piv = (j == 0) ? tj : tj - G[j - 1];
+        G[j] = 1.0f / piv;
+    }
+    float qq[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) qq[j] = 0.f;
+    qq[0] = -d0;
+    qq[N - 1] = -1.0f;
+#pragma unroll
+    for (int j = 1; j < N; ++j) qq[j] = fmaf(G[j - 1], qq[j - 1], qq[j]);
+    qq[N - 1] *= G[N - 1];
+#pragma unroll
+    for (int j = N - 2; j >= 0; --j) qq[j] = (qq[j] + qq[j + 1]) * G[j];
+#pragma unroll
+    for (int j = 0; j < N; ++j) q[j] = qq[j];
+    const float inv_d0 = 1.0f / d0;
+    scal[0] = inv_d0;
+    scal[1] = 1.0f / (1.0f + fmaf(qq[N - 1], inv_d0, qq[0]));
+}
+
+// D_S of class u from a symmetric row-major matrix (stride ld): as rows in
+// 16-byte chunks, chunk-major, or by cyclic diagonals; lanes t of `lanes`.
+template <int N>
+__device__ __forceinline__ void prop_store(const PropArgs &a, const float *Rm, int ld, long long u, bool live, int t,
+                                           int lanes) {
+    if (!live) return;
+    if (a.rows) {
+        float4 *out = reinterpret_cast<float4 *>(a.D + u * (long long)(N * N));
+        for (int e = t; e < N * N / 4; e += lanes) {
+            const int c = e / N, i = e - c * N;
+            out[e] = *reinterpret_cast<const float4 *>(Rm + i * ld + 4 * c);
+        }
+    } else {
+        float *out = a.D + u * (long long)((N / 2 + 1) * N);
+        for (int e = t; e < (N / 2 + 1) * N; e += lanes) {
+            const int m = e / N, i = e - m * N;
+            out[e] = Rm[i * ld + ((i + m) & (N - 1))];
+        }
+    }
+}
+
 template <int N>
 __global__ void __launch_bounds__(PropCfg<N>::WARPS * 32) k_prop_build(const __grid_constant__ PropArgs a) {
     using C = PropCfg<N>;
@@ -203,40 +262,7 @@ __global__ void __launch_bounds__(PropCfg<N>::WARPS * 32) k_prop_build(const __g
         int k, l, lb;
         class_slots(a, live ? u : a.classes - 1, k, l, lb);
         const float wx = sin_2pi_frac(l, a.W), wy = sin_2pi_frac(k, a.H);
-        // torn factor of A' (lane 0 of the class), diagonal d_j = 1/c + 2 + a_j^2/beta
-        if (t == 0) {
-            float d0 = 0.f;
-            float piv = 0.f;
-#pragma unroll 1
-            for (int j = 0; j < N; ++j) {
-                const float ar = fmaf(wx, a.cs[j], wy * a.sn[j]);
-                const float d = (a.inv_c + 2.0f) + ar * ar * a.inv_beta;
-                float tj = d;
-                if (j == 0) {
-                    d0 = d;
-                    tj = 2.0f * d;
-                }
-                if (j == N - 1) tj = d + 1.0f / d0;
-                piv = (j == 0) ? tj : tj - G[j - 1];
-                G[j] = 1.0f / piv;
-            }
-            // q = T^{-1} u, u = (-d0, 0, ..., 0, -1)
-            float qq[N];
-#pragma unroll
-            for (int j = 0; j < N; ++j) qq[j] = 0.f;
-            qq[0] = -d0;
-            qq[N - 1] = -1.0f;
-#pragma unroll
-            for (int j = 1; j < N; ++j) qq[j] = fmaf(G[j - 1], qq[j - 1], qq[j]);
-            qq[N - 1] *= G[N - 1];
-#pragma unroll
-            for (int j = N - 2; j >= 0; --j) qq[j] = (qq[j] + qq[j + 1]) * G[j];
-#pragma unroll
-            for (int j = 0; j < N; ++j) q[j] = qq[j];
-            const float inv_d0 = 1.0f / d0;
-            scal[0] = inv_d0;
-            scal[1] = 1.0f / (1.0f + fmaf(qq[N - 1], inv_d0, qq[0]));
-        }
+        if (t == 0) prop_factor<N>(a, wx, wy, G, q, scal);
         __syncwarp();
         const float inv_d0 = scal[0], inv_den = scal[1];
         // D_1, column by column: 2 A'^{-1} Lap e_c - 2 (a_c^2/beta) A'^{-1} e_c;
@@ -350,6 +376,203 @@ __global__ void __launch_bounds__(PropCfg<N>::WARPS * 32) k_prop_build(const __g
                 }
             }
         }
+        __syncwarp();
+    }
+}
+
+// Build with symmetric products (N = 16, 32). Every matrix of the powering
+// is a function of the one symmetric operator of the class (D_1 = 2 A'^{-1} L
+// with A' = I/c - L), so all of them are symmetric and commute, and so are
+// the products D_m D_m and D_a D_b. A matrix is kept once, row-major (its
+// rows are its columns), and a product is computed on the tiles of its upper
+// triangle only and mirrored: 10 of 16 tiles of 8 x 8 at N = 32 (3 of 4 at
+// N = 16), one lane a tile, 3 classes a warp at N = 32 and 10 at N = 16.
+// The mirrored tile is exactly symmetric; for a diagonal tile the upper half
+// is written and mirrored. D_1, built column by column by the solves, is
+// symmetrised first (the mean of mirrored entries).
+template <int N>
+struct SymCfg {
+    static constexpr int WARPS = 4;
+    static constexpr int NT = N / 8;                 // tiles a side
+    static constexpr int TILES = NT * (NT + 1) / 2;  // upper-triangle tiles: lanes a class
+    static constexpr int CPW = 32 / TILES;           // classes a warp
+    static constexpr int LD = N + 4;                 // row stride, floats
+    static constexpr int MAT = N * LD;
+    static constexpr int CLASS_FLOATS = 2 * MAT + 2 * N + 4;  // P, R, pivots, q, scalars
+    static constexpr int SMEM = WARPS * CPW * CLASS_FLOATS * 4;
+    static constexpr int SBLK = (N / 2 + 1) * N;
+    static_assert(N == 16 || N == 32, "8 x 8 tiles of 16 or 32");
+};
+
+// out = two * X + Y + A B on the upper-triangle tile (bi, bj) of this lane,
+// mirrored; A, B, X, Y, out symmetric N x N row-major (stride LD), Y may be
+// null, out may be an input (the warp synchronises between the reads and
+// the writes; every lane of the warp calls this together).
+template <int N>
+__device__ __forceinline__ void sym_gemm(const float *A, const float *B, const float *X, float two, const float *Y,
+                                         float *out, int bi, int bj, bool active) {
+    using C = SymCfg<N>;
+    const int r0 = 8 * bi, c0 = 8 * bj;
+    f32x2 acc[8][4];  // [row][column pair]
+    if (active) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int c = 0; c < 8; c += 4) {
+                const float4 xv = *reinterpret_cast<const float4 *>(X + (r0 + r) * C::LD + c0 + c);
+                float4 yv = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (Y) yv = *reinterpret_cast<const float4 *>(Y + (r0 + r) * C::LD + c0 + c);
+                acc[r][c / 2] = pk2(fmaf(two, xv.x, yv.x), fmaf(two, xv.y, yv.y));
+                acc[r][c / 2 + 1] = pk2(fmaf(two, xv.z, yv.z), fmaf(two, xv.w, yv.w));
+            }
+#pragma unroll 2
+        for (int k = 0; k < N; ++k) {
+            // A[r][k] = A[k][r]: row k of A, columns r0 .. r0 + 7
+            const float4 a0 = *reinterpret_cast<const float4 *>(A + k * C::LD + r0);
+            const float4 a1 = *reinterpret_cast<const float4 *>(A + k * C::LD + r0 + 4);
+            const float4 b0 = *reinterpret_cast<const float4 *>(B + k * C::LD + c0);
+            const float4 b1 = *reinterpret_cast<const float4 *>(B + k * C::LD + c0 + 4);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const f32x2 bv[4] = {pk2(b0.x, b0.y), pk2(b0.z, b0.w), pk2(b1.x, b1.y), pk2(b1.z, b1.w)};
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const f32x2 s = dup2(av[r]);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = fma2(s, bv[c], acc[r][c]);
+            }
+        }
+    }
+    __syncwarp();
+    if (active) {
+        float v[8][8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                v[r][2 * c] = lo2(acc[r][c]);
+                v[r][2 * c + 1] = hi2(acc[r][c]);
+            }
+        // a diagonal tile takes its upper half for the lower one
+        if (bi == bj) {
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+                for (int c = 0; c < r; ++c) v[r][c] = v[c][r];
+        }
+        // the tile and its transpose, as 16-byte rows
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            *reinterpret_cast<float4 *>(out + (r0 + r) * C::LD + c0) = make_float4(v[r][0], v[r][1], v[r][2], v[r][3]);
+            *reinterpret_cast<float4 *>(out + (r0 + r) * C::LD + c0 + 4) =
+                make_float4(v[r][4], v[r][5], v[r][6], v[r][7]);
+        }
+        if (bi != bj) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                *reinterpret_cast<float4 *>(out + (c0 + c) * C::LD + r0) =
+                    make_float4(v[0][c], v[1][c], v[2][c], v[3][c]);
+                *reinterpret_cast<float4 *>(out + (c0 + c) * C::LD + r0 + 4) =
+                    make_float4(v[4][c], v[5][c], v[6][c], v[7][c]);
+            }
+        }
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(SymCfg<N>::WARPS * 32) k_prop_build_sym(const __grid_constant__ PropArgs a) {
+    using C = SymCfg<N>;
+    extern __shared__ __align__(16) float psm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane / C::TILES, t = lane - g * C::TILES;
+    const bool active = g < C::CPW;
+    // this lane's tile (bi, bj), bi <= bj, in row order of the upper triangle
+    int bi = 0, rem = t;
+    while (rem >= C::NT - bi) {
+        rem -= C::NT - bi;
+        ++bi;
+    }
+    const int bj = bi + rem;
+    float *base = psm + (warp * C::CPW + (active ? g : 0)) * C::CLASS_FLOATS;
+    float *P = base, *R = base + C::MAT;
+    float *G = base + 2 * C::MAT;
+    float *q = G + N;
+    float *scal = q + N;  // 1/d0, 1/(1 + v.q)
+    const long long stride = (long long)gridDim.x * C::WARPS * C::CPW;
+    // classes are taken warp-uniformly so that every lane reaches each __syncwarp
+    for (long long u0 = ((long long)blockIdx.x * C::WARPS + warp) * C::CPW; u0 < a.classes; u0 += stride) {
+        const long long u = u0 + g;
+        const bool live = active && u < a.classes;
+        int k, l, lb;
+        class_slots(a, live ? u : a.classes - 1, k, l, lb);
+        const float wx = sin_2pi_frac(l, a.W), wy = sin_2pi_frac(k, a.H);
+        if (active && t == 0) prop_factor<N>(a, wx, wy, G, q, scal);
+        __syncwarp();
+        // D_1 column by column into R (R row c = column c), then P = (R + R^T) / 2
+        if (active) {
+            const float inv_d0 = scal[0], inv_den = scal[1];
+#pragma unroll 1
+            for (int c = t; c < N; c += C::TILES) {
+                const float ar = fmaf(wx, a.cs[c], wy * a.sn[c]);
+                const float e2 = ar * ar * a.inv_beta;
+                const int cm = (c == 0) ? N - 1 : c - 1, cp = (c == N - 1) ? 0 : c + 1;
+                float x[N], y[N];
+#pragma unroll
+                for (int j = 0; j < N; ++j) {
+                    x[j] = (j == c) ? 1.0f : 0.0f;
+                    y[j] = (j == c) ? -2.0f : ((j == cm || j == cp) ? 1.0f : 0.0f);
+                }
+                prop_solve2<N>(x, y, G, q, inv_d0, inv_den);
+#pragma unroll
+                for (int j = 0; j < N; j += 4)
+                    *reinterpret_cast<float4 *>(R + c * C::LD + j) =
+                        make_float4(fmaf(2.0f, y[j], -2.0f * e2 * x[j]), fmaf(2.0f, y[j + 1], -2.0f * e2 * x[j + 1]),
+                                    fmaf(2.0f, y[j + 2], -2.0f * e2 * x[j + 2]),
+                                    fmaf(2.0f, y[j + 3], -2.0f * e2 * x[j + 3]));
+            }
+        }
+        __syncwarp();
+        // rows i of this lane: P[i][j] = (R[i][j] + R[j][i]) / 2, which gives
+        // P[j][i] the same bits
+        if (active) {
+#pragma unroll 1
+            for (int i = t; i < N; i += C::TILES)
+#pragma unroll
+                for (int j = 0; j < N; j += 4) {
+                    const float4 ri = *reinterpret_cast<const float4 *>(R + i * C::LD + j);
+                    *reinterpret_cast<float4 *>(P + i * C::LD + j) =
+                        make_float4(0.5f * (ri.x + R[j * C::LD + i]), 0.5f * (ri.y + R[(j + 1) * C::LD + i]),
+                                    0.5f * (ri.z + R[(j + 2) * C::LD + i]), 0.5f * (ri.w + R[(j + 3) * C::LD + i]));
+                }
+        }
+        __syncwarp();
+        // binary powering: P runs through D_1, D_2, D_4, ...; R collects the
+        // set bits of S
+        bool have_r = false;
+        int s = a.steps;
+#pragma unroll 1
+        while (true) {
+            if (s & 1) {
+                if (!have_r) {
+                    if (active) {
+#pragma unroll 1
+                        for (int i = t; i < N; i += C::TILES)
+#pragma unroll
+                            for (int j = 0; j < N; j += 4)
+                                *reinterpret_cast<float4 *>(R + i * C::LD + j) =
+                                    *reinterpret_cast<const float4 *>(P + i * C::LD + j);
+                    }
+                    have_r = true;
+                } else {
+                    sym_gemm<N>(R, P, R, 1.0f, P, R, bi, bj, active);  // R + P + R P
+                }
+                __syncwarp();
+            }
+            s >>= 1;
+            if (!s) break;
+            sym_gemm<N>(P, P, P, 2.0f, nullptr, P, bi, bj, active);  // 2 P + P P
+            __syncwarp();
+        }
+        prop_store<N>(a, R, C::LD, u, live, t, C::TILES);
         __syncwarp();
     }
 }
@@ -479,20 +702,28 @@ __global__ void __launch_bounds__(ApplyCfg<N>::WARPS * 32) k_prop_apply(const __
     }
 }
 
-template <int N>
-cudaError_t launch_build(const PropArgs &a, int num_sms, cudaStream_t s) {
-    using C = PropCfg<N>;
-    cudaError_t e = cudaFuncSetAttribute(k_prop_build<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+template <typename C, typename K>
+cudaError_t launch_build_kernel(K kernel, const PropArgs &a, int num_sms, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_prop_build<N>, C::WARPS * 32, C::SMEM);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, C::WARPS * 32, C::SMEM);
     if (e != cudaSuccess) return e;
     const long long per_block = (long long)C::WARPS * C::CPW;
     long long blocks = (a.classes + per_block - 1) / per_block;
     const long long cap = (long long)num_sms * (per_sm > 0 ? per_sm : 1);
     if (blocks > cap) blocks = cap;
-    k_prop_build<N><<<(unsigned)blocks, C::WARPS * 32, C::SMEM, s>>>(a);
+    kernel<<<(unsigned)blocks, C::WARPS * 32, C::SMEM, s>>>(a);
     return cudaGetLastError();
+}
+
+// N = 16, 32: symmetric products; N = 64: full products (one warp a class)
+template <int N>
+cudaError_t launch_build(const PropArgs &a, int num_sms, cudaStream_t s) {
+    if constexpr (N == 64)
+        return launch_build_kernel<PropCfg<N>>(k_prop_build<N>, a, num_sms, s);
+    else
+        return launch_build_kernel<SymCfg<N>>(k_prop_build_sym<N>, a, num_sms, s);
 }
 
 template <int N>
@@ -525,14 +756,14 @@ long long se2n_prop_classes(int H, int W, bool half) {
 cudaError_t se2n_prop_prepare(int N) {
     switch (N) {
         case 16:
-            return cudaFuncSetAttribute(se2n::k_prop_build<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        se2n::PropCfg<16>::SMEM) == cudaSuccess
+            return cudaFuncSetAttribute(se2n::k_prop_build_sym<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        se2n::SymCfg<16>::SMEM) == cudaSuccess
                        ? cudaFuncSetAttribute(se2n::k_prop_apply<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               se2n::ApplyCfg<16>::SMEM)
                        : cudaGetLastError();
         case 32:
-            return cudaFuncSetAttribute(se2n::k_prop_build<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        se2n::PropCfg<32>::SMEM) == cudaSuccess
+            return cudaFuncSetAttribute(se2n::k_prop_build_sym<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        se2n::SymCfg<32>::SMEM) == cudaSuccess
                        ? cudaFuncSetAttribute(se2n::k_prop_apply<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               se2n::ApplyCfg<32>::SMEM)
                        : cudaGetLastError();
