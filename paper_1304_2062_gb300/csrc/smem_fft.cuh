@@ -12,11 +12,11 @@
 // butterflies' inputs in registers.
 //
 // Layout: element i of transform n at n (L + 1) + (i ^ s(i / 16)), with
-// s(m) = (m mod 8) + 8 (bit 2 of m): planes L + 1 apart put the N elements
-// of one index on different banks (the per-frequency work between the
-// transforms), and the XOR inside each run of 16 keeps the three access
-// patterns of the passes (consecutive; stride 8; runs of 8 that are 64
-// apart) free of bank conflicts.
+// s(m) = (m mod 8) + 8 (bit 2 of m xor bit 3 of m): planes L + 1 apart put
+// the N elements of one index on different banks (the per-frequency work
+// between the transforms), and the XOR inside each run of 16 keeps the access
+// patterns of the passes (consecutive; stride 8; stride 16; runs of 8 that
+// are 64 apart) free of bank conflicts.
 #pragma once
 
 namespace se2n {
@@ -25,7 +25,7 @@ namespace se2n {
 template <int L>
 __device__ __forceinline__ int xoff(int i) {
     const int m = i >> 4;
-    return i ^ ((m & 7) | ((m << 1) & 8));
+    return i ^ ((m & 7) | (((m << 1) ^ m) & 8));
 }
 template <int L>
 __device__ __forceinline__ int xsm(int e) {
@@ -54,7 +54,17 @@ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 
-// V_k = sum_n v_n exp(DIR 2 pi i n k / R), in place, for R = 2, 4, 8.
+// z times exp(DIR 2 pi i m / 16) for m = 1, 2, 3, 6, 9 (the inner twiddles of
+// the 16-point DFT), from cos(pi / 8), sin(pi / 8) and cos(pi / 4)
+template <int DIR, int M>
+__device__ __forceinline__ float2 w16(float2 z) {
+    constexpr float c8 = 0.92387953251128674f, s8 = 0.38268343236508977f, h = 0.70710678118654752f;
+    constexpr float wr = M == 1 ? c8 : M == 2 ? h : M == 3 ? s8 : M == 6 ? -h : -c8;
+    constexpr float wi = DIR * (M == 1 ? s8 : M == 2 ? h : M == 3 ? c8 : M == 6 ? h : -s8);
+    return make_float2(fmaf(z.x, wr, -z.y * wi), fmaf(z.x, wi, z.y * wr));
+}
+
+// V_k = sum_n v_n exp(DIR 2 pi i n k / R), in place, for R = 2, 4, 8, 16.
 template <int R, int DIR>
 __device__ __forceinline__ void dft_small(float2 (&v)[R]) {
     if constexpr (R == 2) {
@@ -68,6 +78,33 @@ __device__ __forceinline__ void dft_small(float2 (&v)[R]) {
         v[2] = csub(t0, t2);
         v[1] = cadd(t1, t3);
         v[3] = csub(t1, t3);
+    } else if constexpr (R == 16) {
+        // n = a + 4 m, k = b + 4 c: 4-point DFTs over m, the twiddle
+        // exp(DIR 2 pi i a b / 16), 4-point DFTs over a, output b + 4 c
+        float2 u[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            float2 t[4] = {v[a], v[a + 4], v[a + 8], v[a + 12]};
+            dft_small<4, DIR>(t);
+#pragma unroll
+            for (int b = 0; b < 4; ++b) u[a][b] = t[b];
+        }
+        u[1][1] = w16<DIR, 1>(u[1][1]);
+        u[1][2] = w16<DIR, 2>(u[1][2]);
+        u[1][3] = w16<DIR, 3>(u[1][3]);
+        u[2][1] = w16<DIR, 2>(u[2][1]);
+        u[2][2] = quarter<DIR>(u[2][2]);
+        u[2][3] = w16<DIR, 6>(u[2][3]);
+        u[3][1] = w16<DIR, 3>(u[3][1]);
+        u[3][2] = w16<DIR, 6>(u[3][2]);
+        u[3][3] = w16<DIR, 9>(u[3][3]);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            float2 t[4] = {u[0][b], u[1][b], u[2][b], u[3][b]};
+            dft_small<4, DIR>(t);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) v[b + 4 * c] = t[c];
+        }
     } else {
         // even and odd halves, then V_k = E_k + w^k O_k, V_{k+4} = E_k - w^k O_k
         float2 e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
@@ -142,10 +179,16 @@ __device__ __forceinline__ void fft_pass(float2 *X, const float2 *tw, int tid) {
 }
 
 // The N DFTs of length L (32 = 8 x 4, 64 = 8 x 8, 128 = 8 x 8 x 2,
-// 256 = 8 x 8 x 4, 512 = 8 x 8 x 8). The caller synchronises before and after.
+// 256 = 16 x 16, 512 = 8 x 8 x 8). The caller synchronises before and after.
 template <int T, int N, int L, int DIR, int TS>
 __device__ __forceinline__ void fft_smem(float2 *X, const float2 *tw, int tid) {
     static_assert(L == 32 || L == 64 || L == 128 || L == 256 || L == 512, "transform length");
+    if constexpr (L == 256) {
+        fft_pass<T, N, L, 16, 1, DIR, TS>(X, tw, tid);
+        __syncthreads();
+        fft_pass<T, N, L, 16, 16, DIR, TS>(X, tw, tid);
+        return;
+    }
     fft_pass<T, N, L, 8, 1, DIR, TS>(X, tw, tid);
     __syncthreads();
     if constexpr (L == 32) {
