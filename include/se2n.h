@@ -377,8 +377,10 @@ SE2N_API se2n_status se2n_batch_create(se2n_batch **out, const se2n_image_desc *
 SE2N_API se2n_status se2n_batch_run(se2n_batch *b);
 
 /* The same results computed the plain way: se2n_inpaint on each image in
- * turn (one diffusion launch per image and interval). Bitwise equal to
- * se2n_batch_run; kept as the comparison baseline. */
+ * turn (one diffusion launch per image and interval; images that take
+ * propagators use the separate apply, and each shape's propagators are
+ * built again, as in se2n_batch_run). Bitwise equal to se2n_batch_run; kept
+ * as the comparison baseline. */
 SE2N_API se2n_status se2n_batch_run_per_image(se2n_batch *b);
 
 /* One persistent diffusion launch over the batch's volumes as they stand

@@ -1396,6 +1396,8 @@ se2n_status se2n_batch_run(se2n_batch *b) {
 
 se2n_status se2n_batch_run_per_image(se2n_batch *b) {
     if (!b) return SE2N_EINVAL;
+    // the same work as the graph: every shape's propagators built again
+    for (se2n_plan *pl : b->plans) pl->prop_valid = false;
     for (int i = 0; i < b->count; ++i) {
         se2n_params q = b->p;
         q.N = b->imgs[i].N;
