@@ -302,11 +302,14 @@ def run_ours(args, rank, world, local_rank):
                                  "achieved_gbs": round(row_bytes / r_s / 1e9, 1), "peak_gbs": hbm,
                                  "frac": round(row_bytes / r_s / 1e9 / hbm, 4) if hbm else None,
                                  "traffic": stored_traffic("row_pass")},
-                    "build": {"kernel": f"k_prop_build<{w.N}> ({classes} classes, FP32 products)", "bound": "alu",
+                    "build": {"kernel": f"k_prop_build_sym<{w.N}> ({classes} classes, FP32 symmetric products; "
+                                        "on a side stream, overlapping the orientation and the first row pass)",
+                              "bound": "alu",
                               "avg_launch_ms": round(b_s * 1e3, 4), "flops_per_launch": flops,
                               "flops_basis": "classes x (squarings + combinations) x 2 N^3, "
                               f"S = {w.steps}: {w.steps.bit_length() - 1} squarings, "
-                              f"{bin(w.steps).count('1') - 1} combinations",
+                              f"{bin(w.steps).count('1') - 1} combinations (full products; the symmetric kernel "
+                              "performs the 10 upper-triangle tiles of 16 of each)",
                               "achieved_tflops": round(flops / b_s / 1e12, 3), "peak_tflops": round(peak, 3),
                               "frac": round(flops / b_s / 1e12 / peak, 4), "peak_basis": peak_basis,
                               "traffic": stored_traffic("prop_build")},
@@ -351,7 +354,11 @@ def run_ours(args, rank, world, local_rank):
                 torch.cuda.synchronize(dev)
                 return sum(a.elapsed_time(b) for a, b in evs) / 3
             se2n.se2n_inpaint(plan, f_d, m_d, None, prm, vol, out)
+            torch.cuda.synchronize(dev)
+            se2n.se2n_plan_profile(plan, True)
             kept = timed3(lambda: se2n.se2n_inpaint(plan, f_d, m_d, None, prm, vol, out))
+            kprof = se2n.se2n_plan_profile_read(plan, reset=True)
+            se2n.se2n_plan_profile(plan, False)
             prm_s = se2n.se2n_params_default(N=w.N, beta=w.beta, T=w.T, steps=w.steps, rounds=w.rounds, eps=w.eps,
                                              sigma_smooth=w.sigma, dynamic=int(dynamic))
             se2n.se2n_inpaint(plan, f_d, m_d, None, prm_s, vol, out)
@@ -363,6 +370,21 @@ def run_ours(args, rank, world, local_rank):
         sd_s = sprof["diffuse"][0] / sprof["diffuse"][1] / 1e3
         s_ach = FLOPS_PER_UPDATE * updates_per_launch / sd_s / 1e12
         result["propagators_kept"] = {"ms_per_step": round(kept, 4), "value": world * w.updates() / (kept / 1e3)}
+        # the row and column passes timed where nothing runs beside them (in the
+        # timed inpaints the build overlaps the orientation and the first row pass)
+        c_s = kprof["diffuse"][0] / kprof["diffuse"][1] / 1e3
+        r_s = kprof["fft"][0] / kprof["fft"][1] / 1e3
+        hbm = roofline["peak"]
+        col_bytes, row_bytes = roofline["bytes_per_launch"], roofline["row_pass"]["bytes_per_launch"]
+        roofline.update({"achieved": round(col_bytes / c_s / 1e9, 1), "avg_launch_ms": round(c_s * 1e3, 4),
+                         "frac": round(col_bytes / c_s / 1e9 / hbm, 4) if hbm else None,
+                         "frac_of_fp32_peak": round(roofline["flops_per_launch"] / c_s / 1e12 / peak, 4),
+                         "timed_on": "the inpaints that reuse the propagators (CUDA events around each launch)"})
+        roofline["row_pass"].update({"avg_launch_ms": round(r_s * 1e3, 4),
+                                     "achieved_gbs": round(row_bytes / r_s / 1e9, 1),
+                                     "frac": round(row_bytes / r_s / 1e9 / hbm, 4) if hbm else None,
+                                     "timed_on": "the inpaints that reuse the propagators; the average over all "
+                                                 "row passes of an inpaint (lift and projection included)"})
         result["step_by_step"] = {
             "ms_per_step": round(stepwise, 4), "value": world * w.updates() / (stepwise / 1e3),
             "roofline": {"bound": "alu", "kernel": "k_diffuse_x2<32,2,false>", "avg_launch_ms": round(sd_s * 1e3, 4),

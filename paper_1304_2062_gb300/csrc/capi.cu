@@ -31,7 +31,9 @@ struct StageTimer {
     se2n_plan *plan;
     int stage;
     bool on;
-    StageTimer(se2n_plan *p, int s) : plan(p), stage(s), on(p->profiling) {
+    cudaStream_t stream;
+    StageTimer(se2n_plan *p, int s, cudaStream_t st = nullptr)
+        : plan(p), stage(s), on(p->profiling), stream(st ? st : p->stream) {
         if (!on) return;
         std::vector<cudaEvent_t> &ev = plan->stage_ev[stage];
         const size_t need = 2 * (size_t)plan->stage_used[stage] + 2;
@@ -44,12 +46,12 @@ struct StageTimer {
             }
             ev.push_back(e);
         }
-        cudaEventRecord(ev[need - 2], plan->stream);
+        cudaEventRecord(ev[need - 2], stream);
     }
     ~StageTimer() {
         if (!on) return;
         const int u = plan->stage_used[stage]++;
-        cudaEventRecord(plan->stage_ev[stage][2 * u + 1], plan->stream);
+        cudaEventRecord(plan->stage_ev[stage][2 * u + 1], stream);
     }
 };
 
@@ -139,9 +141,39 @@ PropArgs prop_args(se2n_plan *plan, float2 *vol, double beta, double bdt, int st
     return a;
 }
 
+// The plan's side stream and the events that fork work to it and join it back.
+se2n_status side_ensure(se2n_plan *plan) {
+    if (plan->side) return SE2N_OK;
+    cudaStream_t st = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess) {
+        (void)cudaGetLastError();
+        if (st) cudaStreamDestroy(st);
+        if (fork) cudaEventDestroy(fork);
+        return SE2N_ECUDA;
+    }
+    plan->side = st;
+    plan->ev_fork = fork;
+    plan->ev_join = join;
+    return SE2N_OK;
+}
+
+// The plan's stream waits for the propagators built on the side stream.
+void prop_join(se2n_plan *plan) {
+    if (!plan->join_pending) return;
+    cudaStreamWaitEvent(plan->stream, plan->ev_join, 0);
+    plan->join_pending = false;
+}
+
 // The S-step propagators of every class of frequencies, built when beta dt,
-// S, the spectrum half or the storage changed.
-se2n_status prop_ensure(se2n_plan *plan, double beta, double bdt, int steps, bool half, bool rows) {
+// S, the spectrum half or the storage changed. With side = true the build
+// runs on the plan's side stream after everything queued on the plan's
+// stream so far (it reads nothing that work writes), overlapping what the
+// plan's stream does next until prop_join.
+se2n_status prop_ensure(se2n_plan *plan, double beta, double bdt, int steps, bool half, bool rows,
+                        bool side = false) {
     if (!se2n_prop_supported(plan->N)) return SE2N_EUNSUPPORTED;
     SE2N_TRY(prop_reserve(plan, half, rows));
     if (plan->prop_valid && plan->prop_beta == beta && plan->prop_bdt == bdt && plan->prop_steps == steps &&
@@ -149,9 +181,24 @@ se2n_status prop_ensure(se2n_plan *plan, double beta, double bdt, int steps, boo
         return SE2N_OK;
     plan->prop_valid = false;
     const PropArgs a = prop_args(plan, nullptr, beta, bdt, steps, half, rows);
-    StageTimer timer(plan, SE2N_STAGE_PROPAGATOR);
-    plan->kernels += 1;
-    SE2N_TRY(cuda_status(plan, se2n_launch_prop_build(plan->N, a, plan->num_sms, plan->stream)));
+    cudaStream_t st = plan->stream;
+    if (side) {
+        SE2N_TRY(side_ensure(plan));
+        prop_join(plan);  // an earlier build on the side stream, if any
+        if (cudaEventRecord(plan->ev_fork, plan->stream) != cudaSuccess ||
+            cudaStreamWaitEvent(plan->side, plan->ev_fork, 0) != cudaSuccess)
+            return SE2N_ECUDA;
+        st = plan->side;
+    }
+    {
+        StageTimer timer(plan, SE2N_STAGE_PROPAGATOR, st);
+        plan->kernels += 1;
+        SE2N_TRY(cuda_status(plan, se2n_launch_prop_build(plan->N, a, plan->num_sms, st)));
+    }
+    if (side) {
+        if (cudaEventRecord(plan->ev_join, plan->side) != cudaSuccess) return SE2N_ECUDA;
+        plan->join_pending = true;
+    }
     plan->prop_valid = true;
     plan->prop_beta = beta;
     plan->prop_bdt = bdt;
@@ -164,6 +211,7 @@ se2n_status prop_ensure(se2n_plan *plan, double beta, double bdt, int steps, boo
 // The propagators applied once to the spectrum vol (by diagonals).
 se2n_status propagate_impl(se2n_plan *plan, float2 *vol, double beta, double bdt, int steps, bool half) {
     SE2N_TRY(prop_ensure(plan, beta, bdt, steps, half, false));
+    prop_join(plan);
     const PropArgs a = prop_args(plan, vol, beta, bdt, steps, half, false);
     StageTimer timer(plan, SE2N_STAGE_DIFFUSE);
     plan->kernels += 1;
@@ -251,6 +299,7 @@ se2n_status col_diffuse(se2n_plan *plan, double beta, double T, int steps) {
     const double bdt = beta * (T / steps);
     if (!(bdt >= 1e-30 && bdt <= 1e3)) return SE2N_ENUMERIC;
     SE2N_TRY(prop_ensure(plan, beta, bdt, steps, true, true));
+    prop_join(plan);
     ColArgs a;
     a.col = plan->colbuf;
     a.D = plan->prop_D;
@@ -489,6 +538,15 @@ se2n_status inpaint_impl(se2n_plan *plan, const float *f, const uint8_t *mask, c
     const long long HW = plan->HW;
     const int N = plan->N;
     const uint8_t *bins = bins_in;
+    const bool col = allow_col && col_path(plan, p);
+    if (col) {
+        SE2N_TRY(col_ensure(plan));
+        // the propagators depend on beta dt and S only: built on the side
+        // stream while the orientation and the lift run
+        const double bdt = p->beta * (p->T / p->rounds) / p->steps;
+        if (p->T > 0.0 && bdt >= 1e-30 && bdt <= 1e3)
+            SE2N_TRY(prop_ensure(plan, p->beta, bdt, p->steps, true, true, true));
+    }
     if (!bins) {
         SE2N_TRY(orient_impl(plan, f, mask, p->sigma_smooth, p->flat_tol, plan->bins));
         bins = plan->bins;
@@ -508,14 +566,13 @@ se2n_status inpaint_impl(se2n_plan *plan, const float *f, const uint8_t *mask, c
         // even in the frequency): integrate the half l = 0 .. W/2 only, with
         // real-to-complex transforms, and let the inverse transform rebuild
         // the rest.
-        if (allow_col && col_path(plan, p)) {
+        if (col) {
             // With propagators on a supported shape the volume stays
             // row-transformed between intervals: a row pass (lift, or
             // inverse DFT along x, restoration and forward DFT along x) and
             // a column pass (DFT along y, propagators, inverse DFT along y)
             // an interval, the projection fused into the last row pass.
             // Dynamic restoration takes the real volume in vol between.
-            SE2N_TRY(col_ensure(plan));
             RowArgs r = row_args(plan, f, mask, bins, inv_hw, eps, guard);
             r.in_mode = SE2N_ROW_IN_LIFT;
             SE2N_TRY(row_pass(plan, r));
@@ -593,6 +650,12 @@ void free_plan(se2n_plan *plan) {
     if (plan->fft_two) cufftDestroy(plan->fft_two);
     if (plan->fft_r2c) cufftDestroy(plan->fft_r2c);
     if (plan->fft_c2r) cufftDestroy(plan->fft_c2r);
+    if (plan->side) {
+        cudaStreamSynchronize(plan->side);
+        cudaStreamDestroy(plan->side);
+        cudaEventDestroy(plan->ev_fork);
+        cudaEventDestroy(plan->ev_join);
+    }
     cudaFree(plan->colbuf);
     cudaFree(plan->col_tw);
     cudaFree(plan->row_tw);
@@ -845,6 +908,7 @@ se2n_status se2n_plan_drop_propagators(se2n_plan *plan, int free_memory) {
     SE2N_TRY(check_plan(plan));
     plan->prop_valid = false;
     if (free_memory && plan->prop_D) {
+        prop_join(plan);  // a build still running on the side stream
         SE2N_TRY(cuda_status(plan, cudaStreamSynchronize(plan->stream)));
         cudaFree(plan->prop_D);
         plan->prop_D = nullptr;

@@ -51,6 +51,12 @@ struct se2n_plan {
     int prop_steps;
     bool prop_half;
     bool prop_rows;        // stored as full rows (the column pass) or by diagonals
+    // side stream for a build that overlaps the start of an inpaint, and the
+    // events that order it after the plan's stream and the plan's stream
+    // after it (join_pending until the plan's stream waits on ev_join)
+    cudaStream_t side;
+    cudaEvent_t ev_fork, ev_join;
+    bool join_pending;
     // row and column passes of the Hermitian half (se2n_inpaint with
     // propagators): the row-transformed volume [Wc][H][N] complex
     float2 *colbuf;
