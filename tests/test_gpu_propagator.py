@@ -186,3 +186,33 @@ def test_row_and_column_passes_match_oracle(H, W, N, dynamic, final_mix, proj, r
     assert prof["fft"][1] == (6 if dynamic else 4)
     assert mx <= MAX_REL_RESTORED
     assert r2 <= REL_L2
+
+
+def test_side_stream_build_is_ordered_with_the_plan_stream():
+    """se2n_inpaint builds its propagators on a side stream while the
+    orientation and the lift run. Inpaints queued back to back with a new
+    beta dt each (every one forks a build while the previous one's passes
+    may still run), a drop with its memory freed in between, and a plan
+    destroyed with work still queued must all give the oracle's results."""
+    H, W, N = 64, 128, 32
+    w = synth.workload_512(H=H, W=W, steps=40, rounds=2)
+    f32 = w.f.astype(np.float32)
+    f64 = f32.astype(np.float64)
+    bins = oracle.orient(f64, w.mask, N, 1.0, 0, 1e-4)["bins"]
+    plan = se2n.se2n_plan_create(H, W, N)
+    f_d, m_d, b_d = t_f32(f32), t_u8(w.mask), t_u8(bins)
+    vol = torch.empty((N, H, W), dtype=torch.complex64, device="cuda")
+    outs, refs = [], []
+    for i, T in enumerate([2.0, 4.0, 4.0, 6.0]):
+        p = oracle.Params(N=N, beta=0.25, T=T, steps=40, rounds=2)
+        out = torch.empty((H, W), dtype=torch.float32, device="cuda")
+        se2n.se2n_inpaint(plan, f_d, m_d, b_d, _params(p), vol, out)   # no synchronisation in between
+        if i == 1:
+            se2n.se2n_plan_drop_propagators(plan, True)
+        outs.append(out)
+        refs.append(oracle.inpaint(f64, w.mask, p, bins=bins)["out"])
+    plan.close()   # destroys the plan (and its side stream) with nothing synchronised yet
+    for out, ref in zip(outs, refs):
+        got = host(out)
+        assert rel_l2(got, ref) <= REL_L2
+        assert np.abs(got - ref).max() <= MAX_REL_RESTORED * np.abs(f64).max()
