@@ -284,6 +284,10 @@ RowArgs row_args(se2n_plan *plan, const float *f, const uint8_t *mask, const uin
     r.proj = SE2N_PROJ_MAX;
     r.reinject = 0;
     r.scale_proj = 1.0f;
+    r.rf = nullptr;
+    r.rmask = nullptr;
+    r.h_out = nullptr;
+    r.amax_out = nullptr;
     return r;
 }
 
@@ -496,6 +500,17 @@ se2n_status dr_step(se2n_plan *plan, DrState &d, const float2 *vol, float scale,
     return cuda_status(plan, e);
 }
 
+// The growth step itself, from h and amax already in d (the row pass with
+// SE2N_ROW_OUT_H computes them).
+se2n_status dr_grow_only(se2n_plan *plan, DrState &d) {
+    StageTimer timer(plan, SE2N_STAGE_DR);
+    plan->kernels += 1;
+    const cudaError_t e = se2n_launch_dr_grow(d.h, d.amax, d.mask[d.cur], d.mask[d.cur ^ 1], d.fref, d.bins, plan->H,
+                                              plan->W, plan->stream);
+    d.cur ^= 1;
+    return cuda_status(plan, e);
+}
+
 // The restoration at the end of an interval: static on (f, mask, bins), or,
 // with dr, one growth step of the good set and then the static restoration
 // towards the references of the grown set.
@@ -572,25 +587,34 @@ se2n_status inpaint_impl(se2n_plan *plan, const float *f, const uint8_t *mask, c
             // inverse DFT along x, restoration and forward DFT along x) and
             // a column pass (DFT along y, propagators, inverse DFT along y)
             // an interval, the projection fused into the last row pass.
-            // Dynamic restoration takes the real volume in vol between.
+            // Dynamic restoration adds a row pass that gives the image
+            // value and its argmax angle before each growth step.
             RowArgs r = row_args(plan, f, mask, bins, inv_hw, eps, guard);
             r.in_mode = SE2N_ROW_IN_LIFT;
             SE2N_TRY(row_pass(plan, r));
             SE2N_TRY(col_diffuse(plan, p->beta, Tr, p->steps));
             for (int i = 1; i <= p->rounds; ++i) {
                 const bool last = i == p->rounds;
-                r = row_args(plan, f, mask, bins, inv_hw, eps, guard);
-                if (dr) {
-                    r.out_mode = SE2N_ROW_OUT_REAL;
-                    r.real_out = (float *)vol;
-                    SE2N_TRY(row_pass(plan, r));
-                    if (last) break;
-                    SE2N_TRY(restore_impl(plan, dr, vol, f, mask, bins, inv_hw, eps, guard, true));
+                const float *rf = f;
+                const uint8_t *rmask = mask, *rbins = bins;
+                if (dr && (!last || p->final_mix)) {
+                    // a growth step: the image value h and its argmax angle
+                    // from one row pass, then the set grows; the restoration
+                    // below pulls the grown set to its references
                     r = row_args(plan, f, mask, bins, inv_hw, eps, guard);
-                    r.in_mode = SE2N_ROW_IN_REAL;
-                    r.real_in = (const float *)vol;
+                    r.out_mode = SE2N_ROW_OUT_H;
+                    r.h_out = dr->h;
+                    r.amax_out = dr->amax;
                     SE2N_TRY(row_pass(plan, r));
-                } else if (last) {
+                    SE2N_TRY(dr_grow_only(plan, *dr));
+                    rf = dr->fref;
+                    rmask = dr->mask[dr->cur];
+                    rbins = dr->bins;
+                }
+                r = row_args(plan, rf, rmask, rbins, inv_hw, eps, guard);
+                r.rf = f;     // reinjection keeps the given known pixels
+                r.rmask = mask;
+                if (last) {
                     r.mix = p->final_mix;
                     r.out_mode = SE2N_ROW_OUT_PROJ;
                     r.proj_out = out;
@@ -598,10 +622,9 @@ se2n_status inpaint_impl(se2n_plan *plan, const float *f, const uint8_t *mask, c
                     r.reinject = p->reinject;
                     r.scale_proj = p->final_mix ? 1.0f : inv_hw;
                     return row_pass(plan, r);
-                } else {
-                    r.mix = 1;
-                    SE2N_TRY(row_pass(plan, r));
                 }
+                r.mix = 1;
+                SE2N_TRY(row_pass(plan, r));
                 SE2N_TRY(col_diffuse(plan, p->beta, Tr, p->steps));
             }
         } else {

@@ -9,7 +9,9 @@
 //      restore.cuh, with h(t) the maximum over the angles);
 //   3. writes the forward real DFT along x back to the row-transformed
 //      volume, or the real row, or the projection over the angles (max or
-//      mean, with the known pixels reinjected on request).
+//      mean, with the known pixels reinjected on request), or the image
+//      value h = max over the angles and the angle of its first maximum
+//      (the input of a growth step of dynamic restoration).
 // So the restoration between two intervals (Section 5.2) costs one read and
 // one write of the half spectrum, and the lift and the projection none.
 //
@@ -164,12 +166,33 @@ __global__ void __launch_bounds__(kRowThreads) k_row(const __grid_constant__ Row
                 a1 /= (float)N;
             }
             if (a.reinject) {
-                const float2 fv = reinterpret_cast<const float2 *>(a.f + row)[m];
-                const uchar2 mk = reinterpret_cast<const uchar2 *>(a.mask + row)[m];
+                const float2 fv = reinterpret_cast<const float2 *>((a.rf ? a.rf : a.f) + row)[m];
+                const uchar2 mk = reinterpret_cast<const uchar2 *>((a.rmask ? a.rmask : a.mask) + row)[m];
                 if (mk.x) a0 = fv.x;
                 if (mk.y) a1 = fv.y;
             }
             reinterpret_cast<float2 *>(a.proj_out + row)[m] = make_float2(a0, a1);
+        }
+    } else if (a.out_mode == SE2N_ROW_OUT_H) {
+        for (int m = tid; m < WH; m += T) {
+            const float2 *Zm = Z + xoff<WH>(m);
+            float b0 = -INFINITY, b1 = -INFINITY;
+            int r0 = 0, r1 = 0;
+#pragma unroll 8
+            for (int n = 0; n < N; ++n) {
+                const float2 v = Zm[n * (WH + 1)];
+                const float v0 = v.x * a.scale, v1 = v.y * a.scale;
+                if (v0 > b0) {
+                    b0 = v0;
+                    r0 = n;
+                }
+                if (v1 > b1) {
+                    b1 = v1;
+                    r1 = n;
+                }
+            }
+            reinterpret_cast<float2 *>(a.h_out + row)[m] = make_float2(b0, b1);
+            reinterpret_cast<uchar2 *>(a.amax_out + row)[m] = make_uchar2((uint8_t)r0, (uint8_t)r1);
         }
     } else {
         fft_smem<T, N, WH, -1, 2>(Z, tws, tid);

@@ -145,7 +145,7 @@ cudaError_t se2n_launch_col_prop(int N, const ColArgs &a, cudaStream_t s);
 // image (inverse real DFT along x), restored, and transformed again, or the
 // row comes from the lift, or goes to the projection or to the real volume.
 enum { SE2N_ROW_IN_LIFT = 0, SE2N_ROW_IN_SPEC = 1, SE2N_ROW_IN_REAL = 2 };
-enum { SE2N_ROW_OUT_SPEC = 0, SE2N_ROW_OUT_REAL = 1, SE2N_ROW_OUT_PROJ = 2 };
+enum { SE2N_ROW_OUT_SPEC = 0, SE2N_ROW_OUT_REAL = 1, SE2N_ROW_OUT_PROJ = 2, SE2N_ROW_OUT_H = 3 };
 struct RowArgs {
     const float2 *spec_in;  // [Wc][H][N] complex (IN_SPEC)
     float2 *spec_out;       // [Wc][H][N] complex (OUT_SPEC); may be spec_in
@@ -161,6 +161,10 @@ struct RowArgs {
     float scale, eps, guard;
     int proj, reinject;     // OUT_PROJ: max or mean over the angles of scale_proj * value
     float scale_proj;
+    const float *rf;        // OUT_PROJ: the reinjected image and its known pixels
+    const uint8_t *rmask;   //   (f and mask when null)
+    float *h_out;           // OUT_H: [H][W] max over the angles of scale * value
+    uint8_t *amax_out;      //   and the angle of its first maximum
 };
 bool se2n_row_supported(int N, int W);
 cudaError_t se2n_row_prepare(int N, int W);

@@ -91,11 +91,11 @@ def test_overlapping_masks_are_rejected():
     plan.close()
 
 
-def _params(p, full=0, dynamic=1):
+def _params(p, full=0, dynamic=1, flags=0):
     return se2n.se2n_params_default(N=p.N, beta=p.beta, T=p.T, steps=p.steps, rounds=p.rounds, eps=p.eps,
                                     sigma_smooth=p.sigma, flat_tol=p.flat_tol, proj=p.proj,
                                     final_mix=p.final_mix, guard=p.guard, reinject=p.reinject,
-                                    full_spectrum=full, dynamic=dynamic)
+                                    full_spectrum=full, dynamic=dynamic, diffuse_flags=flags)
 
 
 def _gpu_inpaint(f32, mask, bins, prm):
@@ -166,14 +166,16 @@ def test_batch_with_dynamic_restoration_is_bitwise_per_image():
         assert not np.array_equal(x, z)       # the dynamic run is a different result
 
 
-@pytest.mark.parametrize("full", [0, 1])
-def test_full_512_N32_ten_rounds_against_stored_oracle(full):
+@pytest.mark.parametrize("full,flags", [(0, 0), (1, 0), (0, se2n.SE2N_DIFFUSE_PROPAGATOR)])
+def test_full_512_N32_ten_rounds_against_stored_oracle(full, flags):
     """The full workload (512x512, N=32, beta=0.25, 10 intervals of 500
     steps) with dynamic restoration against the FP64 oracle's result written
     by tests/golden/make_references.py: nine growth steps, about 1e6
     decisions, 187,433 of the 222,213 corrupted pixels join, and 1,575
     decisions come within 1e-5 of a tie (the closest 1.4e-8). Such a decision
     may go the other way on FP32 images and both results are correct, so:
+    (step by step on both spectrum layouts, and with propagators on the row
+    and column passes, where a row pass gives each growth step its input)
     every pixel outside the tolerance must lie within 8 px of one of those
     near-tie decisions, there are few of them, and all pixels farther than
     4 px from them meet the restored-result tolerance."""
@@ -183,7 +185,7 @@ def test_full_512_N32_ten_rounds_against_stored_oracle(full):
     g = np.load(GOLDEN)
     w = synth.workload_512()
     p = oracle.Params(N=32, beta=0.25, T=20.0, steps=500, rounds=10, dynamic=1)
-    got = _gpu_inpaint(w.f.astype(np.float32), w.mask, g["bins"], _params(p, full))
+    got = _gpu_inpaint(w.f.astype(np.float32), w.mask, g["bins"], _params(p, full, flags=flags))
     ref = g["out"].astype(np.float64)
     d = np.abs(got - ref) / np.abs(w.f).max()
     off = d > MAX_REL_RESTORED
@@ -191,7 +193,7 @@ def test_full_512_N32_ten_rounds_against_stored_oracle(full):
     near = ndimage.binary_dilation(off, structure=np.ones((9, 9), dtype=bool))
     rest = ~near
     r2 = float(np.linalg.norm((got - ref)[rest]) / np.linalg.norm(ref[rest]))
-    print(f"512x512 dynamic full={full}: {int(off.sum())} pixels above {MAX_REL_RESTORED:g} (max {d.max():.2e}), "
+    print(f"512x512 dynamic full={full} flags={flags}: {int(off.sum())} pixels above {MAX_REL_RESTORED:g} (max {d.max():.2e}), "
           f"{float(to_tie[off].max()) if off.any() else 0.0:.1f} px from a near-tie at most; elsewhere "
           f"max {d[rest].max():.2e}, rel-L2 {r2:.2e}")
     assert off.sum() <= 50

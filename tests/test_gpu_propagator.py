@@ -164,8 +164,10 @@ def test_row_and_column_passes_match_oracle(H, W, N, dynamic, final_mix, proj, r
     passes: a row pass (lift, or inverse DFT along x, restoration and forward
     DFT along x, or projection) and a column pass (DFT along y, propagators,
     inverse DFT along y) an interval. Cases cover every radix mix of both
-    lengths (8 x 4 .. 8 x 8 x 8), the final restoration, mean projection,
-    reinjection and dynamic restoration (the real volume between passes)."""
+    lengths (8 x 4 .. 16 x 16), the final restoration, mean projection,
+    reinjection and dynamic restoration (a row pass gives the image value and
+    its argmax angle to each growth step; the restoration pulls the grown set
+    to its references while reinjection keeps the given known pixels)."""
     w = synth.workload_512(H=H, W=W, steps=60, rounds=3)
     p = oracle.Params(N=N, beta=0.25, T=6.0, steps=60, rounds=3, dynamic=dynamic, final_mix=final_mix, proj=proj,
                       reinject=reinject)
@@ -181,9 +183,11 @@ def test_row_and_column_passes_match_oracle(H, W, N, dynamic, final_mix, proj, r
     print(f"{H}x{W} N={N} dynamic={dynamic} final_mix={final_mix} proj={proj} reinject={reinject}: "
           f"max-abs/max|f| {mx:.2e}, rel-L2 {r2:.2e}")
     # one build; one column pass an interval; row passes: lift, one between
-    # intervals (two around the real volume with dynamic restoration), last
+    # intervals, last, and with dynamic restoration one more (image value and
+    # argmax) before each growth step
     assert prof["propagator"][1] == 1 and prof["diffuse"][1] == 3
-    assert prof["fft"][1] == (6 if dynamic else 4)
+    assert prof["fft"][1] == 4 + (2 + final_mix if dynamic else 0)
+    assert prof["dr"][1] == (2 + final_mix if dynamic else 0) and prof["mix"][1] == 0
     assert mx <= MAX_REL_RESTORED
     assert r2 <= REL_L2
 
