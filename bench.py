@@ -405,17 +405,22 @@ def run_ours(args, rank, world, local_rank):
                          "frac": round(s_ach / peak, 4), "traffic": stored_traffic(),
                          "flops_per_update": FLOPS_PER_UPDATE, "updates_per_launch": updates_per_launch}}
     if dynamic:
-        # one growth step reads the real volume once (max and argmax over the
-        # angles) and a few bytes a pixel of image and set state
+        # with propagators the image value h and its argmax angle come from a
+        # row pass (counted with the row passes); the growth kernel reads h,
+        # the argmax and the set and updates set, references and bins: about
+        # 16 bytes a pixel. Step by step, the growth step also reads the real
+        # volume once (4 N bytes a pixel) for the maximum.
         dr_ms, dr_calls = prof["dr"]
-        per_px = 4 * w.N + 16
+        per_px = 16 if prop else 4 * w.N + 16
         dr_s = dr_ms / dr_calls / 1e3
         result["dynamic_restoration"] = {
             "growth_steps_per_inpaint": dr_calls / args.steps,
             "ms_per_growth_step": round(dr_s * 1e3, 4),
             "algorithmic_bytes_per_growth_step": per_px * w.H * w.W,
             "hbm_gbs": round(per_px * w.H * w.W / dr_s / 1e9, 1),
-            "bytes_basis": "4 N bytes a pixel (the real volume, read once) + 16 (h, argmax, set, reference)"}
+            "bytes_basis": ("16 bytes a pixel (h 4, argmax 1, set in and out 2, reference and bin read and "
+                            "written 10); h and the argmax come from a row pass") if prop else
+                           "4 N bytes a pixel (the real volume, read once) + 16 (h, argmax, set, reference)"}
     result["clocks"] = clocks.summary()
 
     # end to end from pinned host buffers through se2n_inpaint_host
