@@ -593,11 +593,14 @@ def run_batch(args, rank, world, local_rank):
     return {"metric": METRIC, "value": total_updates / (ms / 1e3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "batch of 256 seeded images, sides U{128..1024}, N U{16,32,64}, "
+            "config": {"workload": "batch of 256 seeded images, sides from {128,256,384,512,768,1024}, N U{16,32,64}, "
                                    "60-90% corrupted, beta=0.25, T=2, 100 CN steps, 1 interval",
                        "images_this_rank": len(mine), "updates_per_step": total_updates,
                        "diffusion": ("S-step propagators for the shapes where they are estimated cheaper "
-                                     f"({info['prop_images']} images), the persistent step kernel for the rest")
+                                     f"({info['prop_images']} images; {info['fused_images']} of them, the "
+                                     "power-of-two planes with N = 16 or 32, whole inpaints on the row and column "
+                                     "passes, the others with the separate apply), the persistent step kernel for "
+                                     "the rest")
                        if prop else "the persistent step-by-step kernel for every image",
                        "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas"},
             "per_image_launches": {"ms_per_step": ms_per_image, "value": total_updates / (ms_per_image / 1e3),

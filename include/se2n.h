@@ -356,6 +356,7 @@ typedef struct se2n_batch_info {
     double volume_bytes;             /* device bytes of the lifted volumes */
     int prop_images;                 /* images integrated by their shape's propagators */
     double step_updates;             /* frequencies x N x steps of one interval the persistent kernel integrates */
+    int fused_images;                /* of prop_images, those whose whole inpaint runs on the row and column passes */
 } se2n_batch_info;
 
 /* Build a batch of `count` images. p->N is ignored (each image has its

@@ -1027,7 +1027,8 @@ struct se2n_batch {
     std::vector<uint8_t *> bins;
     std::vector<DrState> dr;  // per image, with dynamic restoration
     std::vector<char> img_prop;   // per image: integrated by its shape's propagators
-    int prop_images = 0;
+    std::vector<char> img_fused;  // per image: the whole inpaint on the row and column passes
+    int prop_images = 0, fused_images = 0;
     std::vector<BatchImage> h_imgs;
     float *d_tables = nullptr;
     BatchImage *d_imgs = nullptr;
@@ -1108,7 +1109,7 @@ se2n_status batch_interval(se2n_batch *b, double Tr, bool half) {
     if (b->prop_images < b->count) SE2N_TRY(batch_diffuse(b, p.steps, Tr));
     if (b->prop_images > 0)
         for (int i = 0; i < b->count; ++i)
-            if (b->img_prop[i])
+            if (b->img_prop[i] && !b->img_fused[i])
                 SE2N_TRY(diffuse_impl(b->plan_of[i], b->vols[i], p.beta, Tr, p.steps, p.diffuse_flags, half));
     return SE2N_OK;
 }
@@ -1122,7 +1123,9 @@ se2n_status batch_interval(se2n_batch *b, double Tr, bool half) {
 void choose_propagators(se2n_batch *b) {
     const se2n_params &p = b->p;
     b->img_prop.assign(b->count, 0);
+    b->img_fused.assign(b->count, 0);
     b->prop_images = 0;
+    b->fused_images = 0;
     if (!(p.diffuse_flags & SE2N_DIFFUSE_PROPAGATOR)) return;
     const bool half = !p.full_spectrum;
     const int S = p.steps;
@@ -1138,12 +1141,17 @@ void choose_propagators(se2n_batch *b) {
         const double classes = (double)se2n_prop_classes(pl->H, pl->W, half);
         const double build_s = classes * products * 2.0 * N * N * N / 30e12;
         const double apply_s = n_img * (double)p.rounds * (classes * 4.0 * N * (N / 2 + 1) + 16.0 * freqs * N) / 2e12;
-        if (build_s + apply_s < steps_s)
+        if (build_s + apply_s < steps_s) {
+            // shapes the row and column passes cover take them (whole inpaints)
+            const bool fused = col_path(pl, &p);
             for (int i = 0; i < b->count; ++i)
                 if (b->plan_of[i] == pl) {
                     b->img_prop[i] = 1;
                     b->prop_images += 1;
+                    b->img_fused[i] = fused;
+                    b->fused_images += fused;
                 }
+        }
     }
 }
 
@@ -1212,6 +1220,7 @@ se2n_status enqueue_batch_half(se2n_batch *b) {
         } else {
             SE2N_TRY(orient_impl(pl, d.f, d.mask, p.sigma_smooth, p.flat_tol, b->bins[i]));
         }
+        if (b->img_fused[i]) continue;
         SE2N_TRY(lift_half_impl(pl, d.f, d.mask, b->bins[i], b->vols[i]));
         SE2N_TRY(fft_half(pl, b->vols[i], true));
         if (p.dynamic) SE2N_TRY(dr_begin(pl, b->dr[i], d.f, d.mask, b->bins[i]));
@@ -1219,6 +1228,7 @@ se2n_status enqueue_batch_half(se2n_batch *b) {
     SE2N_TRY(batch_interval(b, Tr, true));
     for (int r = 1; r < p.rounds; ++r) {
         for (int i = 0; i < b->count; ++i) {
+            if (b->img_fused[i]) continue;
             se2n_plan *pl = b->plan_of[i];
             const se2n_image_desc &d = b->imgs[i];
             SE2N_TRY(fft_half(pl, b->vols[i], false));
@@ -1229,6 +1239,7 @@ se2n_status enqueue_batch_half(se2n_batch *b) {
         SE2N_TRY(batch_interval(b, Tr, true));
     }
     for (int i = 0; i < b->count; ++i) {
+        if (b->img_fused[i]) continue;
         se2n_plan *pl = b->plan_of[i];
         const se2n_image_desc &d = b->imgs[i];
         const float inv_hw = (float)(1.0 / (double)pl->HW);
@@ -1241,6 +1252,15 @@ se2n_status enqueue_batch_half(se2n_batch *b) {
         }
         SE2N_TRY(project_half_impl(pl, b->vols[i], scale, p.proj, p.reinject ? d.f : nullptr,
                                    p.reinject ? d.mask : nullptr, d.out));
+    }
+    // the images on the row and column passes, each whole inpaint in turn
+    // (images of one shape share their plan's buffers and propagators)
+    for (int i = 0; i < b->count; ++i) {
+        if (!b->img_fused[i]) continue;
+        se2n_params q = p;
+        q.N = b->imgs[i].N;
+        SE2N_TRY(inpaint_impl(b->plan_of[i], b->imgs[i].f, b->imgs[i].mask, b->bins[i], &q, b->vols[i],
+                              b->imgs[i].out, true));
     }
     return SE2N_OK;
 }
@@ -1401,7 +1421,17 @@ se2n_status create_batch(se2n_batch *b, const se2n_image_desc *imgs) {
         bool used = false;
         for (int i = 0; i < b->count; ++i) used = used || (b->img_prop[i] && b->plan_of[i] == pl);
         if (!used) continue;
-        SE2N_TRY(prop_reserve(pl, !b->p.full_spectrum));
+        bool fused = false;
+        for (int i = 0; i < b->count; ++i) fused = fused || (b->img_fused[i] && b->plan_of[i] == pl);
+        if (fused) {
+            // everything the whole inpaints allocate or create, before the capture
+            SE2N_TRY(col_ensure(pl));
+            SE2N_TRY(side_ensure(pl));
+            SE2N_TRY(prop_reserve(pl, true, true));
+            if (b->p.dynamic) SE2N_TRY(dr_alloc(pl->dr, pl->HW));
+        } else {
+            SE2N_TRY(prop_reserve(pl, !b->p.full_spectrum));
+        }
         if (se2n_prop_prepare(pl->N) != cudaSuccess) return SE2N_ECUDA;
         pl->prop_valid = false;
     }
@@ -1490,8 +1520,9 @@ se2n_status se2n_batch_run_per_image(se2n_batch *b) {
         q.N = b->imgs[i].N;
         // the same integration the batch chose for this image's shape
         if (b->img_prop.empty() || !b->img_prop[i]) q.diffuse_flags &= ~SE2N_DIFFUSE_PROPAGATOR;
+        const bool fused = !b->img_fused.empty() && b->img_fused[i];
         SE2N_TRY(inpaint_impl(b->plan_of[i], b->imgs[i].f, b->imgs[i].mask, b->imgs[i].bins, &q, b->vols[i],
-                              b->imgs[i].out, false));
+                              b->imgs[i].out, fused));
     }
     return SE2N_OK;
 }
@@ -1519,6 +1550,7 @@ se2n_status se2n_batch_get_info(se2n_batch *b, se2n_batch_info *out) {
     out->updates_per_run = b->updates;
     out->volume_bytes = (double)b->vol_bytes;
     out->prop_images = b->prop_images;
+    out->fused_images = b->fused_images;
     out->step_updates = 0.0;
     for (int i = 0; i < b->count; ++i)
         if (b->img_prop.empty() || !b->img_prop[i])

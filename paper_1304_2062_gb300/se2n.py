@@ -63,7 +63,8 @@ class se2n_batch_info(ctypes.Structure):
                 ("p64", ctypes.c_int), ("fast", ctypes.c_int), ("split", ctypes.c_int),
                 ("candidates", ctypes.c_int), ("best_ms", ctypes.c_double), ("worst_ms", ctypes.c_double),
                 ("updates_per_run", ctypes.c_double), ("volume_bytes", ctypes.c_double),
-                ("prop_images", ctypes.c_int), ("step_updates", ctypes.c_double)]
+                ("prop_images", ctypes.c_int), ("step_updates", ctypes.c_double),
+                ("fused_images", ctypes.c_int)]
 
 
 class se2n_params(ctypes.Structure):

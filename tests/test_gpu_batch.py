@@ -143,7 +143,8 @@ def test_batch_with_propagators(full):
     are built once in the graph and shared by its images (repeated shapes
     here); the graph replays bitwise, equals the per-image path bitwise and
     matches the oracle."""
-    shapes = SHAPES + [(16, 24, 32), (32, 32, 16), (40, 64, 64)]
+    shapes = SHAPES + [(16, 24, 32), (32, 32, 16), (40, 64, 64), (64, 64, 16), (64, 64, 16), (64, 128, 32),
+                       (64, 128, 32)]
     inputs = _inputs(shapes, seed=70)
     T, S, R = 4.0, 100, 4
     bins = [oracle.orient(f.astype(np.float32).astype(np.float64), m, N)["bins"] for f, m, N in inputs]
@@ -163,8 +164,12 @@ def test_batch_with_propagators(full):
     # 4 intervals of 100 steps: the cost estimate sends the small shapes to
     # propagators and the rest to the persistent step-by-step kernel; both
     # paths must be taken for the checks below to cover the mixed graph
-    print(f"{info['prop_images']} of {info['images']} images by propagators")
+    print(f"{info['prop_images']} of {info['images']} images by propagators, {info['fused_images']} of them on "
+          "the row and column passes")
     assert 0 < info["prop_images"] < info["images"]
+    # the 64 x 64 and 64 x 128 shapes take the row and column passes in the
+    # graph (the Hermitian half only)
+    assert info["fused_images"] == (0 if full else 4)
     for (f, m, N), bb, a, c, d in zip(inputs, bins, first, second, per):
         np.testing.assert_array_equal(a, c)
         np.testing.assert_array_equal(a, d)
