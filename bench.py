@@ -3,24 +3,28 @@
 One step = one whole inpaint of the 512x512, N=32 workload (seeded
 piecewise-smooth image, 80 % random mask plus 4-px bars every 32 px,
 beta = 0.25, 10 restoration intervals of 500 Crank-Nicolson steps, T = 2 per
-interval): orientation, lift, forward DFT, 10 x diffusion, 9 x (inverse
+interval): orientation, lift, the 2-D DFT, 10 x diffusion, 9 x (inverse
 DFT, static restoration, forward DFT), inverse DFT, projection, all through
 se2n_inpaint with the inputs resident in HBM. By default each interval's
 500 steps are applied as one precomputed S-step propagator per class of
-equal-coefficient frequencies, built inside every timed inpaint
-(--diffusion propagator); --diffusion steps runs the fused step-by-step
-kernel instead, and the default line reports that path too.
+frequencies, built inside every timed inpaint, and each interval runs as
+one column pass (DFT along y, propagators, inverse DFT) and one row pass
+(real DFTs along x around the restoration) (--diffusion propagator);
+--diffusion steps runs the fused step-by-step kernel between cuFFT
+transforms instead, and the default line reports that path too.
 
 Metric: Mathieu updates per second, updates = frequencies x N x steps per
 interval x intervals = 512^2 * 32 * 500 * 10 per inpaint (the method's
 work on all M^2 frequencies), over the whole inpaint time (value), plus ms
 per inpaint, the FP32 error against the FP64 oracle, the roofline of the
-dominant kernel (the propagator build, FP32 ALU bound; or the step kernel,
-whose flops are those of the frequencies it integrates, the Hermitian half
-512 x 257 of the spectrum), the end-to-end number from host buffers
-(se2n_inpaint_host) and the oracle's CPU rate.
+dominant kernel (the column pass against the measured copy rate, with the
+row pass and the propagator build beside it; or the step kernel, FP32 ALU
+bound, whose flops are those of the frequencies it integrates, the
+Hermitian half 512 x 257 of the spectrum), the end-to-end number from host
+buffers (se2n_inpaint_host) and the oracle's CPU rate.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+       [--workload 512|dr|batch|surrogate|unet-forward] [--diffusion propagator|steps]
 Multi-GPU (torchrun): every rank inpaints its own image (replicas, weak
 scaling); the time is the max over ranks.
 """
