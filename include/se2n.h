@@ -73,17 +73,28 @@ typedef enum se2n_status {
 #define SE2N_DIFFUSE_SPLIT_DIAG 2  /* keep a_r^2/beta apart from the angular second difference
                                       (always on when beta * T > 8, see se2n_diffuse) */
 #define SE2N_DIFFUSE_FULL_CORRECTION 4  /* apply the corner correction on every angle (no truncation) */
-/* Integrate by the S-step propagator: for every class of frequencies with
- * equal coefficients (rows k and (H/2 - k) mod H, columns l and (W/2 - l)
- * mod W) the matrix (B-^{-1} B+)^S - I is built once in FP32 by binary
- * powering in increment form and applied as one N x N product per frequency
- * (Section 4: the integration over an interval is one linear map). The same
- * result as S Crank-Nicolson steps up to rounding. The plan keeps the
- * matrices (symmetric, stored by cyclic diagonals: 4 N (N/2 + 1) bytes a
- * class, about H W N^2 / 2 bytes in all) and reuses them
- * while beta dt, S and the spectrum half stay the same, so the intervals of
- * one inpaint build them once. N = 16, 32 or 64 (else SE2N_EUNSUPPORTED);
- * the other flags do not apply. */
+/* Integrate by the S-step propagator: for every class of frequencies that
+ * share it (rows s, H/2 - s as they are and rows H/2 + s, H - s with the
+ * angles reversed, times columns l and (W/2 - l) mod W) the matrix
+ * (B-^{-1} B+)^S - I is built once in FP32 by binary powering in increment
+ * form and applied as one N x N product per frequency (Section 4: the
+ * integration over an interval is one linear map). The same result as S
+ * Crank-Nicolson steps up to rounding. The plan keeps the matrices
+ * (symmetric; by cyclic diagonals, 4 N (N/2 + 1) bytes a class, or as rows,
+ * 4 N^2 bytes a class, for the column pass below: about H W N^2 / 4 bytes in
+ * all) and reuses them while beta dt, S, the spectrum half and the storage
+ * stay the same, so the intervals of one inpaint build them once. N = 16, 32
+ * or 64 (else SE2N_EUNSUPPORTED); the other flags do not apply.
+ * In se2n_inpaint on the Hermitian half with N = 16 or 32 and H, W powers of
+ * two in 64..512, this flag alone selects the row and column passes: the
+ * volume stays row-transformed between intervals in a plan buffer of
+ * 8 (W/2 + 1) H N bytes, each interval is one kernel a column (DFT along y,
+ * propagators, inverse DFT) and one kernel a row (real DFTs along x around
+ * the restoration), and no cuFFT call is made. The first such call
+ * allocates that buffer and a second stream of the plan, on which each
+ * build runs beside the orientation and the lift (ordered after the work
+ * already on the plan's stream, joined before the first column pass);
+ * call once before capturing se2n_inpaint into a graph. */
 #define SE2N_DIFFUSE_PROPAGATOR 8
 
 /* Largest N the library has kernels for. */
@@ -270,7 +281,8 @@ SE2N_API se2n_status se2n_inpaint_host(se2n_plan *plan, const float *f_host, con
 /* Forget the S-step propagators the plan keeps for SE2N_DIFFUSE_PROPAGATOR:
  * the next such call builds them again. free_memory != 0 also releases their
  * device memory (allocated again on next use). Enqueues nothing; waits for
- * the plan's stream first when it frees. */
+ * the plan's stream (and a build still running on its second stream) first
+ * when it frees. */
 SE2N_API se2n_status se2n_plan_drop_propagators(se2n_plan *plan, int free_memory);
 
 /* Tuning of the diffusion launch (used by the autotuner): threads per
