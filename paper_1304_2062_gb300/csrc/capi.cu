@@ -262,6 +262,17 @@ se2n_status col_ensure(se2n_plan *plan) {
     return SE2N_OK;
 }
 
+// The row and column passes' buffers, and the propagators: they depend on
+// beta dt and S only, so they are built on the side stream while the
+// orientation, the lift (and the host copies of se2n_inpaint_host) run.
+se2n_status col_start(se2n_plan *plan, const se2n_params *p) {
+    SE2N_TRY(col_ensure(plan));
+    const double bdt = p->beta * (p->T / p->rounds) / p->steps;
+    if (p->T > 0.0 && bdt >= 1e-30 && bdt <= 1e3)
+        SE2N_TRY(prop_ensure(plan, p->beta, bdt, p->steps, true, true, true));
+    return SE2N_OK;
+}
+
 RowArgs row_args(se2n_plan *plan, const float *f, const uint8_t *mask, const uint8_t *bins, float scale, float eps,
                  float guard) {
     RowArgs r;
@@ -554,14 +565,7 @@ se2n_status inpaint_impl(se2n_plan *plan, const float *f, const uint8_t *mask, c
     const int N = plan->N;
     const uint8_t *bins = bins_in;
     const bool col = allow_col && col_path(plan, p);
-    if (col) {
-        SE2N_TRY(col_ensure(plan));
-        // the propagators depend on beta dt and S only: built on the side
-        // stream while the orientation and the lift run
-        const double bdt = p->beta * (p->T / p->rounds) / p->steps;
-        if (p->T > 0.0 && bdt >= 1e-30 && bdt <= 1e3)
-            SE2N_TRY(prop_ensure(plan, p->beta, bdt, p->steps, true, true, true));
-    }
+    if (col) SE2N_TRY(col_start(plan, p));
     if (!bins) {
         SE2N_TRY(orient_impl(plan, f, mask, p->sigma_smooth, p->flat_tol, plan->bins));
         bins = plan->bins;
@@ -918,6 +922,7 @@ se2n_status se2n_inpaint_host(se2n_plan *plan, const float *f_host, const uint8_
             return cuda_status(plan, e);
         }
     }
+    if (col_path(plan, p)) SE2N_TRY(col_start(plan, p));  // the build overlaps the copies too
     SE2N_TRY(cuda_status(plan, cudaMemcpyAsync(plan->h_f, f_host, sizeof(float) * HW, cudaMemcpyHostToDevice,
                                                plan->stream)));
     SE2N_TRY(cuda_status(plan, cudaMemcpyAsync(plan->h_mask, mask_host, HW, cudaMemcpyHostToDevice, plan->stream)));
