@@ -164,16 +164,22 @@ def test_own_bins_path_is_orient_then_inpaint():
     np.testing.assert_array_equal(a, c)
 
 
-def test_host_entry_point_matches_device_entry_point():
+@pytest.mark.parametrize("flags", [0, se2n.SE2N_DIFFUSE_PROPAGATOR])
+def test_host_entry_point_matches_device_entry_point(flags):
+    """se2n_inpaint_host gives se2n_inpaint's bits, step by step and on the
+    row and column passes (where it starts the propagator build before its
+    host copies; the second call reuses the propagators)."""
     w = synth.workload_512(H=128, W=64, steps=20, rounds=2)
     p = oracle.Params(N=32, beta=0.25, T=4.0, steps=20, rounds=2)
     f32 = np.ascontiguousarray(w.f.astype(np.float32))
     mask = np.ascontiguousarray(w.mask.astype(np.uint8))
-    dev = _gpu_inpaint(f32, mask, None, _params(p))
+    prm = _params(p)
+    prm.diffuse_flags = flags
+    dev = _gpu_inpaint(f32, mask, None, prm)
     plan = se2n.se2n_plan_create(w.H, w.W, 32)
     out = np.zeros((w.H, w.W), np.float32)
     for _ in range(2):  # the second call reuses the plan's buffers
-        se2n.se2n_inpaint_host(plan, f32, mask, _params(p), out)
+        se2n.se2n_inpaint_host(plan, f32, mask, prm, out)
         np.testing.assert_array_equal(out, dev)
     plan.close()
 
