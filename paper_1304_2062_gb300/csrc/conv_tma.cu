@@ -56,7 +56,8 @@ struct FwdEpi {
 };
 
 // The last convolution (32 channels, ReLU) with the 1x1 head and the input
-// skip: d[m][:] = bf16(relu(v + bias)) as FwdEpi, and
+// skip: d[m][:] = bf16(relu(v + bias)) as FwdEpi (not stored when out is
+// null: inference needs only y), and
 // y[m] = f[m] (mask[m] != 0) + hb + sum_c hw[c] d[m][c] (FP32, c in order).
 struct HeadEpi {
     const float *bias;
@@ -77,7 +78,7 @@ struct HeadEpi {
             w[q] = __bfloat162float(__float2bfloat16_rn(w[q]));
             st = fmaf(sm[32 + n + q], w[q], st);
         }
-        store16(out + (long long)m * 32 + n, w);
+        if (out) store16(out + (long long)m * 32 + n, w);
     }
     __device__ __forceinline__ void finish(int m, float st, const float *) const {
         y[m] = (mask[m] ? f[m] : 0.0f) + st;

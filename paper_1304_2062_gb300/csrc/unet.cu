@@ -97,7 +97,9 @@ bool dev_ptr(const void *p, size_t align) {
     return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
 }
 
-se2n_status forward(se2n_unet *u, const float *f, const uint8_t *mask, int n) {
+// keep: write every activation the backward pass reads (the last
+// convolution's output d0 is needed only there)
+se2n_status forward(se2n_unet *u, const float *f, const uint8_t *mask, int n, bool keep) {
     using namespace se2n::nn;
     cudaStream_t s = u->stream;
     const int H = u->H, W = u->W;
@@ -132,8 +134,8 @@ se2n_status forward(se2n_unet *u, const float *f, const uint8_t *mask, int n) {
         if (k == 2) {
             // last convolution with the head and the input skip fused, when the tile shape allows
             const HeadArgs h{u->p + u->hw_off, u->p + u->hb_off, f, mask, u->out};
-            const cudaError_t e =
-                conv_forward_tma(u->c[k], n, Hl, Wl, Bb.cin, Wt(lb), Bi(lb), Bb.cout, 1, u->d[k], Bb.cout, &h, s);
+            const cudaError_t e = conv_forward_tma(u->c[k], n, Hl, Wl, Bb.cin, Wt(lb), Bi(lb), Bb.cout, 1,
+                                                   keep ? u->d[k] : nullptr, Bb.cout, &h, s);
             if (e == cudaSuccess) break;
             if (e != cudaErrorNotSupported) return cuda_st(e);
         }
@@ -390,7 +392,7 @@ se2n_status se2n_unet_init(se2n_unet *u, unsigned long long seed) {
 se2n_status se2n_unet_forward(se2n_unet *u, const float *f, const uint8_t *mask, int count, float *out) {
     if (!u || count < 1 || count > u->B) return SE2N_EINVAL;
     if (!dev_ptr(f, 4) || !dev_ptr(mask, 1) || !dev_ptr(out, 4)) return SE2N_EINVAL;
-    TRY(forward(u, f, mask, count));
+    TRY(forward(u, f, mask, count, false));
     return cuda_st(cudaMemcpyAsync(out, u->out, sizeof(float) * count * u->H * u->W, cudaMemcpyDeviceToDevice,
                                    u->stream));
 }
@@ -402,7 +404,7 @@ se2n_status se2n_unet_backward(se2n_unet *u, const float *f, const uint8_t *mask
     if (loss_device && !dev_ptr(loss_device, 4)) return SE2N_EINVAL;
     TRYC(cudaMemcpyAsync(u->target, target, sizeof(float) * count * u->H * u->W, cudaMemcpyDeviceToDevice,
                          u->stream));
-    TRY(forward(u, f, mask, count));
+    TRY(forward(u, f, mask, count, true));
     TRY(backward(u, f, mask, count));
     if (loss_device) TRYC(cudaMemcpyAsync(loss_device, u->loss, sizeof(float), cudaMemcpyDeviceToDevice, u->stream));
     return SE2N_OK;
