@@ -3,7 +3,7 @@
 per interval, eps = 0.5) to curves_noise_512_N32.npz, and the same with
 dynamic restoration (Section 5.3) to curves_noise_512_N32_dynamic.npz
 (which also holds the final good set, the smallest decision margin and
-the pixels whose decision came within 1e-5 of a tie in some growth step).
+the pixels whose decision came within 3e-5 of a tie in some growth step).
 
 Calls only oracle/ and synth/. The orientation bins are the oracle's own
 (FP64 decision on the FP32-rounded image the GPU also receives); the stored
@@ -26,9 +26,12 @@ import synth  # noqa: E402
 
 OUT = os.path.join(HERE, "curves_noise_512_N32.npz")
 OUT_DYNAMIC = os.path.join(HERE, "curves_noise_512_N32_dynamic.npz")
-# a growth decision this close to a tie may go either way in FP32 (the GPU's
-# images differ from the oracle's by ~1e-7 of max|f|)
-TIE_TOL = 1e-5
+# a growth decision this close to a tie may go either way in FP32: the FP32
+# path's images differ from the oracle's by about 1e-6 of max|f| in rel-L2
+# but by up to 1.5e-5 of max|f| at single pixels, and a decision compares
+# such values (Section 5.3: h against the mean of the bad block), so the
+# tolerance is twice that largest pointwise difference
+TIE_TOL = 3e-5
 
 
 def write(path, dynamic):
