@@ -76,8 +76,8 @@ typedef enum se2n_status {
 /* Integrate by the S-step propagator: for every class of frequencies that
  * share it (rows s, H/2 - s as they are and rows H/2 + s, H - s with the
  * angles reversed, times columns l and (W/2 - l) mod W) the matrix
- * (B-^{-1} B+)^S - I is built once in FP32 by binary powering in increment
- * form and applied as one N x N product per frequency (Section 4: the
+ * (B-^{-1} B+)^S - I is built once in FP32 by the powering program of
+ * se2n_prop_chain, in increment form, and applied as one N x N product per frequency (Section 4: the
  * integration over an interval is one linear map). The same result as S
  * Crank-Nicolson steps up to rounding. The plan keeps the matrices
  * (symmetric; by cyclic diagonals, 4 N (N/2 + 1) bytes a class, or as rows,
@@ -99,6 +99,9 @@ typedef enum se2n_status {
 
 /* Largest N the library has kernels for. */
 #define SE2N_MAX_N 64
+
+/* Longest powering program of se2n_prop_chain. */
+#define SE2N_PROP_CHAIN_MAX 64
 
 typedef struct se2n_plan se2n_plan;
 
@@ -165,6 +168,20 @@ SE2N_API se2n_status se2n_params_from_paper(double alpha, double T_paper, int M,
 
 /* Human-readable name of a status (static storage, never NULL). */
 SE2N_API const char *se2n_status_string(se2n_status s);
+
+/* The program by which the propagator build (SE2N_DIFFUSE_PROPAGATOR) raises
+ * the one-step matrix M to the power S = steps; host only, for inspection.
+ * It works on two matrices in increment form, D_m = M^m - I: P, which starts
+ * as D_1, and R, which starts empty. Op 0 squares P (D_p -> D_2p: 2 P + P P
+ * into P); op 1 squares R into P (D_r -> D_2r); op 2 combines
+ * (D_r, D_p -> D_r+p: R + P + R P into R); op 3 copies P into R. Every op but
+ * the copy is one N x N product. For S <= 4096 the program has the fewest
+ * products of all such two-matrix programs (then the fewest copies), found
+ * by a search; above, it is binary powering (lowest bit first). Writes the
+ * ops to ops[0 .. *len - 1] and *in_r = 1 when the result ends in R, 0 in P.
+ * SE2N_EINVAL for steps < 1, null pointers or cap < the program's length
+ * (SE2N_PROP_CHAIN_MAX always suffices). */
+SE2N_API se2n_status se2n_prop_chain(int steps, unsigned char *ops, int cap, int *len, int *in_r);
 
 /* Create a plan for H x W images with N angles. H and W even (>= 2), N one
  * of 4, 8, 12, 16, 24, 30, 32, 48, 64 (else SE2N_EUNSUPPORTED), angle_conv 0

@@ -123,7 +123,7 @@ se2n_status prop_reserve(se2n_plan *plan, bool half, bool rows = false) {
 }
 
 PropArgs prop_args(se2n_plan *plan, float2 *vol, double beta, double bdt, int steps, bool half, bool rows) {
-    PropArgs a;
+    PropArgs a{};
     a.vol = vol;
     a.rows = rows ? 1 : 0;
     a.H = plan->H;
@@ -180,7 +180,14 @@ se2n_status prop_ensure(se2n_plan *plan, double beta, double bdt, int steps, boo
         plan->prop_half == half && plan->prop_rows == rows)
         return SE2N_OK;
     plan->prop_valid = false;
-    const PropArgs a = prop_args(plan, nullptr, beta, bdt, steps, half, rows);
+    if (plan->chain_steps != steps) {
+        SE2N_TRY(se2n_prop_chain(steps, plan->chain, SE2N_PROP_CHAIN_MAX, &plan->chain_len, &plan->chain_in_r));
+        plan->chain_steps = steps;
+    }
+    PropArgs a = prop_args(plan, nullptr, beta, bdt, steps, half, rows);
+    std::copy(plan->chain, plan->chain + plan->chain_len, a.chain);
+    a.chain_len = plan->chain_len;
+    a.chain_in_r = plan->chain_in_r;
     cudaStream_t st = plan->stream;
     if (side) {
         SE2N_TRY(side_ensure(plan));

@@ -25,7 +25,9 @@
 //   D_2m = 2 D_m + D_m D_m       (squaring)
 //   D_a+b = D_a + D_b + D_a D_b  (combination)
 // and the propagator is applied as x <- x + D_S x, so rounding is relative to
-// the change of x, as in the step-by-step integration.
+// the change of x, as in the step-by-step integration. D_S is reached by a
+// program of squarings and combinations over two matrices with the fewest
+// products (se2n_prop_chain): 11 for S = 500 where binary powering takes 13.
 //
 // Storage. B+ and B- are polynomials in one symmetric matrix, so M and D_S
 // are symmetric. D_S is kept by cyclic diagonals, S_m[i] = D[i, (i + m) mod N]
@@ -40,6 +42,10 @@
 // second difference, so the -2 and the a_i^2/beta never meet in one FP32
 // number. A' is cyclic tridiagonal: Thomas elimination of its torn part plus
 // one Sherman-Morrison correction.
+#include <algorithm>
+#include <unordered_map>
+#include <vector>
+
 #include "diffuse_x2.cuh"
 #include "prop_classes.cuh"
 
@@ -312,35 +318,46 @@ __global__ void __launch_bounds__(PropCfg<N>::WARPS * 32) k_prop_build(const __g
             for (int j = 0; j < N; ++j) D1r[j * C::LD + c] = D1[c * C::LD + j];
         }
         __syncwarp();
-        // binary powering: P (column- and row-major) runs through D_1, D_2,
-        // D_4, ...; R collects the set bits of S; products in place
+        // the powering program: P (column- and row-major) starts as D_1, R
+        // (column-major) empty; products in place. Squaring R first copies R
+        // into both layouts of P (B's rows are read from the row-major copy:
+        // the products stay exact, not symmetric up to rounding).
         float *P = base, *Pr = base + C::MAT, *R = base + 2 * C::MAT;
-        bool have_r = false;
-        int s = a.steps;
 #pragma unroll 1
-        while (true) {
-            if (s & 1) {
-                if (!have_r) {
-                    // R = P: copy this lane's columns
+        for (int o = 0; o < a.chain_len; ++o) {
+            const int op = a.chain[o];
+            if (op == PROP_SQ_R) {
 #pragma unroll 1
-                    for (int cc = 0; cc < C::CPL; ++cc) {
-                        const int c = t + cc * C::LPC;
-#pragma unroll
-                        for (int j = 0; j < N; j += 4)
-                            *reinterpret_cast<float4 *>(R + c * C::LD + j) =
-                                *reinterpret_cast<const float4 *>(P + c * C::LD + j);
+                for (int cc = 0; cc < C::CPL; ++cc) {
+                    const int c = t + cc * C::LPC;
+#pragma unroll 4
+                    for (int j = 0; j < N; ++j) {
+                        const float v = R[c * C::LD + j];
+                        P[c * C::LD + j] = v;
+                        Pr[j * C::LD + c] = v;
                     }
-                    have_r = true;
-                } else {
-                    prop_gemm<N>(R, Pr, R, 1.0f, P, R, nullptr, t);  // R + P + R P
                 }
                 __syncwarp();
             }
-            s >>= 1;
-            if (!s) break;
-            prop_gemm<N>(P, Pr, P, 2.0f, nullptr, P, Pr, t);  // 2 P + P P
+            if (op != PROP_COPY) {
+                // 2 P + P P into P (and Pr), or R + P + R P into R
+                const bool add = op == PROP_ADD;
+                const float *A = add ? R : P;
+                prop_gemm<N>(A, Pr, A, add ? 1.0f : 2.0f, add ? P : nullptr, add ? R : P, add ? nullptr : Pr, t);
+            } else {
+                // R = P: copy this lane's columns
+#pragma unroll 1
+                for (int cc = 0; cc < C::CPL; ++cc) {
+                    const int c = t + cc * C::LPC;
+#pragma unroll
+                    for (int j = 0; j < N; j += 4)
+                        *reinterpret_cast<float4 *>(R + c * C::LD + j) =
+                            *reinterpret_cast<const float4 *>(P + c * C::LD + j);
+                }
+            }
             __syncwarp();
         }
+        if (!a.chain_in_r) R = P;
         // D_S symmetrised, as rows in 16-byte chunks stored chunk-major
         // (D[i][4c .. 4c + 3] at float4 c N + i): this lane writes rows i = t,
         // t + LPC, ..., consecutive lanes consecutive chunks
@@ -545,34 +562,27 @@ __global__ void __launch_bounds__(SymCfg<N>::WARPS * 32) k_prop_build_sym(const 
                 }
         }
         __syncwarp();
-        // binary powering: P runs through D_1, D_2, D_4, ...; R collects the
-        // set bits of S
-        bool have_r = false;
-        int s = a.steps;
+        // the powering program: P starts as D_1, R empty
 #pragma unroll 1
-        while (true) {
-            if (s & 1) {
-                if (!have_r) {
-                    if (active) {
+        for (int o = 0; o < a.chain_len; ++o) {
+            const int op = a.chain[o];
+            if (op != PROP_COPY) {
+                // 2 P + P P into P, 2 R + R R into P, or R + P + R P into R
+                // (one call site: the products share their registers)
+                const bool add = op == PROP_ADD;
+                const float *A = op == PROP_SQ_P ? P : R;
+                sym_gemm<N>(A, add ? P : A, A, add ? 1.0f : 2.0f, add ? P : nullptr, add ? R : P, bi, bj, active);
+            } else if (active) {
 #pragma unroll 1
-                        for (int i = t; i < N; i += C::TILES)
+                for (int i = t; i < N; i += C::TILES)
 #pragma unroll
-                            for (int j = 0; j < N; j += 4)
-                                *reinterpret_cast<float4 *>(R + i * C::LD + j) =
-                                    *reinterpret_cast<const float4 *>(P + i * C::LD + j);
-                    }
-                    have_r = true;
-                } else {
-                    sym_gemm<N>(R, P, R, 1.0f, P, R, bi, bj, active);  // R + P + R P
-                }
-                __syncwarp();
+                    for (int j = 0; j < N; j += 4)
+                        *reinterpret_cast<float4 *>(R + i * C::LD + j) =
+                            *reinterpret_cast<const float4 *>(P + i * C::LD + j);
             }
-            s >>= 1;
-            if (!s) break;
-            sym_gemm<N>(P, P, P, 2.0f, nullptr, P, bi, bj, active);  // 2 P + P P
             __syncwarp();
         }
-        prop_store<N>(a, R, C::LD, u, live, t, C::TILES);
+        prop_store<N>(a, a.chain_in_r ? R : P, C::LD, u, live, t, C::TILES);
         __syncwarp();
     }
 }
@@ -739,9 +749,103 @@ cudaError_t launch_apply(const PropArgs &a, int num_sms, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Powering programs over two matrices. A state is the pair of exponents
+// (p, r) of P and R (r = 0: R empty); an op costs CHAIN_PRODUCT a product
+// and 1 a copy, so that the fewest products come first and the fewest copies
+// second. The search is A* with the lower bound CHAIN_PRODUCT times the
+// doublings from max(p, r) to S (no op more than doubles the largest
+// exponent, so the bound never overestimates and never drops by more than
+// an op costs), within the cost of binary powering.
+constexpr int CHAIN_PRODUCT = 64;
+
+int chain_bound(long long m, int S) {
+    int d = 0;
+    for (; m < S; m *= 2) ++d;
+    return CHAIN_PRODUCT * d;
+}
+
+// binary powering, lowest bit first: P runs through D_1, D_2, D_4, ... and R
+// collects the set bits
+void chain_binary(int S, std::vector<unsigned char> &ops) {
+    ops.clear();
+    bool have_r = false;
+    for (int s = S;;) {
+        if (s & 1) {
+            ops.push_back(have_r ? PROP_ADD : PROP_COPY);
+            have_r = true;
+        }
+        s >>= 1;
+        if (!s) break;
+        ops.push_back(PROP_SQ_P);
+    }
+}
+
+int chain_cost(const std::vector<unsigned char> &ops) {
+    int c = 0;
+    for (const unsigned char o : ops) c += o == PROP_COPY ? 1 : CHAIN_PRODUCT;
+    return c;
+}
+
+bool chain_search(int S, int budget, std::vector<unsigned char> &ops, int &in_r) {
+    struct Node {
+        int g;
+        long long pred;
+        unsigned char op;
+    };
+    const long long W = (long long)S + 1;
+    std::unordered_map<long long, Node> seen;
+    std::vector<std::vector<long long>> bucket(budget + 1);
+    auto visit = [&](int p, int r, int g, long long pred, unsigned char op) {
+        const int f = g + chain_bound(std::max(p, r), S);
+        if (f > budget) return;
+        const long long key = p * W + r;
+        const auto it = seen.find(key);
+        if (it != seen.end() && it->second.g <= g) return;
+        seen[key] = Node{g, pred, op};
+        bucket[f].push_back(key);
+    };
+    visit(1, 0, 0, -1, 0);
+    for (int f = 0; f <= budget; ++f) {
+        for (size_t i = 0; i < bucket[f].size(); ++i) {
+            const long long key = bucket[f][i];
+            const int p = (int)(key / W), r = (int)(key % W);
+            const int g = seen[key].g;
+            if (g + chain_bound(std::max(p, r), S) != f) continue;  // reached again at a lower cost
+            if (p == S || r == S) {
+                in_r = p == S ? 0 : 1;
+                ops.clear();
+                for (long long k = key; seen[k].pred >= 0; k = seen[k].pred) ops.push_back(seen[k].op);
+                std::reverse(ops.begin(), ops.end());
+                return true;
+            }
+            if (2LL * p <= S) visit(2 * p, r, g + CHAIN_PRODUCT, key, PROP_SQ_P);
+            if (r > 0 && 2LL * r <= S) visit(2 * r, r, g + CHAIN_PRODUCT, key, PROP_SQ_R);
+            if (r > 0 && (long long)p + r <= S) visit(p, p + r, g + CHAIN_PRODUCT, key, PROP_ADD);
+            if (r != p) visit(p, p, g + 1, key, PROP_COPY);
+        }
+    }
+    return false;
+}
+
 }  // namespace
 
 }  // namespace se2n
+
+se2n_status se2n_prop_chain(int steps, unsigned char *ops, int cap, int *len, int *in_r) {
+    if (steps < 1 || !ops || !len || !in_r) return SE2N_EINVAL;
+    std::vector<unsigned char> prog, best;
+    int r = 1, best_r = 1;
+    se2n::chain_binary(steps, prog);
+    if (steps <= 4096 && se2n::chain_search(steps, se2n::chain_cost(prog), best, best_r)) {
+        prog.swap(best);
+        r = best_r;
+    }
+    if ((int)prog.size() > cap) return SE2N_EINVAL;
+    std::copy(prog.begin(), prog.end(), ops);
+    *len = (int)prog.size();
+    *in_r = r;
+    return SE2N_OK;
+}
 
 bool se2n_prop_supported(int N) { return N == 16 || N == 32 || N == 64; }
 

@@ -51,6 +51,10 @@ struct se2n_plan {
     int prop_steps;
     bool prop_half;
     bool prop_rows;        // stored as full rows (the column pass) or by diagonals
+    // the powering program of S = chain_steps (0: none yet)
+    int chain_steps;
+    unsigned char chain[SE2N_PROP_CHAIN_MAX];
+    int chain_len, chain_in_r;
     // side stream for a build that overlaps the start of an inpaint, and the
     // events that order it after the plan's stream and the plan's stream
     // after it (join_pending until the plan's stream waits on ev_join)
@@ -101,6 +105,13 @@ struct DiffuseArgs {
 
 // Parameters of the propagator kernels (propagator.cu): build D_S for every
 // class of frequencies with equal coefficients, or apply it to the volume.
+// Ops of the powering program, in increment form D_m = M^m - I:
+//   PROP_SQ_P  P <- 2 P + P P  (D_p -> D_2p)
+//   PROP_SQ_R  P <- 2 R + R R  (D_r -> D_2r)
+//   PROP_ADD   R <- R + P + R P  (D_r, D_p -> D_r+p)
+//   PROP_COPY  R <- P
+enum PropOp : unsigned char { PROP_SQ_P = 0, PROP_SQ_R = 1, PROP_ADD = 2, PROP_COPY = 3 };
+
 struct PropArgs {
     float *D;          // D_S = (B-^{-1} B+)^S - I a class: [classes][N/2 + 1][N] cyclic
                        // diagonals, or when rows != 0 [classes][N/4][N] float4:
@@ -112,6 +123,11 @@ struct PropArgs {
     int col_slots;     // column classes a row class
     long long classes;
     int steps;         // S
+    // the powering program (se2n_prop_chain): ops PROP_* on P (starting as
+    // D_1) and R (empty); the result ends in R when chain_in_r
+    unsigned char chain[SE2N_PROP_CHAIN_MAX];
+    int chain_len;
+    int chain_in_r;
     float inv_c;       // 2 / (beta dt)
     float inv_beta;
     int half;          // 1: the Hermitian half (columns l <= W/2), 0: all W columns

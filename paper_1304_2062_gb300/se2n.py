@@ -93,6 +93,8 @@ _SIGS = {
     "se2n_params_default": (ctypes.c_int, [ctypes.POINTER(se2n_params)]),
     "se2n_params_from_paper": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "se2n_prop_chain": (ctypes.c_int, [ctypes.c_int, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int)]),
     "se2n_plan_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, _P]),
     "se2n_plan_destroy": (ctypes.c_int, [_P]),
@@ -203,6 +205,20 @@ def se2n_params_from_paper(alpha, T_paper, M, N):
     _check(lib.se2n_params_from_paper(alpha, T_paper, M, N, ctypes.byref(b), ctypes.byref(t)),
            "se2n_params_from_paper")
     return b.value, t.value
+
+
+PROP_CHAIN_MAX = 64
+PROP_SQ_P, PROP_SQ_R, PROP_ADD, PROP_COPY = 0, 1, 2, 3
+
+
+def se2n_prop_chain(steps):
+    """The propagator build's powering program for S = steps: (ops, in_r),
+    ops a list of PROP_* codes on P (starting as D_1) and R."""
+    buf = (ctypes.c_ubyte * PROP_CHAIN_MAX)()
+    n = ctypes.c_int()
+    in_r = ctypes.c_int()
+    _check(lib.se2n_prop_chain(steps, buf, PROP_CHAIN_MAX, ctypes.byref(n), ctypes.byref(in_r)), "se2n_prop_chain")
+    return list(buf[:n.value]), in_r.value
 
 
 class Plan:

@@ -105,3 +105,74 @@ def test_python_binding_loads_and_names_match_the_c_abi():
     from paper_1304_2062_gb300 import se2n
     for name in _declared():
         assert callable(getattr(se2n, name)), name
+
+
+def _run_chain(ops, in_r):
+    """Exponents of P and R after the program (P = D_1, R empty at the start)."""
+    p, r = 1, 0
+    for o in ops:
+        if o == 0:
+            p = 2 * p
+        elif o == 1:
+            assert r > 0
+            p = 2 * r
+        elif o == 2:
+            assert r > 0
+            r = r + p
+        else:
+            assert o == 3
+            r = p
+    return r if in_r else p
+
+
+def _fewest_products(S):
+    """Brute force: breadth-first over the exponent pairs (p, r) of every
+    two-matrix program, products cost 1 and copies 0."""
+    from collections import deque
+    dist = {(1, 0): 0}
+    q = deque([(1, 0)])
+    while q:
+        p, r = q.popleft()
+        d = dist[(p, r)]
+        if p == S or r == S:
+            return d
+        moves = [((p, p), 0)] if r != p else []
+        if 2 * p <= S:
+            moves.append(((2 * p, r), 1))
+        if r and 2 * r <= S:
+            moves.append(((2 * r, r), 1))
+        if r and p + r <= S:
+            moves.append(((p, p + r), 1))
+        for st, c in moves:
+            if st not in dist or dist[st] > d + c:
+                dist[st] = d + c
+                (q.appendleft if c == 0 else q.append)(st)
+    raise AssertionError(S)
+
+
+def test_powering_program_reaches_S_with_the_fewest_products():
+    """The propagator's powering program (D_m = M^m - I over two matrices):
+    it reaches S, takes no more products than binary powering, and as few as
+    a brute-force search over all two-matrix programs."""
+    from paper_1304_2062_gb300 import se2n
+    for S in list(range(1, 65)) + [100, 127, 255, 500, 1000, 4095, 4096, 4097, 100000, 2 ** 31 - 1]:
+        ops, in_r = se2n.se2n_prop_chain(S)
+        assert _run_chain(ops, in_r) == S
+        products = sum(o != 3 for o in ops)
+        assert products <= S.bit_length() - 1 + bin(S).count("1") - 1
+        if S <= 64 or S == 500:
+            assert products == _fewest_products(S), S
+    assert sum(o != 3 for o in se2n.se2n_prop_chain(500)[0]) == 11
+
+
+def test_powering_program_arguments_are_checked(lib):
+    f = lib.se2n_prop_chain
+    f.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                  ctypes.POINTER(ctypes.c_int)]
+    buf = (ctypes.c_ubyte * 64)()
+    n, r = ctypes.c_int(), ctypes.c_int()
+    assert f(0, buf, 64, ctypes.byref(n), ctypes.byref(r)) == 1
+    assert f(500, None, 64, ctypes.byref(n), ctypes.byref(r)) == 1
+    assert f(500, buf, 64, None, ctypes.byref(r)) == 1
+    assert f(500, buf, 5, ctypes.byref(n), ctypes.byref(r)) == 1
+    assert f(1, buf, 0, ctypes.byref(n), ctypes.byref(r)) == 0 and n.value == 0 and r.value == 0

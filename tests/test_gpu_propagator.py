@@ -45,8 +45,11 @@ def _run(vol, N, beta, T, S, flags):
     (32, 40, 40, 0.25, 2.0, 500), (32, 20, 24, 0.25, 2.0, 1), (32, 20, 24, 0.25, 2.0, 2),
     (16, 12, 64, 0.25, 2.0, 256), (64, 22, 30, 0.7, 3.0, 100),
     (32, 18, 14, 10.0, 20.0, 20), (64, 18, 14, 10.0, 20.0, 20), (16, 2, 6, 0.5, 1.0, 9),
-    (16, 4, 8, 0.5, 2.0, 30), (32, 6, 10, 0.5, 2.0, 30), (16, 10, 4, 0.4, 2.0, 25)])
+    (16, 4, 8, 0.5, 2.0, 30), (32, 6, 10, 0.5, 2.0, 30), (16, 10, 4, 0.4, 2.0, 25),
+    (64, 16, 20, 0.25, 2.0, 500), (64, 18, 14, 0.5, 2.0, 30), (32, 18, 14, 10.0, 30.0, 30)])
 def test_propagator_matches_oracle(N, H, W, beta, T, S):
+    """The powering programs of S = 15, 30 and 500 square R into P (op 1);
+    the others only square P and combine."""
     vol = synth.random_volume(N, H, W, seed=N + H + S).astype(np.complex64)
     ref = oracle.diffuse(vol.astype(np.complex128), beta, T, S)
     got = _run(vol, N, beta, T, S, PROP)
