@@ -261,8 +261,11 @@ __global__ void __launch_bounds__(PropCfg<N>::WARPS * 32) k_prop_build(const __g
     float *q = G + N;
     float *scal = q + N;  // 1/d0, 1/(1 + v.q)
     const long long stride = (long long)gridDim.x * C::WARPS * C::CPW;
-    // classes are taken warp-uniformly so that every lane reaches each __syncwarp
-    for (long long u0 = ((long long)blockIdx.x * C::WARPS + warp) * C::CPW; u0 < a.classes; u0 += stride) {
+    // classes are taken warp-uniformly so that every lane reaches each __syncwarp,
+    // warp-major over the grid: where the classes do not divide evenly, the
+    // warps that take one chunk more are spread over the blocks (and SMs)
+    // instead of filling the first blocks
+    for (long long u0 = ((long long)warp * gridDim.x + blockIdx.x) * C::CPW; u0 < a.classes; u0 += stride) {
         const long long u = u0 + g;
         const bool live = u < a.classes;
         int k, l, lb;
@@ -515,8 +518,11 @@ __global__ void __launch_bounds__(SymCfg<N>::WARPS * 32) k_prop_build_sym(const 
     float *q = G + N;
     float *scal = q + N;  // 1/d0, 1/(1 + v.q)
     const long long stride = (long long)gridDim.x * C::WARPS * C::CPW;
-    // classes are taken warp-uniformly so that every lane reaches each __syncwarp
-    for (long long u0 = ((long long)blockIdx.x * C::WARPS + warp) * C::CPW; u0 < a.classes; u0 += stride) {
+    // classes are taken warp-uniformly so that every lane reaches each __syncwarp,
+    // warp-major over the grid: where the classes do not divide evenly, the
+    // warps that take one chunk more are spread over the blocks (and SMs)
+    // instead of filling the first blocks
+    for (long long u0 = ((long long)warp * gridDim.x + blockIdx.x) * C::CPW; u0 < a.classes; u0 += stride) {
         const long long u = u0 + g;
         const bool live = active && u < a.classes;
         int k, l, lb;
