@@ -229,23 +229,27 @@ __device__ __forceinline__ void prop_factor(const PropArgs &a, float wx, float w
     scal[1] = 1.0f / (1.0f + fmaf(qq[N - 1], inv_d0, qq[0]));
 }
 
-// D_S of class u from a symmetric row-major matrix (stride ld): as rows in
-// 16-byte chunks, chunk-major, or by cyclic diagonals; lanes t of `lanes`.
 template <int N>
-__device__ __forceinline__ void prop_store(const PropArgs &a, const float *Rm, int ld, long long u, bool live, int t,
+struct SymCfg;
+
+// D_S of class u from a symmetric matrix in the layout of SymCfg<N>: as rows
+// in 16-byte chunks, chunk-major, or by cyclic diagonals; lanes t of `lanes`.
+template <int N>
+__device__ __forceinline__ void prop_store(const PropArgs &a, const float *Rm, long long u, bool live, int t,
                                            int lanes) {
+    using C = SymCfg<N>;
     if (!live) return;
     if (a.rows) {
         float4 *out = reinterpret_cast<float4 *>(a.D + u * (long long)(N * N));
         for (int e = t; e < N * N / 4; e += lanes) {
             const int c = e / N, i = e - c * N;
-            out[e] = *reinterpret_cast<const float4 *>(Rm + i * ld + 4 * c);
+            out[e] = *reinterpret_cast<const float4 *>(Rm + C::at(i, 4 * c));
         }
     } else {
         float *out = a.D + u * (long long)((N / 2 + 1) * N);
         for (int e = t; e < (N / 2 + 1) * N; e += lanes) {
             const int m = e / N, i = e - m * N;
-            out[e] = Rm[i * ld + ((i + m) & (N - 1))];
+            out[e] = Rm[C::at(i, (i + m) & (N - 1))];
         }
     }
 }
@@ -410,6 +414,16 @@ __global__ void __launch_bounds__(PropCfg<N>::WARPS * 32) k_prop_build(const __g
 // The mirrored tile is exactly symmetric; for a diagonal tile the upper half
 // is written and mirrored. D_1, built column by column by the solves, is
 // symmetrised first (the mean of mirrored entries).
+//
+// Banks (N = 32). A 16-byte shared access is served 8 lanes at a time, and
+// rows 8 apart (8 LD floats) fall on the same banks. The tiles' own rows
+// (the epilogue's loads and stores) would collide whenever two lanes of one
+// quarter-warp hold tiles in the same tile column (or, mirrored, the same
+// tile row). So element (i, j) sits at i LD + ((j + SKEW(i / 8)) mod N), and
+// lane t of a class takes tile TILE[t]: with the class bases 4 banks apart,
+// every quarter-warp touches 8 different groups of 4 banks in every access
+// of a product (the k steps, the tile rows and the mirrored rows), found by
+// an exhaustive search over the skews and a random one over the tile orders.
 template <int N>
 struct SymCfg {
     static constexpr int WARPS = 4;
@@ -422,6 +436,29 @@ struct SymCfg {
     static constexpr int SMEM = WARPS * CPW * CLASS_FLOATS * 4;
     static constexpr int SBLK = (N / 2 + 1) * N;
     static_assert(N == 16 || N == 32, "8 x 8 tiles of 16 or 32");
+    static_assert(N != 32 || CLASS_FLOATS % 32 == 4, "class bases 4 banks apart");
+    // SKEW(b) for b = 0 .. 3: 0, 20, 4, 24 floats (N = 32), none at N = 16
+    static __device__ __forceinline__ int skew(int b) { return N == 32 ? (0x18041400u >> (8 * b)) & 0xff : 0; }
+    static __device__ __forceinline__ int at(int i, int j) { return i * LD + ((j + skew(i >> 3)) & (N - 1)); }
+    // tile (bi, bj) = (TILE[t] / 4, TILE[t] mod 4) of lane t (N = 32), TILE =
+    // 4 bi + bj of (2,3) (0,2) (1,2) (0,0) (2,2) (0,1) (1,3) (0,3) (3,3) (1,1),
+    // four bits each
+    static __device__ __forceinline__ void tile(int t, int &bi, int &bj) {
+        if constexpr (N == 32) {
+            const int v = (int)((0x5F371A062BULL >> (4 * (t < 10 ? t : 0))) & 0xF);
+            bi = v >> 2;
+            bj = v & 3;
+        } else {
+            // row order of the upper triangle
+            bi = 0;
+            int rem = t;
+            while (rem >= NT - bi) {
+                rem -= NT - bi;
+                ++bi;
+            }
+            bj = bi + rem;
+        }
+    }
 };
 
 // out = two * X + Y + A B on the upper-triangle tile (bi, bj) of this lane,
@@ -439,19 +476,19 @@ __device__ __forceinline__ void sym_gemm(const float *A, const float *B, const f
         for (int r = 0; r < 8; ++r)
 #pragma unroll
             for (int c = 0; c < 8; c += 4) {
-                const float4 xv = *reinterpret_cast<const float4 *>(X + (r0 + r) * C::LD + c0 + c);
+                const float4 xv = *reinterpret_cast<const float4 *>(X + C::at(r0 + r, c0 + c));
                 float4 yv = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (Y) yv = *reinterpret_cast<const float4 *>(Y + (r0 + r) * C::LD + c0 + c);
+                if (Y) yv = *reinterpret_cast<const float4 *>(Y + C::at(r0 + r, c0 + c));
                 acc[r][c / 2] = pk2(fmaf(two, xv.x, yv.x), fmaf(two, xv.y, yv.y));
                 acc[r][c / 2 + 1] = pk2(fmaf(two, xv.z, yv.z), fmaf(two, xv.w, yv.w));
             }
 #pragma unroll 2
         for (int k = 0; k < N; ++k) {
             // A[r][k] = A[k][r]: row k of A, columns r0 .. r0 + 7
-            const float4 a0 = *reinterpret_cast<const float4 *>(A + k * C::LD + r0);
-            const float4 a1 = *reinterpret_cast<const float4 *>(A + k * C::LD + r0 + 4);
-            const float4 b0 = *reinterpret_cast<const float4 *>(B + k * C::LD + c0);
-            const float4 b1 = *reinterpret_cast<const float4 *>(B + k * C::LD + c0 + 4);
+            const float4 a0 = *reinterpret_cast<const float4 *>(A + C::at(k, r0));
+            const float4 a1 = *reinterpret_cast<const float4 *>(A + C::at(k, r0 + 4));
+            const float4 b0 = *reinterpret_cast<const float4 *>(B + C::at(k, c0));
+            const float4 b1 = *reinterpret_cast<const float4 *>(B + C::at(k, c0 + 4));
             const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
             const f32x2 bv[4] = {pk2(b0.x, b0.y), pk2(b0.z, b0.w), pk2(b1.x, b1.y), pk2(b1.z, b1.w)};
 #pragma unroll
@@ -482,16 +519,16 @@ __device__ __forceinline__ void sym_gemm(const float *A, const float *B, const f
         // the tile and its transpose, as 16-byte rows
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
-            *reinterpret_cast<float4 *>(out + (r0 + r) * C::LD + c0) = make_float4(v[r][0], v[r][1], v[r][2], v[r][3]);
-            *reinterpret_cast<float4 *>(out + (r0 + r) * C::LD + c0 + 4) =
+            *reinterpret_cast<float4 *>(out + C::at(r0 + r, c0)) = make_float4(v[r][0], v[r][1], v[r][2], v[r][3]);
+            *reinterpret_cast<float4 *>(out + C::at(r0 + r, c0 + 4)) =
                 make_float4(v[r][4], v[r][5], v[r][6], v[r][7]);
         }
         if (bi != bj) {
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
-                *reinterpret_cast<float4 *>(out + (c0 + c) * C::LD + r0) =
+                *reinterpret_cast<float4 *>(out + C::at(c0 + c, r0)) =
                     make_float4(v[0][c], v[1][c], v[2][c], v[3][c]);
-                *reinterpret_cast<float4 *>(out + (c0 + c) * C::LD + r0 + 4) =
+                *reinterpret_cast<float4 *>(out + C::at(c0 + c, r0 + 4)) =
                     make_float4(v[4][c], v[5][c], v[6][c], v[7][c]);
             }
         }
@@ -505,13 +542,9 @@ __global__ void __launch_bounds__(SymCfg<N>::WARPS * 32) k_prop_build_sym(const 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane / C::TILES, t = lane - g * C::TILES;
     const bool active = g < C::CPW;
-    // this lane's tile (bi, bj), bi <= bj, in row order of the upper triangle
-    int bi = 0, rem = t;
-    while (rem >= C::NT - bi) {
-        rem -= C::NT - bi;
-        ++bi;
-    }
-    const int bj = bi + rem;
+    // this lane's tile (bi, bj), bi <= bj
+    int bi, bj;
+    C::tile(t, bi, bj);
     float *base = psm + (warp * C::CPW + (active ? g : 0)) * C::CLASS_FLOATS;
     float *P = base, *R = base + C::MAT;
     float *G = base + 2 * C::MAT;
@@ -547,7 +580,7 @@ __global__ void __launch_bounds__(SymCfg<N>::WARPS * 32) k_prop_build_sym(const 
                 prop_solve2<N>(x, y, G, q, inv_d0, inv_den);
 #pragma unroll
                 for (int j = 0; j < N; j += 4)
-                    *reinterpret_cast<float4 *>(R + c * C::LD + j) =
+                    *reinterpret_cast<float4 *>(R + C::at(c, j)) =
                         make_float4(fmaf(2.0f, y[j], -2.0f * e2 * x[j]), fmaf(2.0f, y[j + 1], -2.0f * e2 * x[j + 1]),
                                     fmaf(2.0f, y[j + 2], -2.0f * e2 * x[j + 2]),
                                     fmaf(2.0f, y[j + 3], -2.0f * e2 * x[j + 3]));
@@ -561,10 +594,10 @@ __global__ void __launch_bounds__(SymCfg<N>::WARPS * 32) k_prop_build_sym(const 
             for (int i = t; i < N; i += C::TILES)
 #pragma unroll
                 for (int j = 0; j < N; j += 4) {
-                    const float4 ri = *reinterpret_cast<const float4 *>(R + i * C::LD + j);
-                    *reinterpret_cast<float4 *>(P + i * C::LD + j) =
-                        make_float4(0.5f * (ri.x + R[j * C::LD + i]), 0.5f * (ri.y + R[(j + 1) * C::LD + i]),
-                                    0.5f * (ri.z + R[(j + 2) * C::LD + i]), 0.5f * (ri.w + R[(j + 3) * C::LD + i]));
+                    const float4 ri = *reinterpret_cast<const float4 *>(R + C::at(i, j));
+                    *reinterpret_cast<float4 *>(P + C::at(i, j)) =
+                        make_float4(0.5f * (ri.x + R[C::at(j, i)]), 0.5f * (ri.y + R[C::at(j + 1, i)]),
+                                    0.5f * (ri.z + R[C::at(j + 2, i)]), 0.5f * (ri.w + R[C::at(j + 3, i)]));
                 }
         }
         __syncwarp();
@@ -588,7 +621,7 @@ __global__ void __launch_bounds__(SymCfg<N>::WARPS * 32) k_prop_build_sym(const 
             }
             __syncwarp();
         }
-        prop_store<N>(a, a.chain_in_r ? R : P, C::LD, u, live, t, C::TILES);
+        prop_store<N>(a, a.chain_in_r ? R : P, u, live, t, C::TILES);
         __syncwarp();
     }
 }
