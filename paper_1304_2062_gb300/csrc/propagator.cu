@@ -482,20 +482,27 @@ __device__ __forceinline__ void sym_gemm(const float *A, const float *B, const f
                 acc[r][c / 2] = pk2(fmaf(two, xv.x, yv.x), fmaf(two, xv.y, yv.y));
                 acc[r][c / 2 + 1] = pk2(fmaf(two, xv.z, yv.z), fmaf(two, xv.w, yv.w));
             }
+        // blocks of 8 rows k share their skew: the four slice offsets are
+        // formed once a block and the rows are then fixed strides apart
+#pragma unroll 1
+        for (int kb = 0; kb < N; kb += 8) {
+            const float *Ak0 = A + C::at(kb, r0), *Ak1 = A + C::at(kb, r0 + 4);
+            const float *Bk0 = B + C::at(kb, c0), *Bk1 = B + C::at(kb, c0 + 4);
 #pragma unroll 2
-        for (int k = 0; k < N; ++k) {
-            // A[r][k] = A[k][r]: row k of A, columns r0 .. r0 + 7
-            const float4 a0 = *reinterpret_cast<const float4 *>(A + C::at(k, r0));
-            const float4 a1 = *reinterpret_cast<const float4 *>(A + C::at(k, r0 + 4));
-            const float4 b0 = *reinterpret_cast<const float4 *>(B + C::at(k, c0));
-            const float4 b1 = *reinterpret_cast<const float4 *>(B + C::at(k, c0 + 4));
-            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            const f32x2 bv[4] = {pk2(b0.x, b0.y), pk2(b0.z, b0.w), pk2(b1.x, b1.y), pk2(b1.z, b1.w)};
+            for (int kk = 0; kk < 8; ++kk) {
+                // A[r][k] = A[k][r]: row k of A, columns r0 .. r0 + 7
+                const float4 a0 = *reinterpret_cast<const float4 *>(Ak0 + kk * C::LD);
+                const float4 a1 = *reinterpret_cast<const float4 *>(Ak1 + kk * C::LD);
+                const float4 b0 = *reinterpret_cast<const float4 *>(Bk0 + kk * C::LD);
+                const float4 b1 = *reinterpret_cast<const float4 *>(Bk1 + kk * C::LD);
+                const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                const f32x2 bv[4] = {pk2(b0.x, b0.y), pk2(b0.z, b0.w), pk2(b1.x, b1.y), pk2(b1.z, b1.w)};
 #pragma unroll
-            for (int r = 0; r < 8; ++r) {
-                const f32x2 s = dup2(av[r]);
+                for (int r = 0; r < 8; ++r) {
+                    const f32x2 s = dup2(av[r]);
 #pragma unroll
-                for (int c = 0; c < 4; ++c) acc[r][c] = fma2(s, bv[c], acc[r][c]);
+                    for (int c = 0; c < 4; ++c) acc[r][c] = fma2(s, bv[c], acc[r][c]);
+                }
             }
         }
     }
