@@ -15,8 +15,6 @@
 #include <math.h>
 #include <string.h>
 
-#include <mutex>
-
 #include "diffuse_x2.cuh"
 #include "se2n_batch.h"
 
@@ -25,9 +23,10 @@ namespace {
 constexpr int kMaxVolumes = SE2N_NOALLOC_MAX_VOLUMES;
 constexpr int kPasses = 8;  // warp passes (32/P frequencies each) per work item
 
-struct StaticScratch {
-    unsigned int counter;          // work items claimed; set to 0 by every call
-    unsigned int pad[63];          // keeps the records 256 bytes apart from the counter
+// The records of one call: built on the host and handed to the set-up kernel
+// by value, as its launch parameter, so the call copies nothing from host
+// memory and keeps no pointer to the host stack.
+struct NoallocRecords {
     int count;                     // volumes in this call
     int tile[kMaxVolumes];         // frequencies per work item of volume i
     long long prefix[kMaxVolumes + 1];  // work items before volume i
@@ -35,10 +34,17 @@ struct StaticScratch {
     float tables[2 * (16 + 32 + 64)];   // cos[N] then sin[N], for N = 16, 32, 64
 };
 
+struct StaticScratch {
+    unsigned int counter;          // work items claimed; set to 0 by every call
+    unsigned int pad[63];          // keeps the records 256 bytes apart from the counter
+    NoallocRecords rec;
+};
+
 // The whole scratch of the entry point. Every GPU that loads the library
 // holds these bytes until the process exits; every call shares them.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SE2N_NOALLOC_SCRATCH_BYTES];
 static_assert(sizeof(StaticScratch) <= SE2N_NOALLOC_SCRATCH_BYTES, "scratch layout exceeds the stated size");
+static_assert(sizeof(NoallocRecords) % 4 == 0 && sizeof(NoallocRecords) <= 16384, "records fit one launch parameter");
 
 constexpr int table_offset(int N) { return N == 16 ? 0 : (N == 32 ? 2 * 16 : 2 * (16 + 32)); }
 
@@ -67,8 +73,9 @@ __device__ __forceinline__ void static_item(const StepParams &sp, const float *t
 template <bool FAST, bool SPLIT>
 __global__ void __launch_bounds__(256) k_diffuse_static(const StepParams sp, StaticScratch *s) {
     const int lane = threadIdx.x & 31;
-    const int count = s->count;
-    const long long total = s->prefix[count];
+    const NoallocRecords &r = s->rec;
+    const int count = r.count;
+    const long long total = r.prefix[count];
     for (;;) {
         unsigned int it = 0;
         if (lane == 0) it = atomicAdd(&s->counter, 1u);
@@ -77,16 +84,26 @@ __global__ void __launch_bounds__(256) k_diffuse_static(const StepParams sp, Sta
         int lo = 0, hi = count - 1;  // the volume i with prefix[i] <= it < prefix[i + 1]
         while (lo < hi) {
             const int mid = (lo + hi + 1) / 2;
-            if (s->prefix[mid] <= (long long)it) lo = mid;
+            if (r.prefix[mid] <= (long long)it) lo = mid;
             else hi = mid - 1;
         }
-        const BatchImage im = s->vols[lo];
-        const long long first = ((long long)it - s->prefix[lo]) * s->tile[lo];
-        const int n = (int)min((long long)s->tile[lo], im.HW - first);
-        if (im.N == 64) static_item<64, 4, FAST, SPLIT>(sp, s->tables, im, first, n, lane);
-        else if (im.N == 32) static_item<32, 2, FAST, SPLIT>(sp, s->tables, im, first, n, lane);
-        else static_item<16, 1, FAST, SPLIT>(sp, s->tables, im, first, n, lane);
+        const BatchImage im = r.vols[lo];
+        const long long first = ((long long)it - r.prefix[lo]) * r.tile[lo];
+        const int n = (int)min((long long)r.tile[lo], im.HW - first);
+        if (im.N == 64) static_item<64, 4, FAST, SPLIT>(sp, r.tables, im, first, n, lane);
+        else if (im.N == 32) static_item<32, 2, FAST, SPLIT>(sp, r.tables, im, first, n, lane);
+        else static_item<16, 1, FAST, SPLIT>(sp, r.tables, im, first, n, lane);
     }
+}
+
+// Copies the call's records from the launch parameter into the scratch array
+// and sets the work counter to zero. One block; it runs to completion before
+// the diffusion launch that follows it on the same stream.
+__global__ void __launch_bounds__(256) k_noalloc_setup(const __grid_constant__ NoallocRecords rec, StaticScratch *s) {
+    const unsigned int *src = reinterpret_cast<const unsigned int *>(&rec);
+    unsigned int *dst = reinterpret_cast<unsigned int *>(&s->rec);
+    for (int i = threadIdx.x; i < (int)(sizeof(NoallocRecords) / 4); i += blockDim.x) dst[i] = src[i];
+    if (threadIdx.x == 0) s->counter = 0u;
 }
 
 const void *static_kernel(bool fast, bool split) {
@@ -104,24 +121,17 @@ bool device_ptr16(const void *p) {
     return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
 }
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-StaticScratch *g_scratch_addr[kMaxDevices];
-
-// Device address of the scratch array on the current device, looked up once
-// per device (host code cannot use the symbol itself as a device address).
-se2n_status scratch_address(int dev, StaticScratch **out) {
-    if (dev < 0 || dev >= kMaxDevices) return SE2N_EUNSUPPORTED;
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-            (void)cudaGetLastError();
-            return SE2N_ECUDA;
-        }
-        g_scratch_addr[dev] = (StaticScratch *)p;
+// Device address of the scratch array on the current device. Host code
+// cannot use the symbol itself as a device address; the lookup allocates
+// nothing and is repeated on every call, so the address stays right if the
+// device's context is ever created again.
+se2n_status scratch_address(StaticScratch **out) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+        (void)cudaGetLastError();
+        return SE2N_ECUDA;
     }
-    *out = g_scratch_addr[dev];
+    *out = (StaticScratch *)p;
     return SE2N_OK;
 }
 
@@ -150,12 +160,12 @@ extern "C" se2n_status se2n_diffuse_many_noalloc(const se2n_volume_desc *vols, i
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return SE2N_ECUDA;
     StaticScratch *d_scratch = nullptr;
-    se2n_status st = scratch_address(dev, &d_scratch);
+    se2n_status st = scratch_address(&d_scratch);
     if (st != SE2N_OK) return st;
 
-    // The call's records, built on the host stack and copied in one piece;
-    // the copy also sets the shared counter back to zero.
-    StaticScratch h;
+    // The call's records, passed by value to the set-up kernel (which also
+    // sets the shared counter back to zero).
+    NoallocRecords h;
     memset(&h, 0, sizeof(h));
     h.count = count;
     const int Ns[3] = {16, 32, 64};
@@ -178,7 +188,8 @@ extern "C" se2n_status se2n_diffuse_many_noalloc(const se2n_volume_desc *vols, i
         h.prefix[i + 1] = h.prefix[i] + (bi.HW + h.tile[i] - 1) / h.tile[i];
     }
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = cudaMemcpyAsync(d_scratch, &h, sizeof(h), cudaMemcpyHostToDevice, s);
+    k_noalloc_setup<<<1, 256, 0, s>>>(h, d_scratch);
+    cudaError_t e = cudaGetLastError();
     int per_sm = 0;
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, static_kernel(fast, split), 256, 0);
     if (e == cudaSuccess) {

@@ -396,8 +396,12 @@ def se2n_batch_destroy(batch):
 def se2n_diffuse_many_noalloc(volumes, beta, T, steps, angle_conv=0, flags=0, stream=None):
     """volumes: sequence of complex64 device tensors [N][H][W] (diffused in
     place). Calls the entry point that allocates no device memory."""
+    import torch
     descs = (se2n_volume_desc * max(len(volumes), 1))()
     for i, v in enumerate(volumes):
+        if v.dtype != torch.complex64 or not v.is_cuda or v.dim() != 3 or not v.is_contiguous():
+            raise ValueError(f"volume {i}: a contiguous complex64 CUDA tensor [N][H][W] is required "
+                             f"(got {v.dtype}, {tuple(v.shape)}, device {v.device})")
         N, H, W = v.shape
         descs[i] = se2n_volume_desc(_ptr(v), H, W, N)
     _check(lib.se2n_diffuse_many_noalloc(descs, len(volumes), beta, T, steps, angle_conv, flags, _stream(stream)),
