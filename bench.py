@@ -13,10 +13,14 @@ one column pass (DFT along y, propagators, inverse DFT) and one row pass
 --diffusion steps runs the fused step-by-step kernel between cuFFT
 transforms instead, and the default line reports that path too.
 
-Metric: Mathieu updates per second, updates = frequencies x N x steps per
-interval x intervals = 512^2 * 32 * 500 * 10 per inpaint (the method's
-work on all M^2 frequencies), over the whole inpaint time (value), plus ms
-per inpaint, the FP32 error against the FP64 oracle, the roofline of the
+Metric: Mathieu updates per second over the whole inpaint time (value),
+counting the frequencies the path integrates: the lifted volume is real, so
+the H x (W/2 + 1) frequencies of the Hermitian half carry the whole
+spectrum, and updates = 512 * 257 * 32 * 500 * 10 per inpaint (on the
+propagator path these are equivalent updates: each interval's 500 steps
+are applied as one precomputed map). The count over all M^2 frequencies
+that the method's own formulation integrates is reported beside it
+(m2_updates_per_s). Plus ms per inpaint (the first figure of the line), the FP32 error against the FP64 oracle, the roofline of the
 dominant kernel (the column pass against the measured copy rate, with the
 row pass and the propagator build beside it; or the step kernel, FP32 ALU
 bound, whose flops are those of the frequencies it integrates, the
@@ -59,6 +63,31 @@ def _workload():
     return synth.workload_512()
 
 
+def integrated_updates(H, W, N, steps, rounds):
+    """Crank-Nicolson updates of one inpaint over the frequencies the path
+    integrates: the Hermitian half, H x (W/2 + 1) frequencies, N angles,
+    `steps` steps in each of `rounds` intervals."""
+    return H * (W // 2 + 1) * N * steps * rounds
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 GOLDEN_DYNAMIC = os.path.join(ROOT, "tests", "golden", "curves_noise_512_N32_dynamic.npz")
 
 
@@ -68,7 +97,10 @@ def _config(w, extra=None, dynamic=False):
                     f"beta={w.beta}, {w.rounds} restoration intervals x {w.steps} CN steps, T={w.T}, eps={w.eps}, "
                     "80% random mask + 4-px bars every 32 px"
                     + (", dynamic restoration (Section 5.3)" if dynamic else ""),
-        "updates_per_step": w.updates(),
+        "updates_per_step": integrated_updates(w.H, w.W, w.N, w.steps, w.rounds),
+        "updates_basis": "H x (W/2 + 1) frequencies (the Hermitian half the path integrates) x N x steps x "
+                         "intervals; the method's M^2 count is m2_updates_per_step",
+        "m2_updates_per_step": w.updates(),
         "l2": "flushed between timed steps (256 MiB write)",
         "parallelism": "replicas",
     }
@@ -273,7 +305,8 @@ def run_ours(args, rank, world, local_rank):
     total_ms = float(sum(step_ms))
     total_ms = max_over_ranks(total_ms, dist, dev)
     ms_per_step = total_ms / args.steps
-    value = world * w.updates() * args.steps / (total_ms / 1e3)
+    upd = integrated_updates(w.H, w.W, w.N, w.steps, w.rounds)
+    value = world * upd * args.steps / (total_ms / 1e3)
 
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
     peak_basis = "152 SMs x 128 FP32 lanes x 2 flop/FMA x 2070 MHz (derived, not measured)"
@@ -297,6 +330,9 @@ def run_ours(args, rank, world, local_rank):
         row_bytes = 2 * spec_bytes + 6 * w.H * w.W
         col_flops = 2 * wc * w.N * 5 * w.H * int(math.log2(w.H)) + 4 * w.N * w.N * w.H * wc
         flops, products = propagator_gemm_flops(classes, w.N, w.steps)
+        # the symmetric build (N = 16, 32) computes the 10 upper-triangle 8 x 8
+        # tiles of the 16 of every product and mirrors them
+        exec_flops = flops * 10 // 16 if w.N in (16, 32) else flops
         hbm = _peaks().get("hbm_gbs")
         hbm_basis = "MEASURED_PEAKS.json hbm_gbs (copy, burst)"
         roofline = {"bound": "hbm", "achieved": round(col_bytes / c_s / 1e9, 1), "peak": hbm, "unit": "GB/s",
@@ -321,15 +357,18 @@ def run_ours(args, rank, world, local_rank):
                     "build": {"kernel": f"k_prop_build_sym<{w.N}> ({classes} classes, FP32 symmetric products; "
                                         "on a side stream, overlapping the orientation and the first row pass)",
                               "bound": "alu",
-                              "avg_launch_ms": round(b_s * 1e3, 4), "flops_per_launch": flops,
-                              "flops_basis": "classes x products x 2 N^3, "
+                              "avg_launch_ms": round(b_s * 1e3, 4),
+                              "flops_basis": "executed flops: classes x products x 2 N^3 x 10/16 (the symmetric "
+                              "kernel computes the 10 upper-triangle 8x8 tiles of 16 and mirrors them), "
                               f"S = {w.steps}: {products} products (se2n_prop_chain's program; binary powering "
-                              f"takes {w.steps.bit_length() - 1 + bin(w.steps).count('1') - 1}); full products, of "
-                              "which the symmetric kernel performs the 10 upper-triangle tiles of 16",
-                              "achieved_tflops": round(flops / b_s / 1e12, 3), "peak_tflops": round(peak, 3),
-                              "frac": round(flops / b_s / 1e12 / peak, 4), "peak_basis": peak_basis,
+                              f"takes {w.steps.bit_length() - 1 + bin(w.steps).count('1') - 1})",
+                              "flops_per_launch": exec_flops,
+                              "full_product_flops_per_launch": flops,
+                              "achieved_tflops": round(exec_flops / b_s / 1e12, 3), "peak_tflops": round(peak, 3),
+                              "frac": round(exec_flops / b_s / 1e12 / peak, 4), "peak_basis": peak_basis,
+                              "frac_full_product_equivalent": round(flops / b_s / 1e12 / peak, 4),
                               "traffic": stored_traffic("prop_build")},
-                    "frequencies_integrated": "Hermitian half, H x (W/2 + 1) (value counts all M^2 frequencies)"}
+                    "frequencies_integrated": "Hermitian half, H x (W/2 + 1)"}
     else:
         d_ms, d_calls = prof["diffuse"]
         d_avg_s = d_ms / d_calls / 1e3
@@ -342,14 +381,16 @@ def run_ours(args, rank, world, local_rank):
                     "avg_launch_ms": round(d_avg_s * 1e3, 4), "peak_basis": peak_basis,
                     "diffuse_updates_per_s": updates_per_launch / d_avg_s,
                     "hbm_gbs_of_diffuse": round(16 * w.H * (w.W // 2 + 1) * w.N / d_avg_s / 1e9, 1),
-                    "frequencies_integrated": "Hermitian half, H x (W/2 + 1) (value counts all M^2 frequencies)"}
+                    "frequencies_integrated": "Hermitian half, H x (W/2 + 1)"}
     stages = {k: {"ms_per_step": round(v[0] / args.steps, 4), "calls_per_step": v[1] / args.steps}
               for k, v in prof.items() if k != "kernels"}
     launches = int(prof["kernels"])
 
     cfg = _config(w, {"diffusion": "S-step propagators built every inpaint (SE2N_DIFFUSE_PROPAGATOR)" if prop
                       else "step by step, the fused Crank-Nicolson kernel"}, dynamic=dynamic)
-    result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+    result = {"metric": METRIC, "ms_per_inpaint": round(ms_per_step, 4), "value": value, "unit": UNIT,
+              "m2_updates_per_s": world * w.updates() * args.steps / (total_ms / 1e3),
+              "n_gpus": world, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
               "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
               "roofline": roofline, "gpu_launches": launches, "stages_ms": stages,
@@ -389,7 +430,7 @@ def run_ours(args, rank, world, local_rank):
             se2n.se2n_plan_profile(plan, False)
         sd_s = sprof["diffuse"][0] / sprof["diffuse"][1] / 1e3
         s_ach = FLOPS_PER_UPDATE * updates_per_launch / sd_s / 1e12
-        result["propagators_kept"] = {"ms_per_step": round(kept, 4), "value": world * w.updates() / (kept / 1e3)}
+        result["propagators_kept"] = {"ms_per_step": round(kept, 4), "value": world * upd / (kept / 1e3)}
         # the row and column passes timed where nothing runs beside them (in the
         # timed inpaints the build overlaps the orientation and the first row pass)
         c_s = kprof["diffuse"][0] / kprof["diffuse"][1] / 1e3
@@ -406,7 +447,7 @@ def run_ours(args, rank, world, local_rank):
                                      "timed_on": "the inpaints that reuse the propagators; the average over all "
                                                  "row passes of an inpaint (lift and projection included)"})
         result["step_by_step"] = {
-            "ms_per_step": round(stepwise, 4), "value": world * w.updates() / (stepwise / 1e3),
+            "ms_per_step": round(stepwise, 4), "value": world * upd / (stepwise / 1e3),
             "roofline": {"bound": "alu", "kernel": "k_diffuse_x2<32,2,false>", "avg_launch_ms": round(sd_s * 1e3, 4),
                          "achieved": round(s_ach, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
                          "frac": round(s_ach / peak, 4), "traffic": stored_traffic(),
@@ -446,7 +487,7 @@ def run_ours(args, rank, world, local_rank):
         se2n.se2n_inpaint_host(plan, f_h.data_ptr(), m_h.data_ptr(), prm, o_h.data_ptr())
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_step = statistics.median(e2e_ms)
-    result["e2e"] = {"value": world * w.updates() / (e2e_step / 1e3), "unit": UNIT,
+    result["e2e"] = {"value": world * upd / (e2e_step / 1e3), "unit": UNIT,
                      "ms_per_step": e2e_step, "h2d_bytes_per_step": f32.nbytes + w.mask.nbytes,
                      "d2h_bytes_per_step": o_h.numel() * 4, "api": "se2n_inpaint_host (pinned host buffers)"}
 
@@ -481,24 +522,49 @@ def run_ours(args, rank, world, local_rank):
 # the oracle as CPU baseline / reference arm
 # ----------------------------------------------------------------------------
 
-def _oracle_sample(w, steps, rounds, dynamic=False):
+def _oracle_sample(w, steps, rounds, dynamic=False, nthreads=None):
+    """The oracle's whole inpaint of the workload's image with `rounds`
+    intervals of `steps` steps (same dt), on `nthreads` threads (all host
+    cores by default). Returns (updates, seconds), updates counted like our
+    arm's value (the Hermitian half; the oracle itself integrates all M^2
+    frequencies, so per such update it does twice the work)."""
     import oracle
     p = oracle.Params(N=w.N, beta=w.beta, T=w.T / w.rounds * rounds, steps=steps, rounds=rounds, eps=w.eps,
                       dynamic=int(dynamic))
     f = w.f.astype(np.float32).astype(np.float64)
     t0 = time.perf_counter()
-    oracle.inpaint(f, w.mask, p)
+    oracle.inpaint(f, w.mask, p, nthreads=nthreads or os.cpu_count())
     dt = time.perf_counter() - t0
-    return w.H * w.W * w.N * steps * rounds, dt
+    return integrated_updates(w.H, w.W, w.N, steps, rounds), dt
 
 
 def cpu_baseline(w, steps=75, rounds=2, dynamic=False):
-    upd, dt = _oracle_sample(w, steps, rounds, dynamic)
-    return {"value": upd / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+    """The oracle as it stands on this host: a bounded sample of the workload
+    on all cores, a smaller one on one core, and the time of the full run
+    that wrote the stored reference result."""
+    cores = os.cpu_count()
+    upd, dt = _oracle_sample(w, steps, rounds, dynamic, nthreads=cores)
+    s1 = max(steps // 4, 5)
+    upd1, dt1 = _oracle_sample(w, s1, rounds, dynamic, nthreads=1)
+    _oracle_sample(w, 1, 1, dynamic, nthreads=cores)  # the OpenMP thread count back to all cores
+    golden = GOLDEN_DYNAMIC if dynamic else GOLDEN
+    full = None
+    if os.path.exists(golden):
+        g = np.load(golden)
+        full = {"seconds": round(float(g["oracle_seconds"][0]), 2),
+                "run": f"the FP64 oracle's complete {w.rounds} x {w.steps}-step inpaint that wrote "
+                       f"tests/golden/{os.path.basename(golden)} (tests/golden/make_references.py, 8-core x86 host)",
+                "value": integrated_updates(w.H, w.W, w.N, w.steps, w.rounds) / float(g["oracle_seconds"][0])}
+    return {"value": upd / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
             "sample": f"the FP64 oracle's whole inpaint of the same 512x512 N=32 image with {rounds} intervals "
-                      f"x {steps} CN steps ({upd:.3g} updates, {dt:.1f} s)"
+                      f"x {steps} CN steps ({upd:.3g} updates counted like value, {dt:.1f} s)"
                       + (", dynamic restoration" if dynamic else "")
-                      + ", all host cores (OpenMP over frequencies, numpy FFTs)"}
+                      + ", all host cores (OpenMP over frequencies, numpy FFTs)",
+            "one_core": {"value": upd1 / dt1, "unit": UNIT, "cores": 1,
+                         "sample": f"{rounds} intervals x {s1} CN steps ({upd1:.3g} updates, {dt1:.1f} s), one "
+                                   "OpenMP thread"},
+            "full_run_stored": full,
+            "build": "gcc -O3 -fopenmp (portable flags: the same source and results on x86_64 and aarch64)"}
 
 
 def run_batch(args, rank, world, local_rank):
@@ -532,7 +598,9 @@ def run_batch(args, rank, world, local_rank):
     create_s = time.perf_counter() - t0
     info = se2n.se2n_batch_get_info(batch)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    updates = info["updates_per_run"]
+    # updates over the frequencies integrated (the Hermitian half of every
+    # image's spectrum); the library's count over all M^2 is updates_per_run
+    updates = sum(integrated_updates(w.H, w.W, w.N, w.steps, w.rounds) for w in mine)
 
     def timed(fn, k):
         evs = []
@@ -603,6 +671,9 @@ def run_batch(args, rank, world, local_rank):
             "config": {"workload": "batch of 256 seeded images, sides from {128,256,384,512,768,1024}, N U{16,32,64}, "
                                    "60-90% corrupted, beta=0.25, T=2, 100 CN steps, 1 interval",
                        "images_this_rank": len(mine), "updates_per_step": total_updates,
+                       "updates_basis": "H x (W/2 + 1) frequencies (the Hermitian half) x N x steps, summed over "
+                                        "the images; m2_updates_per_step counts all H x W",
+                       "m2_updates_per_step": info["updates_per_run"] * world,
                        "diffusion": ("S-step propagators for the shapes where they are estimated cheaper "
                                      f"({info['prop_images']} images; {info['fused_images']} of them, the "
                                      "power-of-two planes with N = 16 or 32, whole inpaints on the row and column "
@@ -1056,7 +1127,7 @@ def run_reference(args, rank, world):
             pp = oracle.Params(N=w.N, beta=w.beta, T=w.T * steps / w.steps, steps=steps, rounds=1, eps=w.eps)
             t0 = time.perf_counter()
             oracle.inpaint(w.f, w.mask, pp)
-            return w.H * w.W * w.N * steps, time.perf_counter() - t0
+            return integrated_updates(w.H, w.W, w.N, steps, 1), time.perf_counter() - t0
         for k in range(args.warmup):
             one(k)
         upd, total = 0, 0.0
@@ -1082,7 +1153,8 @@ def run_reference(args, rank, world):
     total = sum(times)
     value = upd * args.steps / total
     sample = (f"each step: the FP64 oracle's inpaint of the 512x512 N=32 image with {rounds} interval(s) x {steps} "
-              f"CN steps ({upd:.3g} updates){', dynamic restoration' if dynamic else ''}, all host cores")
+              f"CN steps ({upd:.3g} updates counted like our arm's value){', dynamic restoration' if dynamic else ''}, "
+              f"all host cores ({cpu_model()})")
     return _reference_line(args, world, METRIC, UNIT, value, total / args.steps * 1e3,
                            _config(w, {"reference_sample": f"{rounds} x {steps} steps per step"}, dynamic=dynamic),
                            sample)

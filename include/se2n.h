@@ -94,7 +94,14 @@ typedef enum se2n_status {
  * allocates that buffer and a second stream of the plan, on which each
  * build runs beside the orientation and the lift (ordered after the work
  * already on the plan's stream, joined before the first column pass);
- * call once before capturing se2n_inpaint into a graph. */
+ * call once before capturing se2n_inpaint into a graph.
+ * Accuracy guard: the FP32 powering in increment form cancels digits when
+ * a Crank-Nicolson factor (1 - dt lambda/2) / (1 + dt lambda/2) of the
+ * system approaches -1 (stiff modes at large beta dt). The flag is therefore
+ * honoured only where every such factor is >= 0, i.e. dt (2 + 4 beta) <= 2
+ * (lambda <= max a_r^2 + 4 beta <= 2 + 4 beta); for a larger dt the call runs
+ * the step-by-step kernel instead (same result within the 1e-5 bound; the
+ * plan's profile then counts no propagator build). */
 #define SE2N_DIFFUSE_PROPAGATOR 8
 
 /* Largest N the library has kernels for. */
@@ -491,25 +498,29 @@ SE2N_API se2n_status se2n_surrogate_inpaint(se2n_unet *u, se2n_plan *plan, const
  * that cannot afford the implicit device-wide synchronisation cudaMalloc and
  * cudaFree may cause.
  *
- * It integrates eq. (deceq) exactly as se2n_diffuse does, for up to
+ * It integrates the same per-frequency Crank-Nicolson systems as
+ * se2n_diffuse, with the same per-frequency kernel code, for up to
  * SE2N_NOALLOC_MAX_VOLUMES transformed volumes (N = 16, 32 or 64, H and W
  * even) in one persistent launch, in place. The caller passes the volumes;
  * the only other memory used is a fixed array of SE2N_NOALLOC_SCRATCH_BYTES
  * bytes compiled into the library, which every GPU that loads the library
  * holds until the process exits. No cudaMalloc, cudaFree or allocating
- * library routine is called.
+ * library routine is called, and nothing is copied from host memory: the
+ * call's records (volume pointers, sizes, angle tables) travel as the launch
+ * parameter of a small set-up kernel that writes them into the array and
+ * sets its work counter to zero, followed by the diffusion launch. Both are
+ * enqueued on `stream` and the call returns without waiting for the GPU.
  *
  * All calls share that array and it keeps the last call's contents; each
- * call resets what must start at zero. Calls that overlap on the GPU (on
- * different streams, or from several threads without ordering) race on the
- * array and give wrong results: order them. The first call on a device looks
- * up the array's device address (once per device); make that first call
- * before any stream capture. flags: SE2N_DIFFUSE_SPLIT_DIAG and
- * SE2N_DIFFUSE_FULL_CORRECTION as for se2n_diffuse (the FP64 correction is
- * not offered here). SE2N_EINVAL for count < 1 or count >
- * SE2N_NOALLOC_MAX_VOLUMES, bad sizes, parameters or pointers;
- * SE2N_EUNSUPPORTED for another N. The host copy of the call's records
- * waits for earlier work on the stream to finish. */
+ * call rewrites what it needs. Calls that overlap on the GPU (on different
+ * streams, or from several threads without ordering) race on the array and
+ * give wrong results: order them. The array's device address is looked up
+ * on every call (no allocation); the first call on a device also loads the
+ * library's device code, so make that first call before any stream capture.
+ * flags: SE2N_DIFFUSE_SPLIT_DIAG and SE2N_DIFFUSE_FULL_CORRECTION as for
+ * se2n_diffuse (the FP64 correction is not offered here). SE2N_EINVAL for
+ * count < 1 or count > SE2N_NOALLOC_MAX_VOLUMES, bad sizes, parameters or
+ * pointers; SE2N_EUNSUPPORTED for another N. */
 #define SE2N_NOALLOC_MAX_VOLUMES 64
 #define SE2N_NOALLOC_SCRATCH_BYTES 8192
 

@@ -385,7 +385,7 @@ def dr_grow(vol, mask, fref, bins, dtype=np.float64, return_margin=False):
 # the whole method
 # ----------------------------------------------------------------------------
 
-def inpaint(f, mask, p: Params, bins=None, nthreads=0, keep=False, tie_tol=0.0):
+def inpaint(f, mask, p: Params, bins=None, nthreads=0, keep=False, tie_tol=0.0, store=None):
     """Lift, then `rounds` intervals of length T/rounds: the first starts
     from the lift; each later one starts from the statically restored state
     (the mix at t_0 is the identity, sigma = 1). The state at T is inverted
@@ -400,7 +400,15 @@ def inpaint(f, mask, p: Params, bins=None, nthreads=0, keep=False, tie_tol=0.0):
     equal to the given one without dynamic), the smallest decision margin of
     the growth steps (dr_margin, inf without dynamic), the pixels whose
     decision came within tie_tol of a tie in some growth step (dr_ties) and,
-    if keep, the final volume."""
+    if keep, the final volume.
+
+    store: a function applied to the volume at every point where an
+    implementation of the method keeps it in memory between two stages
+    (after the lift, each transform, each diffusion and each restoration);
+    None is the identity. Rounding it to complex64 there measures how far
+    FP32 storage alone moves the FP64 result (the sensitivity that bounds
+    any FP32 implementation from below); it changes no arithmetic of the
+    method."""
     if bins is None:
         bins = orient(f, mask, p.N, p.sigma, p.angle_conv, p.flat_tol)["bins"]
     g_mask = (np.asarray(mask) != 0).astype(np.uint8)
@@ -417,15 +425,16 @@ def inpaint(f, mask, p: Params, bins=None, nthreads=0, keep=False, tie_tol=0.0):
             ties |= m < tie_tol
         return mix(v, g_fref, g_mask, g_bins, p.eps, p.guard)
 
+    st = store if store is not None else (lambda x: x)
     Tr = p.T / p.rounds
-    v = forward(lift(f, mask, bins, p.N))
-    v = diffuse(v, p.beta, Tr, p.steps, p.angle_conv, nthreads=nthreads)
+    v = st(forward(st(lift(f, mask, bins, p.N))))
+    v = st(diffuse(v, p.beta, Tr, p.steps, p.angle_conv, nthreads=nthreads))
     for _ in range(1, p.rounds):
-        v = restore(inverse(v))
-        v = diffuse(forward(v), p.beta, Tr, p.steps, p.angle_conv, nthreads=nthreads)
-    v = inverse(v)
+        v = st(restore(st(inverse(v))))
+        v = st(diffuse(st(forward(v)), p.beta, Tr, p.steps, p.angle_conv, nthreads=nthreads))
+    v = st(inverse(v))
     if p.final_mix:
-        v = restore(v)
+        v = st(restore(v))
     out = project(v, p.proj)
     if p.reinject:
         out = np.where(np.asarray(mask) != 0, np.asarray(f, dtype=np.float64), out)

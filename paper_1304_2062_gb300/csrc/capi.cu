@@ -167,6 +167,19 @@ void prop_join(se2n_plan *plan) {
     plan->join_pending = false;
 }
 
+// Whether the propagator form keeps the 1e-5 accuracy of the step kernel.
+// The build raises M = B-^-1 B+ to the power S in increment form, D -> 2D + D^2
+// for a squaring. For an eigenvalue mu of M that is >= 0, D = mu - 1 lies in
+// [-1, 0] and no product cancels; as mu approaches -1 (stiff modes at large
+// beta dt), D approaches -2, 2D + D^2 cancels to a small number and FP32
+// loses digits at every squaring (measured on the GPU: N = 64, S = 30,
+// beta dt = 10 gave 1.3e-5 against the oracle). So propagators are used only
+// where every mu = (1 - dt lambda / 2) / (1 + dt lambda / 2) is >= 0, i.e.
+// dt lambda <= 2 for the largest eigenvalue lambda of -A; by Gershgorin
+// lambda <= max a_r^2 + 4 beta <= 2 + 4 beta (a_r^2 <= wx^2 + wy^2 <= 2).
+// Elsewhere the step kernel runs instead.
+bool prop_admissible(double beta, double dt) { return dt * (2.0 + 4.0 * beta) <= 2.0; }
+
 // The S-step propagators of every class of frequencies, built when beta dt,
 // S, the spectrum half or the storage changed. With side = true the build
 // runs on the plan's side stream after everything queued on the plan's
@@ -229,7 +242,8 @@ se2n_status propagate_impl(se2n_plan *plan, float2 *vol, double beta, double bdt
 // row-transformed volume [Wc][H][N] complex and the twiddle tables.
 bool col_path(const se2n_plan *plan, const se2n_params *p) {
     return !p->full_spectrum && p->diffuse_flags == SE2N_DIFFUSE_PROPAGATOR &&
-           se2n_col_supported(plan->N, plan->H) && se2n_row_supported(plan->N, plan->W);
+           prop_admissible(p->beta, p->T / p->rounds / p->steps) && se2n_col_supported(plan->N, plan->H) &&
+           se2n_row_supported(plan->N, plan->W);
 }
 
 // exp(-2 pi i m / n), m < n, from the exact fraction m / n
@@ -345,7 +359,11 @@ se2n_status diffuse_impl(se2n_plan *plan, float2 *vol, double beta, double T, in
     const double dt = T / steps;
     const double bdt = beta * dt;
     if (!(bdt >= 1e-30 && bdt <= 1e3)) return SE2N_ENUMERIC;
-    if (flags & SE2N_DIFFUSE_PROPAGATOR) return propagate_impl(plan, vol, beta, bdt, steps, half);
+    if (flags & SE2N_DIFFUSE_PROPAGATOR) {
+        if (!se2n_prop_supported(plan->N)) return SE2N_EUNSUPPORTED;
+        if (prop_admissible(beta, dt)) return propagate_impl(plan, vol, beta, bdt, steps, half);
+        flags &= ~SE2N_DIFFUSE_PROPAGATOR;  // stiff: the step kernel keeps the accuracy
+    }
     const bool fp64 = (flags & SE2N_DIFFUSE_SM_FP64) != 0;
     // The fused diagonal 2 + a^2/beta perturbs decay rates by ~1.2e-7 beta per
     // unit time; past beta T = 8 that exceeds 1e-6 and the split form is used.
@@ -1139,6 +1157,7 @@ void choose_propagators(se2n_batch *b) {
     b->prop_images = 0;
     b->fused_images = 0;
     if (!(p.diffuse_flags & SE2N_DIFFUSE_PROPAGATOR)) return;
+    if (!prop_admissible(p.beta, p.T / p.rounds / p.steps)) return;
     const bool half = !p.full_spectrum;
     const int S = p.steps;
     int products = -1;

@@ -23,6 +23,39 @@ MAX_REL = 1e-5
 MAX_REL_RESTORED = 1e-4
 
 
+def restoration_sigma_max(f64, mask, bins, p):
+    """The largest factor sigma = (eps h(0) + (1-eps) h(t_i)) / h(t_i) that
+    the static restoration (Section 5) applies to a good pixel in the FP64
+    oracle's run of the method: an absolute error d of the volume at that
+    pixel leaves the restoration as sigma * d, so sigma measures how
+    strongly the restoration amplifies FP32 rounding."""
+    import oracle
+    lifted = oracle.lift(f64, mask, bins, p.N)
+    h0 = lifted.real.max(axis=0)
+    good = np.asarray(mask) != 0
+    Tr = p.T / p.rounds
+    v = oracle.diffuse(oracle.forward(lifted), p.beta, Tr, p.steps, p.angle_conv)
+    worst = 1.0
+    for _ in range(1, p.rounds):
+        x = oracle.inverse(v)
+        ht = x.real.max(axis=0)
+        scaled = good & (ht > p.guard * h0) & (ht > 0.0)
+        if scaled.any():
+            worst = max(worst, float(((p.eps * h0[scaled] + (1.0 - p.eps) * ht[scaled]) / ht[scaled]).max()))
+        v = oracle.diffuse(oracle.forward(oracle.mix(x, f64, mask, bins, p.eps, p.guard)), p.beta, Tr, p.steps,
+                           p.angle_conv)
+    return worst
+
+
+def max_rel_for_sigma(sigma_max):
+    """Max-abs bound (relative to max|f|) of a multi-interval result whose
+    restorations scale a good pixel by at most sigma_max: MAX_REL up to
+    sigma = 10 (measured on the GPU at guard 0: sigma 7.3 and 9.9 stay
+    below it), growing in proportion to sigma beyond, since the restoration
+    multiplies an absolute error at the pixel by sigma."""
+    return MAX_REL * max(1.0, sigma_max / 10.0)
+
+
 def dev():
     return torch.device("cuda:0")
 

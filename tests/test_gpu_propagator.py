@@ -18,7 +18,7 @@ import pytest
 
 import oracle
 import synth
-from _gpu import MAX_REL_RESTORED, REL_L2, host, rel_l2, t_c64, t_f32, t_u8
+from _gpu import MAX_REL_RESTORED, REL_L2, host, max_rel_for_sigma, rel_l2, restoration_sigma_max, t_c64, t_f32, t_u8
 
 pytestmark = pytest.mark.gpu
 
@@ -59,6 +59,34 @@ def test_propagator_matches_oracle(N, H, W, beta, T, S):
           f"vs the step kernel {e_steps:.2e}")
     assert e_ref <= REL_L2
     assert e_steps <= 2 * REL_L2
+
+
+@pytest.mark.parametrize("N,H,W,beta,T,S,builds", [
+    (64, 18, 14, 10.0, 30.0, 30, 0),     # beta dt = 10: propagators measured at 1.3e-5, the step kernel runs
+    (32, 18, 14, 10.0, 30.0, 30, 0),
+    (32, 18, 14, 0.5, 0.5, 1, 1),        # one step of dt = 0.5: dt (2 + 4 beta) = 2, admitted
+    (32, 18, 14, 0.25, 2.0, 3, 1),       # dt = 2/3: dt (2 + 4 beta) = 2, the edge, still admitted
+    (32, 18, 14, 0.25, 2.0, 2, 0)])      # dt = 1: dt (2 + 4 beta) = 3 > 2
+def test_stiff_steps_fall_back_to_the_step_kernel(N, H, W, beta, T, S, builds):
+    """The propagator form is used only where every Crank-Nicolson factor of
+    the system is >= 0 (dt (2 + 4 beta) <= 2); elsewhere the step kernel
+    runs, and the result is within the bound either way."""
+    vol = synth.random_volume(N, H, W, seed=7 + N + S).astype(np.complex64)
+    ref = oracle.diffuse(vol.astype(np.complex128), beta, T, S)
+    plan = se2n.se2n_plan_create(H, W, N)
+    se2n.se2n_plan_profile(plan, True)
+    v = t_c64(vol)
+    se2n.se2n_diffuse(plan, v, beta, T, S, PROP)
+    got = host(v)
+    prof = se2n.se2n_plan_profile_read(plan)
+    plan.close()
+    dt = T / S
+    expect = 1 if dt * (2 + 4 * beta) <= 2 else 0
+    assert expect == builds
+    assert prof["propagator"][1] == builds
+    err = rel_l2(got, ref)
+    print(f"N={N} beta*dt={beta * dt:.3g} S={S}: {'propagator' if builds else 'step kernel'}, rel-L2 {err:.2e}")
+    assert err <= REL_L2
 
 
 def test_lifted_image_spectrum():
@@ -192,6 +220,30 @@ def test_row_and_column_passes_match_oracle(H, W, N, dynamic, final_mix, proj, r
     assert prof["fft"][1] == 4 + (2 + final_mix if dynamic else 0)
     assert prof["dr"][1] == (2 + final_mix if dynamic else 0) and prof["mix"][1] == 0
     assert mx <= MAX_REL_RESTORED
+    assert r2 <= REL_L2
+
+
+@pytest.mark.parametrize("H,W,N", [(64, 128, 32), (128, 64, 16), (128, 128, 32), (96, 96, 32)])
+def test_paper_sigma_rule_guard_zero_on_the_propagator_paths(H, W, N):
+    """Section 5's restoration with no relative guard (guard = 0 on both
+    sides) on the row and column passes (power-of-two planes) and on the
+    separate propagator apply (96 x 96), several intervals; the max-abs bound
+    is MAX_REL up to a largest restoration factor sigma of 10 and grows with
+    sigma beyond (64x128 reaches 233 at guard 0)."""
+    w = synth.workload_512(H=H, W=W, steps=60, rounds=3)
+    p = oracle.Params(N=N, beta=0.25, T=6.0, steps=60, rounds=3, guard=0.0)
+    f32 = w.f.astype(np.float32)
+    f64 = f32.astype(np.float64)
+    bins = oracle.orient(f64, w.mask, p.N, p.sigma, 0, p.flat_tol)["bins"]
+    ref = oracle.inpaint(f64, w.mask, p, bins=bins)["out"]
+    got, prof = _gpu_inpaint(f32, w.mask, bins, _params(p), profile=True)
+    mx = np.abs(got - ref).max() / np.abs(f64).max()
+    r2 = rel_l2(got, ref)
+    sig = restoration_sigma_max(f64, w.mask, bins, p)
+    print(f"guard 0, {H}x{W} N={N}: max-abs/max|f| {mx:.2e}, rel-L2 {r2:.2e}, largest sigma {sig:.3g}, "
+          f"bound {max_rel_for_sigma(sig):.2e}")
+    assert prof["propagator"][1] == 1
+    assert mx <= max_rel_for_sigma(sig)
     assert r2 <= REL_L2
 
 
