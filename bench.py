@@ -215,6 +215,16 @@ def propagator_classes(H, W, half=True):
     return row_slots * cols
 
 
+def propagator_build_items(H, W, half=True):
+    """Classes the build computes: on square planes (Hermitian half) a class
+    and its transpose share one build, so n (n + 1) / 2 of the n x n slot
+    pairs; otherwise every class."""
+    if half and H == W:
+        n = W // 4 + 1
+        return n * (n + 1) // 2
+    return propagator_classes(H, W, half)
+
+
 def max_over_ranks(value, dist=None, device="cpu"):
     """The largest value over all ranks (the job's time is its slowest rank's)."""
     if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
@@ -329,7 +339,8 @@ def run_ours(args, rank, world, local_rank):
         col_bytes = 2 * spec_bytes + 4 * w.N * w.N * classes
         row_bytes = 2 * spec_bytes + 6 * w.H * w.W
         col_flops = 2 * wc * w.N * 5 * w.H * int(math.log2(w.H)) + 4 * w.N * w.N * w.H * wc
-        flops, products = propagator_gemm_flops(classes, w.N, w.steps)
+        items = propagator_build_items(w.H, w.W)
+        flops, products = propagator_gemm_flops(items, w.N, w.steps)
         # the symmetric build (N = 16, 32) computes the 10 upper-triangle 8 x 8
         # tiles of the 16 of every product and mirrors them
         exec_flops = flops * 10 // 16 if w.N in (16, 32) else flops
@@ -354,11 +365,12 @@ def run_ours(args, rank, world, local_rank):
                                  "achieved_gbs": round(row_bytes / r_s / 1e9, 1), "peak_gbs": hbm,
                                  "frac": round(row_bytes / r_s / 1e9 / hbm, 4) if hbm else None,
                                  "traffic": stored_traffic("row_pass")},
-                    "build": {"kernel": f"k_prop_build_sym<{w.N}> ({classes} classes, FP32 symmetric products; "
-                                        "on a side stream, overlapping the orientation and the first row pass)",
+                    "build": {"kernel": f"k_prop_build_sym<{w.N}> ({items} of the {classes} classes computed, each "
+                                        "also stored permuted for its transpose; FP32 symmetric products; on a side "
+                                        "stream, overlapping the orientation and the first row pass)",
                               "bound": "alu",
                               "avg_launch_ms": round(b_s * 1e3, 4),
-                              "flops_basis": "executed flops: classes x products x 2 N^3 x 10/16 (the symmetric "
+                              "flops_basis": "executed flops: classes built x products x 2 N^3 x 10/16 (the symmetric "
                               "kernel computes the 10 upper-triangle 8x8 tiles of 16 and mirrors them), "
                               f"S = {w.steps}: {products} products (se2n_prop_chain's program; binary powering "
                               f"takes {w.steps.bit_length() - 1 + bin(w.steps).count('1') - 1})",

@@ -133,6 +133,12 @@ PropArgs prop_args(se2n_plan *plan, float2 *vol, double beta, double bdt, int st
     a.half = half ? 1 : 0;
     a.col_slots = se2n_prop_col_slots(plan->W, half);
     a.classes = se2n_prop_classes(plan->H, plan->W, half);
+    // square planes on the Hermitian half: a class and its transpose share
+    // one build (the angle reflection th -> pi/2 - th maps one operator onto
+    // the other; on the 2 pi r / N grid it needs 4 | N)
+    a.share_t = half && plan->H == plan->W && (plan->angle_conv == 0 || plan->N % 4 == 0) ? 1 : 0;
+    a.perm_shift = plan->angle_conv ? plan->N / 4 : plan->N / 2;
+    a.items = a.share_t ? (long long)a.col_slots * (a.col_slots + 1) / 2 : a.classes;
     a.steps = steps;
     a.inv_c = (float)(2.0 / bdt);
     a.inv_beta = (float)(1.0 / beta);

@@ -83,6 +83,39 @@ __device__ __forceinline__ void class_slots(const PropArgs &a, long long u, int 
     }
 }
 
+// The class that build item w computes, and the class that receives it
+// permuted (its transpose) or -1. Without sharing, item w is class w. With
+// sharing (square planes, Hermitian half) the items are the n (n + 1) / 2
+// slot pairs i <= j of the n x n grid of row and column slots, row by row:
+// class (i, j) has wy = sin(2 pi i / H), wx = sin(2 pi j / W), and class
+// (j, i) swaps them; a_r = wx cos th_r + wy sin th_r becomes a at the angle
+// pi/2 - th_r, i.e. index perm_shift - r, so the transpose's operator is
+// P A P with the permutation P: r -> (perm_shift - r) mod N (which keeps the
+// cyclic second difference), and its propagator is P D_S P.
+__device__ __forceinline__ long long build_class(const PropArgs &a, long long w, long long &partner) {
+    if (!a.share_t) {
+        partner = -1;
+        return w;
+    }
+    const long long n = a.col_slots;
+    // row i starts at item i n - i (i - 1) / 2
+    const double b = 2.0 * (double)n + 1.0;
+    long long i = (long long)((b - sqrt(b * b - 8.0 * (double)w)) * 0.5);
+    if (i < 0) i = 0;
+    while (i > 0 && i * n - i * (i - 1) / 2 > w) --i;
+    while ((i + 1) * n - (i + 1) * i / 2 <= w) ++i;
+    const long long j = i + (w - (i * n - i * (i - 1) / 2));
+    partner = i != j ? j * n + i : -1;
+    return i * n + j;
+}
+
+// Entry (i, j) of the stored matrix of class u: P D_S P for a transposed
+// partner (shift = perm_shift), D_S itself (shift < 0).
+template <int N>
+__device__ __forceinline__ int perm_index(int i, int shift) {
+    return shift < 0 ? i : (shift - i) & (N - 1);
+}
+
 // out = two * X + Y + A B for one class, N x N in shared memory: A, X, Y and
 // out column-major, B row-major (stride LD), Y may be null, out_row (if not
 // null) receives the result row-major too. Every lane of the warp calls this
@@ -234,22 +267,31 @@ struct SymCfg;
 
 // D_S of class u from a symmetric matrix in the layout of SymCfg<N>: as rows
 // in 16-byte chunks, chunk-major, or by cyclic diagonals; lanes t of `lanes`.
+// shift >= 0 stores the permuted matrix P D_S P of a transposed class.
 template <int N>
 __device__ __forceinline__ void prop_store(const PropArgs &a, const float *Rm, long long u, bool live, int t,
-                                           int lanes) {
+                                           int lanes, int shift = -1) {
     using C = SymCfg<N>;
-    if (!live) return;
+    if (!live || u < 0) return;
     if (a.rows) {
         float4 *out = reinterpret_cast<float4 *>(a.D + u * (long long)(N * N));
         for (int e = t; e < N * N / 4; e += lanes) {
             const int c = e / N, i = e - c * N;
-            out[e] = *reinterpret_cast<const float4 *>(Rm + C::at(i, 4 * c));
+            if (shift < 0) {
+                out[e] = *reinterpret_cast<const float4 *>(Rm + C::at(i, 4 * c));
+            } else {
+                const int pi = perm_index<N>(i, shift);
+                out[e] = make_float4(Rm[C::at(pi, perm_index<N>(4 * c, shift))],
+                                     Rm[C::at(pi, perm_index<N>(4 * c + 1, shift))],
+                                     Rm[C::at(pi, perm_index<N>(4 * c + 2, shift))],
+                                     Rm[C::at(pi, perm_index<N>(4 * c + 3, shift))]);
+            }
         }
     } else {
         float *out = a.D + u * (long long)((N / 2 + 1) * N);
         for (int e = t; e < (N / 2 + 1) * N; e += lanes) {
             const int m = e / N, i = e - m * N;
-            out[e] = Rm[C::at(i, (i + m) & (N - 1))];
+            out[e] = Rm[C::at(perm_index<N>(i, shift), perm_index<N>((i + m) & (N - 1), shift))];
         }
     }
 }
@@ -269,11 +311,12 @@ __global__ void __launch_bounds__(PropCfg<N>::WARPS * 32) k_prop_build(const __g
     // warp-major over the grid: where the classes do not divide evenly, the
     // warps that take one chunk more are spread over the blocks (and SMs)
     // instead of filling the first blocks
-    for (long long u0 = ((long long)warp * gridDim.x + blockIdx.x) * C::CPW; u0 < a.classes; u0 += stride) {
-        const long long u = u0 + g;
-        const bool live = u < a.classes;
+    for (long long u0 = ((long long)warp * gridDim.x + blockIdx.x) * C::CPW; u0 < a.items; u0 += stride) {
+        const bool live = u0 + g < a.items;
+        long long partner;
+        const long long u = build_class(a, live ? u0 + g : a.items - 1, partner);
         int k, l, lb;
-        class_slots(a, live ? u : a.classes - 1, k, l, lb);
+        class_slots(a, u, k, l, lb);
         const float wx = sin_2pi_frac(l, a.W), wy = sin_2pi_frac(k, a.H);
         if (t == 0) prop_factor<N>(a, wx, wy, G, q, scal);
         __syncwarp();
@@ -365,38 +408,45 @@ __global__ void __launch_bounds__(PropCfg<N>::WARPS * 32) k_prop_build(const __g
             __syncwarp();
         }
         if (!a.chain_in_r) R = P;
-        // D_S symmetrised, as rows in 16-byte chunks stored chunk-major
-        // (D[i][4c .. 4c + 3] at float4 c N + i): this lane writes rows i = t,
-        // t + LPC, ..., consecutive lanes consecutive chunks
-        if (live && a.rows) {
-            float4 *out = reinterpret_cast<float4 *>(a.D + u * (long long)(N * N));
+        // D_S symmetrised, and for a transposed partner P D_S P as well
 #pragma unroll 1
-            for (int cc = 0; cc < C::CPL; ++cc) {
-                const int i = t + cc * C::LPC;
+        for (int pass = 0; pass < 2; ++pass) {
+            const long long v = pass ? partner : u;
+            const int sh = pass ? a.perm_shift : -1;
+            if (!live || v < 0) continue;
+            // as rows in 16-byte chunks stored chunk-major (D[i][4c .. 4c + 3]
+            // at float4 c N + i): this lane writes rows i = t, t + LPC, ...,
+            // consecutive lanes consecutive chunks
+            if (a.rows) {
+                float4 *out = reinterpret_cast<float4 *>(a.D + v * (long long)(N * N));
+#pragma unroll 1
+                for (int cc = 0; cc < C::CPL; ++cc) {
+                    const int i = t + cc * C::LPC, pi = perm_index<N>(i, sh);
 #pragma unroll 2
-                for (int c = 0; c < N / 4; ++c) {
-                    float d[4];
+                    for (int c = 0; c < N / 4; ++c) {
+                        float d[4];
 #pragma unroll
-                    for (int m = 0; m < 4; ++m) {
-                        const int j = 4 * c + m;
-                        d[m] = 0.5f * (R[j * C::LD + i] + R[i * C::LD + j]);
+                        for (int m = 0; m < 4; ++m) {
+                            const int j = perm_index<N>(4 * c + m, sh);
+                            d[m] = 0.5f * (R[j * C::LD + pi] + R[pi * C::LD + j]);
+                        }
+                        out[c * N + i] = make_float4(d[0], d[1], d[2], d[3]);
                     }
-                    out[c * N + i] = make_float4(d[0], d[1], d[2], d[3]);
                 }
-            }
-        }
-        // D_S by cyclic diagonals: this lane writes S_m[i] for i = t, t + LPC, ...
-        // (R is column-major: D[i, j] = R[j LD + i]; both reads run at stride
-        // LD + 1 across the lanes, free of bank conflicts)
-        if (live && !a.rows) {
-            float *out = a.D + u * (long long)C::SBLK;
+            } else {
+                // by cyclic diagonals: this lane writes S_m[i] for i = t, t +
+                // LPC, ... (R is column-major: D[i, j] = R[j LD + i]; without
+                // the permutation both reads run at stride LD + 1 across the
+                // lanes, free of bank conflicts)
+                float *out = a.D + v * (long long)C::SBLK;
 #pragma unroll 1
-            for (int cc = 0; cc < C::CPL; ++cc) {
-                const int i = t + cc * C::LPC;
+                for (int cc = 0; cc < C::CPL; ++cc) {
+                    const int i = t + cc * C::LPC, pi = perm_index<N>(i, sh);
 #pragma unroll 4
-                for (int m = 0; m <= N / 2; ++m) {
-                    const int j = (i + m) & (N - 1);
-                    out[m * N + i] = 0.5f * (R[j * C::LD + i] + R[i * C::LD + j]);
+                    for (int m = 0; m <= N / 2; ++m) {
+                        const int j = perm_index<N>((i + m) & (N - 1), sh);
+                        out[m * N + i] = 0.5f * (R[j * C::LD + pi] + R[pi * C::LD + j]);
+                    }
                 }
             }
         }
@@ -562,11 +612,12 @@ __global__ void __launch_bounds__(SymCfg<N>::WARPS * 32) k_prop_build_sym(const 
     // warp-major over the grid: where the classes do not divide evenly, the
     // warps that take one chunk more are spread over the blocks (and SMs)
     // instead of filling the first blocks
-    for (long long u0 = ((long long)warp * gridDim.x + blockIdx.x) * C::CPW; u0 < a.classes; u0 += stride) {
-        const long long u = u0 + g;
-        const bool live = active && u < a.classes;
+    for (long long u0 = ((long long)warp * gridDim.x + blockIdx.x) * C::CPW; u0 < a.items; u0 += stride) {
+        const bool live = active && u0 + g < a.items;
+        long long partner;
+        const long long u = build_class(a, live ? u0 + g : a.items - 1, partner);
         int k, l, lb;
-        class_slots(a, live ? u : a.classes - 1, k, l, lb);
+        class_slots(a, u, k, l, lb);
         const float wx = sin_2pi_frac(l, a.W), wy = sin_2pi_frac(k, a.H);
         if (active && t == 0) prop_factor<N>(a, wx, wy, G, q, scal);
         __syncwarp();
@@ -629,6 +680,7 @@ __global__ void __launch_bounds__(SymCfg<N>::WARPS * 32) k_prop_build_sym(const 
             __syncwarp();
         }
         prop_store<N>(a, a.chain_in_r ? R : P, u, live, t, C::TILES);
+        prop_store<N>(a, a.chain_in_r ? R : P, partner, live, t, C::TILES, a.perm_shift);
         __syncwarp();
     }
 }
@@ -766,7 +818,7 @@ cudaError_t launch_build_kernel(K kernel, const PropArgs &a, int num_sms, cudaSt
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, C::WARPS * 32, C::SMEM);
     if (e != cudaSuccess) return e;
     const long long per_block = (long long)C::WARPS * C::CPW;
-    long long blocks = (a.classes + per_block - 1) / per_block;
+    long long blocks = (a.items + per_block - 1) / per_block;
     const long long cap = (long long)num_sms * (per_sm > 0 ? per_sm : 1);
     if (blocks > cap) blocks = cap;
     kernel<<<(unsigned)blocks, C::WARPS * 32, C::SMEM, s>>>(a);

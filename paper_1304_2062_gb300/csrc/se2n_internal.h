@@ -122,6 +122,12 @@ struct PropArgs {
     long long HW;      // H * Wc
     int col_slots;     // column classes a row class
     long long classes;
+    // classes the build computes: all of them, or with share_t (square
+    // planes, Hermitian half) the row slot <= column slot ones, each also
+    // stored permuted for its transpose, angle r -> (perm_shift - r) mod N
+    long long items;
+    int share_t;
+    int perm_shift;
     int steps;         // S
     // the powering program (se2n_prop_chain): ops PROP_* on P (starting as
     // D_1) and R (empty); the result ends in R when chain_in_r

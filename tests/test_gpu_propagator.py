@@ -18,7 +18,7 @@ import pytest
 
 import oracle
 import synth
-from _gpu import MAX_REL_RESTORED, REL_L2, host, max_rel_for_sigma, rel_l2, restoration_sigma_max, t_c64, t_f32, t_u8
+from _gpu import MAX_REL, MAX_REL_RESTORED, REL_L2, host, max_rel_for_sigma, rel_l2, restoration_sigma_max, t_c64, t_f32, t_u8
 
 pytestmark = pytest.mark.gpu
 
@@ -87,6 +87,50 @@ def test_stiff_steps_fall_back_to_the_step_kernel(N, H, W, beta, T, S, builds):
     err = rel_l2(got, ref)
     print(f"N={N} beta*dt={beta * dt:.3g} S={S}: {'propagator' if builds else 'step kernel'}, rel-L2 {err:.2e}")
     assert err <= REL_L2
+
+
+@pytest.mark.parametrize("N,H,conv", [(16, 24, 0), (32, 40, 0), (64, 20, 0), (32, 40, 1), (64, 28, 1), (16, 12, 1)])
+def test_transposed_classes_share_one_build(N, H, conv):
+    """On square planes a class and its transpose (row and column slots
+    swapped) are one operator up to the angle reflection r -> N/2 - r
+    (N/4 - r on the 2 pi r / N grid), so the build computes the upper
+    triangle of slot pairs and stores each matrix permuted for its
+    transpose: every frequency must still match the oracle."""
+    vol = synth.random_volume(N, H, H, seed=N + 3 * H + conv).astype(np.complex64)
+    ref = oracle.diffuse(vol.astype(np.complex128), 0.25, 2.0, 60, angle_conv=conv)
+    plan = se2n.se2n_plan_create(H, H, N, conv)
+    v = t_c64(vol)
+    se2n.se2n_diffuse(plan, v, 0.25, 2.0, 60, PROP)
+    got = host(v)
+    plan.close()
+    err = rel_l2(got, ref)
+    print(f"N={N} {H}x{H} conv={conv}: rel-L2 {err:.2e}")
+    assert err <= REL_L2
+
+
+@pytest.mark.parametrize("N,conv", [(32, 1), (16, 1), (32, 0)])
+def test_square_inpaint_on_the_passes_with_either_angle_grid(N, conv):
+    """The row and column passes on a square plane (transposed classes share
+    one build, the matrices stored as rows) with both angle grids."""
+    w = synth.workload_512(H=128, W=128, steps=60, rounds=3)
+    p = oracle.Params(N=N, beta=0.25, T=6.0, steps=60, rounds=3, angle_conv=conv)
+    f32 = w.f.astype(np.float32)
+    f64 = f32.astype(np.float64)
+    bins = oracle.orient(f64, w.mask, p.N, p.sigma, conv, p.flat_tol)["bins"]
+    ref = oracle.inpaint(f64, w.mask, p, bins=bins)["out"]
+    plan = se2n.se2n_plan_create(128, 128, N, conv)
+    se2n.se2n_plan_profile(plan, True)
+    vol = torch.empty((N, 128, 128), dtype=torch.complex64, device="cuda")
+    out = torch.empty((128, 128), dtype=torch.float32, device="cuda")
+    se2n.se2n_inpaint(plan, t_f32(f32), t_u8(w.mask), t_u8(bins), _params(p), vol, out)
+    got = host(out)
+    prof = se2n.se2n_plan_profile_read(plan)
+    plan.close()
+    mx = np.abs(got - ref).max() / np.abs(f64).max()
+    print(f"128x128 N={N} conv={conv}: max-abs/max|f| {mx:.2e}, rel-L2 {rel_l2(got, ref):.2e}")
+    assert prof["propagator"][1] == 1 and prof["diffuse"][1] == 3
+    assert mx <= MAX_REL
+    assert rel_l2(got, ref) <= REL_L2
 
 
 def test_lifted_image_spectrum():
