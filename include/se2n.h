@@ -254,6 +254,17 @@ SE2N_API se2n_status se2n_inverse(se2n_plan *plan, void *vol);
  * SE2N_DIFFUSE_FULL_CORRECTION forces the general kernel. */
 SE2N_API se2n_status se2n_diffuse(se2n_plan *plan, void *vol_hat, double beta, double T, int steps, int flags);
 
+/* The same integration for a row shard of the full spectrum: vol_rows holds
+ * rows k0 .. k0 + rows - 1 of every angle plane, [N][rows][W] complex,
+ * contiguous (the frequencies one GPU owns when a single image is spread
+ * over several GPUs: Theorem 2 makes every frequency's system independent,
+ * so any set of frequencies can be integrated apart from the rest). The
+ * plan's H, W, N and angle grid fix the coefficients a_r of row k0 + i.
+ * 0 <= k0, rows >= 1, k0 + rows <= H, else SE2N_EINVAL; flags as for
+ * se2n_diffuse except SE2N_DIFFUSE_PROPAGATOR (SE2N_EUNSUPPORTED). */
+SE2N_API se2n_status se2n_diffuse_rows(se2n_plan *plan, void *vol_rows, int k0, int rows, double beta, double T,
+                                       int steps, int flags);
+
 /* One step of dynamic restoration (Section 5.3) on the real part of the
  * (normalised) complex volume vol [N][H][W]: with h = max_r Re vol_r, a pixel
  * that is bad in mask_in (0) and has a good 8-neighbour becomes good when h
@@ -279,6 +290,17 @@ SE2N_API se2n_status se2n_dr_grow(se2n_plan *plan, const void *vol, const uint8_
  * everywhere. 0 <= eps <= 1. */
 SE2N_API se2n_status se2n_mix(se2n_plan *plan, void *vol, const float *f, const uint8_t *mask,
                      const uint8_t *bins, double eps, double guard);
+
+/* Static restoration (Section 5, SR) with h(t) given: h_t [H][W] float is
+ * the maximum over ALL N angles of the real volume at the restoration time,
+ * of which vol may hold only a subset of the planes (an angle shard: a plan
+ * created with that many planes, and bins renumbered so that a pixel lifted
+ * to an angle outside the shard names no plane of it, 0 .. 254, or stays
+ * SE2N_BIN_FLAT). h(0) comes from f itself (the lift's maximum over all
+ * angles: f, or max(f, 0) for a pixel on one angle). The rule and the guard
+ * are se2n_mix's. */
+SE2N_API se2n_status se2n_mix_given(se2n_plan *plan, void *vol, const float *f, const uint8_t *mask,
+                                    const uint8_t *bins, const float *h_t, double eps, double guard);
 
 /* Projection to the image (Section 1.2.4): out = max_r Re vol_r
  * (SE2N_PROJ_MAX) or the mean over r (SE2N_PROJ_MEAN). out [H][W] float. */

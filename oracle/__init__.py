@@ -298,7 +298,7 @@ def diffuse_dense(vol_hat, beta, T, steps, angle_conv=0):
 # static restoration
 # ----------------------------------------------------------------------------
 
-def mix(vol, f, mask, bins, eps, guard=0.1):
+def mix(vol, f, mask, bins, eps, guard=0.1, ht=None, h0=None):
     """Static restoration at the good pixels (Section 5, SR).
 
     h(t) = max over angles of the current volume, h(0) = max over angles of
@@ -308,12 +308,16 @@ def mix(vol, f, mask, bins, eps, guard=0.1):
     eps/guard, and the good pixel is instead set to eps * lift + (1-eps) * psi,
     which moves its maximum to about the same eps h(0) + (1-eps) h(t). The
     volume is real (the imaginary part is dropped everywhere); B pixels are
-    otherwise unchanged."""
+    otherwise unchanged.
+
+    ht, h0 (optional): h(t) and h(0) given instead of taken over the planes
+    of vol, for a volume that holds only some of the angles (bins then
+    number the planes of vol; a pixel lifted elsewhere names none of them)."""
     re = np.asarray(vol).real.copy()
     N = re.shape[0]
     psi0 = lift(f, mask, bins, N).real
-    h0 = psi0.max(axis=0)
-    ht = re.max(axis=0)
+    h0 = psi0.max(axis=0) if h0 is None else np.asarray(h0, dtype=np.float64)
+    ht = re.max(axis=0) if ht is None else np.asarray(ht, dtype=np.float64)
     good = np.asarray(mask) != 0
     scaled = good & (ht > guard * h0) & (ht > 0.0)
     lin = good & ~scaled

@@ -356,7 +356,10 @@ se2n_status col_diffuse(se2n_plan *plan, double beta, double T, int steps) {
 }
 
 // half: vol holds the Hermitian half [N][H][W/2 + 1] of the spectrum.
-se2n_status diffuse_impl(se2n_plan *plan, float2 *vol, double beta, double T, int steps, int flags, bool half = false) {
+// rows >= 0: vol holds only spectrum rows k0 .. k0 + rows - 1 of every plane
+// ([N][rows][W], a row shard of the full spectrum).
+se2n_status diffuse_impl(se2n_plan *plan, float2 *vol, double beta, double T, int steps, int flags, bool half = false,
+                         int k0 = 0, int rows = -1) {
     if (!(beta > 0.0) || !(T >= 0.0) || steps < 1 || !isfinite(beta) || !isfinite(T)) return SE2N_EINVAL;
     if (flags & ~(SE2N_DIFFUSE_SM_FP64 | SE2N_DIFFUSE_SPLIT_DIAG | SE2N_DIFFUSE_FULL_CORRECTION |
                   SE2N_DIFFUSE_PROPAGATOR))
@@ -366,7 +369,7 @@ se2n_status diffuse_impl(se2n_plan *plan, float2 *vol, double beta, double T, in
     const double bdt = beta * dt;
     if (!(bdt >= 1e-30 && bdt <= 1e3)) return SE2N_ENUMERIC;
     if (flags & SE2N_DIFFUSE_PROPAGATOR) {
-        if (!se2n_prop_supported(plan->N)) return SE2N_EUNSUPPORTED;
+        if (!se2n_prop_supported(plan->N) || rows >= 0) return SE2N_EUNSUPPORTED;
         if (prop_admissible(beta, dt)) return propagate_impl(plan, vol, beta, bdt, steps, half);
         flags &= ~SE2N_DIFFUSE_PROPAGATOR;  // stiff: the step kernel keeps the accuracy
     }
@@ -379,7 +382,8 @@ se2n_status diffuse_impl(se2n_plan *plan, float2 *vol, double beta, double T, in
     DiffuseArgs a;
     a.vol = vol;
     a.Wc = half ? plan->Wc : plan->W;
-    a.HW = (long long)plan->H * a.Wc;
+    a.HW = (long long)(rows >= 0 ? rows : plan->H) * a.Wc;
+    a.k0 = rows >= 0 ? k0 : 0;
     a.H = plan->H;
     a.W = plan->W;
     a.sp = step_params(beta, bdt, steps);
@@ -888,6 +892,13 @@ se2n_status se2n_diffuse(se2n_plan *plan, void *vol_hat, double beta, double T, 
     return diffuse_impl(plan, (float2 *)vol_hat, beta, T, steps, flags);
 }
 
+se2n_status se2n_diffuse_rows(se2n_plan *plan, void *vol_rows, int k0, int rows, double beta, double T, int steps,
+                              int flags) {
+    SE2N_TRY(check_plan(plan));
+    if (!device_ptr(vol_rows, 16) || k0 < 0 || rows < 1 || k0 + rows > plan->H) return SE2N_EINVAL;
+    return diffuse_impl(plan, (float2 *)vol_rows, beta, T, steps, flags, false, k0, rows);
+}
+
 se2n_status se2n_dr_grow(se2n_plan *plan, const void *vol, const uint8_t *mask_in, uint8_t *mask_out, float *fref,
                          uint8_t *bins) {
     SE2N_TRY(check_plan(plan));
@@ -913,6 +924,19 @@ se2n_status se2n_mix(se2n_plan *plan, void *vol, const float *f, const uint8_t *
         return SE2N_EINVAL;
     if (!(eps >= 0.0 && eps <= 1.0) || !(guard >= 0.0) || !isfinite(guard)) return SE2N_EINVAL;
     return mix_impl(plan, (float2 *)vol, f, mask, bins, 1.0f, (float)eps, (float)guard);
+}
+
+se2n_status se2n_mix_given(se2n_plan *plan, void *vol, const float *f, const uint8_t *mask, const uint8_t *bins,
+                           const float *h_t, double eps, double guard) {
+    SE2N_TRY(check_plan(plan));
+    if (!device_ptr(vol, 16) || !device_ptr(f, 8) || !device_ptr(mask, 2) || !device_ptr(bins, 2) ||
+        !device_ptr(h_t, 8))
+        return SE2N_EINVAL;
+    if (!(eps >= 0.0 && eps <= 1.0) || !(guard >= 0.0) || !isfinite(guard)) return SE2N_EINVAL;
+    StageTimer timer(plan, SE2N_STAGE_MIX);
+    plan->kernels += 1;
+    return cuda_status(plan, se2n_launch_mix_given((float2 *)vol, f, mask, bins, h_t, plan->HW, plan->N,
+                                                   (float)eps, (float)guard, plan->stream));
 }
 
 se2n_status se2n_project(se2n_plan *plan, const void *vol, int proj, float *out) {

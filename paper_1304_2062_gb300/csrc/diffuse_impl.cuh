@@ -190,7 +190,7 @@ __device__ __forceinline__ void tear_setup(const TearInfo<P> &ti, const T (&diag
 // (shuffles); a lane with !active works on a valid frequency without storing.
 template <int N, int P, bool FP64, bool SPLIT>
 __device__ __forceinline__ void diffuse_group(const StepParams &sp, const float *cs, const float *sn,
-    float2 *vol, int H, int W, int Wc, long long HW, long long fc, bool active) {
+    float2 *vol, int H, int W, int Wc, long long HW, long long fc, bool active, int k0 = 0) {
     constexpr int K = N / P;
     constexpr int Q = TearInfo<P>::Q;
     static_assert(P == 1 || P == 2 || P == 4, "threads per frequency");
@@ -208,7 +208,7 @@ __device__ __forceinline__ void diffuse_group(const StepParams &sp, const float 
     const int k = (int)(fc / Wc);
     const int l = (int)(fc - (long long)k * Wc);
     const float wx = sin_2pi_frac(l, W);
-    const float wy = sin_2pi_frac(k, H);
+    const float wy = sin_2pi_frac(k0 + k, H);  // k0: first row of a row shard
     float2 *col = vol + (long long)row0 * HW + fc;
     const long long stride = (long long)rstep * HW;
 
@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(256) k_diffuse(const __grid_constant__ Diffuse
         const long long f = slot + base;
         const bool active = f < a.HW;
         diffuse_group<N, P, FP64, SPLIT>(a.sp, a.cs, a.sn, a.vol, a.H, a.W, a.Wc, a.HW, active ? f : a.HW - 1,
-                                         active);
+                                         active, a.k0);
     }
 }
 

@@ -86,7 +86,7 @@ constexpr int x2_max_block(int N) { return N >= 48 ? kDiffuseMaxBlock : 256; }
 // (shuffles); a lane with !active works on a valid frequency without storing.
 template <int N, int P, bool SPLIT>
 __device__ __forceinline__ void diffuse_group_x2(const StepParams &sp, const float *cs, const float *sn,
-    float2 *vol, int H, int W, int Wc, long long HW, long long fc, bool active) {
+    float2 *vol, int H, int W, int Wc, long long HW, long long fc, bool active, int k0 = 0) {
     constexpr int K = N / P;
     constexpr int Q = TearInfo<P>::Q;
     constexpr int KZ = (K < kTruncRows) ? K : kTruncRows;
@@ -104,7 +104,7 @@ __device__ __forceinline__ void diffuse_group_x2(const StepParams &sp, const flo
     const int k = (int)(fc / Wc);
     const int l = (int)(fc - (long long)k * Wc);
     const float wx = sin_2pi_frac(l, W);
-    const float wy = sin_2pi_frac(k, H);
+    const float wy = sin_2pi_frac(k0 + k, H);  // k0: first row of a row shard
     float2 *col = vol + (long long)row0 * HW + fc;
     const long long stride = (long long)rstep * HW;
 
@@ -259,7 +259,8 @@ __global__ void __launch_bounds__(x2_max_block(N), 1) k_diffuse_x2(const __grid_
     for (long long base = 0; warp_slot0 + base < a.HW; base += nslots) {
         const long long f = slot + base;
         const bool active = f < a.HW;
-        diffuse_group_x2<N, P, SPLIT>(a.sp, a.cs, a.sn, a.vol, a.H, a.W, a.Wc, a.HW, active ? f : a.HW - 1, active);
+        diffuse_group_x2<N, P, SPLIT>(a.sp, a.cs, a.sn, a.vol, a.H, a.W, a.Wc, a.HW, active ? f : a.HW - 1, active,
+                                      a.k0);
     }
 }
 

@@ -119,16 +119,25 @@ __global__ void k_lift(const float2 *__restrict__ f, const uchar2 *__restrict__ 
 
 using se2n::sr_value;
 
+// ht_given (if not null): h(t) of every pixel, the maximum over all angles,
+// of which vol may hold only some planes (an angle shard; bins then name
+// no plane of vol for the pixels lifted elsewhere).
 __global__ void k_mix(float4 *__restrict__ vol, const float2 *__restrict__ f, const uchar2 *__restrict__ mask,
                       const uchar2 *__restrict__ bins, long long npairs, int N, float scale, float eps,
-                      float guard) {
+                      float guard, const float2 *__restrict__ ht_given) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npairs;
          i += (long long)gridDim.x * blockDim.x) {
         float ht0 = -INFINITY, ht1 = -INFINITY;
-        for (int r = 0; r < N; ++r) {
-            const float4 v = vol[(long long)r * npairs + i];
-            ht0 = fmaxf(ht0, v.x * scale);
-            ht1 = fmaxf(ht1, v.z * scale);
+        if (ht_given) {
+            const float2 h = ht_given[i];
+            ht0 = h.x;
+            ht1 = h.y;
+        } else {
+            for (int r = 0; r < N; ++r) {
+                const float4 v = vol[(long long)r * npairs + i];
+                ht0 = fmaxf(ht0, v.x * scale);
+                ht1 = fmaxf(ht1, v.z * scale);
+            }
         }
         const float2 fv = f[i];
         const uchar2 m = mask[i];
@@ -422,7 +431,15 @@ cudaError_t se2n_launch_mix(float2 *vol, const float *f, const uint8_t *mask, co
                             long long HW, int N, float scale, float eps, float guard, cudaStream_t s) {
     const long long n = HW / 2;
     k_mix<<<grid_for(n), kBlock, 0, s>>>((float4 *)vol, (const float2 *)f, (const uchar2 *)mask,
-                                         (const uchar2 *)bins, n, N, scale, eps, guard);
+                                         (const uchar2 *)bins, n, N, scale, eps, guard, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t se2n_launch_mix_given(float2 *vol, const float *f, const uint8_t *mask, const uint8_t *bins,
+                                  const float *h_t, long long HW, int N, float eps, float guard, cudaStream_t s) {
+    const long long n = HW / 2;
+    k_mix<<<grid_for(n), kBlock, 0, s>>>((float4 *)vol, (const float2 *)f, (const uchar2 *)mask,
+                                         (const uchar2 *)bins, n, N, 1.0f, eps, guard, (const float2 *)h_t);
     return cudaGetLastError();
 }
 

@@ -98,6 +98,7 @@ struct DiffuseArgs {
     long long HW;  // frequencies per plane (the plane's stride in complex elements)
     int H, W;
     int Wc;        // stored columns per row: W, or W/2 + 1 for the Hermitian half
+    int k0;        // first spectrum row of vol (a row shard), 0 for a whole volume
     StepParams sp;
     float cs[SE2N_MAX_N];
     float sn[SE2N_MAX_N];
@@ -232,6 +233,10 @@ cudaError_t se2n_launch_lift(const float *f, const uint8_t *mask, const uint8_t 
                              long long HW, int N, cudaStream_t s);
 cudaError_t se2n_launch_mix(float2 *vol, const float *f, const uint8_t *mask, const uint8_t *bins,
                             long long HW, int N, float scale, float eps, float guard, cudaStream_t s);
+// The same rule with h(t) given (the maximum over all angles, of which vol
+// may hold only some planes); vol already normalised.
+cudaError_t se2n_launch_mix_given(float2 *vol, const float *f, const uint8_t *mask, const uint8_t *bins,
+                                  const float *h_t, long long HW, int N, float eps, float guard, cudaStream_t s);
 // out = max_r (or mean_r) of scale * Re vol[r]; where mask != null, pixels
 // with mask != 0 take f instead (the inpainted image).
 // The same stages on the real volume of the Hermitian-half path: planes of H

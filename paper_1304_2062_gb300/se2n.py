@@ -121,6 +121,9 @@ _SIGS = {
     "se2n_batch_run_diffusion": (ctypes.c_int, [_P]),
     "se2n_batch_get_info": (ctypes.c_int, [_P, ctypes.POINTER(se2n_batch_info)]),
     "se2n_batch_destroy": (ctypes.c_int, [_P]),
+    "se2n_diffuse_rows": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_int, ctypes.c_int]),
+    "se2n_mix_given": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.c_double, ctypes.c_double]),
     "se2n_diffuse_many_noalloc": (ctypes.c_int, [ctypes.POINTER(se2n_volume_desc), ctypes.c_int, ctypes.c_double,
                                                  ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
     "se2n_unet_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
@@ -280,6 +283,17 @@ def se2n_inverse(plan, vol):
 
 def se2n_diffuse(plan, vol_hat, beta, T, steps, flags=0):
     _check(lib.se2n_diffuse(plan.handle, _ptr(vol_hat), beta, T, steps, flags), "se2n_diffuse")
+
+
+def se2n_diffuse_rows(plan, vol_rows, k0, beta, T, steps, flags=0):
+    """vol_rows: complex64 device tensor [N][rows][W], spectrum rows k0 .. k0 + rows - 1."""
+    _check(lib.se2n_diffuse_rows(plan.handle, _ptr(vol_rows), k0, vol_rows.shape[1], beta, T, steps, flags),
+           "se2n_diffuse_rows")
+
+
+def se2n_mix_given(plan, vol, f, mask, bins, h_t, eps, guard=0.1):
+    _check(lib.se2n_mix_given(plan.handle, _ptr(vol), _ptr(f), _ptr(mask), _ptr(bins), _ptr(h_t), eps, guard),
+           "se2n_mix_given")
 
 
 def se2n_mix(plan, vol, f, mask, bins, eps, guard=0.1):
