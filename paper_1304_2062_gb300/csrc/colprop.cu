@@ -123,7 +123,7 @@ template <int N, int H>
 struct ColCfg {
     static constexpr int L = H / 2;                      // half a column
     static constexpr int XF = SmemBlock<N, L>::COMPLEX;  // one half, complex
-    static constexpr int SMEM = (XF + H) * 8;            // and the twiddles
+    static constexpr int SMEM = (XF + H + FftTw<L>::SIZE) * 8;  // and the twiddles
     // two angles (one float4) of one row of the upper half of the block a step
     static constexpr int NP = N * L / 2 / kColThreads;
     static_assert(NP * 2 * kColThreads == N * L, "whole half blocks");
@@ -147,12 +147,14 @@ __global__ void __launch_bounds__(kColThreads, 2) k_col_prop(const __grid_consta
     extern __shared__ __align__(16) float2 csm[];
     float2 *X = csm;
     float2 *tws = csm + C::XF;  // exp(-2 pi i m / H), m < H
+    float2 *twp = tws + H;      // the transforms' pass tables
     const int tid = threadIdx.x;
     const int b = blockIdx.x, h = b >> 1;
     const int l = (b & 1) ? a.W / 2 - h : h;
     const int scol = half_col_slot(l, a.W);
     float4 *g = reinterpret_cast<float4 *>(a.col + (long long)l * (N * H));
     for (int m = tid; m < H; m += T) tws[m] = a.tw[m];
+    fft_twiddles<T, L, 2>(twp, a.tw, tid);  // from the table in device memory
     __syncthreads();
     // 1. u = x_k + x_{k+L} into shared memory, v = (x_k - x_{k+L}) w^k into
     //    the upper rows of the block (each thread later reads back only what
@@ -169,11 +171,11 @@ __global__ void __launch_bounds__(kColThreads, 2) k_col_prop(const __grid_consta
     }
     __syncthreads();
     // 2. the even frequencies, into y_e in the lower rows of the block
-    fft_smem<T, N, L, -1, 2>(X, tws, tid);
+    fft_smem<T, N, L, -1>(X, twp, tid);
     __syncthreads();
     col_apply<N, H>(X, a.D, scol, a.col_slots, 0, tid);
     __syncthreads();
-    fft_smem<T, N, L, 1, 2>(X, tws, tid);
+    fft_smem<T, N, L, 1>(X, twp, tid);
     __syncthreads();
 #pragma unroll 4
     for (int q = 0; q < C::NP; ++q) {
@@ -191,11 +193,11 @@ __global__ void __launch_bounds__(kColThreads, 2) k_col_prop(const __grid_consta
         put2<N, L>(X, k, n, make_float2(v.x, v.y), make_float2(v.z, v.w));
     }
     __syncthreads();
-    fft_smem<T, N, L, -1, 2>(X, tws, tid);
+    fft_smem<T, N, L, -1>(X, twp, tid);
     __syncthreads();
     col_apply<N, H>(X, a.D, scol, a.col_slots, 1, tid);
     __syncthreads();
-    fft_smem<T, N, L, 1, 2>(X, tws, tid);
+    fft_smem<T, N, L, 1>(X, twp, tid);
     __syncthreads();
     // 4. x_k = y_e + w^-k y_o, x_{k+L} = y_e - w^-k y_o
 #pragma unroll 4

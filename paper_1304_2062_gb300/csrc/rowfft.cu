@@ -37,7 +37,7 @@ template <int N, int W>
 struct RowCfg {
     static constexpr int WH = W / 2;
     static constexpr int XF = SmemBlock<N, WH>::COMPLEX;
-    static constexpr int SMEM = (XF + W) * 8;
+    static constexpr int SMEM = (XF + W + FftTw<WH>::SIZE) * 8;
 };
 
 template <int N, int W>
@@ -46,10 +46,12 @@ __global__ void __launch_bounds__(kRowThreads) k_row(const __grid_constant__ Row
     extern __shared__ __align__(16) float2 rsm[];
     float2 *Z = rsm;                       // [N][W/2]: z_m of every angle
     float2 *tws = rsm + RowCfg<N, W>::XF;  // exp(-2 pi i m / W)
+    float2 *twp = tws + W;                 // the transforms' pass tables
     const int tid = threadIdx.x, y = blockIdx.x;
     const long long H = a.H;
     const long long row = (long long)y * W;  // first pixel of the row
     for (int m = tid; m < W; m += T) tws[m] = a.tw[m];
+    fft_twiddles<T, WH, 2>(twp, a.tw, tid);  // from the table in device memory
     // 1. the row
     if (a.in_mode == SE2N_ROW_IN_LIFT) {
         for (int m = tid; m < WH; m += T) {
@@ -103,7 +105,7 @@ __global__ void __launch_bounds__(kRowThreads) k_row(const __grid_constant__ Row
             }
         }
         __syncthreads();
-        fft_smem<T, N, WH, 1, 2>(Z, tws, tid);
+        fft_smem<T, N, WH, 1>(Z, twp, tid);
     }
     __syncthreads();
     // 2. the restoration, one pixel pair (2m, 2m + 1) a thread
@@ -195,7 +197,7 @@ __global__ void __launch_bounds__(kRowThreads) k_row(const __grid_constant__ Row
             reinterpret_cast<uchar2 *>(a.amax_out + row)[m] = make_uchar2((uint8_t)r0, (uint8_t)r1);
         }
     } else {
-        fft_smem<T, N, WH, -1, 2>(Z, tws, tid);
+        fft_smem<T, N, WH, -1>(Z, twp, tid);
         __syncthreads();
         constexpr int LP = WH / 2 + 1, TL = T / N, IT = (LP + TL - 1) / TL;
         const int n = tid % N, l0 = tid / N;

@@ -128,9 +128,11 @@ __device__ __forceinline__ void dft_small(float2 (&v)[R]) {
     }
 }
 
-// One pass of T threads over the block X; tw[m * TS] = exp(-2 pi i m / L).
-template <int T, int N, int L, int R, int NS, int DIR, int TS>
-__device__ __forceinline__ void fft_pass(float2 *X, const float2 *tw, int tid) {
+// One pass of T threads over the block X; twp[r NS + k] = exp(-2 pi i r k /
+// (NS R)), this pass's twiddles (fft_twiddles below), read at consecutive
+// entries by the lanes of consecutive k (free of bank conflicts).
+template <int T, int N, int L, int R, int NS, int DIR>
+__device__ __forceinline__ void fft_pass(float2 *X, const float2 *twp, int tid) {
     constexpr int M = L / R;  // butterflies a transform
     constexpr int NB = N * M;
     constexpr int BPT = (NB + T - 1) / T;
@@ -159,7 +161,7 @@ __device__ __forceinline__ void fft_pass(float2 *X, const float2 *tw, int tid) {
     float2 w[R];
     if constexpr (NS > 1) {
 #pragma unroll
-        for (int r = 1; r < R; ++r) w[r] = tw[r * k * (L / (NS * R)) * TS];
+        for (int r = 1; r < R; ++r) w[r] = twp[r * NS + k];
     }
     __syncthreads();
 #pragma unroll
@@ -178,27 +180,63 @@ __device__ __forceinline__ void fft_pass(float2 *X, const float2 *tw, int tid) {
     }
 }
 
-// The N DFTs of length L (32 = 8 x 4, 64 = 8 x 8, 128 = 8 x 8 x 2,
-// 256 = 16 x 16, 512 = 8 x 8 x 8). The caller synchronises before and after.
-template <int T, int N, int L, int DIR, int TS>
-__device__ __forceinline__ void fft_smem(float2 *X, const float2 *tw, int tid) {
+// The passes with twiddles (NS > 1) of the DFTs of length L, and their
+// tables: pass (R, NS) needs exp(-2 pi i r k / (NS R)) for r < R, k < NS,
+// kept at twp[offset + r NS + k]. Lengths 32 = 8 x 4, 64 = 8 x 8,
+// 128 = 8 x 8 x 2, 256 = 16 x 16, 512 = 8 x 8 x 8.
+template <int L>
+struct FftTw {
+    // (R, NS) of the second and third pass (0 where there is none)
+    static constexpr int R2 = L == 32 ? 4 : (L == 256 ? 16 : 8);
+    static constexpr int NS2 = L == 256 ? 16 : 8;
+    static constexpr int R3 = L == 128 ? 2 : (L == 512 ? 8 : 0);
+    static constexpr int NS3 = 64;
+    static constexpr int OFF3 = R2 * NS2;
+    static constexpr int SIZE = OFF3 + R3 * NS3;  // complex entries
+};
+
+// Fill the pass tables from tw[m TS] = exp(-2 pi i m / L) (a table of L TS
+// entries); T threads. The caller synchronises after.
+template <int T, int L, int TS>
+__device__ __forceinline__ void fft_twiddles(float2 *twp, const float2 *tw, int tid) {
+    using F = FftTw<L>;
+    for (int e = tid; e < F::SIZE; e += T) {
+        int r, k, step;
+        if (e < F::OFF3) {
+            r = e / F::NS2;
+            k = e - r * F::NS2;
+            step = L / (F::NS2 * F::R2);
+        } else {
+            r = (e - F::OFF3) / F::NS3;
+            k = (e - F::OFF3) - r * F::NS3;
+            step = F::R3 ? L / (F::NS3 * F::R3) : 0;
+        }
+        twp[e] = tw[r * k * step * TS];
+    }
+}
+
+// The N DFTs of length L. twp: the pass tables of fft_twiddles. The caller
+// synchronises before and after.
+template <int T, int N, int L, int DIR>
+__device__ __forceinline__ void fft_smem(float2 *X, const float2 *twp, int tid) {
     static_assert(L == 32 || L == 64 || L == 128 || L == 256 || L == 512, "transform length");
+    using F = FftTw<L>;
     if constexpr (L == 256) {
-        fft_pass<T, N, L, 16, 1, DIR, TS>(X, tw, tid);
+        fft_pass<T, N, L, 16, 1, DIR>(X, twp, tid);
         __syncthreads();
-        fft_pass<T, N, L, 16, 16, DIR, TS>(X, tw, tid);
+        fft_pass<T, N, L, 16, 16, DIR>(X, twp, tid);
         return;
     }
-    fft_pass<T, N, L, 8, 1, DIR, TS>(X, tw, tid);
+    fft_pass<T, N, L, 8, 1, DIR>(X, twp, tid);
     __syncthreads();
     if constexpr (L == 32) {
-        fft_pass<T, N, L, 4, 8, DIR, TS>(X, tw, tid);
+        fft_pass<T, N, L, 4, 8, DIR>(X, twp, tid);
     } else if constexpr (L == 64) {
-        fft_pass<T, N, L, 8, 8, DIR, TS>(X, tw, tid);
+        fft_pass<T, N, L, 8, 8, DIR>(X, twp, tid);
     } else {
-        fft_pass<T, N, L, 8, 8, DIR, TS>(X, tw, tid);
+        fft_pass<T, N, L, 8, 8, DIR>(X, twp, tid);
         __syncthreads();
-        fft_pass<T, N, L, L / 64, 64, DIR, TS>(X, tw, tid);
+        fft_pass<T, N, L, L / 64, 64, DIR>(X, twp + F::OFF3, tid);
     }
 }
 
