@@ -34,7 +34,10 @@ namespace se2n {
 
 namespace {
 
-constexpr int kColThreads = 256;
+// threads a block: 256, and 512 for half columns of 512 (H = 1024), whose
+// transform passes would otherwise hold 64 complex values a thread
+template <int H>
+__host__ __device__ constexpr int col_threads() { return H >= 1024 ? 512 : 256; }
 
 // x <- x + D_S x for every frequency (k, l) of one half of the column (its
 // classes s = parity, parity + 2, ...; frequency k at index k / 2 of the
@@ -44,7 +47,7 @@ constexpr int kColThreads = 256;
 // reversed (angle -j in place of j).
 template <int N, int H>
 __device__ __forceinline__ void col_apply(float2 *X, const float *D, int scol, int col_slots, int parity, int tid) {
-    constexpr int L = H / 2, RPL = 2, LPC = N / RPL, CPW = 32 / LPC, WARPS = kColThreads / 32;
+    constexpr int L = H / 2, RPL = 2, LPC = N / RPL, CPW = 32 / LPC, WARPS = col_threads<H>() / 32;
     const int count = parity ? H / 8 : H / 8 + 1;
     const int warp = tid >> 5, lane = tid & 31;
     const int g = lane / LPC, t = lane - g * LPC;
@@ -125,8 +128,9 @@ struct ColCfg {
     static constexpr int XF = SmemBlock<N, L>::COMPLEX;  // one half, complex
     static constexpr int SMEM = (XF + H + FftTw<L>::SIZE) * 8;  // and the twiddles
     // two angles (one float4) of one row of the upper half of the block a step
-    static constexpr int NP = N * L / 2 / kColThreads;
-    static_assert(NP * 2 * kColThreads == N * L, "whole half blocks");
+    static constexpr int T = col_threads<H>();
+    static constexpr int NP = N * L / 2 / T;
+    static_assert(NP * 2 * T == N * L, "whole half blocks");
 };
 
 // a float4 of two angles n, n + 1 of frequency (half row) k, from / into the
@@ -141,9 +145,9 @@ __device__ __forceinline__ void put2(float2 *X, int k, int n, float2 a, float2 b
 // Block b takes column b / 2 (b even) or W/2 - b / 2 (b odd), so the two
 // columns of a class run side by side and share its propagators in L2.
 template <int N, int H>
-__global__ void __launch_bounds__(kColThreads, 2) k_col_prop(const __grid_constant__ ColArgs a) {
+__global__ void __launch_bounds__(col_threads<H>(), H >= 1024 ? 1 : 2) k_col_prop(const __grid_constant__ ColArgs a) {
     using C = ColCfg<N, H>;
-    constexpr int L = C::L, T = kColThreads, HALF4 = N * L / 2;  // float4s in half a block
+    constexpr int L = C::L, T = C::T, HALF4 = N * L / 2;  // float4s in half a block
     extern __shared__ __align__(16) float2 csm[];
     float2 *X = csm;
     float2 *tws = csm + C::XF;  // exp(-2 pi i m / H), m < H
@@ -221,7 +225,7 @@ template <int N, int H>
 cudaError_t col_launch(const ColArgs &a, cudaStream_t s) {
     cudaError_t e = col_attr<N, H>();
     if (e != cudaSuccess) return e;
-    k_col_prop<N, H><<<a.Wc, kColThreads, ColCfg<N, H>::SMEM, s>>>(a);
+    k_col_prop<N, H><<<a.Wc, ColCfg<N, H>::T, ColCfg<N, H>::SMEM, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -232,6 +236,7 @@ cudaError_t col_dispatch(int H, const ColArgs *a, cudaStream_t s) {
         case 128: return a ? col_launch<N, 128>(*a, s) : col_attr<N, 128>();
         case 256: return a ? col_launch<N, 256>(*a, s) : col_attr<N, 256>();
         case 512: return a ? col_launch<N, 512>(*a, s) : col_attr<N, 512>();
+        case 1024: return a ? col_launch<N, 1024>(*a, s) : col_attr<N, 1024>();
         default: return cudaErrorInvalidValue;
     }
 }
@@ -240,7 +245,9 @@ cudaError_t col_dispatch(int H, const ColArgs *a, cudaStream_t s) {
 
 }  // namespace se2n
 
-bool se2n_col_supported(int N, int H) { return (N == 16 || N == 32) && (H == 64 || H == 128 || H == 256 || H == 512); }
+bool se2n_col_supported(int N, int H) {
+    return (N == 16 || N == 32) && (H == 64 || H == 128 || H == 256 || H == 512 || H == 1024);
+}
 
 cudaError_t se2n_col_prepare(int N, int H) {
     if (!se2n_col_supported(N, H)) return cudaErrorInvalidValue;

@@ -31,7 +31,10 @@ namespace se2n {
 
 namespace {
 
-constexpr int kRowThreads = 256;
+// threads a block: 256, and 512 for rows of 1024 (transforms of length
+// 512), which would otherwise hold 64 complex values a thread
+template <int W>
+__host__ __device__ constexpr int row_threads() { return W >= 1024 ? 512 : 256; }
 
 template <int N, int W>
 struct RowCfg {
@@ -41,8 +44,8 @@ struct RowCfg {
 };
 
 template <int N, int W>
-__global__ void __launch_bounds__(kRowThreads) k_row(const __grid_constant__ RowArgs a) {
-    constexpr int WH = W / 2, T = kRowThreads;
+__global__ void __launch_bounds__(row_threads<W>()) k_row(const __grid_constant__ RowArgs a) {
+    constexpr int WH = W / 2, T = row_threads<W>();
     extern __shared__ __align__(16) float2 rsm[];
     float2 *Z = rsm;                       // [N][W/2]: z_m of every angle
     float2 *tws = rsm + RowCfg<N, W>::XF;  // exp(-2 pi i m / W)
@@ -228,7 +231,7 @@ template <int N, int W>
 cudaError_t row_launch(const RowArgs &a, cudaStream_t s) {
     cudaError_t e = row_attr<N, W>();
     if (e != cudaSuccess) return e;
-    k_row<N, W><<<a.H, kRowThreads, RowCfg<N, W>::SMEM, s>>>(a);
+    k_row<N, W><<<a.H, row_threads<W>(), RowCfg<N, W>::SMEM, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -239,6 +242,7 @@ cudaError_t row_dispatch(int W, const RowArgs *a, cudaStream_t s) {
         case 128: return a ? row_launch<N, 128>(*a, s) : row_attr<N, 128>();
         case 256: return a ? row_launch<N, 256>(*a, s) : row_attr<N, 256>();
         case 512: return a ? row_launch<N, 512>(*a, s) : row_attr<N, 512>();
+        case 1024: return a ? row_launch<N, 1024>(*a, s) : row_attr<N, 1024>();
         default: return cudaErrorInvalidValue;
     }
 }
@@ -247,7 +251,9 @@ cudaError_t row_dispatch(int W, const RowArgs *a, cudaStream_t s) {
 
 }  // namespace se2n
 
-bool se2n_row_supported(int N, int W) { return (N == 16 || N == 32) && (W == 64 || W == 128 || W == 256 || W == 512); }
+bool se2n_row_supported(int N, int W) {
+    return (N == 16 || N == 32) && (W == 64 || W == 128 || W == 256 || W == 512 || W == 1024);
+}
 
 cudaError_t se2n_row_prepare(int N, int W) {
     if (!se2n_row_supported(N, W)) return cudaErrorInvalidValue;
