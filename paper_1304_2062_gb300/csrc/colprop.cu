@@ -34,10 +34,10 @@ namespace se2n {
 
 namespace {
 
-// threads a block: 256, and 512 for half columns of 512 (H = 1024), whose
-// transform passes would otherwise hold 64 complex values a thread
+// threads a block: 256, and 512 for half columns of 384 and 512 (H = 768,
+// 1024), whose transform passes would otherwise hold too many values a thread
 template <int H>
-__host__ __device__ constexpr int col_threads() { return H >= 1024 ? 512 : 256; }
+__host__ __device__ constexpr int col_threads() { return H >= 768 ? 512 : 256; }
 
 // x <- x + D_S x for every frequency (k, l) of one half of the column (its
 // classes s = parity, parity + 2, ...; frequency k at index k / 2 of the
@@ -145,7 +145,7 @@ __device__ __forceinline__ void put2(float2 *X, int k, int n, float2 a, float2 b
 // Block b takes column b / 2 (b even) or W/2 - b / 2 (b odd), so the two
 // columns of a class run side by side and share its propagators in L2.
 template <int N, int H>
-__global__ void __launch_bounds__(col_threads<H>(), H >= 1024 ? 1 : 2) k_col_prop(const __grid_constant__ ColArgs a) {
+__global__ void __launch_bounds__(col_threads<H>(), H >= 768 ? 1 : 2) k_col_prop(const __grid_constant__ ColArgs a) {
     using C = ColCfg<N, H>;
     constexpr int L = C::L, T = C::T, HALF4 = N * L / 2;  // float4s in half a block
     extern __shared__ __align__(16) float2 csm[];
@@ -237,6 +237,8 @@ cudaError_t col_dispatch(int H, const ColArgs *a, cudaStream_t s) {
         case 256: return a ? col_launch<N, 256>(*a, s) : col_attr<N, 256>();
         case 512: return a ? col_launch<N, 512>(*a, s) : col_attr<N, 512>();
         case 1024: return a ? col_launch<N, 1024>(*a, s) : col_attr<N, 1024>();
+        case 384: return a ? col_launch<N, 384>(*a, s) : col_attr<N, 384>();
+        case 768: return a ? col_launch<N, 768>(*a, s) : col_attr<N, 768>();
         default: return cudaErrorInvalidValue;
     }
 }
@@ -246,7 +248,8 @@ cudaError_t col_dispatch(int H, const ColArgs *a, cudaStream_t s) {
 }  // namespace se2n
 
 bool se2n_col_supported(int N, int H) {
-    return (N == 16 || N == 32) && (H == 64 || H == 128 || H == 256 || H == 512 || H == 1024);
+    return (N == 16 || N == 32) &&
+           (H == 64 || H == 128 || H == 256 || H == 512 || H == 1024 || H == 384 || H == 768);
 }
 
 cudaError_t se2n_col_prepare(int N, int H) {

@@ -31,10 +31,10 @@ namespace se2n {
 
 namespace {
 
-// threads a block: 256, and 512 for rows of 1024 (transforms of length
-// 512), which would otherwise hold 64 complex values a thread
+// threads a block: 256, and 512 for rows of 768 and 1024 (transforms of
+// length 384 and 512), which would otherwise hold too many values a thread
 template <int W>
-__host__ __device__ constexpr int row_threads() { return W >= 1024 ? 512 : 256; }
+__host__ __device__ constexpr int row_threads() { return W >= 768 ? 512 : 256; }
 
 template <int N, int W>
 struct RowCfg {
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(row_threads<W>()) k_row(const __grid_constant_
             const int l = l0 + i * TL;
             if (LP % TL == 0 || l < LP) {
                 const float2 zl = Zn[xoff<WH>(l)];
-                const float2 zc = cconj(Zn[xoff<WH>((WH - l) & (WH - 1))]);
+                const float2 zc = cconj(Zn[xoff<WH>(l == 0 ? 0 : WH - l)]);
                 const float2 s = cadd(zl, zc), d = csub(zl, zc);
                 const float2 E = make_float2(0.5f * s.x, 0.5f * s.y);
                 const float2 O = make_float2(0.5f * d.y, -0.5f * d.x);  // -i d / 2
@@ -243,6 +243,8 @@ cudaError_t row_dispatch(int W, const RowArgs *a, cudaStream_t s) {
         case 256: return a ? row_launch<N, 256>(*a, s) : row_attr<N, 256>();
         case 512: return a ? row_launch<N, 512>(*a, s) : row_attr<N, 512>();
         case 1024: return a ? row_launch<N, 1024>(*a, s) : row_attr<N, 1024>();
+        case 384: return a ? row_launch<N, 384>(*a, s) : row_attr<N, 384>();
+        case 768: return a ? row_launch<N, 768>(*a, s) : row_attr<N, 768>();
         default: return cudaErrorInvalidValue;
     }
 }
@@ -252,7 +254,8 @@ cudaError_t row_dispatch(int W, const RowArgs *a, cudaStream_t s) {
 }  // namespace se2n
 
 bool se2n_row_supported(int N, int W) {
-    return (N == 16 || N == 32) && (W == 64 || W == 128 || W == 256 || W == 512 || W == 1024);
+    return (N == 16 || N == 32) &&
+           (W == 64 || W == 128 || W == 256 || W == 512 || W == 1024 || W == 384 || W == 768);
 }
 
 cudaError_t se2n_row_prepare(int N, int W) {

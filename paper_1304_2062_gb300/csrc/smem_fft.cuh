@@ -1,8 +1,9 @@
 // Batched complex DFTs in shared memory, the building block of the row and
 // column passes (rowfft.cu, colprop.cu): N transforms of length L (a power
-// of two, 32 .. 512) held as a block [N][L], transformed in place by
-// mixed-radix Stockham (self-sorting) passes, radix 8 and then one pass of
-// radix 2 or 4 where L is not a power of 8:
+// of two, 32 .. 512, or 192 or 384) held as a block [N][L], transformed in
+// place by mixed-radix Stockham (self-sorting) passes: radix 8 and then one
+// pass of radix 2 or 4 where L is not a power of 8, two of radix 16 for 256,
+// and a radix-3 pass first for 192 = 3 x 64 and 384 = 3 x 128:
 //   pass with radix R over sub-transforms of length NS already done:
 //   butterfly j reads elements j + r L / R (r < R), multiplies them by
 //   exp(DIR 2 pi i r (j mod NS) / (NS R)), takes the R-point DFT, and writes
@@ -29,7 +30,7 @@ __device__ __forceinline__ int xoff(int i) {
 }
 template <int L>
 __device__ __forceinline__ int xsm(int e) {
-    return (e / L) * (L + 1) + xoff<L>(e & (L - 1));
+    return (e / L) * (L + 1) + xoff<L>(e % L);
 }
 
 template <int N, int L>
@@ -64,10 +65,20 @@ __device__ __forceinline__ float2 w16(float2 z) {
     return make_float2(fmaf(z.x, wr, -z.y * wi), fmaf(z.x, wi, z.y * wr));
 }
 
-// V_k = sum_n v_n exp(DIR 2 pi i n k / R), in place, for R = 2, 4, 8, 16.
+// V_k = sum_n v_n exp(DIR 2 pi i n k / R), in place, for R = 2, 3, 4, 8, 16.
 template <int R, int DIR>
 __device__ __forceinline__ void dft_small(float2 (&v)[R]) {
-    if constexpr (R == 2) {
+    if constexpr (R == 3) {
+        // w = exp(DIR 2 pi i / 3) = -1/2 + DIR i sqrt(3)/2: V_0 = a + (b + c),
+        // V_1,2 = a - (b + c)/2 +- DIR i (sqrt(3)/2) (b - c)
+        constexpr float h3 = 0.86602540378443865f;  // sqrt(3) / 2
+        const float2 a = v[0], t1 = cadd(v[1], v[2]), t2 = csub(v[1], v[2]);
+        const float2 m = make_float2(fmaf(-0.5f, t1.x, a.x), fmaf(-0.5f, t1.y, a.y));
+        const float2 n = DIR < 0 ? make_float2(h3 * t2.y, -h3 * t2.x) : make_float2(-h3 * t2.y, h3 * t2.x);
+        v[0] = cadd(a, t1);
+        v[1] = cadd(m, n);
+        v[2] = csub(m, n);
+    } else if constexpr (R == 2) {
         const float2 a = v[0], b = v[1];
         v[0] = cadd(a, b);
         v[1] = csub(a, b);
@@ -136,17 +147,19 @@ __device__ __forceinline__ void fft_pass(float2 *X, const float2 *twp, int tid) 
     constexpr int M = L / R;  // butterflies a transform
     constexpr int NB = N * M;
     constexpr int BPT = (NB + T - 1) / T;
-    static_assert(T % M == 0, "j depends on the thread only");
-    // butterfly b = tid + q T: transform b / M, index j = tid mod M for every
-    // q, so the twiddles are read once
-    const int j = tid % M, k = j & (NS - 1);
-    // positions inside the plane of this thread's inputs and outputs, the
-    // same for all its butterflies
-    int ro[R], wo[R];
+    // butterfly b = tid + q T: transform b / M, index j = b mod M. Where T is
+    // a multiple of M, j = tid mod M for every q, so the positions and the
+    // twiddles are formed once; otherwise (radix-3 lengths) once a butterfly.
+    constexpr bool UNIFORM = T % M == 0;
+    int ro[UNIFORM ? R : 1], wo[UNIFORM ? R : 1];
+    float2 w[UNIFORM ? R : 1];
+    if constexpr (UNIFORM) {
+        const int j = tid % M, k = j % NS;
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        ro[r] = xoff<L>(j + r * M);
-        wo[r] = xoff<L>((j - k) * R + k + r * NS);
+        for (int r = 0; r < R; ++r) {
+            ro[r] = xoff<L>(j + r * M);
+            wo[r] = xoff<L>((j - k) * R + k + r * NS);
+        }
     }
     float2 v[BPT][R];
 #pragma unroll
@@ -154,12 +167,13 @@ __device__ __forceinline__ void fft_pass(float2 *X, const float2 *twp, int tid) 
         const int b = tid + q * T;
         if (NB % T == 0 || b < NB) {
             const float2 *Xn = X + (b / M) * (L + 1);
+            const int j = b % M;
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[q][r] = Xn[ro[r]];
+            for (int r = 0; r < R; ++r) v[q][r] = Xn[UNIFORM ? ro[r] : xoff<L>(j + r * M)];
         }
     }
-    float2 w[R];
-    if constexpr (NS > 1) {
+    if constexpr (UNIFORM && NS > 1) {
+        const int k = (tid % M) % NS;
 #pragma unroll
         for (int r = 1; r < R; ++r) w[r] = twp[r * NS + k];
     }
@@ -168,14 +182,15 @@ __device__ __forceinline__ void fft_pass(float2 *X, const float2 *twp, int tid) 
     for (int q = 0; q < BPT; ++q) {
         const int b = tid + q * T;
         if (NB % T == 0 || b < NB) {
+            const int j = b % M, k = j % NS;
             if constexpr (NS > 1) {
 #pragma unroll
-                for (int r = 1; r < R; ++r) v[q][r] = twiddle<DIR>(v[q][r], w[r]);
+                for (int r = 1; r < R; ++r) v[q][r] = twiddle<DIR>(v[q][r], UNIFORM ? w[r] : twp[r * NS + k]);
             }
             dft_small<R, DIR>(v[q]);
             float2 *Xn = X + (b / M) * (L + 1);
 #pragma unroll
-            for (int r = 0; r < R; ++r) Xn[wo[r]] = v[q][r];
+            for (int r = 0; r < R; ++r) Xn[UNIFORM ? wo[r] : xoff<L>((j - k) * R + k + r * NS)] = v[q][r];
         }
     }
 }
@@ -183,16 +198,21 @@ __device__ __forceinline__ void fft_pass(float2 *X, const float2 *twp, int tid) 
 // The passes with twiddles (NS > 1) of the DFTs of length L, and their
 // tables: pass (R, NS) needs exp(-2 pi i r k / (NS R)) for r < R, k < NS,
 // kept at twp[offset + r NS + k]. Lengths 32 = 8 x 4, 64 = 8 x 8,
-// 128 = 8 x 8 x 2, 256 = 16 x 16, 512 = 8 x 8 x 8.
+// 128 = 8 x 8 x 2, 256 = 16 x 16, 512 = 8 x 8 x 8, 192 = 3 x 8 x 8,
+// 384 = 3 x 8 x 8 x 2: up to three passes after the first (NS = 1).
 template <int L>
 struct FftTw {
-    // (R, NS) of the second and third pass (0 where there is none)
+    static constexpr bool TRI = L == 192 || L == 384;
+    // (R, NS) of the second, third and fourth pass (R = 0 where there is none)
     static constexpr int R2 = L == 32 ? 4 : (L == 256 ? 16 : 8);
-    static constexpr int NS2 = L == 256 ? 16 : 8;
-    static constexpr int R3 = L == 128 ? 2 : (L == 512 ? 8 : 0);
-    static constexpr int NS3 = 64;
+    static constexpr int NS2 = TRI ? 3 : (L == 256 ? 16 : 8);
+    static constexpr int R3 = TRI ? 8 : (L == 128 ? 2 : (L == 512 ? 8 : 0));
+    static constexpr int NS3 = TRI ? 24 : 64;
+    static constexpr int R4 = L == 384 ? 2 : 0;
+    static constexpr int NS4 = 192;
     static constexpr int OFF3 = R2 * NS2;
-    static constexpr int SIZE = OFF3 + R3 * NS3;  // complex entries
+    static constexpr int OFF4 = OFF3 + R3 * NS3;
+    static constexpr int SIZE = OFF4 + R4 * NS4;  // complex entries
 };
 
 // Fill the pass tables from tw[m TS] = exp(-2 pi i m / L) (a table of L TS
@@ -206,10 +226,14 @@ __device__ __forceinline__ void fft_twiddles(float2 *twp, const float2 *tw, int 
             r = e / F::NS2;
             k = e - r * F::NS2;
             step = L / (F::NS2 * F::R2);
-        } else {
+        } else if (e < F::OFF4) {
             r = (e - F::OFF3) / F::NS3;
             k = (e - F::OFF3) - r * F::NS3;
             step = F::R3 ? L / (F::NS3 * F::R3) : 0;
+        } else {
+            r = (e - F::OFF4) / F::NS4;
+            k = (e - F::OFF4) - r * F::NS4;
+            step = F::R4 ? L / (F::NS4 * F::R4) : 0;
         }
         twp[e] = tw[r * k * step * TS];
     }
@@ -219,12 +243,25 @@ __device__ __forceinline__ void fft_twiddles(float2 *twp, const float2 *tw, int 
 // synchronises before and after.
 template <int T, int N, int L, int DIR>
 __device__ __forceinline__ void fft_smem(float2 *X, const float2 *twp, int tid) {
-    static_assert(L == 32 || L == 64 || L == 128 || L == 256 || L == 512, "transform length");
+    static_assert(L == 32 || L == 64 || L == 128 || L == 256 || L == 512 || L == 192 || L == 384,
+                  "transform length");
     using F = FftTw<L>;
     if constexpr (L == 256) {
         fft_pass<T, N, L, 16, 1, DIR>(X, twp, tid);
         __syncthreads();
         fft_pass<T, N, L, 16, 16, DIR>(X, twp, tid);
+        return;
+    }
+    if constexpr (F::TRI) {
+        fft_pass<T, N, L, 3, 1, DIR>(X, twp, tid);
+        __syncthreads();
+        fft_pass<T, N, L, 8, 3, DIR>(X, twp, tid);
+        __syncthreads();
+        fft_pass<T, N, L, 8, 24, DIR>(X, twp + F::OFF3, tid);
+        if constexpr (L == 384) {
+            __syncthreads();
+            fft_pass<T, N, L, 2, 192, DIR>(X, twp + F::OFF4, tid);
+        }
         return;
     }
     fft_pass<T, N, L, 8, 1, DIR>(X, twp, tid);

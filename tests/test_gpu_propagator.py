@@ -234,13 +234,15 @@ def test_full_512_N32_ten_rounds_against_stored_oracle():
 @pytest.mark.parametrize("H,W,N,dynamic,final_mix,proj,reinject", [
     (64, 128, 32, 0, 0, 0, 0), (128, 64, 16, 0, 1, 0, 0), (256, 64, 32, 0, 0, 1, 1), (64, 64, 16, 1, 0, 0, 0),
     (128, 128, 32, 1, 1, 0, 1), (512, 256, 16, 0, 1, 1, 0), (1024, 128, 32, 0, 0, 0, 0),
-    (128, 1024, 16, 0, 0, 0, 1), (1024, 64, 32, 1, 0, 0, 0)])
+    (128, 1024, 16, 0, 0, 0, 1), (1024, 64, 32, 1, 0, 0, 0), (384, 256, 32, 0, 0, 0, 0), (256, 768, 16, 0, 1, 1, 0),
+    (768, 64, 32, 1, 0, 0, 1), (384, 384, 32, 0, 0, 0, 0)])
 def test_row_and_column_passes_match_oracle(H, W, N, dynamic, final_mix, proj, reinject):
-    """Plane sizes with H and W in 64 .. 1024 and N = 16 or 32 run the fused
-    passes: a row pass (lift, or inverse DFT along x, restoration and forward
-    DFT along x, or projection) and a column pass (DFT along y, propagators,
-    inverse DFT along y) an interval. Cases cover every radix mix of both
-    lengths (8 x 4 .. 16 x 16), the final restoration, mean projection,
+    """Plane sizes with H and W in {64, 128, 256, 384, 512, 768, 1024} and N =
+    16 or 32 run the fused passes: a row pass (lift, or inverse DFT along x,
+    restoration and forward DFT along x, or projection) and a column pass
+    (DFT along y, propagators, inverse DFT along y) an interval. Cases cover
+    every radix mix of both lengths (8 x 4 .. 16 x 16, 8 x 8 x 8 and the
+    radix-3 lengths 3 x 8 x 8 (x 2)), the final restoration, mean projection,
     reinjection and dynamic restoration (a row pass gives the image value and
     its argmax angle to each growth step; the restoration pulls the grown set
     to its references while reinjection keeps the given known pixels)."""
