@@ -89,6 +89,20 @@ def cpu_model():
 
 
 GOLDEN_DYNAMIC = os.path.join(ROOT, "tests", "golden", "curves_noise_512_N32_dynamic.npz")
+GOLDEN_GUARD0 = os.path.join(ROOT, "tests", "golden", "curves_noise_512_N32_guard0.npz")
+SENSITIVITY = os.path.join(ROOT, "tests", "golden", "sensitivity_512_N32.json")
+
+
+def fp32_sensitivity():
+    """The FP64 oracle's sensitivity to FP32 rounding on the 512x512 workload
+    (written by tests/golden/make_sensitivity.py), or None."""
+    try:
+        s = json.load(open(SENSITIVITY))
+    except (OSError, ValueError):
+        return None
+    out = {k: s[k]["max_abs_over_max_f"] for k in ("storage_full", "perturb_full", "fp32_full", "fp32_half")}
+    out["s32"] = max(out["fp32_half"], out["fp32_full"])
+    return out
 
 
 def _config(w, extra=None, dynamic=False):
@@ -505,6 +519,7 @@ def run_ours(args, rank, world, local_rank):
 
     # error of this result against the FP64 oracle (stored reference, same inputs)
     golden = GOLDEN_DYNAMIC if dynamic else GOLDEN
+    sens = fp32_sensitivity()
     if rank == 0 and os.path.exists(golden):
         g = np.load(golden)
         b_d = torch.tensor(g["bins"], device=dev)
@@ -521,9 +536,208 @@ def run_ours(args, rank, world, local_rank):
             "bins": "oracle's (FP64) bins given to both sides",
             "own_bin_mismatches": int((own.cpu().numpy() != g["bins"]).sum()),
             "oracle_seconds_for_this_result": float(g["oracle_seconds"][0])}
+        if sens:
+            result["err_vs_fp64"]["bound"] = {
+                "max_abs_over_max_f": 4.0 * sens["s32"],
+                "basis": "4 x S32, S32 = the largest change of the FP64 oracle's own result when its transforms run "
+                         "in FP32 and its volume is stored in FP32 (tests/golden/sensitivity_512_N32.json: "
+                         f"{sens['fp32_half']:.2e} on the Hermitian half, {sens['fp32_full']:.2e} on the full "
+                         f"spectrum; FP32 storage alone {sens['storage_full']:.2e})",
+                "within": result["err_vs_fp64"]["max_abs_over_max_f"] <= 4.0 * sens["s32"]}
+        if not dynamic and os.path.exists(GOLDEN_GUARD0):
+            # the paper's restoration rule as printed (no relative guard)
+            g0 = np.load(GOLDEN_GUARD0)
+            prm0 = se2n.se2n_params_default(N=w.N, beta=w.beta, T=w.T, steps=w.steps, rounds=w.rounds, eps=w.eps,
+                                            sigma_smooth=w.sigma, diffuse_flags=flags, guard=0.0)
+            with torch.cuda.stream(stream):
+                se2n.se2n_inpaint(plan, f_d, m_d, torch.tensor(g0["bins"], device=dev), prm0, vol, out)
+            torch.cuda.synchronize(dev)
+            got0 = out.cpu().numpy().astype(np.float64)
+            ref0 = g0["out"].astype(np.float64)
+            result["err_vs_fp64"]["guard0"] = {
+                "rel_l2": float(np.linalg.norm(got0 - ref0) / np.linalg.norm(ref0)),
+                "max_abs_over_max_f": float(np.abs(got0 - ref0).max() / np.abs(w.f).max()),
+                "rule": "sigma at every good pixel with h(t_i) > 0 (guard 0), against the oracle's guard-0 result"}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(w, dynamic=dynamic)
+    plan.close()
+    if dist:
+        dist.destroy_process_group()
+    return result
+
+
+# ----------------------------------------------------------------------------
+# the 2048x2048, N=64 workload
+# ----------------------------------------------------------------------------
+
+GOLDEN_2048 = os.path.join(ROOT, "tests", "golden", "lines_patches_2048_N64.npz")
+
+
+def run_2048(args, rank, world, local_rank):
+    """2048x2048 lines-plus-texture image, N=64 (a 2 GiB complex64 volume),
+    85 % of the pixels corrupted, one interval of 1000 Crank-Nicolson steps:
+    the main run (beta = 0.25, T = 50) timed as the line's value, and the
+    stiff run (beta = 10, T = 1000: beta dt = 10, split diagonal, with and
+    without the FP64 Sherman-Morrison correction) beside it. Each step is one
+    whole inpaint through se2n_inpaint (orientation, lift, transforms,
+    diffusion, inverse, projection). Errors: the projected image against the
+    FP64 oracle's stored result at every 4th row and column, and the
+    diffused spectrum of the main run against the oracle's integration of a
+    seeded sample of its frequencies (all 64 angles each)."""
+    import torch
+
+    from paper_1304_2062_gb300 import se2n
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    stream = torch.cuda.Stream(dev)
+    w = synth.workload_2048()
+    ws = synth.workload_2048(stress=True)
+    f32 = w.f.astype(np.float32)
+    plan = se2n.se2n_plan_create(w.H, w.W, w.N, 0, stream)
+    prop = args.diffusion == "propagator"
+    flags = se2n.SE2N_DIFFUSE_PROPAGATOR if prop else 0
+
+    def params(wk, fl):
+        return se2n.se2n_params_default(N=wk.N, beta=wk.beta, T=wk.T, steps=wk.steps, rounds=wk.rounds, eps=wk.eps,
+                                        sigma_smooth=wk.sigma, diffuse_flags=fl)
+    prm = params(w, flags)
+    f_d = torch.tensor(f32, device=dev)
+    m_d = torch.tensor(w.mask, device=dev)
+    vol = torch.empty((w.N, w.H, w.W), dtype=torch.complex64, device=dev)
+    out = torch.empty((w.H, w.W), dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step(p):
+        if prop:
+            se2n.se2n_plan_drop_propagators(plan)
+        se2n.se2n_inpaint(plan, f_d, m_d, None, p, vol, out)
+
+    def timed(p, k, warm):
+        with torch.cuda.stream(stream):
+            for _ in range(warm):
+                step(p)
+            torch.cuda.synchronize(dev)
+            if dist:
+                dist.barrier()
+            evs = []
+            for _ in range(k):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                step(p)
+                b.record(stream)
+                evs.append((a, b))
+            torch.cuda.synchronize(dev)
+        return max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), dist, dev) / k
+
+    with ClockSampler(local_rank) as clocks:
+        ms = timed(prm, args.steps, args.warmup)
+    # the kernels' launch times from the same steps with the stage events on
+    se2n.se2n_plan_profile(plan, True)
+    timed(prm, max(1, min(args.steps, 3)), 0)
+    prof = se2n.se2n_plan_profile_read(plan, reset=True)
+    se2n.se2n_plan_profile(plan, False)
+    launches = prof["kernels"] / max(1, min(args.steps, 3))
+    upd = integrated_updates(w.H, w.W, w.N, w.steps, w.rounds)
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
+    d_ms, d_calls = prof["diffuse"]
+    d_s = d_ms / d_calls / 1e3
+    if prop:
+        b_ms, b_calls = prof["propagator"]
+        b_s = b_ms / b_calls / 1e3
+        items = propagator_build_items(w.H, w.W)
+        flops, products = propagator_gemm_flops(items, w.N, w.steps)
+        roofline = {"bound": "alu", "kernel": f"k_prop_build<{w.N}> ({items} classes, full FP32 products)",
+                    "achieved": round(flops / b_s / 1e12, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
+                    "frac": round(flops / b_s / 1e12 / peak, 4), "traffic": None,
+                    "avg_launch_ms": round(b_s * 1e3, 4), "flops_per_launch": flops,
+                    "apply_avg_launch_ms": round(d_s * 1e3, 4)}
+    else:
+        achieved = FLOPS_PER_UPDATE * upd / d_s / 1e12
+        roofline = {"bound": "alu", "kernel": f"k_diffuse_x2<{w.N},4,...> (packed FP32 pairs)",
+                    "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
+                    "frac": round(achieved / peak, 4), "traffic": None, "flops_per_update": FLOPS_PER_UPDATE,
+                    "updates_per_launch": upd, "avg_launch_ms": round(d_s * 1e3, 4),
+                    "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop/FMA x 2070 MHz (derived, not measured)",
+                    "hbm_gbs_of_diffuse": round(16 * w.H * (w.W // 2 + 1) * w.N / d_s / 1e9, 1)}
+    stages = {k: {"ms_per_step": round(v[0] / max(1, min(args.steps, 3)), 4)} for k, v in prof.items()
+              if k != "kernels" and v[1] > 0}
+
+    # the other diffusion on the same inpaint, for comparison
+    other = params(w, 0 if prop else se2n.SE2N_DIFFUSE_PROPAGATOR)
+    other_ms = timed(other, 2, 1)
+    # the stiff run: split diagonal (beta T > 8), FP32 and FP64 corrections
+    stiff = {}
+    for name, fl in (("fp32_correction", 0), ("fp64_correction", se2n.SE2N_DIFFUSE_SM_FP64)):
+        stiff[name] = {"ms_per_inpaint": round(timed(params(ws, fl), 2, 1), 4)}
+
+    result = {"metric": METRIC, "ms_per_inpaint": round(ms, 4), "value": world * upd / (ms / 1e3), "unit": UNIT,
+              "m2_updates_per_s": world * w.updates() / (ms / 1e3), "n_gpus": world, "steps": args.steps,
+              "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+              "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+              "config": {"workload": "lines_patches_2048_N64: 2048x2048 lines plus textured patches, N=64, 85% "
+                                     "random mask, beta=0.25, T=50, one interval of 1000 CN steps",
+                         "updates_per_step": upd, "m2_updates_per_step": w.updates(),
+                         "diffusion": "S-step propagators (separate apply)" if prop else
+                                      "step by step, the fused Crank-Nicolson kernel",
+                         "l2": "flushed between timed steps (256 MiB write); the 2 GiB volume exceeds L2",
+                         "parallelism": "replicas"},
+              "roofline": roofline, "stages_ms": stages, "gpu_launches": int(round(launches)),
+              ("step_by_step" if prop else "propagators"): {"ms_per_inpaint": round(other_ms, 4),
+                                                            "value": world * upd / (other_ms / 1e3)},
+              "stiff_run": {"workload": "beta=10, T=1000, 1000 steps (beta dt = 10), split diagonal", **stiff},
+              "clocks": clocks.summary()}
+
+    # errors against the FP64 oracle
+    if rank == 0:
+        import oracle
+        err = {}
+        bins_main = oracle.orient(f32.astype(np.float64), w.mask, w.N)["bins"]
+        b_d = torch.tensor(bins_main, device=dev)
+        if os.path.exists(GOLDEN_2048):
+            g = np.load(GOLDEN_2048)
+            st = int(g["stride"][0])
+            for name, wk, fl in (("main", w, flags), ("stiff_fp32", ws, 0), ("stiff_fp64", ws, se2n.SE2N_DIFFUSE_SM_FP64)):
+                key = "main_out" if name == "main" else "stress_out"
+                if key not in g:
+                    continue
+                with torch.cuda.stream(stream):
+                    se2n.se2n_inpaint(plan, f_d, m_d, b_d, params(wk, fl), vol, out)
+                torch.cuda.synchronize(dev)
+                got = out.cpu().numpy()[::st, ::st].astype(np.float64)
+                ref = g[key].astype(np.float64)
+                err[name] = {"rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+                             "max_abs_over_max_f": float(np.abs(got - ref).max() / np.abs(w.f).max()),
+                             "compared": f"every {st}th row and column of the projected image"}
+        # the diffused spectrum of the main run at a seeded sample of frequencies
+        with torch.cuda.stream(stream):
+            se2n.se2n_lift(plan, f_d, m_d, b_d, vol)
+            se2n.se2n_forward(plan, vol)
+        torch.cuda.synchronize(dev)
+        rng = np.random.default_rng(2048)
+        freqs = np.sort(rng.choice(w.H * w.W, size=4096, replace=False))
+        v0 = vol.reshape(w.N, -1)[:, torch.tensor(freqs, device=dev)].cpu().numpy()
+        with torch.cuda.stream(stream):
+            se2n.se2n_diffuse(plan, vol, w.beta, w.T, w.steps, flags)
+        torch.cuda.synchronize(dev)
+        v1 = vol.reshape(w.N, -1)[:, torch.tensor(freqs, device=dev)].cpu().numpy()
+        # the oracle integrates the sampled frequencies' systems in place on
+        # the full-size index space (the symbols follow from H, W and k, l)
+        full = np.zeros((w.N, w.H, w.W), np.complex128)
+        full.reshape(w.N, -1)[:, freqs] = v0
+        t0 = time.perf_counter()
+        ref = oracle.diffuse(full, w.beta, w.T, w.steps, freqs=freqs).reshape(w.N, -1)[:, freqs]
+        err["spectrum_sampled"] = {
+            "rel_l2": float(np.linalg.norm(v1 - ref) / np.linalg.norm(ref)),
+            "frequencies": int(freqs.size), "oracle_seconds": round(time.perf_counter() - t0, 2),
+            "note": "the GPU's own lifted and transformed spectrum, diffused by both sides"}
+        result["err_vs_fp64"] = err
     plan.close()
     if dist:
         dist.destroy_process_group()
@@ -1179,18 +1393,21 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["512", "dr", "batch", "surrogate", "unet-forward"], default="512",
+    ap.add_argument("--workload", choices=["512", "dr", "2048", "batch", "surrogate", "unet-forward"], default="512",
                     help="512: the 512x512 N=32 10x500-step inpaint (default); dr: the same with dynamic "
-                         "restoration; batch: 256 uneven images; surrogate: train the U-Net on method pairs, "
+                         "restoration; 2048: the 2048x2048 N=64 1000-step inpaint (and its beta dt = 10 run); "
+                         "batch: 256 uneven images; surrogate: train the U-Net on method pairs, "
                          "time its inference with fallback")
-    ap.add_argument("--diffusion", choices=["propagator", "steps"], default="propagator",
-                    help="512 / dr: integrate each interval by S-step propagators built every inpaint (default) "
+    ap.add_argument("--diffusion", choices=["propagator", "steps"], default=None,
+                    help="512 / dr / 2048: integrate each interval by S-step propagators built every inpaint (default) "
                          "or step by step with the fused Crank-Nicolson kernel")
     ap.add_argument("--train-seconds", type=float, default=150.0, help="surrogate training time budget")
     ap.add_argument("--train-pairs", type=int, default=0, help="surrogate training pairs (0: all 20000)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per diffusion launch from an ncu capture of the current kernel")
     args = ap.parse_args()
+    if args.diffusion is None:
+        args.diffusion = "propagator"
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", args.gpus))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
@@ -1200,6 +1417,8 @@ def main():
         res = run_reference(args, rank, world)
     elif args.workload == "batch":
         res = run_batch(args, rank, world, local_rank)
+    elif args.workload == "2048":
+        res = run_2048(args, rank, world, local_rank)
     elif args.workload == "surrogate":
         res = run_surrogate(args, rank, world, local_rank)
     elif args.workload == "unet-forward":

@@ -1,26 +1,48 @@
 """Helpers shared by the GPU parity tests: device tensors from numpy inputs
 and the comparison metrics with their tolerances.
 
-Tolerances (the diffusion runs in FP32 against the FP64 oracle):
+Tolerances (the path runs in FP32 against the FP64 oracle):
   * REL_L2 = 1e-5: relative L2 error over a whole volume or image;
   * MAX_REL = 1e-5: max-abs error of a projected image relative to max|f|.
-Both are the stated accuracy target of the path; the measured errors are
-typically 1e-7 .. 2e-6 (see the test output).
+Both are the stated accuracy target of the path; every result below full
+size meets them (the measured errors are 1e-7 .. 2e-6, see the test output).
 
-  * MAX_REL_RESTORED = 1e-4: max-abs bound for results of several
-    restoration intervals. The restoration divides by h(t) (sigma up to
-    eps/guard + 1 - eps = 5.5), which amplifies pointwise FP32 differences at
-    the rescaled pixels from one interval to the next; FP32 rounding of the
-    stored volume alone already moves the FP64 result by ~7e-6 pointwise on
-    the 512x512 workload. The relative L2 bound REL_L2 still applies to
-    these results.
+  * MAX_REL_512 = 4 x S32: the max-abs bound of the full 512x512 workload
+    (10 restoration intervals), derived from the FP64 oracle itself. S32 is
+    the larger of the two measured changes of the oracle's result when its
+    transforms run in FP32 and its volume is stored in FP32, on the full and
+    on the Hermitian-half spectrum (oracle/sensitivity.py, written by
+    tests/golden/make_sensitivity.py to sensitivity_512_N32.json: 3.8e-6
+    and 8.2e-6 at one pixel, while FP32 storage rounding alone moves it by
+    5.3e-7). The workload amplifies rounding at that pixel: a corrupted
+    region whose value the restorations pump up over the intervals, so
+    that an exact FP32 transform already misses 1e-5 by little. The GPU
+    also rounds the diffusion and the restoration in FP32 (each adding
+    per-interval error of the order of one transform), hence the factor 4.
+  * TIE_TOL_512 = 2 x MAX_REL_512: a dynamic-restoration decision compares
+    two such values, so one within this distance of a tie may go either way.
 """
+import json
+import os
+
 import numpy as np
 import torch
 
 REL_L2 = 1e-5
 MAX_REL = 1e-5
-MAX_REL_RESTORED = 1e-4
+
+_SENS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "sensitivity_512_N32.json")
+
+
+def fp32_sensitivity_512():
+    """S32 of the 512x512 workload from the stored FP64-oracle sensitivity run."""
+    with open(_SENS) as fh:
+        s = json.load(fh)
+    return max(s["fp32_half"]["max_abs_over_max_f"], s["fp32_full"]["max_abs_over_max_f"])
+
+
+MAX_REL_512 = 4.0 * fp32_sensitivity_512()
+TIE_TOL_512 = 2.0 * MAX_REL_512
 
 
 def restoration_sigma_max(f64, mask, bins, p):
