@@ -350,7 +350,11 @@ def run_ours(args, rank, world, local_rank):
         classes = propagator_classes(w.H, w.W)
         wc = w.W // 2 + 1
         spec_bytes = 8 * wc * w.H * w.N
-        col_bytes = 2 * spec_bytes + 4 * w.N * w.N * classes
+        # the method's bytes: the half spectrum in and out, and every class's
+        # propagator once as its N (N + 1) / 2 distinct entries (the kernel
+        # reads the stored rows, 4 N^2 bytes a class: stored_bytes_per_launch)
+        col_bytes = 2 * spec_bytes + 4 * (w.N * (w.N + 1) // 2) * classes
+        col_stored_bytes = 2 * spec_bytes + 4 * w.N * w.N * classes
         row_bytes = 2 * spec_bytes + 6 * w.H * w.W
         col_flops = 2 * wc * w.N * 5 * w.H * int(math.log2(w.H)) + 4 * w.N * w.N * w.H * wc
         items = propagator_build_items(w.H, w.W)
@@ -367,7 +371,10 @@ def run_ours(args, rank, world, local_rank):
                               "one block a column)",
                     "bytes_per_launch": col_bytes,
                     "bytes_basis": "one read and one write of the row-transformed half spectrum (8 (W/2+1) H N "
-                                   "bytes each) + the propagators as rows, read once (4 N^2 bytes a class)",
+                                   "bytes each) + every class's symmetric propagator once, as its N (N + 1) / 2 "
+                                   "distinct entries (4 N (N + 1) / 2 bytes a class)",
+                    "stored_bytes_per_launch": col_stored_bytes,
+                    "stored_basis": "the propagators as the kernel reads them, full rows (4 N^2 bytes a class)",
                     "avg_launch_ms": round(c_s * 1e3, 4), "peak_basis": hbm_basis,
                     "flops_per_launch": col_flops,
                     "flops_basis": "2 (W/2+1) N complex DFTs of length H at 5 H log2 H + 4 N^2 a frequency",
