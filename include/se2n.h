@@ -83,10 +83,12 @@ typedef enum se2n_status {
  * (symmetric; by cyclic diagonals, 4 N (N/2 + 1) bytes a class, or as rows,
  * 4 N^2 bytes a class, for the column pass below: about H W N^2 / 4 bytes in
  * all) and reuses them while beta dt, S, the spectrum half and the storage
- * stay the same, so the intervals of one inpaint build them once. N = 16, 32
- * or 64 (else SE2N_EUNSUPPORTED); the other flags do not apply.
- * In se2n_inpaint on the Hermitian half with N = 16 or 32 and H, W powers of
- * two in 64..512, this flag alone selects the row and column passes: the
+ * stay the same, so the intervals of one inpaint build them once. N = 16,
+ * 30, 32 or 64 (else SE2N_EUNSUPPORTED); N = 30 is built and stored as
+ * 32 x 32 matrices whose last two rows and columns are zero (the bytes of
+ * N = 32). The other flags do not apply.
+ * In se2n_inpaint on the Hermitian half with N = 16 or 32 and H, W each one
+ * of 64, 128, 256, 384, 512, 768, 1024, this flag alone selects the row and column passes: the
  * volume stays row-transformed between intervals in a plan buffer of
  * 8 (W/2 + 1) H N bytes, each interval is one kernel a column (DFT along y,
  * propagators, inverse DFT) and one kernel a row (real DFTs along x around

@@ -110,10 +110,13 @@ __device__ __forceinline__ long long build_class(const PropArgs &a, long long w,
 }
 
 // Entry (i, j) of the stored matrix of class u: P D_S P for a transposed
-// partner (shift = perm_shift), D_S itself (shift < 0).
-template <int N>
+// partner (shift = perm_shift), D_S itself (shift < 0). NE <= N angles are
+// the system's; a padded index i >= NE stays where it is.
+template <int N, int NE = N>
 __device__ __forceinline__ int perm_index(int i, int shift) {
-    return shift < 0 ? i : (shift - i) & (N - 1);
+    if (shift < 0 || i >= NE) return i;
+    const int v = shift - i;
+    return v < 0 ? v + NE : v;
 }
 
 // out = two * X + Y + A B for one class, N x N in shared memory: A, X, Y and
@@ -268,7 +271,7 @@ struct SymCfg;
 // D_S of class u from a symmetric matrix in the layout of SymCfg<N>: as rows
 // in 16-byte chunks, chunk-major, or by cyclic diagonals; lanes t of `lanes`.
 // shift >= 0 stores the permuted matrix P D_S P of a transposed class.
-template <int N>
+template <int N, int NE = N>
 __device__ __forceinline__ void prop_store(const PropArgs &a, const float *Rm, long long u, bool live, int t,
                                            int lanes, int shift = -1) {
     using C = SymCfg<N>;
@@ -280,18 +283,18 @@ __device__ __forceinline__ void prop_store(const PropArgs &a, const float *Rm, l
             if (shift < 0) {
                 out[e] = *reinterpret_cast<const float4 *>(Rm + C::at(i, 4 * c));
             } else {
-                const int pi = perm_index<N>(i, shift);
-                out[e] = make_float4(Rm[C::at(pi, perm_index<N>(4 * c, shift))],
-                                     Rm[C::at(pi, perm_index<N>(4 * c + 1, shift))],
-                                     Rm[C::at(pi, perm_index<N>(4 * c + 2, shift))],
-                                     Rm[C::at(pi, perm_index<N>(4 * c + 3, shift))]);
+                const int pi = perm_index<N, NE>(i, shift);
+                out[e] = make_float4(Rm[C::at(pi, perm_index<N, NE>(4 * c, shift))],
+                                     Rm[C::at(pi, perm_index<N, NE>(4 * c + 1, shift))],
+                                     Rm[C::at(pi, perm_index<N, NE>(4 * c + 2, shift))],
+                                     Rm[C::at(pi, perm_index<N, NE>(4 * c + 3, shift))]);
             }
         }
     } else {
         float *out = a.D + u * (long long)((N / 2 + 1) * N);
         for (int e = t; e < (N / 2 + 1) * N; e += lanes) {
             const int m = e / N, i = e - m * N;
-            out[e] = Rm[C::at(perm_index<N>(i, shift), perm_index<N>((i + m) & (N - 1), shift))];
+            out[e] = Rm[C::at(perm_index<N, NE>(i, shift), perm_index<N, NE>((i + m) & (N - 1), shift))];
         }
     }
 }
@@ -592,7 +595,7 @@ __device__ __forceinline__ void sym_gemm(const float *A, const float *B, const f
     }
 }
 
-template <int N>
+template <int N, int NE = N>
 __global__ void __launch_bounds__(SymCfg<N>::WARPS * 32) k_prop_build_sym(const __grid_constant__ PropArgs a) {
     using C = SymCfg<N>;
     extern __shared__ __align__(16) float psm[];
@@ -619,29 +622,42 @@ __global__ void __launch_bounds__(SymCfg<N>::WARPS * 32) k_prop_build_sym(const 
         int k, l, lb;
         class_slots(a, u, k, l, lb);
         const float wx = sin_2pi_frac(l, a.W), wy = sin_2pi_frac(k, a.H);
-        if (active && t == 0) prop_factor<N>(a, wx, wy, G, q, scal);
+        if (active && t == 0) prop_factor<NE>(a, wx, wy, G, q, scal);
         __syncwarp();
-        // D_1 column by column into R (R row c = column c), then P = (R + R^T) / 2
+        // D_1 column by column into R (R row c = column c), then P = (R + R^T) / 2.
+        // A system of NE < N angles sits in the top-left NE x NE block, the
+        // rest zero: the powering keeps the zero blocks zero (2 D + D D and
+        // D_a + D_b + D_a D_b of block-diagonal matrices), so the block is the
+        // NE-angle system's D_S.
         if (active) {
             const float inv_d0 = scal[0], inv_den = scal[1];
 #pragma unroll 1
-            for (int c = t; c < N; c += C::TILES) {
+            for (int c = t; c < NE; c += C::TILES) {
                 const float ar = fmaf(wx, a.cs[c], wy * a.sn[c]);
                 const float e2 = ar * ar * a.inv_beta;
-                const int cm = (c == 0) ? N - 1 : c - 1, cp = (c == N - 1) ? 0 : c + 1;
-                float x[N], y[N];
+                const int cm = (c == 0) ? NE - 1 : c - 1, cp = (c == NE - 1) ? 0 : c + 1;
+                float x[NE], y[NE];
 #pragma unroll
-                for (int j = 0; j < N; ++j) {
+                for (int j = 0; j < NE; ++j) {
                     x[j] = (j == c) ? 1.0f : 0.0f;
                     y[j] = (j == c) ? -2.0f : ((j == cm || j == cp) ? 1.0f : 0.0f);
                 }
-                prop_solve2<N>(x, y, G, q, inv_d0, inv_den);
+                prop_solve2<NE>(x, y, G, q, inv_d0, inv_den);
+                float d[N];
+#pragma unroll
+                for (int j = NE; j < N; ++j) d[j] = 0.0f;
+#pragma unroll
+                for (int j = 0; j < NE; ++j) d[j] = fmaf(2.0f, y[j], -2.0f * e2 * x[j]);
 #pragma unroll
                 for (int j = 0; j < N; j += 4)
-                    *reinterpret_cast<float4 *>(R + C::at(c, j)) =
-                        make_float4(fmaf(2.0f, y[j], -2.0f * e2 * x[j]), fmaf(2.0f, y[j + 1], -2.0f * e2 * x[j + 1]),
-                                    fmaf(2.0f, y[j + 2], -2.0f * e2 * x[j + 2]),
-                                    fmaf(2.0f, y[j + 3], -2.0f * e2 * x[j + 3]));
+                    *reinterpret_cast<float4 *>(R + C::at(c, j)) = make_float4(d[j], d[j + 1], d[j + 2], d[j + 3]);
+            }
+            if constexpr (NE < N) {
+#pragma unroll 1
+                for (int c = NE + t; c < N; c += C::TILES)
+#pragma unroll
+                    for (int j = 0; j < N; j += 4)
+                        *reinterpret_cast<float4 *>(R + C::at(c, j)) = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             }
         }
         __syncwarp();
@@ -679,8 +695,8 @@ __global__ void __launch_bounds__(SymCfg<N>::WARPS * 32) k_prop_build_sym(const 
             }
             __syncwarp();
         }
-        prop_store<N>(a, a.chain_in_r ? R : P, u, live, t, C::TILES);
-        prop_store<N>(a, a.chain_in_r ? R : P, partner, live, t, C::TILES, a.perm_shift);
+        prop_store<N, NE>(a, a.chain_in_r ? R : P, u, live, t, C::TILES);
+        prop_store<N, NE>(a, a.chain_in_r ? R : P, partner, live, t, C::TILES, a.perm_shift);
         __syncwarp();
     }
 }
@@ -713,7 +729,10 @@ struct ApplyCfg {
     static_assert(XF % 4 == 0 && (CLASS_FLOATS % 4) == 0, "16-byte vectors");
 };
 
-template <int N>
+// NE < N: a system of NE angles stored padded to N (the propagator's rows and
+// columns NE .. N - 1 zero); only angles below NE are loaded and stored, and
+// the reversal of rows 2 and 3 is modulo NE.
+template <int N, int NE = N>
 __global__ void __launch_bounds__(ApplyCfg<N>::WARPS * 32) k_prop_apply(const __grid_constant__ PropArgs a) {
     using C = ApplyCfg<N>;
     constexpr int M = C::MEM;
@@ -753,12 +772,13 @@ __global__ void __launch_bounds__(ApplyCfg<N>::WARPS * 32) k_prop_apply(const __
 #pragma unroll
             for (int d = 1; d < N / 2; ++d) dv[i][N / 2 + d] = __ldg(Sc + d * N + ((r - d) & (N - 1)));
 #pragma unroll
-            for (int m = 0; m < M; ++m) mine[m][i] = on[m] ? a.vol[(long long)r * a.HW + f[m]] : make_float2(0.f, 0.f);
+            for (int m = 0; m < M; ++m)
+                mine[m][i] = on[m] && r < NE ? a.vol[(long long)r * a.HW + f[m]] : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int i = 0; i < C::RPL; ++i) {
             const int r = t + i * C::LPC;
-            const int rr = (N - r) & (N - 1);
+            const int rr = r < NE ? (r == 0 ? 0 : NE - r) : r;
 #pragma unroll
             for (int d = 0; d <= N / 2; ++d) Df[r * C::DLD + ((r + d) & (N - 1))] = dv[i][d];
 #pragma unroll
@@ -796,10 +816,10 @@ __global__ void __launch_bounds__(ApplyCfg<N>::WARPS * 32) k_prop_apply(const __
 #pragma unroll
         for (int i = 0; i < C::RPL; ++i) {
             const int r = t + i * C::LPC;
-            const int rr = (N - r) & (N - 1);
+            const int rr = r < NE ? (r == 0 ? 0 : NE - r) : r;
 #pragma unroll
             for (int m = 0; m < M; ++m)
-                if (on[m]) {
+                if (on[m] && r < NE) {
                     // slot r holds the value of angle r (rows 0, 1) or -r (rows 2, 3)
                     const float2 x0 = *reinterpret_cast<const float2 *>(xs + r * (2 * M) + 2 * m);
                     a.vol[(long long)(m < 4 ? r : rr) * a.HW + f[m]] =
@@ -825,25 +845,26 @@ cudaError_t launch_build_kernel(K kernel, const PropArgs &a, int num_sms, cudaSt
     return cudaGetLastError();
 }
 
-// N = 16, 32: symmetric products; N = 64: full products (one warp a class)
-template <int N>
+// N = 16, 32: symmetric products (NE = 30 angles padded to 32); N = 64: full
+// products (one warp a class)
+template <int N, int NE = N>
 cudaError_t launch_build(const PropArgs &a, int num_sms, cudaStream_t s) {
     if constexpr (N == 64)
         return launch_build_kernel<PropCfg<N>>(k_prop_build<N>, a, num_sms, s);
     else
-        return launch_build_kernel<SymCfg<N>>(k_prop_build_sym<N>, a, num_sms, s);
+        return launch_build_kernel<SymCfg<N>>(k_prop_build_sym<N, NE>, a, num_sms, s);
 }
 
-template <int N>
+template <int N, int NE = N>
 cudaError_t launch_apply(const PropArgs &a, int num_sms, cudaStream_t s) {
     using C = ApplyCfg<N>;
-    cudaError_t e = cudaFuncSetAttribute(k_prop_apply<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_prop_apply<N, NE>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
     const long long per_block = (long long)C::WARPS * C::CPW;
     long long blocks = (a.classes + per_block - 1) / per_block;
     const long long cap = (long long)num_sms * 64;
     if (blocks > cap) blocks = cap;
-    k_prop_apply<N><<<(unsigned)blocks, C::WARPS * 32, C::SMEM, s>>>(a);
+    k_prop_apply<N, NE><<<(unsigned)blocks, C::WARPS * 32, C::SMEM, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -945,9 +966,15 @@ se2n_status se2n_prop_chain(int steps, unsigned char *ops, int cap, int *len, in
     return SE2N_OK;
 }
 
-bool se2n_prop_supported(int N) { return N == 16 || N == 32 || N == 64; }
+bool se2n_prop_supported(int N) { return N == 16 || N == 30 || N == 32 || N == 64; }
 
-long long se2n_prop_floats(int N, bool rows) { return rows ? (long long)N * N : (long long)(N / 2 + 1) * N; }
+// N = 30 is stored padded to 32 angles (zero rows and columns 30, 31)
+int se2n_prop_dim(int N) { return N == 30 ? 32 : N; }
+
+long long se2n_prop_floats(int N, bool rows) {
+    const long long n = se2n_prop_dim(N);
+    return rows ? n * n : (n / 2 + 1) * n;
+}
 
 int se2n_prop_col_slots(int W, bool half) { return half ? W / 4 + 1 : se2n::pair_rows(W); }
 
@@ -969,6 +996,12 @@ cudaError_t se2n_prop_prepare(int N) {
                        ? cudaFuncSetAttribute(se2n::k_prop_apply<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               se2n::ApplyCfg<32>::SMEM)
                        : cudaGetLastError();
+        case 30:
+            return cudaFuncSetAttribute(se2n::k_prop_build_sym<32, 30>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        se2n::SymCfg<32>::SMEM) == cudaSuccess
+                       ? cudaFuncSetAttribute(se2n::k_prop_apply<32, 30>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              se2n::ApplyCfg<32>::SMEM)
+                       : cudaGetLastError();
         case 64:
             return cudaFuncSetAttribute(se2n::k_prop_build<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         se2n::PropCfg<64>::SMEM) == cudaSuccess
@@ -983,6 +1016,7 @@ cudaError_t se2n_launch_prop_build(int N, const PropArgs &a, int num_sms, cudaSt
     switch (N) {
         case 16: return se2n::launch_build<16>(a, num_sms, s);
         case 32: return se2n::launch_build<32>(a, num_sms, s);
+        case 30: return se2n::launch_build<32, 30>(a, num_sms, s);
         case 64: return se2n::launch_build<64>(a, num_sms, s);
         default: return cudaErrorInvalidValue;
     }
@@ -992,6 +1026,7 @@ cudaError_t se2n_launch_prop_apply(int N, const PropArgs &a, int num_sms, cudaSt
     switch (N) {
         case 16: return se2n::launch_apply<16>(a, num_sms, s);
         case 32: return se2n::launch_apply<32>(a, num_sms, s);
+        case 30: return se2n::launch_apply<32, 30>(a, num_sms, s);
         case 64: return se2n::launch_apply<64>(a, num_sms, s);
         default: return cudaErrorInvalidValue;
     }

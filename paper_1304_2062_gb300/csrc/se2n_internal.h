@@ -141,7 +141,8 @@ struct PropArgs {
     float cs[SE2N_MAX_N];
     float sn[SE2N_MAX_N];
 };
-bool se2n_prop_supported(int N);
+bool se2n_prop_supported(int N);  // 16, 30 (stored as 32), 32, 64
+int se2n_prop_dim(int N);          // angles of the stored propagator
 long long se2n_prop_floats(int N, bool rows = false);  // stored floats a class
 int se2n_prop_col_slots(int W, bool half);
 long long se2n_prop_classes(int H, int W, bool half);

@@ -46,10 +46,13 @@ def _run(vol, N, beta, T, S, flags):
     (16, 12, 64, 0.25, 2.0, 256), (64, 22, 30, 0.7, 3.0, 100),
     (32, 18, 14, 10.0, 20.0, 20), (64, 18, 14, 10.0, 20.0, 20), (16, 2, 6, 0.5, 1.0, 9),
     (16, 4, 8, 0.5, 2.0, 30), (32, 6, 10, 0.5, 2.0, 30), (16, 10, 4, 0.4, 2.0, 25),
-    (64, 16, 20, 0.25, 2.0, 500), (64, 18, 14, 0.5, 2.0, 30), (32, 18, 14, 10.0, 30.0, 30)])
+    (64, 16, 20, 0.25, 2.0, 500), (64, 18, 14, 0.5, 2.0, 30), (32, 18, 14, 10.0, 30.0, 30),
+    (30, 34, 22, 0.25, 2.0, 500), (30, 6, 10, 0.5, 2.0, 30), (30, 18, 14, 0.3, 2.0, 15), (30, 2, 6, 0.5, 1.0, 9)])
 def test_propagator_matches_oracle(N, H, W, beta, T, S):
     """The powering programs of S = 15, 30 and 500 square R into P (op 1);
-    the others only square P and combine."""
+    the others only square P and combine. N = 30 (the angle count of the
+    paper's experiments) runs as a 30-angle system in the top-left block of
+    32-angle matrices, the padding zero."""
     vol = synth.random_volume(N, H, W, seed=N + H + S).astype(np.complex64)
     ref = oracle.diffuse(vol.astype(np.complex128), beta, T, S)
     got = _run(vol, N, beta, T, S, PROP)
@@ -89,13 +92,16 @@ def test_stiff_steps_fall_back_to_the_step_kernel(N, H, W, beta, T, S, builds):
     assert err <= REL_L2
 
 
-@pytest.mark.parametrize("N,H,conv", [(16, 24, 0), (32, 40, 0), (64, 20, 0), (32, 40, 1), (64, 28, 1), (16, 12, 1)])
+@pytest.mark.parametrize("N,H,conv", [(16, 24, 0), (32, 40, 0), (64, 20, 0), (32, 40, 1), (64, 28, 1), (16, 12, 1),
+                                      (30, 36, 0), (30, 20, 1)])
 def test_transposed_classes_share_one_build(N, H, conv):
     """On square planes a class and its transpose (row and column slots
     swapped) are one operator up to the angle reflection r -> N/2 - r
     (N/4 - r on the 2 pi r / N grid), so the build computes the upper
     triangle of slot pairs and stores each matrix permuted for its
-    transpose: every frequency must still match the oracle."""
+    transpose: every frequency must still match the oracle. N = 30 on the
+    2 pi r / N grid has no such reflection (4 does not divide 30): every
+    class is built."""
     vol = synth.random_volume(N, H, H, seed=N + 3 * H + conv).astype(np.complex64)
     ref = oracle.diffuse(vol.astype(np.complex128), 0.25, 2.0, 60, angle_conv=conv)
     plan = se2n.se2n_plan_create(H, H, N, conv)
@@ -147,8 +153,8 @@ def test_lifted_image_spectrum():
 
 
 def test_unsupported_angle_count():
-    plan = se2n.se2n_plan_create(8, 8, 30)
-    v = torch.zeros((30, 8, 8), dtype=torch.complex64, device="cuda")
+    plan = se2n.se2n_plan_create(8, 8, 24)
+    v = torch.zeros((24, 8, 8), dtype=torch.complex64, device="cuda")
     with pytest.raises(se2n.Se2nError) as e:
         se2n.se2n_diffuse(plan, v, 0.25, 1.0, 10, PROP)
     assert e.value.status == se2n.SE2N_EUNSUPPORTED
@@ -199,7 +205,7 @@ def _gpu_inpaint(f32, mask, bins, prm, profile=False):
 
 
 @pytest.mark.parametrize("H,W,N,full", [(96, 96, 32, 0), (64, 160, 32, 1), (64, 64, 16, 0), (48, 80, 64, 0),
-                                         (66, 70, 16, 0), (70, 66, 32, 1)])
+                                         (66, 70, 16, 0), (70, 66, 32, 1), (96, 96, 30, 0), (64, 80, 30, 1)])
 def test_inpaint_with_propagators_matches_oracle(H, W, N, full):
     w = synth.workload_512(H=H, W=W, steps=60, rounds=3)
     p = oracle.Params(N=N, beta=0.25, T=6.0, steps=60, rounds=3)
