@@ -180,7 +180,7 @@ class ClockSampler:
 
 KERNEL_SOURCES = {"diffuse": ("diffuse_impl.cuh", "diffuse_x2.cuh", "diffuse.cu"),
                   "prop_build": ("propagator.cu", "prop_classes.cuh", "diffuse_x2.cuh", "diffuse_impl.cuh"),
-                  "col_prop": ("colprop.cu", "smem_fft.cuh", "prop_classes.cuh", "diffuse_x2.cuh"),
+                  "col_prop": ("colprop.cu", "bulk_copy.cuh", "smem_fft.cuh", "prop_classes.cuh", "diffuse_x2.cuh"),
                   "row_pass": ("rowfft.cu", "smem_fft.cuh", "restore.cuh")}
 TRAFFIC_FILES = {"diffuse": "diffuse_traffic.json", "prop_build": "prop_build_traffic.json",
                  "col_prop": "col_prop_traffic.json", "row_pass": "row_pass_traffic.json"}
@@ -367,8 +367,8 @@ def run_ours(args, rank, world, local_rank):
         roofline = {"bound": "hbm", "achieved": round(col_bytes / c_s / 1e9, 1), "peak": hbm, "unit": "GB/s",
                     "frac": round(col_bytes / c_s / 1e9 / hbm, 4) if hbm else None,
                     "traffic": args.traffic if args.traffic is not None else stored_traffic("col_prop"),
-                    "kernel": f"k_col_prop<{w.N},{w.H}> (column pass: DFT along y, x <- x + D_S x, inverse DFT; "
-                              "one block a column)",
+                    "kernel": f"k_col_tma<{w.N},{w.H}> (column pass: DFT along y, x <- x + D_S x, inverse DFT; "
+                              "whole columns in shared memory, bulk copies in and out, one persistent block an SM)",
                     "bytes_per_launch": col_bytes,
                     "bytes_basis": "one read and one write of the row-transformed half spectrum (8 (W/2+1) H N "
                                    "bytes each) + every class's symmetric propagator once, as its N (N + 1) / 2 "

@@ -350,6 +350,7 @@ se2n_status col_diffuse(se2n_plan *plan, double beta, double T, int steps) {
     a.W = plan->W;
     a.Wc = plan->Wc;
     a.col_slots = se2n_prop_col_slots(plan->W, true);
+    a.num_sms = plan->num_sms;
     StageTimer timer(plan, SE2N_STAGE_DIFFUSE);
     plan->kernels += 1;
     return cuda_status(plan, se2n_launch_col_prop(plan->N, a, plan->stream));

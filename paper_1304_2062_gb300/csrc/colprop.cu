@@ -2,35 +2,43 @@
 // spectrum, fused. Between intervals the volume is row-transformed: the DFT
 // along x (index l) of every row of every angle plane, stored as complex
 // [Wc][H][N] (rowfft.cu writes and reads it), so column l's H x N block is
-// contiguous and a frequency's N angles are adjacent. One block a column l:
-//   1. takes the DFT along y (index k) of every angle plane (unnormalised),
-//      which completes the two-dimensional DFT of the lifted volume;
-//   2. applies x <- x + D_S x to the N-vector of every frequency (k, l),
-//      D_S the S-step propagator of its class, stored by 16-byte chunks of
-//      its rows, chunk-major (eq. (deceq), Theorem 2, integrated by S
-//      Crank-Nicolson steps; see propagator.cu), with the angles reversed
-//      for rows H/2 + s and H - s;
-//   3. takes the inverse DFT along k,
-// in shared memory (smem_fft.cuh), so the spectrum of the interval never
-// goes through device memory.
+// contiguous and a frequency's N angles are adjacent. For every column l:
+//   1. the DFT along y (index k) of every angle plane (unnormalised), which
+//      completes the two-dimensional DFT of the lifted volume;
+//   2. x <- x + D_S x for the N-vector of every frequency (k, l), D_S the
+//      S-step propagator of its class, stored by 16-byte chunks of its rows,
+//      chunk-major (eq. (deceq), Theorem 2, integrated by S Crank-Nicolson
+//      steps; see propagator.cu), with the angles reversed for rows H/2 + s
+//      and H - s;
+//   3. the inverse DFT along k,
+// in shared memory, so the spectrum of the interval never goes through
+// device memory.
 //
 // The four rows s, H/2 - s, H/2 + s, H - s of a class have the parity of s,
 // so a first radix-2 step (decimation in frequency) splits each column into
 // its even and odd frequencies, u_k = x_k + x_{k+H/2} and
 // v_k = (x_k - x_{k+H/2}) w^k (w = exp(-2 pi i / H)), whose H/2-point DFTs
-// are X_{2k} and X_{2k+1}: each half holds whole classes. A block takes the
-// halves one after the other (forward DFT, apply, inverse DFT), keeping v
-// and then the even half's result y_e in the rows of its own column block,
-// and ends with x_k = y_e,k + w^-k y_o,k, x_{k+H/2} = y_e,k - w^-k y_o,k.
-// Half a column in shared memory (66 KB at H = 512, N = 32) lets two
-// blocks share an SM, so the 257 columns of a 512 x 512 plane run in one
-// wave and one block's loads overlap the other's arithmetic.
+// are X_{2k} and X_{2k+1}: each half holds whole classes, and the column is
+// put back by x_k = y_e,k + w^-k y_o,k, x_{k+H/2} = y_e,k - w^-k y_o,k.
+//
+// Two kernels. k_col_tma (wherever the column fits in shared memory: N H
+// complex up to 192 KB) keeps the whole column in the rows of device memory
+// ([k][n]), brought in and out by bulk asynchronous copies, with in-place
+// transforms whose every access is a run of whole rows. k_col_prop (N = 32,
+// H = 1024) keeps half a column in angle planes [n][k] (smem_fft.cuh), the
+// halves one after the other, v and then the even half's result y_e held in
+// the rows of the column's own block in device memory.
 #include "diffuse_x2.cuh"
 #include "prop_classes.cuh"
 #include "se2n_internal.h"
 #include "smem_fft.cuh"
+#include "bulk_copy.cuh"
 
 namespace se2n {
+
+// Set by a column pass whose bounded wait for its copy-in ran out (which would
+// mean the device stopped making progress); read by se2n_col_fault().
+__device__ int g_col_fault;
 
 namespace {
 
@@ -216,16 +224,432 @@ __global__ void __launch_bounds__(col_threads<H>(), H >= 768 ? 1 : 2) k_col_prop
     }
 }
 
+// ---------------------------------------------------------------------------
+// The column pass with the whole column in shared memory (N H complex: up to
+// H = 768 for N = 32 and H = 1024 for N = 16). Rows stay as they are in device
+// memory, X[k N + n] (row k, angle n), so one bulk asynchronous copy brings
+// the column in and one takes it back, and every access of the transforms
+// (a row of all the angles) is one contiguous run of shared memory.
+//
+// The transforms along k are in place: decimation in frequency forward (the
+// half-column spectrum ends in digit-reversed order, col_pos), decimation in
+// time inverse (back to natural order). Rows 0 .. L-1 of the column hold the
+// even half and rows L .. H-1 the odd half (L = H / 2); the radix-2 split is
+// folded into the reads of the first forward pass and the recombination into
+// the writes of the last inverse pass.
+
+// radices of the half-column DFT of length L, first pass first (R3 = 1: two
+// passes); the first radix is small so that the first pass has many butterflies
+template <int L>
+struct ColPlan {
+    static constexpr int R1 = L == 32 ? 4 : (L == 256 ? 16 : (L == 192 || L == 384 ? 3 : 8));
+    static constexpr int R2 = L == 32 || L == 64 || L == 192 || L == 384 || L == 512 ? 8 : 16;
+    static constexpr int R3 = L / (R1 * R2);
+    static_assert(R1 * R2 * R3 == L && (R3 == 1 || R3 == 8 || R3 == 16), "radix plan");
+};
+
+// row of the half-column holding frequency f after the forward passes:
+// f = f1 + R1 f2 + R1 R2 f3 sits at f1 L / R1 + f2 L / (R1 R2) + f3
+template <int L>
+__device__ __forceinline__ int col_pos(int f) {
+    using P = ColPlan<L>;
+    const int f1 = f % P::R1, q = f / P::R1;
+    const int f2 = q % P::R2, f3 = q / P::R2;
+    return f1 * (L / P::R1) + f2 * (L / (P::R1 * P::R2)) + f3;
+}
+
+enum { CP_PLAIN = 0, CP_SPLIT = 1, CP_MERGE = 2 };
+
+// One in-place radix-R pass over blocks of LS rows (S = LS / R): butterfly
+// (block c, j < S) of angle n on rows c LS + j + m S, m < R, of both halves
+// (CP_PLAIN), or of the two halves at once with the split u = x_k + x_{k+L},
+// v = (x_k - x_{k+L}) w^k (w = exp(-2 pi i / H)) folded into its reads
+// (CP_SPLIT, first forward pass) or the recombination x_k = y_k + w^-k z_k,
+// x_{k+L} = y_k - w^-k z_k into its writes (CP_MERGE, last inverse pass).
+// Forward (DIR = -1): the R-point DFT, output r times w_LS^{j r}, back to row
+// j + r S; inverse: input r times w_LS^{-j r}, the inverse R-point DFT,
+// output m back to row j + m S. w_LS^e = tws[e H / LS].
+template <int T, int N, int L, int R, int LS, int DIR, int MODE>
+__device__ __forceinline__ void col_pass(float2 *XA, float2 *XB, const float2 *tws, int tid) {
+    constexpr int S = LS / R, BLK = L / LS, TW = 2 * L / LS;
+    constexpr int BF = BLK * S;  // butterflies of one half and angle
+    constexpr int TASKS = (MODE == CP_PLAIN ? 2 : 1) * BF * N;
+    static_assert(T % N == 0, "one angle a thread");
+    const int n = tid % N;
+#pragma unroll
+    for (int task = tid; task < TASKS; task += T) {
+        const int u = task / N;
+        const int half = MODE == CP_PLAIN ? u / BF : 0;
+        const int rest = u - half * BF;
+        const int c = rest / S, j = rest - c * S;
+        float2 *Xa = (half ? XB : XA) + (c * LS + j) * N + n;  // row m of the butterfly: Xa[m S N]
+        float2 *Xb = XB + (c * LS + j) * N + n;                // the same row of the odd half
+        float2 p[R], q[MODE == CP_PLAIN ? 1 : R];
+        if constexpr (MODE == CP_SPLIT) {
+#pragma unroll
+            for (int m = 0; m < R; ++m) {
+                const float2 x0 = Xa[m * S * N], x1 = Xb[m * S * N];
+                p[m] = cadd(x0, x1);
+                q[m] = twiddle<-1>(csub(x0, x1), tws[j + m * S]);
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < R; ++m) {
+                p[m] = Xa[m * S * N];
+                if constexpr (MODE == CP_MERGE) q[m] = Xb[m * S * N];
+            }
+        }
+        if constexpr (DIR > 0) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                const float2 w = tws[j * r * TW];
+                p[r] = twiddle<1>(p[r], w);
+                if constexpr (MODE != CP_PLAIN) q[r] = twiddle<1>(q[r], w);
+            }
+        }
+        dft_small<R, DIR>(p);
+        if constexpr (MODE != CP_PLAIN) dft_small<R, DIR>(q);
+        if constexpr (DIR < 0) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                const float2 w = tws[j * r * TW];
+                p[r] = twiddle<-1>(p[r], w);
+                if constexpr (MODE != CP_PLAIN) q[r] = twiddle<-1>(q[r], w);
+            }
+        }
+        if constexpr (MODE == CP_MERGE) {
+#pragma unroll
+            for (int m = 0; m < R; ++m) {
+                const float2 o = twiddle<1>(q[m], tws[j + m * S]);
+                Xa[m * S * N] = cadd(p[m], o);
+                Xb[m * S * N] = csub(p[m], o);
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < R; ++m) {
+                Xa[m * S * N] = p[m];
+                if constexpr (MODE == CP_SPLIT) Xb[m * S * N] = q[m];
+            }
+        }
+    }
+}
+
+// forward: the split, then the DFTs of both halves (natural order in,
+// digit-reversed out); the caller synchronises before and after
+template <int T, int N, int L>
+__device__ __forceinline__ void col_forward(float2 *XA, float2 *XB, const float2 *tws, int tid) {
+    using P = ColPlan<L>;
+    col_pass<T, N, L, P::R1, L, -1, CP_SPLIT>(XA, XB, tws, tid);
+    __syncthreads();
+    col_pass<T, N, L, P::R2, L / P::R1, -1, CP_PLAIN>(XA, XB, tws, tid);
+    if constexpr (P::R3 > 1) {
+        __syncthreads();
+        col_pass<T, N, L, P::R3, P::R3, -1, CP_PLAIN>(XA, XB, tws, tid);
+    }
+}
+
+// inverse: the mirror of col_forward, ending in the recombination
+template <int T, int N, int L>
+__device__ __forceinline__ void col_inverse(float2 *XA, float2 *XB, const float2 *tws, int tid) {
+    using P = ColPlan<L>;
+    if constexpr (P::R3 > 1) {
+        col_pass<T, N, L, P::R3, P::R3, 1, CP_PLAIN>(XA, XB, tws, tid);
+        __syncthreads();
+    }
+    col_pass<T, N, L, P::R2, L / P::R1, 1, CP_PLAIN>(XA, XB, tws, tid);
+    __syncthreads();
+    col_pass<T, N, L, P::R1, L, 1, CP_MERGE>(XA, XB, tws, tid);
+}
+
+// x <- x + D_S x for every frequency of the column, classes s = 0 .. H/4
+// (the even half for even s, the odd half for odd s): one class per N/2
+// lanes, rows t and t + N/2 of D_S a lane in registers (drow), a class after
+// another. x_j, x_{j+1} of one frequency are one 16-byte shared-memory
+// broadcast for the lanes of a class; the classes of one warp take the
+// columns j rotated by 16 / (classes a warp), so that their broadcasts fall
+// on different banks (drow holds the rotated columns). Rows 0 and 1 take
+// columns 2p, 2p + 1 at step p; the reversed rows 2 and 3 read angles
+// -2p, -2p + 1 (adjacent in the row) for columns 2p, 2p - 1, except that
+// column 0 is taken at step 0, column N/2 - 1 at the end of the first half,
+// N/2 at the start of the second and N - 1 at the end (the order in which a
+// row's terms are summed is fixed, so every run gives the same bits). The
+// next class's rows are prefetched into L1 while this one is applied.
+template <int T, int N, int H>
+__device__ __forceinline__ void col_apply_rows(float2 *XA, float2 *XB, const float *D, int scol, int col_slots,
+                                               int tid) {
+    constexpr int L = H / 2, LPC = N / 2, CPW = 32 / LPC, WARPS = T / 32, ROT = 16 / CPW;
+    constexpr int COUNT = H / 4 + 1, STRIDE = WARPS * CPW, NC = N / 4;  // NC: 16-byte chunks a row
+    const int warp = tid >> 5, lane = tid & 31;
+    const int g = lane / LPC, t = lane - g * LPC, rot = ROT * g;
+    float drow[2][N];
+    // chunks [c0, c0 + NC/2) of rows t, t + N/2 of class s (rotated columns);
+    // chunk-major storage: D[r][4c .. 4c + 3] is float4 c N + r
+    auto load_half = [&](int s, int c0) {
+        const float4 *Dc = reinterpret_cast<const float4 *>(D + ((long long)s * col_slots + scol) * (N * N));
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+            for (int c = c0; c < c0 + NC / 2; ++c) {
+                const float4 d = __ldg(Dc + ((c + rot / 4) & (NC - 1)) * N + t + q * LPC);
+                drow[q][4 * c] = d.x;
+                drow[q][4 * c + 1] = d.y;
+                drow[q][4 * c + 2] = d.z;
+                drow[q][4 * c + 3] = d.w;
+            }
+    };
+    // classes are taken warp-uniformly so that every lane reaches each __syncwarp
+    for (int i0 = warp * CPW; i0 < COUNT; i0 += STRIDE) {
+        const int i = i0 + g;
+        const bool live = i < COUNT, more = i + STRIDE < COUNT;
+        const int s = live ? i : COUNT - 1;
+        load_half(s, 0);
+        load_half(s, NC / 2);
+        // the class this lane takes next, into L1 while this one is applied
+        if (more) {
+            const char *Dn = reinterpret_cast<const char *>(D + ((long long)(i + STRIDE) * col_slots + scol) * (N * N));
+#pragma unroll
+            for (int c = 0; c < N / 16; ++c) asm volatile("prefetch.global.L1 [%0];" ::"l"(Dn + (t + c * LPC) * 128));
+        }
+        int k[4];
+        bool kon[4];
+        slot_rows(s, H, k, kon);
+        float2 *Xh = (s & 1) ? XB : XA;
+        int xo[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) xo[m] = col_pos<L>(k[m] >> 1) * N;
+        // shared-memory addresses: normal rows read angle 2p + rot, reversed
+        // rows angle (N - rot - 2p) mod N; where N = 32 each wraps at one step
+        // for every class of a warp (12 and 13), so each row has one address
+        // before that step and one after, plus one for step 0 of a reversed row
+        uint32_t a0[4], a1[4], az[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const uint32_t row = bulk::saddr(Xh + xo[m]);
+            if (m < 2) {
+                a0[m] = row + 8u * rot;
+                a1[m] = a0[m] - 8u * N * (rot > 0);
+                az[m] = 0;
+            } else {
+                a0[m] = row + 8u * (N - rot);
+                a1[m] = a0[m] + 8u * N * (rot > 0);
+                az[m] = row + 8u * ((N - rot) & (N - 1));
+            }
+        }
+        auto xget = [&](int m, int p) -> float4 {
+            float4 v;
+            if constexpr (N == 32) {
+                const uint32_t ad = m < 2 ? (p < 12 ? a0[m] : a1[m]) + 16u * p
+                                          : (p == 0 ? az[m] : (p < 13 ? a0[m] : a1[m]) - 16u * p);
+                asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n"
+                             : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                             : "r"(ad));
+            } else {
+                const int j = m < 2 ? (2 * p + rot) & (N - 1) : (N - rot - 2 * p) & (N - 1);
+                v = *reinterpret_cast<const float4 *>(Xh + xo[m] + j);
+            }
+            return v;
+        };
+        f32x2 acc[2][4];
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+            for (int m = 0; m < 4; ++m) acc[q][m] = pk2(0.f, 0.f);
+        auto fma_col = [&](int m, int col, f32x2 x) {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) acc[q][m] = fma2(dup2(drow[q][col]), x, acc[q][m]);
+        };
+        f32x2 keep_last[2];  // angle -(N - 1) of the reversed rows, for column N - 1
+        f32x2 keep_mid[2];   // angle -N/2 of the reversed rows, for column N/2
+#pragma unroll
+        for (int p = 0; p < N / 4; ++p) {
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const float4 v = xget(m, p);
+                const f32x2 lo = pk2(v.x, v.y), hi = pk2(v.z, v.w);
+                if (m < 2) {
+                    fma_col(m, 2 * p, lo);
+                    fma_col(m, 2 * p + 1, hi);
+                } else if (p == 0) {
+                    fma_col(m, 0, lo);
+                    keep_last[m - 2] = hi;
+                } else {
+                    fma_col(m, 2 * p, lo);
+                    fma_col(m, 2 * p - 1, hi);
+                }
+            }
+        }
+#pragma unroll
+        for (int m = 2; m < 4; ++m) {
+            const float4 v = xget(m, N / 4);
+            fma_col(m, N / 2 - 1, pk2(v.z, v.w));
+            keep_mid[m - 2] = pk2(v.x, v.y);
+        }
+#pragma unroll
+        for (int m = 2; m < 4; ++m) fma_col(m, N / 2, keep_mid[m - 2]);
+#pragma unroll
+        for (int p = N / 4; p < N / 2; ++p) {
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                if (m >= 2 && p == N / 4) continue;  // taken above
+                const float4 v = xget(m, p);
+                const f32x2 lo = pk2(v.x, v.y), hi = pk2(v.z, v.w);
+                if (m < 2) {
+                    fma_col(m, 2 * p, lo);
+                    fma_col(m, 2 * p + 1, hi);
+                } else {
+                    fma_col(m, 2 * p, lo);
+                    fma_col(m, 2 * p - 1, hi);
+                }
+            }
+        }
+#pragma unroll
+        for (int m = 2; m < 4; ++m) fma_col(m, N - 1, keep_last[m - 2]);
+        __syncwarp();
+        if (live) {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int r = t + q * LPC, rr = (N - r) & (N - 1);
+#pragma unroll
+                for (int m = 0; m < 4; ++m)
+                    if (kon[m]) {
+                        // slot r of a reversed row is angle -r
+                        float2 &x = Xh[xo[m] + (m < 2 ? r : rr)];
+                        x = make_float2(x.x + lo2(acc[q][m]), x.y + hi2(acc[q][m]));
+                    }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// threads: enough for the first pass's butterflies (both halves at once), 128 .. 512
+template <int N, int H>
+__host__ __device__ constexpr int col_tma_threads() {
+    return (H / 2 / ColPlan<H / 2>::R1) * N >= 512   ? 512
+           : (H / 2 / ColPlan<H / 2>::R1) * N <= 128 ? 128
+                                                     : (H / 2 / ColPlan<H / 2>::R1) * N;
+}
+
+template <int N, int H>
+struct ColTmaCfg {
+    static constexpr int L = H / 2;
+    static constexpr int T = col_tma_threads<N, H>();
+    static constexpr int HB = L * N * 8;   // bytes of half a column
+    static constexpr int TWB = H * 8 + 16;  // w^m (m < H) and a barrier a half
+    static constexpr int SMEM = 2 * HB + TWB;
+    // blocks an SM the registers are shaped for: two where the column is
+    // small (up to 128 registers a thread at T <= 256), else one
+    static constexpr int MINB = T < 512 && 2 * SMEM <= 227 * 1024 ? 2 : 1;
+};
+
+template <int N, int H>
+constexpr bool col_tma_fits() {
+    return ColTmaCfg<N, H>::SMEM <= 227 * 1024;
+}
+
+// Column l of unit c: the two columns of a class are consecutive units, so
+// they run side by side and share its propagators in L2.
+__device__ __forceinline__ int col_of_unit(int c, int W) { return (c & 1) ? W / 2 - (c >> 1) : c >> 1; }
+
+// Persistent: block x takes units x, x + gridDim.x, ... Each half of the
+// column has its slot of shared memory (rows 0 .. L-1 and L .. H-1), its
+// copy-in completing on the slot's barrier; the next column is copied in as
+// soon as the copy-out of this one has read the slots. (A third slot, to copy
+// the next column's even half in during the transforms, measured slower: the
+// propagators' stream from device memory during the apply has no bandwidth
+// to spare.) Every wait for a copy-in is bounded; one that runs out sets
+// g_col_fault and returns once the copies in flight have landed (again
+// bounded), leaving the unit's column as it was.
+template <int N, int H>
+__global__ void __launch_bounds__(ColTmaCfg<N, H>::T, ColTmaCfg<N, H>::MINB)
+    k_col_tma(const __grid_constant__ ColArgs a) {
+    using C = ColTmaCfg<N, H>;
+    constexpr int L = C::L, T = C::T, HB = C::HB, HF = L * N;  // HF: complex a half
+    extern __shared__ __align__(128) float2 ctm[];
+    float2 *XA = ctm, *XB = ctm + HF;
+    float2 *tws = ctm + 2 * HF;  // exp(-2 pi i m / H), m < H
+    const uint32_t bar = bulk::saddr(tws + H), sa = bulk::saddr(XA), sb = bulk::saddr(XB);  // barriers at bar, bar + 8
+    const int tid = threadIdx.x;
+    int c = blockIdx.x;
+    if (c >= a.Wc) return;
+    if (tid == 0) {
+        bulk::bar_init(bar, 1);
+        bulk::bar_init(bar + 8, 1);
+    }
+    __syncthreads();
+    auto copy_in = [&](int unit) {  // one thread
+        const float2 *g = a.col + (long long)col_of_unit(unit, a.W) * (N * H);
+        bulk::bar_expect(bar, HB);
+        bulk::load(sa, g, HB, bar);
+        bulk::bar_expect(bar + 8, HB);
+        bulk::load(sb, g + HF, HB, bar + 8);
+    };
+    if (tid == 0) copy_in(c);
+    for (int m = tid; m < H; m += T) tws[m] = a.tw[m];
+    for (uint32_t ph = 0; c < a.Wc; c += gridDim.x, ph ^= 1u) {
+        const int l = col_of_unit(c, a.W);
+        const bool ok = bulk::bar_wait(bar, ph) && bulk::bar_wait(bar + 8, ph);
+        if (!__syncthreads_and(ok)) {
+            if (tid == 0) {
+                atomicExch(&g_col_fault, 1);
+                (void)bulk::bar_wait(bar, ph);
+                (void)bulk::bar_wait(bar + 8, ph);
+                bulk::store_commit_wait();
+            }
+            return;
+        }
+        col_forward<T, N, L>(XA, XB, tws, tid);
+        __syncthreads();
+        col_apply_rows<T, N, H>(XA, XB, a.D, half_col_slot(l, a.W), a.col_slots, tid);
+        __syncthreads();
+        col_inverse<T, N, L>(XA, XB, tws, tid);
+        bulk::fence_to_async();
+        __syncthreads();
+        if (tid == 0) {
+            float2 *g = a.col + (long long)l * (N * H);
+            bulk::store(g, sa, HB);
+            bulk::store(g + HF, sb, HB);
+            bulk::store_commit();
+            if (c + (int)gridDim.x < a.Wc) {
+                bulk::store_wait_read();  // the copy-out has read both slots
+                copy_in(c + gridDim.x);
+            }
+        }
+    }
+    if (tid == 0) bulk::store_commit_wait();
+}
+
+// persistent grid: the columns, at most the blocks resident at once
+template <int N, int H>
+int col_grid(const ColArgs &a) {
+    static int per_sm = 0;  // per instantiation, the same on every GB300
+    if (per_sm <= 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_col_tma<N, H>, ColTmaCfg<N, H>::T,
+                                                                      ColTmaCfg<N, H>::SMEM) != cudaSuccess)
+        per_sm = 0;
+    const long long cap = (long long)(a.num_sms > 0 ? a.num_sms : 1) * (per_sm > 0 ? per_sm : 1);
+    return (int)(a.Wc < cap ? a.Wc : cap);
+}
+
+// the whole-column kernel where the column fits in shared memory, else the
+// kernel of half columns
 template <int N, int H>
 cudaError_t col_attr() {
-    return cudaFuncSetAttribute(k_col_prop<N, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, ColCfg<N, H>::SMEM);
+    if constexpr (col_tma_fits<N, H>())
+        return cudaFuncSetAttribute(k_col_tma<N, H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    ColTmaCfg<N, H>::SMEM);
+    else
+        return cudaFuncSetAttribute(k_col_prop<N, H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    ColCfg<N, H>::SMEM);
 }
 
 template <int N, int H>
 cudaError_t col_launch(const ColArgs &a, cudaStream_t s) {
     cudaError_t e = col_attr<N, H>();
     if (e != cudaSuccess) return e;
-    k_col_prop<N, H><<<a.Wc, ColCfg<N, H>::T, ColCfg<N, H>::SMEM, s>>>(a);
+    if constexpr (col_tma_fits<N, H>())
+        k_col_tma<N, H><<<col_grid<N, H>(a), ColTmaCfg<N, H>::T, ColTmaCfg<N, H>::SMEM, s>>>(a);
+    else
+        k_col_prop<N, H><<<a.Wc, ColCfg<N, H>::T, ColCfg<N, H>::SMEM, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -260,4 +684,13 @@ cudaError_t se2n_col_prepare(int N, int H) {
 cudaError_t se2n_launch_col_prop(int N, const ColArgs &a, cudaStream_t s) {
     if (!se2n_col_supported(N, a.H)) return cudaErrorInvalidValue;
     return N == 16 ? se2n::col_dispatch<16>(a.H, &a, s) : se2n::col_dispatch<32>(a.H, &a, s);
+}
+
+cudaError_t se2n_col_fault(int *host_flag, bool reset) {
+    cudaError_t e = cudaMemcpyFromSymbol(host_flag, se2n::g_col_fault, sizeof(int));
+    if (e == cudaSuccess && reset && *host_flag) {
+        const int zero = 0;
+        e = cudaMemcpyToSymbol(se2n::g_col_fault, &zero, sizeof(int));
+    }
+    return e;
 }

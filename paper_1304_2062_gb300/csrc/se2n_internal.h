@@ -159,10 +159,13 @@ struct ColArgs {
     const float *D;     // [classes][N/4][N] float4 (see PropArgs)
     const float2 *tw;   // exp(-2 pi i m / H), m < H
     int H, W, Wc, col_slots;
+    int num_sms;        // the device's SMs (the persistent grid's size)
 };
 bool se2n_col_supported(int N, int H);
 cudaError_t se2n_col_prepare(int N, int H);
 cudaError_t se2n_launch_col_prop(int N, const ColArgs &a, cudaStream_t s);
+// 1 in *host_flag when a column pass gave up waiting for its copy-in (reset clears it)
+cudaError_t se2n_col_fault(int *host_flag, bool reset);
 
 // rowfft.cu: the row pass between column passes, one block a row y with all
 // its angles: the row-transformed volume [Wc][H][N] is taken back to the
