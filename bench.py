@@ -180,7 +180,7 @@ class ClockSampler:
 
 KERNEL_SOURCES = {"diffuse": ("diffuse_impl.cuh", "diffuse_x2.cuh", "diffuse.cu"),
                   "prop_build": ("propagator.cu", "prop_classes.cuh", "diffuse_x2.cuh", "diffuse_impl.cuh"),
-                  "col_prop": ("colprop.cu", "bulk_copy.cuh", "smem_fft.cuh", "prop_classes.cuh", "diffuse_x2.cuh"),
+                  "col_prop": ("colprop.cu", "bulk_copy.cuh", "rowdft.cuh", "smem_fft.cuh", "prop_classes.cuh", "diffuse_x2.cuh"),
                   "row_pass": ("rowfft.cu", "smem_fft.cuh", "restore.cuh")}
 TRAFFIC_FILES = {"diffuse": "diffuse_traffic.json", "prop_build": "prop_build_traffic.json",
                  "col_prop": "col_prop_traffic.json", "row_pass": "row_pass_traffic.json"}

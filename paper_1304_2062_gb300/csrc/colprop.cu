@@ -33,6 +33,7 @@
 #include "se2n_internal.h"
 #include "smem_fft.cuh"
 #include "bulk_copy.cuh"
+#include "rowdft.cuh"
 
 namespace se2n {
 
@@ -231,135 +232,12 @@ __global__ void __launch_bounds__(col_threads<H>(), H >= 768 ? 1 : 2) k_col_prop
 // the column in and one takes it back, and every access of the transforms
 // (a row of all the angles) is one contiguous run of shared memory.
 //
-// The transforms along k are in place: decimation in frequency forward (the
-// half-column spectrum ends in digit-reversed order, col_pos), decimation in
-// time inverse (back to natural order). Rows 0 .. L-1 of the column hold the
+// The transforms along k are in place (rowdft.cuh): decimation in frequency
+// forward (the half-column spectrum ends in digit-reversed order, rd_pos),
+// decimation in time inverse (back to natural order). Rows 0 .. L-1 of the column hold the
 // even half and rows L .. H-1 the odd half (L = H / 2); the radix-2 split is
 // folded into the reads of the first forward pass and the recombination into
 // the writes of the last inverse pass.
-
-// radices of the half-column DFT of length L, first pass first (R3 = 1: two
-// passes); the first radix is small so that the first pass has many butterflies
-template <int L>
-struct ColPlan {
-    static constexpr int R1 = L == 32 ? 4 : (L == 256 ? 16 : (L == 192 || L == 384 ? 3 : 8));
-    static constexpr int R2 = L == 32 || L == 64 || L == 192 || L == 384 || L == 512 ? 8 : 16;
-    static constexpr int R3 = L / (R1 * R2);
-    static_assert(R1 * R2 * R3 == L && (R3 == 1 || R3 == 8 || R3 == 16), "radix plan");
-};
-
-// row of the half-column holding frequency f after the forward passes:
-// f = f1 + R1 f2 + R1 R2 f3 sits at f1 L / R1 + f2 L / (R1 R2) + f3
-template <int L>
-__device__ __forceinline__ int col_pos(int f) {
-    using P = ColPlan<L>;
-    const int f1 = f % P::R1, q = f / P::R1;
-    const int f2 = q % P::R2, f3 = q / P::R2;
-    return f1 * (L / P::R1) + f2 * (L / (P::R1 * P::R2)) + f3;
-}
-
-enum { CP_PLAIN = 0, CP_SPLIT = 1, CP_MERGE = 2 };
-
-// One in-place radix-R pass over blocks of LS rows (S = LS / R): butterfly
-// (block c, j < S) of angle n on rows c LS + j + m S, m < R, of both halves
-// (CP_PLAIN), or of the two halves at once with the split u = x_k + x_{k+L},
-// v = (x_k - x_{k+L}) w^k (w = exp(-2 pi i / H)) folded into its reads
-// (CP_SPLIT, first forward pass) or the recombination x_k = y_k + w^-k z_k,
-// x_{k+L} = y_k - w^-k z_k into its writes (CP_MERGE, last inverse pass).
-// Forward (DIR = -1): the R-point DFT, output r times w_LS^{j r}, back to row
-// j + r S; inverse: input r times w_LS^{-j r}, the inverse R-point DFT,
-// output m back to row j + m S. w_LS^e = tws[e H / LS].
-template <int T, int N, int L, int R, int LS, int DIR, int MODE>
-__device__ __forceinline__ void col_pass(float2 *XA, float2 *XB, const float2 *tws, int tid) {
-    constexpr int S = LS / R, BLK = L / LS, TW = 2 * L / LS;
-    constexpr int BF = BLK * S;  // butterflies of one half and angle
-    constexpr int TASKS = (MODE == CP_PLAIN ? 2 : 1) * BF * N;
-    static_assert(T % N == 0, "one angle a thread");
-    const int n = tid % N;
-#pragma unroll
-    for (int task = tid; task < TASKS; task += T) {
-        const int u = task / N;
-        const int half = MODE == CP_PLAIN ? u / BF : 0;
-        const int rest = u - half * BF;
-        const int c = rest / S, j = rest - c * S;
-        float2 *Xa = (half ? XB : XA) + (c * LS + j) * N + n;  // row m of the butterfly: Xa[m S N]
-        float2 *Xb = XB + (c * LS + j) * N + n;                // the same row of the odd half
-        float2 p[R], q[MODE == CP_PLAIN ? 1 : R];
-        if constexpr (MODE == CP_SPLIT) {
-#pragma unroll
-            for (int m = 0; m < R; ++m) {
-                const float2 x0 = Xa[m * S * N], x1 = Xb[m * S * N];
-                p[m] = cadd(x0, x1);
-                q[m] = twiddle<-1>(csub(x0, x1), tws[j + m * S]);
-            }
-        } else {
-#pragma unroll
-            for (int m = 0; m < R; ++m) {
-                p[m] = Xa[m * S * N];
-                if constexpr (MODE == CP_MERGE) q[m] = Xb[m * S * N];
-            }
-        }
-        if constexpr (DIR > 0) {
-#pragma unroll
-            for (int r = 1; r < R; ++r) {
-                const float2 w = tws[j * r * TW];
-                p[r] = twiddle<1>(p[r], w);
-                if constexpr (MODE != CP_PLAIN) q[r] = twiddle<1>(q[r], w);
-            }
-        }
-        dft_small<R, DIR>(p);
-        if constexpr (MODE != CP_PLAIN) dft_small<R, DIR>(q);
-        if constexpr (DIR < 0) {
-#pragma unroll
-            for (int r = 1; r < R; ++r) {
-                const float2 w = tws[j * r * TW];
-                p[r] = twiddle<-1>(p[r], w);
-                if constexpr (MODE != CP_PLAIN) q[r] = twiddle<-1>(q[r], w);
-            }
-        }
-        if constexpr (MODE == CP_MERGE) {
-#pragma unroll
-            for (int m = 0; m < R; ++m) {
-                const float2 o = twiddle<1>(q[m], tws[j + m * S]);
-                Xa[m * S * N] = cadd(p[m], o);
-                Xb[m * S * N] = csub(p[m], o);
-            }
-        } else {
-#pragma unroll
-            for (int m = 0; m < R; ++m) {
-                Xa[m * S * N] = p[m];
-                if constexpr (MODE == CP_SPLIT) Xb[m * S * N] = q[m];
-            }
-        }
-    }
-}
-
-// forward: the split, then the DFTs of both halves (natural order in,
-// digit-reversed out); the caller synchronises before and after
-template <int T, int N, int L>
-__device__ __forceinline__ void col_forward(float2 *XA, float2 *XB, const float2 *tws, int tid) {
-    using P = ColPlan<L>;
-    col_pass<T, N, L, P::R1, L, -1, CP_SPLIT>(XA, XB, tws, tid);
-    __syncthreads();
-    col_pass<T, N, L, P::R2, L / P::R1, -1, CP_PLAIN>(XA, XB, tws, tid);
-    if constexpr (P::R3 > 1) {
-        __syncthreads();
-        col_pass<T, N, L, P::R3, P::R3, -1, CP_PLAIN>(XA, XB, tws, tid);
-    }
-}
-
-// inverse: the mirror of col_forward, ending in the recombination
-template <int T, int N, int L>
-__device__ __forceinline__ void col_inverse(float2 *XA, float2 *XB, const float2 *tws, int tid) {
-    using P = ColPlan<L>;
-    if constexpr (P::R3 > 1) {
-        col_pass<T, N, L, P::R3, P::R3, 1, CP_PLAIN>(XA, XB, tws, tid);
-        __syncthreads();
-    }
-    col_pass<T, N, L, P::R2, L / P::R1, 1, CP_PLAIN>(XA, XB, tws, tid);
-    __syncthreads();
-    col_pass<T, N, L, P::R1, L, 1, CP_MERGE>(XA, XB, tws, tid);
-}
 
 // x <- x + D_S x for every frequency of the column, classes s = 0 .. H/4
 // (the even half for even s, the odd half for odd s): one class per N/2
@@ -416,7 +294,7 @@ __device__ __forceinline__ void col_apply_rows(float2 *XA, float2 *XB, const flo
         float2 *Xh = (s & 1) ? XB : XA;
         int xo[4];
 #pragma unroll
-        for (int m = 0; m < 4; ++m) xo[m] = col_pos<L>(k[m] >> 1) * N;
+        for (int m = 0; m < 4; ++m) xo[m] = rd_pos<L>(k[m] >> 1) * N;
         // shared-memory addresses: normal rows read angle 2p + rot, reversed
         // rows angle (N - rot - 2p) mod N; where N = 32 each wraps at one step
         // for every class of a warp (12 and 13), so each row has one address
@@ -522,18 +400,10 @@ __device__ __forceinline__ void col_apply_rows(float2 *XA, float2 *XB, const flo
     }
 }
 
-// threads: enough for the first pass's butterflies (both halves at once), 128 .. 512
-template <int N, int H>
-__host__ __device__ constexpr int col_tma_threads() {
-    return (H / 2 / ColPlan<H / 2>::R1) * N >= 512   ? 512
-           : (H / 2 / ColPlan<H / 2>::R1) * N <= 128 ? 128
-                                                     : (H / 2 / ColPlan<H / 2>::R1) * N;
-}
-
 template <int N, int H>
 struct ColTmaCfg {
     static constexpr int L = H / 2;
-    static constexpr int T = col_tma_threads<N, H>();
+    static constexpr int T = rd_threads<N, H / 2>();  // the first pass takes both halves at once
     static constexpr int HB = L * N * 8;   // bytes of half a column
     static constexpr int TWB = H * 8 + 16;  // w^m (m < H) and a barrier a half
     static constexpr int SMEM = 2 * HB + TWB;
@@ -598,11 +468,11 @@ __global__ void __launch_bounds__(ColTmaCfg<N, H>::T, ColTmaCfg<N, H>::MINB)
             }
             return;
         }
-        col_forward<T, N, L>(XA, XB, tws, tid);
+        rd_dif<T, N, L, -1, RD_SPLIT, RD_TWO>(XA, XB, tws, tid);
         __syncthreads();
         col_apply_rows<T, N, H>(XA, XB, a.D, half_col_slot(l, a.W), a.col_slots, tid);
         __syncthreads();
-        col_inverse<T, N, L>(XA, XB, tws, tid);
+        rd_dit<T, N, L, 1, RD_TWO, RD_MERGE>(XA, XB, tws, tid);
         bulk::fence_to_async();
         __syncthreads();
         if (tid == 0) {
