@@ -9,7 +9,7 @@
  * Units. The diffusion is written in pixel units,
  *     dpsi_r/dt = -a_r^2 psi_r + beta (psi_{r+1} - 2 psi_r + psi_{r-1}),
  *     a_r = wx cos(th_r) + wy sin(th_r),  wx = sin(2 pi l/W), wy = sin(2 pi k/H),
- * for the DFT coefficient (k,l) of every angle plane. This is eq. (deceq)
+ * for the DFT coefficient (k,l) of every angle plane. This is eq. (4.2)
  * of the paper (Theorem 2) with unit mesh step; se2n_params_from_paper maps
  * the paper's (alpha, T) on an M x M image to (beta, T) here exactly.
  * Angles: th_r = pi r / N (directions, the paper's projectivised picture),
@@ -168,8 +168,8 @@ typedef struct se2n_params {
 SE2N_API se2n_status se2n_params_default(se2n_params *p);
 
 /* Map the paper's weighting alpha and time T_paper on an M x M image with N
- * angles to pixel units. eq. (relation): beta_N = alpha (N / 2 pi)^2;
- * eq. (FTE) has mesh step 1/sqrt(M) and a factor 1/2, hence
+ * angles to pixel units. eq. (2.14): beta_N = alpha (N / 2 pi)^2;
+ * eq. (4.1) has mesh step 1/sqrt(M) and a factor 1/2, hence
  * beta = beta_N / M and T = (M/2) T_paper. SE2N_EINVAL for null outputs,
  * M < 2, N < 3, alpha < 0 or T_paper < 0. */
 SE2N_API se2n_status se2n_params_from_paper(double alpha, double T_paper, int M, int N,
@@ -236,7 +236,7 @@ SE2N_API se2n_status se2n_forward(se2n_plan *plan, void *vol);
 /* Inverse 2-D DFT of every angle plane including 1/(H W), in place. */
 SE2N_API se2n_status se2n_inverse(se2n_plan *plan, void *vol);
 
-/* Crank-Nicolson integration of eq. (deceq) for every frequency of the
+/* Crank-Nicolson integration of eq. (4.2) for every frequency of the
  * transformed volume, in place: steps steps of dt = T/steps,
  *     (I - dt/2 A) psi_new = (I + dt/2 A) psi,  A = -diag(a_r^2) + beta L,
  * L the cyclic second difference (Section 4, remark after Theorem 2: CN, a

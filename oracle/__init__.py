@@ -12,7 +12,7 @@ diffusion and human vision: a semi-discrete new twist"):
                      gradient both taken in the FFT domain, each pixel lifted
                      to the closest discrete direction;
 * forward/inverse -- Theorem 2: 2-D DFT of every angle plane;
-* diffuse         -- eq. (deceq) integrated by Crank-Nicolson (Section 4,
+* diffuse         -- eq. (4.2) integrated by Crank-Nicolson (Section 4,
                      remark after Theorem 2), see se2n_oracle.c;
 * mix             -- static restoration (Section 5, "Static restoration"):
                      sigma = (eps h(0) + (1-eps) h(t_i)) / h(t_i) on the good set;
@@ -26,7 +26,7 @@ Canonical units. The operator is written in pixel units,
     dpsi_r/dt = (cos th_r Dx + sin th_r Dy)^2 psi_r + beta (psi_{r-1} - 2 psi_r + psi_{r+1}),
 with Dx, Dy the periodic central differences (psi[x+1]-psi[x-1])/2, so the
 DFT symbol of the first term is -a_r^2 with a_r = wx cos th_r + wy sin th_r,
-wx = sin(2 pi l/W), wy = sin(2 pi k/H). The paper's eq. (FTE) uses the mesh
+wx = sin(2 pi l/W), wy = sin(2 pi k/H). The paper's eq. (4.1) uses the mesh
 step 1/sqrt(M) and a factor 1/2; params_from_paper maps its (alpha, T) onto
 this form exactly.
 
@@ -145,7 +145,7 @@ def symbol(H: int, W: int, N: int, angle_conv: int = 0) -> np.ndarray:
 def params_from_paper(alpha: float, T_paper: float, M: int, N: int):
     """Map the paper's (alpha, T) on an M x M image to pixel units.
 
-    eq. (relation): alpha = beta_N (2 pi / N)^2. eq. (FTE) has mesh step
+    eq. (2.14): alpha = beta_N (2 pi / N)^2. eq. (4.1) has mesh step
     1/sqrt(M) and the factor 1/2, so in the paper's time t_p the system reads
     dpsi/dt_p = (M/2) [ -a^2 psi + (beta_N/M) L psi ]; with t = (M/2) t_p it is
     the pixel-unit form with beta = beta_N / M.
@@ -237,7 +237,7 @@ def inverse(vol_hat):
 
 
 def diffuse(vol_hat, beta, T, steps, angle_conv=0, freqs=None, nthreads=0):
-    """Crank-Nicolson integration of eq. (deceq) over time T in `steps`
+    """Crank-Nicolson integration of eq. (4.2) over time T in `steps`
     steps, for every frequency (or only the flat indices k*W+l in freqs;
     other frequencies are returned unchanged). Returns a new array."""
     v = np.array(vol_hat, dtype=np.complex128, order="C", copy=True)
@@ -477,7 +477,7 @@ def _central_diff(n, step=1.0):
 
 
 def dense_operator(H, W, N, beta, angle_conv=0):
-    """The fully discrete operator of eq. (FTE) in pixel units, assembled in
+    """The fully discrete operator of eq. (4.1) in pixel units, assembled in
     real space without any Fourier transform: block r is
     (cos th_r Dx + sin th_r Dy)^2 with periodic central differences, plus
     beta * (L kron I). Index order r*H*W + y*W + x. Size (N H W)^2."""
@@ -494,7 +494,7 @@ def dense_operator(H, W, N, beta, angle_conv=0):
 
 
 def dense_paper_operator(M, N, beta_N):
-    """The right-hand side (1/2) D of eq. (FTE) in the paper's own units on
+    """The right-hand side (1/2) D of eq. (4.1) in the paper's own units on
     an M x M grid: mesh step 1/sqrt(M), differences (sqrt(M)/2)(psi_{k+1} -
     psi_{k-1}), angular term beta_N (psi^{r-1} - 2 psi^r + psi^{r+1}),
     directions e_r = pi r / N."""

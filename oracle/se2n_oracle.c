@@ -3,7 +3,7 @@
  * method. TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the CPU
  * baseline of the benchmark call it; the CUDA library never does.
  *
- * What it computes (Section 4 of the paper, Theorem 2 and eq. (deceq)):
+ * What it computes (Section 4 of the paper, Theorem 2 and eq. (4.2)):
  * after the 2-D DFT of every angle plane, each frequency (k,l) carries an
  * independent N-vector psi that obeys dpsi/dt = A psi with
  *
@@ -11,7 +11,7 @@
  *     wx = sin(2 pi l / W),  wy = sin(2 pi k / H),
  *
  * L the N x N cyclic second difference (diagonal -2, off-diagonals and the two
- * corners +1). This is eq. (deceq) in pixel units: the exact rescaling of the
+ * corners +1). This is eq. (4.2) in pixel units: the exact rescaling of the
  * paper's time and beta_N is done by the Python side (params_from_paper).
  *
  * It is integrated by the Crank-Nicolson scheme the paper recommends

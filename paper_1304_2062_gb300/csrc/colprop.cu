@@ -7,7 +7,7 @@
 //      completes the two-dimensional DFT of the lifted volume;
 //   2. x <- x + D_S x for the N-vector of every frequency (k, l), D_S the
 //      S-step propagator of its class, stored by 16-byte chunks of its rows,
-//      chunk-major (eq. (deceq), Theorem 2, integrated by S Crank-Nicolson
+//      chunk-major (eq. (4.2), Theorem 2, integrated by S Crank-Nicolson
 //      steps; see propagator.cu), with the angles reversed for rows H/2 + s
 //      and H - s;
 //   3. the inverse DFT along k,

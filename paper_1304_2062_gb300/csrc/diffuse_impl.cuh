@@ -1,5 +1,5 @@
 // Fused Crank-Nicolson diffusion of the decoupled Mathieu-type systems
-// (eq. (deceq), Theorem 2; Crank-Nicolson as recommended in Section 4).
+// (eq. (4.2), Theorem 2; Crank-Nicolson as recommended in Section 4).
 //
 // Every DFT coefficient (k,l) of the lifted volume carries an N-vector psi
 // with dpsi/dt = A psi, A = -diag(a_r^2) + beta L (L: cyclic second

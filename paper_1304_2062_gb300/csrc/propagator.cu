@@ -1,4 +1,4 @@
-// The S-step propagator of the Crank-Nicolson integration of eq. (deceq).
+// The S-step propagator of the Crank-Nicolson integration of eq. (4.2).
 //
 // Every interval of se2n_inpaint integrates T/rounds in S steps with the same
 // beta, so for one frequency the S steps are one fixed linear map: the

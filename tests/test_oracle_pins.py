@@ -62,7 +62,7 @@ def test_forward_inverse_roundtrip(oracle_mod):
 
 @pytest.mark.parametrize("H,W,N,conv", [(4, 6, 4, 0), (6, 4, 8, 0), (8, 8, 4, 1), (4, 4, 8, 1), (6, 6, 3, 0)])
 def test_fourier_cn_equals_dense_real_space_cn(oracle_mod, H, W, N, conv):
-    """One Crank-Nicolson integration of eq. (FTE) assembled densely in real
+    """One Crank-Nicolson integration of eq. (4.1) assembled densely in real
     space (no Fourier transform anywhere) equals FFT -> per-frequency CN ->
     iFFT (Theorem 2 states the decoupling is exact)."""
     beta, T, S = 0.7, 0.9, 5
@@ -83,7 +83,7 @@ def test_dense_operator_is_symmetric_generator(oracle_mod):
 
 
 def test_cn_is_second_order_towards_matrix_exponential(oracle_mod):
-    """CN converges to e^{T A} (eq. (soleq)) as O(dt^2): halving dt divides
+    """CN converges to e^{T A} (eq. (4.3)) as O(dt^2): halving dt divides
     the error by ~4. The exact propagator is taken from an eigendecomposition
     of the dense real-space operator."""
     H, W, N, beta, T = 6, 6, 4, 0.5, 1.0
@@ -177,12 +177,12 @@ def test_frequency_subset_leaves_others_untouched(oracle_mod):
 
 
 # --------------------------------------------------------------------------
-# the paper's units (eq. (FTE), eq. (relation))
+# the paper's units (eq. (4.1), eq. (2.14))
 # --------------------------------------------------------------------------
 
 @pytest.mark.parametrize("M,N", [(4, 4), (6, 8)])
 def test_paper_units_map_exactly(oracle_mod, M, N):
-    """(1/2) D of eq. (FTE) (mesh 1/sqrt(M), beta_N) equals (M/2) times the
+    """(1/2) D of eq. (4.1) (mesh 1/sqrt(M), beta_N) equals (M/2) times the
     pixel-unit operator with beta = beta_N / M, so e^{t_p (1/2) D} is the
     pixel-unit propagator at T = (M/2) t_p; and alpha = beta_N (2 pi/N)^2."""
     alpha, Tp = 0.33, 0.07
@@ -281,7 +281,7 @@ def test_rotation_by_90_degrees_shifts_channels(oracle_mod, N):
     """Rotating the image by 90 degrees (an exact pixel permutation on the
     periodic grid) rotates the lifted, diffused and restored volume and
     shifts its channels by N/2 (th_r = pi r/N): the discrete form of the
-    rotation theorem of Section 3 and of eq. (Xc)."""
+    rotation theorem of Section 3 and of eq. (B.3)."""
     f, mask = _equivariance_inputs()
     _no_ties(oracle_mod, f, mask, N)
     p = oracle_mod.Params(N=N, beta=0.5, T=1.0, steps=8, rounds=2)
@@ -309,7 +309,7 @@ def test_flips_map_channels(oracle_mod):
 
 
 def test_shift_identity_of_the_appendix(oracle_mod):
-    """eq. (Xc): the system at the frequency rotated by 90 degrees is the
+    """eq. (B.3): the system at the frequency rotated by 90 degrees is the
     original one conjugated by the channel shift S^{N/2}; so diffusing
     S^{N/2} v at the rotated frequency gives S^{N/2} of the original result."""
     M, N = 12, 8
