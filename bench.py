@@ -90,14 +90,16 @@ def cpu_model():
 
 GOLDEN_DYNAMIC = os.path.join(ROOT, "tests", "golden", "curves_noise_512_N32_dynamic.npz")
 GOLDEN_GUARD0 = os.path.join(ROOT, "tests", "golden", "curves_noise_512_N32_guard0.npz")
+GOLDEN_N30 = os.path.join(ROOT, "tests", "golden", "curves_noise_512_N30.npz")
+SENSITIVITY_N30 = os.path.join(ROOT, "tests", "golden", "sensitivity_512_N30.json")
 SENSITIVITY = os.path.join(ROOT, "tests", "golden", "sensitivity_512_N32.json")
 
 
-def fp32_sensitivity():
+def fp32_sensitivity(path=SENSITIVITY):
     """The FP64 oracle's sensitivity to FP32 rounding on the 512x512 workload
     (written by tests/golden/make_sensitivity.py), or None."""
     try:
-        s = json.load(open(SENSITIVITY))
+        s = json.load(open(path))
     except (OSError, ValueError):
         return None
     out = {k: s[k]["max_abs_over_max_f"] for k in ("storage_full", "perturb_full", "fp32_full", "fp32_half")}
@@ -566,12 +568,65 @@ def run_ours(args, rank, world, local_rank):
                 "max_abs_over_max_f": float(np.abs(got0 - ref0).max() / np.abs(w.f).max()),
                 "rule": "sigma at every good pixel with h(t_i) > 0 (guard 0), against the oracle's guard-0 result"}
 
+    if rank == 0 and prop and not dynamic:
+        result["paper_angle_count"] = paper_angle_count(w, dev, stream, flush)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(w, dynamic=dynamic)
     plan.close()
     if dist:
         dist.destroy_process_group()
     return result
+
+
+def paper_angle_count(w, dev, stream, flush):
+    """The same 512x512 inpaint with the paper's N = 30 angles (propagators
+    built every inpaint, the row and column passes with the 30 angles in 32
+    slots): ms per inpaint over 5 flushed runs and the error against the
+    FP64 oracle's stored N = 30 result."""
+    from paper_1304_2062_gb300 import se2n
+    w30 = synth.workload_512(N=30)
+    f32 = w30.f.astype(np.float32)
+    plan = se2n.se2n_plan_create(w30.H, w30.W, 30, 0, stream)
+    f_d = torch.tensor(f32, device=dev)
+    m_d = torch.tensor(w30.mask, device=dev)
+    vol = torch.empty((30, w30.H, w30.W), dtype=torch.complex64, device=dev)
+    out = torch.empty((w30.H, w30.W), dtype=torch.float32, device=dev)
+    prm = se2n.se2n_params_default(N=30, beta=w30.beta, T=w30.T, steps=w30.steps, rounds=w30.rounds, eps=w30.eps,
+                                   sigma_smooth=w30.sigma, diffuse_flags=se2n.SE2N_DIFFUSE_PROPAGATOR)
+    res = {"N": 30, "workload": "the same image, mask and parameters with N = 30"}
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            se2n.se2n_plan_drop_propagators(plan)
+            se2n.se2n_inpaint(plan, f_d, m_d, None, prm, vol, out)
+        ms = []
+        for _ in range(5):
+            flush.zero_()
+            se2n.se2n_plan_drop_propagators(plan)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            se2n.se2n_inpaint(plan, f_d, m_d, None, prm, vol, out)
+            b.record(stream)
+            ms.append((a, b))
+        torch.cuda.synchronize(dev)
+    res["ms_per_inpaint"] = round(sum(a.elapsed_time(b) for a, b in ms) / len(ms), 4)
+    res["timing"] = "CUDA events, L2 flushed and the propagators rebuilt before each of 5 inpaints"
+    if os.path.exists(GOLDEN_N30):
+        g = np.load(GOLDEN_N30)
+        with torch.cuda.stream(stream):
+            se2n.se2n_inpaint(plan, f_d, m_d, torch.tensor(g["bins"], device=dev), prm, vol, out)
+        torch.cuda.synchronize(dev)
+        got = out.cpu().numpy().astype(np.float64)
+        ref = g["out"].astype(np.float64)
+        err = {"rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+               "max_abs_over_max_f": float(np.abs(got - ref).max() / np.abs(w30.f).max())}
+        sens = fp32_sensitivity(SENSITIVITY_N30)
+        if sens:
+            err["bound"] = {"max_abs_over_max_f": 4.0 * sens["s32"],
+                            "basis": "4 x S32 of tests/golden/sensitivity_512_N30.json",
+                            "within": err["max_abs_over_max_f"] <= 4.0 * sens["s32"]}
+        res["err_vs_fp64"] = err
+    plan.close()
+    return res
 
 
 # ----------------------------------------------------------------------------

@@ -87,7 +87,7 @@ typedef enum se2n_status {
  * 30, 32 or 64 (else SE2N_EUNSUPPORTED); N = 30 is built and stored as
  * 32 x 32 matrices whose last two rows and columns are zero (the bytes of
  * N = 32). The other flags do not apply.
- * In se2n_inpaint on the Hermitian half with N = 16 or 32 and H, W each one
+ * In se2n_inpaint on the Hermitian half with N = 16, 30 or 32 and H, W each one
  * of 64, 128, 256, 384, 512, 768, 1024, this flag alone selects the row and column passes: the
  * volume stays row-transformed between intervals in a plan buffer of
  * 8 (W/2 + 1) H N bytes, each interval is one kernel a column (DFT along y,

@@ -273,7 +273,9 @@ se2n_status upload_twiddles(float2 **dst, int n) {
 se2n_status col_ensure(se2n_plan *plan) {
     if (plan->col_ready) return SE2N_OK;
     if (!plan->colbuf) {
-        cudaError_t e = cudaMalloc(&plan->colbuf, (size_t)plan->Wc * plan->N * plan->H * sizeof(float2));
+        // N = 30 is held in 32 slots
+        cudaError_t e =
+            cudaMalloc(&plan->colbuf, (size_t)plan->Wc * se2n_prop_dim(plan->N) * plan->H * sizeof(float2));
         if (e != cudaSuccess) {
             plan->colbuf = nullptr;
             (void)cudaGetLastError();

@@ -541,8 +541,9 @@ cudaError_t col_dispatch(int H, const ColArgs *a, cudaStream_t s) {
 
 }  // namespace se2n
 
+// N = 30: the 30-angle system in 32 slots (its propagators stored by slots)
 bool se2n_col_supported(int N, int H) {
-    return (N == 16 || N == 32) &&
+    return (N == 16 || N == 30 || N == 32) &&
            (H == 64 || H == 128 || H == 256 || H == 512 || H == 1024 || H == 384 || H == 768);
 }
 

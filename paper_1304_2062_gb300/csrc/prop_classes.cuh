@@ -36,6 +36,28 @@ __host__ __device__ __forceinline__ void slot_rows(int s, int H, int (&k)[4], bo
     on[3] = s != 0 && !quarter;
 }
 
+// The slots of a system of NE = N - 2 angles (30 in 32) in the row and
+// column passes, whose kernels are written for N: angle r < NE/2 at slot r,
+// NE/2 at slot N/2, r > NE/2 at slot r + 2; slots NE/2 and N/2 + 1 stay empty
+// (zero in every plane and in every propagator's rows and columns). Angle
+// reversal modulo NE is then slot reversal modulo N, which the column pass
+// does. angle_of_slot gives NE, NE + 1 for the two empty slots; NE = N is the
+// identity.
+template <int N, int NE>
+__host__ __device__ constexpr int slot_of_angle(int r) {
+    return NE == N ? r : (r < NE / 2 ? r : (r == NE / 2 ? N / 2 : r + 2));
+}
+template <int N, int NE>
+__host__ __device__ constexpr int angle_of_slot(int s) {
+    return NE == N ? s
+                   : (s < NE / 2 ? s
+                                 : (s == NE / 2 ? NE : (s == N / 2 ? NE / 2 : (s == N / 2 + 1 ? NE + 1 : s - 2))));
+}
+static_assert(angle_of_slot<32, 30>(slot_of_angle<32, 30>(15)) == 15 &&
+                  angle_of_slot<32, 30>(slot_of_angle<32, 30>(29)) == 29 && slot_of_angle<32, 30>(29) == 31 &&
+                  (32 - slot_of_angle<32, 30>(1)) % 32 == slot_of_angle<32, 30>(29),
+              "the slots of 30 angles in 32");
+
 // Column slot of column l of the Hermitian half (l in [0, W/2]): columns l
 // and W/2 - l share slot min(l, W/2 - l) in [0, W/4].
 __host__ __device__ __forceinline__ int half_col_slot(int l, int W) { return l <= W / 4 ? l : W / 2 - l; }

@@ -277,17 +277,19 @@ __device__ __forceinline__ void prop_store(const PropArgs &a, const float *Rm, l
     using C = SymCfg<N>;
     if (!live || u < 0) return;
     if (a.rows) {
+        // for the column pass: row i, columns 4c .. 4c + 3 as slots (an
+        // NE-angle system at the slots of slot_of_angle)
         float4 *out = reinterpret_cast<float4 *>(a.D + u * (long long)(N * N));
         for (int e = t; e < N * N / 4; e += lanes) {
             const int c = e / N, i = e - c * N;
-            if (shift < 0) {
+            if (shift < 0 && NE == N) {
                 out[e] = *reinterpret_cast<const float4 *>(Rm + C::at(i, 4 * c));
             } else {
-                const int pi = perm_index<N, NE>(i, shift);
-                out[e] = make_float4(Rm[C::at(pi, perm_index<N, NE>(4 * c, shift))],
-                                     Rm[C::at(pi, perm_index<N, NE>(4 * c + 1, shift))],
-                                     Rm[C::at(pi, perm_index<N, NE>(4 * c + 2, shift))],
-                                     Rm[C::at(pi, perm_index<N, NE>(4 * c + 3, shift))]);
+                const int pi = perm_index<N, NE>(angle_of_slot<N, NE>(i), shift);
+                out[e] = make_float4(Rm[C::at(pi, perm_index<N, NE>(angle_of_slot<N, NE>(4 * c), shift))],
+                                     Rm[C::at(pi, perm_index<N, NE>(angle_of_slot<N, NE>(4 * c + 1), shift))],
+                                     Rm[C::at(pi, perm_index<N, NE>(angle_of_slot<N, NE>(4 * c + 2), shift))],
+                                     Rm[C::at(pi, perm_index<N, NE>(angle_of_slot<N, NE>(4 * c + 3), shift))]);
             }
         }
     } else {

@@ -23,6 +23,7 @@
 // imaginary parts of X_0 and X_{W/2} ignored): Z_l = P + i Q and
 // Z_{W/2-l} = conj P + i conj Q with P = X_l + conj X_{W/2-l} and
 // Q = conj(w^l) (X_l - conj X_{W/2-l}), then z = inverse DFT of Z.
+#include "prop_classes.cuh"
 #include "restore.cuh"
 #include "se2n_internal.h"
 #include "smem_fft.cuh"
@@ -43,7 +44,9 @@ struct RowCfg {
     static constexpr int SMEM = (XF + W + FftTw<WH>::SIZE) * 8;
 };
 
-template <int N, int W>
+// NE < N: an NE-angle system at the slots of slot_of_angle (prop_classes.cuh);
+// the empty slots take no part in the maxima, means and argmaxima and stay zero
+template <int N, int W, int NE = N>
 __global__ void __launch_bounds__(row_threads<W>()) k_row(const __grid_constant__ RowArgs a) {
     constexpr int WH = W / 2, T = row_threads<W>();
     extern __shared__ __align__(16) float2 rsm[];
@@ -65,8 +68,9 @@ __global__ void __launch_bounds__(row_threads<W>()) k_row(const __grid_constant_
             float2 *Zm = Z + xoff<WH>(m);
 #pragma unroll 8
             for (int n = 0; n < N; ++n) {
-                const bool on0 = (bn.x == n) || (bn.x == SE2N_BIN_FLAT);
-                const bool on1 = (bn.y == n) || (bn.y == SE2N_BIN_FLAT);
+                const int an = angle_of_slot<N, NE>(n);
+                const bool on0 = an < NE && ((bn.x == an) || (bn.x == SE2N_BIN_FLAT));
+                const bool on1 = an < NE && ((bn.y == an) || (bn.y == SE2N_BIN_FLAT));
                 Zm[n * (WH + 1)] = make_float2(on0 ? a0 : 0.0f, on1 ? a1 : 0.0f);
             }
         }
@@ -118,6 +122,7 @@ __global__ void __launch_bounds__(row_threads<W>()) k_row(const __grid_constant_
             float ht0 = -INFINITY, ht1 = -INFINITY;
 #pragma unroll 8
             for (int n = 0; n < N; ++n) {
+                if (angle_of_slot<N, NE>(n) >= NE) continue;
                 const float2 v = Zm[n * (WH + 1)];
                 ht0 = fmaxf(ht0, v.x * a.scale);
                 ht1 = fmaxf(ht1, v.y * a.scale);
@@ -131,8 +136,9 @@ __global__ void __launch_bounds__(row_threads<W>()) k_row(const __grid_constant_
 #pragma unroll 8
             for (int n = 0; n < N; ++n) {
                 float2 &v = Zm[n * (WH + 1)];
-                const float l0 = ((bn.x == n) || (bn.x == SE2N_BIN_FLAT)) ? a0 : 0.0f;
-                const float l1 = ((bn.y == n) || (bn.y == SE2N_BIN_FLAT)) ? a1 : 0.0f;
+                const int an = angle_of_slot<N, NE>(n);
+                const float l0 = an < NE && ((bn.x == an) || (bn.x == SE2N_BIN_FLAT)) ? a0 : 0.0f;
+                const float l1 = an < NE && ((bn.y == an) || (bn.y == SE2N_BIN_FLAT)) ? a1 : 0.0f;
                 v = make_float2(sr_value(v.x * a.scale, h00, ht0, l0, mk.x != 0, a.eps, a.guard),
                                 sr_value(v.y * a.scale, h01, ht1, l1, mk.y != 0, a.eps, a.guard));
             }
@@ -154,6 +160,7 @@ __global__ void __launch_bounds__(row_threads<W>()) k_row(const __grid_constant_
                 a1 = -INFINITY;
 #pragma unroll 8
                 for (int n = 0; n < N; ++n) {
+                    if (angle_of_slot<N, NE>(n) >= NE) continue;
                     const float2 v = Zm[n * (WH + 1)];
                     a0 = fmaxf(a0, v.x * a.scale_proj);
                     a1 = fmaxf(a1, v.y * a.scale_proj);
@@ -167,8 +174,8 @@ __global__ void __launch_bounds__(row_threads<W>()) k_row(const __grid_constant_
                     a0 += v.x * a.scale_proj;
                     a1 += v.y * a.scale_proj;
                 }
-                a0 /= (float)N;
-                a1 /= (float)N;
+                a0 /= (float)NE;  // the empty slots add zero
+                a1 /= (float)NE;
             }
             if (a.reinject) {
                 const float2 fv = reinterpret_cast<const float2 *>((a.rf ? a.rf : a.f) + row)[m];
@@ -185,15 +192,18 @@ __global__ void __launch_bounds__(row_threads<W>()) k_row(const __grid_constant_
             int r0 = 0, r1 = 0;
 #pragma unroll 8
             for (int n = 0; n < N; ++n) {
+                const int an = angle_of_slot<N, NE>(n);
+                if (an >= NE) continue;
                 const float2 v = Zm[n * (WH + 1)];
                 const float v0 = v.x * a.scale, v1 = v.y * a.scale;
+                // the slots run in angle order: the first maximum is the first angle
                 if (v0 > b0) {
                     b0 = v0;
-                    r0 = n;
+                    r0 = an;
                 }
                 if (v1 > b1) {
                     b1 = v1;
-                    r1 = n;
+                    r1 = an;
                 }
             }
             reinterpret_cast<float2 *>(a.h_out + row)[m] = make_float2(b0, b1);
@@ -222,29 +232,31 @@ __global__ void __launch_bounds__(row_threads<W>()) k_row(const __grid_constant_
     }
 }
 
-template <int N, int W>
+template <int N, int W, int NE>
 cudaError_t row_attr() {
-    return cudaFuncSetAttribute(k_row<N, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowCfg<N, W>::SMEM);
+    return cudaFuncSetAttribute(k_row<N, W, NE>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowCfg<N, W>::SMEM);
 }
 
-template <int N, int W>
+template <int N, int W, int NE>
 cudaError_t row_launch(const RowArgs &a, cudaStream_t s) {
-    cudaError_t e = row_attr<N, W>();
+    // the real volume has NE planes, not N slots
+    if (NE != N && (a.in_mode == SE2N_ROW_IN_REAL || a.out_mode == SE2N_ROW_OUT_REAL)) return cudaErrorInvalidValue;
+    cudaError_t e = row_attr<N, W, NE>();
     if (e != cudaSuccess) return e;
-    k_row<N, W><<<a.H, row_threads<W>(), RowCfg<N, W>::SMEM, s>>>(a);
+    k_row<N, W, NE><<<a.H, row_threads<W>(), RowCfg<N, W>::SMEM, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int N>
+template <int N, int NE = N>
 cudaError_t row_dispatch(int W, const RowArgs *a, cudaStream_t s) {
     switch (W) {
-        case 64: return a ? row_launch<N, 64>(*a, s) : row_attr<N, 64>();
-        case 128: return a ? row_launch<N, 128>(*a, s) : row_attr<N, 128>();
-        case 256: return a ? row_launch<N, 256>(*a, s) : row_attr<N, 256>();
-        case 512: return a ? row_launch<N, 512>(*a, s) : row_attr<N, 512>();
-        case 1024: return a ? row_launch<N, 1024>(*a, s) : row_attr<N, 1024>();
-        case 384: return a ? row_launch<N, 384>(*a, s) : row_attr<N, 384>();
-        case 768: return a ? row_launch<N, 768>(*a, s) : row_attr<N, 768>();
+        case 64: return a ? row_launch<N, 64, NE>(*a, s) : row_attr<N, 64, NE>();
+        case 128: return a ? row_launch<N, 128, NE>(*a, s) : row_attr<N, 128, NE>();
+        case 256: return a ? row_launch<N, 256, NE>(*a, s) : row_attr<N, 256, NE>();
+        case 512: return a ? row_launch<N, 512, NE>(*a, s) : row_attr<N, 512, NE>();
+        case 1024: return a ? row_launch<N, 1024, NE>(*a, s) : row_attr<N, 1024, NE>();
+        case 384: return a ? row_launch<N, 384, NE>(*a, s) : row_attr<N, 384, NE>();
+        case 768: return a ? row_launch<N, 768, NE>(*a, s) : row_attr<N, 768, NE>();
         default: return cudaErrorInvalidValue;
     }
 }
@@ -253,17 +265,22 @@ cudaError_t row_dispatch(int W, const RowArgs *a, cudaStream_t s) {
 
 }  // namespace se2n
 
+// N = 30: the 30-angle system in 32 slots
 bool se2n_row_supported(int N, int W) {
-    return (N == 16 || N == 32) &&
+    return (N == 16 || N == 30 || N == 32) &&
            (W == 64 || W == 128 || W == 256 || W == 512 || W == 1024 || W == 384 || W == 768);
 }
 
 cudaError_t se2n_row_prepare(int N, int W) {
     if (!se2n_row_supported(N, W)) return cudaErrorInvalidValue;
-    return N == 16 ? se2n::row_dispatch<16>(W, nullptr, nullptr) : se2n::row_dispatch<32>(W, nullptr, nullptr);
+    return N == 16   ? se2n::row_dispatch<16>(W, nullptr, nullptr)
+           : N == 30 ? se2n::row_dispatch<32, 30>(W, nullptr, nullptr)
+                     : se2n::row_dispatch<32>(W, nullptr, nullptr);
 }
 
 cudaError_t se2n_launch_row(int N, int W, const RowArgs &a, cudaStream_t s) {
     if (!se2n_row_supported(N, W)) return cudaErrorInvalidValue;
-    return N == 16 ? se2n::row_dispatch<16>(W, &a, s) : se2n::row_dispatch<32>(W, &a, s);
+    return N == 16 ? se2n::row_dispatch<16>(W, &a, s)
+           : N == 30 ? se2n::row_dispatch<32, 30>(W, &a, s)
+                     : se2n::row_dispatch<32>(W, &a, s);
 }

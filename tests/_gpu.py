@@ -19,6 +19,8 @@ size meets them (the measured errors are 1e-7 .. 2e-6, see the test output).
     that an exact FP32 transform already misses 1e-5 by little. The GPU
     also rounds the diffusion and the restoration in FP32 (each adding
     per-interval error of the order of one transform), hence the factor 4.
+    The same derivation with N = 30 (the paper's angle count) reads
+    sensitivity_512_N30.json.
   * TIE_TOL_512 = 2 x MAX_REL_512: a dynamic-restoration decision compares
     two such values, so one within this distance of a tie may go either way.
 """
@@ -31,12 +33,13 @@ import torch
 REL_L2 = 1e-5
 MAX_REL = 1e-5
 
-_SENS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "sensitivity_512_N32.json")
+_GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
-def fp32_sensitivity_512():
-    """S32 of the 512x512 workload from the stored FP64-oracle sensitivity run."""
-    with open(_SENS) as fh:
+def fp32_sensitivity_512(N=32):
+    """S32 of the 512x512 workload with N angles from the stored FP64-oracle
+    sensitivity run (sensitivity_512_N{N}.json)."""
+    with open(os.path.join(_GOLDEN, f"sensitivity_512_N{N}.json")) as fh:
         s = json.load(fh)
     return max(s["fp32_half"]["max_abs_over_max_f"], s["fp32_full"]["max_abs_over_max_f"])
 

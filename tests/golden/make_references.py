@@ -10,9 +10,10 @@ Calls only oracle/ and synth/. The orientation bins are the oracle's own
 image is the oracle's projected output, rounded to float32 (its 6e-8
 relative resolution is far below the 1e-5 comparison tolerance).
 Also writes curves_noise_512_N32_guard0.npz: the static restoration with no
-relative guard (Section 5's rule as printed). Takes about 3 minutes on 8
-cores per file; `python make_references.py dynamic` (or static, guard0)
-writes only that one.
+relative guard (Section 5's rule as printed), and curves_noise_512_N30.npz:
+the static workload with the paper's angle count N = 30. Takes about 3
+minutes on 8 cores per file; `python make_references.py dynamic` (or
+static, guard0, n30) writes only that one.
 """
 import json
 import os
@@ -30,6 +31,7 @@ import synth  # noqa: E402
 OUT = os.path.join(HERE, "curves_noise_512_N32.npz")
 OUT_DYNAMIC = os.path.join(HERE, "curves_noise_512_N32_dynamic.npz")
 OUT_GUARD0 = os.path.join(HERE, "curves_noise_512_N32_guard0.npz")
+OUT_N30 = os.path.join(HERE, "curves_noise_512_N30.npz")
 SENSITIVITY = os.path.join(HERE, "sensitivity_512_N32.json")
 
 
@@ -50,8 +52,8 @@ def tie_tol():
 TIE_TOL = tie_tol()
 
 
-def write(path, dynamic):
-    w = synth.workload_512()
+def write(path, dynamic, N=32):
+    w = synth.workload_512(N=N)
     f = w.f.astype(np.float32).astype(np.float64)
     p = oracle.Params(N=w.N, beta=w.beta, T=w.T, steps=w.steps, rounds=w.rounds, eps=w.eps, dynamic=dynamic)
     bins = oracle.orient(f, w.mask, p.N)["bins"]
@@ -85,13 +87,15 @@ def write_guard0(path):
 
 
 def main():
-    which = sys.argv[1:] or ["static", "dynamic", "guard0"]
+    which = sys.argv[1:] or ["static", "dynamic", "guard0", "n30"]
     if "static" in which:
         write(OUT, 0)
     if "dynamic" in which:
         write(OUT_DYNAMIC, 1)
     if "guard0" in which:
         write_guard0(OUT_GUARD0)
+    if "n30" in which:
+        write(OUT_N30, 0, N=30)
 
 
 if __name__ == "__main__":

@@ -18,7 +18,8 @@ import pytest
 
 import oracle
 import synth
-from _gpu import MAX_REL, MAX_REL_512, REL_L2, host, max_rel_for_sigma, rel_l2, restoration_sigma_max, t_c64, t_f32, t_u8
+from _gpu import (MAX_REL, MAX_REL_512, REL_L2, fp32_sensitivity_512, host, max_rel_for_sigma, rel_l2,
+                  restoration_sigma_max, t_c64, t_f32, t_u8)
 
 pytestmark = pytest.mark.gpu
 
@@ -114,7 +115,7 @@ def test_transposed_classes_share_one_build(N, H, conv):
     assert err <= REL_L2
 
 
-@pytest.mark.parametrize("N,conv", [(32, 1), (16, 1), (32, 0)])
+@pytest.mark.parametrize("N,conv", [(32, 1), (16, 1), (32, 0), (30, 0), (30, 1)])
 def test_square_inpaint_on_the_passes_with_either_angle_grid(N, conv):
     """The row and column passes on a square plane (transposed classes share
     one build, the matrices stored as rows) with both angle grids."""
@@ -237,14 +238,40 @@ def test_full_512_N32_ten_rounds_against_stored_oracle():
     assert r2 <= REL_L2
 
 
+def test_full_512_paper_angle_count_N30_against_stored_oracle():
+    """The 512x512 workload with the paper's N = 30 on the row and column
+    passes (the 30-angle system in 32 slots), against the FP64 oracle's
+    stored result; the bound is derived as for N = 32, from the oracle's own
+    sensitivity to FP32 rounding at N = 30."""
+    path = os.path.join(os.path.dirname(GOLDEN), "curves_noise_512_N30.npz")
+    if not os.path.exists(path):
+        pytest.fail("missing tests/golden/curves_noise_512_N30.npz: run tests/golden/make_references.py n30")
+    g = np.load(path)
+    w = synth.workload_512(N=30)
+    p = oracle.Params(N=30, beta=0.25, T=20.0, steps=500, rounds=10)
+    got, prof = _gpu_inpaint(w.f.astype(np.float32), w.mask, g["bins"], _params(p), profile=True)
+    ref = g["out"].astype(np.float64)
+    bound = 4.0 * fp32_sensitivity_512(30)
+    mx = np.abs(got - ref).max() / np.abs(w.f).max()
+    r2 = rel_l2(got, ref)
+    print(f"512x512 N=30 propagators: max-abs/max|f| {mx:.2e}, rel-L2 {r2:.2e} (bound {bound:.2e})")
+    assert prof["propagator"][1] == 1 and prof["diffuse"][1] == 10 and prof["fft"][1] == 11
+    assert mx <= bound
+    assert r2 <= REL_L2
+
+
 @pytest.mark.parametrize("H,W,N,dynamic,final_mix,proj,reinject", [
     (64, 128, 32, 0, 0, 0, 0), (128, 64, 16, 0, 1, 0, 0), (256, 64, 32, 0, 0, 1, 1), (64, 64, 16, 1, 0, 0, 0),
     (128, 128, 32, 1, 1, 0, 1), (512, 256, 16, 0, 1, 1, 0), (1024, 128, 32, 0, 0, 0, 0),
     (128, 1024, 16, 0, 0, 0, 1), (1024, 64, 32, 1, 0, 0, 0), (384, 256, 32, 0, 0, 0, 0), (256, 768, 16, 0, 1, 1, 0),
-    (768, 64, 32, 1, 0, 0, 1), (384, 384, 32, 0, 0, 0, 0)])
+    (768, 64, 32, 1, 0, 0, 1), (384, 384, 32, 0, 0, 0, 0),
+    (64, 128, 30, 0, 0, 0, 0), (128, 128, 30, 1, 1, 0, 1), (256, 64, 30, 0, 0, 1, 1), (384, 128, 30, 0, 1, 0, 0)])
 def test_row_and_column_passes_match_oracle(H, W, N, dynamic, final_mix, proj, reinject):
     """Plane sizes with H and W in {64, 128, 256, 384, 512, 768, 1024} and N =
-    16 or 32 run the fused passes: a row pass (lift, or inverse DFT along x,
+    16, 30 or 32 run the fused passes (N = 30, the paper's angle count, as a
+    30-angle system in 32 slots: angle r at slot r below 15, 15 at slot 16,
+    the others two slots up, so that angle reversal modulo 30 is slot reversal
+    modulo 32 and slots 15 and 17 stay empty): a row pass (lift, or inverse DFT along x,
     restoration and forward DFT along x, or projection) and a column pass
     (DFT along y, propagators, inverse DFT along y) an interval. Cases cover
     every radix mix of both lengths (8 x 4 .. 16 x 16, 8 x 8 x 8 and the
