@@ -583,6 +583,8 @@ def paper_angle_count(w, dev, stream, flush):
     built every inpaint, the row and column passes with the 30 angles in 32
     slots): ms per inpaint over 5 flushed runs and the error against the
     FP64 oracle's stored N = 30 result."""
+    import torch
+
     from paper_1304_2062_gb300 import se2n
     w30 = synth.workload_512(N=30)
     f32 = w30.f.astype(np.float32)
