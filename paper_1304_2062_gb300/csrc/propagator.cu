@@ -53,24 +53,6 @@ namespace se2n {
 
 namespace {
 
-// Build kernel: a lane owns a TR x TC tile of every product (4 x 4 at N = 16,
-// 8 x 8 at N = 32, 16 x 8 at N = 64: 16, 16 and 32 lanes a class) and, in the
-// column-wise steps, N / LPC columns.
-template <int N>
-struct PropCfg {
-    static constexpr int WARPS = N == 64 ? 2 : 4;  // warps a block
-    static constexpr int LPC = N == 64 ? 32 : 16;  // lanes a class
-    static constexpr int CPW = 32 / LPC;           // classes a warp
-    static constexpr int CPL = N / LPC;            // columns a lane in the column-wise steps
-    static constexpr int LD = N + 4;               // column (or row) stride in shared memory, floats
-    static constexpr int MAT = N * LD;             // floats a matrix
-    // P column- and row-major and R (products are formed in place); pivots, q, scalars
-    static constexpr int CLASS_FLOATS = 3 * MAT + 2 * N + 4;
-    static constexpr int SBLK = (N / 2 + 1) * N;   // stored floats a class
-    static constexpr int SMEM = WARPS * CPW * CLASS_FLOATS * 4;
-    static_assert(N % 4 == 0 && LD % 4 == 0, "16-byte shared-memory vectors");
-};
-
 // The row slot and the column pair of class u.
 __device__ __forceinline__ void class_slots(const PropArgs &a, long long u, int &srow, int &l, int &lb) {
     srow = (int)(u / a.col_slots);
@@ -117,87 +99,6 @@ __device__ __forceinline__ int perm_index(int i, int shift) {
     if (shift < 0 || i >= NE) return i;
     const int v = shift - i;
     return v < 0 ? v + NE : v;
-}
-
-// out = two * X + Y + A B for one class, N x N in shared memory: A, X, Y and
-// out column-major, B row-major (stride LD), Y may be null, out_row (if not
-// null) receives the result row-major too. Every lane of the warp calls this
-// together: the warp synchronises between the last read of the inputs and
-// the first write, so out and out_row may be inputs (products in place).
-// Register-blocked: lane t owns the TR x TC tile at rows (t % RB) TR, columns
-// (t / RB) TC, and per k loads the tile's slice of column k of A and of row k
-// of B with 16-byte loads (one or a few distinct addresses a warp).
-template <int N>
-struct GemmTile {
-    static constexpr int TR = N == 16 ? 4 : (N == 32 ? 8 : 16);
-    static constexpr int TC = N == 16 ? 4 : 8;
-    static constexpr int RB = N / TR;
-    static_assert((N / TR) * (N / TC) == PropCfg<N>::LPC, "one tile a lane");
-    static_assert(TR % 4 == 0 && TC % 4 == 0, "16-byte vectors");
-};
-
-template <int N>
-__device__ __forceinline__ void prop_gemm(const float *A, const float *Brow, const float *X, float two, const float *Y,
-                                          float *out, float *out_row, int t) {
-    using C = PropCfg<N>;
-    using Tl = GemmTile<N>;
-    const int r0 = (t % Tl::RB) * Tl::TR, c0 = (t / Tl::RB) * Tl::TC;
-    f32x2 acc[Tl::TC][Tl::TR / 2];
-#pragma unroll
-    for (int c = 0; c < Tl::TC; ++c)
-#pragma unroll
-        for (int i = 0; i < Tl::TR; i += 4) {
-            const float4 xv = *reinterpret_cast<const float4 *>(X + (c0 + c) * C::LD + r0 + i);
-            float4 yv = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (Y) yv = *reinterpret_cast<const float4 *>(Y + (c0 + c) * C::LD + r0 + i);
-            acc[c][i / 2] = pk2(fmaf(two, xv.x, yv.x), fmaf(two, xv.y, yv.y));
-            acc[c][i / 2 + 1] = pk2(fmaf(two, xv.z, yv.z), fmaf(two, xv.w, yv.w));
-        }
-#pragma unroll 2
-    for (int kk = 0; kk < N; ++kk) {
-        f32x2 av[Tl::TR / 2];
-#pragma unroll
-        for (int i = 0; i < Tl::TR; i += 4) {
-            const float4 v = *reinterpret_cast<const float4 *>(A + kk * C::LD + r0 + i);
-            av[i / 2] = pk2(v.x, v.y);
-            av[i / 2 + 1] = pk2(v.z, v.w);
-        }
-        float bv[Tl::TC];
-#pragma unroll
-        for (int c = 0; c < Tl::TC; c += 4) {
-            const float4 v = *reinterpret_cast<const float4 *>(Brow + kk * C::LD + c0 + c);
-            bv[c] = v.x;
-            bv[c + 1] = v.y;
-            bv[c + 2] = v.z;
-            bv[c + 3] = v.w;
-        }
-#pragma unroll
-        for (int c = 0; c < Tl::TC; ++c) {
-            const f32x2 s = dup2(bv[c]);
-#pragma unroll
-            for (int i = 0; i < Tl::TR / 2; ++i) acc[c][i] = fma2(av[i], s, acc[c][i]);
-        }
-    }
-    __syncwarp();
-#pragma unroll
-    for (int c = 0; c < Tl::TC; ++c)
-#pragma unroll
-        for (int i = 0; i < Tl::TR; i += 4)
-            *reinterpret_cast<float4 *>(out + (c0 + c) * C::LD + r0 + i) =
-                make_float4(lo2(acc[c][i / 2]), hi2(acc[c][i / 2]), lo2(acc[c][i / 2 + 1]), hi2(acc[c][i / 2 + 1]));
-    if (out_row) {
-#pragma unroll
-        for (int i = 0; i < Tl::TR; i += 2)
-#pragma unroll
-            for (int c = 0; c < Tl::TC; c += 4) {
-                *reinterpret_cast<float4 *>(out_row + (r0 + i) * C::LD + c0 + c) =
-                    make_float4(lo2(acc[c][i / 2]), lo2(acc[c + 1][i / 2]), lo2(acc[c + 2][i / 2]),
-                                lo2(acc[c + 3][i / 2]));
-                *reinterpret_cast<float4 *>(out_row + (r0 + i + 1) * C::LD + c0 + c) =
-                    make_float4(hi2(acc[c][i / 2]), hi2(acc[c + 1][i / 2]), hi2(acc[c + 2][i / 2]),
-                                hi2(acc[c + 3][i / 2]));
-            }
-    }
 }
 
 // x = A'^{-1} r and y = A'^{-1} s in place (N values each), with the torn
@@ -301,165 +202,7 @@ __device__ __forceinline__ void prop_store(const PropArgs &a, const float *Rm, l
     }
 }
 
-template <int N>
-__global__ void __launch_bounds__(PropCfg<N>::WARPS * 32) k_prop_build(const __grid_constant__ PropArgs a) {
-    using C = PropCfg<N>;
-    extern __shared__ __align__(16) float psm[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane / C::LPC, t = lane - g * C::LPC;
-    float *base = psm + (warp * C::CPW + g) * C::CLASS_FLOATS;
-    float *G = base + 3 * C::MAT;
-    float *q = G + N;
-    float *scal = q + N;  // 1/d0, 1/(1 + v.q)
-    const long long stride = (long long)gridDim.x * C::WARPS * C::CPW;
-    // classes are taken warp-uniformly so that every lane reaches each __syncwarp,
-    // warp-major over the grid: where the classes do not divide evenly, the
-    // warps that take one chunk more are spread over the blocks (and SMs)
-    // instead of filling the first blocks
-    for (long long u0 = ((long long)warp * gridDim.x + blockIdx.x) * C::CPW; u0 < a.items; u0 += stride) {
-        const bool live = u0 + g < a.items;
-        long long partner;
-        const long long u = build_class(a, live ? u0 + g : a.items - 1, partner);
-        int k, l, lb;
-        class_slots(a, u, k, l, lb);
-        const float wx = sin_2pi_frac(l, a.W), wy = sin_2pi_frac(k, a.H);
-        if (t == 0) prop_factor<N>(a, wx, wy, G, q, scal);
-        __syncwarp();
-        const float inv_d0 = scal[0], inv_den = scal[1];
-        // D_1, column by column: 2 A'^{-1} Lap e_c - 2 (a_c^2/beta) A'^{-1} e_c;
-        // pivots and q are read into registers once (broadcast loads)
-        // (N = 64 reads them from shared memory: four 64-entry arrays exceed the registers)
-        float *D1 = base;
-        constexpr int NR = N <= 32 ? N : 1;
-        float Gr[NR], qr[NR];
-        if constexpr (N <= 32) {
-#pragma unroll
-            for (int j = 0; j < N; j += 4) {
-                const float4 gv = *reinterpret_cast<const float4 *>(G + j);
-                const float4 qv = *reinterpret_cast<const float4 *>(q + j);
-                Gr[j] = gv.x; Gr[j + 1] = gv.y; Gr[j + 2] = gv.z; Gr[j + 3] = gv.w;
-                qr[j] = qv.x; qr[j + 1] = qv.y; qr[j + 2] = qv.z; qr[j + 3] = qv.w;
-            }
-        }
-        const float *Gs = N <= 32 ? Gr : G;
-        const float *qs = N <= 32 ? qr : q;
-#pragma unroll 1
-        for (int cc = 0; cc < C::CPL; ++cc) {
-            const int c = t + cc * C::LPC;
-            const float ar = fmaf(wx, a.cs[c], wy * a.sn[c]);
-            const float e2 = ar * ar * a.inv_beta;
-            const int cm = (c == 0) ? N - 1 : c - 1, cp = (c == N - 1) ? 0 : c + 1;
-            float x[N], y[N];
-#pragma unroll
-            for (int j = 0; j < N; ++j) {
-                x[j] = (j == c) ? 1.0f : 0.0f;
-                y[j] = (j == c) ? -2.0f : ((j == cm || j == cp) ? 1.0f : 0.0f);
-            }
-            prop_solve2<N>(x, y, Gs, qs, inv_d0, inv_den);
-            float *dc = D1 + c * C::LD;
-#pragma unroll
-            for (int j = 0; j < N; j += 4)
-                *reinterpret_cast<float4 *>(dc + j) =
-                    make_float4(fmaf(2.0f, y[j], -2.0f * e2 * x[j]), fmaf(2.0f, y[j + 1], -2.0f * e2 * x[j + 1]),
-                                fmaf(2.0f, y[j + 2], -2.0f * e2 * x[j + 2]), fmaf(2.0f, y[j + 3], -2.0f * e2 * x[j + 3]));
-        }
-        __syncwarp();
-        // and row-major (this lane's column c becomes entries c of every row)
-        float *D1r = base + C::MAT;
-#pragma unroll 1
-        for (int cc = 0; cc < C::CPL; ++cc) {
-            const int c = t + cc * C::LPC;
-#pragma unroll
-            for (int j = 0; j < N; ++j) D1r[j * C::LD + c] = D1[c * C::LD + j];
-        }
-        __syncwarp();
-        // the powering program: P (column- and row-major) starts as D_1, R
-        // (column-major) empty; products in place. Squaring R first copies R
-        // into both layouts of P (B's rows are read from the row-major copy:
-        // the products stay exact, not symmetric up to rounding).
-        float *P = base, *Pr = base + C::MAT, *R = base + 2 * C::MAT;
-#pragma unroll 1
-        for (int o = 0; o < a.chain_len; ++o) {
-            const int op = a.chain[o];
-            if (op == PROP_SQ_R) {
-#pragma unroll 1
-                for (int cc = 0; cc < C::CPL; ++cc) {
-                    const int c = t + cc * C::LPC;
-#pragma unroll 4
-                    for (int j = 0; j < N; ++j) {
-                        const float v = R[c * C::LD + j];
-                        P[c * C::LD + j] = v;
-                        Pr[j * C::LD + c] = v;
-                    }
-                }
-                __syncwarp();
-            }
-            if (op != PROP_COPY) {
-                // 2 P + P P into P (and Pr), or R + P + R P into R
-                const bool add = op == PROP_ADD;
-                const float *A = add ? R : P;
-                prop_gemm<N>(A, Pr, A, add ? 1.0f : 2.0f, add ? P : nullptr, add ? R : P, add ? nullptr : Pr, t);
-            } else {
-                // R = P: copy this lane's columns
-#pragma unroll 1
-                for (int cc = 0; cc < C::CPL; ++cc) {
-                    const int c = t + cc * C::LPC;
-#pragma unroll
-                    for (int j = 0; j < N; j += 4)
-                        *reinterpret_cast<float4 *>(R + c * C::LD + j) =
-                            *reinterpret_cast<const float4 *>(P + c * C::LD + j);
-                }
-            }
-            __syncwarp();
-        }
-        if (!a.chain_in_r) R = P;
-        // D_S symmetrised, and for a transposed partner P D_S P as well
-#pragma unroll 1
-        for (int pass = 0; pass < 2; ++pass) {
-            const long long v = pass ? partner : u;
-            const int sh = pass ? a.perm_shift : -1;
-            if (!live || v < 0) continue;
-            // as rows in 16-byte chunks stored chunk-major (D[i][4c .. 4c + 3]
-            // at float4 c N + i): this lane writes rows i = t, t + LPC, ...,
-            // consecutive lanes consecutive chunks
-            if (a.rows) {
-                float4 *out = reinterpret_cast<float4 *>(a.D + v * (long long)(N * N));
-#pragma unroll 1
-                for (int cc = 0; cc < C::CPL; ++cc) {
-                    const int i = t + cc * C::LPC, pi = perm_index<N>(i, sh);
-#pragma unroll 2
-                    for (int c = 0; c < N / 4; ++c) {
-                        float d[4];
-#pragma unroll
-                        for (int m = 0; m < 4; ++m) {
-                            const int j = perm_index<N>(4 * c + m, sh);
-                            d[m] = 0.5f * (R[j * C::LD + pi] + R[pi * C::LD + j]);
-                        }
-                        out[c * N + i] = make_float4(d[0], d[1], d[2], d[3]);
-                    }
-                }
-            } else {
-                // by cyclic diagonals: this lane writes S_m[i] for i = t, t +
-                // LPC, ... (R is column-major: D[i, j] = R[j LD + i]; without
-                // the permutation both reads run at stride LD + 1 across the
-                // lanes, free of bank conflicts)
-                float *out = a.D + v * (long long)C::SBLK;
-#pragma unroll 1
-                for (int cc = 0; cc < C::CPL; ++cc) {
-                    const int i = t + cc * C::LPC, pi = perm_index<N>(i, sh);
-#pragma unroll 4
-                    for (int m = 0; m <= N / 2; ++m) {
-                        const int j = perm_index<N>((i + m) & (N - 1), sh);
-                        out[m * N + i] = 0.5f * (R[j * C::LD + pi] + R[pi * C::LD + j]);
-                    }
-                }
-            }
-        }
-        __syncwarp();
-    }
-}
-
-// Build with symmetric products (N = 16, 32). Every matrix of the powering
+// Build with symmetric products (N = 16, 32; N = 64 below). Every matrix of the powering
 // is a function of the one symmetric operator of the class (D_1 = 2 A'^{-1} L
 // with A' = I/c - L), so all of them are symmetric and commute, and so are
 // the products D_m D_m and D_a D_b. A matrix is kept once, row-major (its
@@ -490,7 +233,7 @@ struct SymCfg {
     static constexpr int CLASS_FLOATS = 2 * MAT + 2 * N + 4;  // P, R, pivots, q, scalars
     static constexpr int SMEM = WARPS * CPW * CLASS_FLOATS * 4;
     static constexpr int SBLK = (N / 2 + 1) * N;
-    static_assert(N == 16 || N == 32, "8 x 8 tiles of 16 or 32");
+    static_assert(N == 16 || N == 32 || N == 64, "8 x 8 tiles of 16, 32 or 64");
     static_assert(N != 32 || CLASS_FLOATS % 32 == 4, "class bases 4 banks apart");
     // SKEW(b) for b = 0 .. 3: 0, 20, 4, 24 floats (N = 32), none at N = 16
     static __device__ __forceinline__ int skew(int b) { return N == 32 ? (0x18041400u >> (8 * b)) & 0xff : 0; }
@@ -518,9 +261,9 @@ struct SymCfg {
 
 // out = two * X + Y + A B on the upper-triangle tile (bi, bj) of this lane,
 // mirrored; A, B, X, Y, out symmetric N x N row-major (stride LD), Y may be
-// null, out may be an input (the warp synchronises between the reads and
-// the writes; every lane of the warp calls this together).
-template <int N>
+// null, out may be an input (the warp, or with BLOCK the block, synchronises
+// between the reads and the writes; every lane of it calls this together).
+template <int N, bool BLOCK = false>
 __device__ __forceinline__ void sym_gemm(const float *A, const float *B, const float *X, float two, const float *Y,
                                          float *out, int bi, int bj, bool active) {
     using C = SymCfg<N>;
@@ -561,7 +304,10 @@ __device__ __forceinline__ void sym_gemm(const float *A, const float *B, const f
             }
         }
     }
-    __syncwarp();
+    if constexpr (BLOCK)
+        __syncthreads();
+    else
+        __syncwarp();
     if (active) {
         float v[8][8];
 #pragma unroll
@@ -703,6 +449,125 @@ __global__ void __launch_bounds__(SymCfg<N>::WARPS * 32) k_prop_build_sym(const 
     }
 }
 
+// The symmetric build at N = 64: the 36 upper-triangle 8 x 8 tiles of a
+// product take 36 lanes, so a class spans two warps; three classes a
+// 128-thread block, synchronised block-wide. As at N = 16, 32, each matrix is
+// kept once (its rows are its columns) and every tile is written with its
+// transpose, so the result is exactly symmetric: two matrices a class
+// instead of the three of a full product kept column- and row-major, and 36
+// of the 64 tiles of a product computed.
+template <int N>
+struct SymWideCfg {
+    using S = SymCfg<N>;
+    static constexpr int THREADS = 128;
+    static constexpr int LPC = S::TILES;           // lanes a class
+    static constexpr int CPB = THREADS / LPC;      // classes a block
+    static constexpr int SMEM = CPB * S::CLASS_FLOATS * 4;
+};
+
+template <int N>
+__global__ void __launch_bounds__(SymWideCfg<N>::THREADS) k_prop_build_symw(const __grid_constant__ PropArgs a) {
+    using S = SymCfg<N>;
+    using C = SymWideCfg<N>;
+    extern __shared__ __align__(16) float psm[];
+    const int tid = threadIdx.x, cb = tid / C::LPC, t = tid - cb * C::LPC;
+    const bool active = cb < C::CPB;
+    int bi, bj;
+    S::tile(active ? t : 0, bi, bj);
+    float *base = psm + (active ? cb : 0) * S::CLASS_FLOATS;
+    float *P = base, *R = base + S::MAT;
+    float *G = base + 2 * S::MAT;
+    float *q = G + N;
+    float *scal = q + N;  // 1/d0, 1/(1 + v.q)
+    const long long stride = (long long)gridDim.x * C::CPB;
+    // classes are taken block-uniformly so that every thread reaches each barrier
+    for (long long u0 = (long long)blockIdx.x * C::CPB; u0 < a.items; u0 += stride) {
+        const bool live = active && u0 + cb < a.items;
+        long long partner;
+        const long long u = build_class(a, live ? u0 + cb : a.items - 1, partner);
+        int k, l, lb;
+        class_slots(a, u, k, l, lb);
+        const float wx = sin_2pi_frac(l, a.W), wy = sin_2pi_frac(k, a.H);
+        if (active && t == 0) prop_factor<N>(a, wx, wy, G, q, scal);
+        __syncthreads();
+        // D_1 column by column into R (R row c = column c); pivots and q are
+        // read from shared memory (their 2 N values exceed the registers)
+        if (active) {
+            const float inv_d0 = scal[0], inv_den = scal[1];
+#pragma unroll 1
+            for (int c = t; c < N; c += C::LPC) {
+                const float ar = fmaf(wx, a.cs[c], wy * a.sn[c]);
+                const float e2 = ar * ar * a.inv_beta;
+                const int cm = (c == 0) ? N - 1 : c - 1, cp = (c == N - 1) ? 0 : c + 1;
+                float x[N], y[N];
+#pragma unroll
+                for (int j = 0; j < N; ++j) {
+                    x[j] = (j == c) ? 1.0f : 0.0f;
+                    y[j] = (j == c) ? -2.0f : ((j == cm || j == cp) ? 1.0f : 0.0f);
+                }
+                prop_solve2<N>(x, y, G, q, inv_d0, inv_den);
+#pragma unroll
+                for (int j = 0; j < N; j += 4)
+                    *reinterpret_cast<float4 *>(R + S::at(c, j)) =
+                        make_float4(fmaf(2.0f, y[j], -2.0f * e2 * x[j]), fmaf(2.0f, y[j + 1], -2.0f * e2 * x[j + 1]),
+                                    fmaf(2.0f, y[j + 2], -2.0f * e2 * x[j + 2]),
+                                    fmaf(2.0f, y[j + 3], -2.0f * e2 * x[j + 3]));
+            }
+        }
+        __syncthreads();
+        // P = (R + R^T) / 2, rows of this lane (P[j][i] gets the same bits)
+        if (active) {
+#pragma unroll 1
+            for (int i = t; i < N; i += C::LPC)
+#pragma unroll 4
+                for (int j = 0; j < N; j += 4) {
+                    const float4 ri = *reinterpret_cast<const float4 *>(R + S::at(i, j));
+                    *reinterpret_cast<float4 *>(P + S::at(i, j)) =
+                        make_float4(0.5f * (ri.x + R[S::at(j, i)]), 0.5f * (ri.y + R[S::at(j + 1, i)]),
+                                    0.5f * (ri.z + R[S::at(j + 2, i)]), 0.5f * (ri.w + R[S::at(j + 3, i)]));
+                }
+        }
+        __syncthreads();
+        // the powering program: P starts as D_1, R empty
+#pragma unroll 1
+        for (int o = 0; o < a.chain_len; ++o) {
+            const int op = a.chain[o];
+            if (op != PROP_COPY) {
+                const bool add = op == PROP_ADD;
+                const float *A = op == PROP_SQ_P ? P : R;
+                sym_gemm<N, true>(A, add ? P : A, A, add ? 1.0f : 2.0f, add ? P : nullptr, add ? R : P, bi, bj,
+                                  active);
+            } else if (active) {
+#pragma unroll 1
+                for (int i = t; i < N; i += C::LPC)
+#pragma unroll 4
+                    for (int j = 0; j < N; j += 4)
+                        *reinterpret_cast<float4 *>(R + i * S::LD + j) =
+                            *reinterpret_cast<const float4 *>(P + i * S::LD + j);
+            }
+            __syncthreads();
+        }
+        prop_store<N>(a, a.chain_in_r ? R : P, u, live, t, C::LPC);
+        prop_store<N>(a, a.chain_in_r ? R : P, partner, live, t, C::LPC, a.perm_shift);
+        __syncthreads();
+    }
+}
+
+template <int N>
+cudaError_t launch_build_wide(const PropArgs &a, int num_sms, cudaStream_t s) {
+    using C = SymWideCfg<N>;
+    cudaError_t e = cudaFuncSetAttribute(k_prop_build_symw<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_prop_build_symw<N>, C::THREADS, C::SMEM);
+    if (e != cudaSuccess) return e;
+    long long blocks = (a.items + C::CPB - 1) / C::CPB;
+    const long long cap = (long long)num_sms * (per_sm > 0 ? per_sm : 1);
+    if (blocks > cap) blocks = cap;
+    k_prop_build_symw<N><<<(unsigned)blocks, C::THREADS, C::SMEM, s>>>(a);
+    return cudaGetLastError();
+}
+
 // x <- x + D_S x for the (up to eight) frequencies of every class. A lane
 // owns RPL rows of a class. It issues every global load it needs at once (its
 // rows' diagonal entries, coalesced across the lanes of the class, and its
@@ -726,7 +591,7 @@ struct ApplyCfg {
     // class regions 8 floats apart modulo 32 so that the classes of a warp
     // fall on different banks
     static constexpr int CLASS_FLOATS = ((DF + XF + 31) / 32) * 32 + 8;
-    static constexpr int SBLK = PropCfg<N>::SBLK;
+    static constexpr int SBLK = (N / 2 + 1) * N;  // stored floats a class (cyclic diagonals)
     static constexpr int SMEM = WARPS * CPW * CLASS_FLOATS * 4;
     static_assert(XF % 4 == 0 && (CLASS_FLOATS % 4) == 0, "16-byte vectors");
 };
@@ -847,12 +712,12 @@ cudaError_t launch_build_kernel(K kernel, const PropArgs &a, int num_sms, cudaSt
     return cudaGetLastError();
 }
 
-// N = 16, 32: symmetric products (NE = 30 angles padded to 32); N = 64: full
-// products (one warp a class)
+// symmetric products: N = 16, 32 (NE = 30 angles padded to 32) a class on
+// 10 or 3 lanes, N = 64 a class on 36 lanes across two warps
 template <int N, int NE = N>
 cudaError_t launch_build(const PropArgs &a, int num_sms, cudaStream_t s) {
     if constexpr (N == 64)
-        return launch_build_kernel<PropCfg<N>>(k_prop_build<N>, a, num_sms, s);
+        return launch_build_wide<N>(a, num_sms, s);
     else
         return launch_build_kernel<SymCfg<N>>(k_prop_build_sym<N, NE>, a, num_sms, s);
 }
@@ -1005,8 +870,8 @@ cudaError_t se2n_prop_prepare(int N) {
                                               se2n::ApplyCfg<32>::SMEM)
                        : cudaGetLastError();
         case 64:
-            return cudaFuncSetAttribute(se2n::k_prop_build<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        se2n::PropCfg<64>::SMEM) == cudaSuccess
+            return cudaFuncSetAttribute(se2n::k_prop_build_symw<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        se2n::SymWideCfg<64>::SMEM) == cudaSuccess
                        ? cudaFuncSetAttribute(se2n::k_prop_apply<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               se2n::ApplyCfg<64>::SMEM)
                        : cudaGetLastError();
