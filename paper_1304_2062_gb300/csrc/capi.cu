@@ -1180,9 +1180,13 @@ se2n_status batch_interval(se2n_batch *b, double Tr, bool half) {
 // With SE2N_DIFFUSE_PROPAGATOR, the images of one shape are integrated by
 // that shape's propagators when building them once and applying them to every
 // image and interval is estimated to cost less than the step-by-step kernel on
-// those images. The estimate uses this library's measured rates on a GB300
-// (512^2, N = 32): step kernel about 54 TFLOP/s at 22 flops an update, build
-// about 30 TFLOP/s at 2 N^3 flops a product, apply about 2 TB/s.
+// those images. The estimate uses this library's measured rates on a GB300:
+// the step kernel about 54 TFLOP/s at 22 flops an update; the build about
+// 22 TFLOP/s (N = 16, 32) and 28 TFLOP/s (N = 64) of the flops it executes
+// (the powering program's products, 2 N^3 flops each, on the 3 of 4, 10 of
+// 16 or 36 of 64 upper-triangle tiles, for the classes it builds: half of
+// them on square planes of the Hermitian half, whose transposed classes
+// share a build); the apply about 2 TB/s.
 void choose_propagators(se2n_batch *b) {
     const se2n_params &p = b->p;
     b->img_prop.assign(b->count, 0);
@@ -1193,17 +1197,21 @@ void choose_propagators(se2n_batch *b) {
     if (!prop_admissible(p.beta, p.T / p.rounds / p.steps)) return;
     const bool half = !p.full_spectrum;
     const int S = p.steps;
-    int products = -1;
-    for (int s = S; s; s >>= 1) products += 1 + (s & 1);  // squarings + combinations
-    products -= 1;
+    unsigned char ops[SE2N_PROP_CHAIN_MAX];
+    int len = 0, in_r = 0, products = 0;
+    if (se2n_prop_chain(S, ops, SE2N_PROP_CHAIN_MAX, &len, &in_r) != SE2N_OK) return;
+    for (int o = 0; o < len; ++o) products += ops[o] != PROP_COPY;
     for (se2n_plan *pl : b->plans) {
         int n_img = 0;
         for (int i = 0; i < b->count; ++i) n_img += b->plan_of[i] == pl;
         const double freqs = (double)pl->H * (half ? pl->W / 2 + 1 : pl->W);
-        const double N = pl->N;
-        const double steps_s = n_img * (double)p.rounds * freqs * N * S * 22.0 / 54e12;
+        const double N = se2n_prop_dim(pl->N);
+        const double steps_s = n_img * (double)p.rounds * freqs * pl->N * S * 22.0 / 54e12;
         const double classes = (double)se2n_prop_classes(pl->H, pl->W, half);
-        const double build_s = classes * products * 2.0 * N * N * N / 30e12;
+        const bool share_t = half && pl->H == pl->W && (pl->angle_conv == 0 || pl->N % 4 == 0);
+        const double built = share_t ? classes * 0.5 : classes;
+        const double tiles = N == 16 ? 3.0 / 4.0 : (N == 32 ? 10.0 / 16.0 : 36.0 / 64.0);
+        const double build_s = built * products * 2.0 * N * N * N * tiles / (N == 64 ? 28e12 : 22e12);
         const double apply_s = n_img * (double)p.rounds * (classes * 4.0 * N * (N / 2 + 1) + 16.0 * freqs * N) / 2e12;
         if (build_s + apply_s < steps_s) {
             // shapes the row and column passes cover take them (whole inpaints)
