@@ -660,8 +660,8 @@ def run_2048(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     stream = torch.cuda.Stream(dev)
-    w = synth.workload_2048()
-    ws = synth.workload_2048(stress=True)
+    w = synth.workload_2048(side=args.side)
+    ws = synth.workload_2048(stress=True, side=args.side)
     f32 = w.f.astype(np.float32)
     plan = se2n.se2n_plan_create(w.H, w.W, w.N, 0, stream)
     prop = args.diffusion == "propagator"
@@ -721,8 +721,8 @@ def run_2048(args, rank, world, local_rank):
         # 64 of every N = 64 product and mirrors them
         exec_flops = flops * 36 // 64
         roofline = {"bound": "alu",
-                    "kernel": f"k_prop_build_symw<{w.N}> ({items} classes computed, each also stored permuted for "
-                              "its transpose; FP32 symmetric products)",
+                    "kernel": f"k_prop_build_symw<{w.N}> ({items} classes computed, row slot <= column slot; a "
+                              "transposed class applies its transpose's rows; FP32 symmetric products)",
                     "achieved": round(exec_flops / b_s / 1e12, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
                     "frac": round(exec_flops / b_s / 1e12 / peak, 4), "traffic": None,
                     "avg_launch_ms": round(b_s * 1e3, 4), "flops_per_launch": exec_flops,
@@ -732,6 +732,19 @@ def run_2048(args, rank, world, local_rank):
                     "frac_full_product_equivalent": round(flops / b_s / 1e12 / peak, 4),
                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop/FMA x 2070 MHz (derived, not measured)",
                     "apply_avg_launch_ms": round(d_s * 1e3, 4)}
+        # the separate apply on the Hermitian half, tile by tile: the half
+        # spectrum in and out, and every built class's N x N rows once (a
+        # transposed class reads its transpose's rows, from L2 when the
+        # super-tile order works)
+        wc = w.W // 2 + 1
+        a_bytes = 2 * 8 * w.N * w.H * wc + 4 * w.N * w.N * items
+        hbm = _peaks().get("hbm_gbs")
+        roofline["apply"] = {"kernel": f"k_prop_apply_tiled<{w.N}>", "bound": "hbm", "avg_launch_ms": round(d_s * 1e3, 4),
+                             "bytes_per_launch": a_bytes,
+                             "bytes_basis": "8 N H (W/2 + 1) bytes in and out + 4 N^2 bytes a built class",
+                             "achieved": round(a_bytes / d_s / 1e9, 1), "peak": hbm, "unit": "GB/s",
+                             "frac": round(a_bytes / d_s / 1e9 / hbm, 4) if hbm else None,
+                             "peak_basis": "MEASURED_PEAKS.json hbm_gbs (copy, burst)"}
     else:
         achieved = FLOPS_PER_UPDATE * upd / d_s / 1e12
         roofline = {"bound": "alu", "kernel": f"k_diffuse_x2<{w.N},4,...> (packed FP32 pairs)",
@@ -755,7 +768,7 @@ def run_2048(args, rank, world, local_rank):
               "m2_updates_per_s": world * w.updates() / (ms / 1e3), "n_gpus": world, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
               "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-              "config": {"workload": "lines_patches_2048_N64: 2048x2048 lines plus textured patches, N=64, 85% "
+              "config": {"workload": f"{w.name}: {w.H}x{w.W} lines plus textured patches, N=64, 85% "
                                      "random mask, beta=0.25, T=50, one interval of 1000 CN steps",
                          "updates_per_step": upd, "m2_updates_per_step": w.updates(),
                          "diffusion": "S-step propagators (separate apply)" if prop else
@@ -774,7 +787,7 @@ def run_2048(args, rank, world, local_rank):
         err = {}
         bins_main = oracle.orient(f32.astype(np.float64), w.mask, w.N)["bins"]
         b_d = torch.tensor(bins_main, device=dev)
-        if os.path.exists(GOLDEN_2048):
+        if os.path.exists(GOLDEN_2048) and w.H == 2048:
             g = np.load(GOLDEN_2048)
             st = int(g["stride"][0])
             for name, wk, fl in (("main", w, flags), ("stiff_fp32", ws, 0), ("stiff_fp64", ws, se2n.SE2N_DIFFUSE_SM_FP64)):
@@ -1479,6 +1492,9 @@ def main():
     ap.add_argument("--diffusion", choices=["propagator", "steps"], default=None,
                     help="512 / dr / 2048: integrate each interval by S-step propagators built every inpaint (default) "
                          "or step by step with the fused Crank-Nicolson kernel")
+    ap.add_argument("--side", type=int, default=2048,
+                    help="2048: the same workload on a side x side image, a smaller case for profiling (the "
+                         "stored FP64 result it is compared with is for 2048 only)")
     ap.add_argument("--train-seconds", type=float, default=150.0, help="surrogate training time budget")
     ap.add_argument("--train-pairs", type=int, default=0, help="surrogate training pairs (0: all 20000)")
     ap.add_argument("--traffic", type=float, default=None,

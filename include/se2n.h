@@ -81,8 +81,10 @@ typedef enum se2n_status {
  * integration over an interval is one linear map). The same result as S
  * Crank-Nicolson steps up to rounding. The plan keeps the matrices
  * (symmetric; by cyclic diagonals, 4 N (N/2 + 1) bytes a class, or as rows,
- * 4 N^2 bytes a class, for the column pass below: about H W N^2 / 4 bytes in
- * all) and reuses them while beta dt, S, the spectrum half and the storage
+ * 4 N^2 bytes a class, for the column pass below and for N = 64 on the
+ * Hermitian half, where they are applied 16 classes of one row slot at a
+ * time: about H W N^2 / 4 bytes in all) and reuses them while beta dt, S,
+ * the spectrum half and the storage
  * stay the same, so the intervals of one inpaint build them once. N = 16,
  * 30, 32 or 64 (else SE2N_EUNSUPPORTED); N = 30 is built and stored as
  * 32 x 32 matrices whose last two rows and columns are zero (the bytes of

@@ -104,9 +104,9 @@ namespace {
 
 // Device memory for the plan's propagators (grown when too small, which
 // invalidates them).
-se2n_status prop_reserve(se2n_plan *plan, bool half, bool rows = false) {
+se2n_status prop_reserve(se2n_plan *plan, bool half, int fmt) {
     const size_t need =
-        (size_t)se2n_prop_classes(plan->H, plan->W, half) * (size_t)se2n_prop_floats(plan->N, rows) * sizeof(float);
+        (size_t)se2n_prop_classes(plan->H, plan->W, half) * (size_t)se2n_prop_floats(plan->N, fmt) * sizeof(float);
     if (plan->prop_bytes >= need) return SE2N_OK;
     cudaFree(plan->prop_D);
     plan->prop_D = nullptr;
@@ -122,10 +122,10 @@ se2n_status prop_reserve(se2n_plan *plan, bool half, bool rows = false) {
     return SE2N_OK;
 }
 
-PropArgs prop_args(se2n_plan *plan, float2 *vol, double beta, double bdt, int steps, bool half, bool rows) {
+PropArgs prop_args(se2n_plan *plan, float2 *vol, double beta, double bdt, int steps, bool half, int fmt) {
     PropArgs a{};
     a.vol = vol;
-    a.rows = rows ? 1 : 0;
+    a.rows = fmt;
     a.H = plan->H;
     a.W = plan->W;
     a.Wc = half ? plan->Wc : plan->W;
@@ -191,19 +191,19 @@ bool prop_admissible(double beta, double dt) { return dt * (2.0 + 4.0 * beta) <=
 // runs on the plan's side stream after everything queued on the plan's
 // stream so far (it reads nothing that work writes), overlapping what the
 // plan's stream does next until prop_join.
-se2n_status prop_ensure(se2n_plan *plan, double beta, double bdt, int steps, bool half, bool rows,
+se2n_status prop_ensure(se2n_plan *plan, double beta, double bdt, int steps, bool half, int fmt,
                         bool side = false) {
     if (!se2n_prop_supported(plan->N)) return SE2N_EUNSUPPORTED;
-    SE2N_TRY(prop_reserve(plan, half, rows));
+    SE2N_TRY(prop_reserve(plan, half, fmt));
     if (plan->prop_valid && plan->prop_beta == beta && plan->prop_bdt == bdt && plan->prop_steps == steps &&
-        plan->prop_half == half && plan->prop_rows == rows)
+        plan->prop_half == half && plan->prop_fmt == fmt)
         return SE2N_OK;
     plan->prop_valid = false;
     if (plan->chain_steps != steps) {
         SE2N_TRY(se2n_prop_chain(steps, plan->chain, SE2N_PROP_CHAIN_MAX, &plan->chain_len, &plan->chain_in_r));
         plan->chain_steps = steps;
     }
-    PropArgs a = prop_args(plan, nullptr, beta, bdt, steps, half, rows);
+    PropArgs a = prop_args(plan, nullptr, beta, bdt, steps, half, fmt);
     std::copy(plan->chain, plan->chain + plan->chain_len, a.chain);
     a.chain_len = plan->chain_len;
     a.chain_in_r = plan->chain_in_r;
@@ -230,15 +230,17 @@ se2n_status prop_ensure(se2n_plan *plan, double beta, double bdt, int steps, boo
     plan->prop_bdt = bdt;
     plan->prop_steps = steps;
     plan->prop_half = half;
-    plan->prop_rows = rows;
+    plan->prop_fmt = fmt;
     return SE2N_OK;
 }
 
-// The propagators applied once to the spectrum vol (by diagonals).
+// The propagators applied once to the spectrum vol (by diagonals, or tile
+// by tile from rows: se2n_prop_apply_fmt).
 se2n_status propagate_impl(se2n_plan *plan, float2 *vol, double beta, double bdt, int steps, bool half) {
-    SE2N_TRY(prop_ensure(plan, beta, bdt, steps, half, false));
+    const int fmt = se2n_prop_apply_fmt(plan->N, half);
+    SE2N_TRY(prop_ensure(plan, beta, bdt, steps, half, fmt));
     prop_join(plan);
-    const PropArgs a = prop_args(plan, vol, beta, bdt, steps, half, false);
+    const PropArgs a = prop_args(plan, vol, beta, bdt, steps, half, fmt);
     StageTimer timer(plan, SE2N_STAGE_DIFFUSE);
     plan->kernels += 1;
     return cuda_status(plan, se2n_launch_prop_apply(plan->N, a, plan->num_sms, plan->stream));
@@ -298,7 +300,7 @@ se2n_status col_start(se2n_plan *plan, const se2n_params *p) {
     SE2N_TRY(col_ensure(plan));
     const double bdt = p->beta * (p->T / p->rounds) / p->steps;
     if (p->T > 0.0 && bdt >= 1e-30 && bdt <= 1e3)
-        SE2N_TRY(prop_ensure(plan, p->beta, bdt, p->steps, true, true, true));
+        SE2N_TRY(prop_ensure(plan, p->beta, bdt, p->steps, true, PROP_CHUNKS, true));
     return SE2N_OK;
 }
 
@@ -342,7 +344,7 @@ se2n_status col_diffuse(se2n_plan *plan, double beta, double T, int steps) {
     if (T == 0.0) return SE2N_OK;
     const double bdt = beta * (T / steps);
     if (!(bdt >= 1e-30 && bdt <= 1e3)) return SE2N_ENUMERIC;
-    SE2N_TRY(prop_ensure(plan, beta, bdt, steps, true, true));
+    SE2N_TRY(prop_ensure(plan, beta, bdt, steps, true, PROP_CHUNKS));
     prop_join(plan);
     ColArgs a;
     a.col = plan->colbuf;
@@ -1212,7 +1214,12 @@ void choose_propagators(se2n_batch *b) {
         const double built = share_t ? classes * 0.5 : classes;
         const double tiles = N == 16 ? 3.0 / 4.0 : (N == 32 ? 10.0 / 16.0 : 36.0 / 64.0);
         const double build_s = built * products * 2.0 * N * N * N * tiles / (N == 64 ? 28e12 : 22e12);
-        const double apply_s = n_img * (double)p.rounds * (classes * 4.0 * N * (N / 2 + 1) + 16.0 * freqs * N) / 2e12;
+        // the apply: by diagonals (about 2 TB/s), or tile by tile from the
+        // built classes' rows (N = 64 on the half: 3.05 TB/s measured at 1024 x 1024)
+        const double apply_s =
+            se2n_prop_apply_fmt(pl->N, half) == PROP_ROWS
+                ? n_img * (double)p.rounds * (built * 4.0 * N * N + 16.0 * freqs * N) / 3e12
+                : n_img * (double)p.rounds * (classes * 4.0 * N * (N / 2 + 1) + 16.0 * freqs * N) / 2e12;
         if (build_s + apply_s < steps_s) {
             // shapes the row and column passes cover take them (whole inpaints)
             const bool fused = col_path(pl, &p);
@@ -1499,10 +1506,10 @@ se2n_status create_batch(se2n_batch *b, const se2n_image_desc *imgs) {
             // everything the whole inpaints allocate or create, before the capture
             SE2N_TRY(col_ensure(pl));
             SE2N_TRY(side_ensure(pl));
-            SE2N_TRY(prop_reserve(pl, true, true));
+            SE2N_TRY(prop_reserve(pl, true, PROP_CHUNKS));
             if (b->p.dynamic) SE2N_TRY(dr_alloc(pl->dr, pl->HW));
         } else {
-            SE2N_TRY(prop_reserve(pl, !b->p.full_spectrum));
+            SE2N_TRY(prop_reserve(pl, !b->p.full_spectrum, se2n_prop_apply_fmt(pl->N, !b->p.full_spectrum)));
         }
         if (se2n_prop_prepare(pl->N) != cudaSuccess) return SE2N_ECUDA;
         pl->prop_valid = false;

@@ -170,14 +170,23 @@ template <int N>
 struct SymCfg;
 
 // D_S of class u from a symmetric matrix in the layout of SymCfg<N>: as rows
-// in 16-byte chunks, chunk-major, or by cyclic diagonals; lanes t of `lanes`.
-// shift >= 0 stores the permuted matrix P D_S P of a transposed class.
+// in 16-byte chunks, chunk-major (PROP_CHUNKS), row-major (PROP_ROWS) or by
+// cyclic diagonals; lanes t of `lanes`. shift >= 0 stores the permuted matrix
+// P D_S P of a transposed class, which PROP_ROWS leaves out (the tiled apply
+// reads the built class).
 template <int N, int NE = N>
 __device__ __forceinline__ void prop_store(const PropArgs &a, const float *Rm, long long u, bool live, int t,
                                            int lanes, int shift = -1) {
     using C = SymCfg<N>;
     if (!live || u < 0) return;
-    if (a.rows) {
+    if (a.rows == PROP_ROWS) {
+        if (shift >= 0) return;  // (N angles only: se2n_prop_apply_fmt)
+        float4 *out = reinterpret_cast<float4 *>(a.D + u * (long long)(N * N));
+        for (int e = t; e < N * N / 4; e += lanes) {
+            const int i = e / (N / 4), c = e - i * (N / 4);
+            out[e] = *reinterpret_cast<const float4 *>(Rm + C::at(i, 4 * c));
+        }
+    } else if (a.rows == PROP_CHUNKS) {
         // for the column pass: row i, columns 4c .. 4c + 3 as slots (an
         // NE-angle system at the slots of slot_of_angle)
         float4 *out = reinterpret_cast<float4 *>(a.D + u * (long long)(N * N));
@@ -697,6 +706,235 @@ __global__ void __launch_bounds__(ApplyCfg<N>::WARPS * 32) k_prop_apply(const __
     }
 }
 
+// The apply on the Hermitian half at N = 64, tile by tile. A tile is one row
+// slot times CT = 16 consecutive column slots: 16 classes, 128 frequencies.
+// Its vectors come in as runs of 16 consecutive columns of one row of one
+// angle plane (128 bytes) and go back the same way, so every access to the
+// volume is coalesced, where a class on its own touches 8 bytes in each of
+// 512 places. In shared memory a class is [N slots][8 frequencies] complex,
+// and the slot of angle r folds in the reversal of rows 2, 3 and, for a
+// transposed class (share_t, row slot > column slot), the permutation P: such
+// a class applies P D P with D the propagator of its transpose, built and
+// stored once, as x + P D P x = P (P x + D (P x)). D_S is stored row-major;
+// its row j is its column j (symmetric), so the eight lanes (rb) that hold
+// rows 4 rb .. 4 rb + 3 and N/2 + 4 rb .. N/2 + 4 rb + 3 read column j of
+// their rows as one coalesced 128-byte run. A warp applies one class: lane
+// (rb, mp) accumulates its eight rows for frequencies 2 mp and 2 mp + 1, two
+// rows a packed FMA, with x_j of both frequencies one 16-byte broadcast from
+// shared memory; the sums run over j in slot order and x is added last.
+// Tiles go in super-tiles of 32 x 32 classes, each (above the diagonal)
+// followed by its transpose, so the transposed classes find their
+// propagators in L2.
+template <int N>
+struct TileCfg {
+    static constexpr int CT = 16;                  // column slots (classes) a tile
+    static constexpr int WARPS = 8;                // a class a warp at a time
+    static constexpr int THREADS = WARPS * 32;
+    static constexpr int QF = 16 * N;              // floats a class: [N slots][8 frequencies] complex
+    static constexpr int SMEM = CT * QF * 4;
+    static constexpr int SUPER = 32;               // row and column slots a side of a super-tile
+    static constexpr int SUPER_BLOCKS = SUPER * (SUPER / CT);
+    static constexpr int GROUPS = THREADS / CT;    // runs loaded at once
+    static constexpr int LOADS = 8 * N / GROUPS;   // (row, side, angle) runs a thread
+    static_assert(N == 64, "eight rows a lane: 4 rb .. 4 rb + 3 and N/2 + 4 rb ..");
+    static_assert(N % GROUPS == 0 && CT % WARPS == 0, "runs and classes");
+};
+
+// Tile of block b: row slot srow, column slots c0 .. c0 + CT - 1; false for
+// the padding blocks of the super-tile grid.
+template <int N>
+__device__ __forceinline__ bool tile_of_block(const PropArgs &a, long long b, int &srow, int &c0) {
+    using C = TileCfg<N>;
+    const int n = a.col_slots, nr = row_slots(a.H);
+    if (!a.share_t) {
+        const int tr = (n + C::CT - 1) / C::CT;
+        srow = (int)(b / tr);
+        c0 = (int)(b - (long long)srow * tr) * C::CT;
+        return srow < nr;
+    }
+    // super-tiles column by column: (I, J) and (J, I) for I < J, then (J, J);
+    // the J^2 super-tiles of columns < J come first
+    const long long sg = b / C::SUPER_BLOCKS;
+    const int w = (int)(b - sg * C::SUPER_BLOCKS);
+    long long J = (long long)sqrt((double)sg);
+    while (J * J > sg) --J;
+    while ((J + 1) * (J + 1) <= sg) ++J;
+    const long long p = sg - J * J;
+    long long R = J, Cs = J;
+    if (p < 2 * J) {
+        if (p & 1) Cs = p >> 1;
+        else R = p >> 1;
+    }
+    srow = (int)(R * C::SUPER) + w / (C::SUPER / C::CT);
+    c0 = (int)(Cs * C::SUPER) + (w % (C::SUPER / C::CT)) * C::CT;
+    return srow < nr && c0 < n;
+}
+
+long long tiled_blocks(const PropArgs &a) {
+    constexpr int CT = 16, SUPER = 32;
+    const long long n = a.col_slots, nr = row_slots(a.H);
+    if (!a.share_t) return nr * ((n + CT - 1) / CT);
+    const long long sb = (n + SUPER - 1) / SUPER;
+    return sb * sb * (long long)SUPER * (SUPER / CT);
+}
+
+template <int N>
+__global__ void __launch_bounds__(TileCfg<N>::THREADS, 2) k_prop_apply_tiled(const __grid_constant__ PropArgs a) {
+    using C = TileCfg<N>;
+    extern __shared__ __align__(16) float tsm[];
+    int srow, c0;
+    if (!tile_of_block<N>(a, blockIdx.x, srow, c0)) return;
+    const int tid = threadIdx.x, n = a.col_slots;
+    int k[4];
+    bool kon[4];
+    slot_rows(srow, a.H, k, kon);
+    // the propagator a class of the tile reads: its own, or its transpose's
+    auto built = [&](int q) -> long long {
+        const long long sc = c0 + q;
+        return a.share_t && srow > sc ? sc * n + srow : (long long)srow * n + sc;
+    };
+    // into L2 while the vectors come in: 16 threads a class, 8 lines each
+    {
+        const int q = tid / (C::THREADS / C::CT), t = tid % (C::THREADS / C::CT);
+        if (c0 + q < n) {
+            const char *Dq = reinterpret_cast<const char *>(a.D + built(q) * (long long)(N * N));
+#pragma unroll
+            for (int i = 0; i < N * N * 4 / 128 / (C::THREADS / C::CT); ++i)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(Dq + (t + i * (C::THREADS / C::CT)) * 128));
+        }
+    }
+    // Element (slot a, frequency m) of class q: 16-float row a ^ qh ^ (bit 2
+    // of a), 16-byte unit ((m ^ qm) >> 1) ^ (bits 3, 4 of a), float pair
+    // (m ^ qm) & 1, with qh = bit 3 of q and qm its low three bits. The 16
+    // lanes of a run (one slot and m, 16 classes) fall on 16 different pairs
+    // of banks, and the eight rows 4 rb + c (rb = 0 .. 7) of one unit that a
+    // quarter-warp updates at the end on eight different groups of four.
+    // m = 2 (row of the class) + side (0: column l, 1: column W/2 - l).
+    const int q = tid % C::CT, g = tid / C::CT;
+    const int sc = c0 + q, l = sc, lb = a.W / 2 - sc;
+    const bool qlive = sc < n;
+    const bool tq = a.share_t && srow > sc;
+    const int qh = (q >> 3) & 1, qm = q & 7;
+    float *xq = tsm + q * C::QF;
+    auto xrow = [](int a, int h) { return a ^ h ^ ((a >> 2) & 1); };
+    auto xunit = [](int a, int u) { return u ^ ((a >> 3) & 3); };
+    auto xpos = [&](int a, int m, int h, int mm) {
+        return xrow(a, h) * 16 + 4 * xunit(a, (m ^ mm) >> 1) + 2 * ((m ^ mm) & 1);
+    };
+    // run it of this thread: angle r = g + GROUPS (it mod (N / GROUPS)), m = it / (N / GROUPS)
+    constexpr int RPM = N / C::GROUPS;
+    auto run_ok = [&](int m) { return qlive && kon[m >> 1] && ((m & 1) == 0 || lb != l); };
+    auto run_src = [&](int m, int r) -> long long {
+        return (long long)r * a.HW + (long long)k[m >> 1] * a.Wc + ((m & 1) ? lb : l);
+    };
+    auto run_slot = [&](int m, int r) -> int {
+        const bool neg = ((m >> 1) >= 2) != tq;
+        return ((tq ? a.perm_shift : 0) + (neg ? -r : r)) & (N - 1);
+    };
+    {
+        float2 v[C::LOADS];
+#pragma unroll
+        for (int it = 0; it < C::LOADS; ++it) {
+            const int m = it / RPM, r = g + C::GROUPS * (it % RPM);
+            v[it] = run_ok(m) ? a.vol[run_src(m, r)] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int it = 0; it < C::LOADS; ++it) {
+            const int m = it / RPM, r = g + C::GROUPS * (it % RPM);
+            *reinterpret_cast<float2 *>(xq + xpos(run_slot(m, r), m, qh, qm)) = v[it];
+        }
+    }
+    __syncthreads();
+    {
+        const int warp = tid >> 5, lane = tid & 31, rb = lane & 7, mp = lane >> 3;
+#pragma unroll 1
+        for (int cq = warp; cq < C::CT; cq += C::WARPS) {
+            if (c0 + cq >= n) break;  // warp-uniform
+            const int ch = (cq >> 3) & 1, cm = cq & 7;
+            float *xc = tsm + cq * C::QF;
+            const int uu = mp ^ (cm >> 1);  // the 16-byte unit of frequencies 2 mp, 2 mp + 1
+            const ulonglong2 *Dr = reinterpret_cast<const ulonglong2 *>(a.D + built(cq) * (long long)(N * N)) + rb;
+            // acc[h][p][f]: rows 4 (rb + 8 h) + 2 p, + 1 (a pair); f = the
+            // unit's four floats (re, im of its two frequencies)
+            f32x2 acc[2][2][4];
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int p = 0; p < 2; ++p)
+#pragma unroll
+                    for (int f = 0; f < 4; ++f) acc[h][p][f] = pk2(0.f, 0.f);
+            // rows j .. j + 3 of D in flight while the four before are used
+            ulonglong2 d[2][4][2];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) d[0][jj][h] = __ldg(Dr + jj * (N / 4) + 8 * h);
+            // row j0 + jl of an 8-row block at xj + (jx ^ ch) 16, jx = jl ^ (bit 2 of jl)
+            const int ro = ch * 16;
+            auto chunk = [&](const float *xj, int cur) {
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    const int jl = jj + 4 * cur, jx = jl ^ ((jl >> 2) & 1);
+                    const float4 xv = *reinterpret_cast<const float4 *>(xj + (jx & ~1) * 16 + ((jx & 1) ? 16 - ro : ro));
+                    const f32x2 xs[4] = {dup2(xv.x), dup2(xv.y), dup2(xv.z), dup2(xv.w)};
+#pragma unroll
+                    for (int h = 0; h < 2; ++h)
+#pragma unroll
+                        for (int f = 0; f < 4; ++f) {
+                            acc[h][0][f] = fma2(d[cur][jj][h].x, xs[f], acc[h][0][f]);
+                            acc[h][1][f] = fma2(d[cur][jj][h].y, xs[f], acc[h][1][f]);
+                        }
+                }
+            };
+#pragma unroll 1
+            for (int j0 = 0; j0 < N; j0 += 8) {
+                // rows j0 + 8 .. j0 + 15 into L1 (16 lines), two loads ahead
+                if (lane < 16 && j0 + 8 < N)
+                    asm volatile("prefetch.global.L1 [%0];" ::"l"(Dr - rb + (j0 + 8 + (lane >> 1)) * (N / 4) +
+                                                                   8 * (lane & 1)));
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) d[1][jj][h] = __ldg(Dr + (j0 + 4 + jj) * (N / 4) + 8 * h);
+                const float *xj = xc + j0 * 16 + 4 * xunit(j0, uu);
+                chunk(xj, 0);
+                if (j0 + 8 < N) {
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) d[0][jj][h] = __ldg(Dr + (j0 + 8 + jj) * (N / 4) + 8 * h);
+                }
+                chunk(xj, 1);
+            }
+            __syncwarp();
+            // x <- x + D x on the lane's rows, in place
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int p = 0; p < 2; ++p)
+#pragma unroll
+                    for (int o = 0; o < 2; ++o) {
+                        const int row = 4 * (rb + 8 * h) + 2 * p + o;
+                        float4 *px = reinterpret_cast<float4 *>(xc + xrow(row, ch) * 16 + 4 * xunit(row, uu));
+                        float4 x = *px;
+                        x.x += o ? hi2(acc[h][p][0]) : lo2(acc[h][p][0]);
+                        x.y += o ? hi2(acc[h][p][1]) : lo2(acc[h][p][1]);
+                        x.z += o ? hi2(acc[h][p][2]) : lo2(acc[h][p][2]);
+                        x.w += o ? hi2(acc[h][p][3]) : lo2(acc[h][p][3]);
+                        *px = x;
+                    }
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < C::LOADS; ++it) {
+        const int m = it / RPM, r = g + C::GROUPS * (it % RPM);
+        if (run_ok(m))
+            a.vol[run_src(m, r)] = *reinterpret_cast<const float2 *>(xq + xpos(run_slot(m, r), m, qh, qm));
+    }
+}
+
 template <typename C, typename K>
 cudaError_t launch_build_kernel(K kernel, const PropArgs &a, int num_sms, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
@@ -720,6 +958,18 @@ cudaError_t launch_build(const PropArgs &a, int num_sms, cudaStream_t s) {
         return launch_build_wide<N>(a, num_sms, s);
     else
         return launch_build_kernel<SymCfg<N>>(k_prop_build_sym<N, NE>, a, num_sms, s);
+}
+
+template <int N>
+cudaError_t launch_apply_tiled(const PropArgs &a, cudaStream_t s) {
+    using C = TileCfg<N>;
+    cudaError_t e = cudaFuncSetAttribute(k_prop_apply_tiled<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return e;
+    const long long blocks = tiled_blocks(a);
+    if (blocks <= 0) return cudaSuccess;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    k_prop_apply_tiled<N><<<(unsigned)blocks, C::THREADS, C::SMEM, s>>>(a);
+    return cudaGetLastError();
 }
 
 template <int N, int NE = N>
@@ -838,10 +1088,12 @@ bool se2n_prop_supported(int N) { return N == 16 || N == 30 || N == 32 || N == 6
 // N = 30 is stored padded to 32 angles (zero rows and columns 30, 31)
 int se2n_prop_dim(int N) { return N == 30 ? 32 : N; }
 
-long long se2n_prop_floats(int N, bool rows) {
+long long se2n_prop_floats(int N, int fmt) {
     const long long n = se2n_prop_dim(N);
-    return rows ? n * n : (n / 2 + 1) * n;
+    return fmt != PROP_DIAGONALS ? n * n : (n / 2 + 1) * n;
 }
+
+int se2n_prop_apply_fmt(int N, bool half) { return half && N == 64 ? PROP_ROWS : PROP_DIAGONALS; }
 
 int se2n_prop_col_slots(int W, bool half) { return half ? W / 4 + 1 : se2n::pair_rows(W); }
 
@@ -872,8 +1124,10 @@ cudaError_t se2n_prop_prepare(int N) {
         case 64:
             return cudaFuncSetAttribute(se2n::k_prop_build_symw<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         se2n::SymWideCfg<64>::SMEM) == cudaSuccess
-                       ? cudaFuncSetAttribute(se2n::k_prop_apply<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              se2n::ApplyCfg<64>::SMEM)
+                           && cudaFuncSetAttribute(se2n::k_prop_apply<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   se2n::ApplyCfg<64>::SMEM) == cudaSuccess
+                       ? cudaFuncSetAttribute(se2n::k_prop_apply_tiled<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              se2n::TileCfg<64>::SMEM)
                        : cudaGetLastError();
         default: return cudaErrorInvalidValue;
     }
@@ -894,7 +1148,8 @@ cudaError_t se2n_launch_prop_apply(int N, const PropArgs &a, int num_sms, cudaSt
         case 16: return se2n::launch_apply<16>(a, num_sms, s);
         case 32: return se2n::launch_apply<32>(a, num_sms, s);
         case 30: return se2n::launch_apply<32, 30>(a, num_sms, s);
-        case 64: return se2n::launch_apply<64>(a, num_sms, s);
+        case 64:
+            return a.rows == PROP_ROWS ? se2n::launch_apply_tiled<64>(a, s) : se2n::launch_apply<64>(a, num_sms, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -50,7 +50,7 @@ struct se2n_plan {
     double prop_beta, prop_bdt;
     int prop_steps;
     bool prop_half;
-    bool prop_rows;        // stored as full rows (the column pass) or by diagonals
+    int prop_fmt;          // storage: PROP_DIAGONALS, PROP_CHUNKS or PROP_ROWS
     // the powering program of S = chain_steps (0: none yet)
     int chain_steps;
     unsigned char chain[SE2N_PROP_CHAIN_MAX];
@@ -113,11 +113,17 @@ struct DiffuseArgs {
 //   PROP_COPY  R <- P
 enum PropOp : unsigned char { PROP_SQ_P = 0, PROP_SQ_R = 1, PROP_ADD = 2, PROP_COPY = 3 };
 
+// Storage of the propagators of a plan (PropArgs::rows).
+enum : int {
+    PROP_DIAGONALS = 0,  // [classes][N/2 + 1][N] cyclic diagonals (the apply of the full spectrum)
+    PROP_CHUNKS = 1,     // [classes][N/4][N] float4: row i's entries 4c .. 4c + 3 at float4 c N + i
+                         // (the column pass)
+    PROP_ROWS = 2        // [classes][N][N] row-major, built classes only (the tiled apply)
+};
+
 struct PropArgs {
-    float *D;          // D_S = (B-^{-1} B+)^S - I a class: [classes][N/2 + 1][N] cyclic
-                       // diagonals, or when rows != 0 [classes][N/4][N] float4:
-                       // row i's entries 4c .. 4c + 3 at float4 c N + i
-    int rows;          // storage of D (build only; the apply reads diagonals)
+    float *D;          // D_S = (B-^{-1} B+)^S - I a class, stored as `rows` says
+    int rows;          // PROP_DIAGONALS, PROP_CHUNKS or PROP_ROWS
     float2 *vol;       // [N][H][Wc] complex (apply only)
     int H, W, Wc;
     long long HW;      // H * Wc
@@ -126,6 +132,7 @@ struct PropArgs {
     // classes the build computes: all of them, or with share_t (square
     // planes, Hermitian half) the row slot <= column slot ones, each also
     // stored permuted for its transpose, angle r -> (perm_shift - r) mod N
+    // (not with PROP_ROWS: the tiled apply permutes the vectors instead)
     long long items;
     int share_t;
     int perm_shift;
@@ -143,7 +150,10 @@ struct PropArgs {
 };
 bool se2n_prop_supported(int N);  // 16, 30 (stored as 32), 32, 64
 int se2n_prop_dim(int N);          // angles of the stored propagator
-long long se2n_prop_floats(int N, bool rows = false);  // stored floats a class
+long long se2n_prop_floats(int N, int fmt = PROP_DIAGONALS);  // stored floats a class
+// The storage se2n_launch_prop_apply reads: PROP_ROWS for the tiled apply
+// (Hermitian half, N = 64), else PROP_DIAGONALS.
+int se2n_prop_apply_fmt(int N, bool half);
 int se2n_prop_col_slots(int W, bool half);
 long long se2n_prop_classes(int H, int W, bool half);
 // Set the kernels' shared-memory attributes for N (before a graph capture).

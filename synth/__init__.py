@@ -236,16 +236,18 @@ def workload_batch(count=256, seed=3, sides=(128, 256, 384, 512, 768, 1024), Ns=
     return out
 
 
-def workload_2048(stress=False, seed=4):
+def workload_2048(stress=False, seed=4, side=2048):
     """2048x2048 lines-plus-texture image, N=64, 85 % of the pixels masked,
     1000 fused steps. Main run: beta=0.25, T=50 (dt=0.05); stress run:
-    beta=10, dt=1, so beta*dt=10."""
-    H = W = 2048
+    beta=10, dt=1, so beta*dt=10. `side` draws the same recipe on a smaller
+    square image (for profiling a smaller case)."""
+    H = W = side
     clean = lines_patches_image(H, W, seed)
     mask = bernoulli_mask(H, W, seed + 1000, 0.85)
     if stress:
-        return Workload("lines_patches_2048_N64_stress", clean, mask, N=64, beta=10.0, T=1000.0, steps=1000, rounds=1)
-    return Workload("lines_patches_2048_N64", clean, mask, N=64, beta=0.25, T=50.0, steps=1000, rounds=1)
+        return Workload(f"lines_patches_{side}_N64_stress", clean, mask, N=64, beta=10.0, T=1000.0, steps=1000,
+                        rounds=1)
+    return Workload(f"lines_patches_{side}_N64", clean, mask, N=64, beta=0.25, T=50.0, steps=1000, rounds=1)
 
 
 # the surrogate's data: the 64x64 generator at 256x256, half of the pixels

@@ -140,6 +140,36 @@ def test_square_inpaint_on_the_passes_with_either_angle_grid(N, conv):
     assert rel_l2(got, ref) <= REL_L2
 
 
+@pytest.mark.parametrize("H,W,conv", [(136, 136, 0), (136, 136, 1), (72, 136, 0), (136, 72, 0), (20, 20, 1),
+                                      (64, 64, 0)])
+def test_tiled_apply_N64_on_the_hermitian_half(H, W, conv):
+    """N = 64 on the Hermitian half: the propagators stored as rows (a
+    square plane builds only the classes with row slot <= column slot) and
+    applied a tile of 16 column slots at a time, a transposed class through
+    the permuted vectors. 136 x 136 has 35 row and column slots: two
+    super-tiles a side, the second ragged, and a ragged last tile in every
+    row slot."""
+    w = synth.workload_512(H=H, W=W, steps=60, rounds=3)
+    p = oracle.Params(N=64, beta=0.25, T=6.0, steps=60, rounds=3, angle_conv=conv)
+    f32 = w.f.astype(np.float32)
+    f64 = f32.astype(np.float64)
+    bins = oracle.orient(f64, w.mask, p.N, p.sigma, conv, p.flat_tol)["bins"]
+    ref = oracle.inpaint(f64, w.mask, p, bins=bins)["out"]
+    plan = se2n.se2n_plan_create(H, W, 64, conv)
+    se2n.se2n_plan_profile(plan, True)
+    vol = torch.empty((64, H, W), dtype=torch.complex64, device="cuda")
+    out = torch.empty((H, W), dtype=torch.float32, device="cuda")
+    se2n.se2n_inpaint(plan, t_f32(f32), t_u8(w.mask), t_u8(bins), _params(p), vol, out)
+    got = host(out)
+    prof = se2n.se2n_plan_profile_read(plan)
+    plan.close()
+    mx = np.abs(got - ref).max() / np.abs(f64).max()
+    print(f"{H}x{W} N=64 conv={conv}: max-abs/max|f| {mx:.2e}, rel-L2 {rel_l2(got, ref):.2e}")
+    assert prof["propagator"][1] == 1 and prof["diffuse"][1] == 3
+    assert mx <= MAX_REL
+    assert rel_l2(got, ref) <= REL_L2
+
+
 def test_lifted_image_spectrum():
     """The workload's shape: the DFT of a lifted image, dominated by the low
     frequencies, 500 steps."""
