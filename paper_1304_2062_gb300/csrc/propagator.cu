@@ -237,7 +237,11 @@ struct SymCfg {
     static constexpr int NT = N / 8;                 // tiles a side
     static constexpr int TILES = NT * (NT + 1) / 2;  // upper-triangle tiles: lanes a class
     static constexpr int CPW = 32 / TILES;           // classes a warp
-    static constexpr int LD = N + 4;                 // row stride, floats
+    // row stride, floats; at N = 64 columns 32 .. 63 sit 4 floats further
+    // on, so that the 16-byte pieces at columns 8 b and 8 b + 4 (b = 0 .. 7)
+    // that the eight lanes of a quarter-warp read in a product fall on
+    // eight different groups of four banks
+    static constexpr int LD = N == 64 ? 72 : N + 4;
     static constexpr int MAT = N * LD;
     static constexpr int CLASS_FLOATS = 2 * MAT + 2 * N + 4;  // P, R, pivots, q, scalars
     static constexpr int SMEM = WARPS * CPW * CLASS_FLOATS * 4;
@@ -246,7 +250,9 @@ struct SymCfg {
     static_assert(N != 32 || CLASS_FLOATS % 32 == 4, "class bases 4 banks apart");
     // SKEW(b) for b = 0 .. 3: 0, 20, 4, 24 floats (N = 32), none at N = 16
     static __device__ __forceinline__ int skew(int b) { return N == 32 ? (0x18041400u >> (8 * b)) & 0xff : 0; }
-    static __device__ __forceinline__ int at(int i, int j) { return i * LD + ((j + skew(i >> 3)) & (N - 1)); }
+    static __device__ __forceinline__ int at(int i, int j) {
+        return N == 64 ? i * LD + j + 4 * (j >> 5) : i * LD + ((j + skew(i >> 3)) & (N - 1));
+    }
     // tile (bi, bj) = (TILE[t] / 4, TILE[t] mod 4) of lane t (N = 32), TILE =
     // 4 bi + bj of (2,3) (0,2) (1,2) (0,0) (2,2) (0,1) (1,3) (0,3) (3,3) (1,1),
     // four bits each
@@ -550,7 +556,7 @@ __global__ void __launch_bounds__(SymWideCfg<N>::THREADS) k_prop_build_symw(cons
 #pragma unroll 1
                 for (int i = t; i < N; i += C::LPC)
 #pragma unroll 4
-                    for (int j = 0; j < N; j += 4)
+                    for (int j = 0; j < S::LD; j += 4)
                         *reinterpret_cast<float4 *>(R + i * S::LD + j) =
                             *reinterpret_cast<const float4 *>(P + i * S::LD + j);
             }
@@ -718,7 +724,10 @@ __global__ void __launch_bounds__(ApplyCfg<N>::WARPS * 32) k_prop_apply(const __
 // stored once, as x + P D P x = P (P x + D (P x)). D_S is stored row-major;
 // its row j is its column j (symmetric), so the eight lanes (rb) that hold
 // rows 4 rb .. 4 rb + 3 and N/2 + 4 rb .. N/2 + 4 rb + 3 read column j of
-// their rows as one coalesced 128-byte run. A warp applies one class: lane
+// their rows as one 128-byte run. Rows of D come in four at a time (1 KB)
+// by asynchronous copies into a ring of four slots a warp, three ahead of
+// the rows in use, so that 48 KB of them are in flight on an SM at a time
+// without registers to hold them. A warp applies one class: lane
 // (rb, mp) accumulates its eight rows for frequencies 2 mp and 2 mp + 1, two
 // rows a packed FMA, with x_j of both frequencies one 16-byte broadcast from
 // shared memory; the sums run over j in slot order and x is added last.
@@ -731,7 +740,8 @@ struct TileCfg {
     static constexpr int WARPS = 8;                // a class a warp at a time
     static constexpr int THREADS = WARPS * 32;
     static constexpr int QF = 16 * N;              // floats a class: [N slots][8 frequencies] complex
-    static constexpr int SMEM = CT * QF * 4;
+    static constexpr int R = 4;                    // ring slots of 4 rows of D a warp
+    static constexpr int SMEM = CT * QF * 4 + WARPS * R * 4 * N * 4;
     static constexpr int SUPER = 32;               // row and column slots a side of a super-tile
     static constexpr int SUPER_BLOCKS = SUPER * (SUPER / CT);
     static constexpr int GROUPS = THREADS / CT;    // runs loaded at once
@@ -739,6 +749,17 @@ struct TileCfg {
     static_assert(N == 64, "eight rows a lane: 4 rb .. 4 rb + 3 and N/2 + 4 rb ..");
     static_assert(N % GROUPS == 0 && CT % WARPS == 0, "runs and classes");
 };
+
+__device__ __forceinline__ void cp_async16(float *dst, const float *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
+}
 
 // Tile of block b: row slot srow, column slots c0 .. c0 + CT - 1; false for
 // the padding blocks of the super-tile grid.
@@ -847,13 +868,25 @@ __global__ void __launch_bounds__(TileCfg<N>::THREADS, 2) k_prop_apply_tiled(con
     __syncthreads();
     {
         const int warp = tid >> 5, lane = tid & 31, rb = lane & 7, mp = lane >> 3;
+        float *ring = tsm + C::CT * C::QF + warp * (C::R * 4 * N);
 #pragma unroll 1
         for (int cq = warp; cq < C::CT; cq += C::WARPS) {
             if (c0 + cq >= n) break;  // warp-uniform
             const int ch = (cq >> 3) & 1, cm = cq & 7;
             float *xc = tsm + cq * C::QF;
             const int uu = mp ^ (cm >> 1);  // the 16-byte unit of frequencies 2 mp, 2 mp + 1
-            const ulonglong2 *Dr = reinterpret_cast<const ulonglong2 *>(a.D + built(cq) * (long long)(N * N)) + rb;
+            // rows 4 c .. 4 c + 3 of D (1 KB, contiguous) into ring slot c mod R,
+            // 16 bytes a copy, one commit group a chunk (empty past the end)
+            const float *Dq = a.D + built(cq) * (long long)(N * N);
+            auto issue = [&](int c) {
+                if (c < N / 4) {
+#pragma unroll
+                    for (int p = lane; p < N; p += 32) cp_async16(ring + (c % C::R) * (4 * N) + 4 * p, Dq + c * (4 * N) + 4 * p);
+                }
+                cp_async_commit();
+            };
+#pragma unroll
+            for (int c = 0; c < C::R - 1; ++c) issue(c);
             // acc[h][p][f]: rows 4 (rb + 8 h) + 2 p, + 1 (a pair); f = the
             // unit's four floats (re, im of its two frequencies)
             f32x2 acc[2][2][4];
@@ -863,48 +896,30 @@ __global__ void __launch_bounds__(TileCfg<N>::THREADS, 2) k_prop_apply_tiled(con
                 for (int p = 0; p < 2; ++p)
 #pragma unroll
                     for (int f = 0; f < 4; ++f) acc[h][p][f] = pk2(0.f, 0.f);
-            // rows j .. j + 3 of D in flight while the four before are used
-            ulonglong2 d[2][4][2];
-#pragma unroll
-            for (int jj = 0; jj < 4; ++jj)
-#pragma unroll
-                for (int h = 0; h < 2; ++h) d[0][jj][h] = __ldg(Dr + jj * (N / 4) + 8 * h);
-            // row j0 + jl of an 8-row block at xj + (jx ^ ch) 16, jx = jl ^ (bit 2 of jl)
-            const int ro = ch * 16;
-            auto chunk = [&](const float *xj, int cur) {
+#pragma unroll 1
+            for (int c = 0; c < N / 4; ++c) {
+                cp_async_wait<C::R - 2>();  // this lane's copies of chunk c
+                __syncwarp();               // everyone's, and chunk c - 1 read by all
+                issue(c + C::R - 1);
+                const float *dc = ring + (c % C::R) * (4 * N) + 4 * rb;
+                // row 4 c + jj of x: 16-float row 4 c + (jj ^ e), e = ch ^ (c & 1)
+                const float *xj = xc + 4 * c * 16 + 4 * xunit(4 * c, uu);
+                const int ro = (ch ^ (c & 1)) * 16;
 #pragma unroll
                 for (int jj = 0; jj < 4; ++jj) {
-                    const int jl = jj + 4 * cur, jx = jl ^ ((jl >> 2) & 1);
-                    const float4 xv = *reinterpret_cast<const float4 *>(xj + (jx & ~1) * 16 + ((jx & 1) ? 16 - ro : ro));
+                    const float4 xv = *reinterpret_cast<const float4 *>(xj + (jj & 2) * 16 + ((jj & 1) ? 16 - ro : ro));
                     const f32x2 xs[4] = {dup2(xv.x), dup2(xv.y), dup2(xv.z), dup2(xv.w)};
 #pragma unroll
-                    for (int h = 0; h < 2; ++h)
+                    for (int h = 0; h < 2; ++h) {
+                        // column 4 c + jj of rows 4 (rb + 8 h) .. + 3 (D is symmetric)
+                        const ulonglong2 dd = *reinterpret_cast<const ulonglong2 *>(dc + jj * N + 32 * h);
 #pragma unroll
                         for (int f = 0; f < 4; ++f) {
-                            acc[h][0][f] = fma2(d[cur][jj][h].x, xs[f], acc[h][0][f]);
-                            acc[h][1][f] = fma2(d[cur][jj][h].y, xs[f], acc[h][1][f]);
+                            acc[h][0][f] = fma2(dd.x, xs[f], acc[h][0][f]);
+                            acc[h][1][f] = fma2(dd.y, xs[f], acc[h][1][f]);
                         }
+                    }
                 }
-            };
-#pragma unroll 1
-            for (int j0 = 0; j0 < N; j0 += 8) {
-                // rows j0 + 8 .. j0 + 15 into L1 (16 lines), two loads ahead
-                if (lane < 16 && j0 + 8 < N)
-                    asm volatile("prefetch.global.L1 [%0];" ::"l"(Dr - rb + (j0 + 8 + (lane >> 1)) * (N / 4) +
-                                                                   8 * (lane & 1)));
-#pragma unroll
-                for (int jj = 0; jj < 4; ++jj)
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) d[1][jj][h] = __ldg(Dr + (j0 + 4 + jj) * (N / 4) + 8 * h);
-                const float *xj = xc + j0 * 16 + 4 * xunit(j0, uu);
-                chunk(xj, 0);
-                if (j0 + 8 < N) {
-#pragma unroll
-                    for (int jj = 0; jj < 4; ++jj)
-#pragma unroll
-                        for (int h = 0; h < 2; ++h) d[0][jj][h] = __ldg(Dr + (j0 + 8 + jj) * (N / 4) + 8 * h);
-                }
-                chunk(xj, 1);
             }
             __syncwarp();
             // x <- x + D x on the lane's rows, in place
