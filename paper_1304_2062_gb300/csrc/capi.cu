@@ -1344,6 +1344,41 @@ se2n_status enqueue_batch_half(se2n_batch *b) {
     return SE2N_OK;
 }
 
+// With every image on propagators, the images of one shape touch only that
+// shape's plan (its buffers, transforms and propagators) and their own
+// volumes, so the shapes are independent: each runs its images in turn (the
+// sequence se2n_inpaint enqueues for one image) on a stream of its own,
+// forked from the batch's stream and joined back to it, and the graph holds
+// the shapes side by side where one stream would run every kernel of every
+// image one after another.
+bool batch_by_shape(const se2n_batch *b) {
+    return !b->p.full_spectrum && b->prop_images == b->count && b->plans.size() > 1;
+}
+
+se2n_status enqueue_by_shape(se2n_batch *b, const std::vector<cudaStream_t> &ss, const std::vector<cudaEvent_t> &evs,
+                             cudaEvent_t fork) {
+    if (cudaEventRecord(fork, b->stream) != cudaSuccess) return SE2N_ECUDA;
+    se2n_status st = SE2N_OK;
+    size_t forked = 0;
+    for (; forked < b->plans.size() && st == SE2N_OK; ++forked) {
+        if (cudaStreamWaitEvent(ss[forked], fork, 0) != cudaSuccess) st = SE2N_ECUDA;
+        if (st == SE2N_OK) st = se2n_plan_set_stream(b->plans[forked], ss[forked]);
+    }
+    for (int i = 0; i < b->count && st == SE2N_OK; ++i) {
+        se2n_params q = b->p;
+        q.N = b->imgs[i].N;
+        st = inpaint_impl(b->plan_of[i], b->imgs[i].f, b->imgs[i].mask, b->imgs[i].bins, &q, b->vols[i],
+                          b->imgs[i].out, b->img_fused[i]);
+    }
+    // every forked stream joins back, also after an error, so that the capture ends
+    for (size_t k = 0; k < forked; ++k) {
+        if (cudaEventRecord(evs[k], ss[k]) != cudaSuccess || cudaStreamWaitEvent(b->stream, evs[k], 0) != cudaSuccess)
+            st = SE2N_ECUDA;
+        if (se2n_plan_set_stream(b->plans[k], b->stream) != SE2N_OK && st == SE2N_OK) st = SE2N_ECUFFT;
+    }
+    return st;
+}
+
 se2n_status enqueue_batch(se2n_batch *b) {
     const se2n_params &p = b->p;
     if (!p.full_spectrum) return enqueue_batch_half(b);
@@ -1519,11 +1554,42 @@ se2n_status create_batch(se2n_batch *b, const se2n_image_desc *imgs) {
     } else {
         SE2N_TRY(set_shape(b, 0, 8, 256));
     }
-    // capture the whole method into a graph
-    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SE2N_ECUDA;
-    se2n_status st = enqueue_batch(b);
+    // capture the whole method into a graph: the shapes side by side when
+    // they are independent (their streams and events exist for the capture only)
+    const bool by_shape = batch_by_shape(b);
+    std::vector<cudaStream_t> ss;
+    std::vector<cudaEvent_t> evs;
+    cudaEvent_t fork = nullptr;
+    auto release = [&]() {
+        for (cudaStream_t x : ss) cudaStreamDestroy(x);
+        for (cudaEvent_t x : evs) cudaEventDestroy(x);
+        if (fork) cudaEventDestroy(fork);
+    };
+    if (by_shape) {
+        if (b->p.dynamic)
+            for (se2n_plan *pl : b->plans) SE2N_TRY(dr_alloc(pl->dr, pl->HW));
+        bool ok = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess;
+        for (size_t k = 0; k < b->plans.size() && ok; ++k) {
+            cudaStream_t x = nullptr;
+            cudaEvent_t e = nullptr;
+            ok = cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) == cudaSuccess;
+            if (ok) ss.push_back(x);
+            ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+            if (ok) evs.push_back(e);
+        }
+        if (!ok) {
+            release();
+            return SE2N_ECUDA;
+        }
+    }
+    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        release();
+        return SE2N_ECUDA;
+    }
+    se2n_status st = by_shape ? enqueue_by_shape(b, ss, evs, fork) : enqueue_batch(b);
     cudaGraph_t g = nullptr;
     cudaError_t ce = cudaStreamEndCapture(b->stream, &g);
+    release();
     if (st != SE2N_OK) {
         if (g) cudaGraphDestroy(g);
         return st;
