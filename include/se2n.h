@@ -432,7 +432,10 @@ typedef struct se2n_batch_info {
  * in p->diffuse_flags, the images of each distinct (H, W, N) are integrated
  * by that shape's S-step propagators (built once a run, shared by the images)
  * when that is estimated to cost less than stepping them, the others by the
- * persistent step-by-step kernel; se2n_batch_get_info reports how many. */
+ * persistent step-by-step kernel; se2n_batch_get_info reports how many.
+ * When every image takes propagators (on the Hermitian half), the graph runs
+ * the shapes side by side: each shape's images in turn, as se2n_inpaint
+ * runs one image, on a branch of their own. */
 SE2N_API se2n_status se2n_batch_create(se2n_batch **out, const se2n_image_desc *imgs, int count,
                                        const se2n_params *p, int angle_conv, int flags, void *stream);
 
