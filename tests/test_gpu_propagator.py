@@ -141,14 +141,15 @@ def test_square_inpaint_on_the_passes_with_either_angle_grid(N, conv):
 
 
 @pytest.mark.parametrize("H,W,conv", [(136, 136, 0), (136, 136, 1), (72, 136, 0), (136, 72, 0), (20, 20, 1),
-                                      (64, 64, 0)])
+                                      (64, 64, 0), (22, 22, 1), (26, 18, 0)])
 def test_tiled_apply_N64_on_the_hermitian_half(H, W, conv):
     """N = 64 on the Hermitian half: the propagators stored as rows (a
     square plane builds only the classes with row slot <= column slot) and
     applied a tile of 16 column slots at a time, a transposed class through
     the permuted vectors. 136 x 136 has 35 row and column slots: two
     super-tiles a side, the second ragged, and a ragged last tile in every
-    row slot."""
+    row slot; sides of 4m + 2 pair columns l, W/2 - l with W/2 odd (no
+    self-paired column) and have no self-paired row."""
     w = synth.workload_512(H=H, W=W, steps=60, rounds=3)
     p = oracle.Params(N=64, beta=0.25, T=6.0, steps=60, rounds=3, angle_conv=conv)
     f32 = w.f.astype(np.float32)
