@@ -731,9 +731,9 @@ __global__ void __launch_bounds__(ApplyCfg<N>::WARPS * 32) k_prop_apply(const __
 // (rb, mp) accumulates its eight rows for frequencies 2 mp and 2 mp + 1, two
 // rows a packed FMA, with x_j of both frequencies one 16-byte broadcast from
 // shared memory; the sums run over j in slot order and x is added last.
-// Tiles go in super-tiles of 32 x 32 classes, each (above the diagonal)
-// followed by its transpose, so the transposed classes find their
-// propagators in L2.
+// Tiles go in super-tiles of 16 x 16 classes (one tile wide), each (above
+// the diagonal) followed by its transpose, so the transposed classes find
+// their propagators in L2.
 template <int N>
 struct TileCfg {
     static constexpr int CT = 16;                  // column slots (classes) a tile
@@ -742,7 +742,7 @@ struct TileCfg {
     static constexpr int QF = 16 * N;              // floats a class: [N slots][8 frequencies] complex
     static constexpr int R = 4;                    // ring slots of 4 rows of D a warp
     static constexpr int SMEM = CT * QF * 4 + WARPS * R * 4 * N * 4;
-    static constexpr int SUPER = 32;               // row and column slots a side of a super-tile
+    static constexpr int SUPER = 16;               // row and column slots a side of a super-tile
     static constexpr int SUPER_BLOCKS = SUPER * (SUPER / CT);
     static constexpr int GROUPS = THREADS / CT;    // runs loaded at once
     static constexpr int LOADS = 8 * N / GROUPS;   // (row, side, angle) runs a thread
@@ -792,7 +792,7 @@ __device__ __forceinline__ bool tile_of_block(const PropArgs &a, long long b, in
 }
 
 long long tiled_blocks(const PropArgs &a) {
-    constexpr int CT = 16, SUPER = 32;
+    constexpr int CT = 16, SUPER = 16;
     const long long n = a.col_slots, nr = row_slots(a.H);
     if (!a.share_t) return nr * ((n + CT - 1) / CT);
     const long long sb = (n + SUPER - 1) / SUPER;
