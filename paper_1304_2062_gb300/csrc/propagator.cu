@@ -959,7 +959,10 @@ cudaError_t launch_build_kernel(K kernel, const PropArgs &a, int num_sms, cudaSt
     if (e != cudaSuccess) return e;
     const long long per_block = (long long)C::WARPS * C::CPW;
     long long blocks = (a.items + per_block - 1) / per_block;
-    const long long cap = (long long)num_sms * (per_sm > 0 ? per_sm : 1);
+    // every block slot but one on an eighth of the SMs: the build runs on a
+    // side stream beside the orientation and the first row pass, whose
+    // kernels would otherwise wait for the build's blocks to leave
+    const long long cap = (long long)num_sms * (per_sm > 0 ? per_sm : 1) - (per_sm > 1 ? num_sms / 8 : 0);
     if (blocks > cap) blocks = cap;
     kernel<<<(unsigned)blocks, C::WARPS * 32, C::SMEM, s>>>(a);
     return cudaGetLastError();
