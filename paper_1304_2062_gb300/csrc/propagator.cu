@@ -791,12 +791,14 @@ __device__ __forceinline__ bool tile_of_block(const PropArgs &a, long long b, in
     return srow < nr && c0 < n;
 }
 
+// blocks of the launch: every tile, or the whole super-tile grid
+template <int N>
 long long tiled_blocks(const PropArgs &a) {
-    constexpr int CT = 16, SUPER = 16;
+    using C = TileCfg<N>;
     const long long n = a.col_slots, nr = row_slots(a.H);
-    if (!a.share_t) return nr * ((n + CT - 1) / CT);
-    const long long sb = (n + SUPER - 1) / SUPER;
-    return sb * sb * (long long)SUPER * (SUPER / CT);
+    if (!a.share_t) return nr * ((n + C::CT - 1) / C::CT);
+    const long long sb = (n + C::SUPER - 1) / C::SUPER;
+    return sb * sb * (long long)C::SUPER_BLOCKS;
 }
 
 template <int N>
@@ -983,7 +985,7 @@ cudaError_t launch_apply_tiled(const PropArgs &a, cudaStream_t s) {
     using C = TileCfg<N>;
     cudaError_t e = cudaFuncSetAttribute(k_prop_apply_tiled<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
-    const long long blocks = tiled_blocks(a);
+    const long long blocks = tiled_blocks<N>(a);
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
     k_prop_apply_tiled<N><<<(unsigned)blocks, C::THREADS, C::SMEM, s>>>(a);
