@@ -183,9 +183,13 @@ class ClockSampler:
 KERNEL_SOURCES = {"diffuse": ("diffuse_impl.cuh", "diffuse_x2.cuh", "diffuse.cu"),
                   "prop_build": ("propagator.cu", "prop_classes.cuh", "diffuse_x2.cuh", "diffuse_impl.cuh"),
                   "col_prop": ("colprop.cu", "bulk_copy.cuh", "rowdft.cuh", "smem_fft.cuh", "prop_classes.cuh", "diffuse_x2.cuh"),
-                  "row_pass": ("rowfft.cu", "smem_fft.cuh", "restore.cuh")}
+                  "row_pass": ("rowfft.cu", "smem_fft.cuh", "restore.cuh"),
+                  "prop_build_wide": ("propagator.cu", "prop_classes.cuh", "diffuse_x2.cuh", "diffuse_impl.cuh"),
+                  "prop_apply_tiled": ("propagator.cu", "prop_classes.cuh", "diffuse_x2.cuh", "diffuse_impl.cuh")}
 TRAFFIC_FILES = {"diffuse": "diffuse_traffic.json", "prop_build": "prop_build_traffic.json",
-                 "col_prop": "col_prop_traffic.json", "row_pass": "row_pass_traffic.json"}
+                 "col_prop": "col_prop_traffic.json", "row_pass": "row_pass_traffic.json",
+                 "prop_build_wide": "prop_build_wide_traffic.json",
+                 "prop_apply_tiled": "prop_apply_tiled_traffic.json"}
 
 
 def kernel_source_hash(kind="diffuse"):
@@ -199,16 +203,21 @@ def kernel_source_hash(kind="diffuse"):
     return h.hexdigest()[:16]
 
 
-def stored_traffic(kind="diffuse"):
-    """DRAM bytes per launch of the kernel from the committed ncu summary, or
-    None if it was taken on a different kernel source."""
+def stored_record(kind):
+    """The committed ncu traffic record of the kernel, or None if it was taken
+    on a different kernel source."""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", TRAFFIC_FILES[kind])))
     except (OSError, ValueError):
         return None
-    if rec.get("kernel_source_hash") != kernel_source_hash(kind):
-        return None
-    return rec.get("dram_bytes_per_launch")
+    return rec if rec.get("kernel_source_hash") == kernel_source_hash(kind) else None
+
+
+def stored_traffic(kind="diffuse"):
+    """DRAM bytes per launch of the kernel from the committed ncu summary, or
+    None if it was taken on a different kernel source."""
+    rec = stored_record(kind)
+    return rec.get("dram_bytes_per_launch") if rec else None
 
 
 def propagator_gemm_flops(classes, N, S):
@@ -720,11 +729,18 @@ def run_2048(args, rank, world, local_rank):
         # the symmetric build computes the 36 upper-triangle 8 x 8 tiles of the
         # 64 of every N = 64 product and mirrors them
         exec_flops = flops * 36 // 64
+        # DRAM traffic from a one-launch capture of a smaller square plane of
+        # the same workload, scaled to this launch by the classes built (the
+        # build) and by the method's bytes (the apply)
+        rec_b, rec_a = stored_record("prop_build_wide"), stored_record("prop_apply_tiled")
+        b_traffic = round(rec_b["dram_bytes_per_launch"] * items / rec_b["classes_built"]) if rec_b else None
         roofline = {"bound": "alu",
                     "kernel": f"k_prop_build_symw<{w.N}> ({items} classes computed, row slot <= column slot; a "
                               "transposed class applies its transpose's rows; FP32 symmetric products)",
                     "achieved": round(exec_flops / b_s / 1e12, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
-                    "frac": round(exec_flops / b_s / 1e12 / peak, 4), "traffic": None,
+                    "frac": round(exec_flops / b_s / 1e12 / peak, 4), "traffic": b_traffic,
+                    "traffic_basis": (f"ncu on {rec_b['workload']} ({rec_b['dram_bytes_per_launch']} bytes, "
+                                      f"{rec_b['classes_built']} classes) x classes built") if rec_b else None,
                     "avg_launch_ms": round(b_s * 1e3, 4), "flops_per_launch": exec_flops,
                     "flops_basis": f"executed flops: classes x {products} products x 2 N^3 x 36/64 (the upper-triangle "
                                    "8x8 tiles)",
@@ -741,6 +757,11 @@ def run_2048(args, rank, world, local_rank):
         hbm = _peaks().get("hbm_gbs")
         roofline["apply"] = {"kernel": f"k_prop_apply_tiled<{w.N}>", "bound": "hbm", "avg_launch_ms": round(d_s * 1e3, 4),
                              "bytes_per_launch": a_bytes,
+                             "traffic": round(rec_a["dram_bytes_per_launch"] * a_bytes / rec_a["method_bytes"])
+                             if rec_a else None,
+                             "traffic_basis": (f"ncu on {rec_a['workload']} ({rec_a['dram_bytes_per_launch']} bytes for "
+                                               f"{rec_a['method_bytes']} method's bytes) x method's bytes")
+                             if rec_a else None,
                              "bytes_basis": "8 N H (W/2 + 1) bytes in and out + 4 N^2 bytes a built class",
                              "achieved": round(a_bytes / d_s / 1e9, 1), "peak": hbm, "unit": "GB/s",
                              "frac": round(a_bytes / d_s / 1e9 / hbm, 4) if hbm else None,
